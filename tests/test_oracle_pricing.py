@@ -1,0 +1,143 @@
+"""Pins of the pricing step (Section 2.2.2): best opening per MLC row, CP
+price, best CP, and the leaf-travel windows (Eq. 2 compatibility reading)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def brute_best_opening(row, Lmin, Lmax, Rmin, Rmax):
+    """All feasible [L, R) by explicit loops; key (v desc, width, centredness, L)."""
+    N = len(row)
+    P = [0.0]
+    for p in row:
+        P.append(P[-1] + float(p))
+    best = None
+    for L in range(N + 1):
+        for R in range(L, N + 1):
+            if not (Lmin <= L <= Lmax and Rmin <= R <= Rmax):
+                continue
+            key = (-(P[R] - P[L]), R - L, abs(L + R - N), L)
+            if best is None or key < best[0]:
+                best = (key, P[R] - P[L], L, R)
+    if best is None:
+        return None, -1, -1
+    return best[1], best[2], best[3]
+
+
+def test_worked_row():
+    # [1, 3) collects 2 + 3 = 5; [4, 5) gives 4; [1, 5) gives 4
+    assert oracle.best_opening(np.float32([-1, 2, 3, -5, 4]), 0, 5, 0, 5) == (5.0, 1, 3)
+
+
+def test_all_negative_row_closes_centred():
+    v, L, R = oracle.best_opening(np.float32([-1, -2, -3, -4, -5]), 0, 5, 0, 5)
+    assert (v, L, R) == (0.0, 2, 2)
+    assert oracle.best_opening(np.zeros(4, np.float32), 0, 4, 0, 4) == (0.0, 2, 2)
+
+
+def test_equal_value_prefers_narrow():
+    # [0, 1) = 2 and [0, 3) = 2: the narrower wins
+    assert oracle.best_opening(np.float32([2, -1, 1]), 0, 3, 0, 3) == (2.0, 0, 1)
+
+
+def test_windows_can_force_negative_row():
+    # L forced to 0 and R forced to >= 2 around a negative region
+    v, L, R = oracle.best_opening(np.float32([-1, -1, 3, -1]), 0, 0, 2, 4)
+    assert (L, R) == (0, 3) and v == 1.0
+
+
+def test_prefix_sum_is_sequential():
+    rng = np.random.default_rng(1)
+    row = rng.normal(size=97).astype(np.float32) * np.float32(1e3)
+    P = oracle.prefix_sums(row)
+    acc = 0.0
+    for c, p in enumerate(row):
+        acc = acc + float(p)
+        assert P[c + 1] == acc  # bitwise: same order of float64 additions
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_best_opening_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    N = int(rng.integers(1, 13))
+    for _ in range(40):
+        row = rng.integers(-3, 4, size=N).astype(np.float32)   # small integers: many ties
+        if rng.random() < 0.5:
+            a, b = sorted(rng.integers(0, N + 1, 2))
+            c, d = sorted(rng.integers(0, N + 1, 2))
+        else:
+            a, b, c, d = 0, N, 0, N
+        got = oracle.best_opening(row, a, b, c, d)
+        want = brute_best_opening(row, a, b, c, d)
+        assert got == want
+
+
+def tiny_mlc(K=6, n_rows=3, n_cols=4, arcs=(0,), travel=1):
+    return synth.MLC(K, n_rows, n_cols, np.array(arcs, np.int32), travel)
+
+
+def test_cp_price_is_best_over_all_aperture_combinations():
+    mlc = tiny_mlc()
+    rng = np.random.default_rng(7)
+    pi = rng.integers(-4, 5, size=mlc.K * mlc.n_rows * mlc.n_cols).astype(np.float32)
+    occupied = np.zeros(mlc.K, bool)
+    leaves = np.zeros((mlc.K, mlc.n_rows, 2), np.int64)
+    N = mlc.n_cols
+    openings = [(L, R) for L in range(N + 1) for R in range(L, N + 1)]
+    for k in range(mlc.K):
+        price, lv = oracle.price_cp(mlc, pi, occupied, leaves, k)
+        best = -np.inf
+        for combo in itertools.product(openings, repeat=mlc.n_rows):
+            tot = 0.0
+            for r, (L, R) in enumerate(combo):
+                base = (k * mlc.n_rows + r) * N
+                tot += float(np.sum(pi[base + L: base + R].astype(np.float64)))
+            best = max(best, tot)
+        assert price == best
+        tot = sum(float(np.sum(pi[(k * mlc.n_rows + r) * N + L:(k * mlc.n_rows + r) * N + R].astype(np.float64)))
+                  for r, (L, R) in enumerate(lv))
+        assert tot == price
+
+
+def test_leaf_windows_reading():
+    mlc = tiny_mlc(K=6, n_rows=2, n_cols=8, travel=1)
+    occupied = np.zeros(6, bool)
+    leaves = np.zeros((6, 2, 2), np.int64)
+    occupied[1] = True
+    leaves[1] = [[2, 5], [0, 8]]
+    Lmin, Lmax, Rmin, Rmax = oracle.leaf_windows(mlc, occupied, leaves, 3)   # distance 2
+    assert list(Lmin) == [0, 0] and list(Lmax) == [4, 2]
+    assert list(Rmin) == [3, 6] and list(Rmax) == [7, 8]
+    occupied[4] = True
+    leaves[4] = [[3, 4], [1, 2]]
+    Lmin, Lmax, Rmin, Rmax = oracle.leaf_windows(mlc, occupied, leaves, 3)   # plus distance 1 on the right
+    assert list(Lmin) == [2, 0] and list(Lmax) == [4, 2]
+    assert list(Rmin) == [3, 6] and list(Rmax) == [5, 3]
+
+
+def test_windows_stop_at_arc_boundary():
+    mlc = tiny_mlc(K=6, n_rows=1, n_cols=8, arcs=(0, 3), travel=1)
+    occupied = np.zeros(6, bool)
+    leaves = np.zeros((6, 1, 2), np.int64)
+    occupied[2] = True
+    leaves[2] = [[4, 4]]
+    assert [int(a[0]) for a in oracle.leaf_windows(mlc, occupied, leaves, 3)] == [0, 8, 0, 8]
+    assert [int(a[0]) for a in oracle.leaf_windows(mlc, occupied, leaves, 1)] == [3, 5, 3, 5]
+
+
+def test_best_cp_ties_pick_smallest_index():
+    mlc = tiny_mlc(K=4, n_rows=1, n_cols=3)
+    pi = np.float32([1, 1, 0,  0, 2, 0,  2, 0, 0,  0, 0, 0])
+    occupied = np.zeros(4, bool)
+    leaves = np.zeros((4, 1, 2), np.int64)
+    k, lv, price = oracle.price_apertures(mlc, pi, occupied, leaves)
+    assert (k, price) == (0, 2.0) and list(lv[0]) == [0, 2]
+    occupied[0] = True
+    leaves[0] = [[0, 2]]
+    k, lv, price = oracle.price_apertures(mlc, pi, occupied, leaves)
+    # CP 1 (distance 1, travel 1): L in [0, 1], R in [1, 3] -> [1, 2) = 2; CP 2: [0, 1) = 2
+    assert (k, price) == (1, 2.0) and list(lv[0]) == [1, 2]
