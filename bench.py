@@ -1,0 +1,386 @@
+"""Benchmark: column-generation VMAT plans on the H&N-like synthetic workload.
+
+One step = one full cg_plan (60 apertures) on the 128x128x96-voxel, 180-CP,
+64x64-beamlet DDC, every hot-path stage included (gradient, beamlet price over
+the unoccupied CPs, pricing, aperture dose vectors, BB master problems, final
+FP32 dose).  The DDC (CSR of D and of D^T) is resident in HBM before timing.
+
+value = effective DDC bandwidth of the plan: the algorithmic bytes of every
+D x and D^T g pass the plan makes, divided by the plan's wall time (GB/s).
+ms_per_step = plan wall time.  roofline = the beamlet-price SpMV, timed by the
+library's CUDA events on its launch stream during the timed plans.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference that exists) on
+a bounded sample of the same workload.  With torchrun, every rank plans its own
+replica (plans are independent; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DDC D·x + Dᵀ·g effective HBM GB/s; CG plan wall time at matched objective"
+WORKLOAD = "cfg2"
+WORKLOAD_DESC = ("H&N-like: 128x128x96 voxels @2.5 mm, 3 targets + 6 OARs, one arc of 180 CPs, "
+                 "64x64 beamlets (737,280), pencil-beam DDC FP32, 60 apertures")
+# CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
+SAMPLE_CP_STRIDE = 12
+SAMPLE_APERTURES = 5
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("VMAT_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+def sample_case():
+    """The CPU sample: every SAMPLE_CP_STRIDE-th CP of the workload's geometry."""
+    import numpy as np
+    import synth
+    geom = synth.GEOMETRIES[WORKLOAD]
+    bpc = geom.n_rows * geom.n_cols
+    keep_cp = np.arange(0, geom.K, SAMPLE_CP_STRIDE)
+    vox, blt, val = synth.generate_coo_cps(geom, keep_cp)
+    structs = synth.make_structures(WORKLOAD, geom, 0)
+    mlc = synth.MLC(len(keep_cp), geom.n_rows, geom.n_cols, np.array([0], np.int32), 3)
+    return geom.V, len(keep_cp) * bpc, vox, blt, val, structs, mlc
+
+
+def run_oracle_steps(steps, warmup):
+    """Time the FP64 oracle's column generation on the CPU sample (one thread)."""
+    import numpy as np
+    import oracle
+    from paper_1503_01721_gb300 import roofline
+    V, J, vox, blt, val, structs, mlc = sample_case()
+    D = oracle.ddc_matrix(V, J, vox, blt, val)
+    nnz = len(val)
+    bpc = mlc.n_rows * mlc.n_cols
+    n_rows_D = int(np.count_nonzero(np.bincount(vox, minlength=V)))
+    per_cp = np.bincount(blt // bpc, minlength=mlc.K)
+    times, gbytes = [], 0.0
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        plan = oracle.cg_plan(D, mlc, structs, SAMPLE_APERTURES)
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            times.append(dt)
+    # bytes moved by the plan's sparse passes, in the same FP32-CSR byte model as the GPU
+    n_price = len(plan.cps) + (plan.stop == "price")
+    b = 0.0
+    occupied = set()
+    for t in range(n_price):
+        act = [k for k in range(mlc.K) if k not in occupied]
+        b += sum(int(per_cp[k]) for k in act) * roofline.csr_bytes_per_nnz("f32") + len(act) * bpc * 12 + 4 * V
+        if t < len(plan.cps):
+            occupied.add(plan.cps[t])
+    b += roofline.spmv_bytes(nnz, n_rows_D, J, V)
+    per_step = sum(times) / len(times)
+    return {"value": b / per_step / 1e9, "sec_per_plan": per_step, "nnz": nnz, "J": J, "V": V,
+            "apertures": len(plan.cps), "F": plan.F}
+
+
+def cpu_baseline_subprocess(steps=1, warmup=0):
+    """Run the oracle sample in a fresh single-threaded process (no CUDA in it)."""
+    # the timed oracle is single-threaded (scipy sparse products, BLAS pinned to one
+    # thread); the untimed input generator keeps its OpenMP threads
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="",
+               VMAT_ORACLE_SUBPROCESS="1")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.run_oracle_steps({steps}, {warmup})))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def sample_desc(res):
+    return (f"FP64 oracle cg_plan, {SAMPLE_APERTURES} apertures, on every {SAMPLE_CP_STRIDE}th CP of the "
+            f"{WORKLOAD} geometry ({res['J']} beamlets, {res['nnz']} nonzeros); same byte model")
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import synth
+    from paper_1503_01721_gb300 import api, roofline
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    case = synth.make_case(WORKLOAD, seed=rank, cache=False)
+    log(f"[rank {rank}] generated {case.nnz} nonzeros in {time.time() - t0:.1f}s")
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+    vox_h, blt_h, val_h = pin(case.vox, torch.int32), pin(case.blt, torch.int32), pin(case.val, torch.float32)
+    vox = api.VoxelParams.from_numpy(case.structs, dev)
+    n_ap = case.n_apertures
+
+    # resident DDC
+    h = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
+    api.ddc_build(h, args.dtype)
+    info = api.ddc_info(h)
+    log(f"[rank {rank}] build {info['build_ms']:.1f} ms, active voxels {info['n_active_vox']}")
+
+    cps = torch.empty(n_ap, dtype=torch.int32).pin_memory()
+    lv = torch.empty(n_ap * case.mlc.n_rows * 2, dtype=torch.int16).pin_memory()
+    y = torch.empty(n_ap, dtype=torch.float32).pin_memory()
+    dose = torch.empty(case.V, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        api.cg_plan(h, case.mlc, vox, n_ap, dose_out=dose)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats_all = []
+    Fs = []
+    launches0 = api.launch_count()
+    for _ in range(args.steps):
+        F, st = api.cg_plan(h, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
+        stats_all.append(st)
+        Fs.append(F)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = api.launch_count() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(ms_total / args.steps, world)
+    bytes_step = sum(s["pp1_spmv_bytes"] + s["other_spmv_bytes"] for s in stats_all) / args.steps
+    value_rank = bytes_step / (ms_step * 1e-3) / 1e9
+    value = value_rank * world  # every rank moved the same bytes in at most ms_step
+
+    # dominant kernel: the beamlet-price SpMV, from the library's events over the timed plans
+    spmv_ms = sum(s["pp1_spmv_ms"] for s in stats_all)
+    spmv_n = sum(s["pp1_spmv_launches"] for s in stats_all)
+    spmv_bytes = sum(s["pp1_spmv_bytes"] for s in stats_all)
+    peaks = roofline.measured_peaks()
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "spmv_tile_kernel (beamlet price D^T g, active tiles) + spmv_fixup",
+            "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": peaks["source"], "bytes_per_launch": round(spmv_bytes / max(spmv_n, 1)),
+            "avg_launch_ms": round(spmv_ms / max(spmv_n, 1), 4)}
+
+    # isolated full passes: D^T g and D x over the whole matrix
+    g = torch.rand(case.V, device=dev)
+    x = torch.rand(case.J, device=dev)
+    pi = torch.empty(case.J, device=dev)
+    d = torch.empty(case.V, device=dev)
+    for _ in range(3):
+        api.beamlet_price(h, g, pi)
+        api.dose_forward(h, x, d)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 20
+    e[0].record(stream)
+    for _ in range(reps):
+        api.beamlet_price(h, g, pi)
+    e[1].record(stream)
+    for _ in range(reps):
+        api.dose_forward(h, x, d)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    b_dt = roofline.spmv_bytes(case.nnz, case.J, case.V, case.J, args.dtype, case.J if args.dtype == "fp8" else 0)
+    b_d = roofline.spmv_bytes(case.nnz, info["n_active_vox"], case.J, case.V, args.dtype,
+                              case.J if args.dtype == "fp8" else 0)
+    t_dt = e[0].elapsed_time(e[1]) / reps
+    t_d = e[1].elapsed_time(e[2]) / reps
+    pair = {"dt_g_ms": round(t_dt, 4), "dt_g_gbs": round(b_dt / t_dt / 1e6, 1), "d_x_ms": round(t_d, 4),
+            "d_x_gbs": round(b_d / t_d / 1e6, 1), "pair_gbs": round((b_dt + b_d) / (t_dt + t_d) / 1e6, 1),
+            "pair_frac": round((b_dt + b_d) / (t_dt + t_d) / 1e6 / peaks["hbm_gbs"], 4)}
+
+    # end to end through the C ABI with host buffers: H2D of the COO, build, plan, D2H of the results
+    dose_h = torch.empty(case.V, dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for it in range(1 + args.e2e_steps):
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        h2 = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
+        api.ddc_build(h2, args.dtype)
+        F2, st2 = api.cg_plan(h2, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose_h)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t_a)
+        api.ddc_free(h2)
+    e2e_s = max_over_ranks(sum(e2e_times[1:]) / max(1, len(e2e_times) - 1), world)
+    h2d = 12 * case.nnz
+    d2h = cps.numel() * 4 + lv.numel() * 2 + y.numel() * 4 + dose_h.numel() * 4
+    e2e = {"value": round(bytes_step / e2e_s / 1e9 * world, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 2),
+           "includes": "COO host->device, ddc_build, cg_plan, results device->host"}
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline_subprocess(1, 0) if world == 1 and not args.no_cpu else None
+        st = stats_all[-1]
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else args.dtype, "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} {WORKLOAD_DESC}", "V": case.V, "J": case.J, "nnz": case.nnz,
+                       "n_active_vox": info["n_active_vox"], "n_apertures": n_ap, "storage": args.dtype,
+                       "l2": "inputs larger than L2 (CSR D + D^T %.1f GB)" % ((info["bytes_D"] + info["bytes_Dt"]) / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": None if cpu is None else {
+                "value": round(cpu["value"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": sample_desc(cpu), "sec_per_plan": round(cpu["sec_per_plan"], 3)},
+            "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+            "plan": {"F": Fs[-1], "F_spread": max(Fs) - min(Fs), "apertures": st["n_apertures"],
+                     "stop": st["stop"], "bb_iters": st["bb_iters_total"],
+                     "phases_ms": {k: round(st[k], 3) for k in
+                                   ("t_pp1_ms", "t_pp2_ms", "t_da_ms", "t_mp_ms", "t_final_ms", "t_total_ms")},
+                     "build_ms": round(info["build_ms"], 1)},
+            "spmv_pair": pair,
+        }
+    api.ddc_free(h)
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    res = cpu_baseline_subprocess(args.steps, args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": round(res["value"], 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["sec_per_plan"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} {WORKLOAD_DESC}", "sample": sample_desc(res)},
+            "cpu_baseline": {"value": round(res["value"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc(res)},
+            "e2e": {"value": round(res["value"], 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("note: fewer than 3 warm-up steps")
+    rank, world, local = dist_setup(args.gpus)
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * vmat.h -- C ABI of libvmat, the GB300 (sm_103a) hot path of column-generation
+ * VMAT optimisation (Tian et al., arXiv:1503.01721).
+ *
+ * Conventions (apply to every entry point unless its comment says otherwise):
+ *  - Array arguments are caller-owned DEVICE memory, dense and contiguous
+ *    (e.g. PyTorch tensors).  The library keeps no pointer past the call,
+ *    except the matrices held inside a vmat_ddc handle (freed by ddc_free).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it unless marked "synchronises".
+ *  - Every call returns a vmat_status.  Arguments are validated before any
+ *    launch (VMAT_EINVAL); CUDA failures return VMAT_ECUDA.  The message of the
+ *    last failure on the calling thread is returned by vmat_last_error().
+ *    No C++ exception crosses this interface.
+ *  - Kernels never trap.  A device-side problem (a bounded wait that ran out,
+ *    an index out of range found by a check) sets the library's device status
+ *    word, read and cleared by vmat_device_status().
+ *  - Beamlet layout (Section 2.2.2 of the paper: beamlets of one control point
+ *    (CP) form the MLC rows the pricing step walks):
+ *        beamlet j = (k * n_rows + r) * n_cols + c
+ *    for CP k, leaf pair (MLC row) r, column c.  An aperture row is the
+ *    half-open column interval [L, R); L == R is a closed row.
+ */
+#ifndef VMAT_H
+#define VMAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vmat_status;
+#define VMAT_OK 0
+#define VMAT_EINVAL (-1)       /* bad argument (pointer, size, index range) */
+#define VMAT_ENOMEM (-2)       /* device allocation failed */
+#define VMAT_ECUDA (-3)        /* CUDA runtime/launch error */
+#define VMAT_ESTATE (-4)       /* handle not in the required state (e.g. not built) */
+#define VMAT_ETIMEOUT (-5)     /* a bounded device-side wait ran out */
+#define VMAT_EUNSUPPORTED (-6) /* valid request outside what this build supports */
+
+typedef enum { VMAT_F32 = 0, VMAT_BF16 = 1, VMAT_FP8E4M3 = 2 } vmat_dtype;
+
+/* Opaque dose-deposition-coefficient (DDC) matrix D (V voxels x J beamlets),
+ * library-owned device memory. */
+typedef struct vmat_ddc_s *vmat_ddc;
+
+/* MLC geometry.  arc_first_cp is HOST memory: n_arcs ascending CP indices,
+ * arc_first_cp[0] == 0; arc a spans [arc_first_cp[a], arc_first_cp[a+1]) (the
+ * last arc ends at K).  travel_cols: columns a leaf may travel per CP step
+ * (the neighbour-compatibility reading of Eq. 2). */
+typedef struct {
+    int32_t K, n_rows, n_cols;
+    int32_t n_arcs;
+    const int32_t *arc_first_cp;
+    int32_t travel_cols;
+} vmat_mlc;
+
+/* Voxel penalty parameters of Eq. 1: per-voxel structure label (device uint8
+ * [V]) and per-structure prescription/threshold T, overdose weight w_over and
+ * underdose weight w_under (device float [n_struct], n_struct <= 256). */
+typedef struct {
+    const uint8_t *struct_id;
+    int32_t n_struct;
+    const float *T;
+    const float *w_over;
+    const float *w_under;
+} vmat_voxels;
+
+/* Build options for ddc_build. */
+typedef struct {
+    vmat_dtype dtype;   /* stored value type; FP8 uses per-beamlet power-of-two scales */
+    int32_t build_D;    /* nonzero: build CSR(D), voxel rows (dose_forward, aperture_dose) */
+    int32_t build_Dt;   /* nonzero: build CSR(D^T), beamlet rows (beamlet_price) */
+    int32_t tile_cfg;   /* SpMV tile configuration index, -1 = library default */
+    int32_t autotune;   /* nonzero: time every tile configuration and keep the fastest */
+    int32_t keep_coo;   /* nonzero: keep the COO copy after the build */
+} vmat_build_opts;
+
+/* Master-problem (Eq. 6-10) options.  Stopping rules of Section 2.1:
+ * |F_{t-5} - F_t| <= rel_tol5 * F_t, or max|y_t - y_{t-1}| <= step_tol *
+ * max(1, max|y_t|), or max_iter iterations.  Steps are clamped to
+ * [delta_min, delta_max] times the first (Cauchy) step. */
+typedef struct {
+    int32_t max_iter;
+    double rel_tol5;
+    double step_tol;
+    double delta_min;
+    double delta_max;
+} vmat_bb_opts;
+
+#define VMAT_STOP_REL 1
+#define VMAT_STOP_STEP 2
+#define VMAT_STOP_MAXIT 3
+#define VMAT_STOP_GRAD0 4
+#define VMAT_STOP_FLAT 5
+#define VMAT_STOP_PRICE 10 /* cg_plan: best CP price <= 0 (Section 2.1) */
+#define VMAT_STOP_COUNT 11 /* cg_plan: n_apertures generated */
+
+typedef struct {
+    int32_t iters;       /* BB iterations run */
+    int32_t stop_reason; /* VMAT_STOP_* */
+    double F;            /* objective at the returned y */
+} vmat_bb_report;
+
+typedef struct {
+    int32_t V, J;
+    int64_t nnz;
+    int32_t n_active_vox;   /* voxels with at least one nonzero (rows of CSR(D)) */
+    vmat_dtype dtype;
+    int32_t built_D, built_Dt;
+    int32_t tile_nnz_D, tile_nnz_Dt; /* nonzeros per SpMV tile */
+    int64_t bytes_D, bytes_Dt;       /* device bytes of each CSR (values, columns, row pointers) */
+    double build_ms;                 /* device time of the last ddc_build */
+} vmat_ddc_info;
+
+/* Per-phase device times of cg_plan, named as the paper's Table 2 phases. */
+typedef struct {
+    double t_total_ms;  /* whole call */
+    double t_pp1_ms;    /* gradient + beamlet price (Eq. 3-4) */
+    double t_pp2_ms;    /* pricing kernels + choice readback */
+    double t_da_ms;     /* aperture dose vectors (Eq. 5) */
+    double t_mp_ms;     /* master problems (Eq. 6-10) */
+    double t_final_ms;  /* final dose D (A y) and objective */
+    double pp1_spmv_ms; /* the D^T g kernels alone */
+    int64_t pp1_spmv_launches;
+    double pp1_spmv_bytes;  /* algorithmic bytes of those launches */
+    double other_spmv_bytes; /* algorithmic bytes of the D x / aperture-dose passes */
+    int32_t n_apertures;
+    int32_t bb_iters_total;
+    int32_t stop_reason;
+    int64_t kernel_launches; /* kernels this call launched */
+} vmat_plan_stats;
+
+/* ---- DDC matrix ---------------------------------------------------------- */
+
+/* Copy a COO DDC matrix into a new handle (Section 2.2.2: the dose engine
+ * writes D as COO, value + voxel index + beamlet index).
+ * vox[e] in [0, V), blt[e] in [0, J), val[e] finite; nnz >= 0.
+ * on_device != 0: the three arrays are device memory; otherwise host memory
+ * (pinned or pageable).  Duplicate (voxel, beamlet) pairs are rejected by
+ * ddc_build.  On success *out owns device copies; free with ddc_free. */
+vmat_status ddc_load_coo(int32_t V, int32_t J, int64_t nnz, const int32_t *vox, const int32_t *blt,
+                         const float *val, int32_t on_device, void *stream, vmat_ddc *out);
+
+/* Build the device matrices (Section 2.2.2: CSR of D^T for the beamlet
+ * price; the paper converts at initialisation).  CSR(D^T): row j = beamlet j,
+ * entries sorted by voxel.  CSR(D): rows = voxels with at least one entry,
+ * entries sorted by beamlet.  Values stored as opts->dtype: F32 as given,
+ * BF16 round-to-nearest-even, FP8 E4M3 (saturating, nearest-even) of
+ * D_ij / s_j with s_j the least power of two with 448 s_j >= max_i |D_ij|.
+ * Index checks and the duplicate check report VMAT_EINVAL.  Synchronises. */
+vmat_status ddc_build(vmat_ddc h, const vmat_build_opts *opts, void *stream);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+vmat_status ddc_free(vmat_ddc h);
+
+/* Sizes and build facts of a handle (host struct). */
+vmat_status ddc_info(vmat_ddc h, vmat_ddc_info *out);
+
+/* ---- Sparse products (hot path) ------------------------------------------ */
+
+/* d = D x (Section 2.1: z_i = sum_j D_ij x_j; Eq. 5 is the case x = the
+ * indicator of an aperture).  x: device float [J]; d: device float [V],
+ * fully written (voxels without entries get 0).  FP32 accumulation.
+ * Needs build_D. */
+vmat_status dose_forward(vmat_ddc h, const float *x, float *d, void *stream);
+
+/* pi = D^T g (Eq. 3, beamlet price, with g = -grad F of Eq. 4).
+ * g: device float [V]; pi: device float [J].  cp_active: device uint8 [K]
+ * or NULL (all CPs); when given, only the beamlets of CPs with
+ * cp_active[k] != 0 are priced (the paper prices unoccupied CPs only) and
+ * entries of inactive CPs are left unspecified.  beamlets_per_cp =
+ * n_rows * n_cols (ignored when cp_active is NULL).  FP32 accumulation.
+ * Needs build_Dt. */
+vmat_status beamlet_price(vmat_ddc h, const float *g, float *pi, const uint8_t *cp_active,
+                          int32_t beamlets_per_cp, void *stream);
+
+/* ---- Objective ------------------------------------------------------------ */
+
+/* F(z) of Eq. 1 and g = -grad F of Eq. 4 for V voxels.
+ * z: device float [V]; g: device float [V] (FP32) or NULL; F: device double
+ * [1] (FP64 sum, deterministic order) or NULL. */
+vmat_status objective_grad(int32_t V, const float *z, const vmat_voxels *vox, float *g, double *F,
+                           void *stream);
+
+/* ---- Pricing problem, second step (Section 2.2.2) ------------------------- */
+
+/* For every unoccupied CP k (occupied[k] == 0) and MLC row r, the opening
+ * [L, R) maximising the summed price (within leaf-travel windows set by the
+ * nearest occupied CP on each side of the same arc, Eq. 2 compatibility),
+ * then the CP whose row sum is largest.  Row values are P_R - P_L with P the
+ * sequential float64 prefix sum of the float32 prices; ties are broken by
+ * (width asc, |L + R - n_cols| asc, L asc); the CP price is the sequential
+ * float64 sum over rows; CP ties go to the smallest k.  The result is
+ * bit-for-bit reproducible from pi.
+ * pi: device float [J]; occupied: device uint8 [K]; leaves: device int16
+ * [K][n_rows][2] (read for occupied CPs only).  Outputs (device): best_cp
+ * int32 [1] (-1 if no CP is feasible), best_leaves int16 [n_rows][2],
+ * best_price double [1].  n_cols <= 1024. */
+vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
+                            int32_t *best_cp, int16_t *best_leaves, double *best_price, void *stream);
+
+/* ---- Apertures <-> beamlets ------------------------------------------------ */
+
+/* DA(A) = sum_{j in A} D_{:,j} (Eq. 5) for the aperture at CP `cp` with
+ * leaves (device int16 [n_rows][2]).  da: device float [V], fully written.
+ * Needs build_D. */
+vmat_status aperture_dose(vmat_ddc h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
+                          void *stream);
+
+/* x = A y: x_j = sum of y_n over the apertures n that contain beamlet j (in
+ * order of n).  cps: device int32 [n_ap]; leaves: device int16
+ * [n_ap][n_rows][2]; y: device float [n_ap]; x: device float [J]. */
+vmat_status aperture_fluence(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps, const int16_t *leaves,
+                             const float *y, float *x, void *stream);
+
+/* gy = A^T pi: gy_n = sum of pi over the beamlets of aperture n (FP64
+ * accumulation, fixed order).  gy: device float [n_ap]. */
+vmat_status aperture_grad(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps, const int16_t *leaves,
+                          const float *pi, float *gy, void *stream);
+
+/* ---- Master problem (Eq. 6-10) -------------------------------------------- */
+
+/* min F(DA y) subject to lo <= y <= hi, by Barzilai-Borwein steps (Eq. 7-8,
+ * alternated) with the subspace bound scheme (Eq. 9-10) and the stopping
+ * rules of Section 2.1.  DA: device float, column-major [n_ap][ld] (column n
+ * = aperture n's dose vector over V voxels, ld >= V).  lo, hi: device float
+ * [n_ap] or NULL (0 and +inf).  y: device float [n_ap], warm start in,
+ * solution out.  z: device float [V], receives DA y.  opts NULL = defaults
+ * (500, 1e-6, 1e-9, 1e-12, 1e12).  rep: HOST struct or NULL.
+ * The step lengths, objective and stopping tests use FP64; the products FP32.
+ * Synchronises. */
+vmat_status mp_bb_solve(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const vmat_voxels *vox,
+                        const float *lo, const float *hi, float *y, float *z, const vmat_bb_opts *opts,
+                        vmat_bb_report *rep, void *stream);
+
+/* ---- Column generation (Section 2.1, Fig. 1a) ---------------------------- */
+
+/* Generate up to n_apertures apertures: repeat { g = -grad F(z); pi = D^T g
+ * over unoccupied CPs; best aperture; DA column (Eq. 5); master problem over
+ * all apertures (warm start, new y = 0) } until n_apertures are generated or
+ * the best price is <= 0.  Finally dose = D (A y) in FP32 and F(dose).
+ * Outputs may be host or device memory (copied with cudaMemcpyDefault), any
+ * may be NULL: cps_out int32 [n_apertures] (unused slots -1), leaves_out
+ * int16 [n_apertures][n_rows][2], y_out float [n_apertures], dose_out float
+ * [V].  F_out: host double.  stats: host struct or NULL.  Needs build_D and
+ * build_Dt.  Synchronises. */
+vmat_status cg_plan(vmat_ddc h, const vmat_mlc *mlc, const vmat_voxels *vox, int32_t n_apertures,
+                    const vmat_bb_opts *opts, int32_t *cps_out, int16_t *leaves_out, float *y_out, float *dose_out,
+                    double *F_out, vmat_plan_stats *stats, void *stream);
+
+/* ---- Diagnostics ---------------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *vmat_last_error(void);
+
+/* Device status word (bit 0: a bounded wait ran out; bit 1: an index check
+ * failed; bit 2: duplicate COO entry).  reset != 0 clears it.  Synchronises
+ * with the device. */
+int32_t vmat_device_status(int32_t reset);
+
+/* Library version string. */
+const char *vmat_version(void);
+
+/* Number of kernels libvmat has launched in this process (all threads). */
+int64_t vmat_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMAT_H */

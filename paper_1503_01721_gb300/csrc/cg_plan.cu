@@ -1,0 +1,312 @@
+// Column generation (Section 2.1, Fig. 1a): starting from z = 0 and no
+// apertures, repeat
+//   PP1  g = -grad F(z) (Eq. 4) and pi = D^T g over the unoccupied CPs (Eq. 3)
+//   PP2  best opening per MLC row, best CP (Section 2.2.2)
+//   DA   the new aperture's dose vector (Eq. 5)
+//   MP   BB solve over all apertures (Eq. 6-10), warm start, new y = 0
+// until n_apertures exist or no CP has a positive price.  Then the final dose
+// D (A y) is recomputed in FP32 from the stored matrix and F is evaluated.
+//
+// Everything stays on the device.  The master problem runs in the compact
+// space of voxels that have at least one nonzero (the rows of CSR(D)); the
+// other voxels always receive zero dose, so their penalty is a constant added
+// to F.  The host reads back only the chosen CP and its price (to stop) and
+// the MP stop flag.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace vmat {
+
+vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
+                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s);
+size_t objective_scratch_bytes(int n_sm);
+vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);
+vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
+                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s);
+size_t pricing_scratch_bytes(const vmat_mlc *mlc);
+
+__global__ void gather_u8(const uint8_t *src, const int32_t *idx, int32_t n, uint8_t *dst) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
+__global__ void fill_u8(uint8_t *p, int32_t n, uint8_t v) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void fill_i32(int32_t *p, int32_t n, int32_t v) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// rowptr of CSR(D^T) at the first beamlet of every CP (K + 1 values).
+__global__ void cp_offsets(const int64_t *rowptr, int32_t K, int32_t bpc, int64_t *out) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x)
+        out[k] = rowptr[(int64_t)k * bpc];
+}
+
+namespace {
+
+struct DevArena {
+    std::vector<void *> ptrs;
+    ~DevArena() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T> vmat_status get(T **out, size_t n) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(n * sizeof(T), 16));
+        if (e != cudaSuccess)
+            return set_error(e == cudaErrorMemoryAllocation ? VMAT_ENOMEM : VMAT_ECUDA, "cg_plan: %s",
+                             cudaGetErrorString(e));
+        ptrs.push_back(p);
+        *out = static_cast<T *>(p);
+        return VMAT_OK;
+    }
+};
+
+struct PhaseTimer {
+    bool on;
+    cudaStream_t s;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> which; // phase index of each (start, end) pair
+    explicit PhaseTimer(bool on_, cudaStream_t s_) : on(on_), s(s_) {}
+    ~PhaseTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    void mark(int phase) { // start of a phase
+        if (!on) return;
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, s);
+        ev.push_back(a);
+        which.push_back(phase);
+    }
+    void end() { mark(-1); }
+    void accumulate(double *acc) { // acc[phase] += ms between a phase mark and the next mark
+        for (size_t i = 0; i + 1 < ev.size(); ++i) {
+            if (which[i] < 0) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[which[i]] += ms;
+        }
+    }
+};
+
+enum { PH_PP1 = 0, PH_SPMV, PH_PP2, PH_DA, PH_MP, PH_FINAL, PH_N };
+
+} // namespace
+
+} // namespace vmat
+
+using namespace vmat;
+
+extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxels *vox, int32_t n_apertures,
+                               const vmat_bb_opts *opts, int32_t *cps_out, int16_t *leaves_out, float *y_out,
+                               float *dose_out, double *F_out, vmat_plan_stats *stats, void *stream) {
+    clear_error();
+    if (!hd) return set_error(VMAT_EINVAL, "cg_plan: handle is NULL");
+    VMAT_TRY(validate_mlc(mlc));
+    VMAT_TRY(validate_voxels(vox));
+    Ddc &h = *as_ddc(hd);
+    if (!h.built_D || !h.built_Dt) return set_error(VMAT_ESTATE, "cg_plan: needs both CSR(D) and CSR(D^T)");
+    if ((int64_t)mlc->K * mlc->n_rows * mlc->n_cols != h.J)
+        return set_error(VMAT_EINVAL, "cg_plan: K*n_rows*n_cols != J");
+    if (n_apertures < 0 || n_apertures > mlc->K)
+        return set_error(VMAT_EINVAL, "cg_plan: n_apertures must be in [0, K] (each CP holds one aperture)");
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    cudaStream_t s = as_stream(stream);
+    const int32_t V = h.V, J = h.J, K = mlc->K, NR = mlc->n_rows, NA = h.n_active;
+    const int32_t bpc = NR * mlc->n_cols;
+    const int64_t ld = ((int64_t)std::max(NA, 1) + 31) / 32 * 32;
+    const int nap_max = std::max(n_apertures, 1);
+    const int g256 = std::max(1, ctx->n_sm * 4);
+
+    DevArena ar;
+    float *z_c, *g_full, *pi, *DA, *y, *x, *dose;
+    uint8_t *occupied, *active, *sid_c;
+    int16_t *leaves_all, *best_leaves, *leaves_seq;
+    int32_t *best_cp, *cps_dev;
+    double *best_price, *F_dev, *F0;
+    void *obj_ws, *pr_ws;
+    VMAT_TRY(ar.get(&z_c, std::max(NA, 1)));
+    VMAT_TRY(ar.get(&g_full, V));
+    VMAT_TRY(ar.get(&pi, J));
+    VMAT_TRY(ar.get(&DA, (size_t)ld * nap_max));
+    VMAT_TRY(ar.get(&y, nap_max));
+    VMAT_TRY(ar.get(&x, J));
+    VMAT_TRY(ar.get(&dose, V));
+    VMAT_TRY(ar.get(&occupied, K));
+    VMAT_TRY(ar.get(&active, K));
+    VMAT_TRY(ar.get(&sid_c, std::max(NA, 1)));
+    VMAT_TRY(ar.get(&leaves_all, (size_t)K * NR * 2));
+    VMAT_TRY(ar.get(&best_leaves, (size_t)NR * 2));
+    VMAT_TRY(ar.get(&leaves_seq, (size_t)nap_max * NR * 2));
+    VMAT_TRY(ar.get(&best_cp, 2));
+    VMAT_TRY(ar.get(&cps_dev, nap_max));
+    VMAT_TRY(ar.get(&best_price, 2));
+    VMAT_TRY(ar.get(&F_dev, 2));
+    VMAT_TRY(ar.get(&F0, 2));
+    VMAT_TRY(ar.get((char **)&obj_ws, objective_scratch_bytes(ctx->n_sm)));
+    VMAT_TRY(ar.get((char **)&pr_ws, pricing_scratch_bytes(mlc)));
+    struct Pinned {
+        int32_t cp;
+        int32_t pad;
+        double price;
+    } *hp = nullptr;
+    VMAT_CUDA(cudaMallocHost(&hp, sizeof(Pinned)));
+    struct FreeHost {
+        void *p;
+        ~FreeHost() { cudaFreeHost(p); }
+    } fh{hp};
+
+    const long long launches0 = g_launches.load();
+    PhaseTimer tm(stats != nullptr, s);
+    cudaEvent_t t0, t1;
+    VMAT_CUDA(cudaEventCreate(&t0));
+    VMAT_CUDA(cudaEventCreate(&t1));
+    VMAT_CUDA(cudaEventRecord(t0, s));
+
+    VMAT_CUDA(cudaMemsetAsync(z_c, 0, (size_t)std::max(NA, 1) * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(g_full, 0, (size_t)V * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(occupied, 0, K, s));
+    VMAT_CUDA(cudaMemsetAsync(leaves_all, 0, (size_t)K * NR * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(obj_ws, 0, 64, s));
+    fill_u8<<<std::max(1, (K + 255) / 256), 256, 0, s>>>(active, K, 1);
+    VMAT_LAUNCH_CHECK();
+    fill_i32<<<1, 256, 0, s>>>(cps_dev, nap_max, -1);
+    VMAT_LAUNCH_CHECK();
+    if (NA > 0) {
+        gather_u8<<<std::max(1, std::min(g256, (NA + 255) / 256)), 256, 0, s>>>(vox->struct_id, h.act_vox, NA, sid_c);
+        VMAT_LAUNCH_CHECK();
+    }
+    VMAT_TRY(inactive_objective(h, vox, F0, s));
+    double F_offset = 0.0;
+    VMAT_CUDA(cudaMemcpyAsync(&F_offset, F0, sizeof(double), cudaMemcpyDeviceToHost, s));
+    // nonzeros per CP in CSR(D^T): algorithmic bytes of each pricing pass
+    int64_t *cpo_dev;
+    VMAT_TRY(ar.get(&cpo_dev, (size_t)K + 1));
+    cp_offsets<<<std::max(1, (K + 256) / 256), 256, 0, s>>>(h.Dt.rowptr, K, bpc, cpo_dev);
+    VMAT_LAUNCH_CHECK();
+    std::vector<int64_t> cpo(K + 1);
+    VMAT_CUDA(cudaMemcpyAsync(cpo.data(), cpo_dev, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    std::vector<char> occ_host(K, 0);
+    vmat_voxels vox_c = *vox;
+    vox_c.struct_id = sid_c;
+
+    std::vector<int32_t> cps_host;
+    int stop = VMAT_STOP_COUNT;
+    int bb_total = 0;
+    int64_t spmv_launches = 0;
+    double pp1_bytes = 0.0, other_bytes = 0.0;
+    const int vb = value_bytes(h.dtype);
+    const double bytes_D_full = (double)h.D.nnz * (vb + 4) + 8.0 * (h.D.n_rows + 1) + 4.0 * J + 4.0 * V +
+                                (h.dtype == VMAT_FP8E4M3 ? 4.0 * J : 0.0);
+
+    for (int t = 0; t < n_apertures; ++t) {
+        // ---- PP1
+        tm.mark(PH_PP1);
+        if (NA > 0)
+            VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s));
+        tm.mark(PH_SPMV);
+        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, active, bpc, s));
+        ++spmv_launches;
+        { // the format's own bytes for the rows of the unoccupied CPs, plus g once
+            double b = 4.0 * V;
+            for (int kk = 0; kk < K; ++kk)
+                if (!occ_host[kk])
+                    b += (double)(cpo[kk + 1] - cpo[kk]) * (vb + 4) + bpc * (8.0 + 4.0) +
+                         (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
+            pp1_bytes += b;
+        }
+        // ---- PP2
+        tm.mark(PH_PP2);
+        VMAT_TRY(price_apertures_impl(mlc, pi, occupied, leaves_all, best_cp, best_leaves, best_price, pr_ws, s));
+        VMAT_CUDA(cudaMemcpyAsync(&hp->cp, best_cp, 4, cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaMemcpyAsync(&hp->price, best_price, 8, cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        const int32_t k = hp->cp;
+        if (k < 0 || !(hp->price > 0.0)) {
+            stop = VMAT_STOP_PRICE;
+            break;
+        }
+        VMAT_CUDA(cudaMemsetAsync(occupied + k, 1, 1, s));
+        VMAT_CUDA(cudaMemsetAsync(active + k, 0, 1, s));
+        VMAT_CUDA(cudaMemcpyAsync(leaves_all + (size_t)k * NR * 2, best_leaves, (size_t)NR * 4,
+                                  cudaMemcpyDeviceToDevice, s));
+        VMAT_CUDA(cudaMemcpyAsync(leaves_seq + (size_t)t * NR * 2, best_leaves, (size_t)NR * 4,
+                                  cudaMemcpyDeviceToDevice, s));
+        VMAT_CUDA(cudaMemcpyAsync(cps_dev + t, best_cp, 4, cudaMemcpyDeviceToDevice, s));
+        cps_host.push_back(k);
+        occ_host[k] = 1;
+        // ---- DA (Eq. 5)
+        tm.mark(PH_DA);
+        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)t * ld, true, s));
+        // ---- MP (Eq. 6-10)
+        tm.mark(PH_MP);
+        VMAT_CUDA(cudaMemsetAsync(y + t, 0, 4, s));
+        vmat_bb_report rep;
+        if (NA > 0) {
+            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, nullptr, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
+                                &rep, s));
+            bb_total += rep.iters;
+        }
+        tm.end();
+    }
+    const int n_ap = (int)cps_host.size();
+    // ---- final dose D (A y) in FP32 and its objective
+    tm.mark(PH_FINAL);
+    VMAT_TRY(aperture_fluence(mlc, n_ap, cps_dev, leaves_seq, y, x, s));
+    VMAT_TRY(dose_forward_impl(h, x, dose, false, s));
+    other_bytes += bytes_D_full;
+    VMAT_TRY(objective_impl(V, dose, nullptr, vox, nullptr, nullptr, F_dev, 0.0, s));
+    tm.end();
+    VMAT_CUDA(cudaEventRecord(t1, s));
+
+    if (cps_out) {
+        VMAT_CUDA(cudaMemcpyAsync(cps_out, cps_dev, (size_t)std::max(n_apertures, 0) * 4, cudaMemcpyDefault, s));
+    }
+    if (leaves_out && n_apertures > 0) {
+        VMAT_CUDA(cudaMemsetAsync(leaves_seq + (size_t)n_ap * NR * 2, 0, (size_t)(n_apertures - n_ap) * NR * 4, s));
+        VMAT_CUDA(cudaMemcpyAsync(leaves_out, leaves_seq, (size_t)n_apertures * NR * 4, cudaMemcpyDefault, s));
+    }
+    if (y_out && n_apertures > 0) {
+        VMAT_CUDA(cudaMemsetAsync(y + n_ap, 0, (size_t)(n_apertures - n_ap) * 4, s));
+        VMAT_CUDA(cudaMemcpyAsync(y_out, y, (size_t)n_apertures * 4, cudaMemcpyDefault, s));
+    }
+    if (dose_out) VMAT_CUDA(cudaMemcpyAsync(dose_out, dose, (size_t)V * 4, cudaMemcpyDefault, s));
+    double Fh = 0.0;
+    VMAT_CUDA(cudaMemcpyAsync(&Fh, F_dev, 8, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    if (F_out) *F_out = Fh;
+    if (stats) {
+        double acc[PH_N] = {0};
+        tm.accumulate(acc);
+        memset(stats, 0, sizeof(*stats));
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, t0, t1);
+        stats->t_total_ms = tot;
+        stats->pp1_spmv_ms = acc[PH_SPMV];
+        stats->t_pp1_ms = acc[PH_PP1] + acc[PH_SPMV];
+        stats->t_pp2_ms = acc[PH_PP2];
+        stats->t_da_ms = acc[PH_DA];
+        stats->t_mp_ms = acc[PH_MP];
+        stats->t_final_ms = acc[PH_FINAL];
+        stats->pp1_spmv_launches = spmv_launches;
+        stats->pp1_spmv_bytes = pp1_bytes;
+        stats->other_spmv_bytes = other_bytes;
+        stats->n_apertures = n_ap;
+        stats->bb_iters_total = bb_total;
+        stats->stop_reason = stop;
+        stats->kernel_launches = g_launches.load() - launches0;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    int32_t dev_status = 0;
+    VMAT_CUDA(cudaMemcpy(&dev_status, ctx->status, 4, cudaMemcpyDeviceToHost));
+    if (dev_status & DEV_TIMEOUT) return set_error(VMAT_ETIMEOUT, "cg_plan: a device-side wait ran out");
+    return VMAT_OK;
+}

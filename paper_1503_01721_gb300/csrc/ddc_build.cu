@@ -1,0 +1,504 @@
+// ddc_build: COO -> CSR(D^T) (beamlet rows) and CSR(D) (non-empty voxel rows).
+//
+// Section 2.2.2 of the paper keeps D as COO on the host and converts it to a
+// CSR of D^T on the GPU at initialisation.  Here both orientations are built on
+// the device: counting sort by row (histogram, scan, atomic scatter), then a
+// per-row bitonic sort by column so that the layout does not depend on the
+// scatter order, then optional BF16 / FP8-E4M3 quantisation.
+#include <limits.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace vmat {
+
+namespace {
+
+constexpr int BUILD_THREADS = 256;
+constexpr int SORT_SMEM_CAP_MAX = 16384; // entries (key + value = 128 KB)
+
+int sort_smem_cap() {
+    // A smaller cap (power of two >= 32) can be forced to exercise the long-row path.
+    const char *e = getenv("VMAT_SORT_SMEM_CAP");
+    if (e) {
+        int v = atoi(e);
+        if (v >= 32 && v <= SORT_SMEM_CAP_MAX && (v & (v - 1)) == 0) return v;
+    }
+    return SORT_SMEM_CAP_MAX;
+}
+
+__global__ void coo_check_hist(const int32_t *__restrict__ vox, const int32_t *__restrict__ blt,
+                               const float *__restrict__ val, int64_t nnz, int32_t V, int32_t J, int32_t *cnt_vox,
+                               int32_t *cnt_blt, unsigned *colmax_bits, int32_t *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int32_t i = vox[e], j = blt[e];
+        float v = val[e];
+        if (i < 0 || i >= V || j < 0 || j >= J || !isfinite(v)) {
+            atomicOr(bad, DEV_INDEX);
+            continue;
+        }
+        atomicAdd(&cnt_vox[i], 1);
+        atomicAdd(&cnt_blt[j], 1);
+        if (colmax_bits) atomicMax(&colmax_bits[j], __float_as_uint(fabsf(v)));
+    }
+}
+
+__global__ void flag_nonzero(const int32_t *cnt, int32_t n, int32_t *flag) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = cnt[i] > 0 ? 1 : 0;
+}
+
+__global__ void compact_voxels(const int32_t *cnt_vox, const int64_t *off, int32_t V, int32_t *act_vox,
+                               int32_t *vox2act, int32_t *cnt_act) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        int32_t c = cnt_vox[v];
+        if (c > 0) {
+            int32_t a = (int32_t)off[v];
+            act_vox[a] = v;
+            vox2act[v] = a;
+            cnt_act[a] = c;
+        } else {
+            vox2act[v] = -1;
+        }
+    }
+}
+
+__global__ void coo_scatter(const int32_t *__restrict__ vox, const int32_t *__restrict__ blt,
+                            const float *__restrict__ val, int64_t nnz, const int64_t *rp_t, int32_t *cur_t,
+                            int32_t *col_t, float *val_t, const int64_t *rp_d, const int32_t *vox2act, int32_t *cur_d,
+                            int32_t *col_d, float *val_d) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int32_t i = vox[e], j = blt[e];
+        float v = val[e];
+        if (col_t) {
+            int64_t p = rp_t[j] + atomicAdd(&cur_t[j], 1);
+            col_t[p] = i;
+            val_t[p] = v;
+        }
+        if (col_d) {
+            int32_t a = vox2act[i];
+            int64_t q = rp_d[a] + atomicAdd(&cur_d[a], 1);
+            col_d[q] = j;
+            val_d[q] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void bitonic_smem(int32_t *k, float *v, int P) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int j = i ^ stride;
+                if (j > i) {
+                    bool up = (i & size) == 0;
+                    int32_t a = k[i], b = k[j];
+                    if ((a > b) == up) {
+                        k[i] = b;
+                        k[j] = a;
+                        float t = v[i];
+                        v[i] = v[j];
+                        v[j] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void row_sort_smem(const int64_t *rowptr, int32_t *col, float *val, int32_t n_rows, int cap,
+                              int32_t *bad) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    int32_t *k = reinterpret_cast<int32_t *>(sm);
+    float *v = reinterpret_cast<float *>(k + cap);
+    for (int32_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
+        int64_t s = rowptr[r];
+        int n = (int)(rowptr[r + 1] - s);
+        if (n < 2 || n > cap) continue;
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            k[i] = i < n ? col[s + i] : INT_MAX;
+            v[i] = i < n ? val[s + i] : 0.f;
+        }
+        __syncthreads();
+        bitonic_smem(k, v, P);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            col[s + i] = k[i];
+            val[s + i] = v[i];
+            if (i > 0 && k[i] == k[i - 1]) atomicOr(bad, DEV_DUPLICATE);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void list_long_rows(const int64_t *rowptr, int32_t n_rows, int cap, int32_t *list, int32_t *n_list) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += gridDim.x * blockDim.x)
+        if (rowptr[r + 1] - rowptr[r] > cap) list[atomicAdd(n_list, 1)] = r;
+}
+
+// Rows longer than the shared-memory cap: bitonic network over a global buffer,
+// one block per row (the block's __syncthreads orders its global accesses).
+__global__ void row_sort_global(const int64_t *rowptr, int32_t *col, float *val, const int32_t *list,
+                                int32_t n_long, int32_t *kbuf, float *vbuf, int64_t pmax, int32_t *bad) {
+    int32_t *k = kbuf + (int64_t)blockIdx.x * pmax;
+    float *v = vbuf + (int64_t)blockIdx.x * pmax;
+    for (int32_t t = blockIdx.x; t < n_long; t += gridDim.x) {
+        int32_t r = list[t];
+        int64_t s = rowptr[r];
+        int64_t n = rowptr[r + 1] - s;
+        int64_t P = 1;
+        while (P < n) P <<= 1;
+        for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+            k[i] = i < n ? col[s + i] : INT_MAX;
+            v[i] = i < n ? val[s + i] : 0.f;
+        }
+        __syncthreads();
+        for (int64_t size = 2; size <= P; size <<= 1) {
+            for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    int64_t j = i ^ stride;
+                    if (j > i) {
+                        bool up = (i & size) == 0;
+                        int32_t a = k[i], b = k[j];
+                        if ((a > b) == up) {
+                            k[i] = b;
+                            k[j] = a;
+                            float tv = v[i];
+                            v[i] = v[j];
+                            v[j] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            col[s + i] = k[i];
+            val[s + i] = v[i];
+            if (i > 0 && k[i] == k[i - 1]) atomicOr(bad, DEV_DUPLICATE);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void max_count(const int32_t *cnt, int32_t n, int32_t *out) {
+    int32_t m = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, cnt[i]);
+    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, d));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// s_j = least power of two with 448 * s_j >= max_i |D_ij| (1 for an empty beamlet).
+__global__ void fp8_scales(const unsigned *colmax_bits, int32_t J, float *scale) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < J; j += gridDim.x * blockDim.x) {
+        float m = __uint_as_float(colmax_bits[j]);
+        float s = 1.f;
+        if (m > 0.f) {
+            int e;
+            frexpf(m / 448.f, &e);
+            s = ldexpf(1.f, e);
+            while (448.f * s < m) s *= 2.f;
+            while (448.f * (s * 0.5f) >= m) s *= 0.5f;
+        }
+        scale[j] = s;
+    }
+}
+
+__global__ void to_bf16(const float *in, __nv_bfloat16 *out, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = __float2bfloat16_rn(in[e]);
+}
+
+// FP8 with the scale of column col[e] (CSR(D): columns are beamlets).
+__global__ void to_fp8_by_col(const float *in, const int32_t *col, const float *scale, uint8_t *out, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (uint8_t)__nv_cvt_float_to_fp8(in[e] / scale[col[e]], __NV_SATFINITE, __NV_E4M3);
+}
+
+// FP8 with the scale of the row (CSR(D^T): rows are beamlets); one warp per row.
+__global__ void to_fp8_by_row(const float *in, const int64_t *rowptr, int32_t n_rows, const float *scale,
+                              uint8_t *out) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += (gridDim.x * blockDim.x) >> 5) {
+        float s = scale[r];
+        for (int64_t e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32)
+            out[e] = (uint8_t)__nv_cvt_float_to_fp8(in[e] / s, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
+    void *release() {
+        void *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+int grid_for(int64_t n, int n_sm) {
+    int64_t g = (n + BUILD_THREADS - 1) / BUILD_THREADS;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)n_sm * 16));
+}
+
+int64_t round_pad(int64_t nnz) { return ((std::max<int64_t>(nnz, 1) + NNZ_PAD - 1) / NNZ_PAD) * NNZ_PAD; }
+
+// Sort each row of a CSR by column, check duplicates.
+vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows, int32_t *col, float *val,
+                      int32_t *bad, int n_sm, cudaStream_t s) {
+    if (n_rows == 0) return VMAT_OK;
+    int32_t *dmax = nullptr;
+    DevBuf bmax;
+    VMAT_CUDA(bmax.alloc(2 * sizeof(int32_t)));
+    dmax = (int32_t *)bmax.p;
+    VMAT_CUDA(cudaMemsetAsync(dmax, 0, 2 * sizeof(int32_t), s));
+    max_count<<<grid_for(n_rows, n_sm), BUILD_THREADS, 0, s>>>(cnt, n_rows, dmax);
+    VMAT_LAUNCH_CHECK();
+    int32_t maxlen = 0;
+    VMAT_CUDA(cudaMemcpyAsync(&maxlen, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    if (maxlen < 2) return VMAT_OK;
+    int cap_max = sort_smem_cap();
+    int cap = 32;
+    while (cap < maxlen && cap < cap_max) cap <<= 1;
+    size_t smem = (size_t)cap * 8;
+    VMAT_CUDA(cudaFuncSetAttribute(row_sort_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = (int)std::min<int64_t>(n_rows, (int64_t)n_sm * 8);
+    row_sort_smem<<<grid, BUILD_THREADS, smem, s>>>(rowptr, col, val, n_rows, cap, bad);
+    VMAT_LAUNCH_CHECK();
+    if (maxlen > cap) {
+        DevBuf blist;
+        VMAT_CUDA(blist.alloc((size_t)n_rows * 4));
+        int32_t *list = (int32_t *)blist.p;
+        list_long_rows<<<grid_for(n_rows, n_sm), BUILD_THREADS, 0, s>>>(rowptr, n_rows, cap, list, dmax + 1);
+        VMAT_LAUNCH_CHECK();
+        int32_t n_long = 0;
+        VMAT_CUDA(cudaMemcpyAsync(&n_long, dmax + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        int64_t pmax = 1;
+        while (pmax < maxlen) pmax <<= 1;
+        int gl = std::min<int32_t>(n_long, 64);
+        DevBuf kb, vb;
+        VMAT_CUDA(kb.alloc((size_t)gl * pmax * 4));
+        VMAT_CUDA(vb.alloc((size_t)gl * pmax * 4));
+        row_sort_global<<<gl, 1024, 0, s>>>(rowptr, col, val, list, n_long, (int32_t *)kb.p, (float *)vb.p, pmax,
+                                            bad);
+        VMAT_LAUNCH_CHECK();
+        VMAT_CUDA(cudaStreamSynchronize(s));
+    }
+    return VMAT_OK;
+}
+
+} // namespace
+
+} // namespace vmat
+
+using namespace vmat;
+
+extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, void *stream) {
+    clear_error();
+    if (!hd) return set_error(VMAT_EINVAL, "ddc_build: handle is NULL");
+    Ddc *h = as_ddc(hd);
+    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0};
+    if (opts_in) opts = *opts_in;
+    if (opts.dtype != VMAT_F32 && opts.dtype != VMAT_BF16 && opts.dtype != VMAT_FP8E4M3)
+        return set_error(VMAT_EINVAL, "ddc_build: unknown dtype %d", (int)opts.dtype);
+    if (!opts.build_D && !opts.build_Dt) return set_error(VMAT_EINVAL, "ddc_build: nothing to build");
+    if (opts.tile_cfg >= spmv_n_configs()) return set_error(VMAT_EINVAL, "ddc_build: tile_cfg out of range");
+    if (!h->coo_vox) return set_error(VMAT_ESTATE, "ddc_build: the COO copy was released by an earlier build");
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    cudaStream_t s = as_stream(stream);
+    const int n_sm = ctx->n_sm;
+    const int32_t V = h->V, J = h->J;
+    const int64_t nnz = h->nnz;
+
+    // drop an earlier build
+    {
+        Ddc keep = *h;
+        h->coo_vox = nullptr;
+        h->coo_blt = nullptr;
+        h->coo_val = nullptr;
+        h->free_all();
+        h->coo_vox = keep.coo_vox;
+        h->coo_blt = keep.coo_blt;
+        h->coo_val = keep.coo_val;
+        h->built_D = h->built_Dt = false;
+    }
+
+    cudaEvent_t e0, e1;
+    VMAT_CUDA(cudaEventCreate(&e0));
+    VMAT_CUDA(cudaEventCreate(&e1));
+    VMAT_CUDA(cudaEventRecord(e0, s));
+
+    DevBuf b_cnt_vox, b_cnt_blt, b_colmax, b_bad, b_flag, b_off, b_cnt_act, b_cur_t, b_cur_d;
+    DevBuf b_rp_t, b_col_t, b_val_t, b_rp_d, b_col_d, b_val_d, b_act, b_v2a, b_scale;
+    VMAT_CUDA(b_cnt_vox.alloc((size_t)V * 4));
+    VMAT_CUDA(b_cnt_blt.alloc((size_t)J * 4));
+    VMAT_CUDA(b_bad.alloc(4));
+    const bool fp8 = opts.dtype == VMAT_FP8E4M3;
+    if (fp8) VMAT_CUDA(b_colmax.alloc((size_t)J * 4));
+    int32_t *cnt_vox = (int32_t *)b_cnt_vox.p, *cnt_blt = (int32_t *)b_cnt_blt.p, *bad = (int32_t *)b_bad.p;
+    VMAT_CUDA(cudaMemsetAsync(cnt_vox, 0, (size_t)V * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(cnt_blt, 0, (size_t)J * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+    if (fp8) VMAT_CUDA(cudaMemsetAsync(b_colmax.p, 0, (size_t)J * 4, s));
+    if (nnz > 0) {
+        coo_check_hist<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(h->coo_vox, h->coo_blt, h->coo_val, nnz, V, J,
+                                                                      cnt_vox, cnt_blt, (unsigned *)b_colmax.p, bad);
+        VMAT_LAUNCH_CHECK();
+    }
+    int32_t hbad = 0;
+    VMAT_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return set_error(VMAT_EINVAL, "ddc_build: COO entry with voxel/beamlet index out of range or a non-finite value");
+
+    const int64_t pad = round_pad(nnz);
+    const int vb = value_bytes(opts.dtype);
+
+    // ---- CSR(D^T): rows = beamlets
+    if (opts.build_Dt) {
+        VMAT_CUDA(b_rp_t.alloc((size_t)(J + 1) * 8));
+        VMAT_TRY(scan_counts(cnt_blt, (int64_t *)b_rp_t.p, J, s));
+        VMAT_CUDA(b_col_t.alloc((size_t)pad * 4));
+        VMAT_CUDA(b_val_t.alloc((size_t)pad * 4));
+        VMAT_CUDA(cudaMemsetAsync(b_col_t.p, 0, (size_t)pad * 4, s));
+        VMAT_CUDA(cudaMemsetAsync(b_val_t.p, 0, (size_t)pad * 4, s));
+        VMAT_CUDA(b_cur_t.alloc((size_t)J * 4));
+        VMAT_CUDA(cudaMemsetAsync(b_cur_t.p, 0, (size_t)J * 4, s));
+    }
+    // ---- CSR(D): rows = voxels with at least one entry
+    int32_t n_active = 0;
+    if (opts.build_D) {
+        VMAT_CUDA(b_flag.alloc((size_t)V * 4));
+        VMAT_CUDA(b_off.alloc((size_t)(V + 1) * 8));
+        flag_nonzero<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, V, (int32_t *)b_flag.p);
+        VMAT_LAUNCH_CHECK();
+        VMAT_TRY(scan_counts((int32_t *)b_flag.p, (int64_t *)b_off.p, V, s));
+        int64_t na = 0;
+        VMAT_CUDA(cudaMemcpyAsync(&na, (int64_t *)b_off.p + V, 8, cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        n_active = (int32_t)na;
+        VMAT_CUDA(b_act.alloc((size_t)std::max(n_active, 1) * 4));
+        VMAT_CUDA(b_v2a.alloc((size_t)V * 4));
+        VMAT_CUDA(b_cnt_act.alloc((size_t)std::max(n_active, 1) * 4));
+        compact_voxels<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, (int64_t *)b_off.p, V,
+                                                                  (int32_t *)b_act.p, (int32_t *)b_v2a.p,
+                                                                  (int32_t *)b_cnt_act.p);
+        VMAT_LAUNCH_CHECK();
+        VMAT_CUDA(b_rp_d.alloc((size_t)(n_active + 1) * 8));
+        VMAT_TRY(scan_counts((int32_t *)b_cnt_act.p, (int64_t *)b_rp_d.p, n_active, s));
+        VMAT_CUDA(b_col_d.alloc((size_t)pad * 4));
+        VMAT_CUDA(b_val_d.alloc((size_t)pad * 4));
+        VMAT_CUDA(cudaMemsetAsync(b_col_d.p, 0, (size_t)pad * 4, s));
+        VMAT_CUDA(cudaMemsetAsync(b_val_d.p, 0, (size_t)pad * 4, s));
+        VMAT_CUDA(b_cur_d.alloc((size_t)std::max(n_active, 1) * 4));
+        VMAT_CUDA(cudaMemsetAsync(b_cur_d.p, 0, (size_t)std::max(n_active, 1) * 4, s));
+    }
+    if (nnz > 0) {
+        coo_scatter<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(
+            h->coo_vox, h->coo_blt, h->coo_val, nnz, (int64_t *)b_rp_t.p, (int32_t *)b_cur_t.p, (int32_t *)b_col_t.p,
+            (float *)b_val_t.p, (int64_t *)b_rp_d.p, (int32_t *)b_v2a.p, (int32_t *)b_cur_d.p, (int32_t *)b_col_d.p,
+            (float *)b_val_d.p);
+        VMAT_LAUNCH_CHECK();
+    }
+    if (opts.build_Dt)
+        VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s));
+    if (opts.build_D)
+        VMAT_TRY(sort_rows((int64_t *)b_rp_d.p, (int32_t *)b_cnt_act.p, n_active, (int32_t *)b_col_d.p,
+                           (float *)b_val_d.p, bad, n_sm, s));
+    VMAT_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    if (hbad & DEV_DUPLICATE) return set_error(VMAT_EINVAL, "ddc_build: duplicate (voxel, beamlet) entry in the COO input");
+
+    // ---- quantisation
+    if (fp8) {
+        VMAT_CUDA(b_scale.alloc((size_t)J * 4));
+        fp8_scales<<<grid_for(J, n_sm), BUILD_THREADS, 0, s>>>((unsigned *)b_colmax.p, J, (float *)b_scale.p);
+        VMAT_LAUNCH_CHECK();
+    }
+    auto quantise = [&](DevBuf &bval, const int32_t *col, const int64_t *rowptr, int32_t n_rows, bool by_row,
+                        void **out) -> vmat_status {
+        if (opts.dtype == VMAT_F32) {
+            *out = bval.release();
+            return VMAT_OK;
+        }
+        DevBuf q;
+        VMAT_CUDA(q.alloc((size_t)pad * vb));
+        VMAT_CUDA(cudaMemsetAsync(q.p, 0, (size_t)pad * vb, s));
+        if (opts.dtype == VMAT_BF16) {
+            to_bf16<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>((float *)bval.p, (__nv_bfloat16 *)q.p, nnz);
+        } else if (by_row) {
+            to_fp8_by_row<<<grid_for((int64_t)n_rows * 32, n_sm), BUILD_THREADS, 0, s>>>(
+                (float *)bval.p, rowptr, n_rows, (float *)b_scale.p, (uint8_t *)q.p);
+        } else {
+            to_fp8_by_col<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>((float *)bval.p, col, (float *)b_scale.p,
+                                                                         (uint8_t *)q.p, nnz);
+        }
+        VMAT_LAUNCH_CHECK();
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        *out = q.release();
+        return VMAT_OK;
+    };
+
+    int cfg = opts.tile_cfg >= 0 ? opts.tile_cfg : spmv_default_config();
+    if (opts.build_Dt) {
+        CsrMat &m = h->Dt;
+        m.n_rows = J;
+        m.n_cols = V;
+        m.nnz = nnz;
+        m.nnz_pad = pad;
+        VMAT_TRY(quantise(b_val_t, (int32_t *)b_col_t.p, (int64_t *)b_rp_t.p, J, true, &m.val));
+        m.rowptr = (int64_t *)b_rp_t.release();
+        m.col = (int32_t *)b_col_t.release();
+        m.row_ids = nullptr;
+        VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
+        h->built_Dt = true;
+    }
+    if (opts.build_D) {
+        CsrMat &m = h->D;
+        m.n_rows = n_active;
+        m.n_cols = J;
+        m.nnz = nnz;
+        m.nnz_pad = pad;
+        VMAT_TRY(quantise(b_val_d, (int32_t *)b_col_d.p, (int64_t *)b_rp_d.p, n_active, false, &m.val));
+        m.rowptr = (int64_t *)b_rp_d.release();
+        m.col = (int32_t *)b_col_d.release();
+        h->act_vox = (int32_t *)b_act.release();
+        h->vox2act = (int32_t *)b_v2a.release();
+        h->n_active = n_active;
+        m.row_ids = h->act_vox;
+        VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
+        h->built_D = true;
+    }
+    if (fp8) {
+        h->scale = (float *)b_scale.release();
+        VMAT_CUDA(cudaMalloc(&h->xs, (size_t)J * 4));
+    }
+    h->dtype = opts.dtype;
+    if (!opts.keep_coo) {
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        cudaFree(h->coo_vox);
+        cudaFree(h->coo_blt);
+        cudaFree(h->coo_val);
+        h->coo_vox = h->coo_blt = nullptr;
+        h->coo_val = nullptr;
+    }
+    VMAT_CUDA(cudaEventRecord(e1, s));
+    VMAT_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->build_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (opts.autotune) VMAT_TRY(spmv_autotune(*h, s));
+    return VMAT_OK;
+}

@@ -1,0 +1,213 @@
+// Internal declarations shared by the libvmat translation units (host + device helpers).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/vmat.h"
+
+namespace vmat {
+
+// ---------------------------------------------------------------------------
+// Error reporting (host)
+// ---------------------------------------------------------------------------
+vmat_status set_error(vmat_status st, const char *fmt, ...);
+void clear_error();
+
+#define VMAT_CUDA(call)                                                                     \
+    do {                                                                                    \
+        cudaError_t err__ = (call);                                                         \
+        if (err__ != cudaSuccess)                                                           \
+            return ::vmat::set_error(err__ == cudaErrorMemoryAllocation ? VMAT_ENOMEM : VMAT_ECUDA, \
+                                     "%s failed: %s (%s:%d)", #call, cudaGetErrorString(err__), \
+                                     __FILE__, __LINE__);                                  \
+    } while (0)
+
+#define VMAT_TRY(expr)                       \
+    do {                                     \
+        vmat_status st__ = (expr);           \
+        if (st__ != VMAT_OK) return st__;    \
+    } while (0)
+
+// Kernels launched by this library in this process (each launch site adds one).
+extern std::atomic<long long> g_launches;
+
+#define VMAT_LAUNCH_CHECK()                                                  \
+    do {                                                                     \
+        ::vmat::g_launches.fetch_add(1, std::memory_order_relaxed);          \
+        VMAT_CUDA(cudaGetLastError());                                       \
+    } while (0)
+
+// Device status word bits (see vmat_device_status).
+enum : int32_t { DEV_TIMEOUT = 1, DEV_INDEX = 2, DEV_DUPLICATE = 4 };
+
+// Per-device facts and the device status word.
+struct DeviceCtx {
+    int device = -1;
+    int n_sm = 0;
+    int32_t *status = nullptr; // device int32, OR-ed by kernels
+};
+vmat_status device_ctx(DeviceCtx **out);
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync).
+struct Scratch {
+    void *ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    ~Scratch() {
+        if (ptr) cudaFreeAsync(ptr, stream);
+    }
+    vmat_status alloc(size_t bytes, cudaStream_t s);
+};
+
+// ---------------------------------------------------------------------------
+// CSR matrix held by a handle
+// ---------------------------------------------------------------------------
+constexpr int64_t NNZ_PAD = 8192; // value/column arrays padded to a multiple of this
+
+struct CsrMat {
+    int32_t n_rows = 0, n_cols = 0;
+    int64_t nnz = 0, nnz_pad = 0;
+    int64_t *rowptr = nullptr;   // [n_rows + 1]
+    int32_t *col = nullptr;      // [nnz_pad], padding 0
+    void *val = nullptr;         // [nnz_pad] of the stored type, padding 0
+    const int32_t *row_ids = nullptr; // output index of each row (CSR(D): compact -> voxel), or null
+    // tiles
+    int cfg = 0;                 // tile configuration index
+    int32_t tile = 0;            // nonzeros per tile
+    int32_t n_tiles = 0;
+    int32_t *tile_row = nullptr; // [n_tiles + 1]
+    float *carry_val = nullptr;  // [n_tiles]
+    int32_t *tile_flag = nullptr; // [n_tiles] scratch for active-tile lists
+    int32_t *tile_list = nullptr; // [n_tiles]
+    int32_t *n_list = nullptr;   // [1]
+};
+
+struct Ddc {
+    int32_t V = 0, J = 0;
+    int64_t nnz = 0;
+    int device = -1;
+    int32_t *coo_vox = nullptr, *coo_blt = nullptr;
+    float *coo_val = nullptr;
+    vmat_dtype dtype = VMAT_F32;
+    bool built_D = false, built_Dt = false;
+    CsrMat D, Dt;
+    int32_t n_active = 0;
+    int32_t *act_vox = nullptr; // [n_active] compact row -> voxel
+    int32_t *vox2act = nullptr; // [V] voxel -> compact row or -1
+    float *scale = nullptr;     // [J] FP8 per-beamlet scale
+    float *xs = nullptr;        // [J] scratch: scaled x for FP8 CSR(D)
+    double build_ms = 0.0;
+    void free_all();
+};
+
+inline Ddc *as_ddc(vmat_ddc h) { return reinterpret_cast<Ddc *>(h); }
+
+// ---------------------------------------------------------------------------
+// Cross-file entry points (host)
+// ---------------------------------------------------------------------------
+int value_bytes(vmat_dtype t);
+
+// SpMV on one CSR; x/y device.  cp_active/bpc restrict to rows of active CPs (may be null).
+vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
+                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s);
+vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s);
+int spmv_n_configs();
+int spmv_default_config();
+int32_t spmv_config_tile(int cfg);
+
+vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compact, cudaStream_t s);
+
+// Objective over n voxels.  idx (may be null): voxel i of z is voxel idx[i] of struct_id.
+// g_scatter (may be null): write g[i] to g_scatter[idx[i]] instead of g[i].
+vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
+                           float *g_scatter, double *F, double F_offset, cudaStream_t s);
+
+vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
+                               bool compact, cudaStream_t s);
+
+struct BBWork; // defined in mp_bb.cu
+vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
+                       const int32_t *struct_idx, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);
+
+vmat_status validate_mlc(const vmat_mlc *mlc);
+vmat_status validate_voxels(const vmat_voxels *vox);
+
+// Exclusive scan of int32 counts into int64 offsets (out has n + 1 entries).
+vmat_status scan_counts(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Time every SpMV tile configuration on the handle's matrices and keep the fastest.
+vmat_status spmv_autotune(Ddc &h, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers: shared-memory addresses, mbarrier and bulk async copy (TMA)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after about `limit_cycles` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit_cycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > limit_cycles) return false;
+    }
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 1-D bulk copy global -> shared, completion counted on an mbarrier.
+// dst/src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL; // ~2 s at 2 GHz
+
+} // namespace vmat

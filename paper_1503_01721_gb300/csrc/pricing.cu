@@ -1,0 +1,236 @@
+// Pricing problem, second step (Section 2.2.2): the best opening [L, R) of every
+// MLC row of every unoccupied control point, then the CP whose aperture (the
+// sum of its row bests) has the largest price.
+//
+// The paper uses one thread per row for the first kernel and one thread per CP
+// for the second.  Here one warp handles a row: lane 0 builds the float64
+// prefix sums P_c sequentially in column order, the lanes evaluate every
+// feasible pair (P_R - P_L) and the warp reduces with the full tie-break key
+// (value desc, width asc, |L + R - n_cols| asc, L asc).  Every compared value is
+// produced by the same float64 operations in the same order as the sequential
+// definition, and the key is a total order, so the choice is bit-exact.
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace vmat {
+
+constexpr int MAX_ARCS = 64;
+constexpr int PR_WARPS = 8;
+
+struct PricingGeom {
+    int32_t K, n_rows, n_cols, travel, n_arcs;
+    int32_t arc_first[MAX_ARCS + 1];
+};
+
+struct RowBest {
+    double v;
+    int32_t w, cd, L;
+    bool has;
+};
+
+__device__ __forceinline__ bool better(const RowBest &a, const RowBest &b) {
+    if (!a.has) return false;
+    if (!b.has) return true;
+    if (a.v != b.v) return a.v > b.v;
+    if (a.w != b.w) return a.w < b.w;
+    if (a.cd != b.cd) return a.cd < b.cd;
+    return a.L < b.L;
+}
+
+// Nearest occupied CP on one side of k within its arc (search direction dir).
+__device__ int nearest_occupied(const PricingGeom &g, const uint8_t *occupied, int k, int dir, int lane) {
+    int a = 0;
+    while (a + 1 < g.n_arcs && g.arc_first[a + 1] <= k) ++a;
+    const int lo = g.arc_first[a], hi = g.arc_first[a + 1]; // [lo, hi)
+    for (int base = k + dir; base >= lo && base < hi; base += 32 * dir) {
+        const int kk = base + lane * dir;
+        const bool hit = kk >= lo && kk < hi && occupied[kk];
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) return base + (__ffs(m) - 1) * dir;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(PR_WARPS * 32)
+    price_rows_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
+                      const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok) {
+    extern __shared__ double sP[]; // PR_WARPS x (n_cols + 1)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
+    if (gw >= (int64_t)g.K * g.n_rows) return;
+    const int k = (int)(gw / g.n_rows), r = (int)(gw % g.n_rows);
+    if (occupied[k]) return;
+    const int N = g.n_cols;
+    int Lmin = 0, Lmax = N, Rmin = 0, Rmax = N;
+    for (int dir = -1; dir <= 1; dir += 2) {
+        const int kk = nearest_occupied(g, occupied, k, dir, lane);
+        if (kk >= 0) {
+            const int reach = abs(k - kk) * g.travel;
+            const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
+            Lmin = max(Lmin, Ln - reach);
+            Lmax = min(Lmax, Ln + reach);
+            Rmin = max(Rmin, Rn - reach);
+            Rmax = min(Rmax, Rn + reach);
+        }
+    }
+    double *P = sP + wid * (N + 1);
+    if (lane == 0) {
+        const float *row = pi + ((int64_t)k * g.n_rows + r) * N;
+        double acc = 0.0;
+        P[0] = 0.0;
+        for (int c = 0; c < N; ++c) {
+            acc = acc + (double)row[c];
+            P[c + 1] = acc;
+        }
+    }
+    __syncwarp();
+    RowBest best;
+    best.has = false;
+    best.v = 0.0;
+    best.w = best.cd = best.L = 0;
+    for (int L = Lmin + lane; L <= Lmax; L += 32) {
+        const double PL = P[L];
+        for (int R = max(L, Rmin); R <= Rmax; ++R) {
+            RowBest c;
+            c.has = true;
+            c.v = P[R] - PL;
+            c.w = R - L;
+            c.cd = abs(L + R - N);
+            c.L = L;
+            if (better(c, best)) best = c;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        RowBest o;
+        o.v = __shfl_down_sync(0xffffffffu, best.v, d);
+        o.w = __shfl_down_sync(0xffffffffu, best.w, d);
+        o.cd = __shfl_down_sync(0xffffffffu, best.cd, d);
+        o.L = __shfl_down_sync(0xffffffffu, best.L, d);
+        o.has = __shfl_down_sync(0xffffffffu, (int)best.has, d) != 0;
+        if (lane + d < 32 && better(o, best)) best = o;
+    }
+    if (lane == 0) {
+        rb_v[gw] = best.v;
+        rb_lr[2 * gw] = (int16_t)best.L;
+        rb_lr[2 * gw + 1] = (int16_t)(best.L + best.w);
+        rb_ok[gw] = best.has ? 1 : 0;
+    }
+}
+
+constexpr int CP_THREADS = 1024;
+
+__global__ void __launch_bounds__(CP_THREADS)
+    price_cps_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const double *__restrict__ rb_v,
+                     const int16_t *__restrict__ rb_lr, const uint8_t *__restrict__ rb_ok, int32_t *best_cp,
+                     int16_t *best_leaves, double *best_price) {
+    __shared__ double sv[CP_THREADS / 32];
+    __shared__ int sk[CP_THREADS / 32];
+    __shared__ int kwin;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double bv = -INFINITY;
+    int bk = -1;
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) { // k ascending: a strict > keeps the smallest k
+        if (occupied[k]) continue;
+        double price = 0.0;
+        bool ok = true;
+        for (int r = 0; r < g.n_rows; ++r) {
+            const int64_t i = (int64_t)k * g.n_rows + r;
+            ok = ok && rb_ok[i];
+            price = price + rb_v[i];
+        }
+        if (ok && (bk < 0 || price > bv)) {
+            bv = price;
+            bk = k;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, d);
+        const int ok = __shfl_down_sync(0xffffffffu, bk, d);
+        if (lane + d < 32 && ok >= 0 && (bk < 0 || ov > bv || (ov == bv && ok < bk))) {
+            bv = ov;
+            bk = ok;
+        }
+    }
+    if (lane == 0) {
+        sv[wid] = bv;
+        sk[wid] = bk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = -INFINITY;
+        int kb = -1;
+        for (int w = 0; w < CP_THREADS / 32; ++w)
+            if (sk[w] >= 0 && (kb < 0 || sv[w] > v || (sv[w] == v && sk[w] < kb))) {
+                v = sv[w];
+                kb = sk[w];
+            }
+        *best_cp = kb;
+        *best_price = kb >= 0 ? v : -INFINITY;
+        kwin = kb;
+    }
+    __syncthreads();
+    if (kwin >= 0)
+        for (int r = threadIdx.x; r < g.n_rows; r += blockDim.x) {
+            const int64_t i = (int64_t)kwin * g.n_rows + r;
+            best_leaves[2 * r] = rb_lr[2 * i];
+            best_leaves[2 * r + 1] = rb_lr[2 * i + 1];
+        }
+}
+
+vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
+                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws,
+                                 cudaStream_t s) {
+    if (mlc->n_arcs > MAX_ARCS) return set_error(VMAT_EUNSUPPORTED, "price_apertures: more than %d arcs", MAX_ARCS);
+    PricingGeom g;
+    g.K = mlc->K;
+    g.n_rows = mlc->n_rows;
+    g.n_cols = mlc->n_cols;
+    g.travel = mlc->travel_cols;
+    g.n_arcs = mlc->n_arcs;
+    for (int a = 0; a < mlc->n_arcs; ++a) g.arc_first[a] = mlc->arc_first_cp[a];
+    g.arc_first[mlc->n_arcs] = mlc->K;
+    const int64_t rows = (int64_t)g.K * g.n_rows;
+    double *rb_v = static_cast<double *>(ws);
+    int16_t *rb_lr = reinterpret_cast<int16_t *>(rb_v + rows);
+    uint8_t *rb_ok = reinterpret_cast<uint8_t *>(rb_lr + 2 * rows);
+    const size_t smem = (size_t)PR_WARPS * (g.n_cols + 1) * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        VMAT_CUDA(cudaFuncSetAttribute(price_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(PR_WARPS * 1025 * sizeof(double))));
+        attr_set = true;
+    }
+    const int64_t blocks = (rows + PR_WARPS - 1) / PR_WARPS;
+    price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok);
+    VMAT_LAUNCH_CHECK();
+    price_cps_kernel<<<1, CP_THREADS, 0, s>>>(g, occupied, rb_v, rb_lr, rb_ok, best_cp, best_leaves, best_price);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
+    const size_t rows = (size_t)mlc->K * mlc->n_rows;
+    return rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
+}
+
+} // namespace vmat
+
+using namespace vmat;
+
+extern "C" vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied,
+                                       const int16_t *leaves, int32_t *best_cp, int16_t *best_leaves,
+                                       double *best_price, void *stream) {
+    clear_error();
+    VMAT_TRY(validate_mlc(mlc));
+    if (!pi || !occupied || !leaves || !best_cp || !best_leaves || !best_price)
+        return set_error(VMAT_EINVAL, "price_apertures: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    Scratch ws;
+    VMAT_TRY(ws.alloc(pricing_scratch_bytes(mlc), s));
+    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s);
+}

@@ -1,0 +1,572 @@
+// Tile-streamed CSR SpMV for the two hot products of the paper:
+//   beamlet price   pi = D^T g   (Eq. 3; CSR(D^T), one row per beamlet)
+//   forward dose    d  = D x     (Section 2.1, Eq. 5; CSR(D), one row per non-empty voxel)
+//
+// The paper assigns one warp per beamlet row on Fermi (Section 2.2.2).  Here the
+// nonzeros are cut into fixed tiles of THREADS*E entries independent of row
+// boundaries, so every CTA streams the same number of bytes whatever the row
+// lengths.  Per tile:
+//   1. one elected thread moves the tile's values and column indices into shared
+//      memory with cp.async.bulk (TMA bulk copies, L2 evict-first), STAGES tiles
+//      ahead, completion counted on an mbarrier;
+//   2. every thread takes 4-entry chunks in lane order (consecutive lanes hold
+//      consecutive nonzeros, so the gathers x[col] of a warp touch few L2
+//      sectors), multiplies, and stores the products to shared memory in an
+//      XOR-swizzled layout;
+//   3. every thread reads back E consecutive products (conflict-free), walks its
+//      row boundaries, writes rows that start and end inside its run, and takes
+//      part in a keyed (segmented) scan over the CTA for rows that span threads;
+//   4. the partial sum of the row open at the tile's end is stored as a carry and
+//      a second small kernel adds carries to their rows in tile order.
+// All orders of addition are fixed, so results are bitwise reproducible.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace vmat {
+
+struct SpmvParams {
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+    const float *x;
+    float *y;
+    const float *row_scale;  // multiply row r's sum by row_scale[r] (FP8 CSR(D^T)), or null
+    const int32_t *row_ids;  // write row r to y[row_ids[r]], or null for y[r]
+    const int32_t *tile_row; // [n_tiles + 1]
+    const int32_t *tile_list; // tiles to process, or null for all
+    const int32_t *n_list;   // device count of tile_list
+    int32_t n_tiles;
+    int32_t n_rows;
+    int64_t nnz;
+    float *carry_val;
+    int32_t *status;
+};
+
+template <typename VT> struct Vals;
+template <> struct Vals<float> {
+    static __device__ __forceinline__ void load4(const unsigned char *base, int e0, float v[4]) {
+        float4 t = *reinterpret_cast<const float4 *>(base + (size_t)e0 * 4);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+};
+template <> struct Vals<__nv_bfloat16> {
+    static __device__ __forceinline__ void load4(const unsigned char *base, int e0, float v[4]) {
+        uint2 t = *reinterpret_cast<const uint2 *>(base + (size_t)e0 * 2);
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
+    }
+};
+template <> struct Vals<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ void load4(const unsigned char *base, int e0, float v[4]) {
+        uint32_t t = *reinterpret_cast<const uint32_t *>(base + e0);
+        __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t & 0xffffu), __NV_E4M3);
+        __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t >> 16), __NV_E4M3);
+        float2 fa = __half22float2(*reinterpret_cast<__half2 *>(&a));
+        float2 fb = __half22float2(*reinterpret_cast<__half2 *>(&b));
+        v[0] = fa.x;
+        v[1] = fa.y;
+        v[2] = fb.x;
+        v[3] = fb.y;
+    }
+};
+
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+template <int THREADS, int E, int STAGES, typename VT> struct TileShape {
+    static constexpr int TILE = THREADS * E;
+    static constexpr int NW = THREADS / 32;
+    static constexpr int Q = E / 4;                      // float4 chunks per thread run
+    static constexpr int SWZ_SHIFT = ilog2c(8 / (Q < 8 ? Q : 8)); // keeps 8 readers on distinct 16B slots
+    static constexpr int VBYTES = TILE * (int)sizeof(VT);
+    static constexpr int CBYTES = TILE * 4;
+    static constexpr int OFF_COL = STAGES * VBYTES;
+    static constexpr int OFF_PROD = OFF_COL + STAGES * CBYTES;
+    static constexpr int OFF_BAR = OFF_PROD + TILE * 4;
+    static constexpr int OFF_W = OFF_BAR + STAGES * 8;
+    static constexpr int SMEM = OFF_W + NW * 12;
+    static_assert(E % 4 == 0 && (Q & (Q - 1)) == 0, "E must be 4 * power of two");
+    static_assert(VBYTES % 16 == 0 && CBYTES % 16 == 0, "bulk copies need 16-byte multiples");
+};
+
+__device__ __forceinline__ void store_row(const SpmvParams &p, int32_t r, float v) {
+    if (p.row_scale) v *= p.row_scale[r];
+    p.y[p.row_ids ? p.row_ids[r] : r] = v;
+}
+
+template <int THREADS, int E, int STAGES, typename VT>
+__global__ void __launch_bounds__(THREADS) spmv_tile_kernel(SpmvParams p) {
+    using S = TileShape<THREADS, E, STAGES, VT>;
+    constexpr int TILE = S::TILE, Q = S::Q, NW = S::NW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sval = smem;
+    unsigned char *scol = smem + S::OFF_COL;
+    float *prod = reinterpret_cast<float *>(smem + S::OFF_PROD);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::OFF_BAR);
+    int32_t *wkey = reinterpret_cast<int32_t *>(smem + S::OFF_W);
+    int32_t *wfirst = wkey + NW;
+    float *wval = reinterpret_cast<float *>(wfirst + NW);
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t n_work = p.tile_list ? *p.n_list : p.n_tiles;
+    const int32_t n_rows = p.n_rows;
+    const uint64_t pol = l2_evict_first_policy();
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int32_t w, int s) {
+        const int32_t b = p.tile_list ? p.tile_list[w] : w;
+        mbar_arrive_expect_tx(&bars[s], S::VBYTES + S::CBYTES);
+        bulk_g2s(sval + s * S::VBYTES, static_cast<const unsigned char *>(p.val) + (size_t)b * S::VBYTES, S::VBYTES,
+                 &bars[s], pol);
+        bulk_g2s(scol + s * S::CBYTES, p.col + (size_t)b * TILE, S::CBYTES, &bars[s], pol);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            int32_t w = blockIdx.x + s * gridDim.x;
+            if (w < n_work) issue(w, s);
+        }
+    }
+
+    int it = 0;
+    bool timed_out = false;
+    for (int32_t w = blockIdx.x; w < n_work; w += gridDim.x, ++it) {
+        const int s = it % STAGES;
+        const uint32_t parity = (uint32_t)((it / STAGES) & 1);
+        bool ok = mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_CYCLES);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(p.status, DEV_TIMEOUT);
+            timed_out = true;
+            break;
+        }
+        const int32_t b = p.tile_list ? p.tile_list[w] : w;
+        const int64_t tstart = (int64_t)b * TILE;
+
+        // ---- phase A: products in lane order, stored swizzled
+        const unsigned char *sv = sval + s * S::VBYTES;
+        const int32_t *sc = reinterpret_cast<const int32_t *>(scol + s * S::CBYTES);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int c = q * THREADS + tid; // chunk of 4 entries
+            const int e0 = c * 4;
+            int4 cc = *reinterpret_cast<const int4 *>(sc + e0);
+            float v[4];
+            Vals<VT>::load4(sv, e0, v);
+            const int64_t g0 = tstart + e0;
+            float4 pr;
+            pr.x = g0 + 0 < p.nnz ? v[0] * __ldg(p.x + cc.x) : 0.f;
+            pr.y = g0 + 1 < p.nnz ? v[1] * __ldg(p.x + cc.y) : 0.f;
+            pr.z = g0 + 2 < p.nnz ? v[2] * __ldg(p.x + cc.z) : 0.f;
+            pr.w = g0 + 3 < p.nnz ? v[3] * __ldg(p.x + cc.w) : 0.f;
+            const int tr = c / Q, qq = c % Q;
+            const int phys = tr * Q + (qq ^ ((tr >> S::SWZ_SHIFT) & (Q - 1)));
+            reinterpret_cast<float4 *>(prod)[phys] = pr;
+        }
+        __syncthreads(); // stage s fully consumed, products visible
+        if (tid == 0) {
+            const int32_t wn = w + STAGES * gridDim.x;
+            if (wn < n_work) {
+                fence_proxy_async_smem();
+                issue(wn, s);
+            }
+        }
+
+        // ---- phase B: each thread owns entries [a, a + E) of the tile
+        float pv[E];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int phys = tid * Q + (q ^ ((tid >> S::SWZ_SHIFT) & (Q - 1)));
+            float4 t = reinterpret_cast<const float4 *>(prod)[phys];
+            pv[4 * q + 0] = t.x;
+            pv[4 * q + 1] = t.y;
+            pv[4 * q + 2] = t.z;
+            pv[4 * q + 3] = t.w;
+        }
+        const int64_t a = tstart + (int64_t)tid * E;
+        // row containing entry a: largest r with rowptr[r] <= a (n_rows once past the end)
+        int32_t lo = p.tile_row[b], hi = p.tile_row[b + 1];
+        while (lo < hi) {
+            int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+            if (__ldg(p.rowptr + mid) <= a) lo = mid;
+            else hi = mid - 1;
+        }
+        int32_t r = lo;
+        if (b == 0 && tid == 0)
+            for (int32_t rr = 0; rr < r; ++rr) store_row(p, rr, 0.f); // leading empty rows
+        int64_t nxt = r < n_rows ? __ldg(p.rowptr + r + 1) : INT64_MAX;
+        float run = 0.f;
+        int32_t head_row = -1;
+        float head_val = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            run += pv[e];
+            const int64_t i1 = a + e + 1;
+            while (i1 == nxt) { // row r ends after entry a + e (empty rows end here too)
+                if (head_row < 0 && r == lo) {
+                    head_row = r;
+                    head_val = run;
+                } else {
+                    store_row(p, r, run);
+                }
+                run = 0.f;
+                ++r;
+                nxt = r < n_rows ? __ldg(p.rowptr + r + 1) : INT64_MAX;
+            }
+        }
+        // ---- keyed inclusive scan of the open-row partials over the CTA
+        int32_t key = r;
+        float val = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t k2 = __shfl_up_sync(0xffffffffu, key, d);
+            float v2 = __shfl_up_sync(0xffffffffu, val, d);
+            if (lane >= d && k2 == key) val += v2;
+        }
+        const int32_t kfirst = __shfl_sync(0xffffffffu, key, 0);
+        if (lane == 31) {
+            wkey[wid] = key;
+            wval[wid] = val;
+        }
+        if (lane == 0) wfirst[wid] = key;
+        __syncthreads();
+        float tprev = 0.f;
+        int32_t kprev = -2;
+        if (wid > 0) {
+            float t = 0.f;
+            for (int ww = 0; ww < wid; ++ww) {
+                const bool cont = ww > 0 && wfirst[ww] == wkey[ww] && wkey[ww - 1] == wkey[ww];
+                t = wval[ww] + (cont ? t : 0.f);
+            }
+            tprev = t;
+            kprev = wkey[wid - 1];
+            if (key == kfirst && kprev == key) val += tprev;
+        }
+        float pval = __shfl_up_sync(0xffffffffu, val, 1);
+        int32_t pkey = __shfl_up_sync(0xffffffffu, key, 1);
+        if (lane == 0) {
+            pval = tprev;
+            pkey = kprev;
+        }
+        if (head_row >= 0) store_row(p, head_row, head_val + (pkey == head_row ? pval : 0.f));
+        // The row open at the tile's end is tile_row[b + 1] (the row holding entry
+        // (b + 1) * TILE, or n_rows): the last thread's key.  Its partial is the carry.
+        if (tid == THREADS - 1) p.carry_val[b] = val;
+        __syncthreads(); // products and warp totals are reused by the next tile
+    }
+    if (timed_out && tid == 0) {
+        // let copies already issued land before the CTA exits (bounded)
+        for (int k = 0; k < STAGES; ++k) {
+            const int it2 = it + k;
+            const int32_t w2 = blockIdx.x + it2 * gridDim.x;
+            if (w2 < n_work) mbar_wait_bounded(&bars[it2 % STAGES], (uint32_t)((it2 / STAGES) & 1), WAIT_LIMIT_CYCLES);
+        }
+    }
+}
+
+// Adds tile carries to their rows.  Tile b's carry belongs to row tile_row[b + 1];
+// the first tile of each run of equal keys sums the run left to right.  Rows of
+// inactive CPs are skipped (their tiles may not have run).
+__global__ void spmv_fixup(const int32_t *tile_row, const float *carry_val, int32_t n_tiles,
+                           const int32_t *tile_list, const int32_t *n_list, int32_t n_rows, float *y,
+                           const int32_t *row_ids, const float *row_scale, const uint8_t *cp_active, int32_t bpc) {
+    const int32_t n_work = tile_list ? *n_list : n_tiles;
+    for (int32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
+        const int32_t b = tile_list ? tile_list[w] : w;
+        const int32_t key = tile_row[b + 1];
+        if (key >= n_rows) continue;
+        if (cp_active && !cp_active[key / bpc]) continue;
+        if (b > 0 && tile_row[b] == key) continue;
+        float sum = carry_val[b];
+        for (int32_t bb = b + 1; bb < n_tiles && tile_row[bb + 1] == key; ++bb) sum += carry_val[bb];
+        if (row_scale) sum *= row_scale[key];
+        y[row_ids ? row_ids[key] : key] += sum;
+    }
+}
+
+// tile_row[b] = largest r with rowptr[r] <= b * tile (tile_row[0] = 0, tile_row[n_tiles] = n_rows).
+__global__ void compute_tile_rows(const int64_t *rowptr, int32_t n_rows, int32_t tile, int32_t n_tiles,
+                                  int32_t *tile_row) {
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= n_tiles; b += gridDim.x * blockDim.x) {
+        if (b == 0) {
+            tile_row[0] = 0;
+            continue;
+        }
+        const int64_t a = (int64_t)b * tile;
+        int32_t lo = 0, hi = n_rows;
+        while (lo < hi) {
+            int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+            if (rowptr[mid] <= a) lo = mid;
+            else hi = mid - 1;
+        }
+        tile_row[b] = lo;
+    }
+}
+
+// A tile is active when its row range [tile_row[b], tile_row[b+1]] meets a row of an active CP.
+__global__ void flag_active_tiles(const int32_t *tile_row, int32_t n_tiles, int32_t n_rows, const uint8_t *cp_active,
+                                  int32_t bpc, int32_t *flag) {
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_tiles; b += gridDim.x * blockDim.x) {
+        const int32_t r0 = tile_row[b];
+        const int32_t r1 = min(tile_row[b + 1], n_rows - 1);
+        int32_t f = 0;
+        for (int32_t k = r0 / bpc; k <= r1 / bpc && !f; ++k) f = cp_active[k] != 0;
+        flag[b] = f;
+    }
+}
+
+__global__ void compact_tiles(const int32_t *flag, const int64_t *off, int32_t n_tiles, int32_t *list,
+                              int32_t *n_list) {
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_tiles; b += gridDim.x * blockDim.x)
+        if (flag[b]) list[off[b]] = b;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_list = (int32_t)off[n_tiles];
+}
+
+__global__ void scale_vector(const float *x, const float *s, float *out, int32_t n) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = x[i] * s[i];
+}
+
+// ---------------------------------------------------------------------------
+// Configurations and dispatch
+// ---------------------------------------------------------------------------
+struct Cfg {
+    int threads, e, stages;
+};
+static const Cfg kCfgs[] = {{256, 16, 2}, {256, 8, 3}, {512, 8, 2}, {128, 16, 3}};
+constexpr int N_CFG = 4;
+
+using KernelFn = void (*)(SpmvParams);
+
+template <typename VT> KernelFn kernel_for(int cfg) {
+    switch (cfg) {
+    case 0: return spmv_tile_kernel<256, 16, 2, VT>;
+    case 1: return spmv_tile_kernel<256, 8, 3, VT>;
+    case 2: return spmv_tile_kernel<512, 8, 2, VT>;
+    default: return spmv_tile_kernel<128, 16, 3, VT>;
+    }
+}
+
+template <typename VT> int smem_for(int cfg) {
+    switch (cfg) {
+    case 0: return TileShape<256, 16, 2, VT>::SMEM;
+    case 1: return TileShape<256, 8, 3, VT>::SMEM;
+    case 2: return TileShape<512, 8, 2, VT>::SMEM;
+    default: return TileShape<128, 16, 3, VT>::SMEM;
+    }
+}
+
+struct Launch {
+    KernelFn fn;
+    int threads, smem, blocks_per_sm;
+};
+
+static vmat_status launch_info(vmat_dtype dt, int cfg, Launch *out) {
+    static Launch cache[3][N_CFG] = {};
+    static int cached_dev[3][N_CFG];
+    int dev;
+    VMAT_CUDA(cudaGetDevice(&dev));
+    Launch &L = cache[dt][cfg];
+    if (L.fn && cached_dev[dt][cfg] == dev) {
+        *out = L;
+        return VMAT_OK;
+    }
+    Launch n;
+    n.threads = kCfgs[cfg].threads;
+    if (dt == VMAT_F32) {
+        n.fn = kernel_for<float>(cfg);
+        n.smem = smem_for<float>(cfg);
+    } else if (dt == VMAT_BF16) {
+        n.fn = kernel_for<__nv_bfloat16>(cfg);
+        n.smem = smem_for<__nv_bfloat16>(cfg);
+    } else {
+        n.fn = kernel_for<__nv_fp8_e4m3>(cfg);
+        n.smem = smem_for<__nv_fp8_e4m3>(cfg);
+    }
+    VMAT_CUDA(cudaFuncSetAttribute(n.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, n.smem));
+    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n.blocks_per_sm, n.fn, n.threads, n.smem));
+    if (n.blocks_per_sm < 1) return set_error(VMAT_ECUDA, "spmv: configuration %d does not fit on an SM", cfg);
+    L = n;
+    cached_dev[dt][cfg] = dev;
+    *out = n;
+    return VMAT_OK;
+}
+
+int spmv_n_configs() { return N_CFG; }
+int spmv_default_config() { return 0; }
+int32_t spmv_config_tile(int cfg) { return kCfgs[cfg].threads * kCfgs[cfg].e; }
+
+vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s) {
+    const int32_t tile = spmv_config_tile(cfg);
+    const int32_t n_tiles = (int32_t)std::max<int64_t>(1, (m.nnz + tile - 1) / tile);
+    if ((int64_t)n_tiles * tile > m.nnz_pad) return set_error(VMAT_ECUDA, "spmv: padding smaller than a tile");
+    if (m.tile_row && m.n_tiles != n_tiles) {
+        cudaFree(m.tile_row);
+        cudaFree(m.carry_val);
+        cudaFree(m.tile_flag);
+        cudaFree(m.tile_list);
+        cudaFree(m.n_list);
+        m.tile_row = m.tile_flag = m.tile_list = m.n_list = nullptr;
+        m.carry_val = nullptr;
+    }
+    if (!m.tile_row) {
+        VMAT_CUDA(cudaMalloc(&m.tile_row, (size_t)(n_tiles + 1) * 4));
+        VMAT_CUDA(cudaMalloc(&m.carry_val, (size_t)n_tiles * 4));
+        VMAT_CUDA(cudaMalloc(&m.tile_flag, (size_t)(n_tiles + 1) * 4));
+        VMAT_CUDA(cudaMalloc(&m.tile_list, (size_t)n_tiles * 4));
+        // n_list[0] = count; 8-byte aligned int64 offsets of the tile scan follow at byte 8
+        VMAT_CUDA(cudaMalloc(&m.n_list, 8 + 8 * (size_t)(n_tiles + 1)));
+    }
+    m.cfg = cfg;
+    m.tile = tile;
+    m.n_tiles = n_tiles;
+    compute_tile_rows<<<std::max(1, std::min(1024, (n_tiles + 256) / 256)), 256, 0, s>>>(m.rowptr, m.n_rows, tile,
+                                                                                       n_tiles, m.tile_row);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
+                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    Launch L;
+    VMAT_TRY(launch_info(h.dtype, m.cfg, &L));
+    const int32_t *list = nullptr;
+    int32_t *n_list = nullptr;
+    if (cp_active) {
+        // ordered list of active tiles: flags, exclusive scan, compaction
+        int64_t *off = reinterpret_cast<int64_t *>(m.n_list + 2);
+        int g = std::max(1, std::min(ctx->n_sm * 8, (m.n_tiles + 255) / 256));
+        flag_active_tiles<<<g, 256, 0, s>>>(m.tile_row, m.n_tiles, m.n_rows, cp_active, bpc, m.tile_flag);
+        VMAT_LAUNCH_CHECK();
+        VMAT_TRY(scan_counts(m.tile_flag, off, m.n_tiles, s));
+        compact_tiles<<<g, 256, 0, s>>>(m.tile_flag, off, m.n_tiles, m.tile_list, m.n_list);
+        VMAT_LAUNCH_CHECK();
+        list = m.tile_list;
+        n_list = m.n_list;
+    }
+    SpmvParams p;
+    p.rowptr = m.rowptr;
+    p.col = m.col;
+    p.val = m.val;
+    p.x = x;
+    p.y = y;
+    p.row_scale = row_scale;
+    p.row_ids = m.row_ids;
+    p.tile_row = m.tile_row;
+    p.tile_list = list;
+    p.n_list = n_list;
+    p.n_tiles = m.n_tiles;
+    p.n_rows = m.n_rows;
+    p.nnz = m.nnz;
+    p.carry_val = m.carry_val;
+    p.status = ctx->status;
+    const int grid = std::max(1, std::min(m.n_tiles, ctx->n_sm * L.blocks_per_sm));
+    L.fn<<<grid, L.threads, L.smem, s>>>(p);
+    VMAT_LAUNCH_CHECK();
+    const int gf = std::max(1, std::min(ctx->n_sm * 4, (m.n_tiles + 255) / 256));
+    spmv_fixup<<<gf, 256, 0, s>>>(m.tile_row, m.carry_val, m.n_tiles, list, n_list, m.n_rows, y, m.row_ids,
+                                  row_scale, cp_active, bpc);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compact, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const float *xin = x;
+    if (h.dtype == VMAT_FP8E4M3) { // columns of CSR(D) carry the per-beamlet scale: use s o x
+        scale_vector<<<std::max(1, std::min(ctx->n_sm * 8, (h.J + 255) / 256)), 256, 0, s>>>(x, h.scale, h.xs, h.J);
+        VMAT_LAUNCH_CHECK();
+        xin = h.xs;
+    }
+    if (compact) {
+        CsrMat m = h.D;
+        m.row_ids = nullptr;
+        return spmv_run(h, m, xin, d, nullptr, nullptr, 1, s);
+    }
+    VMAT_CUDA(cudaMemsetAsync(d, 0, (size_t)h.V * 4, s));
+    return spmv_run(h, h.D, xin, d, nullptr, nullptr, 1, s);
+}
+
+vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
+    // Time every configuration on the handle's own matrices and keep the fastest.
+    for (CsrMat *m : {&h.Dt, &h.D}) {
+        const bool isDt = m == &h.Dt;
+        if (isDt ? !h.built_Dt : !h.built_D) continue;
+        float *x = nullptr, *y = nullptr;
+        const int32_t nin = isDt ? h.V : h.J;
+        const int32_t nout = isDt ? h.J : h.V;
+        VMAT_CUDA(cudaMalloc(&x, (size_t)nin * 4));
+        VMAT_CUDA(cudaMalloc(&y, (size_t)nout * 4));
+        VMAT_CUDA(cudaMemsetAsync(x, 0, (size_t)nin * 4, s));
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        int best = m->cfg;
+        float best_ms = 1e30f;
+        for (int cfg = 0; cfg < N_CFG; ++cfg) {
+            vmat_status st = spmv_prepare_tiles(*m, cfg, s);
+            if (st != VMAT_OK) break;
+            float ms_total = 0.f;
+            for (int rep = 0; rep < 6; ++rep) {
+                cudaEventRecord(a, s);
+                st = isDt ? spmv_run(h, *m, x, y, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, nullptr, 1, s)
+                          : dose_forward_impl(h, x, y, false, s);
+                cudaEventRecord(b, s);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep >= 2) ms_total += ms;
+                if (st != VMAT_OK) break;
+            }
+            if (st == VMAT_OK && ms_total < best_ms) {
+                best_ms = ms_total;
+                best = cfg;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaFree(x);
+        cudaFree(y);
+        VMAT_TRY(spmv_prepare_tiles(*m, best, s));
+    }
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    return VMAT_OK;
+}
+
+} // namespace vmat
+
+using namespace vmat;
+
+extern "C" {
+
+vmat_status dose_forward(vmat_ddc hd, const float *x, float *d, void *stream) {
+    clear_error();
+    if (!hd || !x || !d) return set_error(VMAT_EINVAL, "dose_forward: NULL argument");
+    Ddc *h = as_ddc(hd);
+    if (!h->built_D) return set_error(VMAT_ESTATE, "dose_forward: CSR(D) not built");
+    return dose_forward_impl(*h, x, d, false, as_stream(stream));
+}
+
+vmat_status beamlet_price(vmat_ddc hd, const float *g, float *pi, const uint8_t *cp_active, int32_t beamlets_per_cp,
+                          void *stream) {
+    clear_error();
+    if (!hd || !g || !pi) return set_error(VMAT_EINVAL, "beamlet_price: NULL argument");
+    Ddc *h = as_ddc(hd);
+    if (!h->built_Dt) return set_error(VMAT_ESTATE, "beamlet_price: CSR(D^T) not built");
+    if (cp_active && (beamlets_per_cp <= 0 || h->J % beamlets_per_cp != 0))
+        return set_error(VMAT_EINVAL, "beamlet_price: beamlets_per_cp (%d) must divide J (%d)", beamlets_per_cp, h->J);
+    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr, cp_active,
+                    cp_active ? beamlets_per_cp : 1, as_stream(stream));
+}
+
+} // extern "C"

@@ -80,6 +80,12 @@ def _load():
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.synth_n_beamlets.restype = ctypes.c_int64
             lib.synth_n_beamlets.argtypes = [ctypes.POINTER(_Geom)]
+            lib.synth_count_list.restype = ctypes.c_int64
+            lib.synth_count_list.argtypes = [ctypes.POINTER(_Geom), ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p]
+            lib.synth_fill_list.restype = ctypes.c_int
+            lib.synth_fill_list.argtypes = [ctypes.POINTER(_Geom), ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -192,6 +198,26 @@ def generate_coo(geom: Geometry):
     rc = lib.synth_fill(ctypes.byref(g), offsets.ctypes.data, vox.ctypes.data,
                         blt.ctypes.data, val.ctypes.data)
     if rc != 0:
+        raise RuntimeError("synthetic DDC generator: count/fill mismatch")
+    return vox, blt, val
+
+
+def generate_coo_cps(geom: Geometry, cps):
+    """COO of the beamlets of the listed CPs only, renumbered as a K' = len(cps) geometry:
+    beamlet (t, r, c) of the result has the geometry of (cps[t], r, c)."""
+    lib = _load()
+    g = geom._c()
+    bpc = geom.n_rows * geom.n_cols
+    js = (np.asarray(cps, np.int64)[:, None] * bpc + np.arange(bpc, dtype=np.int64)[None, :]).ravel()
+    counts = np.zeros(len(js), dtype=np.int64)
+    total = lib.synth_count_list(ctypes.byref(g), js.ctypes.data, len(js), counts.ctypes.data)
+    offsets = np.zeros(len(js) + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    vox = np.empty(total, dtype=np.int32)
+    blt = np.empty(total, dtype=np.int32)
+    val = np.empty(total, dtype=np.float32)
+    if lib.synth_fill_list(ctypes.byref(g), js.ctypes.data, len(js), offsets.ctypes.data, vox.ctypes.data,
+                           blt.ctypes.data, val.ctypes.data) != 0:
         raise RuntimeError("synthetic DDC generator: count/fill mismatch")
     return vox, blt, val
 

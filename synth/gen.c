@@ -163,6 +163,33 @@ int64_t synth_count(const synth_geom *g, int64_t *counts)
     return total;
 }
 
+/* Counts for a list of beamlets js[0..n) (geometry of beamlet js[t]). */
+int64_t synth_count_list(const synth_geom *g, const int64_t *js, int64_t n, int64_t *counts)
+{
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
+    for (int64_t t = 0; t < n; ++t) {
+        counts[t] = beamlet_entries(g, js[t], NULL, NULL);
+        total += counts[t];
+    }
+    return total;
+}
+
+/* COO of a list of beamlets; entries of js[t] get beamlet index t. */
+int synth_fill_list(const synth_geom *g, const int64_t *js, int64_t n, const int64_t *offsets, int32_t *vox,
+                    int32_t *blt, float *val)
+{
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t o = offsets[t];
+        int64_t c = beamlet_entries(g, js[t], vox + o, val + o);
+        if (c != offsets[t + 1] - o) bad |= 1;
+        for (int64_t e = 0; e < c; ++e) blt[o + e] = (int32_t)t;
+    }
+    return bad ? -1 : 0;
+}
+
 /* Fill COO arrays; offsets[j] is where beamlet j's entries start (J+1 entries). */
 int synth_fill(const synth_geom *g, const int64_t *offsets, int32_t *vox, int32_t *blt, float *val)
 {

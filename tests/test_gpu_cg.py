@@ -1,0 +1,105 @@
+"""Column generation on the GPU (cg_plan) against the FP64 oracle.
+
+Lockstep: after the GPU's first t apertures (cg_plan with n_apertures = t is a
+prefix of the longer run), the oracle recomputes the prices in float64 from the
+GPU's own state and must choose the GPU's next CP, unless its top-two margin is
+within the float32 price error (a near tie).  Independent runs: the plan
+objective within 1e-4 of the oracle's when the aperture sequences agree.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import dev, host, make_ddc, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_plan(ddc, c, n):
+    from paper_1503_01721_gb300 import api
+    vox = api.VoxelParams.from_numpy(c.structs)
+    cps = torch.empty(n, dtype=torch.int32)
+    lv = torch.empty(n * c.mlc.n_rows * 2, dtype=torch.int16)
+    y = torch.empty(n, dtype=torch.float32)
+    dose = torch.empty(c.V, dtype=torch.float32, device="cuda")
+    F, st = api.cg_plan(ddc.h, c.mlc, vox, n, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
+    m = int(st["n_apertures"])
+    return F, st, cps.numpy()[:m], lv.numpy().reshape(n, c.mlc.n_rows, 2)[:m], y.numpy()[:m], host(dose)
+
+
+@pytest.mark.parametrize("name,n", [("tiny", 3), ("ragged", 4), ("cfg1", 20)])
+def test_plan_matches_oracle(name, n):
+    c = synth.make_case(name, seed=0)
+    ddc = make_ddc(c)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    s = c.structs
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, n)
+    # final dose is D (A y) from the stored float32 matrix
+    x = oracle.aperture_fluence(c.mlc, cps, lv, y)
+    d_ref = oracle.dose_forward(D, x)
+    assert np.max(np.abs(dose - d_ref)) <= 1e-5 * max(np.max(np.abs(d_ref)), 1e-30)
+    F_ref_at_gpu, _ = oracle.objective_grad(d_ref, s.struct_id, s.T, s.w_over, s.w_under)
+    assert abs(F - F_ref_at_gpu) <= 1e-5 * F_ref_at_gpu
+    ref = oracle.cg_plan(D, c.mlc, s, n)
+    if list(cps) == ref.cps:
+        assert abs(F - ref.F) <= 1e-4 * ref.F
+    else:
+        pytest.fail(f"aperture sequence differs: gpu {list(cps)} oracle {ref.cps}")
+
+
+@pytest.mark.parametrize("name,n", [("ragged", 4), ("cfg1", 12)])
+def test_lockstep_choices(name, n):
+    c = synth.make_case(name, seed=0)
+    ddc = make_ddc(c)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    s = c.structs
+    _, _, cps_full, _, _, _ = gpu_plan(ddc, c, n)
+    near_ties = 0
+    for t in range(len(cps_full)):
+        if t == 0:
+            z = np.zeros(c.V)
+            occupied = np.zeros(c.mlc.K, bool)
+            leaves_all = np.zeros((c.mlc.K, c.mlc.n_rows, 2), np.int64)
+        else:
+            _, _, cps, lv, y, _ = gpu_plan(ddc, c, t)
+            assert np.array_equal(cps, cps_full[:t])        # prefix property
+            z = oracle.dose_forward(D, oracle.aperture_fluence(c.mlc, cps, lv, y))
+            occupied = np.zeros(c.mlc.K, bool)
+            occupied[cps] = True
+            leaves_all = np.zeros((c.mlc.K, c.mlc.n_rows, 2), np.int64)
+            leaves_all[cps] = lv
+        _, g = oracle.objective_grad(z, s.struct_id, s.T, s.w_over, s.w_under)
+        pi = oracle.beamlet_price(D, g)
+        k_ref, _, p_ref = oracle.price_apertures(c.mlc, pi, occupied, leaves_all)
+        k_gpu = int(cps_full[t])
+        if k_gpu != k_ref:
+            p_gpu, _ = oracle.price_cp(c.mlc, pi, occupied, leaves_all, k_gpu)
+            # float32 price error bound summed over an aperture's beamlets
+            tol = 1e-4 * abs(p_ref)
+            assert p_ref - p_gpu <= tol, f"step {t}: gpu chose CP {k_gpu} ({p_gpu}), oracle {k_ref} ({p_ref})"
+            near_ties += 1
+    assert near_ties <= 1
+
+
+def test_plan_stats_and_stop_rule():
+    c = synth.make_case("tiny", seed=0)
+    ddc = make_ddc(c)
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, 4)
+    assert st["n_apertures"] == len(cps) <= 4
+    assert st["t_total_ms"] > 0 and st["pp1_spmv_launches"] == len(cps) + (st["stop"] == "price")
+    assert st["bb_iters_total"] > 0
+    # zero prescriptions: no positive price, no aperture
+    from paper_1503_01721_gb300 import api
+    s = c.structs
+    zero = synth.Structures(s.struct_id, np.zeros_like(s.T), s.w_over, s.w_under, s.names)
+    F0, st0 = api.cg_plan(ddc.h, c.mlc, api.VoxelParams.from_numpy(zero), 3)
+    assert st0["n_apertures"] == 0 and st0["stop"] == "price" and F0 == 0.0

@@ -1,0 +1,174 @@
+"""Parity of the two hot sparse products with the FP64 oracle:
+beamlet_price pi = D^T g (Eq. 3) and dose_forward d = D x (Section 2.1).
+
+Bound: each output within c * 2^-24 * sum_i |D_ij g_i| of the float64 result on
+the same stored values (the float32 accumulation bound of the tile reduction);
+the dose also within 1e-5 relative L-infinity.  Lower-precision storage is
+compared with the oracle on the dequantised values (same bound) and its total
+error against the float32 matrix is checked against the format's rounding.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import dev, host, make_ddc, require_cuda, spmv_bound
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def run_products(ddc, V, J, g, x, cp_active=None, bpc=0):
+    from paper_1503_01721_gb300 import api
+    pi = torch.full((J,), float("nan"), device="cuda")
+    d = torch.full((V,), float("nan"), device="cuda")
+    api.beamlet_price(ddc.h, dev(g, torch.float32), pi, None if cp_active is None else dev(cp_active, torch.uint8), bpc)
+    api.dose_forward(ddc.h, dev(x, torch.float32), d)
+    torch.cuda.synchronize()
+    return host(pi), host(d)
+
+
+def check_products(V, J, vox, blt, val, dtype="f32", tile_cfg=-1, seed=0):
+    ddc = make_ddc((vox, blt, val), dtype, tile_cfg, V, J)
+    g = synth.random_vector(V, seed + 1)
+    x = synth.random_vector(J, seed + 2, 0.0, 1.0)
+    pi, d = run_products(ddc, V, J, g, x)
+    vq, _ = oracle.quantize_ddc(J, blt, val, dtype)
+    Dq = oracle.ddc_matrix(V, J, vox, blt, vq)
+    absD = abs(Dq)
+    pi_ref = oracle.beamlet_price(Dq, g)
+    d_ref = oracle.dose_forward(Dq, x)
+    assert np.all(np.abs(pi - pi_ref) <= spmv_bound(absD.T @ np.abs(g.astype(np.float64))))
+    assert np.all(np.abs(d - d_ref) <= spmv_bound(absD @ np.abs(x.astype(np.float64))))
+    if d_ref.size and np.max(np.abs(d_ref)) > 0:
+        assert np.max(np.abs(d - d_ref)) <= 1e-5 * np.max(np.abs(d_ref))
+    return ddc, pi, d
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "cfg1"])
+def test_products_f32(name):
+    c = synth.make_case(name, seed=0)
+    check_products(c.V, c.J, c.vox, c.blt, c.val)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_every_tile_config(cfg):
+    c = synth.make_case("ragged", seed=1)
+    check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg)
+    c = synth.make_case("cfg1", seed=0)
+    check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg, seed=5)
+
+
+def test_shuffled_coo_gives_identical_bits():
+    c = synth.make_case("cfg1", seed=0)
+    _, pi1, d1 = check_products(c.V, c.J, c.vox, c.blt, c.val)
+    v2, b2, a2 = synth.shuffled_coo(c.vox, c.blt, c.val, 9)
+    _, pi2, d2 = check_products(c.V, c.J, v2, b2, a2)
+    assert np.array_equal(pi1.view(np.uint32), pi2.view(np.uint32))
+    assert np.array_equal(d1.view(np.uint32), d2.view(np.uint32))
+
+
+def test_repeat_is_bitwise_deterministic():
+    c = synth.make_case("ragged", seed=1)
+    ddc = make_ddc(c)
+    g = synth.random_vector(c.V, 3)
+    x = synth.random_vector(c.J, 4)
+    a = run_products(ddc, c.V, c.J, g, x)
+    b = run_products(ddc, c.V, c.J, g, x)
+    assert all(np.array_equal(u.view(np.uint32), v.view(np.uint32)) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_low_precision_storage(dtype):
+    c = synth.make_case("cfg1", seed=0)
+    _, pi, d = check_products(c.V, c.J, c.vox, c.blt, c.val, dtype=dtype)
+    # total error against the float32 matrix: elementwise storage error <= 2^-8 (bf16), 2^-4 (fp8)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    x = synth.random_vector(c.J, 2, 0.0, 1.0).astype(np.float64)
+    d_ref = oracle.dose_forward(D, x)
+    rel = np.max(np.abs(d - d_ref)) / np.max(np.abs(d_ref))
+    assert rel <= {"bf16": 2.0 ** -8, "fp8": 2.0 ** -4}[dtype] + 1e-5
+
+
+def test_cp_active_restricts_rows():
+    c = synth.make_case("cfg1", seed=0)
+    ddc = make_ddc(c)
+    rng = np.random.default_rng(3)
+    active = (rng.random(c.mlc.K) < 0.5).astype(np.uint8)
+    bpc = c.mlc.n_rows * c.mlc.n_cols
+    g = synth.random_vector(c.V, 6)
+    pi, _ = run_products(ddc, c.V, c.J, g, np.zeros(c.J, np.float32), active, bpc)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    pi_ref = oracle.beamlet_price(D, g)
+    rows = np.repeat(active.astype(bool), bpc)
+    bound = spmv_bound(abs(D).T @ np.abs(g.astype(np.float64)))
+    assert np.all(np.abs(pi[rows] - pi_ref[rows]) <= bound[rows])
+
+
+def test_empty_matrix():
+    V, J = 7, 12
+    e = np.zeros(0, np.int32)
+    ddc = make_ddc((e, e, np.zeros(0, np.float32)), V=V, J=J)
+    pi, d = run_products(ddc, V, J, synth.random_vector(V, 1), synth.random_vector(J, 2))
+    assert np.array_equal(pi, np.zeros(J, np.float32)) and np.array_equal(d, np.zeros(V, np.float32))
+
+
+def test_tile_boundaries_long_rows_and_empty_rows():
+    # beamlet rows of 4096, 0, 1, 8191, 0, 20000 entries (several full tiles, a row
+    # longer than the shared-memory sort limit) and voxels without entries
+    V = 21000
+    lens = [4096, 0, 1, 8191, 0, 20000, 0]
+    rng = np.random.default_rng(0)
+    vox, blt = [], []
+    for j, n in enumerate(lens):
+        vv = rng.choice(V - 100, size=n, replace=False) + 50
+        vox.append(vv)
+        blt.append(np.full(n, j))
+    vox = np.concatenate(vox).astype(np.int32)
+    blt = np.concatenate(blt).astype(np.int32)
+    val = rng.uniform(0.01, 1, len(vox)).astype(np.float32)
+    for cfg in range(4):
+        check_products(V, len(lens), vox, blt, val, tile_cfg=cfg)
+
+
+def test_long_row_sort_path(monkeypatch):
+    monkeypatch.setenv("VMAT_SORT_SMEM_CAP", "32")
+    c = synth.make_case("ragged", seed=1)
+    v2, b2, a2 = synth.shuffled_coo(c.vox, c.blt, c.val, 2)
+    check_products(c.V, c.J, v2, b2, a2)
+
+
+def test_invalid_coo_rejected():
+    from paper_1503_01721_gb300 import _lib, api
+    vox = np.array([0, 1, 5], np.int32)   # 5 is out of range for V = 4
+    blt = np.array([0, 1, 1], np.int32)
+    val = np.ones(3, np.float32)
+    with pytest.raises(_lib.VmatError) as e:
+        make_ddc((vox, blt, val), V=4, J=2)
+    assert e.value.status == _lib.VMAT_EINVAL
+    vox = np.array([0, 1, 1], np.int32)   # duplicate (1, 1)
+    with pytest.raises(_lib.VmatError) as e:
+        make_ddc((vox, blt, val), V=4, J=2)
+    assert e.value.status == _lib.VMAT_EINVAL and "duplicate" in str(e.value)
+    assert api.device_status(reset=True) in (0, 4)
+
+
+def test_host_coo_input_and_info():
+    from paper_1503_01721_gb300 import api
+    c = synth.make_case("ragged", seed=1)
+    h = api.ddc_load_coo(c.V, c.J, torch.from_numpy(c.vox), torch.from_numpy(c.blt), torch.from_numpy(c.val))
+    api.ddc_build(h, "f32")
+    info = api.ddc_info(h)
+    assert info["nnz"] == c.nnz and info["V"] == c.V and info["J"] == c.J
+    assert info["n_active_vox"] == len(np.unique(c.vox))
+    assert info["bytes_Dt"] == c.nnz * 8 + (c.J + 1) * 8
+    api.ddc_free(h)
