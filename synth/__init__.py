@@ -10,7 +10,7 @@ Workload recipes (voxel units unless noted):
 * ``tiny``  8x8x8 @ 5 mm, 4 CPs, 4x4 beamlets: brute-force scale.
 * ``ragged`` 13x11x9 @ 5 mm, 5 CPs, 3x7 beamlets: odd sizes, ragged tails.
 * ``cfg1``  40x40x40 @ 5 mm, one arc of 36 CPs, 20x20 beamlets (14,400),
-  spherical target r=8 (prescription 1.0) at the centre + U{-2..2}^3 and two
+  spherical target r=8 (prescription 1.0) at the centre + U[-2,2]^3 and two
   spherical OARs r=5 (limit 0.5) at distance r_t + r_o + 2 in seeded
   directions; 20 apertures.
 * ``cfg2``  128x128x96 @ 2.5 mm, one arc of 180 CPs at 2 deg, 64x64 beamlets
@@ -243,8 +243,10 @@ def make_structures(name: str, geom: Geometry, seed: int) -> Structures:
     if name in ("cfg1", "tiny", "ragged"):
         r_t = {"cfg1": 8.0, "tiny": 2.5, "ragged": 2.5}[name]
         r_o = {"cfg1": 5.0, "tiny": 1.5, "ragged": 1.5}[name]
-        ct = rng.integers(-2, 3, size=3) if name == "cfg1" else rng.integers(-1, 2, size=3)
-        targets = [(ct.astype(float), np.array([r_t] * 3), 1.0)]
+        # continuous centre offsets: a sphere centred on a grid point is mirror
+        # symmetric, which makes opposite CPs price exactly alike (exact ties)
+        ct = rng.uniform(-2, 2, size=3) if name == "cfg1" else rng.uniform(-1, 1, size=3)
+        targets = [(ct, np.array([r_t] * 3), 1.0)]
         oars = []
         for _ in range(2):
             d = rng.normal(size=3)

@@ -24,36 +24,67 @@ def _cuda():
     __graft_entry__.build()
 
 
-def gpu_plan(ddc, c, n):
+TIGHT = dict(max_iter=3000, rel_tol5=1e-10, step_tol=1e-12, delta_min=1e-12, delta_max=1e12)
+
+
+def gpu_plan(ddc, c, n, opts=None):
     from paper_1503_01721_gb300 import api
     vox = api.VoxelParams.from_numpy(c.structs)
     cps = torch.empty(n, dtype=torch.int32)
     lv = torch.empty(n * c.mlc.n_rows * 2, dtype=torch.int16)
     y = torch.empty(n, dtype=torch.float32)
     dose = torch.empty(c.V, dtype=torch.float32, device="cuda")
-    F, st = api.cg_plan(ddc.h, c.mlc, vox, n, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
+    o = None if opts is None else api.BBOptions(**opts)
+    F, st = api.cg_plan(ddc.h, c.mlc, vox, n, o, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
     m = int(st["n_apertures"])
     return F, st, cps.numpy()[:m], lv.numpy().reshape(n, c.mlc.n_rows, 2)[:m], y.numpy()[:m], host(dose)
 
 
+def near_tie_at(ddc, c, D, t, k_gpu, opts=None):
+    """Does the oracle, pricing in float64 from the GPU's state after t apertures,
+    rate the GPU's CP k_gpu within float32 price error of its own best?"""
+    s = c.structs
+    if t == 0:
+        z = np.zeros(c.V)
+        cps, lv = np.zeros(0, np.int64), np.zeros((0, c.mlc.n_rows, 2), np.int64)
+    else:
+        _, _, cps, lv, y, _ = gpu_plan(ddc, c, t, opts)
+        z = oracle.dose_forward(D, oracle.aperture_fluence(c.mlc, cps, lv, y))
+    occupied = np.zeros(c.mlc.K, bool)
+    occupied[cps] = True
+    leaves_all = np.zeros((c.mlc.K, c.mlc.n_rows, 2), np.int64)
+    leaves_all[cps] = lv
+    _, g = oracle.objective_grad(z, s.struct_id, s.T, s.w_over, s.w_under)
+    pi = oracle.beamlet_price(D, g)
+    _, _, p_ref = oracle.price_apertures(c.mlc, pi, occupied, leaves_all)
+    p_gpu, _ = oracle.price_cp(c.mlc, pi, occupied, leaves_all, int(k_gpu))
+    return p_gpu is not None and p_ref - p_gpu <= 1e-4 * abs(p_ref)
+
+
 @pytest.mark.parametrize("name,n", [("tiny", 3), ("ragged", 4), ("cfg1", 20)])
-def test_plan_matches_oracle(name, n):
+@pytest.mark.parametrize("tight", [False, True])
+def test_plan_matches_oracle(name, n, tight):
     c = synth.make_case(name, seed=0)
     ddc = make_ddc(c)
     D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
     s = c.structs
-    F, st, cps, lv, y, dose = gpu_plan(ddc, c, n)
-    # final dose is D (A y) from the stored float32 matrix
+    opts = TIGHT if tight else None
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, n, opts)
+    # final dose is D (A y) from the stored float32 matrix, F its objective
     x = oracle.aperture_fluence(c.mlc, cps, lv, y)
     d_ref = oracle.dose_forward(D, x)
     assert np.max(np.abs(dose - d_ref)) <= 1e-5 * max(np.max(np.abs(d_ref)), 1e-30)
     F_ref_at_gpu, _ = oracle.objective_grad(d_ref, s.struct_id, s.T, s.w_over, s.w_under)
     assert abs(F - F_ref_at_gpu) <= 1e-5 * F_ref_at_gpu
-    ref = oracle.cg_plan(D, c.mlc, s, n)
+    ref = oracle.cg_plan(D, c.mlc, s, n, oracle.BBOptions(**TIGHT) if tight else None)
     if list(cps) == ref.cps:
-        assert abs(F - ref.F) <= 1e-4 * ref.F
+        # converged master problems agree closely; with the paper's relative-change
+        # stopping rule each MP stops somewhere on its own trajectory
+        assert abs(F - ref.F) <= (1e-4 if tight else 1e-2) * ref.F
     else:
-        pytest.fail(f"aperture sequence differs: gpu {list(cps)} oracle {ref.cps}")
+        t = next(i for i, (a, b) in enumerate(zip(list(cps), ref.cps)) if a != b)
+        assert near_tie_at(ddc, c, D, t, cps[t], opts), \
+            f"aperture sequence differs at step {t}: gpu {list(cps)} oracle {ref.cps}"
 
 
 @pytest.mark.parametrize("name,n", [("ragged", 4), ("cfg1", 12)])
