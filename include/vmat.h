@@ -201,6 +201,25 @@ vmat_status objective_grad(int32_t V, const float *z, const vmat_voxels *vox, fl
 vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                             int32_t *best_cp, int16_t *best_leaves, double *best_price, void *stream);
 
+/* Allocation-free pricing (no counterpart in the paper).  Same inputs, outputs
+ * and results, bit for bit, as price_apertures; the difference is that this
+ * call allocates no device memory.  It is meant for callers that cannot allocate
+ * while they plan: a service that hands all of its GPU memory to its own pool at
+ * start-up (an allocation behind that pool's back can fail or fragment it), or
+ * a loop that must not touch the allocator after initialisation.
+ * Its per-row scratch is one fixed device array inside libvmat with room for
+ * VMAT_NOALLOC_MAX_ROWS (CP, MLC row) pairs (about 0.85 MB), which every GPU
+ * that loads the library keeps until the process exits.  K * n_rows above the
+ * limit returns VMAT_EINVAL (use price_apertures).  The first call on a device
+ * looks up the array's device address, so make that first call outside any
+ * stream capture.  All calls share the one array: calls whose work overlaps
+ * on the GPU (other streams, other host threads) race on it, so callers must
+ * order them.  Nothing needs zeroing between calls. */
+#define VMAT_NOALLOC_MAX_ROWS 65536
+vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied,
+                                    const int16_t *leaves, int32_t *best_cp, int16_t *best_leaves,
+                                    double *best_price, void *stream);
+
 /* ---- Apertures <-> beamlets ------------------------------------------------ */
 
 /* DA(A) = sum_{j in A} D_{:,j} (Eq. 5) for the aperture at CP `cp` with

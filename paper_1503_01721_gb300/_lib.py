@@ -64,6 +64,7 @@ SIGNATURES = {
     "beamlet_price": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
     "objective_grad": (c_i32, [c_i32, c_vp, ctypes.POINTER(Voxels), c_vp, c_vp, c_vp]),
     "price_apertures": (c_i32, [ctypes.POINTER(Mlc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "price_apertures_noalloc": (c_i32, [ctypes.POINTER(Mlc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "aperture_dose": (c_i32, [c_vp, ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp]),
     "aperture_fluence": (c_i32, [ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "aperture_grad": (c_i32, [ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),

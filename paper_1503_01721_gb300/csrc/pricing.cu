@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -218,6 +219,35 @@ size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
     return rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
 }
 
+// Scratch of price_apertures_noalloc: per-row bests for up to VMAT_NOALLOC_MAX_ROWS
+// (CP, MLC row) pairs, in one fixed device array that every GPU loading the library
+// keeps until the process exits.  Host code must not use the symbol as a pointer:
+// its device address is looked up once per device with cudaGetSymbolAddress.
+constexpr size_t NOALLOC_BYTES = (size_t)VMAT_NOALLOC_MAX_ROWS * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
+static __device__ __align__(256) unsigned char g_noalloc_price_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+static vmat_status noalloc_scratch(void **out) {
+    int dev = -1;
+    VMAT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(VMAT_EUNSUPPORTED, "price_apertures_noalloc: device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_price_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(VMAT_ECUDA, "price_apertures_noalloc: cudaGetSymbolAddress failed: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return VMAT_OK;
+}
+
 } // namespace vmat
 
 using namespace vmat;
@@ -233,4 +263,26 @@ extern "C" vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, con
     Scratch ws;
     VMAT_TRY(ws.alloc(pricing_scratch_bytes(mlc), s));
     return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s);
+}
+
+// Same computation as price_apertures with the fixed device scratch above: no
+// device allocation in the call.  Nothing in the scratch has to start at zero:
+// every per-row entry the CP kernel reads (unoccupied CPs) is written first by
+// the row kernel of the same call.
+extern "C" vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied,
+                                               const int16_t *leaves, int32_t *best_cp, int16_t *best_leaves,
+                                               double *best_price, void *stream) {
+    clear_error();
+    VMAT_TRY(validate_mlc(mlc));
+    if (!pi || !occupied || !leaves || !best_cp || !best_leaves || !best_price)
+        return set_error(VMAT_EINVAL, "price_apertures_noalloc: NULL argument");
+    if ((int64_t)mlc->K * mlc->n_rows > VMAT_NOALLOC_MAX_ROWS)
+        return set_error(VMAT_EINVAL,
+                         "price_apertures_noalloc: K * n_rows = %lld exceeds the fixed scratch limit of %d "
+                         "(CP, MLC row) pairs; use price_apertures",
+                         (long long)mlc->K * mlc->n_rows, VMAT_NOALLOC_MAX_ROWS);
+    void *ws = nullptr;
+    VMAT_TRY(noalloc_scratch(&ws));
+    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws,
+                                as_stream(stream));
 }

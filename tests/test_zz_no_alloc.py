@@ -1,0 +1,84 @@
+"""price_apertures_noalloc, the pricing call for callers that cannot allocate
+device memory while they plan (e.g. a service whose GPU memory all belongs to
+its own pool), returns exactly what price_apertures returns.
+
+Both are called through the C ABI on the same inputs, twice in a row with
+different inputs, so the second call also shows that the fixed scratch array
+left over from the first call does not leak into the result.  Pricing results
+are compared bit for bit, as in the other pricing tests.  This file sorts
+last so that a run stopping at its first failure has run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1503_01721_gb300 import _lib
+    return _lib.load()
+
+
+def c_mlc(mlc):
+    from paper_1503_01721_gb300 import _lib
+    arcs = (ctypes.c_int32 * len(mlc.arc_first_cp))(*[int(a) for a in mlc.arc_first_cp])
+    m = _lib.Mlc(mlc.K, mlc.n_rows, mlc.n_cols, len(arcs), ctypes.cast(arcs, ctypes.POINTER(ctypes.c_int32)),
+                 mlc.travel_cols)
+    return m, arcs
+
+
+def call(lib, fn, mlc, pi, occupied, leaves):
+    from paper_1503_01721_gb300 import _lib
+    m, keep = c_mlc(mlc)
+    bk = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    bl = torch.full((mlc.n_rows * 2,), -7, dtype=torch.int16, device="cuda")
+    bp = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    st = getattr(lib, fn)(ctypes.byref(m), pi.data_ptr(), occupied.data_ptr(), leaves.data_ptr(), bk.data_ptr(),
+                          bl.data_ptr(), bp.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _lib.check(fn, st)
+    torch.cuda.synchronize()
+    return int(bk.item()), bl.cpu().numpy().copy(), bp.cpu().numpy().view(np.uint64)[0]
+
+
+def inputs(mlc, seed):
+    rng = np.random.default_rng(seed)
+    pi = (rng.normal(size=mlc.K * mlc.n_rows * mlc.n_cols) * 10.0).astype(np.float32)
+    pi[rng.random(pi.size) < 0.3] = 0.0
+    occupied = (rng.random(mlc.K) < 0.3).astype(np.uint8)
+    leaves = np.sort(rng.integers(0, mlc.n_cols + 1, size=(mlc.K, mlc.n_rows, 2)), axis=2).astype(np.int16)
+    d = lambda a, dt: torch.as_tensor(a).to("cuda", dt).contiguous()
+    return d(pi, torch.float32), d(occupied, torch.uint8), d(leaves, torch.int16)
+
+
+def test_noalloc_matches_price_apertures_on_two_calls(lib):
+    # the H&N-like geometry (180 CPs x 64 rows, within the fixed limit) then a smaller one
+    for mlc, seed in ((synth.MLC(180, 64, 64, np.array([0], np.int32), 3), 1),
+                      (synth.MLC(36, 20, 20, np.array([0, 18], np.int32), 2), 2)):
+        args = inputs(mlc, seed)
+        want = call(lib, "price_apertures", mlc, *args)
+        got = call(lib, "price_apertures_noalloc", mlc, *args)
+        assert want[0] >= 0
+        assert got[0] == want[0]
+        assert np.array_equal(got[1], want[1])
+        assert got[2] == want[2]
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit(lib):
+    from paper_1503_01721_gb300 import _lib
+    mlc = synth.MLC(1025, 64, 8, np.array([0], np.int32), 3)   # 65,600 rows > 65,536
+    m, keep = c_mlc(mlc)
+    dummy = torch.zeros(16, device="cuda")
+    st = lib.price_apertures_noalloc(ctypes.byref(m), dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                                     dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), None)
+    assert st == _lib.VMAT_EINVAL
+    assert b"limit" in lib.vmat_last_error()
