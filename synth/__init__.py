@@ -178,8 +178,10 @@ GEOMETRIES = {
     "cfg1": Geometry(40, 40, 40, 5.0, 36, 20, 20),
     "cfg2": Geometry(128, 128, 96, 2.5, 180, 64, 64),
     "cfg3": Geometry(128, 128, 96, 2.5, 180, 64, 64, n_arcs=2, arc_offset_deg=1.0),
+    # cfg2 geometry with every 4th control point (8 deg): a few-GB case for profiling
+    "cfg2q": Geometry(128, 128, 96, 2.5, 45, 64, 64),
 }
-APERTURES = {"tiny": 3, "ragged": 4, "cfg1": 20, "cfg2": 60, "cfg3": 60}
+APERTURES = {"tiny": 3, "ragged": 4, "cfg1": 20, "cfg2": 60, "cfg3": 60, "cfg2q": 30}
 
 
 def generate_coo(geom: Geometry):
@@ -240,6 +242,8 @@ def make_structures(name: str, geom: Geometry, seed: int) -> Structures:
     V = geom.V
     sid = np.zeros(V, dtype=np.uint8)
     T, wo, wu, names = [], [], [], []
+    if name == "cfg2q":
+        name = "cfg2"
     if name in ("cfg1", "tiny", "ragged"):
         r_t = {"cfg1": 8.0, "tiny": 2.5, "ragged": 2.5}[name]
         r_o = {"cfg1": 5.0, "tiny": 1.5, "ragged": 1.5}[name]
