@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local):
 
     # resident DDC
     h = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-    api.ddc_build(h, args.dtype)
+    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg)
     info = api.ddc_info(h)
     log(f"[rank {rank}] build {info['build_ms']:.1f} ms, active voxels {info['n_active_vox']}")
 
@@ -312,7 +312,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         h2 = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-        api.ddc_build(h2, args.dtype)
+        api.ddc_build(h2, args.dtype, tile_cfg=args.tile_cfg)
         F2, st2 = api.cg_plan(h2, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose_h)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t_a)
@@ -361,23 +361,42 @@ def run_spmv_only(args):
     from paper_1503_01721_gb300 import api
     import __graft_entry__
 
+    from paper_1503_01721_gb300 import roofline
+
     __graft_entry__.build()
     case = synth.make_case(args.workload, seed=0, cache=False)
     d = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
-    ddc = api.Ddc(case.V, case.J, d(case.vox, torch.int32), d(case.blt, torch.int32), d(case.val, torch.float32),
-                  dtype=args.dtype)
+    coo = (d(case.vox, torch.int32), d(case.blt, torch.int32), d(case.val, torch.float32))
     g = torch.rand(case.V, device="cuda")
     x = torch.rand(case.J, device="cuda")
     pi = torch.empty(case.J, device="cuda")
     dd = torch.empty(case.V, device="cuda")
-    for _ in range(3):
-        api.beamlet_price(ddc.h, g, pi)
-        api.dose_forward(ddc.h, x, dd)
-    torch.cuda.synchronize()
-    info = ddc.info()
-    ddc.close()
-    return {"mode": "spmv", "workload": args.workload, "nnz": case.nnz, "tile_Dt": info["tile_nnz_Dt"],
-            "bytes_Dt": info["bytes_Dt"], "bytes_D": info["bytes_D"]}
+    out = {"mode": "spmv", "workload": args.workload, "nnz": case.nnz, "dtype": args.dtype, "configs": {}}
+    for cfg in (range(7) if args.sweep else [args.tile_cfg]):
+        ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg)
+        info = ddc.info()
+        for _ in range(3):
+            api.beamlet_price(ddc.h, g, pi)
+            api.dose_forward(ddc.h, x, dd)
+        torch.cuda.synchronize()
+        if args.sweep:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            for _ in range(10):
+                api.beamlet_price(ddc.h, g, pi)
+            ev[1].record()
+            for _ in range(10):
+                api.dose_forward(ddc.h, x, dd)
+            ev[2].record()
+            torch.cuda.synchronize()
+            sc = case.J if args.dtype == "fp8" else 0
+            b_t = roofline.spmv_bytes(case.nnz, case.J, case.V, case.J, args.dtype, sc)
+            b_d = roofline.spmv_bytes(case.nnz, info["n_active_vox"], case.J, case.V, args.dtype, sc)
+            t_t, t_d = ev[0].elapsed_time(ev[1]) / 10, ev[1].elapsed_time(ev[2]) / 10
+            out["configs"][cfg] = {"dt_g_gbs": round(b_t / t_t / 1e6, 1), "d_x_gbs": round(b_d / t_d / 1e6, 1),
+                                   "dt_g_ms": round(t_t, 4), "d_x_ms": round(t_d, 4)}
+        ddc.close()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -407,6 +426,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS))
     ap.add_argument("--mode", default="plan", choices=["plan", "spmv"],
                     help="spmv: only build and run D^T g and D x a few times (profiling driver)")
+    ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
+    ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.mode == "plan":
         log("note: fewer than 3 warm-up steps")

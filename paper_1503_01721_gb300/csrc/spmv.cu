@@ -272,6 +272,152 @@ __global__ void __launch_bounds__(THREADS) spmv_tile_kernel(SpmvParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-row variant (the paper's mapping, Section 2.2.2), vectorised: each
+// lane streams 4-entry chunks with 128-bit loads that bypass L1 and are marked
+// evict-first in L2 (the matrix is read once), keeps one accumulator per chunk
+// position, and the warp reduces with a fixed butterfly.  Row heads and tails
+// that are not 4-aligned are taken one entry per lane.  No shared memory, so
+// occupancy is set by registers; rows of inactive CPs are skipped outright.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldg_stream_f4(const void *p, uint64_t pol) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ int4 ldg_stream_i4(const void *p, uint64_t pol) {
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ldg_stream_u2(const void *p, uint64_t pol) {
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+        : "=r"(r.x), "=r"(r.y)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ldg_stream_u1(const void *p, uint64_t pol) {
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+template <typename VT> struct StreamVals;
+template <> struct StreamVals<float> {
+    static __device__ __forceinline__ void load4(const void *val, int64_t e0, uint64_t pol, float v[4]) {
+        float4 t = ldg_stream_f4(static_cast<const float *>(val) + e0, pol);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+    static __device__ __forceinline__ float load1(const void *val, int64_t e) {
+        return __ldg(static_cast<const float *>(val) + e);
+    }
+};
+template <> struct StreamVals<__nv_bfloat16> {
+    static __device__ __forceinline__ void load4(const void *val, int64_t e0, uint64_t pol, float v[4]) {
+        uint2 t = ldg_stream_u2(static_cast<const uint16_t *>(val) + e0, pol);
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
+    }
+    static __device__ __forceinline__ float load1(const void *val, int64_t e) {
+        return __uint_as_float((uint32_t)__ldg(static_cast<const unsigned short *>(val) + e) << 16);
+    }
+};
+template <> struct StreamVals<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ void load4(const void *val, int64_t e0, uint64_t pol, float v[4]) {
+        uint32_t t = ldg_stream_u1(static_cast<const uint8_t *>(val) + e0, pol);
+        __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t & 0xffffu), __NV_E4M3);
+        __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t >> 16), __NV_E4M3);
+        float2 fa = __half22float2(*reinterpret_cast<__half2 *>(&a));
+        float2 fb = __half22float2(*reinterpret_cast<__half2 *>(&b));
+        v[0] = fa.x;
+        v[1] = fa.y;
+        v[2] = fb.x;
+        v[3] = fb.y;
+    }
+    static __device__ __forceinline__ float load1(const void *val, int64_t e) {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)__ldg(static_cast<const unsigned char *>(val) + e),
+                                               __NV_E4M3);
+        return __half2float(*reinterpret_cast<__half *>(&h));
+    }
+};
+
+struct RowParams {
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+    const float *x;
+    float *y;
+    const float *row_scale;
+    const int32_t *row_ids;
+    const uint8_t *cp_active; // skip rows r with !cp_active[r / bpc], or null
+    int32_t bpc;
+    int32_t n_rows;
+};
+
+template <int THREADS, int UNROLL, typename VT>
+__global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    const uint64_t pol = l2_evict_first_policy();
+    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
+        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+        const int64_t s = __ldg(p.rowptr + r), e = __ldg(p.rowptr + r + 1);
+        const int64_t a = min((s + 3) & ~(int64_t)3, e); // first 4-aligned entry
+        const int64_t b = max(a, e & ~(int64_t)3);        // end of the aligned body
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // head (< 4 entries) and tail (< 4 entries): one entry per lane
+        if (lane < a - s) {
+            const int64_t i = s + lane;
+            acc[0] = StreamVals<VT>::load1(p.val, i) * __ldg(p.x + __ldg(p.col + i));
+        }
+        if (lane < e - b) {
+            const int64_t i = b + lane;
+            acc[1] = StreamVals<VT>::load1(p.val, i) * __ldg(p.x + __ldg(p.col + i));
+        }
+        const int64_t nch = (b - a) >> 2;
+        for (int64_t c = lane; c < nch; c += 32 * UNROLL) {
+            float v[UNROLL][4];
+            int4 cc[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int64_t cu = c + 32 * u;
+                if (cu < nch) {
+                    const int64_t e0 = a + 4 * cu;
+                    StreamVals<VT>::load4(p.val, e0, pol, v[u]);
+                    cc[u] = ldg_stream_i4(p.col + e0, pol);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (c + 32 * u < nch) {
+                    acc[0] = fmaf(v[u][0], __ldg(p.x + cc[u].x), acc[0]);
+                    acc[1] = fmaf(v[u][1], __ldg(p.x + cc[u].y), acc[1]);
+                    acc[2] = fmaf(v[u][2], __ldg(p.x + cc[u].z), acc[2]);
+                    acc[3] = fmaf(v[u][3], __ldg(p.x + cc[u].w), acc[3]);
+                }
+            }
+        }
+        float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        if (lane == 0) {
+            if (p.row_scale) sum *= p.row_scale[r];
+            p.y[p.row_ids ? p.row_ids[r] : r] = sum;
+        }
+    }
+}
+
 // Adds tile carries to their rows.  Tile b's carry belongs to row tile_row[b + 1];
 // the first tile of each run of equal keys sums the run left to right.  Rows of
 // inactive CPs are skipped (their tiles may not have run).
@@ -338,14 +484,17 @@ __global__ void scale_vector(const float *x, const float *s, float *out, int32_t
 // Configurations and dispatch
 // ---------------------------------------------------------------------------
 struct Cfg {
-    int threads, e, stages;
+    int family; // 0 = tile-segmented, 1 = warp per row
+    int threads, e, stages; // tile: E entries per thread, STAGES bulk-copy stages; warp-row: e = unroll
 };
-static const Cfg kCfgs[] = {{256, 16, 2}, {256, 8, 3}, {512, 8, 2}, {128, 16, 3}};
-constexpr int N_CFG = 4;
+static const Cfg kCfgs[] = {{0, 256, 16, 2}, {0, 256, 8, 3}, {0, 512, 8, 2}, {0, 128, 16, 3},
+                            {1, 256, 2, 0},  {1, 256, 1, 0}, {1, 512, 4, 0}};
+constexpr int N_CFG = 7;
 
-using KernelFn = void (*)(SpmvParams);
+using TileFn = void (*)(SpmvParams);
+using RowFn = void (*)(RowParams);
 
-template <typename VT> KernelFn kernel_for(int cfg) {
+template <typename VT> TileFn tile_kernel_for(int cfg) {
     switch (cfg) {
     case 0: return spmv_tile_kernel<256, 16, 2, VT>;
     case 1: return spmv_tile_kernel<256, 8, 3, VT>;
@@ -354,44 +503,61 @@ template <typename VT> KernelFn kernel_for(int cfg) {
     }
 }
 
+template <typename VT> RowFn row_kernel_for(int cfg) {
+    switch (cfg) {
+    case 4: return spmv_warp_row_kernel<256, 2, VT>;
+    case 5: return spmv_warp_row_kernel<256, 1, VT>;
+    default: return spmv_warp_row_kernel<512, 4, VT>;
+    }
+}
+
 template <typename VT> int smem_for(int cfg) {
     switch (cfg) {
     case 0: return TileShape<256, 16, 2, VT>::SMEM;
     case 1: return TileShape<256, 8, 3, VT>::SMEM;
     case 2: return TileShape<512, 8, 2, VT>::SMEM;
-    default: return TileShape<128, 16, 3, VT>::SMEM;
+    case 3: return TileShape<128, 16, 3, VT>::SMEM;
+    default: return 0;
     }
 }
 
 struct Launch {
-    KernelFn fn;
-    int threads, smem, blocks_per_sm;
+    TileFn tile = nullptr;
+    RowFn row = nullptr;
+    int threads = 0, smem = 0, blocks_per_sm = 0;
 };
 
+template <typename VT> static void pick(int cfg, Launch &n) {
+    if (kCfgs[cfg].family == 0) {
+        n.tile = tile_kernel_for<VT>(cfg);
+        n.smem = smem_for<VT>(cfg);
+    } else {
+        n.row = row_kernel_for<VT>(cfg);
+        n.smem = 0;
+    }
+}
+
 static vmat_status launch_info(vmat_dtype dt, int cfg, Launch *out) {
-    static Launch cache[3][N_CFG] = {};
+    static Launch cache[3][N_CFG];
     static int cached_dev[3][N_CFG];
     int dev;
     VMAT_CUDA(cudaGetDevice(&dev));
     Launch &L = cache[dt][cfg];
-    if (L.fn && cached_dev[dt][cfg] == dev) {
+    if ((L.tile || L.row) && cached_dev[dt][cfg] == dev) {
         *out = L;
         return VMAT_OK;
     }
     Launch n;
     n.threads = kCfgs[cfg].threads;
-    if (dt == VMAT_F32) {
-        n.fn = kernel_for<float>(cfg);
-        n.smem = smem_for<float>(cfg);
-    } else if (dt == VMAT_BF16) {
-        n.fn = kernel_for<__nv_bfloat16>(cfg);
-        n.smem = smem_for<__nv_bfloat16>(cfg);
+    if (dt == VMAT_F32) pick<float>(cfg, n);
+    else if (dt == VMAT_BF16) pick<__nv_bfloat16>(cfg, n);
+    else pick<__nv_fp8_e4m3>(cfg, n);
+    if (n.tile) {
+        VMAT_CUDA(cudaFuncSetAttribute(n.tile, cudaFuncAttributeMaxDynamicSharedMemorySize, n.smem));
+        VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n.blocks_per_sm, n.tile, n.threads, n.smem));
     } else {
-        n.fn = kernel_for<__nv_fp8_e4m3>(cfg);
-        n.smem = smem_for<__nv_fp8_e4m3>(cfg);
+        VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n.blocks_per_sm, n.row, n.threads, 0));
     }
-    VMAT_CUDA(cudaFuncSetAttribute(n.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, n.smem));
-    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n.blocks_per_sm, n.fn, n.threads, n.smem));
     if (n.blocks_per_sm < 1) return set_error(VMAT_ECUDA, "spmv: configuration %d does not fit on an SM", cfg);
     L = n;
     cached_dev[dt][cfg] = dev;
@@ -400,10 +566,15 @@ static vmat_status launch_info(vmat_dtype dt, int cfg, Launch *out) {
 }
 
 int spmv_n_configs() { return N_CFG; }
-int spmv_default_config() { return 0; }
-int32_t spmv_config_tile(int cfg) { return kCfgs[cfg].threads * kCfgs[cfg].e; }
+int spmv_default_config() { return 4; }
+int32_t spmv_config_tile(int cfg) { return kCfgs[cfg].family == 0 ? kCfgs[cfg].threads * kCfgs[cfg].e : 0; }
 
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s) {
+    if (kCfgs[cfg].family != 0) { // warp per row: no tile structure needed
+        m.cfg = cfg;
+        m.tile = 0;
+        return VMAT_OK;
+    }
     const int32_t tile = spmv_config_tile(cfg);
     const int32_t n_tiles = (int32_t)std::max<int64_t>(1, (m.nnz + tile - 1) / tile);
     if ((int64_t)n_tiles * tile > m.nnz_pad) return set_error(VMAT_ECUDA, "spmv: padding smaller than a tile");
@@ -439,6 +610,25 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
     VMAT_TRY(device_ctx(&ctx));
     Launch L;
     VMAT_TRY(launch_info(h.dtype, m.cfg, &L));
+    if (L.row) {
+        RowParams p;
+        p.rowptr = m.rowptr;
+        p.col = m.col;
+        p.val = m.val;
+        p.x = x;
+        p.y = y;
+        p.row_scale = row_scale;
+        p.row_ids = m.row_ids;
+        p.cp_active = cp_active;
+        p.bpc = bpc;
+        p.n_rows = m.n_rows;
+        const int64_t warps = std::max<int64_t>(1, m.n_rows);
+        const int64_t want = (warps * 32 + L.threads - 1) / L.threads;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * L.blocks_per_sm));
+        L.row<<<grid, L.threads, 0, s>>>(p);
+        VMAT_LAUNCH_CHECK();
+        return VMAT_OK;
+    }
     const int32_t *list = nullptr;
     int32_t *n_list = nullptr;
     if (cp_active) {
@@ -470,7 +660,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
     p.carry_val = m.carry_val;
     p.status = ctx->status;
     const int grid = std::max(1, std::min(m.n_tiles, ctx->n_sm * L.blocks_per_sm));
-    L.fn<<<grid, L.threads, L.smem, s>>>(p);
+    L.tile<<<grid, L.threads, L.smem, s>>>(p);
     VMAT_LAUNCH_CHECK();
     const int gf = std::max(1, std::min(ctx->n_sm * 4, (m.n_tiles + 255) / 256));
     spmv_fixup<<<gf, 256, 0, s>>>(m.tile_row, m.carry_val, m.n_tiles, list, n_list, m.n_rows, y, m.row_ids,

@@ -4,10 +4,11 @@ import pytest
 import torch
 
 U32 = 2.0 ** -24  # float32 unit roundoff
-# Depth of the float32 summation tree of one row in the tile SpMV: at most
-# E (16) serial adds in a thread, log2(512) = 9 levels of the keyed scan, one add
-# per spanned tile and the products' own rounding; 64 covers every row length
-# in the tests with margin.
+# Depth of the float32 summation of one row of n entries: the tile kernel adds
+# at most E (16) serially in a thread, log2(512) = 9 levels of keyed scan and one
+# add per spanned tile; the warp-per-row kernel adds n/128 per accumulator, 2
+# levels to join the 4 accumulators and 5 butterfly levels.  (64 + n/64) units
+# of roundoff bound both, for every row length.
 SPMV_C = 64
 
 
@@ -24,9 +25,9 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def spmv_bound(abs_terms_sum):
-    """Componentwise float32 accumulation bound c * u * sum_i |a_i b_i|."""
-    return SPMV_C * U32 * abs_terms_sum + 1e-37
+def spmv_bound(abs_terms_sum, row_len=0):
+    """Componentwise float32 accumulation bound (64 + n/64) * u * sum_i |a_i b_i|."""
+    return (SPMV_C + np.asarray(row_len, np.float64) / 64.0) * U32 * abs_terms_sum + 1e-37
 
 
 def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None):

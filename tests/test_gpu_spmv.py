@@ -47,8 +47,10 @@ def check_products(V, J, vox, blt, val, dtype="f32", tile_cfg=-1, seed=0):
     absD = abs(Dq)
     pi_ref = oracle.beamlet_price(Dq, g)
     d_ref = oracle.dose_forward(Dq, x)
-    assert np.all(np.abs(pi - pi_ref) <= spmv_bound(absD.T @ np.abs(g.astype(np.float64))))
-    assert np.all(np.abs(d - d_ref) <= spmv_bound(absD @ np.abs(x.astype(np.float64))))
+    len_t = np.bincount(blt, minlength=J)
+    len_d = np.bincount(vox, minlength=V)
+    assert np.all(np.abs(pi - pi_ref) <= spmv_bound(absD.T @ np.abs(g.astype(np.float64)), len_t))
+    assert np.all(np.abs(d - d_ref) <= spmv_bound(absD @ np.abs(x.astype(np.float64)), len_d))
     if d_ref.size and np.max(np.abs(d_ref)) > 0:
         assert np.max(np.abs(d - d_ref)) <= 1e-5 * np.max(np.abs(d_ref))
     return ddc, pi, d
@@ -60,7 +62,7 @@ def test_products_f32(name):
     check_products(c.V, c.J, c.vox, c.blt, c.val)
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", list(range(7)))
 def test_every_tile_config(cfg):
     c = synth.make_case("ragged", seed=1)
     check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg)
@@ -110,7 +112,7 @@ def test_cp_active_restricts_rows():
     D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
     pi_ref = oracle.beamlet_price(D, g)
     rows = np.repeat(active.astype(bool), bpc)
-    bound = spmv_bound(abs(D).T @ np.abs(g.astype(np.float64)))
+    bound = spmv_bound(abs(D).T @ np.abs(g.astype(np.float64)), np.bincount(c.blt, minlength=c.J))
     assert np.all(np.abs(pi[rows] - pi_ref[rows]) <= bound[rows])
 
 
@@ -136,7 +138,7 @@ def test_tile_boundaries_long_rows_and_empty_rows():
     vox = np.concatenate(vox).astype(np.int32)
     blt = np.concatenate(blt).astype(np.int32)
     val = rng.uniform(0.01, 1, len(vox)).astype(np.float32)
-    for cfg in range(4):
+    for cfg in range(7):
         check_products(V, len(lens), vox, blt, val, tile_cfg=cfg)
 
 
