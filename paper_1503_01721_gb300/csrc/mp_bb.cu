@@ -3,15 +3,16 @@
 // of Eq. 9-10 and the stopping rules of Section 2.1.
 //
 // The paper runs four steps per iteration on one GPU (aperture gradient, step
-// length with cuBLAS dot products, subspace update, dose update).  Here each
-// iteration is two kernels:
-//   mp_pass  (all SMs): z = DA y, the objective terms and g = -grad F per voxel,
-//            and per-block partials of G = grad_y F = -DA^T g, reading DA once
-//            from HBM (the second read of each column chunk hits L1/L2);
-//   mp_step  (one block): FP64 reduction of the partials in block order, the
-//            Eq. 9-10 freeze, the stopping tests, the BB step and the projected
-//            update of y.
-// The first iteration takes a Cauchy step, which needs DA G: two more kernels.
+// length with cuBLAS dot products, subspace update, dose update).  Here one
+// kernel does a whole iteration: every CTA streams tiles of DA (256 voxels x
+// n apertures, one bulk copy per column, double-buffered on mbarriers) into
+// shared memory and from each tile computes z = DA y, the objective terms,
+// g = -grad F and the partial G = grad_y F = -DA^T g of its voxels, so DA is
+// read from HBM once per iteration.  The last CTA to finish (a ticket counter)
+// reduces the partials in a fixed order (FP64) and takes the step: the Eq. 9-10
+// freeze, the stopping tests, the BB step length and the projected update.
+// The first iteration's Cauchy step needs DA G and takes two more kernels.
+//
 // Readings (where the paper is silent): G is the gradient of F, so both BB
 // step lengths are positive and Eq. 9-10 freeze at lo when G > 0 and at hi when
 // G < 0; y is projected onto the box after each step; BB1 on even and BB2 on
@@ -26,9 +27,11 @@
 
 namespace vmat {
 
-constexpr int MP_THREADS = 256;
+constexpr int MP_THREADS = 256; // = voxels per DA tile
 constexpr int MP_NW = MP_THREADS / 32;
+constexpr int MP_STAGES = 2;
 constexpr int MP_CHUNK = 8; // iterations launched between host polls
+constexpr size_t MP_SMEM_LIMIT = 200 * 1024;
 
 struct BBState {
     double F_hist[6];
@@ -40,7 +43,7 @@ struct BBState {
     int32_t stop;
     int32_t iters;
     int32_t need_cauchy;
-    int32_t pad;
+    uint32_t ticket; // CTAs of the current pass that have written their partials
 };
 
 struct MPArgs {
@@ -58,11 +61,14 @@ struct MPArgs {
     double *part;  // [P][n + 1]
     double *cpart; // [P]
     int32_t P;
+    int32_t n_tiles;
     BBState *st;
+    int32_t *status;
     vmat_bb_opts opts;
     double F_offset;
 };
 
+__device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
 __device__ __forceinline__ float lo_of(const MPArgs &a, int k) { return a.lo ? a.lo[k] : 0.f; }
 __device__ __forceinline__ float hi_of(const MPArgs &a, int k) { return a.hi ? a.hi[k] : INFINITY; }
 
@@ -74,68 +80,7 @@ __global__ void mp_init_kernel(MPArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(MP_THREADS) mp_pass_kernel(MPArgs a) {
-    if (a.st->done || a.st->need_cauchy) return;
-    extern __shared__ __align__(16) unsigned char sm[];
-    float *sy = reinterpret_cast<float *>(sm);                  // [n]
-    double *accG = reinterpret_cast<double *>(sy + ((a.n + 3) & ~3)); // [n]
-    float *gs = reinterpret_cast<float *>(accG + a.n);           // [MP_THREADS]
-    float *sT = gs + MP_THREADS, *sO = sT + 256, *sU = sO + 256;
-    __shared__ double sh[MP_NW];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < a.n; k += MP_THREADS) {
-        sy[k] = a.y[k];
-        accG[k] = 0.0;
-    }
-    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
-        sT[k] = a.T[k];
-        sO[k] = a.wo[k];
-        sU[k] = a.wu[k];
-    }
-    __syncthreads();
-    double facc = 0.0;
-    for (int64_t base = (int64_t)blockIdx.x * MP_THREADS; base < a.V; base += (int64_t)gridDim.x * MP_THREADS) {
-        const int64_t i = base + tid;
-        float gi = 0.f;
-        if (i < a.V) {
-            float zi = 0.f;
-            for (int k = 0; k < a.n; ++k) zi = fmaf(a.DA[(int64_t)k * a.ld + i], sy[k], zi);
-            a.z[i] = zi;
-            const int s = a.sid[i];
-            const float t = sT[s];
-            gi = -2.f * sO[s] * fmaxf(0.f, zi - t) + 2.f * sU[s] * fmaxf(0.f, t - zi);
-            const double dz = (double)zi - (double)t;
-            const double ov = dz > 0.0 ? dz : 0.0, un = dz < 0.0 ? -dz : 0.0;
-            facc += (double)sO[s] * ov * ov + (double)sU[s] * un * un;
-        }
-        gs[tid] = gi;
-        __syncthreads();
-        for (int k = wid; k < a.n; k += MP_NW) {
-            const float *col = a.DA + (int64_t)k * a.ld + base;
-            float sum = 0.f;
-#pragma unroll
-            for (int m = lane; m < MP_THREADS; m += 32)
-                if (base + m < a.V) sum = fmaf(col[m], gs[m], sum);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
-            if (lane == 0) accG[k] += (double)sum;
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) facc += __shfl_down_sync(0xffffffffu, facc, d);
-    if (lane == 0) sh[wid] = facc;
-    __syncthreads();
-    double *out = a.part + (int64_t)blockIdx.x * (a.n + 1);
-    for (int k = tid; k < a.n; k += MP_THREADS) out[k] = accG[k];
-    if (tid == 0) {
-        double f = 0.0;
-        for (int w = 0; w < MP_NW; ++w) f += sh[w];
-        out[a.n] = f;
-    }
-}
-
-// Fixed-order block reduction of a double (result valid in every thread).
+// Fixed-order block reductions (result valid in every thread).
 __device__ double block_reduce_sum(double v, double *sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -177,21 +122,32 @@ __device__ void take_step(const MPArgs &a, double delta) {
     }
 }
 
-__global__ void __launch_bounds__(MP_THREADS) mp_step_kernel(MPArgs a) {
-    BBState *st = a.st;
-    if (st->done || st->need_cauchy) return;
-    __shared__ double sh[MP_NW];
-    const int t = st->t;
+// G_k = -sum_b part[b][k] and F = sum_b part[b][n] + offset.  One warp per column;
+// lane l sums blocks l, l + 32, ... in order, then a fixed butterfly.
+__device__ void reduce_partials(const MPArgs &a, int P) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = a.n;
-    // G_k = -sum_b part[b][k]; F = sum_b part[b][n] + offset (block order)
-    for (int k = threadIdx.x; k <= n; k += MP_THREADS) {
+    for (int k = wid; k <= n; k += MP_NW) {
         double s = 0.0;
-        for (int b = 0; b < a.P; ++b) s += a.part[(int64_t)b * (n + 1) + k];
-        if (k < n) a.G[k] = -s;
-        else st->F = s + a.F_offset;
+        for (int b = lane; b < P; b += 32) s += __ldcg(a.part + (int64_t)b * (n + 1) + k); // other CTAs' writes
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) {
+            if (k < n) a.G[k] = -s;
+            else a.st->F = s + a.F_offset;
+        }
     }
     __syncthreads();
-    // Eq. 9-10: freeze components at a bound whose gradient points out of the box
+}
+
+// Eq. 9-10 freeze, stopping tests, BB step length and projected update (one block).
+__device__ void bb_step(const MPArgs &a) {
+    BBState *st = a.st;
+    __shared__ double sh[MP_NW];
+    __shared__ int decided;
+    __shared__ double delta_s;
+    const int t = st->t;
+    const int n = a.n;
     for (int k = threadIdx.x; k < n; k += MP_THREADS) {
         const float yk = a.y[k], l = lo_of(a, k), h = hi_of(a, k);
         const double g = a.G[k];
@@ -205,7 +161,6 @@ __global__ void __launch_bounds__(MP_THREADS) mp_step_kernel(MPArgs a) {
     }
     __syncthreads();
     const double F = st->F;
-    // stopping tests (Section 2.1)
     double dy = 0.0, ymax = 0.0, gg = 0.0, ss = 0.0, sr = 0.0, rr = 0.0;
     for (int k = threadIdx.x; k < n; k += MP_THREADS) {
         const double yk = a.y[k], g = a.G[k];
@@ -225,8 +180,6 @@ __global__ void __launch_bounds__(MP_THREADS) mp_step_kernel(MPArgs a) {
     ss = block_reduce_sum(ss, sh);
     sr = block_reduce_sum(sr, sh);
     rr = block_reduce_sum(rr, sh);
-    __shared__ int decided;
-    __shared__ double delta_s;
     if (threadIdx.x == 0) {
         decided = 1;
         st->F_hist[t % 6] = F;
@@ -254,6 +207,183 @@ __global__ void __launch_bounds__(MP_THREADS) mp_step_kernel(MPArgs a) {
         take_step(a, delta_s);
         if (threadIdx.x == 0) st->t = t + 1;
     }
+}
+
+// Per-voxel part of an iteration for voxel i with dose zi: returns g_i, adds F_i to facc.
+__device__ __forceinline__ float voxel_terms(const float *sT, const float *sO, const float *sU, int s, float zi,
+                                             double &facc) {
+    const float t = sT[s];
+    const double dz = (double)zi - (double)t;
+    const double ov = dz > 0.0 ? dz : 0.0, un = dz < 0.0 ? -dz : 0.0;
+    facc += (double)sO[s] * ov * ov + (double)sU[s] * un * un;
+    return -2.f * sO[s] * fmaxf(0.f, zi - t) + 2.f * sU[s] * fmaxf(0.f, t - zi);
+}
+
+// Ends a pass: write this CTA's partials; the last CTA reduces them and steps.
+__device__ void pass_epilogue(const MPArgs &a, const double *accG, double facc) {
+    __shared__ double sh[MP_NW];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const double fb = block_reduce_sum(facc, sh);
+    double *out = a.part + (int64_t)blockIdx.x * (a.n + 1);
+    for (int k = tid; k < a.n; k += MP_THREADS) out[k] = accG[k];
+    if (tid == 0) out[a.n] = fb;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&a.st->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    reduce_partials(a, gridDim.x);
+    bb_step(a);
+    if (tid == 0) a.st->ticket = 0u;
+}
+
+// One BB iteration with DA tiles staged in shared memory by bulk copies.
+// Needs DA 16-byte aligned and ld a multiple of 4 (each column chunk is a copy).
+__global__ void __launch_bounds__(MP_THREADS) mp_iter_tma_kernel(MPArgs a) {
+    if (a.st->done || a.st->need_cauchy) return;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int n = a.n;
+    float *DAs = reinterpret_cast<float *>(sm);                        // [STAGES][n][256]
+    float *gs = DAs + (size_t)MP_STAGES * n * MP_THREADS;              // [256]
+    double *accG = reinterpret_cast<double *>(gs + MP_THREADS);        // [n]
+    float *sy = reinterpret_cast<float *>(accG + n);                  // [n]
+    float *sT = sy + ((n + 3) & ~3), *sO = sT + 256, *sU = sO + 256;   // [256] each
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);           // [STAGES]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k = tid; k < n; k += MP_THREADS) {
+        sy[k] = a.y[k];
+        accG[k] = 0.0;
+    }
+    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
+        sT[k] = a.T[k];
+        sO[k] = a.wo[k];
+        sU[k] = a.wu[k];
+    }
+    if (tid == 0) {
+        for (int s = 0; s < MP_STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();
+    auto issue = [&](int32_t tile, int s) {
+        const int64_t i0 = (int64_t)tile * MP_THREADS;
+        const uint32_t bytes = (uint32_t)(min64(MP_THREADS, a.ld - i0) * 4);
+        mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)n);
+        float *dst = DAs + (size_t)s * n * MP_THREADS;
+        for (int k = 0; k < n; ++k) bulk_g2s(dst + (size_t)k * MP_THREADS, a.DA + (int64_t)k * a.ld + i0, bytes, &bars[s], pol);
+    };
+    if (tid == 0)
+        for (int s = 0; s < MP_STAGES; ++s) {
+            const int32_t tile = blockIdx.x + s * gridDim.x;
+            if (tile < a.n_tiles) issue(tile, s);
+        }
+    double facc = 0.0;
+    int it = 0;
+    bool timed_out = false;
+    for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        const int s = it % MP_STAGES;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / MP_STAGES) & 1), WAIT_LIMIT_CYCLES);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const float *T = DAs + (size_t)s * n * MP_THREADS;
+        const int64_t i0 = (int64_t)tile * MP_THREADS, i = i0 + tid;
+        const bool valid = i < a.V;
+        float zi = 0.f;
+        for (int k = 0; k < n; ++k) zi = fmaf(T[k * MP_THREADS + tid], sy[k], zi);
+        float gi = 0.f;
+        if (valid) {
+            a.z[i] = zi;
+            gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
+        }
+        gs[tid] = gi;
+        __syncthreads();
+        const int nvalid = (int)min64(MP_THREADS, a.V - i0);
+        for (int k = wid; k < n; k += MP_NW) {
+            const float *col = T + k * MP_THREADS;
+            float sum = 0.f;
+#pragma unroll
+            for (int m = lane; m < MP_THREADS; m += 32)
+                if (m < nvalid) sum = fmaf(col[m], gs[m], sum);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
+            if (lane == 0) accG[k] += (double)sum;
+        }
+        __syncthreads(); // stage s consumed
+        if (tid == 0) {
+            const int32_t nt = tile + MP_STAGES * gridDim.x;
+            if (nt < a.n_tiles) {
+                fence_proxy_async_smem();
+                issue(nt, s);
+            }
+        }
+    }
+    if (timed_out) {
+        // a copy that never landed: record it, let issued copies finish, stop the solve
+        if (tid == 0) {
+            atomicOr(a.status, DEV_TIMEOUT);
+            a.st->done = 1;
+            a.st->stop = VMAT_STOP_MAXIT;
+            for (int k = 0; k < MP_STAGES; ++k) {
+                const int it2 = it + k;
+                if (blockIdx.x + it2 * gridDim.x < a.n_tiles)
+                    mbar_wait_bounded(&bars[it2 % MP_STAGES], (uint32_t)((it2 / MP_STAGES) & 1), WAIT_LIMIT_CYCLES);
+            }
+        }
+        return;
+    }
+    pass_epilogue(a, accG, facc);
+}
+
+// The same iteration reading DA straight from global memory (any alignment of DA and ld).
+__global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
+    if (a.st->done || a.st->need_cauchy) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int n = a.n;
+    float *sy = reinterpret_cast<float *>(sm);                          // [n]
+    double *accG = reinterpret_cast<double *>(sy + ((n + 3) & ~3));     // [n]
+    float *gs = reinterpret_cast<float *>(accG + n);                    // [256]
+    float *sT = gs + MP_THREADS, *sO = sT + 256, *sU = sO + 256;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k = tid; k < n; k += MP_THREADS) {
+        sy[k] = a.y[k];
+        accG[k] = 0.0;
+    }
+    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
+        sT[k] = a.T[k];
+        sO[k] = a.wo[k];
+        sU[k] = a.wu[k];
+    }
+    __syncthreads();
+    double facc = 0.0;
+    for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        const int64_t i0 = (int64_t)tile * MP_THREADS, i = i0 + tid;
+        float gi = 0.f;
+        if (i < a.V) {
+            float zi = 0.f;
+            for (int k = 0; k < n; ++k) zi = fmaf(a.DA[(int64_t)k * a.ld + i], sy[k], zi);
+            a.z[i] = zi;
+            gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
+        }
+        gs[tid] = gi;
+        __syncthreads();
+        const int nvalid = (int)min64(MP_THREADS, a.V - i0);
+        for (int k = wid; k < n; k += MP_NW) {
+            const float *col = a.DA + (int64_t)k * a.ld + i0;
+            float sum = 0.f;
+#pragma unroll
+            for (int m = lane; m < MP_THREADS; m += 32)
+                if (m < nvalid) sum = fmaf(col[m], gs[m], sum);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
+            if (lane == 0) accG[k] += (double)sum;
+        }
+        __syncthreads();
+    }
+    pass_epilogue(a, accG, facc);
 }
 
 // Cauchy step, part 1: curvature 2 sum_i w_i (DA G)_i^2 with w the active penalty weight.
@@ -285,13 +415,13 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_pass_kernel(MPArgs a) {
 }
 
 // Cauchy step, part 2: delta0 = G.G / curvature, then the first projected step.
-__global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a) {
+__global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a, int P) {
     BBState *st = a.st;
     if (st->done || !st->need_cauchy) return;
     __shared__ double curv_s;
     if (threadIdx.x == 0) {
         double c = 0.0;
-        for (int b = 0; b < a.P; ++b) c += a.cpart[b];
+        for (int b = 0; b < P; ++b) c += a.cpart[b];
         curv_s = 2.0 * c;
         st->need_cauchy = 0;
         if (curv_s == 0.0) finish(st, VMAT_STOP_FLAT, 0);
@@ -303,9 +433,11 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a) {
     if (threadIdx.x == 0) st->t = 1;
 }
 
-size_t mp_scratch_bytes(int32_t n, int P) {
-    return 256 + (size_t)n * (2 * sizeof(double) + sizeof(float)) + (size_t)P * (n + 2) * sizeof(double) + 256;
+static size_t tma_smem(int n) {
+    return (size_t)MP_STAGES * n * MP_THREADS * 4 + MP_THREADS * 4 + (size_t)n * 8 + (size_t)((n + 3) & ~3) * 4 +
+           3 * 256 * 4 + MP_STAGES * 8;
 }
+static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        const int32_t *struct_idx, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
@@ -316,9 +448,31 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
     if (opts_in) opts = *opts_in;
     if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
-    const int P = std::max(1, std::min<int>((int)((V + MP_THREADS - 1) / MP_THREADS), ctx->n_sm * 4));
+    if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
+
+    // pass kernel: bulk-copy tiles when DA and ld allow it and two stages fit
+    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (ld % 4 == 0) && tma_smem(n_ap) <= MP_SMEM_LIMIT;
+    void (*pass)(MPArgs) = tma ? mp_iter_tma_kernel : mp_iter_ldg_kernel;
+    const size_t smem_pass = tma ? tma_smem(n_ap) : ldg_smem(n_ap);
+    static bool attr = false;
+    if (!attr) {
+        VMAT_CUDA(cudaFuncSetAttribute(mp_iter_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
+        VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
+        VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       MP_SMEM_LIMIT));
+        attr = true;
+    }
+    int bps = 1;
+    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pass, MP_THREADS, smem_pass));
+    bps = std::max(bps, 1);
+    const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
+    const int P = std::max(1, std::min<int>(n_tiles, ctx->n_sm * bps));
+    const int Pc = std::max(1, std::min<int>(n_tiles, ctx->n_sm * 4));
+
     Scratch ws;
-    VMAT_TRY(ws.alloc(mp_scratch_bytes(n_ap, P), s));
+    const size_t bytes = 256 + (size_t)n_ap * (2 * sizeof(double) + sizeof(float)) +
+                         (size_t)P * (n_ap + 1) * sizeof(double) + (size_t)Pc * sizeof(double) + 256;
+    VMAT_TRY(ws.alloc(bytes, s));
     char *p = static_cast<char *>(ws.ptr);
     MPArgs a;
     a.st = reinterpret_cast<BBState *>(p);
@@ -327,7 +481,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.Gprev = a.G + n_ap;
     a.part = a.Gprev + n_ap;
     a.cpart = a.part + (size_t)P * (n_ap + 1);
-    a.yprev = reinterpret_cast<float *>(a.cpart + P);
+    a.yprev = reinterpret_cast<float *>(a.cpart + Pc);
     a.DA = DA;
     a.ld = ld;
     a.V = V;
@@ -342,18 +496,12 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.lo = lo;
     a.hi = hi;
     a.P = P;
+    a.n_tiles = n_tiles;
+    a.status = ctx->status;
     a.opts = opts;
     a.F_offset = F_offset;
-
-    const size_t smem_pass = (size_t)((n_ap + 3) & ~3) * 4 + (size_t)n_ap * 8 + MP_THREADS * 4 + 3 * 256 * 4;
     const size_t smem_cauchy = (size_t)((n_ap + 3) & ~3) * 4 + 3 * 256 * 4;
-    if (smem_pass > 200 * 1024) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
-    static bool attr = false;
-    if (!attr) {
-        VMAT_CUDA(cudaFuncSetAttribute(mp_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+
     static thread_local BBState *host_st = nullptr;
     if (!host_st) VMAT_CUDA(cudaMallocHost(&host_st, sizeof(BBState)));
 
@@ -363,12 +511,11 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     while (launched < opts.max_iter) {
         const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
         for (int c = 0; c < chunk; ++c) {
-            mp_pass_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
-            mp_step_kernel<<<1, MP_THREADS, 0, s>>>(a);
-            g_launches.fetch_add(2, std::memory_order_relaxed);
+            pass<<<P, MP_THREADS, smem_pass, s>>>(a);
+            g_launches.fetch_add(1, std::memory_order_relaxed);
             if (launched + c == 0) {
-                mp_cauchy_pass_kernel<<<P, MP_THREADS, smem_cauchy, s>>>(a);
-                mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a);
+                mp_cauchy_pass_kernel<<<Pc, MP_THREADS, smem_cauchy, s>>>(a);
+                mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a, Pc);
                 g_launches.fetch_add(2, std::memory_order_relaxed);
             }
         }
@@ -379,6 +526,9 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
         if (host_st->done) break;
     }
     if (!host_st->done) return set_error(VMAT_ECUDA, "mp_bb_solve: solver did not reach a stopping rule");
+    int32_t dev_status = 0;
+    VMAT_CUDA(cudaMemcpy(&dev_status, ctx->status, 4, cudaMemcpyDeviceToHost));
+    if (dev_status & DEV_TIMEOUT) return set_error(VMAT_ETIMEOUT, "mp_bb_solve: a device-side wait ran out");
     if (rep) {
         rep->iters = host_st->iters;
         rep->stop_reason = host_st->stop;

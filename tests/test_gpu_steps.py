@@ -128,10 +128,13 @@ def random_mp(seed, V=5000, n=8):
     return DA, s
 
 
-@pytest.mark.parametrize("seed,upper", [(0, None), (1, None), (2, 0.05), (3, None)])
-def test_mp_bb_solve(seed, upper):
+@pytest.mark.parametrize("seed,upper,V,n", [(0, None, 5000, 8), (1, None, 5000, 8), (2, 0.05, 5000, 8),
+                                            (3, None, 5000, 37),
+                                            (4, None, 4999, 8),      # ld not a multiple of 4: global-load pass
+                                            (5, None, 3000, 120)])   # too many columns for two staged tiles
+def test_mp_bb_solve(seed, upper, V, n):
     from paper_1503_01721_gb300 import api
-    DA, s = random_mp(seed, n=8 if seed < 3 else 37)
+    DA, s = random_mp(seed, V=V, n=n)
     V, n = DA.shape
     hi = None if upper is None else np.full(n, upper, np.float32)
     y = torch.zeros(n, device="cuda")
