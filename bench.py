@@ -271,7 +271,9 @@ def run_ours(args, rank, world, local):
     spmv_bytes = sum(s["pp1_spmv_bytes"] for s in stats_all)
     peaks = roofline.measured_peaks()
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "spmv_tile_kernel (beamlet price D^T g, active tiles) + spmv_fixup",
+    kname = ("spmv_tile_kernel + spmv_fixup" if info["tile_nnz_Dt"] else "spmv_warp_row_kernel") + \
+        " (beamlet price D^T g over the unoccupied CPs)"
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
             "peak_source": peaks["source"], "bytes_per_launch": round(spmv_bytes / max(spmv_n, 1)),
