@@ -401,6 +401,46 @@ def run_spmv_only(args):
     return out
 
 
+def run_mp_only(args):
+    """Master-problem driver: fixed-length BB solves (stopping rules off) on DA built
+    from seeded random apertures, for several aperture counts."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1503_01721_gb300 import api
+    import __graft_entry__
+
+    __graft_entry__.build()
+    case = synth.make_case(args.workload, seed=0, cache=False)
+    d = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+    ddc = api.Ddc(case.V, case.J, d(case.vox, torch.int32), d(case.blt, torch.int32), d(case.val, torch.float32),
+                  dtype=args.dtype, build_Dt=False)
+    vox = api.VoxelParams.from_numpy(case.structs)
+    out = {"mode": "mp", "workload": args.workload, "V": case.V, "sizes": {}}
+    iters = 60
+    opts = api.BBOptions(max_iter=iters, rel_tol5=0.0, step_tol=0.0)
+    for n in (8, 30, 60):
+        cps, leaves, _ = synth.random_apertures(case.mlc, n, n, 8, 40)
+        DA = torch.empty(n, case.V, device="cuda")
+        for k in range(n):
+            api.aperture_dose(ddc.h, case.mlc, int(cps[k]), d(leaves[k], torch.int16), DA[k])
+        DA.mul_(0.02)  # doses near the prescriptions
+        z = torch.empty(case.V, device="cuda")
+        y = torch.zeros(n, device="cuda")
+        api.mp_bb_solve(DA, vox, y, z, opts=opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y.zero_()
+        rep = api.mp_bb_solve(DA, vox, y, z, opts=opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        b = rep["iters"] * (4.0 * n * case.V + 9.0 * case.V)
+        out["sizes"][n] = {"iters": rep["iters"], "ms_per_iter": round(dt * 1e3 / rep["iters"], 4),
+                           "gbs": round(b / dt / 1e9, 1), "DA_MB": round(4 * n * case.V / 1e6, 1)}
+    ddc.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -426,8 +466,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS))
-    ap.add_argument("--mode", default="plan", choices=["plan", "spmv"],
-                    help="spmv: only build and run D^T g and D x a few times (profiling driver)")
+    ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp"],
+                    help="spmv: only build and run D^T g and D x a few times (profiling driver); "
+                         "mp: fixed-length master-problem solves")
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     args = ap.parse_args()
@@ -436,6 +477,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.mode == "spmv":
         out = run_spmv_only(args) if rank == 0 else None
+    elif args.mode == "mp":
+        out = run_mp_only(args) if rank == 0 else None
     else:
         out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libvmat translation units (host + device helpers).
 #pragma once
 
+#include <cuda.h> // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -140,6 +141,12 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
 vmat_status validate_mlc(const vmat_mlc *mlc);
 vmat_status validate_voxels(const vmat_voxels *vox);
 
+// 2-D tiled tensor map over a float32 matrix stored as `outer` rows of `inner`
+// elements with a row pitch of `pitch_bytes` (multiple of 16); boxes of
+// box_inner x box_outer elements; reads past `inner` or `outer` return 0.
+vmat_status make_tensor_map_2d_f32(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                                   uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer);
+
 // Exclusive scan of int32 counts into int64 offsets (out has n + 1 entries).
 vmat_status scan_counts(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 
@@ -198,6 +205,12 @@ __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     return pol;
 }
 
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // 1-D bulk copy global -> shared, completion counted on an mbarrier.
 // dst/src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
@@ -205,6 +218,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// 2-D tiled bulk tensor copy global -> shared of the box at element (x, y).
+// x * 4 bytes must be a multiple of 16.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar,
+                                            uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 

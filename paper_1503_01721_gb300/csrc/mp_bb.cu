@@ -239,82 +239,76 @@ __device__ void pass_epilogue(const MPArgs &a, const double *accG, double facc) 
     if (tid == 0) a.st->ticket = 0u;
 }
 
-// One BB iteration with DA tiles staged in shared memory by bulk copies.
-// Needs DA 16-byte aligned and ld a multiple of 4 (each column chunk is a copy).
-__global__ void __launch_bounds__(MP_THREADS) mp_iter_tma_kernel(MPArgs a) {
+// One BB iteration with DA tiles staged in shared memory by 2-D tensor copies
+// (one [n x 256] box per tile, `stages` tiles in flight, zero fill past V).
+// Each thread owns one voxel of every tile and keeps its share of
+// G = -DA^T g for all columns in registers (NMAX >= n) across the tiles of its
+// CTA; one block reduction per pass.  Needs DA 16-byte aligned and ld a
+// multiple of 4 (the tensor map's row pitch).
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS)
+    mp_iter_tma_kernel(MPArgs a, const __grid_constant__ CUtensorMap map, int stages, int keep_in_l2) {
     if (a.st->done || a.st->need_cauchy) return;
     extern __shared__ __align__(128) unsigned char sm[];
     const int n = a.n;
-    float *DAs = reinterpret_cast<float *>(sm);                        // [STAGES][n][256]
-    float *gs = DAs + (size_t)MP_STAGES * n * MP_THREADS;              // [256]
-    double *accG = reinterpret_cast<double *>(gs + MP_THREADS);        // [n]
-    float *sy = reinterpret_cast<float *>(accG + n);                  // [n]
+    float *DAs = reinterpret_cast<float *>(sm);                        // [stages][n][256]
+    double *accG = reinterpret_cast<double *>(DAs + (size_t)stages * n * MP_THREADS); // [n]
+    float *wred = reinterpret_cast<float *>(accG + NMAX);              // [MP_NW][NMAX]
+    float *sy = wred + MP_NW * NMAX;                                   // [n]
     float *sT = sy + ((n + 3) & ~3), *sO = sT + 256, *sU = sO + 256;   // [256] each
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);           // [STAGES]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);           // [stages]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < n; k += MP_THREADS) {
-        sy[k] = a.y[k];
-        accG[k] = 0.0;
-    }
+    for (int k = tid; k < n; k += MP_THREADS) sy[k] = a.y[k];
     for (int k = tid; k < a.n_struct; k += MP_THREADS) {
         sT[k] = a.T[k];
         sO[k] = a.wo[k];
         sU[k] = a.wu[k];
     }
     if (tid == 0) {
-        for (int s = 0; s < MP_STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    const uint64_t pol = l2_evict_first_policy();
+    // DA is read again by the next iteration: keep it in L2 when it fits there
+    const uint64_t pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
     auto issue = [&](int32_t tile, int s) {
-        const int64_t i0 = (int64_t)tile * MP_THREADS;
-        const uint32_t bytes = (uint32_t)(min64(MP_THREADS, a.ld - i0) * 4);
-        mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)n);
-        float *dst = DAs + (size_t)s * n * MP_THREADS;
-        for (int k = 0; k < n; ++k) bulk_g2s(dst + (size_t)k * MP_THREADS, a.DA + (int64_t)k * a.ld + i0, bytes, &bars[s], pol);
+        mbar_arrive_expect_tx(&bars[s], (uint32_t)(MP_THREADS * 4) * (uint32_t)n);
+        tma_load_2d(DAs + (size_t)s * n * MP_THREADS, &map, tile * MP_THREADS, 0, &bars[s], pol);
     };
     if (tid == 0)
-        for (int s = 0; s < MP_STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             const int32_t tile = blockIdx.x + s * gridDim.x;
             if (tile < a.n_tiles) issue(tile, s);
         }
+    float gacc[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
     double facc = 0.0;
     int it = 0;
     bool timed_out = false;
     for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-        const int s = it % MP_STAGES;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / MP_STAGES) & 1), WAIT_LIMIT_CYCLES);
+        const int s = it % stages;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / stages) & 1), WAIT_LIMIT_CYCLES);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;
         }
-        const float *T = DAs + (size_t)s * n * MP_THREADS;
-        const int64_t i0 = (int64_t)tile * MP_THREADS, i = i0 + tid;
-        const bool valid = i < a.V;
-        float zi = 0.f;
-        for (int k = 0; k < n; ++k) zi = fmaf(T[k * MP_THREADS + tid], sy[k], zi);
-        float gi = 0.f;
-        if (valid) {
+        const float *T = DAs + (size_t)s * n * MP_THREADS + tid;
+        const int64_t i = (int64_t)tile * MP_THREADS + tid;
+        if (i < a.V) {
+            float zi = 0.f;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k)
+                if (k < n) zi = fmaf(T[k * MP_THREADS], sy[k], zi);
             a.z[i] = zi;
-            gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
-        }
-        gs[tid] = gi;
-        __syncthreads();
-        const int nvalid = (int)min64(MP_THREADS, a.V - i0);
-        for (int k = wid; k < n; k += MP_NW) {
-            const float *col = T + k * MP_THREADS;
-            float sum = 0.f;
+            const float gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
 #pragma unroll
-            for (int m = lane; m < MP_THREADS; m += 32)
-                if (m < nvalid) sum = fmaf(col[m], gs[m], sum);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
-            if (lane == 0) accG[k] += (double)sum;
+            for (int k = 0; k < NMAX; ++k)
+                if (k < n) gacc[k] = fmaf(T[k * MP_THREADS], gi, gacc[k]);
         }
         __syncthreads(); // stage s consumed
         if (tid == 0) {
-            const int32_t nt = tile + MP_STAGES * gridDim.x;
+            const int32_t nt = tile + stages * gridDim.x;
             if (nt < a.n_tiles) {
                 fence_proxy_async_smem();
                 issue(nt, s);
@@ -327,14 +321,31 @@ __global__ void __launch_bounds__(MP_THREADS) mp_iter_tma_kernel(MPArgs a) {
             atomicOr(a.status, DEV_TIMEOUT);
             a.st->done = 1;
             a.st->stop = VMAT_STOP_MAXIT;
-            for (int k = 0; k < MP_STAGES; ++k) {
+            for (int k = 0; k < stages; ++k) {
                 const int it2 = it + k;
                 if (blockIdx.x + it2 * gridDim.x < a.n_tiles)
-                    mbar_wait_bounded(&bars[it2 % MP_STAGES], (uint32_t)((it2 / MP_STAGES) & 1), WAIT_LIMIT_CYCLES);
+                    mbar_wait_bounded(&bars[it2 % stages], (uint32_t)((it2 / stages) & 1), WAIT_LIMIT_CYCLES);
             }
         }
         return;
     }
+    // block reduction of the per-thread shares: butterfly per warp, warps in order
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        if (k < n) {
+            float v = gacc[k];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) wred[wid * NMAX + k] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += MP_THREADS) {
+        double s = 0.0;
+        for (int w = 0; w < MP_NW; ++w) s += (double)wred[w * NMAX + k];
+        accG[k] = s;
+    }
+    __syncthreads();
     pass_epilogue(a, accG, facc);
 }
 
@@ -433,9 +444,33 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a, in
     if (threadIdx.x == 0) st->t = 1;
 }
 
-static size_t tma_smem(int n) {
-    return (size_t)MP_STAGES * n * MP_THREADS * 4 + MP_THREADS * 4 + (size_t)n * 8 + (size_t)((n + 3) & ~3) * 4 +
-           3 * 256 * 4 + MP_STAGES * 8;
+constexpr int MP_NMAX = 96; // register-resident gradient shares: up to 96 apertures
+
+static int tma_nmax(int n) { return ((n + 7) / 8) * 8; }
+static int tma_stages(int n) { return std::max(MP_STAGES, std::min(6, 96 / std::max(n, 1))); } // ~96 KB in flight
+static size_t tma_smem(int n, int stages) {
+    const int nmax = tma_nmax(n);
+    return (size_t)stages * n * MP_THREADS * 4 + (size_t)nmax * 8 + (size_t)MP_NW * nmax * 4 +
+           (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4 + (size_t)stages * 8;
+}
+
+using TmaIterFn = void (*)(MPArgs, const CUtensorMap, int, int);
+static TmaIterFn tma_kernel_for(int n) {
+    switch ((n + 7) / 8) {
+    case 1: return mp_iter_tma_kernel<8>;
+    case 2: return mp_iter_tma_kernel<16>;
+    case 3: return mp_iter_tma_kernel<24>;
+    case 4: return mp_iter_tma_kernel<32>;
+    case 5: return mp_iter_tma_kernel<40>;
+    case 6: return mp_iter_tma_kernel<48>;
+    case 7: return mp_iter_tma_kernel<56>;
+    case 8: return mp_iter_tma_kernel<64>;
+    case 9: return mp_iter_tma_kernel<72>;
+    case 10: return mp_iter_tma_kernel<80>;
+    case 11: return mp_iter_tma_kernel<88>;
+    case 12: return mp_iter_tma_kernel<96>;
+    default: return nullptr;
+    }
 }
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
@@ -450,20 +485,31 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
     if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
 
-    // pass kernel: bulk-copy tiles when DA and ld allow it and two stages fit
-    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (ld % 4 == 0) && tma_smem(n_ap) <= MP_SMEM_LIMIT;
-    void (*pass)(MPArgs) = tma ? mp_iter_tma_kernel : mp_iter_ldg_kernel;
-    const size_t smem_pass = tma ? tma_smem(n_ap) : ldg_smem(n_ap);
+    // pass kernel: bulk-copied tiles with register-resident gradient shares when
+    // DA and ld allow the copies and the apertures fit; otherwise global loads
+    const int stages = tma_stages(n_ap);
+    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (ld % 4 == 0) && n_ap <= MP_NMAX &&
+                     tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
+    TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
+    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : ldg_smem(n_ap);
+    const int keep_in_l2 = (double)n_ap * (double)ld * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
+    CUtensorMap map;
+    if (tma) // rows = apertures (pitch ld floats), columns = voxels; box = 256 voxels x all apertures
+        VMAT_TRY(make_tensor_map_2d_f32(&map, DA, (uint64_t)V, (uint64_t)n_ap, (uint64_t)ld * 4, MP_THREADS,
+                                        (uint32_t)n_ap));
     static bool attr = false;
     if (!attr) {
-        VMAT_CUDA(cudaFuncSetAttribute(mp_iter_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
+        for (int q = 1; q <= MP_NMAX / 8; ++q)
+            VMAT_CUDA(cudaFuncSetAttribute(tma_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           MP_SMEM_LIMIT));
         VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
         VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        MP_SMEM_LIMIT));
         attr = true;
     }
     int bps = 1;
-    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pass, MP_THREADS, smem_pass));
+    if (tma) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tma_fn, MP_THREADS, smem_pass));
+    else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, smem_pass));
     bps = std::max(bps, 1);
     const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
     const int P = std::max(1, std::min<int>(n_tiles, ctx->n_sm * bps));
@@ -511,7 +557,8 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     while (launched < opts.max_iter) {
         const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
         for (int c = 0; c < chunk; ++c) {
-            pass<<<P, MP_THREADS, smem_pass, s>>>(a);
+            if (tma) tma_fn<<<P, MP_THREADS, smem_pass, s>>>(a, map, stages, keep_in_l2);
+            else mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
             g_launches.fetch_add(1, std::memory_order_relaxed);
             if (launched + c == 0) {
                 mp_cauchy_pass_kernel<<<Pc, MP_THREADS, smem_cauchy, s>>>(a);
