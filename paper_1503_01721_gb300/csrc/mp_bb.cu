@@ -249,9 +249,19 @@ template <int NMAX>
 __global__ void __launch_bounds__(MP_THREADS)
     mp_iter_tma_kernel(MPArgs a, const __grid_constant__ CUtensorMap map, int stages, int keep_in_l2) {
     if (a.st->done || a.st->need_cauchy) return;
-    extern __shared__ __align__(128) unsigned char sm[];
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    // tensor copies need a 128-byte aligned destination; static shared memory of
+    // this kernel may shift the dynamic region, so align explicitly (+128 bytes)
+    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
     const int n = a.n;
     float *DAs = reinterpret_cast<float *>(sm);                        // [stages][n][256]
+    if ((smem_u32(DAs) & 127u) != 0u) { // self-check: never issue a misaligned tensor copy
+        if (threadIdx.x == 0) {
+            atomicOr(a.status, DEV_INDEX);
+            a.st->done = 1;
+        }
+        return;
+    }
     double *accG = reinterpret_cast<double *>(DAs + (size_t)stages * n * MP_THREADS); // [n]
     float *wred = reinterpret_cast<float *>(accG + NMAX);              // [MP_NW][NMAX]
     float *sy = wred + MP_NW * NMAX;                                   // [n]
@@ -450,8 +460,8 @@ static int tma_nmax(int n) { return ((n + 7) / 8) * 8; }
 static int tma_stages(int n) { return std::max(MP_STAGES, std::min(6, 96 / std::max(n, 1))); } // ~96 KB in flight
 static size_t tma_smem(int n, int stages) {
     const int nmax = tma_nmax(n);
-    return (size_t)stages * n * MP_THREADS * 4 + (size_t)nmax * 8 + (size_t)MP_NW * nmax * 4 +
-           (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4 + (size_t)stages * 8;
+    return 128 /* alignment slack */ + (size_t)stages * n * MP_THREADS * 4 + (size_t)nmax * 8 +
+           (size_t)MP_NW * nmax * 4 + (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4 + (size_t)stages * 8;
 }
 
 using TmaIterFn = void (*)(MPArgs, const CUtensorMap, int, int);
