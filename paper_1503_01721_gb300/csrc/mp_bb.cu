@@ -129,7 +129,9 @@ __device__ void reduce_partials(const MPArgs &a, int P) {
     const int n = a.n;
     for (int k = wid; k <= n; k += MP_NW) {
         double s = 0.0;
-        for (int b = lane; b < P; b += 32) s += __ldcg(a.part + (int64_t)b * (n + 1) + k); // other CTAs' writes
+        // other CTAs' writes: bypass L1; 8 loads in flight per lane
+#pragma unroll 8
+        for (int b = lane; b < P; b += 32) s += __ldcg(a.part + (int64_t)b * (n + 1) + k);
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
         if (lane == 0) {
@@ -174,12 +176,42 @@ __device__ void bb_step(const MPArgs &a) {
             rr += r * r;
         }
     }
-    dy = block_reduce_max(dy, sh);
-    ymax = block_reduce_max(ymax, sh);
-    gg = block_reduce_sum(gg, sh);
-    ss = block_reduce_sum(ss, sh);
-    sr = block_reduce_sum(sr, sh);
-    rr = block_reduce_sum(rr, sh);
+    { // one combined block reduction of the six quantities (two maxima, four sums)
+        __shared__ double red[MP_NW][6];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            dy = fmax(dy, __shfl_down_sync(0xffffffffu, dy, d));
+            ymax = fmax(ymax, __shfl_down_sync(0xffffffffu, ymax, d));
+            gg += __shfl_down_sync(0xffffffffu, gg, d);
+            ss += __shfl_down_sync(0xffffffffu, ss, d);
+            sr += __shfl_down_sync(0xffffffffu, sr, d);
+            rr += __shfl_down_sync(0xffffffffu, rr, d);
+        }
+        if (lane == 0) {
+            red[wid][0] = dy;
+            red[wid][1] = ymax;
+            red[wid][2] = gg;
+            red[wid][3] = ss;
+            red[wid][4] = sr;
+            red[wid][5] = rr;
+        }
+        __syncthreads();
+        dy = red[0][0];
+        ymax = red[0][1];
+        gg = red[0][2];
+        ss = red[0][3];
+        sr = red[0][4];
+        rr = red[0][5];
+        for (int w = 1; w < MP_NW; ++w) {
+            dy = fmax(dy, red[w][0]);
+            ymax = fmax(ymax, red[w][1]);
+            gg += red[w][2];
+            ss += red[w][3];
+            sr += red[w][4];
+            rr += red[w][5];
+        }
+    }
     if (threadIdx.x == 0) {
         decided = 1;
         st->F_hist[t % 6] = F;
@@ -457,7 +489,13 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a, in
 constexpr int MP_NMAX = 96; // register-resident gradient shares: up to 96 apertures
 
 static int tma_nmax(int n) { return ((n + 7) / 8) * 8; }
-static int tma_stages(int n) { return std::max(MP_STAGES, std::min(6, 96 / std::max(n, 1))); } // ~96 KB in flight
+// Tiles in flight per CTA (n KB each): ~100 KB so that two CTAs share an SM while
+// that still allows 3 stages, else ~190 KB for one CTA; at least double-buffered.
+static int tma_stages(int n) {
+    n = std::max(n, 1);
+    const int budget = 3 * n <= 100 ? 100 : 190;
+    return std::max(MP_STAGES, std::min(6, budget / n));
+}
 static size_t tma_smem(int n, int stages) {
     const int nmax = tma_nmax(n);
     return 128 /* alignment slack */ + (size_t)stages * n * MP_THREADS * 4 + (size_t)nmax * 8 +
