@@ -29,7 +29,8 @@ __device__ __forceinline__ float load_val(const void *val, int64_t e, vmat_dtype
 __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                      const void *__restrict__ val, vmat_dtype dt, const float *__restrict__ scale,
                                      int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp, int32_t n_rrows,
-                                     int32_t n_cols, const int16_t *__restrict__ leaves, float *__restrict__ da) {
+                                     int32_t n_cols, const int16_t *__restrict__ leaves, float *__restrict__ da,
+                                     int64_t tstride) {
     extern __shared__ int16_t sl[]; // [n_rrows][2]
     for (int i = threadIdx.x; i < 2 * n_rrows; i += blockDim.x) sl[i] = leaves[i];
     __syncthreads();
@@ -54,12 +55,15 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
                 acc += v;
             }
         }
-        da[row_ids ? row_ids[row] : row] = acc;
+        // output: voxel space, compact row space, or the tile-contiguous layout of the
+        // master problem (row r at (r / 256) * tstride + r % 256 from da)
+        const int64_t o = row_ids ? row_ids[row] : (tstride ? (int64_t)(row >> 8) * tstride + (row & 255) : row);
+        da[o] = acc;
     }
 }
 
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
-                               bool compact, cudaStream_t s) {
+                               bool compact, cudaStream_t s, int64_t tstride) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     if (!compact) VMAT_CUDA(cudaMemsetAsync(da, 0, (size_t)h.V * 4, s));
@@ -68,7 +72,7 @@ vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, co
     const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
     aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
         h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n,
-        compact ? nullptr : h.D.row_ids, cp, mlc->n_rows, mlc->n_cols, leaves, da);
+        compact ? nullptr : h.D.row_ids, cp, mlc->n_rows, mlc->n_cols, leaves, da, compact ? tstride : 0);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

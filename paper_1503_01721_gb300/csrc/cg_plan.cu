@@ -120,7 +120,11 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     cudaStream_t s = as_stream(stream);
     const int32_t V = h.V, J = h.J, K = mlc->K, NR = mlc->n_rows, NA = h.n_active;
     const int32_t bpc = NR * mlc->n_cols;
-    const int64_t ld = ((int64_t)std::max(NA, 1) + 31) / 32 * 32;
+    // DA in the tile-contiguous layout: 256-voxel tiles, each holding all n_apertures
+    // columns back to back, so one master-problem tile is one contiguous block
+    const int64_t n_vtiles = ((int64_t)std::max(NA, 1) + 255) / 256;
+    const int64_t ld = n_vtiles * 256;                          // voxel slots
+    const int64_t tstride = (int64_t)std::max(n_apertures, 1) * 256; // floats per tile
     const int nap_max = std::max(n_apertures, 1);
     const int g256 = std::max(1, ctx->n_sm * 4);
 
@@ -134,7 +138,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&z_c, std::max(NA, 1)));
     VMAT_TRY(ar.get(&g_full, V));
     VMAT_TRY(ar.get(&pi, J));
-    VMAT_TRY(ar.get(&DA, (size_t)ld * nap_max));
+    VMAT_TRY(ar.get(&DA, (size_t)n_vtiles * tstride));
     VMAT_TRY(ar.get(&y, nap_max));
     VMAT_TRY(ar.get(&x, J));
     VMAT_TRY(ar.get(&dose, V));
@@ -244,13 +248,13 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         occ_host[k] = 1;
         // ---- DA (Eq. 5)
         tm.mark(PH_DA);
-        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)t * ld, true, s));
+        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)t * 256, true, s, tstride));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
         VMAT_CUDA(cudaMemsetAsync(y + t, 0, 4, s));
         vmat_bb_report rep;
         if (NA > 0) {
-            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, nullptr, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
+            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, tstride, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
                                 &rep, s));
             bb_total += rep.iters;
         }

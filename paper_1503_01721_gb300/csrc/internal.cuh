@@ -130,12 +130,16 @@ vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compa
 vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                            float *g_scatter, double *F, double F_offset, cudaStream_t s);
 
+// compact: write row r of CSR(D) (tstride == 0: at da[r]; else at da[(r / 256) * tstride + r % 256]);
+// otherwise write voxel space da[V] (zero where D has no row).
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
-                               bool compact, cudaStream_t s);
+                               bool compact, cudaStream_t s, int64_t tstride = 0);
 
 struct BBWork; // defined in mp_bb.cu
+// DA layout: column-major (DA[k * ld + i]) when tstride == 0, else tile-contiguous
+// (DA[(i / 256) * tstride + k * 256 + i % 256], tstride a multiple of 256).
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
-                       const int32_t *struct_idx, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);
 
 vmat_status validate_mlc(const vmat_mlc *mlc);

@@ -19,6 +19,7 @@
 // odd iterations; s.r <= 0 takes the largest step; steps are clamped to
 // [delta_min, delta_max] times the Cauchy step.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -48,7 +49,8 @@ struct BBState {
 
 struct MPArgs {
     const float *DA;
-    int64_t ld;
+    int64_t ld;      // column-major layout: DA[k * ld + i]
+    int64_t tstride; // tile-contiguous layout when > 0: DA[(i / 256) * tstride + k * 256 + i % 256]
     int32_t V, n;
     const uint8_t *sid;
     const float *T, *wo, *wu;
@@ -69,6 +71,11 @@ struct MPArgs {
 };
 
 __device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
+
+// Offset of DA(voxel i, aperture k) in either layout.
+__device__ __forceinline__ int64_t da_at(const MPArgs &a, int64_t i, int k) {
+    return a.tstride ? (i >> 8) * a.tstride + (int64_t)k * 256 + (i & 255) : (int64_t)k * a.ld + i;
+}
 __device__ __forceinline__ float lo_of(const MPArgs &a, int k) { return a.lo ? a.lo[k] : 0.f; }
 __device__ __forceinline__ float hi_of(const MPArgs &a, int k) { return a.hi ? a.hi[k] : INFINITY; }
 
@@ -314,8 +321,13 @@ __global__ void __launch_bounds__(MP_THREADS)
     // DA is read again by the next iteration: keep it in L2 when it fits there
     const uint64_t pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
     auto issue = [&](int32_t tile, int s) {
-        mbar_arrive_expect_tx(&bars[s], (uint32_t)(MP_THREADS * 4) * (uint32_t)n);
-        tma_load_2d(DAs + (size_t)s * n * MP_THREADS, &map, tile * MP_THREADS, 0, &bars[s], pol);
+        const uint32_t bytes = (uint32_t)(MP_THREADS * 4) * (uint32_t)n;
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        float *dst = DAs + (size_t)s * n * MP_THREADS;
+        if (a.tstride) // tile-contiguous layout: the tile's n columns are one block
+            bulk_g2s(dst, a.DA + (int64_t)tile * a.tstride, bytes, &bars[s], pol);
+        else
+            tma_load_2d(dst, &map, tile * MP_THREADS, 0, &bars[s], pol);
     };
     if (tid == 0)
         for (int s = 0; s < stages; ++s) {
@@ -417,7 +429,7 @@ __global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
         float gi = 0.f;
         if (i < a.V) {
             float zi = 0.f;
-            for (int k = 0; k < n; ++k) zi = fmaf(a.DA[(int64_t)k * a.ld + i], sy[k], zi);
+            for (int k = 0; k < n; ++k) zi = fmaf(a.DA[da_at(a, i, k)], sy[k], zi);
             a.z[i] = zi;
             gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
         }
@@ -425,11 +437,10 @@ __global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
         __syncthreads();
         const int nvalid = (int)min64(MP_THREADS, a.V - i0);
         for (int k = wid; k < n; k += MP_NW) {
-            const float *col = a.DA + (int64_t)k * a.ld + i0;
             float sum = 0.f;
 #pragma unroll
             for (int m = lane; m < MP_THREADS; m += 32)
-                if (m < nvalid) sum = fmaf(col[m], gs[m], sum);
+                if (m < nvalid) sum = fmaf(a.DA[da_at(a, i0 + m, k)], gs[m], sum);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, d);
             if (lane == 0) accG[k] += (double)sum;
@@ -457,7 +468,7 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_pass_kernel(MPArgs a) {
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * MP_THREADS + tid; i < a.V; i += (int64_t)gridDim.x * MP_THREADS) {
         float q = 0.f;
-        for (int k = 0; k < a.n; ++k) q = fmaf(a.DA[(int64_t)k * a.ld + i], sg[k], q);
+        for (int k = 0; k < a.n; ++k) q = fmaf(a.DA[da_at(a, i, k)], sg[k], q);
         const int s = a.sid[i];
         const float zi = a.z[i], t = sT[s];
         const float w = zi > t ? sO[s] : (zi < t ? sU[s] : 0.f);
@@ -523,9 +534,8 @@ static TmaIterFn tma_kernel_for(int n) {
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
-                       const int32_t *struct_idx, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts_in, double F_offset, vmat_bb_report *rep, cudaStream_t s) {
-    (void)struct_idx;
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
@@ -536,13 +546,15 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     // pass kernel: bulk-copied tiles with register-resident gradient shares when
     // DA and ld allow the copies and the apertures fit; otherwise global loads
     const int stages = tma_stages(n_ap);
-    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (ld % 4 == 0) && n_ap <= MP_NMAX &&
-                     tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
+    const bool tiled = tstride > 0;
+    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (tiled ? tstride % 4 == 0 : ld % 4 == 0) &&
+                     n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
     TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
     const size_t smem_pass = tma ? tma_smem(n_ap, stages) : ldg_smem(n_ap);
-    const int keep_in_l2 = (double)n_ap * (double)ld * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
+    const int keep_in_l2 = (double)n_ap * (double)V * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
     CUtensorMap map;
-    if (tma) // rows = apertures (pitch ld floats), columns = voxels; box = 256 voxels x all apertures
+    memset(&map, 0, sizeof(map));
+    if (tma && !tiled) // rows = apertures (pitch ld floats), columns = voxels; box = 256 voxels x all apertures
         VMAT_TRY(make_tensor_map_2d_f32(&map, DA, (uint64_t)V, (uint64_t)n_ap, (uint64_t)ld * 4, MP_THREADS,
                                         (uint32_t)n_ap));
     static bool attr = false;
@@ -578,6 +590,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.yprev = reinterpret_cast<float *>(a.cpart + Pc);
     a.DA = DA;
     a.ld = ld;
+    a.tstride = tiled ? tstride : 0;
     a.V = V;
     a.n = n_ap;
     a.sid = struct_id;
@@ -643,5 +656,5 @@ extern "C" vmat_status mp_bb_solve(const float *DA, int32_t V, int32_t n_ap, int
     VMAT_TRY(validate_voxels(vox));
     if (V <= 0 || n_ap <= 0 || ld < V || !DA || !y || !z)
         return set_error(VMAT_EINVAL, "mp_bb_solve: need V > 0, n_ap > 0, ld >= V and non-NULL DA, y, z");
-    return mp_bb_impl(DA, V, n_ap, ld, vox->struct_id, nullptr, vox, lo, hi, y, z, opts, 0.0, rep, as_stream(stream));
+    return mp_bb_impl(DA, V, n_ap, ld, vox->struct_id, 0, vox, lo, hi, y, z, opts, 0.0, rep, as_stream(stream));
 }
