@@ -363,10 +363,9 @@ __global__ void __launch_bounds__(MP_THREADS)
         __syncthreads(); // stage s consumed
         if (tid == 0) {
             const int32_t nt = tile + stages * gridDim.x;
-            if (nt < a.n_tiles) {
-                fence_proxy_async_smem();
-                issue(nt, s);
-            }
+            // the barrier above orders every thread's reads of stage s before the copy
+            // that overwrites it (no proxy fence: it would also wait for the other stages)
+            if (nt < a.n_tiles) issue(nt, s);
         }
     }
     if (timed_out) {

@@ -172,12 +172,9 @@ __global__ void __launch_bounds__(THREADS) spmv_tile_kernel(SpmvParams p) {
             reinterpret_cast<float4 *>(prod)[phys] = pr;
         }
         __syncthreads(); // stage s fully consumed, products visible
-        if (tid == 0) {
+        if (tid == 0) { // the barrier orders all reads of stage s before its next copy
             const int32_t wn = w + STAGES * gridDim.x;
-            if (wn < n_work) {
-                fence_proxy_async_smem();
-                issue(wn, s);
-            }
+            if (wn < n_work) issue(wn, s);
         }
 
         // ---- phase B: each thread owns entries [a, a + E) of the tile
