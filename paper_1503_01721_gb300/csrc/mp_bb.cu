@@ -402,6 +402,69 @@ __global__ void __launch_bounds__(MP_THREADS)
     pass_epilogue(a, accG, facc);
 }
 
+// One BB iteration streaming DA with plain loads: each thread owns one voxel of
+// each 256-voxel tile, issues its n column loads before the dose FMA chain,
+// then re-reads them (L1 hits) to add DA_ik g_i to its register-resident shares
+// of G for all columns (NMAX >= n).  No shared-memory staging and no barrier
+// per tile; one block reduction per pass.
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS) mp_iter_reg_kernel(MPArgs a) {
+    if (a.st->done || a.st->need_cauchy) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int n = a.n;
+    double *accG = reinterpret_cast<double *>(sm);                    // [NMAX]
+    float *wred = reinterpret_cast<float *>(accG + NMAX);             // [MP_NW][NMAX]
+    float *sy = wred + MP_NW * NMAX;                                  // [n]
+    float *sT = sy + ((n + 3) & ~3), *sO = sT + 256, *sU = sO + 256;  // [256] each
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k = tid; k < n; k += MP_THREADS) sy[k] = a.y[k];
+    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
+        sT[k] = a.T[k];
+        sO[k] = a.wo[k];
+        sU[k] = a.wu[k];
+    }
+    __syncthreads();
+    float gacc[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
+    double facc = 0.0;
+    for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        const int64_t i = (int64_t)tile * MP_THREADS + tid;
+        if (i >= a.V) continue;
+        const float *col0 = a.DA + da_at(a, i, 0);
+        const int64_t kstride = a.tstride ? 256 : a.ld;
+        float v[NMAX];
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) v[k] = k < n ? __ldg(col0 + k * kstride) : 0.f;
+        float zi = 0.f;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < n) zi = fmaf(v[k], sy[k], zi);
+        a.z[i] = zi;
+        const float gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < n) gacc[k] = fmaf(v[k], gi, gacc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        if (k < n) {
+            float x = gacc[k];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+            if (lane == 0) wred[wid * NMAX + k] = x;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += MP_THREADS) {
+        double s = 0.0;
+        for (int w = 0; w < MP_NW; ++w) s += (double)wred[w * NMAX + k];
+        accG[k] = s;
+    }
+    __syncthreads();
+    pass_epilogue(a, accG, facc);
+}
+
 // The same iteration reading DA straight from global memory (any alignment of DA and ld).
 __global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
     if (a.st->done || a.st->need_cauchy) return;
@@ -532,6 +595,35 @@ static TmaIterFn tma_kernel_for(int n) {
 }
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
+using RegIterFn = void (*)(MPArgs);
+static RegIterFn reg_kernel_for(int n) {
+    switch ((n + 7) / 8) {
+    case 1: return mp_iter_reg_kernel<8>;
+    case 2: return mp_iter_reg_kernel<16>;
+    case 3: return mp_iter_reg_kernel<24>;
+    case 4: return mp_iter_reg_kernel<32>;
+    case 5: return mp_iter_reg_kernel<40>;
+    case 6: return mp_iter_reg_kernel<48>;
+    case 7: return mp_iter_reg_kernel<56>;
+    case 8: return mp_iter_reg_kernel<64>;
+    case 9: return mp_iter_reg_kernel<72>;
+    case 10: return mp_iter_reg_kernel<80>;
+    case 11: return mp_iter_reg_kernel<88>;
+    case 12: return mp_iter_reg_kernel<96>;
+    default: return nullptr;
+    }
+}
+static size_t reg_smem(int n) {
+    const int nmax = tma_nmax(n);
+    return (size_t)nmax * 8 + (size_t)MP_NW * nmax * 4 + (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4;
+}
+
+// Pass kernel: plain-load streaming with register-resident gradient shares (the
+// fastest on GB300 for this access pattern) up to 96 apertures, global loads
+// with per-tile reductions beyond; VMAT_MP_PASS=tma selects the bulk-copy
+// staging variant where DA's alignment allows it.
+enum PassKind { PASS_REG, PASS_TMA, PASS_LDG };
+
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts_in, double F_offset, vmat_bb_report *rep, cudaStream_t s) {
@@ -542,14 +634,17 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
     if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
 
-    // pass kernel: bulk-copied tiles with register-resident gradient shares when
-    // DA and ld allow the copies and the apertures fit; otherwise global loads
     const int stages = tma_stages(n_ap);
     const bool tiled = tstride > 0;
-    const bool tma = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (tiled ? tstride % 4 == 0 : ld % 4 == 0) &&
-                     n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
+    const bool tma_ok = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (tiled ? tstride % 4 == 0 : ld % 4 == 0) &&
+                        n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
+    const char *pass_env = getenv("VMAT_MP_PASS");
+    PassKind kind = n_ap <= MP_NMAX ? PASS_REG : PASS_LDG;
+    if (pass_env && strcmp(pass_env, "tma") == 0 && tma_ok) kind = PASS_TMA;
+    const bool tma = kind == PASS_TMA;
     TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
-    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : ldg_smem(n_ap);
+    RegIterFn reg_fn = kind == PASS_REG ? reg_kernel_for(n_ap) : nullptr;
+    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : (kind == PASS_REG ? reg_smem(n_ap) : ldg_smem(n_ap));
     const int keep_in_l2 = (double)n_ap * (double)V * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
@@ -568,6 +663,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     }
     int bps = 1;
     if (tma) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tma_fn, MP_THREADS, smem_pass));
+    else if (reg_fn) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reg_fn, MP_THREADS, smem_pass));
     else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, smem_pass));
     bps = std::max(bps, 1);
     const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
@@ -618,6 +714,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
         const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
         for (int c = 0; c < chunk; ++c) {
             if (tma) tma_fn<<<P, MP_THREADS, smem_pass, s>>>(a, map, stages, keep_in_l2);
+            else if (reg_fn) reg_fn<<<P, MP_THREADS, smem_pass, s>>>(a);
             else mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
             g_launches.fetch_add(1, std::memory_order_relaxed);
             if (launched + c == 0) {
