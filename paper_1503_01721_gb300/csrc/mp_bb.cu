@@ -249,13 +249,16 @@ __device__ void bb_step(const MPArgs &a) {
 }
 
 // Per-voxel part of an iteration for voxel i with dose zi: returns g_i, adds F_i to facc.
+// The deviation d = z - T and the active weight are formed in FP32 (FP64 is a
+// small fraction of the FP32 rate on this GPU); the term w d^2 is then formed and
+// accumulated in FP64 from those FP32 values: one multiply and one FMA per voxel.
 __device__ __forceinline__ float voxel_terms(const float *sT, const float *sO, const float *sU, int s, float zi,
                                              double &facc) {
-    const float t = sT[s];
-    const double dz = (double)zi - (double)t;
-    const double ov = dz > 0.0 ? dz : 0.0, un = dz < 0.0 ? -dz : 0.0;
-    facc += (double)sO[s] * ov * ov + (double)sU[s] * un * un;
-    return -2.f * sO[s] * fmaxf(0.f, zi - t) + 2.f * sU[s] * fmaxf(0.f, t - zi);
+    const float d = zi - sT[s];
+    const float w = d > 0.f ? sO[s] : sU[s];
+    const double dd = (double)d;
+    facc = fma((double)w * dd, dd, facc);
+    return -2.f * w * d; // g = -grad F: -2 w+ (z - T) above, +2 w- (T - z) below
 }
 
 // Ends a pass: write this CTA's partials; the last CTA reduces them and steps.
@@ -618,10 +621,9 @@ static size_t reg_smem(int n) {
     return (size_t)nmax * 8 + (size_t)MP_NW * nmax * 4 + (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4;
 }
 
-// Pass kernel: plain-load streaming with register-resident gradient shares (the
-// fastest on GB300 for this access pattern) up to 96 apertures, global loads
-// with per-tile reductions beyond; VMAT_MP_PASS=tma selects the bulk-copy
-// staging variant where DA's alignment allows it.
+// Pass kernel: bulk-copy staging with register-resident gradient shares where
+// DA's alignment allows it and up to 96 apertures (measured fastest), else the
+// plain-load variants; VMAT_MP_PASS=reg|ldg selects those explicitly.
 enum PassKind { PASS_REG, PASS_TMA, PASS_LDG };
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
@@ -639,8 +641,9 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     const bool tma_ok = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (tiled ? tstride % 4 == 0 : ld % 4 == 0) &&
                         n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
     const char *pass_env = getenv("VMAT_MP_PASS");
-    PassKind kind = n_ap <= MP_NMAX ? PASS_REG : PASS_LDG;
-    if (pass_env && strcmp(pass_env, "tma") == 0 && tma_ok) kind = PASS_TMA;
+    PassKind kind = tma_ok ? PASS_TMA : (n_ap <= MP_NMAX ? PASS_REG : PASS_LDG);
+    if (pass_env && strcmp(pass_env, "reg") == 0 && n_ap <= MP_NMAX) kind = PASS_REG;
+    if (pass_env && strcmp(pass_env, "ldg") == 0) kind = PASS_LDG;
     const bool tma = kind == PASS_TMA;
     TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
     RegIterFn reg_fn = kind == PASS_REG ? reg_kernel_for(n_ap) : nullptr;

@@ -49,9 +49,11 @@ __global__ void __launch_bounds__(OBJ_THREADS)
             if (g_scatter) g_scatter[v] = gi;
             else g[i] = gi;
         }
-        const double dz = (double)zi - (double)t;
-        const double over = dz > 0.0 ? dz : 0.0, under = dz < 0.0 ? -dz : 0.0;
-        acc += (double)sO[k] * over * over + (double)sU[k] * under * under;
+        if (F) { // the FP64 objective only when asked for (FP64 is slow on this GPU)
+            const double dz = (double)zi - (double)t;
+            const double dd = dz > 0.0 ? (double)sO[k] : (double)sU[k];
+            acc = fma(dd * dz, dz, acc);
+        }
     }
     if (!F) return;
     const double bs = block_sum_f64(acc, sh);
