@@ -55,9 +55,10 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
                 acc += v;
             }
         }
-        // output: voxel space, compact row space, or the tile-contiguous layout of the
-        // master problem (row r at (r / 256) * tstride + r % 256 from da)
-        const int64_t o = row_ids ? row_ids[row] : (tstride ? (int64_t)(row >> 8) * tstride + (row & 255) : row);
+        // output: voxel space, compact row space, or the master problem's grouped tile
+        // layout (row r at (r / 256) * tstride + (r % 256) * 4 from da, the column's base)
+        const int64_t o =
+            row_ids ? row_ids[row] : (tstride ? (int64_t)(row >> 8) * tstride + ((row & 255) << 2) : row);
         da[o] = acc;
     }
 }

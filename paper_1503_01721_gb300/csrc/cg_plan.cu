@@ -120,11 +120,11 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     cudaStream_t s = as_stream(stream);
     const int32_t V = h.V, J = h.J, K = mlc->K, NR = mlc->n_rows, NA = h.n_active;
     const int32_t bpc = NR * mlc->n_cols;
-    // DA in the tile-contiguous layout: 256-voxel tiles, each holding all n_apertures
-    // columns back to back, so one master-problem tile is one contiguous block
+    // DA in the master problem's grouped tile layout (256-voxel tiles, apertures in
+    // groups of four interleaved per voxel): a tile's first n columns are one block
     const int64_t n_vtiles = ((int64_t)std::max(NA, 1) + 255) / 256;
-    const int64_t ld = n_vtiles * 256;                          // voxel slots
-    const int64_t tstride = (int64_t)std::max(n_apertures, 1) * 256; // floats per tile
+    const int64_t ld = n_vtiles * 256;                              // voxel slots
+    const int64_t tstride = mp_tile_stride(std::max(n_apertures, 1)); // floats per tile
     const int nap_max = std::max(n_apertures, 1);
     const int g256 = std::max(1, ctx->n_sm * 4);
 
@@ -174,6 +174,8 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_CUDA(cudaEventRecord(t0, s));
 
     VMAT_CUDA(cudaMemsetAsync(z_c, 0, (size_t)std::max(NA, 1) * 4, s));
+    // columns not yet generated (and voxel slots past the last one) must read as 0
+    VMAT_CUDA(cudaMemsetAsync(DA, 0, (size_t)n_vtiles * tstride * 4, s));
     VMAT_CUDA(cudaMemsetAsync(g_full, 0, (size_t)V * 4, s));
     VMAT_CUDA(cudaMemsetAsync(occupied, 0, K, s));
     VMAT_CUDA(cudaMemsetAsync(leaves_all, 0, (size_t)K * NR * 4, s));
@@ -248,7 +250,8 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         occ_host[k] = 1;
         // ---- DA (Eq. 5)
         tm.mark(PH_DA);
-        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)t * 256, true, s, tstride));
+        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)(t >> 2) * 1024 + (t & 3), true, s,
+                                    tstride));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
         VMAT_CUDA(cudaMemsetAsync(y + t, 0, 4, s));

@@ -184,35 +184,6 @@ vmat_status scan_counts(const int32_t *in, int64_t *out, int64_t n, cudaStream_t
     return VMAT_OK;
 }
 
-vmat_status make_tensor_map_2d_f32(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
-                                   uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer) {
-    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static EncodeFn encode = nullptr;
-    static std::mutex mu;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!encode) {
-            void *fn = nullptr;
-            cudaDriverEntryPointQueryResult q;
-            VMAT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-            if (q != cudaDriverEntryPointSuccess || !fn)
-                return set_error(VMAT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-            encode = reinterpret_cast<EncodeFn>(fn);
-        }
-    }
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {pitch_bytes};
-    const cuuint32_t box[2] = {box_inner, box_outer};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return set_error(VMAT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return VMAT_OK;
-}
-
 vmat_status validate_mlc(const vmat_mlc *mlc) {
     if (!mlc) return set_error(VMAT_EINVAL, "mlc is NULL");
     if (mlc->K <= 0 || mlc->n_rows <= 0 || mlc->n_cols <= 0 || mlc->n_cols > 1024 || mlc->travel_cols < 0)

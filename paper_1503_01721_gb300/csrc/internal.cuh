@@ -1,7 +1,6 @@
 // Internal declarations shared by the libvmat translation units (host + device helpers).
 #pragma once
 
-#include <cuda.h> // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -130,26 +129,23 @@ vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compa
 vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                            float *g_scatter, double *F, double F_offset, cudaStream_t s);
 
-// compact: write row r of CSR(D) (tstride == 0: at da[r]; else at da[(r / 256) * tstride + r % 256]);
+// compact: write row r of CSR(D) (tstride == 0: at da[r]; else at da[(r / 256) * tstride + (r % 256) * 4],
+// the master problem's grouped tile layout with da pointing at the column's first slot);
 // otherwise write voxel space da[V] (zero where D has no row).
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
                                bool compact, cudaStream_t s, int64_t tstride = 0);
 
 struct BBWork; // defined in mp_bb.cu
-// DA layout: column-major (DA[k * ld + i]) when tstride == 0, else tile-contiguous
-// (DA[(i / 256) * tstride + k * 256 + i % 256], tstride a multiple of 256).
+// DA layout: column-major (DA[k * ld + i]) when tstride == 0 (copied once into the
+// grouped layout), else the grouped tile layout
+// DA[(i / 256) * tstride + (k / 4) * 1024 + (i % 256) * 4 + k % 4], tstride = mp_tile_stride(n_cap).
+int64_t mp_tile_stride(int32_t n_cap);
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);
 
 vmat_status validate_mlc(const vmat_mlc *mlc);
 vmat_status validate_voxels(const vmat_voxels *vox);
-
-// 2-D tiled tensor map over a float32 matrix stored as `outer` rows of `inner`
-// elements with a row pitch of `pitch_bytes` (multiple of 16); boxes of
-// box_inner x box_outer elements; reads past `inner` or `outer` return 0.
-vmat_status make_tensor_map_2d_f32(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
-                                   uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer);
 
 // Exclusive scan of int32 counts into int64 offsets (out has n + 1 entries).
 vmat_status scan_counts(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
@@ -222,17 +218,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-// 2-D tiled bulk tensor copy global -> shared of the box at element (x, y).
-// x * 4 bytes must be a multiple of 16.
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar,
-                                            uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 

@@ -4,14 +4,20 @@
 //
 // The paper runs four steps per iteration on one GPU (aperture gradient, step
 // length with cuBLAS dot products, subspace update, dose update).  Here one
-// kernel does a whole iteration: every CTA streams tiles of DA (256 voxels x
-// n apertures, one bulk copy per column, double-buffered on mbarriers) into
-// shared memory and from each tile computes z = DA y, the objective terms,
-// g = -grad F and the partial G = grad_y F = -DA^T g of its voxels, so DA is
-// read from HBM once per iteration.  The last CTA to finish (a ticket counter)
-// reduces the partials in a fixed order (FP64) and takes the step: the Eq. 9-10
-// freeze, the stopping tests, the BB step length and the projected update.
-// The first iteration's Cauchy step needs DA G and takes two more kernels.
+// kernel does a whole iteration.  DA is kept in a grouped tile layout:
+// 256-voxel tiles, and inside a tile the apertures in groups of four with the
+// four values of a voxel side by side,
+//     DA(i, k) = DA[(i / 256) * tstride + (k / 4) * 1024 + (i % 256) * 4 + k % 4],
+// so the first n columns of a tile are one contiguous block.  Every CTA streams
+// tiles into shared memory with one bulk copy each (several in flight on an
+// mbarrier ring); each thread owns a voxel, reads its four-aperture groups
+// with 128-bit shared loads, forms z = DA y with four independent chains, the
+// objective terms and g = -grad F, and adds DA_ik g_i to its register-resident
+// shares of G = grad_y F = -DA^T g.  DA is read from HBM once per iteration.
+// The last CTA to finish (a ticket counter) reduces the partials in a fixed
+// order (FP64) and takes the step: the Eq. 9-10 freeze, the stopping tests, the
+// BB step length and the projected update.  The first iteration's Cauchy step
+// needs DA G and takes two more kernels.
 //
 // Readings (where the paper is silent): G is the gradient of F, so both BB
 // step lengths are positive and Eq. 9-10 freeze at lo when G > 0 and at hi when
@@ -33,6 +39,7 @@ constexpr int MP_NW = MP_THREADS / 32;
 constexpr int MP_STAGES = 2;
 constexpr int MP_CHUNK = 8; // iterations launched between host polls
 constexpr size_t MP_SMEM_LIMIT = 200 * 1024;
+constexpr int MP_NMAX = 96; // register-resident gradient shares: up to 96 apertures
 
 struct BBState {
     double F_hist[6];
@@ -48,9 +55,8 @@ struct BBState {
 };
 
 struct MPArgs {
-    const float *DA;
-    int64_t ld;      // column-major layout: DA[k * ld + i]
-    int64_t tstride; // tile-contiguous layout when > 0: DA[(i / 256) * tstride + k * 256 + i % 256]
+    const float *DA; // grouped tile layout (see above)
+    int64_t tstride; // floats per 256-voxel tile (a multiple of 1024)
     int32_t V, n;
     const uint8_t *sid;
     const float *T, *wo, *wu;
@@ -72,10 +78,11 @@ struct MPArgs {
 
 __device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
 
-// Offset of DA(voxel i, aperture k) in either layout.
+// Offset of DA(voxel i, aperture k) in the grouped tile layout.
 __device__ __forceinline__ int64_t da_at(const MPArgs &a, int64_t i, int k) {
-    return a.tstride ? (i >> 8) * a.tstride + (int64_t)k * 256 + (i & 255) : (int64_t)k * a.ld + i;
+    return (i >> 8) * a.tstride + (int64_t)(k >> 2) * 1024 + ((i & 255) << 2) + (k & 3);
 }
+
 __device__ __forceinline__ float lo_of(const MPArgs &a, int k) { return a.lo ? a.lo[k] : 0.f; }
 __device__ __forceinline__ float hi_of(const MPArgs &a, int k) { return a.hi ? a.hi[k] : INFINITY; }
 
@@ -287,30 +294,29 @@ __device__ void pass_epilogue(const MPArgs &a, const double *accG, double facc) 
 // G = -DA^T g for all columns in registers (NMAX >= n) across the tiles of its
 // CTA; one block reduction per pass.  Needs DA 16-byte aligned and ld a
 // multiple of 4 (the tensor map's row pitch).
+
+// One BB iteration: tiles of DA (the first n columns of 256 voxels, one block of
+// ceil(n/4) * 4 KB) are bulk-copied into shared memory, `stages` in flight.
+// Each thread owns one voxel of every tile and keeps its share of G for all
+// columns in registers (NMAX >= n) across the tiles of its CTA; one block
+// reduction per pass.  Slots of columns >= n inside the last group hold 0.
 template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS)
-    mp_iter_tma_kernel(MPArgs a, const __grid_constant__ CUtensorMap map, int stages, int keep_in_l2) {
+__global__ void __launch_bounds__(MP_THREADS) mp_iter_tma_kernel(MPArgs a, int stages, int keep_in_l2) {
     if (a.st->done || a.st->need_cauchy) return;
     extern __shared__ __align__(128) unsigned char sm_raw[];
-    // tensor copies need a 128-byte aligned destination; static shared memory of
-    // this kernel may shift the dynamic region, so align explicitly (+128 bytes)
+    // align the staging area explicitly: this kernel's static shared memory may
+    // shift the dynamic region
     unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
-    const int n = a.n;
-    float *DAs = reinterpret_cast<float *>(sm);                        // [stages][n][256]
-    if ((smem_u32(DAs) & 127u) != 0u) { // self-check: never issue a misaligned tensor copy
-        if (threadIdx.x == 0) {
-            atomicOr(a.status, DEV_INDEX);
-            a.st->done = 1;
-        }
-        return;
-    }
-    double *accG = reinterpret_cast<double *>(DAs + (size_t)stages * n * MP_THREADS); // [n]
-    float *wred = reinterpret_cast<float *>(accG + NMAX);              // [MP_NW][NMAX]
-    float *sy = wred + MP_NW * NMAX;                                   // [n]
-    float *sT = sy + ((n + 3) & ~3), *sO = sT + 256, *sU = sO + 256;   // [256] each
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);           // [stages]
+    constexpr int GMAX = NMAX / 4;
+    const int n = a.n, G = (n + 3) >> 2;
+    float *DAs = reinterpret_cast<float *>(sm);                              // [stages][G][256][4]
+    float4 *sy4 = reinterpret_cast<float4 *>(DAs + (size_t)stages * G * 1024); // [GMAX]
+    double *accG = reinterpret_cast<double *>(sy4 + GMAX);                     // [NMAX]
+    float *wred = reinterpret_cast<float *>(accG + NMAX);                      // [MP_NW][NMAX]
+    float *sT = wred + MP_NW * NMAX, *sO = sT + 256, *sU = sO + 256;           // [256] each
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);                   // [stages]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < n; k += MP_THREADS) sy[k] = a.y[k];
+    for (int k = tid; k < 4 * GMAX; k += MP_THREADS) reinterpret_cast<float *>(sy4)[k] = k < n ? a.y[k] : 0.f;
     for (int k = tid; k < a.n_struct; k += MP_THREADS) {
         sT[k] = a.T[k];
         sO[k] = a.wo[k];
@@ -323,14 +329,10 @@ __global__ void __launch_bounds__(MP_THREADS)
     __syncthreads();
     // DA is read again by the next iteration: keep it in L2 when it fits there
     const uint64_t pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
+    const uint32_t bytes = (uint32_t)G * 4096u;
     auto issue = [&](int32_t tile, int s) {
-        const uint32_t bytes = (uint32_t)(MP_THREADS * 4) * (uint32_t)n;
         mbar_arrive_expect_tx(&bars[s], bytes);
-        float *dst = DAs + (size_t)s * n * MP_THREADS;
-        if (a.tstride) // tile-contiguous layout: the tile's n columns are one block
-            bulk_g2s(dst, a.DA + (int64_t)tile * a.tstride, bytes, &bars[s], pol);
-        else
-            tma_load_2d(dst, &map, tile * MP_THREADS, 0, &bars[s], pol);
+        bulk_g2s(DAs + (size_t)s * G * 1024, a.DA + (int64_t)tile * a.tstride, bytes, &bars[s], pol);
     };
     if (tid == 0)
         for (int s = 0; s < stages; ++s) {
@@ -350,24 +352,35 @@ __global__ void __launch_bounds__(MP_THREADS)
             timed_out = true;
             break;
         }
-        const float *T = DAs + (size_t)s * n * MP_THREADS + tid;
+        const float4 *T4 = reinterpret_cast<const float4 *>(DAs + (size_t)s * G * 1024) + tid; // group g at [g * 256]
         const int64_t i = (int64_t)tile * MP_THREADS + tid;
         if (i < a.V) {
-            float zi = 0.f;
+            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-            for (int k = 0; k < NMAX; ++k)
-                if (k < n) zi = fmaf(T[k * MP_THREADS], sy[k], zi);
+            for (int g = 0; g < GMAX; ++g)
+                if (g < G) {
+                    const float4 v = T4[g * 256], w = sy4[g];
+                    z0 = fmaf(v.x, w.x, z0);
+                    z1 = fmaf(v.y, w.y, z1);
+                    z2 = fmaf(v.z, w.z, z2);
+                    z3 = fmaf(v.w, w.w, z3);
+                }
+            const float zi = (z0 + z1) + (z2 + z3);
             a.z[i] = zi;
             const float gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
 #pragma unroll
-            for (int k = 0; k < NMAX; ++k)
-                if (k < n) gacc[k] = fmaf(T[k * MP_THREADS], gi, gacc[k]);
+            for (int g = 0; g < GMAX; ++g)
+                if (g < G) {
+                    const float4 v = T4[g * 256];
+                    gacc[4 * g + 0] = fmaf(v.x, gi, gacc[4 * g + 0]);
+                    gacc[4 * g + 1] = fmaf(v.y, gi, gacc[4 * g + 1]);
+                    gacc[4 * g + 2] = fmaf(v.z, gi, gacc[4 * g + 2]);
+                    gacc[4 * g + 3] = fmaf(v.w, gi, gacc[4 * g + 3]);
+                }
         }
-        __syncthreads(); // stage s consumed
+        __syncthreads(); // every read of stage s is done before its next copy
         if (tid == 0) {
             const int32_t nt = tile + stages * gridDim.x;
-            // the barrier above orders every thread's reads of stage s before the copy
-            // that overwrites it (no proxy fence: it would also wait for the other stages)
             if (nt < a.n_tiles) issue(nt, s);
         }
     }
@@ -389,69 +402,6 @@ __global__ void __launch_bounds__(MP_THREADS)
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
         if (k < n) {
-            float v = gacc[k];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-            if (lane == 0) wred[wid * NMAX + k] = v;
-        }
-    }
-    __syncthreads();
-    for (int k = tid; k < n; k += MP_THREADS) {
-        double s = 0.0;
-        for (int w = 0; w < MP_NW; ++w) s += (double)wred[w * NMAX + k];
-        accG[k] = s;
-    }
-    __syncthreads();
-    pass_epilogue(a, accG, facc);
-}
-
-// One BB iteration streaming DA with plain loads: each thread owns one voxel of
-// each 256-voxel tile, issues its n column loads before the dose FMA chain,
-// then re-reads them (L1 hits) to add DA_ik g_i to its register-resident shares
-// of G for all columns (NMAX >= n).  No shared-memory staging and no barrier
-// per tile; one block reduction per pass.
-template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS) mp_iter_reg_kernel(MPArgs a) {
-    if (a.st->done || a.st->need_cauchy) return;
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int n = a.n;
-    double *accG = reinterpret_cast<double *>(sm);                    // [NMAX]
-    float *wred = reinterpret_cast<float *>(accG + NMAX);             // [MP_NW][NMAX]
-    float *sy = wred + MP_NW * NMAX;                                  // [n]
-    float *sT = sy + ((n + 3) & ~3), *sO = sT + 256, *sU = sO + 256;  // [256] each
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < n; k += MP_THREADS) sy[k] = a.y[k];
-    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
-        sT[k] = a.T[k];
-        sO[k] = a.wo[k];
-        sU[k] = a.wu[k];
-    }
-    __syncthreads();
-    float gacc[NMAX];
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
-    double facc = 0.0;
-    for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const int64_t i = (int64_t)tile * MP_THREADS + tid;
-        if (i >= a.V) continue;
-        const float *col0 = a.DA + da_at(a, i, 0);
-        const int64_t kstride = a.tstride ? 256 : a.ld;
-        float v[NMAX];
-#pragma unroll
-        for (int k = 0; k < NMAX; ++k) v[k] = k < n ? __ldg(col0 + k * kstride) : 0.f;
-        float zi = 0.f;
-#pragma unroll
-        for (int k = 0; k < NMAX; ++k)
-            if (k < n) zi = fmaf(v[k], sy[k], zi);
-        a.z[i] = zi;
-        const float gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
-#pragma unroll
-        for (int k = 0; k < NMAX; ++k)
-            if (k < n) gacc[k] = fmaf(v[k], gi, gacc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-        if (k < n) {
             float x = gacc[k];
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
@@ -460,15 +410,16 @@ __global__ void __launch_bounds__(MP_THREADS) mp_iter_reg_kernel(MPArgs a) {
     }
     __syncthreads();
     for (int k = tid; k < n; k += MP_THREADS) {
-        double s = 0.0;
-        for (int w = 0; w < MP_NW; ++w) s += (double)wred[w * NMAX + k];
-        accG[k] = s;
+        double sum = 0.0;
+        for (int w = 0; w < MP_NW; ++w) sum += (double)wred[w * NMAX + k];
+        accG[k] = sum;
     }
     __syncthreads();
     pass_epilogue(a, accG, facc);
 }
 
-// The same iteration reading DA straight from global memory (any alignment of DA and ld).
+// The same iteration reading DA from global memory with per-tile reductions
+// (more apertures than the register-resident shares hold).
 __global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
     if (a.st->done || a.st->need_cauchy) return;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -562,23 +513,35 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a, in
     if (threadIdx.x == 0) st->t = 1;
 }
 
-constexpr int MP_NMAX = 96; // register-resident gradient shares: up to 96 apertures
+
+// Grouped tile layout from a column-major matrix (DA[k * ld + i]); padding 0.
+__global__ void to_grouped_tiles(const float *src, int64_t ld, int32_t V, int32_t n, int64_t tstride,
+                                 int32_t n_tiles, float *dst) {
+    const int64_t total = (int64_t)n_tiles * tstride;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = o / tstride, r = o % tstride;
+        const int k = (int)((r >> 10) << 2) + (int)(r & 3);
+        const int64_t i = tile * 256 + ((r & 1023) >> 2);
+        dst[o] = (k < n && i < V) ? src[(int64_t)k * ld + i] : 0.f;
+    }
+}
 
 static int tma_nmax(int n) { return ((n + 7) / 8) * 8; }
-// Tiles in flight per CTA (n KB each): ~100 KB so that two CTAs share an SM while
+// Tiles in flight per CTA (~n KB each): ~100 KB so that two CTAs share an SM while
 // that still allows 3 stages, else ~190 KB for one CTA; at least double-buffered.
 static int tma_stages(int n) {
-    n = std::max(n, 1);
-    const int budget = 3 * n <= 100 ? 100 : 190;
-    return std::max(MP_STAGES, std::min(6, budget / n));
+    const int kb = 4 * ((std::max(n, 1) + 3) / 4);
+    const int budget = 3 * kb <= 100 ? 100 : 190;
+    return std::max(MP_STAGES, std::min(6, budget / kb));
 }
 static size_t tma_smem(int n, int stages) {
-    const int nmax = tma_nmax(n);
-    return 128 /* alignment slack */ + (size_t)stages * n * MP_THREADS * 4 + (size_t)nmax * 8 +
-           (size_t)MP_NW * nmax * 4 + (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4 + (size_t)stages * 8;
+    const int nmax = tma_nmax(n), G = (n + 3) / 4;
+    return 128 /* alignment slack */ + (size_t)stages * G * 4096 + (size_t)(nmax / 4) * 16 + (size_t)nmax * 8 +
+           (size_t)MP_NW * nmax * 4 + 3 * 256 * 4 + (size_t)stages * 8;
 }
 
-using TmaIterFn = void (*)(MPArgs, const CUtensorMap, int, int);
+using TmaIterFn = void (*)(MPArgs, int, int);
 static TmaIterFn tma_kernel_for(int n) {
     switch ((n + 7) / 8) {
     case 1: return mp_iter_tma_kernel<8>;
@@ -598,33 +561,7 @@ static TmaIterFn tma_kernel_for(int n) {
 }
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
-using RegIterFn = void (*)(MPArgs);
-static RegIterFn reg_kernel_for(int n) {
-    switch ((n + 7) / 8) {
-    case 1: return mp_iter_reg_kernel<8>;
-    case 2: return mp_iter_reg_kernel<16>;
-    case 3: return mp_iter_reg_kernel<24>;
-    case 4: return mp_iter_reg_kernel<32>;
-    case 5: return mp_iter_reg_kernel<40>;
-    case 6: return mp_iter_reg_kernel<48>;
-    case 7: return mp_iter_reg_kernel<56>;
-    case 8: return mp_iter_reg_kernel<64>;
-    case 9: return mp_iter_reg_kernel<72>;
-    case 10: return mp_iter_reg_kernel<80>;
-    case 11: return mp_iter_reg_kernel<88>;
-    case 12: return mp_iter_reg_kernel<96>;
-    default: return nullptr;
-    }
-}
-static size_t reg_smem(int n) {
-    const int nmax = tma_nmax(n);
-    return (size_t)nmax * 8 + (size_t)MP_NW * nmax * 4 + (size_t)((n + 3) & ~3) * 4 + 3 * 256 * 4;
-}
-
-// Pass kernel: bulk-copy staging with register-resident gradient shares where
-// DA's alignment allows it and up to 96 apertures (measured fastest), else the
-// plain-load variants; VMAT_MP_PASS=reg|ldg selects those explicitly.
-enum PassKind { PASS_REG, PASS_TMA, PASS_LDG };
+int64_t mp_tile_stride(int32_t n_cap) { return (int64_t)((n_cap + 3) / 4) * 1024; }
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
@@ -635,25 +572,25 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     if (opts_in) opts = *opts_in;
     if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
     if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
+    const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
+
+    // a column-major input is copied once into the grouped tile layout
+    Scratch conv;
+    if (tstride == 0) {
+        tstride = mp_tile_stride(n_ap);
+        VMAT_TRY(conv.alloc((size_t)n_tiles * tstride * sizeof(float), s));
+        const int64_t total = (int64_t)n_tiles * tstride;
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
+        to_grouped_tiles<<<g, 256, 0, s>>>(DA, ld, V, n_ap, tstride, n_tiles, static_cast<float *>(conv.ptr));
+        VMAT_LAUNCH_CHECK();
+        DA = static_cast<const float *>(conv.ptr);
+    }
 
     const int stages = tma_stages(n_ap);
-    const bool tiled = tstride > 0;
-    const bool tma_ok = (reinterpret_cast<uintptr_t>(DA) % 16 == 0) && (tiled ? tstride % 4 == 0 : ld % 4 == 0) &&
-                        n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT;
-    const char *pass_env = getenv("VMAT_MP_PASS");
-    PassKind kind = tma_ok ? PASS_TMA : (n_ap <= MP_NMAX ? PASS_REG : PASS_LDG);
-    if (pass_env && strcmp(pass_env, "reg") == 0 && n_ap <= MP_NMAX) kind = PASS_REG;
-    if (pass_env && strcmp(pass_env, "ldg") == 0) kind = PASS_LDG;
-    const bool tma = kind == PASS_TMA;
+    const bool tma = n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT && tstride % 1024 == 0;
     TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
-    RegIterFn reg_fn = kind == PASS_REG ? reg_kernel_for(n_ap) : nullptr;
-    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : (kind == PASS_REG ? reg_smem(n_ap) : ldg_smem(n_ap));
+    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : ldg_smem(n_ap);
     const int keep_in_l2 = (double)n_ap * (double)V * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
-    CUtensorMap map;
-    memset(&map, 0, sizeof(map));
-    if (tma && !tiled) // rows = apertures (pitch ld floats), columns = voxels; box = 256 voxels x all apertures
-        VMAT_TRY(make_tensor_map_2d_f32(&map, DA, (uint64_t)V, (uint64_t)n_ap, (uint64_t)ld * 4, MP_THREADS,
-                                        (uint32_t)n_ap));
     static bool attr = false;
     if (!attr) {
         for (int q = 1; q <= MP_NMAX / 8; ++q)
@@ -666,10 +603,8 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     }
     int bps = 1;
     if (tma) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tma_fn, MP_THREADS, smem_pass));
-    else if (reg_fn) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reg_fn, MP_THREADS, smem_pass));
     else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, smem_pass));
     bps = std::max(bps, 1);
-    const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
     const int P = std::max(1, std::min<int>(n_tiles, ctx->n_sm * bps));
     const int Pc = std::max(1, std::min<int>(n_tiles, ctx->n_sm * 4));
 
@@ -687,8 +622,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.cpart = a.part + (size_t)P * (n_ap + 1);
     a.yprev = reinterpret_cast<float *>(a.cpart + Pc);
     a.DA = DA;
-    a.ld = ld;
-    a.tstride = tiled ? tstride : 0;
+    a.tstride = tstride;
     a.V = V;
     a.n = n_ap;
     a.sid = struct_id;
@@ -716,8 +650,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     while (launched < opts.max_iter) {
         const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
         for (int c = 0; c < chunk; ++c) {
-            if (tma) tma_fn<<<P, MP_THREADS, smem_pass, s>>>(a, map, stages, keep_in_l2);
-            else if (reg_fn) reg_fn<<<P, MP_THREADS, smem_pass, s>>>(a);
+            if (tma) tma_fn<<<P, MP_THREADS, smem_pass, s>>>(a, stages, keep_in_l2);
             else mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
             g_launches.fetch_add(1, std::memory_order_relaxed);
             if (launched + c == 0) {
