@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local):
 
     # resident DDC
     h = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg)
+    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0)
     info = api.ddc_info(h)
     log(f"[rank {rank}] build {info['build_ms']:.1f} ms, active voxels {info['n_active_vox']}")
 
@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         h2 = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-        api.ddc_build(h2, args.dtype, tile_cfg=args.tile_cfg)
+        api.ddc_build(h2, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0)
         F2, st2 = api.cg_plan(h2, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose_h)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t_a)
