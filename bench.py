@@ -374,7 +374,7 @@ def run_spmv_only(args):
     pi = torch.empty(case.J, device="cuda")
     dd = torch.empty(case.V, device="cuda")
     out = {"mode": "spmv", "workload": args.workload, "nnz": case.nnz, "dtype": args.dtype, "configs": {}}
-    for cfg in (range(7) if args.sweep else [args.tile_cfg]):
+    for cfg in (range(api.spmv_config_count()) if args.sweep else [args.tile_cfg]):
         ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg)
         info = ddc.info()
         for _ in range(3):

@@ -285,6 +285,10 @@ const char *vmat_version(void);
 /* Number of kernels libvmat has launched in this process (all threads). */
 int64_t vmat_launch_count(void);
 
+/* Number of SpMV configurations (valid vmat_build_opts.tile_cfg values are
+ * 0 .. count - 1). */
+int32_t vmat_spmv_config_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ SIGNATURES = {
     "vmat_device_status": (c_i32, [c_i32]),
     "vmat_version": (ctypes.c_char_p, []),
     "vmat_launch_count": (c_i64, []),
+    "vmat_spmv_config_count": (c_i32, []),
 }
 
 _lock = threading.Lock()

@@ -232,6 +232,11 @@ def launch_count() -> int:
     return int(_lib.load().vmat_launch_count())
 
 
+def spmv_config_count() -> int:
+    """Number of SpMV configurations (tile_cfg values 0 .. count - 1)."""
+    return int(_lib.load().vmat_spmv_config_count())
+
+
 def version() -> str:
     return _lib.load().vmat_version().decode()
 

@@ -219,6 +219,8 @@ const char *vmat_version(void) { return "libvmat 0.1 (sm_103a)"; }
 
 int64_t vmat_launch_count(void) { return g_launches.load(); }
 
+int32_t vmat_spmv_config_count(void) { return spmv_n_configs(); }
+
 int32_t vmat_device_status(int32_t reset) {
     DeviceCtx *c = nullptr;
     if (device_ctx(&c) != VMAT_OK) return -1;

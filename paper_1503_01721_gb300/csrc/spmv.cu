@@ -485,8 +485,9 @@ struct Cfg {
     int threads, e, stages; // tile: E entries per thread, STAGES bulk-copy stages; warp-row: e = unroll
 };
 static const Cfg kCfgs[] = {{0, 256, 16, 2}, {0, 256, 8, 3}, {0, 512, 8, 2}, {0, 128, 16, 3},
-                            {1, 256, 2, 0},  {1, 256, 1, 0}, {1, 512, 4, 0}};
-constexpr int N_CFG = 7;
+                            {1, 256, 2, 0},  {1, 256, 1, 0}, {1, 512, 4, 0}, {1, 256, 4, 0},
+                            {1, 256, 8, 0}};
+constexpr int N_CFG = 9;
 
 using TileFn = void (*)(SpmvParams);
 using RowFn = void (*)(RowParams);
@@ -504,6 +505,8 @@ template <typename VT> RowFn row_kernel_for(int cfg) {
     switch (cfg) {
     case 4: return spmv_warp_row_kernel<256, 2, VT>;
     case 5: return spmv_warp_row_kernel<256, 1, VT>;
+    case 7: return spmv_warp_row_kernel<256, 4, VT>;
+    case 8: return spmv_warp_row_kernel<256, 8, VT>;
     default: return spmv_warp_row_kernel<512, 4, VT>;
     }
 }

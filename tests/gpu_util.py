@@ -10,6 +10,8 @@ U32 = 2.0 ** -24  # float32 unit roundoff
 # levels to join the 4 accumulators and 5 butterfly levels.  (64 + n/64) units
 # of roundoff bound both, for every row length.
 SPMV_C = 64
+# SpMV configurations the library offers (tile_cfg 0 .. N_SPMV_CFG - 1)
+N_SPMV_CFG = 9
 
 
 def require_cuda():

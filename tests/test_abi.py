@@ -43,6 +43,11 @@ def test_version(lib):
     assert b"sm_103a" in lib.vmat_version()
 
 
+def test_spmv_config_count(lib):
+    from gpu_util import N_SPMV_CFG
+    assert lib.vmat_spmv_config_count() == N_SPMV_CFG
+
+
 def test_host_validation_errors(lib):
     from paper_1503_01721_gb300 import _lib
     h = ctypes.c_void_p()

@@ -1,18 +1,26 @@
 """Precision form: DDC values stored as BF16, or FP8 E4M3 with per-beamlet
-power-of-two scales, FP32 accumulation, FP64 step lengths and objective.
+power-of-two scales; FP32 accumulation.
 
-The plan objective of the lower-precision DDC must stay within 0.5% of the
-FP64 oracle's plan on the float32 matrix, and the final dose (recomputed in
-FP32 from the stored values) is reported against both the FP64 oracle on the
-float32 values (total error) and on the dequantised values (accumulation only).
+Parity: a low-precision plan is the FP64 oracle's plan on the dequantised
+matrix (the stored values read back as float64): same aperture sequence up to
+near ties, objective within 1e-4.  The final dose is D_q (A y) in FP32 and
+matches the FP64 product of the dequantised matrix to accumulation error; its
+total error against the float32 matrix is bounded by the format's relative
+precision (2^-8 for BF16, 2^-4 for E4M3).
+
+Distance to the FP32 plan (the oracle on the float32 values): BF16 stays within
+0.5%.  E4M3's 3-bit mantissa moves the plan objective by about 1% on the
+40^3 case (the oracle alone, run on the dequantised matrix, gives +0.93%,
+and +0.65% when its plan is scored on the float32 matrix); the test bounds it
+by 1.5%.
 """
 import numpy as np
 import pytest
-import torch
 
 import oracle
 import synth
-from gpu_util import host, make_ddc, require_cuda, spmv_bound
+from gpu_util import make_ddc, require_cuda, spmv_bound
+from test_gpu_cg import TIGHT, gpu_plan, near_tie_at
 
 pytestmark = pytest.mark.gpu
 
@@ -24,30 +32,42 @@ def _cuda():
     __graft_entry__.build()
 
 
+_REF = {}
+
+
+def _oracle_plan(c, n, dtype):
+    key = (c.name, n, dtype)
+    if key not in _REF:
+        v = c.val if dtype == "f32" else oracle.quantize_ddc(c.J, c.blt, c.val, dtype)[0]
+        D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, v)
+        _REF[key] = (D, oracle.cg_plan(D, c.mlc, c.structs, n, oracle.BBOptions(**TIGHT)))
+    return _REF[key]
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-def test_low_precision_plan_objective(dtype):
-    from paper_1503_01721_gb300 import api
+def test_low_precision_plan(dtype):
     c = synth.make_case("cfg1", seed=0)
     n = 20
+    D, ref32 = _oracle_plan(c, n, "f32")
+    Dq, refq = _oracle_plan(c, n, dtype)
     ddc = make_ddc(c, dtype=dtype)
-    vox = api.VoxelParams.from_numpy(c.structs)
-    cps = torch.empty(n, dtype=torch.int32)
-    lv = torch.empty(n * c.mlc.n_rows * 2, dtype=torch.int16)
-    y = torch.empty(n, dtype=torch.float32)
-    dose = torch.empty(c.V, device="cuda")
-    F, st = api.cg_plan(ddc.h, c.mlc, vox, n, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
-    m = st["n_apertures"]
-    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
-    ref = oracle.cg_plan(D, c.mlc, c.structs, n)
-    assert abs(F - ref.F) <= 5e-3 * ref.F, f"{dtype} plan F {F} vs FP64 oracle {ref.F}"
-    # the final dose is D_q (A y) in FP32: exact to accumulation error on the stored values
-    x = oracle.aperture_fluence(c.mlc, cps.numpy()[:m], lv.numpy().reshape(n, -1, 2)[:m], y.numpy()[:m])
-    vq, _ = oracle.quantize_ddc(c.J, c.blt, c.val, dtype)
-    Dq = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, vq)
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, n, TIGHT)
+    assert st["n_apertures"] == n
+    # parity with the oracle on the dequantised matrix
+    if list(cps) == refq.cps:
+        assert abs(F - refq.F) <= 1e-4 * refq.F
+    else:
+        t = next(i for i, (a, b) in enumerate(zip(list(cps), refq.cps)) if a != b)
+        assert near_tie_at(ddc, c, Dq, t, cps[t], TIGHT), \
+            f"aperture sequence differs at step {t}: gpu {list(cps)} oracle {refq.cps}"
+    # the stated distance to the FP32 plan
+    assert abs(F - ref32.F) <= {"bf16": 5e-3, "fp8": 1.5e-2}[dtype] * ref32.F, \
+        f"{dtype} plan F {F} vs FP32-matrix oracle {ref32.F}"
+    # final dose: accumulation error on the stored values, and total error of the format
+    x = oracle.aperture_fluence(c.mlc, cps, lv, y)
     d_q = oracle.dose_forward(Dq, x)
     lens = np.bincount(c.vox, minlength=c.V)
-    assert np.all(np.abs(host(dose) - d_q) <= spmv_bound(abs(Dq) @ np.abs(x), lens))
-    # total error of the stored format against the float32 matrix
+    assert np.all(np.abs(dose - d_q) <= spmv_bound(abs(Dq) @ np.abs(x), lens))
     d_ref = oracle.dose_forward(D, x)
-    rel = np.max(np.abs(host(dose) - d_ref)) / np.max(np.abs(d_ref))
-    assert rel <= {"bf16": 2.0 ** -8, "fp8": 2.0 ** -4}[dtype] + 1e-5
+    rel = np.max(np.abs(dose - d_ref)) / np.max(np.abs(d_ref))
+    assert rel <= {"bf16": 2.0 ** -8, "fp8": 2.0 ** -4}[dtype]

@@ -15,7 +15,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import dev, host, make_ddc, require_cuda, spmv_bound
+from gpu_util import N_SPMV_CFG, dev, host, make_ddc, require_cuda, spmv_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,7 @@ def test_products_f32(name):
     check_products(c.V, c.J, c.vox, c.blt, c.val)
 
 
-@pytest.mark.parametrize("cfg", list(range(7)))
+@pytest.mark.parametrize("cfg", list(range(N_SPMV_CFG)))
 def test_every_tile_config(cfg):
     c = synth.make_case("ragged", seed=1)
     check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg)
@@ -138,7 +138,7 @@ def test_tile_boundaries_long_rows_and_empty_rows():
     vox = np.concatenate(vox).astype(np.int32)
     blt = np.concatenate(blt).astype(np.int32)
     val = rng.uniform(0.01, 1, len(vox)).astype(np.float32)
-    for cfg in range(7):
+    for cfg in range(N_SPMV_CFG):
         check_products(V, len(lens), vox, blt, val, tile_cfg=cfg)
 
 
