@@ -30,7 +30,7 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
                                      const void *__restrict__ val, vmat_dtype dt, const float *__restrict__ scale,
                                      int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp, int32_t n_rrows,
                                      int32_t n_cols, const int16_t *__restrict__ leaves, float *__restrict__ da,
-                                     int64_t tstride) {
+                                     int64_t wstride) {
     extern __shared__ int16_t sl[]; // [n_rrows][2]
     for (int i = threadIdx.x; i < 2 * n_rrows; i += blockDim.x) sl[i] = leaves[i];
     __syncthreads();
@@ -55,16 +55,16 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
                 acc += v;
             }
         }
-        // output: voxel space, compact row space, or the master problem's grouped tile
-        // layout (row r at (r / 256) * tstride + (r % 256) * 4 from da, the column's base)
+        // output: voxel space, compact row space, or the master problem's warp-tile
+        // layout (row r at (r / 32) * wstride + (r % 32) * 4 from da, the column's base)
         const int64_t o =
-            row_ids ? row_ids[row] : (tstride ? (int64_t)(row >> 8) * tstride + ((row & 255) << 2) : row);
+            row_ids ? row_ids[row] : (wstride ? (int64_t)(row >> 5) * wstride + ((row & 31) << 2) : row);
         da[o] = acc;
     }
 }
 
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
-                               bool compact, cudaStream_t s, int64_t tstride) {
+                               bool compact, cudaStream_t s, int64_t wstride) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     if (!compact) VMAT_CUDA(cudaMemsetAsync(da, 0, (size_t)h.V * 4, s));
@@ -73,7 +73,7 @@ vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, co
     const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
     aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
         h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n,
-        compact ? nullptr : h.D.row_ids, cp, mlc->n_rows, mlc->n_cols, leaves, da, compact ? tstride : 0);
+        compact ? nullptr : h.D.row_ids, cp, mlc->n_rows, mlc->n_cols, leaves, da, compact ? wstride : 0);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

@@ -120,11 +120,11 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     cudaStream_t s = as_stream(stream);
     const int32_t V = h.V, J = h.J, K = mlc->K, NR = mlc->n_rows, NA = h.n_active;
     const int32_t bpc = NR * mlc->n_cols;
-    // DA in the master problem's grouped tile layout (256-voxel tiles, apertures in
-    // groups of four interleaved per voxel): a tile's first n columns are one block
-    const int64_t n_vtiles = ((int64_t)std::max(NA, 1) + 255) / 256;
-    const int64_t ld = n_vtiles * 256;                              // voxel slots
-    const int64_t tstride = mp_tile_stride(std::max(n_apertures, 1)); // floats per tile
+    // DA in the master problem's warp-tile layout (32-voxel tiles: a label head, then
+    // the apertures in groups of four interleaved per voxel)
+    const int64_t n_wtiles = ((int64_t)std::max(NA, 1) + 31) / 32;
+    const int64_t ld = n_wtiles * 32;                                  // voxel slots
+    const int64_t wstride = mp_wtile_stride(std::max(n_apertures, 1)); // floats per warp tile
     const int nap_max = std::max(n_apertures, 1);
     const int g256 = std::max(1, ctx->n_sm * 4);
 
@@ -138,7 +138,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&z_c, std::max(NA, 1)));
     VMAT_TRY(ar.get(&g_full, V));
     VMAT_TRY(ar.get(&pi, J));
-    VMAT_TRY(ar.get(&DA, (size_t)n_vtiles * tstride));
+    VMAT_TRY(ar.get(&DA, (size_t)n_wtiles * wstride));
     VMAT_TRY(ar.get(&y, nap_max));
     VMAT_TRY(ar.get(&x, J));
     VMAT_TRY(ar.get(&dose, V));
@@ -175,7 +175,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
 
     VMAT_CUDA(cudaMemsetAsync(z_c, 0, (size_t)std::max(NA, 1) * 4, s));
     // columns not yet generated (and voxel slots past the last one) must read as 0
-    VMAT_CUDA(cudaMemsetAsync(DA, 0, (size_t)n_vtiles * tstride * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(DA, 0, (size_t)n_wtiles * wstride * 4, s));
     VMAT_CUDA(cudaMemsetAsync(g_full, 0, (size_t)V * 4, s));
     VMAT_CUDA(cudaMemsetAsync(occupied, 0, K, s));
     VMAT_CUDA(cudaMemsetAsync(leaves_all, 0, (size_t)K * NR * 4, s));
@@ -187,6 +187,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     if (NA > 0) {
         gather_u8<<<std::max(1, std::min(g256, (NA + 255) / 256)), 256, 0, s>>>(vox->struct_id, h.act_vox, NA, sid_c);
         VMAT_LAUNCH_CHECK();
+        VMAT_TRY(mp_write_labels(sid_c, NA, wstride, DA, s));
     }
     VMAT_TRY(inactive_objective(h, vox, F0, s));
     double F_offset = 0.0;
@@ -250,14 +251,14 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         occ_host[k] = 1;
         // ---- DA (Eq. 5)
         tm.mark(PH_DA);
-        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + (size_t)(t >> 2) * 1024 + (t & 3), true, s,
-                                    tstride));
+        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + 32 + (size_t)(t >> 2) * 128 + (t & 3), true, s,
+                                    wstride));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
         VMAT_CUDA(cudaMemsetAsync(y + t, 0, 4, s));
         vmat_bb_report rep;
         if (NA > 0) {
-            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, tstride, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
+            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
                                 &rep, s));
             bb_total += rep.iters;
         }

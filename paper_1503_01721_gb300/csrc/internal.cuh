@@ -129,19 +129,21 @@ vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compa
 vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                            float *g_scatter, double *F, double F_offset, cudaStream_t s);
 
-// compact: write row r of CSR(D) (tstride == 0: at da[r]; else at da[(r / 256) * tstride + (r % 256) * 4],
-// the master problem's grouped tile layout with da pointing at the column's first slot);
+// compact: write row r of CSR(D) (wstride == 0: at da[r]; else at da[(r / 32) * wstride + (r % 32) * 4],
+// the master problem's warp-tile layout with da pointing at the column's first slot);
 // otherwise write voxel space da[V] (zero where D has no row).
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
-                               bool compact, cudaStream_t s, int64_t tstride = 0);
+                               bool compact, cudaStream_t s, int64_t wstride = 0);
 
 struct BBWork; // defined in mp_bb.cu
-// DA layout: column-major (DA[k * ld + i]) when tstride == 0 (copied once into the
-// grouped layout), else the grouped tile layout
-// DA[(i / 256) * tstride + (k / 4) * 1024 + (i % 256) * 4 + k % 4], tstride = mp_tile_stride(n_cap).
-int64_t mp_tile_stride(int32_t n_cap);
+// DA layout: column-major (DA[k * ld + i]) when wstride == 0 (copied once, with the
+// labels struct_id, into the warp-tile layout), else the warp-tile layout
+// DA[(i / 32) * wstride + 32 + (k / 4) * 128 + (i % 32) * 4 + k % 4], wstride = mp_wtile_stride(n_cap),
+// whose first 32 bytes of every 32-voxel tile hold the tile's labels (mp_write_labels).
+int64_t mp_wtile_stride(int32_t n_cap);
+vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, float *DA, cudaStream_t s);
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
-                       int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);
 
 vmat_status validate_mlc(const vmat_mlc *mlc);

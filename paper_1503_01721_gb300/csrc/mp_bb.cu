@@ -4,20 +4,25 @@
 //
 // The paper runs four steps per iteration on one GPU (aperture gradient, step
 // length with cuBLAS dot products, subspace update, dose update).  Here one
-// kernel does a whole iteration.  DA is kept in a grouped tile layout:
-// 256-voxel tiles, and inside a tile the apertures in groups of four with the
-// four values of a voxel side by side,
-//     DA(i, k) = DA[(i / 256) * tstride + (k / 4) * 1024 + (i % 256) * 4 + k % 4],
-// so the first n columns of a tile are one contiguous block.  Every CTA streams
-// tiles into shared memory with one bulk copy each (several in flight on an
-// mbarrier ring); each thread owns a voxel, reads its four-aperture groups
-// with 128-bit shared loads, forms z = DA y with four independent chains, the
-// objective terms and g = -grad F, and adds DA_ik g_i to its register-resident
-// shares of G = grad_y F = -DA^T g.  DA is read from HBM once per iteration.
-// The last CTA to finish (a ticket counter) reduces the partials in a fixed
-// order (FP64) and takes the step: the Eq. 9-10 freeze, the stopping tests, the
-// BB step length and the projected update.  The first iteration's Cauchy step
-// needs DA G and takes two more kernels.
+// kernel does a whole iteration.  DA is kept in a warp-tile layout: blocks of
+// 32 voxels, each block a 128-byte head holding the 32 voxels' structure
+// labels, then the apertures in groups of four with the four values of a voxel
+// side by side,
+//     DA(i, k) = DA[(i / 32) * wstride + 32 + (k / 4) * 128 + (i % 32) * 4 + k % 4],
+// so the labels and the first n columns of a block are one contiguous run of
+// 128 + 512 ceil(n / 4) bytes.  Every warp streams its own blocks into shared
+// memory with one bulk copy each (several in flight on the warp's own mbarrier
+// ring; no CTA-wide barrier in the loop); each lane owns a voxel, reads its
+// four-aperture groups with 128-bit shared loads, forms z = DA y with four
+// independent chains, the objective term and g = -grad F, and adds DA_ik g_i
+// to its register-resident shares of G = grad_y F = -DA^T g.  DA is read from
+// HBM once per iteration.  Objective terms w d^2 are formed in FP32 and summed
+// per lane with compensation (Kahan), then in FP64 across lanes and CTAs: the
+// voxel loop runs no FP64 instruction (FP64 issues at a small fraction of the
+// FP32 rate on this GPU).  The last CTA to finish (a ticket counter) reduces
+// the partials in a fixed order (FP64) and takes the step: the Eq. 9-10 freeze,
+// the stopping tests, the BB step length and the projected update.  The first
+// iteration's Cauchy step needs DA G and takes two more kernels.
 //
 // Readings (where the paper is silent): G is the gradient of F, so both BB
 // step lengths are positive and Eq. 9-10 freeze at lo when G > 0 and at hi when
@@ -34,11 +39,12 @@
 
 namespace vmat {
 
-constexpr int MP_THREADS = 256; // = voxels per DA tile
+constexpr int MP_THREADS = 256; // voxels per tile of the fallback and Cauchy kernels
 constexpr int MP_NW = MP_THREADS / 32;
-constexpr int MP_STAGES = 2;
-constexpr int MP_CHUNK = 8; // iterations launched between host polls
-constexpr size_t MP_SMEM_LIMIT = 200 * 1024;
+constexpr int MP_WT = 32;       // voxels per warp tile
+constexpr int MP_HEAD = 32;     // floats of a warp tile's label head (128 bytes)
+constexpr int MP_CHUNK = 8;     // iterations launched between host polls
+constexpr size_t MP_SMEM_LIMIT = 220 * 1024;
 constexpr int MP_NMAX = 96; // register-resident gradient shares: up to 96 apertures
 
 struct BBState {
@@ -55,8 +61,8 @@ struct BBState {
 };
 
 struct MPArgs {
-    const float *DA; // grouped tile layout (see above)
-    int64_t tstride; // floats per 256-voxel tile (a multiple of 1024)
+    const float *DA; // warp-tile layout (see above)
+    int64_t wstride; // floats per 32-voxel warp tile (32 + 128 * groups)
     int32_t V, n;
     const uint8_t *sid;
     const float *T, *wo, *wu;
@@ -69,8 +75,10 @@ struct MPArgs {
     double *part;  // [P][n + 1]
     double *cpart; // [P]
     int32_t P;
-    int32_t n_tiles;
+    int32_t n_tiles;  // 256-voxel tiles (fallback and Cauchy kernels)
+    int64_t n_wtiles; // 32-voxel warp tiles
     BBState *st;
+    unsigned *bar_count, *bar_gen; // grid barrier of the persistent solver
     int32_t *status;
     vmat_bb_opts opts;
     double F_offset;
@@ -78,9 +86,9 @@ struct MPArgs {
 
 __device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
 
-// Offset of DA(voxel i, aperture k) in the grouped tile layout.
+// Offset of DA(voxel i, aperture k) in the warp-tile layout.
 __device__ __forceinline__ int64_t da_at(const MPArgs &a, int64_t i, int k) {
-    return (i >> 8) * a.tstride + (int64_t)(k >> 2) * 1024 + ((i & 255) << 2) + (k & 3);
+    return (i >> 5) * a.wstride + MP_HEAD + (int64_t)(k >> 2) * 128 + ((i & 31) << 2) + (k & 3);
 }
 
 __device__ __forceinline__ float lo_of(const MPArgs &a, int k) { return a.lo ? a.lo[k] : 0.f; }
@@ -91,6 +99,10 @@ __global__ void mp_init_kernel(MPArgs a) {
     if (threadIdx.x == 0) {
         BBState s = {};
         *a.st = s;
+        if (a.bar_count) {
+            *a.bar_count = 0u;
+            *a.bar_gen = 0u;
+        }
     }
 }
 
@@ -255,167 +267,504 @@ __device__ void bb_step(const MPArgs &a) {
     }
 }
 
-// Per-voxel part of an iteration for voxel i with dose zi: returns g_i, adds F_i to facc.
-// The deviation d = z - T and the active weight are formed in FP32 (FP64 is a
-// small fraction of the FP32 rate on this GPU); the term w d^2 is then formed and
-// accumulated in FP64 from those FP32 values: one multiply and one FMA per voxel.
+// Per-voxel part of an iteration for voxel i with dose zi (fallback kernel):
+// returns g_i, adds F_i to facc.
 __device__ __forceinline__ float voxel_terms(const float *sT, const float *sO, const float *sU, int s, float zi,
                                              double &facc) {
     const float d = zi - sT[s];
     const float w = d > 0.f ? sO[s] : sU[s];
-    const double dd = (double)d;
-    facc = fma((double)w * dd, dd, facc);
+    facc += (double)((w * d) * d);
     return -2.f * w * d; // g = -grad F: -2 w+ (z - T) above, +2 w- (T - z) below
 }
 
-// Ends a pass: write this CTA's partials; the last CTA reduces them and steps.
-__device__ void pass_epilogue(const MPArgs &a, const double *accG, double facc) {
+// Ends a pass: write this CTA's partials; the last of the n_cta CTAs reduces them and steps.
+__device__ void pass_epilogue(const MPArgs &a, const double *accG, double facc, int cta, int n_cta) {
     __shared__ double sh[MP_NW];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const double fb = block_reduce_sum(facc, sh);
-    double *out = a.part + (int64_t)blockIdx.x * (a.n + 1);
+    double *out = a.part + (int64_t)cta * (a.n + 1);
     for (int k = tid; k < a.n; k += MP_THREADS) out[k] = accG[k];
     if (tid == 0) out[a.n] = fb;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(&a.st->ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) last = atomicAdd(&a.st->ticket, 1u) == (unsigned)n_cta - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    reduce_partials(a, gridDim.x);
+    reduce_partials(a, n_cta);
     bb_step(a);
     if (tid == 0) a.st->ticket = 0u;
 }
 
-// One BB iteration with DA tiles staged in shared memory by 2-D tensor copies
-// (one [n x 256] box per tile, `stages` tiles in flight, zero fill past V).
-// Each thread owns one voxel of every tile and keeps its share of
-// G = -DA^T g for all columns in registers (NMAX >= n) across the tiles of its
-// CTA; one block reduction per pass.  Needs DA 16-byte aligned and ld a
-// multiple of 4 (the tensor map's row pitch).
+// Bytes one bulk copy brings for n apertures: a warp tile's label head and its first ceil(n/4) groups.
+__host__ __device__ constexpr size_t wt_copy_bytes(int n) { return 128 + (size_t)((n + 3) / 4) * 512; }
 
-// One BB iteration: tiles of DA (the first n columns of 256 voxels, one block of
-// ceil(n/4) * 4 KB) are bulk-copied into shared memory, `stages` in flight.
-// Each thread owns one voxel of every tile and keeps its share of G for all
-// columns in registers (NMAX >= n) across the tiles of its CTA; one block
-// reduction per pass.  Slots of columns >= n inside the last group hold 0.
-template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS) mp_iter_tma_kernel(MPArgs a, int stages, int keep_in_l2) {
-    if (a.st->done || a.st->need_cauchy) return;
-    extern __shared__ __align__(128) unsigned char sm_raw[];
-    // align the staging area explicitly: this kernel's static shared memory may
-    // shift the dynamic region
-    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
-    constexpr int GMAX = NMAX / 4;
-    const int n = a.n, G = (n + 3) >> 2;
-    float *DAs = reinterpret_cast<float *>(sm);                              // [stages][G][256][4]
-    float4 *sy4 = reinterpret_cast<float4 *>(DAs + (size_t)stages * G * 1024); // [GMAX]
-    double *accG = reinterpret_cast<double *>(sy4 + GMAX);                     // [NMAX]
-    float *wred = reinterpret_cast<float *>(accG + NMAX);                      // [MP_NW][NMAX]
-    float *sT = wred + MP_NW * NMAX, *sO = sT + 256, *sU = sO + 256;           // [256] each
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sU + 256);                   // [stages]
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < 4 * GMAX; k += MP_THREADS) reinterpret_cast<float *>(sy4)[k] = k < n ? a.y[k] : 0.f;
-    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
-        sT[k] = a.T[k];
-        sO[k] = a.wo[k];
-        sU[k] = a.wu[k];
-    }
-    if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
+// ---------------------------------------------------------------------------
+// Persistent solver: one cooperative launch runs the whole BB loop.  Every
+// iteration is a pass over DA (each warp streams its own tiles), a grid
+// barrier, a column reduction of the CTA partials (one warp per column), a
+// second grid barrier, and the step, which every CTA computes identically in
+// its own shared memory from the same reduced values.  Cross-thread sums of
+// FP32 values are formed as unevaluated float pairs (hi + lo, Knuth's TwoSum),
+// in a fixed order; the BB dot products, F and the step stay FP64.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+
+// (a.hi + a.lo) + (b.hi + b.lo) as a float pair: TwoSum of the high parts, then
+// the low parts, renormalised.  No multiply, so no FMA contraction applies.
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    const float e = (a.hi - (s - bv)) + (b.hi - bv);
+    const float t = e + (a.lo + b.lo);
+    const float h = s + t;
+    return FF{h, t - (h - s)};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF v, int d) {
+    return FF{__shfl_xor_sync(0xffffffffu, v.hi, d), __shfl_xor_sync(0xffffffffu, v.lo, d)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
+
+// Grid barrier over n_cta co-resident CTAs (cooperative launch): arrival counter
+// plus a generation word.  Gives up after WAIT_LIMIT_CYCLES; returns false then.
+__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vg = gen;
+        const unsigned g0 = *vg;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == n_cta - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vg == g0) {
+                if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
     }
     __syncthreads();
-    // DA is read again by the next iteration: keep it in L2 when it fits there
-    const uint64_t pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
-    const uint32_t bytes = (uint32_t)G * 4096u;
-    auto issue = [&](int32_t tile, int s) {
-        mbar_arrive_expect_tx(&bars[s], bytes);
-        bulk_g2s(DAs + (size_t)s * G * 1024, a.DA + (int64_t)tile * a.tstride, bytes, &bars[s], pol);
-    };
-    if (tid == 0)
-        for (int s = 0; s < stages; ++s) {
-            const int32_t tile = blockIdx.x + s * gridDim.x;
-            if (tile < a.n_tiles) issue(tile, s);
-        }
-    float gacc[NMAX];
+    return ok_s != 0;
+}
+
+// Solver state every CTA keeps in shared memory (identical in all CTAs).
+struct PState {
+    double F_hist[6];
+    double F, delta0, gg, delta;
+    int t, done, stop, decided;
+};
+
+struct SolveSmem {
+    unsigned char *stage0; // [MP_NW][stages][cbytes]
+    float4 *sy4;           // [GMAX]   y, zero-padded
+    float4 *sg4;           // [GMAX]   G as float (Cauchy pass), zero-padded
+    double *sG, *sGp;      // [NMAX]   G_t, G_{t-1}
+    float *sYp;            // [NMAX]   y_{t-1}
+    float *wred;           // [MP_NW][NMAX]
+    float *sT, *sO, *sU;   // [256]
+    uint64_t *bars;        // [MP_NW][stages]
+};
+
+template <int NMAX> __host__ __device__ constexpr size_t solve_fixed_smem() {
+    return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 2 * (size_t)NMAX * 8 + (size_t)NMAX * 4 +
+           (size_t)MP_NW * NMAX * 4 + 3 * 256 * 4;
+}
+
+// Bulk copy of the warp's pipeline slot `it` (global tile-use index across passes).
+struct WarpPipe {
+    unsigned char *my;
+    uint64_t *mb;
+    const unsigned char *src;
+    int64_t tile_bytes, w0, W, n_my;
+    uint32_t cbytes;
+    int stages;
+    uint64_t pol;
+    __device__ __forceinline__ void issue(int64_t it) const {
+        const int s = (int)(it % stages);
+        const int64_t wt = w0 + (it % n_my) * W;
+        mbar_arrive_expect_tx(&mb[s], cbytes);
+        bulk_g2s(my + (size_t)s * cbytes, src + wt * tile_bytes, cbytes, &mb[s], pol);
+    }
+    __device__ __forceinline__ bool wait(int64_t it) const {
+        return mbar_wait_bounded(&mb[it % stages], (uint32_t)((it / stages) & 1), WAIT_LIMIT_CYCLES);
+    }
+};
+
+enum { PASS_ITER = 0, PASS_CAUCHY = 1 };
+
+// One sweep over this warp's tiles.  PASS_ITER: z = DA y, objective terms, G
+// shares; PASS_CAUCHY: q = DA G and the curvature terms w q^2.  Consumes
+// pipeline slots it .. it + n_my - 1 (advancing it) and issues slot + stages
+// after each.  Returns false (it at the slot) if a copy never landed.
+template <int NMAX, int MODE>
+__device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, const WarpPipe &P, int64_t &it,
+                                           float *gacc, float &fs, float &fc) {
+    constexpr int GMAX = NMAX / 4;
+    const int G = (a.n + 3) >> 2;
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = 0; j < P.n_my; ++j, ++it) {
+        const bool ok = P.wait(it);
+        if (!__all_sync(0xffffffffu, ok)) return false;
+        const unsigned char *blk = P.my + (size_t)(it % P.stages) * P.cbytes;
+        const float4 *D4 = reinterpret_cast<const float4 *>(blk + 128) + lane; // group g at D4[32 g]
+        const float4 *w4 = MODE == PASS_ITER ? S.sy4 : S.sg4;
+        float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
-    double facc = 0.0;
-    int it = 0;
-    bool timed_out = false;
-    for (int32_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-        const int s = it % stages;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / stages) & 1), WAIT_LIMIT_CYCLES);
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
-        }
-        const float4 *T4 = reinterpret_cast<const float4 *>(DAs + (size_t)s * G * 1024) + tid; // group g at [g * 256]
-        const int64_t i = (int64_t)tile * MP_THREADS + tid;
+        for (int g = 0; g < GMAX; ++g)
+            if (g < G) {
+                const float4 v = D4[32 * g], w = w4[g];
+                z0 = fmaf(v.x, w.x, z0);
+                z1 = fmaf(v.y, w.y, z1);
+                z2 = fmaf(v.z, w.z, z2);
+                z3 = fmaf(v.w, w.w, z3);
+            }
+        const float zi = (z0 + z1) + (z2 + z3);
+        const int64_t i = (P.w0 + j * P.W) * MP_WT + lane;
+        float gi = 0.f;
         if (i < a.V) {
-            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+            const int sid = blk[lane];
+            if (MODE == PASS_ITER) {
+                a.z[i] = zi;
+                const float d = zi - S.sT[sid];
+                const float w = d > 0.f ? S.sO[sid] : S.sU[sid];
+                const float yk = (w * d) * d - fc; // Kahan step
+                const float tk = fs + yk;
+                fc = (tk - fs) - yk;
+                fs = tk;
+                gi = -2.f * w * d; // g = -grad F: -2 w+ (z - T) above, +2 w- (T - z) below
+            } else {
+                // curvature of F along DA G: the active weight (0 exactly at the threshold)
+                const float zc = a.z[i], T = S.sT[sid];
+                const float w = zc > T ? S.sO[sid] : (zc < T ? S.sU[sid] : 0.f);
+                const float yk = (w * zi) * zi - fc;
+                const float tk = fs + yk;
+                fc = (tk - fs) - yk;
+                fs = tk;
+            }
+        }
+        if (MODE == PASS_ITER) {
 #pragma unroll
             for (int g = 0; g < GMAX; ++g)
                 if (g < G) {
-                    const float4 v = T4[g * 256], w = sy4[g];
-                    z0 = fmaf(v.x, w.x, z0);
-                    z1 = fmaf(v.y, w.y, z1);
-                    z2 = fmaf(v.z, w.z, z2);
-                    z3 = fmaf(v.w, w.w, z3);
-                }
-            const float zi = (z0 + z1) + (z2 + z3);
-            a.z[i] = zi;
-            const float gi = voxel_terms(sT, sO, sU, a.sid[i], zi, facc);
-#pragma unroll
-            for (int g = 0; g < GMAX; ++g)
-                if (g < G) {
-                    const float4 v = T4[g * 256];
+                    const float4 v = D4[32 * g];
                     gacc[4 * g + 0] = fmaf(v.x, gi, gacc[4 * g + 0]);
                     gacc[4 * g + 1] = fmaf(v.y, gi, gacc[4 * g + 1]);
                     gacc[4 * g + 2] = fmaf(v.z, gi, gacc[4 * g + 2]);
                     gacc[4 * g + 3] = fmaf(v.w, gi, gacc[4 * g + 3]);
                 }
         }
-        __syncthreads(); // every read of stage s is done before its next copy
-        if (tid == 0) {
-            const int32_t nt = tile + stages * gridDim.x;
-            if (nt < a.n_tiles) issue(nt, s);
+        __syncwarp(); // every lane's reads of this slot are done before its next copy
+        if (lane == 0) P.issue(it + P.stages);
+    }
+    return true;
+}
+
+// CTA sum of one float pair per thread (result in thread 0): warp butterflies, warps in order.
+__device__ FF block_ff(FF v, FF *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    FF t = sh[0];
+    if (threadIdx.x == 0)
+        for (int w = 1; w < MP_NW; ++w) t = ff_add(t, sh[w]);
+    __syncthreads();
+    return t;
+}
+
+// Warp 0: Eq. 9-10 freeze, stopping tests, BB step length, projected update, all
+// on the shared-memory copy of the state.  Every CTA runs it on identical inputs.
+template <int NMAX>
+__device__ void solve_step(const MPArgs &a, const SolveSmem &S, PState &ps) {
+    const int lane = threadIdx.x & 31;
+    const int n = a.n, t = ps.t;
+    float *y = reinterpret_cast<float *>(S.sy4);
+    double dy = 0.0, ymax = 0.0, gg = 0.0, ss = 0.0, sr = 0.0, rr = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        float yk = y[k];
+        const float l = lo_of(a, k), h = hi_of(a, k);
+        double g = S.sG[k];
+        if (yk <= l && g > 0.0) {
+            yk = l;
+            g = 0.0;
+        } else if (yk >= h && g < 0.0) {
+            yk = h;
+            g = 0.0;
+        }
+        y[k] = yk;
+        S.sG[k] = g;
+        ymax = fmax(ymax, fabs((double)yk));
+        gg += g * g;
+        if (t > 0) {
+            const double sk = (double)yk - (double)S.sYp[k], rk = g - S.sGp[k];
+            dy = fmax(dy, fabs(sk));
+            ss += sk * sk;
+            sr += sk * rk;
+            rr += rk * rk;
         }
     }
-    if (timed_out) {
-        // a copy that never landed: record it, let issued copies finish, stop the solve
-        if (tid == 0) {
-            atomicOr(a.status, DEV_TIMEOUT);
-            a.st->done = 1;
-            a.st->stop = VMAT_STOP_MAXIT;
-            for (int k = 0; k < stages; ++k) {
-                const int it2 = it + k;
-                if (blockIdx.x + it2 * gridDim.x < a.n_tiles)
-                    mbar_wait_bounded(&bars[it2 % stages], (uint32_t)((it2 / stages) & 1), WAIT_LIMIT_CYCLES);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        dy = fmax(dy, __shfl_xor_sync(0xffffffffu, dy, d));
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, d));
+        gg += __shfl_xor_sync(0xffffffffu, gg, d);
+        ss += __shfl_xor_sync(0xffffffffu, ss, d);
+        sr += __shfl_xor_sync(0xffffffffu, sr, d);
+        rr += __shfl_xor_sync(0xffffffffu, rr, d);
+    }
+    if (lane == 0) {
+        const double F = ps.F;
+        ps.decided = 1;
+        ps.F_hist[t % 6] = F;
+        if (t >= 5 && fabs(ps.F_hist[(t - 5) % 6] - F) <= a.opts.rel_tol5 * F) {
+            ps.done = 1;
+            ps.stop = VMAT_STOP_REL;
+        } else if (t >= 1 && dy <= a.opts.step_tol * fmax(1.0, ymax)) {
+            ps.done = 1;
+            ps.stop = VMAT_STOP_STEP;
+        } else if (t == a.opts.max_iter - 1) {
+            ps.done = 1;
+            ps.stop = VMAT_STOP_MAXIT;
+        } else if (t == 0) {
+            if (gg == 0.0) {
+                ps.done = 1;
+                ps.stop = VMAT_STOP_GRAD0;
+            } else {
+                ps.gg = gg;
+                ps.decided = 2; // the first step is the Cauchy step (needs DA G)
+            }
+        } else {
+            double delta;
+            if (sr <= 0.0) delta = a.opts.delta_max * ps.delta0;
+            else if (t & 1) delta = sr / rr;
+            else delta = ss / sr;
+            ps.delta = fmin(fmax(delta, a.opts.delta_min * ps.delta0), a.opts.delta_max * ps.delta0);
+            ps.decided = 0;
+        }
+    }
+    __syncwarp();
+}
+
+// y <- clamp(y - delta G) after saving (y, G) as the previous iterate (warp 0).
+__device__ void solve_take_step(const MPArgs &a, const SolveSmem &S, double delta) {
+    float *y = reinterpret_cast<float *>(S.sy4);
+    for (int k = threadIdx.x & 31; k < a.n; k += 32) {
+        const float yk = y[k];
+        S.sYp[k] = yk;
+        S.sGp[k] = S.sG[k];
+        const double yn = (double)yk - delta * S.sG[k];
+        y[k] = fminf(fmaxf((float)yn, lo_of(a, k)), hi_of(a, k));
+    }
+    __syncwarp();
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
+    constexpr int GMAX = NMAX / 4;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    __shared__ PState ps;
+    __shared__ FF shff[MP_NW];
+    __shared__ int abort_s;
+    // align the staging area explicitly: static shared memory may shift the dynamic region
+    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
+    const int n = a.n;
+    const uint32_t cbytes = (uint32_t)wt_copy_bytes(n);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned n_cta = gridDim.x, cta = blockIdx.x;
+    SolveSmem S;
+    S.stage0 = sm;
+    S.sy4 = reinterpret_cast<float4 *>(sm + (size_t)MP_NW * stages * cbytes);
+    S.sg4 = S.sy4 + GMAX;
+    S.sG = reinterpret_cast<double *>(S.sg4 + GMAX);
+    S.sGp = S.sG + NMAX;
+    S.sYp = reinterpret_cast<float *>(S.sGp + NMAX);
+    S.wred = S.sYp + NMAX;
+    S.sT = S.wred + MP_NW * NMAX;
+    S.sO = S.sT + 256;
+    S.sU = S.sO + 256;
+    S.bars = reinterpret_cast<uint64_t *>(S.sU + 256);
+    for (int k = tid; k < 4 * GMAX; k += MP_THREADS) {
+        reinterpret_cast<float *>(S.sy4)[k] = k < n ? a.y[k] : 0.f; // clamped by mp_init_kernel
+        reinterpret_cast<float *>(S.sg4)[k] = 0.f;
+    }
+    for (int k = tid; k < a.n_struct; k += MP_THREADS) {
+        S.sT[k] = a.T[k];
+        S.sO[k] = a.wo[k];
+        S.sU[k] = a.wu[k];
+    }
+    if (tid == 0) {
+        PState z = {};
+        ps = z;
+        abort_s = 0;
+    }
+    WarpPipe P;
+    P.my = S.stage0 + (size_t)wid * stages * cbytes;
+    P.mb = S.bars + wid * stages;
+    P.src = reinterpret_cast<const unsigned char *>(a.DA);
+    P.tile_bytes = a.wstride * 4;
+    P.W = (int64_t)n_cta * MP_NW;
+    P.w0 = (int64_t)cta * MP_NW + wid;
+    P.n_my = P.w0 < a.n_wtiles ? (a.n_wtiles - 1 - P.w0) / P.W + 1 : 0;
+    P.cbytes = cbytes;
+    P.stages = stages;
+    // DA is read again by every iteration: keep it in L2 when it fits there
+    P.pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&P.mb[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (lane == 0 && P.n_my > 0)
+        for (int s = 0; s < stages; ++s) P.issue(s);
+    int64_t it = 0; // pipeline slots consumed by this warp
+    float gacc[NMAX];
+    FF *part = reinterpret_cast<FF *>(a.part);
+    FF *cpart = reinterpret_cast<FF *>(a.cpart);
+    bool ok = true;
+    while (true) {
+        // ---- pass: z = DA y, g, F and this CTA's shares of G = -DA^T g
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
+        float fs = 0.f, fc = 0.f;
+        const bool pass_ok = P.n_my == 0 || solve_pass<NMAX, PASS_ITER>(a, S, P, it, gacc, fs, fc);
+        if (!pass_ok && lane == 0) atomicOr(&abort_s, 1);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < n) {
+                float x = gacc[k];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+                if (lane == 0) S.wred[wid * NMAX + k] = x;
             }
         }
-        return;
+        const FF fb = block_ff(FF{fs, -fc}, shff); // includes a __syncthreads after wred
+        for (int k = tid; k < n; k += MP_THREADS) {
+            FF sum{S.wred[k], 0.f};
+            for (int w = 1; w < MP_NW; ++w) sum = ff_add(sum, FF{S.wred[w * NMAX + k], 0.f});
+            part[(int64_t)cta * (n + 1) + k] = sum;
+        }
+        if (tid == 0) part[(int64_t)cta * (n + 1) + n] = fb;
+        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) {
+            ok = false;
+            break;
+        }
+        // ---- column reduction: warp w of CTA c sums columns c * MP_NW + w, + MP_NW * n_cta, ...
+        for (int k = (int)cta * MP_NW + wid; k <= n; k += MP_NW * (int)n_cta) {
+            {
+                FF v{0.f, 0.f};
+                for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) { // eight loads in flight per lane
+                    float2 q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const unsigned b = b0 + 32u * u;
+                        q[u] = b < n_cta ? __ldcg(reinterpret_cast<const float2 *>(part) + (int64_t)b * (n + 1) + k)
+                                         : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
+                }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
+                if (lane == 0) a.G[k] = ff_to_double(v);
+            }
+        }
+        if (!grid_sync(a.bar_count, a.bar_gen, n_cta)) {
+            ok = false;
+            break;
+        }
+        for (int k = tid; k < n; k += MP_THREADS) S.sG[k] = -__ldcg(a.G + k);
+        if (tid == 0) ps.F = __ldcg(a.G + n) + a.F_offset;
+        __syncthreads();
+        if (wid == 0) {
+            solve_step<NMAX>(a, S, ps);
+            if (ps.decided == 0) solve_take_step(a, S, ps.delta);
+        }
+        __syncthreads();
+        if (ps.decided == 2) {
+            // ---- Cauchy step: delta0 = G.G / (2 sum_i w_i (DA G)_i^2)
+            for (int k = tid; k < 4 * GMAX; k += MP_THREADS)
+                reinterpret_cast<float *>(S.sg4)[k] = k < n ? (float)S.sG[k] : 0.f;
+            __syncthreads();
+            float cs = 0.f, cc = 0.f;
+            const bool c_ok = P.n_my == 0 || solve_pass<NMAX, PASS_CAUCHY>(a, S, P, it, gacc, cs, cc);
+            if (!c_ok && lane == 0) atomicOr(&abort_s, 1);
+            const FF cb = block_ff(FF{cs, -cc}, shff);
+            if (tid == 0) cpart[cta] = cb;
+            if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) {
+                ok = false;
+                break;
+            }
+            if (wid == 0) {
+                FF v{0.f, 0.f};
+                for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) {
+                    float2 q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const unsigned b = b0 + 32u * u;
+                        q[u] = b < n_cta ? __ldcg(reinterpret_cast<const float2 *>(cpart) + b) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
+                }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
+                const double curv = 2.0 * ff_to_double(v);
+                if (lane == 0) {
+                    if (curv == 0.0) {
+                        ps.done = 1;
+                        ps.stop = VMAT_STOP_FLAT;
+                    } else {
+                        ps.delta0 = ps.gg / curv;
+                    }
+                }
+                __syncwarp();
+                if (!ps.done) solve_take_step(a, S, ps.delta0);
+            }
+            __syncthreads();
+        }
+        if (ps.done) break;
+        if (tid == 0) ++ps.t;
+        __syncthreads();
     }
-    // block reduction of the per-thread shares: butterfly per warp, warps in order
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-        if (k < n) {
-            float x = gacc[k];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-            if (lane == 0) wred[wid * NMAX + k] = x;
+    if (!ok) {
+        if (tid == 0) atomicOr(a.status, DEV_TIMEOUT);
+    }
+    // copies issued ahead for a pass that will not run: let them land before exit
+    if (lane == 0 && P.n_my > 0)
+        for (int s = 0; s < stages; ++s) P.wait(it + s);
+    __syncwarp();
+    if (cta == 0 && ok) {
+        const float *y = reinterpret_cast<const float *>(S.sy4);
+        for (int k = tid; k < n; k += MP_THREADS) a.y[k] = y[k];
+        if (tid == 0) {
+            a.st->F = ps.F;
+            a.st->t = ps.t;
+            a.st->done = 1;
+            a.st->stop = ps.stop;
+            a.st->iters = ps.t + 1;
+            a.st->delta0 = ps.delta0;
         }
     }
-    __syncthreads();
-    for (int k = tid; k < n; k += MP_THREADS) {
-        double sum = 0.0;
-        for (int w = 0; w < MP_NW; ++w) sum += (double)wred[w * NMAX + k];
-        accG[k] = sum;
+    if (cta == 0 && !ok && tid == 0) {
+        a.st->done = 1;
+        a.st->stop = VMAT_STOP_MAXIT;
+        a.st->iters = ps.t + 1;
     }
-    __syncthreads();
-    pass_epilogue(a, accG, facc);
 }
 
 // The same iteration reading DA from global memory with per-tile reductions
@@ -463,7 +812,7 @@ __global__ void __launch_bounds__(MP_THREADS) mp_iter_ldg_kernel(MPArgs a) {
         }
         __syncthreads();
     }
-    pass_epilogue(a, accG, facc);
+    pass_epilogue(a, accG, facc, blockIdx.x, gridDim.x);
 }
 
 // Cauchy step, part 1: curvature 2 sum_i w_i (DA G)_i^2 with w the active penalty weight.
@@ -514,57 +863,98 @@ __global__ void __launch_bounds__(MP_THREADS) mp_cauchy_step_kernel(MPArgs a, in
 }
 
 
-// Grouped tile layout from a column-major matrix (DA[k * ld + i]); padding 0.
-__global__ void to_grouped_tiles(const float *src, int64_t ld, int32_t V, int32_t n, int64_t tstride,
-                                 int32_t n_tiles, float *dst) {
-    const int64_t total = (int64_t)n_tiles * tstride;
+// Warp-tile layout from a column-major matrix (DA[k * ld + i]) and the labels; padding 0.
+__global__ void to_warp_tiles(const float *src, int64_t ld, int32_t V, int32_t n, const uint8_t *sid,
+                              int64_t wstride, int64_t n_wtiles, float *dst) {
+    const int64_t total = n_wtiles * wstride;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t tile = o / tstride, r = o % tstride;
-        const int k = (int)((r >> 10) << 2) + (int)(r & 3);
-        const int64_t i = tile * 256 + ((r & 1023) >> 2);
-        dst[o] = (k < n && i < V) ? src[(int64_t)k * ld + i] : 0.f;
+        const int64_t wt = o / wstride, r = o % wstride;
+        if (r < MP_HEAD) { // labels of voxels 4r .. 4r + 3 of the tile (words 8 .. 31 stay 0)
+            uint32_t packed = 0u;
+            if (r < MP_WT / 4)
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t i = wt * MP_WT + 4 * r + j;
+                    if (i < V) packed |= (uint32_t)sid[i] << (8 * j);
+                }
+            reinterpret_cast<uint32_t *>(dst)[o] = packed;
+        } else {
+            const int64_t q = r - MP_HEAD;
+            const int k = (int)((q >> 7) << 2) + (int)(q & 3);
+            const int64_t i = wt * MP_WT + ((q & 127) >> 2);
+            dst[o] = (k < n && i < V) ? src[(int64_t)k * ld + i] : 0.f;
+        }
     }
 }
 
-static int tma_nmax(int n) { return ((n + 7) / 8) * 8; }
-// Tiles in flight per CTA (~n KB each): ~100 KB so that two CTAs share an SM while
-// that still allows 3 stages, else ~190 KB for one CTA; at least double-buffered.
-static int tma_stages(int n) {
-    const int kb = 4 * ((std::max(n, 1) + 3) / 4);
-    const int budget = 3 * kb <= 100 ? 100 : 190;
-    return std::max(MP_STAGES, std::min(6, budget / kb));
-}
-static size_t tma_smem(int n, int stages) {
-    const int nmax = tma_nmax(n), G = (n + 3) / 4;
-    return 128 /* alignment slack */ + (size_t)stages * G * 4096 + (size_t)(nmax / 4) * 16 + (size_t)nmax * 8 +
-           (size_t)MP_NW * nmax * 4 + 3 * 256 * 4 + (size_t)stages * 8;
+// Label heads of every warp tile (the DA columns are written by the caller).
+__global__ void write_label_heads(const uint8_t *sid, int32_t V, int64_t wstride, int64_t n_wtiles,
+                                  uint32_t *dst) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_wtiles * (MP_WT / 4);
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t wt = o / (MP_WT / 4), r = o % (MP_WT / 4);
+        uint32_t packed = 0u;
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = wt * MP_WT + 4 * r + j;
+            if (i < V) packed |= (uint32_t)sid[i] << (8 * j);
+        }
+        dst[wt * wstride + r] = packed;
+    }
 }
 
-using TmaIterFn = void (*)(MPArgs, int, int);
-static TmaIterFn tma_kernel_for(int n) {
+vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, float *DA, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int64_t n_wt = ((int64_t)V + MP_WT - 1) / MP_WT;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n_wt * 8 + 255) / 256, (int64_t)ctx->n_sm * 8));
+    write_label_heads<<<g, 256, 0, s>>>(sid, V, wstride, n_wt, reinterpret_cast<uint32_t *>(DA));
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+static int solve_nmax(int n) { return ((n + 7) / 8) * 8; }
+static size_t solve_fixed(int n) {
+    const int nmax = solve_nmax(n);
+    return 128 /* alignment slack */ + 2 * (size_t)(nmax / 4) * 16 + 2 * (size_t)nmax * 8 + (size_t)nmax * 4 +
+           (size_t)MP_NW * nmax * 4 + 3 * 256 * 4;
+}
+static size_t solve_smem(int n, int stages) {
+    return solve_fixed(n) + (size_t)stages * (MP_NW * wt_copy_bytes(n) + MP_NW * 8);
+}
+// Tiles in flight per warp: as many as fit (up to 8) in ~110 KB, so that two CTAs
+// share an SM; where not even two fit there, up to the per-CTA limit (one CTA per SM).
+static int solve_stages(int n) {
+    const size_t per = MP_NW * wt_copy_bytes(n) + MP_NW * 8;
+    const size_t small = 110 * 1024;
+    const size_t st = solve_fixed(n) + 2 * per <= small ? (small - solve_fixed(n)) / per
+                                                        : (MP_SMEM_LIMIT - solve_fixed(n)) / per;
+    return (int)std::min<size_t>(8, st);
+}
+
+using SolveFn = void (*)(MPArgs, int, int);
+static SolveFn solve_kernel_for(int n) {
     switch ((n + 7) / 8) {
-    case 1: return mp_iter_tma_kernel<8>;
-    case 2: return mp_iter_tma_kernel<16>;
-    case 3: return mp_iter_tma_kernel<24>;
-    case 4: return mp_iter_tma_kernel<32>;
-    case 5: return mp_iter_tma_kernel<40>;
-    case 6: return mp_iter_tma_kernel<48>;
-    case 7: return mp_iter_tma_kernel<56>;
-    case 8: return mp_iter_tma_kernel<64>;
-    case 9: return mp_iter_tma_kernel<72>;
-    case 10: return mp_iter_tma_kernel<80>;
-    case 11: return mp_iter_tma_kernel<88>;
-    case 12: return mp_iter_tma_kernel<96>;
+    case 1: return mp_solve_kernel<8>;
+    case 2: return mp_solve_kernel<16>;
+    case 3: return mp_solve_kernel<24>;
+    case 4: return mp_solve_kernel<32>;
+    case 5: return mp_solve_kernel<40>;
+    case 6: return mp_solve_kernel<48>;
+    case 7: return mp_solve_kernel<56>;
+    case 8: return mp_solve_kernel<64>;
+    case 9: return mp_solve_kernel<72>;
+    case 10: return mp_solve_kernel<80>;
+    case 11: return mp_solve_kernel<88>;
+    case 12: return mp_solve_kernel<96>;
     default: return nullptr;
     }
 }
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
-int64_t mp_tile_stride(int32_t n_cap) { return (int64_t)((n_cap + 3) / 4) * 1024; }
+int64_t mp_wtile_stride(int32_t n_cap) { return MP_HEAD + (int64_t)((n_cap + 3) / 4) * 128; }
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
-                       int64_t tstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts_in, double F_offset, vmat_bb_report *rep, cudaStream_t s) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
@@ -574,27 +964,31 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
     const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
 
-    // a column-major input is copied once into the grouped tile layout
+    const int64_t n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
+
+    // a column-major input is copied once into the warp-tile layout (with the labels)
     Scratch conv;
-    if (tstride == 0) {
-        tstride = mp_tile_stride(n_ap);
-        VMAT_TRY(conv.alloc((size_t)n_tiles * tstride * sizeof(float), s));
-        const int64_t total = (int64_t)n_tiles * tstride;
+    if (wstride == 0) {
+        wstride = mp_wtile_stride(n_ap);
+        VMAT_TRY(conv.alloc((size_t)n_wtiles * wstride * sizeof(float), s));
+        const int64_t total = n_wtiles * wstride;
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
-        to_grouped_tiles<<<g, 256, 0, s>>>(DA, ld, V, n_ap, tstride, n_tiles, static_cast<float *>(conv.ptr));
+        to_warp_tiles<<<g, 256, 0, s>>>(DA, ld, V, n_ap, struct_id, wstride, n_wtiles, static_cast<float *>(conv.ptr));
         VMAT_LAUNCH_CHECK();
         DA = static_cast<const float *>(conv.ptr);
     }
 
-    const int stages = tma_stages(n_ap);
-    const bool tma = n_ap <= MP_NMAX && tma_smem(n_ap, stages) <= MP_SMEM_LIMIT && tstride % 1024 == 0;
-    TmaIterFn tma_fn = tma ? tma_kernel_for(n_ap) : nullptr;
-    const size_t smem_pass = tma ? tma_smem(n_ap, stages) : ldg_smem(n_ap);
-    const int keep_in_l2 = (double)n_ap * (double)V * 4.0 <= 64.0 * 1024 * 1024 ? 1 : 0;
+    // persistent solver (one cooperative launch) up to MP_NMAX apertures, else one
+    // launch per iteration reading DA from global memory
+    const int stages = solve_stages(n_ap);
+    const bool persistent = n_ap <= MP_NMAX && stages >= 2 && solve_smem(n_ap, stages) <= MP_SMEM_LIMIT;
+    SolveFn solve_fn = persistent ? solve_kernel_for(n_ap) : nullptr;
+    const size_t smem_pass = persistent ? solve_smem(n_ap, stages) : ldg_smem(n_ap);
+    const int keep_in_l2 = (double)n_wtiles * (double)wt_copy_bytes(n_ap) <= 64.0 * 1024 * 1024 ? 1 : 0;
     static bool attr = false;
     if (!attr) {
         for (int q = 1; q <= MP_NMAX / 8; ++q)
-            VMAT_CUDA(cudaFuncSetAttribute(tma_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
+            VMAT_CUDA(cudaFuncSetAttribute(solve_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            MP_SMEM_LIMIT));
         VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
         VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -602,27 +996,31 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
         attr = true;
     }
     int bps = 1;
-    if (tma) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tma_fn, MP_THREADS, smem_pass));
+    if (persistent) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, solve_fn, MP_THREADS, smem_pass));
     else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, smem_pass));
-    bps = std::max(bps, 1);
-    const int P = std::max(1, std::min<int>(n_tiles, ctx->n_sm * bps));
+    if (bps < 1) return set_error(VMAT_ECUDA, "mp_bb_solve: the solver kernel does not fit on an SM");
+    // every CTA of the persistent grid must be resident at once (grid barriers)
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(persistent ? (n_wtiles + MP_NW - 1) / MP_NW : n_tiles,
+                                                                (int64_t)ctx->n_sm * bps));
     const int Pc = std::max(1, std::min<int>(n_tiles, ctx->n_sm * 4));
 
     Scratch ws;
-    const size_t bytes = 256 + (size_t)n_ap * (2 * sizeof(double) + sizeof(float)) +
-                         (size_t)P * (n_ap + 1) * sizeof(double) + (size_t)Pc * sizeof(double) + 256;
+    const size_t bytes = 256 + (size_t)(n_ap + 1) * sizeof(double) + (size_t)n_ap * (sizeof(double) + sizeof(float)) +
+                         (size_t)P * (n_ap + 1) * sizeof(double) + (size_t)std::max(P, Pc) * sizeof(double) + 256;
     VMAT_TRY(ws.alloc(bytes, s));
     char *p = static_cast<char *>(ws.ptr);
     MPArgs a;
     a.st = reinterpret_cast<BBState *>(p);
+    a.bar_count = reinterpret_cast<unsigned *>(p + 192);
+    a.bar_gen = reinterpret_cast<unsigned *>(p + 224);
     p += 256;
-    a.G = reinterpret_cast<double *>(p);
-    a.Gprev = a.G + n_ap;
+    a.G = reinterpret_cast<double *>(p); // [n + 1]: G, then F in the persistent solver
+    a.Gprev = a.G + n_ap + 1;
     a.part = a.Gprev + n_ap;
     a.cpart = a.part + (size_t)P * (n_ap + 1);
-    a.yprev = reinterpret_cast<float *>(a.cpart + Pc);
+    a.yprev = reinterpret_cast<float *>(a.cpart + std::max(P, Pc));
     a.DA = DA;
-    a.tstride = tstride;
+    a.wstride = wstride;
     a.V = V;
     a.n = n_ap;
     a.sid = struct_id;
@@ -636,6 +1034,7 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.hi = hi;
     a.P = P;
     a.n_tiles = n_tiles;
+    a.n_wtiles = n_wtiles;
     a.status = ctx->status;
     a.opts = opts;
     a.F_offset = F_offset;
@@ -646,24 +1045,33 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
 
     mp_init_kernel<<<1, MP_THREADS, 0, s>>>(a);
     VMAT_LAUNCH_CHECK();
-    int launched = 0;
-    while (launched < opts.max_iter) {
-        const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
-        for (int c = 0; c < chunk; ++c) {
-            if (tma) tma_fn<<<P, MP_THREADS, smem_pass, s>>>(a, stages, keep_in_l2);
-            else mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
-            g_launches.fetch_add(1, std::memory_order_relaxed);
-            if (launched + c == 0) {
-                mp_cauchy_pass_kernel<<<Pc, MP_THREADS, smem_cauchy, s>>>(a);
-                mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a, Pc);
-                g_launches.fetch_add(2, std::memory_order_relaxed);
-            }
-        }
-        VMAT_CUDA(cudaGetLastError());
-        launched += chunk;
+    if (persistent) {
+        int st_arg = stages, l2_arg = keep_in_l2;
+        void *args[] = {&a, &st_arg, &l2_arg};
+        VMAT_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(solve_fn), dim3(P), dim3(MP_THREADS),
+                                              args, smem_pass, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         VMAT_CUDA(cudaMemcpyAsync(host_st, a.st, sizeof(BBState), cudaMemcpyDeviceToHost, s));
         VMAT_CUDA(cudaStreamSynchronize(s));
-        if (host_st->done) break;
+    } else {
+        int launched = 0;
+        while (launched < opts.max_iter) {
+            const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
+            for (int c = 0; c < chunk; ++c) {
+                mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
+                g_launches.fetch_add(1, std::memory_order_relaxed);
+                if (launched + c == 0) {
+                    mp_cauchy_pass_kernel<<<Pc, MP_THREADS, smem_cauchy, s>>>(a);
+                    mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a, Pc);
+                    g_launches.fetch_add(2, std::memory_order_relaxed);
+                }
+            }
+            VMAT_CUDA(cudaGetLastError());
+            launched += chunk;
+            VMAT_CUDA(cudaMemcpyAsync(host_st, a.st, sizeof(BBState), cudaMemcpyDeviceToHost, s));
+            VMAT_CUDA(cudaStreamSynchronize(s));
+            if (host_st->done) break;
+        }
     }
     if (!host_st->done) return set_error(VMAT_ECUDA, "mp_bb_solve: solver did not reach a stopping rule");
     int32_t dev_status = 0;
