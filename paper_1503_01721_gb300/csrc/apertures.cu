@@ -28,9 +28,11 @@ __device__ __forceinline__ float load_val(const void *val, int64_t e, vmat_dtype
 
 __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                      const void *__restrict__ val, vmat_dtype dt, const float *__restrict__ scale,
-                                     int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp, int32_t n_rrows,
-                                     int32_t n_cols, const int16_t *__restrict__ leaves, float *__restrict__ da,
-                                     int64_t wstride) {
+                                     int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp_arg,
+                                     const int32_t *cp_dev, const int32_t *skip, int32_t n_rrows, int32_t n_cols,
+                                     const int16_t *__restrict__ leaves, float *__restrict__ da, int64_t wstride) {
+    if (skip && *skip) return;
+    const int32_t cp = cp_dev ? *cp_dev : cp_arg;
     extern __shared__ int16_t sl[]; // [n_rrows][2]
     for (int i = threadIdx.x; i < 2 * n_rrows; i += blockDim.x) sl[i] = leaves[i];
     __syncthreads();
@@ -73,7 +75,22 @@ vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, co
     const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
     aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
         h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n,
-        compact ? nullptr : h.D.row_ids, cp, mlc->n_rows, mlc->n_cols, leaves, da, compact ? wstride : 0);
+        compact ? nullptr : h.D.row_ids, cp, nullptr, nullptr, mlc->n_rows, mlc->n_cols, leaves, da,
+        compact ? wstride : 0);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status aperture_dose_dev(const Ddc &h, const vmat_mlc *mlc, const int32_t *cp_dev, const int16_t *leaves,
+                              float *da, int64_t wstride, const int32_t *skip, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int32_t n = h.D.n_rows;
+    if (n == 0) return VMAT_OK;
+    const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
+    aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
+        h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n, nullptr, 0, cp_dev,
+        skip, mlc->n_rows, mlc->n_cols, leaves, da, wstride);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

@@ -7,11 +7,15 @@
 // until n_apertures exist or no CP has a positive price.  Then the final dose
 // D (A y) is recomputed in FP32 from the stored matrix and F is evaluated.
 //
-// Everything stays on the device.  The master problem runs in the compact
-// space of voxels that have at least one nonzero (the rows of CSR(D)); the
-// other voxels always receive zero dose, so their penalty is a constant added
-// to F.  The host reads back only the chosen CP and its price (to stop) and
-// the MP stop flag.
+// Everything stays on the device and the loop is device-driven: a one-thread
+// kernel commits each priced aperture (or sets the stop flag when no CP has a
+// positive price), the aperture dose kernel reads the chosen CP from device
+// memory, and every later kernel returns at once when the stop flag is set.
+// The host enqueues the whole plan without waiting on the GPU (up to 96
+// apertures; beyond that the host-driven master-problem solver polls).  The
+// master problem runs in the compact space of voxels that have at least one
+// nonzero (the rows of CSR(D)); the other voxels always receive zero dose, so
+// their penalty is a constant added to F.
 #include <string.h>
 
 #include <algorithm>
@@ -22,11 +26,13 @@
 namespace vmat {
 
 vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
-                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s);
+                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
+                              const int32_t *skip);
 size_t objective_scratch_bytes(int n_sm);
 vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
-                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s);
+                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s,
+                                 const int32_t *skip);
 size_t pricing_scratch_bytes(const vmat_mlc *mlc);
 
 __global__ void gather_u8(const uint8_t *src, const int32_t *idx, int32_t n, uint8_t *dst) {
@@ -39,6 +45,38 @@ __global__ void fill_u8(uint8_t *p, int32_t n, uint8_t v) {
 
 __global__ void fill_i32(int32_t *p, int32_t n, int32_t v) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Plan control words on the device.
+enum { CTL_STOPPED = 0, CTL_REASON, CTL_NAP, CTL_BBITERS, CTL_N };
+
+// Commits the aperture priced at iteration t, or stops the plan when no CP has a
+// positive price (Section 2.1).  One block; every thread reads the same inputs.
+__global__ void commit_aperture(int32_t t, int32_t NR, const int32_t *best_cp, const double *best_price,
+                                const int16_t *best_leaves, uint8_t *occupied, uint8_t *active, int16_t *leaves_all,
+                                int16_t *leaves_seq, int32_t *cps, float *y, int32_t *ctl) {
+    if (ctl[CTL_STOPPED]) return;
+    const int32_t k = *best_cp;
+    const bool stop = k < 0 || !(*best_price > 0.0);
+    __syncthreads(); // every thread has read the stop flag before it changes
+    if (stop) {
+        if (threadIdx.x == 0) {
+            ctl[CTL_STOPPED] = 1;
+            ctl[CTL_REASON] = VMAT_STOP_PRICE;
+        }
+        return;
+    }
+    for (int r = threadIdx.x; r < 2 * NR; r += blockDim.x) {
+        leaves_all[(int64_t)k * 2 * NR + r] = best_leaves[r];
+        leaves_seq[(int64_t)t * 2 * NR + r] = best_leaves[r];
+    }
+    if (threadIdx.x == 0) {
+        occupied[k] = 1;
+        active[k] = 0;
+        cps[t] = k;
+        y[t] = 0.f;
+        ctl[CTL_NAP] = t + 1;
+    }
 }
 
 // rowptr of CSR(D^T) at the first beamlet of every CP (K + 1 values).
@@ -155,17 +193,6 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&F0, 2));
     VMAT_TRY(ar.get((char **)&obj_ws, objective_scratch_bytes(ctx->n_sm)));
     VMAT_TRY(ar.get((char **)&pr_ws, pricing_scratch_bytes(mlc)));
-    struct Pinned {
-        int32_t cp;
-        int32_t pad;
-        double price;
-    } *hp = nullptr;
-    VMAT_CUDA(cudaMallocHost(&hp, sizeof(Pinned)));
-    struct FreeHost {
-        void *p;
-        ~FreeHost() { cudaFreeHost(p); }
-    } fh{hp};
-
     const long long launches0 = g_launches.load();
     PhaseTimer tm(stats != nullptr, s);
     cudaEvent_t t0, t1;
@@ -200,79 +227,100 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     std::vector<int64_t> cpo(K + 1);
     VMAT_CUDA(cudaMemcpyAsync(cpo.data(), cpo_dev, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
-    std::vector<char> occ_host(K, 0);
     vmat_voxels vox_c = *vox;
     vox_c.struct_id = sid_c;
+    int bb_extra = 0;
 
-    std::vector<int32_t> cps_host;
-    int stop = VMAT_STOP_COUNT;
-    int bb_total = 0;
+    int32_t *ctl;
+    VMAT_TRY(ar.get(&ctl, CTL_N));
+    VMAT_CUDA(cudaMemsetAsync(ctl, 0, CTL_N * sizeof(int32_t), s));
+    const int n_cap = std::min(std::max(n_apertures, 1), 96);
+    void *mp_ws;
+    VMAT_TRY(ar.get((char **)&mp_ws, mp_workspace_bytes(n_cap)));
     int64_t spmv_launches = 0;
-    double pp1_bytes = 0.0, other_bytes = 0.0;
     const int vb = value_bytes(h.dtype);
     const double bytes_D_full = (double)h.D.nnz * (vb + 4) + 8.0 * (h.D.n_rows + 1) + 4.0 * J + 4.0 * V +
                                 (h.dtype == VMAT_FP8E4M3 ? 4.0 * J : 0.0);
+    int32_t *hctl;
+    VMAT_CUDA(cudaMallocHost(&hctl, CTL_N * sizeof(int32_t)));
+    struct FreeCtl {
+        int32_t *p;
+        ~FreeCtl() { cudaFreeHost(p); }
+    } fc{hctl};
 
     for (int t = 0; t < n_apertures; ++t) {
+        if (t + 1 > n_cap) { // past the persistent solver's limit: the host decides whether to go on
+            VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            VMAT_CUDA(cudaStreamSynchronize(s));
+            if (hctl[CTL_STOPPED]) break;
+        }
         // ---- PP1
         tm.mark(PH_PP1);
         if (NA > 0)
-            VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s));
+            VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s, ctl));
         tm.mark(PH_SPMV);
-        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, active, bpc, s));
+        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, active, bpc, s, ctl));
         ++spmv_launches;
-        { // the format's own bytes for the rows of the unoccupied CPs, plus g once
-            double b = 4.0 * V;
-            for (int kk = 0; kk < K; ++kk)
-                if (!occ_host[kk])
-                    b += (double)(cpo[kk + 1] - cpo[kk]) * (vb + 4) + bpc * (8.0 + 4.0) +
-                         (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
-            pp1_bytes += b;
-        }
-        // ---- PP2
+        // ---- PP2, and the commit (or the stop) on the device
         tm.mark(PH_PP2);
-        VMAT_TRY(price_apertures_impl(mlc, pi, occupied, leaves_all, best_cp, best_leaves, best_price, pr_ws, s));
-        VMAT_CUDA(cudaMemcpyAsync(&hp->cp, best_cp, 4, cudaMemcpyDeviceToHost, s));
-        VMAT_CUDA(cudaMemcpyAsync(&hp->price, best_price, 8, cudaMemcpyDeviceToHost, s));
-        VMAT_CUDA(cudaStreamSynchronize(s));
-        const int32_t k = hp->cp;
-        if (k < 0 || !(hp->price > 0.0)) {
-            stop = VMAT_STOP_PRICE;
-            break;
-        }
-        VMAT_CUDA(cudaMemsetAsync(occupied + k, 1, 1, s));
-        VMAT_CUDA(cudaMemsetAsync(active + k, 0, 1, s));
-        VMAT_CUDA(cudaMemcpyAsync(leaves_all + (size_t)k * NR * 2, best_leaves, (size_t)NR * 4,
-                                  cudaMemcpyDeviceToDevice, s));
-        VMAT_CUDA(cudaMemcpyAsync(leaves_seq + (size_t)t * NR * 2, best_leaves, (size_t)NR * 4,
-                                  cudaMemcpyDeviceToDevice, s));
-        VMAT_CUDA(cudaMemcpyAsync(cps_dev + t, best_cp, 4, cudaMemcpyDeviceToDevice, s));
-        cps_host.push_back(k);
-        occ_host[k] = 1;
+        VMAT_TRY(price_apertures_impl(mlc, pi, occupied, leaves_all, best_cp, best_leaves, best_price, pr_ws, s, ctl));
+        commit_aperture<<<1, 128, 0, s>>>(t, NR, best_cp, best_price, best_leaves, occupied, active, leaves_all,
+                                         leaves_seq, cps_dev, y, ctl);
+        VMAT_LAUNCH_CHECK();
         // ---- DA (Eq. 5)
         tm.mark(PH_DA);
-        VMAT_TRY(aperture_dose_impl(h, mlc, k, best_leaves, DA + 32 + (size_t)(t >> 2) * 128 + (t & 3), true, s,
-                                    wstride));
+        VMAT_TRY(aperture_dose_dev(h, mlc, cps_dev + t, best_leaves, DA + 32 + (size_t)(t >> 2) * 128 + (t & 3),
+                                   wstride, ctl, s));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
-        VMAT_CUDA(cudaMemsetAsync(y + t, 0, 4, s));
-        vmat_bb_report rep;
         if (NA > 0) {
-            VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, nullptr, nullptr, y, z_c, opts, F_offset,
-                                &rep, s));
-            bb_total += rep.iters;
+            if (t + 1 <= n_cap) {
+                VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, y, z_c, opts, F_offset, mp_ws,
+                                       ctl, ctl + CTL_BBITERS, s));
+            } else {
+                VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                VMAT_CUDA(cudaStreamSynchronize(s));
+                if (!hctl[CTL_STOPPED]) {
+                    vmat_bb_report rep;
+                    VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, nullptr, nullptr, y, z_c, opts,
+                                        F_offset, &rep, s));
+                    bb_extra += rep.iters;
+                }
+            }
         }
         tm.end();
     }
-    const int n_ap = (int)cps_host.size();
-    // ---- final dose D (A y) in FP32 and its objective
+    // ---- final dose D (A y) in FP32 and its objective (apertures not placed have cps = -1)
     tm.mark(PH_FINAL);
-    VMAT_TRY(aperture_fluence(mlc, n_ap, cps_dev, leaves_seq, y, x, s));
+    VMAT_TRY(aperture_fluence(mlc, n_apertures, cps_dev, leaves_seq, y, x, s));
     VMAT_TRY(dose_forward_impl(h, x, dose, false, s));
-    other_bytes += bytes_D_full;
     VMAT_TRY(objective_impl(V, dose, nullptr, vox, nullptr, nullptr, F_dev, 0.0, s));
     tm.end();
     VMAT_CUDA(cudaEventRecord(t1, s));
+    VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    const int n_ap = hctl[CTL_NAP];
+    const int stop = hctl[CTL_STOPPED] ? hctl[CTL_REASON] : VMAT_STOP_COUNT;
+    const int bb_total = hctl[CTL_BBITERS] + bb_extra;
+    std::vector<int32_t> cps_host(std::max(n_ap, 1));
+    if (n_ap > 0) VMAT_CUDA(cudaMemcpy(cps_host.data(), cps_dev, (size_t)n_ap * 4, cudaMemcpyDeviceToHost));
+    // the format's own bytes of each pricing pass (rows of the CPs unoccupied at that
+    // pass, plus g once) and of the final D x
+    double pp1_bytes = 0.0, other_bytes = bytes_D_full;
+    {
+        std::vector<char> occ(K, 0);
+        const int n_pp1 = n_ap + (stop == VMAT_STOP_PRICE ? 1 : 0);
+        for (int t = 0; t < n_pp1; ++t) {
+            double b = 4.0 * V;
+            for (int kk = 0; kk < K; ++kk)
+                if (!occ[kk])
+                    b += (double)(cpo[kk + 1] - cpo[kk]) * (vb + 4) + bpc * (8.0 + 4.0) +
+                         (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
+            pp1_bytes += b;
+            if (t < n_ap) occ[cps_host[t]] = 1;
+        }
+        spmv_launches = n_pp1;
+    }
 
     if (cps_out) {
         VMAT_CUDA(cudaMemcpyAsync(cps_out, cps_dev, (size_t)std::max(n_apertures, 0) * 4, cudaMemcpyDefault, s));

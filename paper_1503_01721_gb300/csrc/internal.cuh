@@ -115,8 +115,9 @@ inline Ddc *as_ddc(vmat_ddc h) { return reinterpret_cast<Ddc *>(h); }
 int value_bytes(vmat_dtype t);
 
 // SpMV on one CSR; x/y device.  cp_active/bpc restrict to rows of active CPs (may be null).
+// skip (may be null): a device flag; when set at run time the kernels do nothing.
 vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
-                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s);
+                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s, const int32_t *skip = nullptr);
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s);
 int spmv_n_configs();
 int spmv_default_config();
@@ -134,6 +135,9 @@ vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const 
 // otherwise write voxel space da[V] (zero where D has no row).
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
                                bool compact, cudaStream_t s, int64_t wstride = 0);
+// The same with the CP read from device memory (cp_dev) at run time; skip as for spmv_run.
+vmat_status aperture_dose_dev(const Ddc &h, const vmat_mlc *mlc, const int32_t *cp_dev, const int16_t *leaves,
+                              float *da, int64_t wstride, const int32_t *skip, cudaStream_t s);
 
 struct BBWork; // defined in mp_bb.cu
 // DA layout: column-major (DA[k * ld + i]) when wstride == 0 (copied once, with the
@@ -142,6 +146,13 @@ struct BBWork; // defined in mp_bb.cu
 // whose first 32 bytes of every 32-voxel tile hold the tile's labels (mp_write_labels).
 int64_t mp_wtile_stride(int32_t n_cap);
 vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, float *DA, cudaStream_t s);
+// Device-driven solve (persistent solver only, n_ap <= n_cap <= 96): no host synchronisation;
+// ws holds mp_workspace_bytes(n_cap) bytes; skip and iters_acc as in the solver's arguments.
+size_t mp_workspace_bytes(int32_t n_cap);
+vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
+                          const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
+                          const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
+                          int32_t *iters_acc, cudaStream_t s);
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);

@@ -79,6 +79,8 @@ struct MPArgs {
     int64_t n_wtiles; // 32-voxel warp tiles
     BBState *st;
     unsigned *bar_count, *bar_gen; // grid barrier of the persistent solver
+    const int32_t *skip;           // when non-null and set, the solve is skipped (device-driven plans)
+    int32_t *iters_acc;            // when non-null, the persistent solver adds its iteration count
     int32_t *status;
     vmat_bb_opts opts;
     double F_offset;
@@ -95,6 +97,7 @@ __device__ __forceinline__ float lo_of(const MPArgs &a, int k) { return a.lo ? a
 __device__ __forceinline__ float hi_of(const MPArgs &a, int k) { return a.hi ? a.hi[k] : INFINITY; }
 
 __global__ void mp_init_kernel(MPArgs a) {
+    if (a.skip && *a.skip) return;
     for (int k = threadIdx.x; k < a.n; k += blockDim.x) a.y[k] = fminf(fmaxf(a.y[k], lo_of(a, k)), hi_of(a, k));
     if (threadIdx.x == 0) {
         BBState s = {};
@@ -575,6 +578,7 @@ __device__ void solve_take_step(const MPArgs &a, const SolveSmem &S, double delt
 
 template <int NMAX>
 __global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
+    if (a.skip && *a.skip) return; // the same flag for every CTA: all return together
     constexpr int GMAX = NMAX / 4;
     extern __shared__ __align__(128) unsigned char sm_raw[];
     __shared__ PState ps;
@@ -758,6 +762,7 @@ __global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stag
             a.st->stop = ps.stop;
             a.st->iters = ps.t + 1;
             a.st->delta0 = ps.delta0;
+            if (a.iters_acc) *a.iters_acc += ps.t + 1;
         }
     }
     if (cta == 0 && !ok && tid == 0) {
@@ -953,72 +958,76 @@ static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 
 
 int64_t mp_wtile_stride(int32_t n_cap) { return MP_HEAD + (int64_t)((n_cap + 3) / 4) * 128; }
 
-vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
-                       int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
-                       float *z, const vmat_bb_opts *opts_in, double F_offset, vmat_bb_report *rep, cudaStream_t s) {
-    DeviceCtx *ctx;
-    VMAT_TRY(device_ctx(&ctx));
-    vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
-    if (opts_in) opts = *opts_in;
-    if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
-    if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
-    const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
+// Launch configuration of one solve with n apertures over V voxels.
+struct MPLaunch {
+    bool persistent;
+    SolveFn fn;
+    int stages, keep_in_l2, P, Pc;
+    size_t smem;
+};
 
-    const int64_t n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
-
-    // a column-major input is copied once into the warp-tile layout (with the labels)
-    Scratch conv;
-    if (wstride == 0) {
-        wstride = mp_wtile_stride(n_ap);
-        VMAT_TRY(conv.alloc((size_t)n_wtiles * wstride * sizeof(float), s));
-        const int64_t total = n_wtiles * wstride;
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
-        to_warp_tiles<<<g, 256, 0, s>>>(DA, ld, V, n_ap, struct_id, wstride, n_wtiles, static_cast<float *>(conv.ptr));
-        VMAT_LAUNCH_CHECK();
-        DA = static_cast<const float *>(conv.ptr);
-    }
-
-    // persistent solver (one cooperative launch) up to MP_NMAX apertures, else one
-    // launch per iteration reading DA from global memory
-    const int stages = solve_stages(n_ap);
-    const bool persistent = n_ap <= MP_NMAX && stages >= 2 && solve_smem(n_ap, stages) <= MP_SMEM_LIMIT;
-    SolveFn solve_fn = persistent ? solve_kernel_for(n_ap) : nullptr;
-    const size_t smem_pass = persistent ? solve_smem(n_ap, stages) : ldg_smem(n_ap);
-    const int keep_in_l2 = (double)n_wtiles * (double)wt_copy_bytes(n_ap) <= 64.0 * 1024 * 1024 ? 1 : 0;
+static vmat_status mp_set_attributes() {
     static bool attr = false;
-    if (!attr) {
-        for (int q = 1; q <= MP_NMAX / 8; ++q)
-            VMAT_CUDA(cudaFuncSetAttribute(solve_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           MP_SMEM_LIMIT));
-        VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
-        VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (attr) return VMAT_OK;
+    for (int q = 1; q <= MP_NMAX / 8; ++q)
+        VMAT_CUDA(cudaFuncSetAttribute(solve_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        MP_SMEM_LIMIT));
-        attr = true;
-    }
+    VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
+    VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
+    attr = true;
+    return VMAT_OK;
+}
+
+// Persistent solver (one cooperative launch) up to MP_NMAX apertures, else one
+// launch per iteration reading DA from global memory.
+static vmat_status mp_configure(int32_t V, int32_t n_ap, const DeviceCtx *ctx, MPLaunch *L) {
+    VMAT_TRY(mp_set_attributes());
+    const int64_t n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
+    const int32_t n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
+    L->stages = solve_stages(n_ap);
+    L->persistent = n_ap <= MP_NMAX && L->stages >= 2 && solve_smem(n_ap, L->stages) <= MP_SMEM_LIMIT;
+    L->fn = L->persistent ? solve_kernel_for(n_ap) : nullptr;
+    L->smem = L->persistent ? solve_smem(n_ap, L->stages) : ldg_smem(n_ap);
+    L->keep_in_l2 = (double)n_wtiles * (double)wt_copy_bytes(n_ap) <= 64.0 * 1024 * 1024 ? 1 : 0;
     int bps = 1;
-    if (persistent) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, solve_fn, MP_THREADS, smem_pass));
-    else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, smem_pass));
+    if (L->persistent) VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, L->fn, MP_THREADS, L->smem));
+    else VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mp_iter_ldg_kernel, MP_THREADS, L->smem));
     if (bps < 1) return set_error(VMAT_ECUDA, "mp_bb_solve: the solver kernel does not fit on an SM");
     // every CTA of the persistent grid must be resident at once (grid barriers)
-    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(persistent ? (n_wtiles + MP_NW - 1) / MP_NW : n_tiles,
-                                                                (int64_t)ctx->n_sm * bps));
-    const int Pc = std::max(1, std::min<int>(n_tiles, ctx->n_sm * 4));
+    L->P = (int)std::max<int64_t>(1, std::min<int64_t>(L->persistent ? (n_wtiles + MP_NW - 1) / MP_NW : n_tiles,
+                                                        (int64_t)ctx->n_sm * bps));
+    L->Pc = std::max(1, std::min<int>(n_tiles, ctx->n_sm * 4));
+    return VMAT_OK;
+}
 
-    Scratch ws;
-    const size_t bytes = 256 + (size_t)(n_ap + 1) * sizeof(double) + (size_t)n_ap * (sizeof(double) + sizeof(float)) +
-                         (size_t)P * (n_ap + 1) * sizeof(double) + (size_t)std::max(P, Pc) * sizeof(double) + 256;
-    VMAT_TRY(ws.alloc(bytes, s));
-    char *p = static_cast<char *>(ws.ptr);
-    MPArgs a;
+// Upper bound on co-resident CTAs of MP_THREADS threads (2048 threads per SM).
+static int mp_p_max(const DeviceCtx *ctx) { return ctx->n_sm * (2048 / MP_THREADS); }
+
+static size_t mp_ws_bytes(int n_cap, int p_max) {
+    return 256 + (size_t)(n_cap + 1) * sizeof(double) + (size_t)n_cap * (sizeof(double) + sizeof(float)) +
+           (size_t)p_max * (n_cap + 1) * sizeof(double) + (size_t)p_max * sizeof(double) + 256;
+}
+
+size_t mp_workspace_bytes(int32_t n_cap) {
+    DeviceCtx *ctx;
+    if (device_ctx(&ctx) != VMAT_OK) return 0;
+    return mp_ws_bytes(n_cap, mp_p_max(ctx));
+}
+
+static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float *DA, int64_t wstride, int32_t V,
+                         int32_t n_ap, const uint8_t *struct_id, const vmat_voxels *vox, const float *lo,
+                         const float *hi, float *y, float *z, const vmat_bb_opts &opts, double F_offset,
+                         const MPLaunch &L, const DeviceCtx *ctx) {
+    char *p = static_cast<char *>(ws);
     a.st = reinterpret_cast<BBState *>(p);
     a.bar_count = reinterpret_cast<unsigned *>(p + 192);
     a.bar_gen = reinterpret_cast<unsigned *>(p + 224);
     p += 256;
     a.G = reinterpret_cast<double *>(p); // [n + 1]: G, then F in the persistent solver
-    a.Gprev = a.G + n_ap + 1;
-    a.part = a.Gprev + n_ap;
-    a.cpart = a.part + (size_t)P * (n_ap + 1);
-    a.yprev = reinterpret_cast<float *>(a.cpart + std::max(P, Pc));
+    a.Gprev = a.G + n_cap + 1;
+    a.part = a.Gprev + n_cap;
+    a.cpart = a.part + (size_t)p_max * (n_cap + 1);
+    a.yprev = reinterpret_cast<float *>(a.cpart + p_max);
     a.DA = DA;
     a.wstride = wstride;
     a.V = V;
@@ -1032,37 +1041,99 @@ vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, con
     a.z = z;
     a.lo = lo;
     a.hi = hi;
-    a.P = P;
-    a.n_tiles = n_tiles;
-    a.n_wtiles = n_wtiles;
+    a.P = L.P;
+    a.n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
+    a.n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
     a.status = ctx->status;
     a.opts = opts;
     a.F_offset = F_offset;
+    a.skip = nullptr;
+    a.iters_acc = nullptr;
+}
+
+static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream_t s) {
+    mp_init_kernel<<<1, MP_THREADS, 0, s>>>(a);
+    VMAT_LAUNCH_CHECK();
+    int st_arg = L.stages, l2_arg = L.keep_in_l2;
+    void *args[] = {&a, &st_arg, &l2_arg};
+    VMAT_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(L.fn), dim3(L.P), dim3(MP_THREADS), args,
+                                          L.smem, s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return VMAT_OK;
+}
+
+vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
+                          const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
+                          const vmat_bb_opts *opts_in, double F_offset, void *ws, const int32_t *skip,
+                          int32_t *iters_acc, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
+    if (opts_in) opts = *opts_in;
+    if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
+    if (n_ap > n_cap) return set_error(VMAT_EINVAL, "mp_bb_enqueue: n_ap > n_cap");
+    MPLaunch L;
+    VMAT_TRY(mp_configure(V, n_ap, ctx, &L));
+    if (!L.persistent)
+        return set_error(VMAT_EUNSUPPORTED, "mp_bb_enqueue: %d apertures need the host-driven solver", n_ap);
+    MPArgs a;
+    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_ap, struct_id, vox, nullptr, nullptr, y, z, opts,
+                 F_offset, L, ctx);
+    a.skip = skip;
+    a.iters_acc = iters_acc;
+    return mp_launch_persistent(a, L, s);
+}
+
+vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
+                       int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                       float *z, const vmat_bb_opts *opts_in, double F_offset, vmat_bb_report *rep, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
+    if (opts_in) opts = *opts_in;
+    if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
+    if (ldg_smem(n_ap) > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "mp_bb_solve: too many apertures (%d)", n_ap);
+    const int64_t n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
+
+    // a column-major input is copied once into the warp-tile layout (with the labels)
+    Scratch conv;
+    if (wstride == 0) {
+        wstride = mp_wtile_stride(n_ap);
+        VMAT_TRY(conv.alloc((size_t)n_wtiles * wstride * sizeof(float), s));
+        const int64_t total = n_wtiles * wstride;
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 16));
+        to_warp_tiles<<<g, 256, 0, s>>>(DA, ld, V, n_ap, struct_id, wstride, n_wtiles, static_cast<float *>(conv.ptr));
+        VMAT_LAUNCH_CHECK();
+        DA = static_cast<const float *>(conv.ptr);
+    }
+    MPLaunch L;
+    VMAT_TRY(mp_configure(V, n_ap, ctx, &L));
+    const int p_max = std::max(mp_p_max(ctx), std::max(L.P, L.Pc));
+    Scratch ws;
+    VMAT_TRY(ws.alloc(mp_ws_bytes(n_ap, p_max), s));
+    MPArgs a;
+    mp_fill_args(a, ws.ptr, n_ap, p_max, DA, wstride, V, n_ap, struct_id, vox, lo, hi, y, z, opts, F_offset, L, ctx);
     const size_t smem_cauchy = (size_t)((n_ap + 3) & ~3) * 4 + 3 * 256 * 4;
 
     static thread_local BBState *host_st = nullptr;
     if (!host_st) VMAT_CUDA(cudaMallocHost(&host_st, sizeof(BBState)));
 
-    mp_init_kernel<<<1, MP_THREADS, 0, s>>>(a);
-    VMAT_LAUNCH_CHECK();
-    if (persistent) {
-        int st_arg = stages, l2_arg = keep_in_l2;
-        void *args[] = {&a, &st_arg, &l2_arg};
-        VMAT_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(solve_fn), dim3(P), dim3(MP_THREADS),
-                                              args, smem_pass, s));
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (L.persistent) {
+        VMAT_TRY(mp_launch_persistent(a, L, s));
         VMAT_CUDA(cudaMemcpyAsync(host_st, a.st, sizeof(BBState), cudaMemcpyDeviceToHost, s));
         VMAT_CUDA(cudaStreamSynchronize(s));
     } else {
+        mp_init_kernel<<<1, MP_THREADS, 0, s>>>(a);
+        VMAT_LAUNCH_CHECK();
         int launched = 0;
         while (launched < opts.max_iter) {
             const int chunk = launched == 0 ? 1 : std::min(MP_CHUNK, opts.max_iter - launched);
             for (int c = 0; c < chunk; ++c) {
-                mp_iter_ldg_kernel<<<P, MP_THREADS, smem_pass, s>>>(a);
+                mp_iter_ldg_kernel<<<L.P, MP_THREADS, L.smem, s>>>(a);
                 g_launches.fetch_add(1, std::memory_order_relaxed);
                 if (launched + c == 0) {
-                    mp_cauchy_pass_kernel<<<Pc, MP_THREADS, smem_cauchy, s>>>(a);
-                    mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a, Pc);
+                    mp_cauchy_pass_kernel<<<L.Pc, MP_THREADS, smem_cauchy, s>>>(a);
+                    mp_cauchy_step_kernel<<<1, MP_THREADS, 0, s>>>(a, L.Pc);
                     g_launches.fetch_add(2, std::memory_order_relaxed);
                 }
             }

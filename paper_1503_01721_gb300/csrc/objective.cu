@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(OBJ_THREADS)
     objective_kernel(int32_t n, const float *__restrict__ z, const int32_t *__restrict__ idx,
                      const uint8_t *__restrict__ sid, const float *T, const float *wo, const float *wu,
                      int32_t n_struct, float *g, float *g_scatter, double *partial, unsigned *counter, double *F,
-                     double F_offset) {
+                     double F_offset, const int32_t *skip) {
+    if (skip && *skip) return;
     __shared__ float sT[256], sO[256], sU[256];
     __shared__ double sh[OBJ_THREADS / 32];
     __shared__ bool last;
@@ -106,14 +107,15 @@ static int obj_grid(int64_t n, int n_sm) {
 size_t objective_scratch_bytes(int n_sm) { return 64 + (size_t)n_sm * 4 * sizeof(double); }
 
 vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
-                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s) {
+                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
+                              const int32_t *skip) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     const int grid = obj_grid(n, ctx->n_sm);
     unsigned *counter = reinterpret_cast<unsigned *>(ws);
     double *partial = reinterpret_cast<double *>(static_cast<char *>(ws) + 64);
     objective_kernel<<<grid, OBJ_THREADS, 0, s>>>(n, z, idx, vox->struct_id, vox->T, vox->w_over, vox->w_under,
-                                                  vox->n_struct, g, g_scatter, partial, counter, F, F_offset);
+                                                  vox->n_struct, g, g_scatter, partial, counter, F, F_offset, skip);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }
@@ -125,7 +127,7 @@ vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const 
     Scratch ws;
     VMAT_TRY(ws.alloc(objective_scratch_bytes(ctx->n_sm), s));
     VMAT_CUDA(cudaMemsetAsync(ws.ptr, 0, 64, s));
-    return objective_impl_ws(n, z, idx, vox, g, g_scatter, F, F_offset, ws.ptr, s);
+    return objective_impl_ws(n, z, idx, vox, g, g_scatter, F, F_offset, ws.ptr, s, nullptr);
 }
 
 vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s) {

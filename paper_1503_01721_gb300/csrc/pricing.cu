@@ -57,7 +57,9 @@ __device__ int nearest_occupied(const PricingGeom &g, const uint8_t *occupied, i
 
 __global__ void __launch_bounds__(PR_WARPS * 32)
     price_rows_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
-                      const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok) {
+                      const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok,
+                      const int32_t *skip) {
+    if (skip && *skip) return;
     extern __shared__ double sP[]; // PR_WARPS x (n_cols + 1)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
@@ -127,7 +129,8 @@ constexpr int CP_THREADS = 1024;
 __global__ void __launch_bounds__(CP_THREADS)
     price_cps_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const double *__restrict__ rb_v,
                      const int16_t *__restrict__ rb_lr, const uint8_t *__restrict__ rb_ok, int32_t *best_cp,
-                     int16_t *best_leaves, double *best_price) {
+                     int16_t *best_leaves, double *best_price, const int32_t *skip) {
+    if (skip && *skip) return;
     __shared__ double sv[CP_THREADS / 32];
     __shared__ int sk[CP_THREADS / 32];
     __shared__ int kwin;
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(CP_THREADS)
 
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                                  int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const int32_t *skip) {
     if (mlc->n_arcs > MAX_ARCS) return set_error(VMAT_EUNSUPPORTED, "price_apertures: more than %d arcs", MAX_ARCS);
     PricingGeom g;
     g.K = mlc->K;
@@ -207,9 +210,9 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         attr_set = true;
     }
     const int64_t blocks = (rows + PR_WARPS - 1) / PR_WARPS;
-    price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok);
+    price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok, skip);
     VMAT_LAUNCH_CHECK();
-    price_cps_kernel<<<1, CP_THREADS, 0, s>>>(g, occupied, rb_v, rb_lr, rb_ok, best_cp, best_leaves, best_price);
+    price_cps_kernel<<<1, CP_THREADS, 0, s>>>(g, occupied, rb_v, rb_lr, rb_ok, best_cp, best_leaves, best_price, skip);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }
@@ -262,7 +265,7 @@ extern "C" vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, con
     cudaStream_t s = as_stream(stream);
     Scratch ws;
     VMAT_TRY(ws.alloc(pricing_scratch_bytes(mlc), s));
-    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s);
+    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s, nullptr);
 }
 
 // Same computation as price_apertures with the fixed device scratch above: no
@@ -284,5 +287,5 @@ extern "C" vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float 
     void *ws = nullptr;
     VMAT_TRY(noalloc_scratch(&ws));
     return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws,
-                                as_stream(stream));
+                                as_stream(stream), nullptr);
 }

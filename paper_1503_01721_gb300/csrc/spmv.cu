@@ -41,6 +41,7 @@ struct SpmvParams {
     int64_t nnz;
     float *carry_val;
     int32_t *status;
+    const int32_t *skip; // when non-null and set, the kernel does nothing
 };
 
 template <typename VT> struct Vals;
@@ -101,6 +102,7 @@ __device__ __forceinline__ void store_row(const SpmvParams &p, int32_t r, float 
 
 template <int THREADS, int E, int STAGES, typename VT>
 __global__ void __launch_bounds__(THREADS) spmv_tile_kernel(SpmvParams p) {
+    if (p.skip && *p.skip) return;
     using S = TileShape<THREADS, E, STAGES, VT>;
     constexpr int TILE = S::TILE, Q = S::Q, NW = S::NW;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -359,10 +361,12 @@ struct RowParams {
     const uint8_t *cp_active; // skip rows r with !cp_active[r / bpc], or null
     int32_t bpc;
     int32_t n_rows;
+    const int32_t *skip; // when non-null and set, the kernel does nothing
 };
 
 template <int THREADS, int UNROLL, typename VT>
 __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
+    if (p.skip && *p.skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
@@ -605,7 +609,7 @@ vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s) {
 }
 
 vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
-                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s) {
+                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s, const int32_t *skip) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     Launch L;
@@ -622,6 +626,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
         p.cp_active = cp_active;
         p.bpc = bpc;
         p.n_rows = m.n_rows;
+        p.skip = skip;
         const int64_t warps = std::max<int64_t>(1, m.n_rows);
         const int64_t want = (warps * 32 + L.threads - 1) / L.threads;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * L.blocks_per_sm));
@@ -659,6 +664,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
     p.nnz = m.nnz;
     p.carry_val = m.carry_val;
     p.status = ctx->status;
+    p.skip = skip;
     const int grid = std::max(1, std::min(m.n_tiles, ctx->n_sm * L.blocks_per_sm));
     L.tile<<<grid, L.threads, L.smem, s>>>(p);
     VMAT_LAUNCH_CHECK();
