@@ -441,6 +441,76 @@ def run_mp_only(args):
     return out
 
 
+def run_batch(args):
+    """Batched plans: every plan of a batch workload resident in HBM, then timed
+    runs of the whole batch (one CUDA graph per run) against the same plans run one
+    after another through cg_plan.  Aggregate GB/s = the algorithmic bytes of every
+    plan's D^T g and final D x passes over the wall time."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1503_01721_gb300 import api, roofline
+    import __graft_entry__
+
+    __graft_entry__.build()
+    dtype = args.dtype
+    specs = synth.batch_specs(args.workload)
+    plans, keep, nnz = [], [], 0
+    t0 = time.time()
+    for sp in specs:
+        c = synth.make_plan_case(sp)
+        h = api.ddc_load_coo(c.V, c.J, torch.from_numpy(c.vox), torch.from_numpy(c.blt), torch.from_numpy(c.val))
+        api.ddc_build(h, dtype)
+        vox = api.VoxelParams.from_numpy(c.structs)
+        plans.append((h, c.mlc, vox, sp.n_apertures))
+        keep.append(c.mlc)
+        nnz += c.nnz
+        del c
+    log(f"[batch] {len(specs)} plans, {nnz} nonzeros resident in {time.time() - t0:.1f}s")
+    batch = api.Batch(plans)
+    info = batch.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Fb, stb = batch.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    bytes_run = sum(s["pp1_spmv_bytes"] + s["other_spmv_bytes"] for s in stb)
+    # the same plans one after another
+    for h, mlc, vox, n in plans:
+        api.cg_plan(h, mlc, vox, n)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        Fs, sts = [], []
+        for h, mlc, vox, n in plans:
+            F, st = api.cg_plan(h, mlc, vox, n)
+            Fs.append(F)
+            sts.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / args.steps
+    bytes_seq = sum(s["pp1_spmv_bytes"] + s["other_spmv_bytes"] for s in sts)
+    rel = [abs(a - b) / max(abs(b), 1e-30) for a, b in zip(Fb, Fs)]
+    peaks = roofline.measured_peaks()
+    out = {"mode": "batch", "workload": args.workload, "n_plans": len(specs), "nnz": nnz, "dtype": dtype,
+           "batched": {"ms_per_run": round(ms_batch, 3), "gbs": round(bytes_run / ms_batch / 1e6, 1),
+                       "frac_of_hbm": round(bytes_run / ms_batch / 1e6 / peaks["hbm_gbs"], 4)},
+           "one_by_one": {"ms_per_run": round(ms_seq, 3), "gbs": round(bytes_seq / ms_seq / 1e6, 1)},
+           "speedup": round(ms_seq / ms_batch, 3), "bb_iters": sum(s["bb_iters_total"] for s in stb),
+           "apertures": [s["n_apertures"] for s in stb], "F_rel_diff_max": max(rel),
+           "info": {k: v for k, v in info.items()}}
+    batch.close()
+    for h, _, _, _ in plans:
+        api.ddc_free(h)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -465,10 +535,11 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS))
-    ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS) + ["cfg5", "cfg5q", "batch_small"])
+    ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp", "batch"],
                     help="spmv: only build and run D^T g and D x a few times (profiling driver); "
-                         "mp: fixed-length master-problem solves")
+                         "mp: fixed-length master-problem solves; batch: a batch workload (cfg5, cfg5q, "
+                         "batch_small) batched against one by one")
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     args = ap.parse_args()
@@ -479,6 +550,8 @@ def main():
         out = run_spmv_only(args) if rank == 0 else None
     elif args.mode == "mp":
         out = run_mp_only(args) if rank == 0 else None
+    elif args.mode == "batch":
+        out = run_batch(args) if rank == 0 else None
     else:
         out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

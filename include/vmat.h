@@ -269,6 +269,54 @@ vmat_status cg_plan(vmat_ddc h, const vmat_mlc *mlc, const vmat_voxels *vox, int
                     const vmat_bb_opts *opts, int32_t *cps_out, int16_t *leaves_out, float *y_out, float *dose_out,
                     double *F_out, vmat_plan_stats *stats, void *stream);
 
+/* ---- Batched plans (independent plans advanced together) ----------------- */
+
+/* One plan of a batch.  ddc: built with CSR(D) and CSR(D^T); every plan of a
+ * batch stores its values in the same type.  mlc, vox: as for cg_plan (vox over
+ * the plan's V voxels, device arrays).  n_apertures: 0 .. min(K, 96). */
+typedef struct {
+    vmat_ddc ddc;
+    const vmat_mlc *mlc;
+    const vmat_voxels *vox;
+    int32_t n_apertures;
+} vmat_plan_desc;
+
+typedef struct vmat_batch_s *vmat_batch; /* opaque; owns every plan's device state */
+
+typedef struct {
+    int32_t n_plans;
+    int32_t max_apertures;    /* iterations of the batched loop */
+    int32_t spmv_cfg;         /* warp-row SpMV configuration chosen by the autotuner */
+    int32_t graph;            /* 1: the run is one CUDA graph launch */
+    int64_t graph_nodes;      /* nodes of that graph (0 without a graph) */
+    int64_t device_bytes;     /* device memory the batch holds (plan state, tables) */
+    double autotune_ms[16];   /* D^T g time of each configuration tried (0 = not a candidate) */
+} vmat_batch_info;
+
+/* Column generation (as cg_plan) for n_plans independent plans (1 .. 64)
+ * advanced together: iteration t of every plan runs in shared launches (the
+ * gradient, D^T g, pricing, the commit, the aperture dose and a persistent
+ * master-problem solver whose CTAs are split among the plans), and the whole run
+ * is recorded once as a CUDA graph.  The batched D^T g configuration is chosen
+ * by timing every warp-row configuration on the batch.  The handles and the
+ * descriptors' arrays must stay valid until vmat_batch_free.  opts NULL =
+ * defaults.  Synchronises. */
+vmat_status vmat_batch_create(int32_t n_plans, const vmat_plan_desc *plans, const vmat_bb_opts *opts, void *stream,
+                              vmat_batch *out);
+
+/* Runs every plan once (one graph launch) and synchronises.  F_out: host double
+ * [n_plans] or NULL; stats: host [n_plans] or NULL (t_total_ms is the whole
+ * batch; phase times are 0). */
+vmat_status vmat_batch_run(vmat_batch b, double *F_out, vmat_plan_stats *stats, void *stream);
+
+/* Plan p's results of the last run, as cg_plan's outputs (host or device
+ * pointers, any may be NULL).  Synchronises. */
+vmat_status vmat_batch_result(vmat_batch b, int32_t p, int32_t *cps_out, int16_t *leaves_out, float *y_out,
+                              float *dose_out, void *stream);
+
+vmat_status vmat_batch_info_get(vmat_batch b, vmat_batch_info *info);
+vmat_status vmat_batch_free(vmat_batch b);
+
 /* ---- Diagnostics ---------------------------------------------------------- */
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -54,6 +54,15 @@ class PlanStats(ctypes.Structure):
                 ("bb_iters_total", c_i32), ("stop_reason", c_i32), ("kernel_launches", c_i64)]
 
 
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("ddc", c_vp), ("mlc", ctypes.POINTER(Mlc)), ("vox", ctypes.POINTER(Voxels)), ("n_apertures", c_i32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_plans", c_i32), ("max_apertures", c_i32), ("spmv_cfg", c_i32), ("graph", c_i32),
+                ("graph_nodes", c_i64), ("device_bytes", c_i64), ("autotune_ms", c_f64 * 16)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/vmat.h
 SIGNATURES = {
     "ddc_load_coo": (c_i32, [c_i32, c_i32, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, ctypes.POINTER(c_vp)]),
@@ -72,6 +81,12 @@ SIGNATURES = {
                             ctypes.POINTER(BBOpts), ctypes.POINTER(BBReport), c_vp]),
     "cg_plan": (c_i32, [c_vp, ctypes.POINTER(Mlc), ctypes.POINTER(Voxels), c_i32, ctypes.POINTER(BBOpts),
                         c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_f64), ctypes.POINTER(PlanStats), c_vp]),
+    "vmat_batch_create": (c_i32, [c_i32, ctypes.POINTER(PlanDesc), ctypes.POINTER(BBOpts), c_vp,
+                                  ctypes.POINTER(c_vp)]),
+    "vmat_batch_run": (c_i32, [c_vp, ctypes.POINTER(c_f64), ctypes.POINTER(PlanStats), c_vp]),
+    "vmat_batch_result": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "vmat_batch_info_get": (c_i32, [c_vp, ctypes.POINTER(BatchInfo)]),
+    "vmat_batch_free": (c_i32, [c_vp]),
     "vmat_last_error": (ctypes.c_char_p, []),
     "vmat_device_status": (c_i32, [c_i32]),
     "vmat_version": (ctypes.c_char_p, []),

@@ -223,6 +223,73 @@ def cg_plan(h: int, mlc, vox: VoxelParams, n_apertures: int, opts: BBOptions | N
     return F.value, stats
 
 
+class Batch:
+    """Independent plans advanced together (vmat_batch_*): one CUDA graph per run.
+
+    ``plans`` is a list of (ddc_handle, mlc, VoxelParams, n_apertures).  The
+    handles, MLC arrays and voxel tensors must outlive the batch.
+    """
+
+    def __init__(self, plans, opts: BBOptions | None = None, stream=None):
+        self._keep = []
+        descs = (_lib.PlanDesc * len(plans))()
+        for i, (h, mlc, vox, n_ap) in enumerate(plans):
+            m = _MlcC(mlc)
+            vc = vox.c()
+            self._keep += [m, vc, vox]
+            descs[i] = _lib.PlanDesc(ctypes.c_void_p(h), ctypes.pointer(m.s), ctypes.pointer(vc), int(n_ap))
+        self._descs = descs
+        self.n = len(plans)
+        self._V = [int(v.struct_id.numel()) for _, _, v, _ in plans]
+        self._ap = [int(p[3]) for p in plans]
+        self._rows = [int(p[1].n_rows) for p in plans]
+        o = _bb_opts(opts)
+        hb = ctypes.c_void_p()
+        check("vmat_batch_create", _lib.load().vmat_batch_create(
+            len(plans), descs, ctypes.byref(o) if o is not None else None, _stream(stream), ctypes.byref(hb)))
+        self.h = hb.value
+
+    def run(self, stream=None):
+        """Run every plan once; returns (F list, stats list)."""
+        F = (ctypes.c_double * self.n)()
+        st = (_lib.PlanStats * self.n)()
+        check("vmat_batch_run", _lib.load().vmat_batch_run(ctypes.c_void_p(self.h), F, st, _stream(stream)))
+        stats = []
+        for i in range(self.n):
+            d = {f: getattr(st[i], f) for f, _ in st[i]._fields_}
+            d["stop"] = _lib.STOP_NAMES.get(d["stop_reason"], d["stop_reason"])
+            stats.append(d)
+        return list(F), stats
+
+    def result(self, i: int, cps_out=None, leaves_out=None, y_out=None, dose_out=None, stream=None):
+        n, nr, V = self._ap[i], self._rows[i], self._V[i]
+
+        def anyp(t, dt, k, name):
+            return None if t is None else _ptr(t, dt, k, name, device=False)
+        check("vmat_batch_result", _lib.load().vmat_batch_result(
+            ctypes.c_void_p(self.h), int(i), anyp(cps_out, torch.int32, n, "cps_out"),
+            anyp(leaves_out, torch.int16, n * nr * 2, "leaves_out"), anyp(y_out, torch.float32, n, "y_out"),
+            anyp(dose_out, torch.float32, V, "dose_out"), _stream(stream)))
+
+    def info(self) -> dict:
+        inf = _lib.BatchInfo()
+        check("vmat_batch_info_get", _lib.load().vmat_batch_info_get(ctypes.c_void_p(self.h), ctypes.byref(inf)))
+        d = {f: getattr(inf, f) for f, _ in inf._fields_ if f != "autotune_ms"}
+        d["autotune_ms"] = {c: inf.autotune_ms[c] for c in range(16) if inf.autotune_ms[c] > 0}
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().vmat_batch_free(ctypes.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def device_status(reset: bool = False) -> int:
     return int(_lib.load().vmat_device_status(int(reset)))
 

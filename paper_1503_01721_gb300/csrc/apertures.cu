@@ -26,6 +26,22 @@ __device__ __forceinline__ float load_val(const void *val, int64_t e, vmat_dtype
     return __half2float(*reinterpret_cast<__half *>(&hr));
 }
 
+template <typename VT> struct StoredVal;
+template <> struct StoredVal<float> {
+    static __device__ __forceinline__ float get(const void *v, int64_t e) { return static_cast<const float *>(v)[e]; }
+};
+template <> struct StoredVal<__nv_bfloat16> {
+    static __device__ __forceinline__ float get(const void *v, int64_t e) {
+        return __uint_as_float((uint32_t) static_cast<const uint16_t *>(v)[e] << 16);
+    }
+};
+template <> struct StoredVal<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float get(const void *v, int64_t e) {
+        __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t) static_cast<const uint8_t *>(v)[e], __NV_E4M3);
+        return __half2float(*reinterpret_cast<__half *>(&hr));
+    }
+};
+
 __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                      const void *__restrict__ val, vmat_dtype dt, const float *__restrict__ scale,
                                      int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp_arg,
@@ -63,6 +79,65 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
             row_ids ? row_ids[row] : (wstride ? (int64_t)(row >> 5) * wstride + ((row & 31) << 2) : row);
         da[o] = acc;
     }
+}
+
+// Batched Eq. 5 for aperture t of every plan: global row g is compact row g - off[p]
+// of plan p; the CP is cps[t] and the leaves best_leaves (device), the column goes
+// to the plan's warp-tile DA.  One thread per row, plan looked up by binary search.
+template <typename VT>
+__global__ void aperture_dose_batched_kernel(const DaPlan *__restrict__ plans, const int64_t *__restrict__ off,
+                                             int32_t n_plans, int64_t total, int32_t t) {
+    __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n_plans; i += blockDim.x) soff[i] = off[i];
+    __syncthreads();
+    for (int64_t gr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gr < total;
+         gr += (int64_t)gridDim.x * blockDim.x) {
+        int a = 0, b = n_plans;
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if (soff[m] <= gr) a = m;
+            else b = m;
+        }
+        const DaPlan &P = plans[a];
+        if (P.skip && *P.skip) continue;
+        const int32_t row = (int32_t)(gr - soff[a]);
+        const int32_t bpc = P.n_rrows * P.n_cols;
+        const int32_t cp = P.cps[t];
+        const int32_t j0 = cp * bpc, j1 = j0 + bpc;
+        int64_t lo = P.rowptr[row], hi = P.rowptr[row + 1];
+        while (lo < hi) { // first entry with column >= j0
+            const int64_t mid = (lo + hi) >> 1;
+            if (P.col[mid] < j0) lo = mid + 1;
+            else hi = mid;
+        }
+        float acc = 0.f;
+        const int64_t end = P.rowptr[row + 1];
+        for (int64_t e = lo; e < end; ++e) {
+            const int32_t j = P.col[e];
+            if (j >= j1) break;
+            const int32_t loc = j - j0, r = loc / P.n_cols, c = loc - r * P.n_cols;
+            if (c >= P.leaves[2 * r] && c < P.leaves[2 * r + 1]) {
+                float v = StoredVal<VT>::get(P.val, e);
+                if (P.scale) v *= P.scale[j];
+                acc += v;
+            }
+        }
+        P.DA[32 + (int64_t)(t >> 2) * 128 + (t & 3) + (int64_t)(row >> 5) * P.wstride + ((row & 31) << 2)] = acc;
+    }
+}
+
+vmat_status aperture_dose_batched(vmat_dtype dt, const DaPlan *plans, const int64_t *off, int32_t n_plans,
+                                  int64_t total, int32_t t, cudaStream_t s) {
+    if (total <= 0) return VMAT_OK;
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ctx->n_sm * 8));
+    if (dt == VMAT_F32) aperture_dose_batched_kernel<float><<<grid, 256, 0, s>>>(plans, off, n_plans, total, t);
+    else if (dt == VMAT_BF16)
+        aperture_dose_batched_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(plans, off, n_plans, total, t);
+    else aperture_dose_batched_kernel<__nv_fp8_e4m3><<<grid, 256, 0, s>>>(plans, off, n_plans, total, t);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
 }
 
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,

@@ -47,36 +47,13 @@ __global__ void fill_i32(int32_t *p, int32_t n, int32_t v) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
-// Plan control words on the device.
-enum { CTL_STOPPED = 0, CTL_REASON, CTL_NAP, CTL_BBITERS, CTL_N };
-
 // Commits the aperture priced at iteration t, or stops the plan when no CP has a
-// positive price (Section 2.1).  One block; every thread reads the same inputs.
+// positive price (Section 2.1).  One block.
 __global__ void commit_aperture(int32_t t, int32_t NR, const int32_t *best_cp, const double *best_price,
                                 const int16_t *best_leaves, uint8_t *occupied, uint8_t *active, int16_t *leaves_all,
                                 int16_t *leaves_seq, int32_t *cps, float *y, int32_t *ctl) {
-    if (ctl[CTL_STOPPED]) return;
-    const int32_t k = *best_cp;
-    const bool stop = k < 0 || !(*best_price > 0.0);
-    __syncthreads(); // every thread has read the stop flag before it changes
-    if (stop) {
-        if (threadIdx.x == 0) {
-            ctl[CTL_STOPPED] = 1;
-            ctl[CTL_REASON] = VMAT_STOP_PRICE;
-        }
-        return;
-    }
-    for (int r = threadIdx.x; r < 2 * NR; r += blockDim.x) {
-        leaves_all[(int64_t)k * 2 * NR + r] = best_leaves[r];
-        leaves_seq[(int64_t)t * 2 * NR + r] = best_leaves[r];
-    }
-    if (threadIdx.x == 0) {
-        occupied[k] = 1;
-        active[k] = 0;
-        cps[t] = k;
-        y[t] = 0.f;
-        ctl[CTL_NAP] = t + 1;
-    }
+    commit_aperture_block(t, NR, best_cp, best_price, best_leaves, occupied, active, leaves_all, leaves_seq, cps, y,
+                          ctl);
 }
 
 // rowptr of CSR(D^T) at the first beamlet of every CP (K + 1 values).

@@ -125,6 +125,81 @@ int32_t spmv_config_tile(int cfg);
 
 vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compact, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched phases: one launch covers every plan of a batch.  Work item g of a
+// launch belongs to plan p with off[p] <= g < off[p + 1] (device prefix arrays).
+// ---------------------------------------------------------------------------
+constexpr int VMAT_MAX_BATCH = 64;
+
+struct SpmvPlan { // one plan's matrix and vectors in a batched warp-row SpMV
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+    const float *x;
+    float *y;
+    const float *row_scale;   // or null
+    const int32_t *row_ids;   // or null
+    const uint8_t *cp_active; // or null
+    const int32_t *skip;      // or null
+    int32_t bpc;
+    int32_t n_rows;
+};
+bool spmv_batched_config(int cfg);
+
+constexpr int MAX_ARCS = 64;
+struct PricingGeom {
+    int32_t K, n_rows, n_cols, travel, n_arcs;
+    int32_t arc_first[MAX_ARCS + 1];
+};
+vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g);
+size_t pricing_scratch_bytes(const vmat_mlc *mlc);
+
+struct PricePlan { // one plan's pricing inputs, per-row scratch and results
+    PricingGeom g;
+    const float *pi;
+    const uint8_t *occupied;
+    const int16_t *leaves;
+    double *rb_v;
+    int16_t *rb_lr;
+    uint8_t *rb_ok;
+    int32_t *best_cp;
+    int16_t *best_leaves;
+    double *best_price;
+    const int32_t *skip;
+};
+struct DaPlan { // one plan's CSR(D) and warp-tile DA for the batched aperture dose
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+    const float *scale; // FP8 column scale, or null
+    int32_t n_rrows, n_cols;
+    const int32_t *cps;         // the aperture's CP is cps[t]
+    const int16_t *leaves;      // its leaves [n_rrows][2]
+    float *DA;
+    int64_t wstride;
+    const int32_t *skip;
+};
+// off: prefix of the compact row counts over the plans.
+vmat_status aperture_dose_batched(vmat_dtype dt, const DaPlan *plans, const int64_t *off, int32_t n_plans,
+                                  int64_t total, int32_t t, cudaStream_t s);
+
+struct ObjPlan { // one plan's compact dose and labels for the batched gradient
+    const float *z;
+    const int32_t *idx;
+    const uint8_t *sid;
+    const float *T, *wo, *wu;
+    float *g_scatter;
+    const int32_t *skip;
+};
+vmat_status objective_grad_batched(const ObjPlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
+                                   cudaStream_t s);
+
+// off: prefix of K * n_rows over the plans (total entries); max_cols: largest n_cols.
+vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
+                                    int32_t max_cols, cudaStream_t s);
+vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
+                              int64_t total_rows, cudaStream_t s);
+
 // Objective over n voxels.  idx (may be null): voxel i of z is voxel idx[i] of struct_id.
 // g_scatter (may be null): write g[i] to g_scatter[idx[i]] instead of g[i].
 vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
@@ -153,6 +228,18 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
                           const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
                           const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
                           int32_t *iters_acc, cudaStream_t s);
+// Batched master problems (persistent solver, one cooperative launch for all plans).
+// Per-plan arguments are an opaque mp_args_bytes() record filled by mp_fill_plan_args
+// (ws: mp_workspace_bytes(n_cap) bytes); mp_batched_grid splits the resident CTAs
+// among plans of V_list[p] compact voxels for n apertures.
+size_t mp_args_bytes();
+vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
+                              const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
+                              const vmat_bb_opts *opts, double F_offset, const int32_t *skip, int32_t *iters_acc);
+vmat_status mp_batched_grid(int32_t n, const int64_t *V_list, int32_t n_plans, int32_t *cta_start, int32_t *grid,
+                            int32_t *stages, size_t *smem);
+vmat_status mp_bb_enqueue_batched(const void *args, const int32_t *cta_start, int32_t n_plans, int32_t n,
+                                  int32_t grid, int32_t stages, size_t smem, int keep_in_l2, cudaStream_t s);
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                        float *z, const vmat_bb_opts *opts, double F_offset, vmat_bb_report *rep, cudaStream_t s);
@@ -235,5 +322,40 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL; // ~2 s at 2 GHz
+
+// ---------------------------------------------------------------------------
+// Device-driven column generation: per-plan control words and the commit step
+// ---------------------------------------------------------------------------
+enum { CTL_STOPPED = 0, CTL_REASON, CTL_NAP, CTL_BBITERS, CTL_N };
+
+// Commits the aperture priced at iteration t (best_cp, best_leaves), or sets the
+// stop flag when no CP has a positive price (Section 2.1).  Called by one block.
+__device__ __forceinline__ void commit_aperture_block(int32_t t, int32_t NR, const int32_t *best_cp,
+                                                      const double *best_price, const int16_t *best_leaves,
+                                                      uint8_t *occupied, uint8_t *active, int16_t *leaves_all,
+                                                      int16_t *leaves_seq, int32_t *cps, float *y, int32_t *ctl) {
+    if (ctl[CTL_STOPPED]) return;
+    const int32_t k = *best_cp;
+    const bool stop = k < 0 || !(*best_price > 0.0);
+    __syncthreads(); // every thread has read the stop flag before it changes
+    if (stop) {
+        if (threadIdx.x == 0) {
+            ctl[CTL_STOPPED] = 1;
+            ctl[CTL_REASON] = VMAT_STOP_PRICE;
+        }
+        return;
+    }
+    for (int r = threadIdx.x; r < 2 * NR; r += blockDim.x) {
+        leaves_all[(int64_t)k * 2 * NR + r] = best_leaves[r];
+        leaves_seq[(int64_t)t * 2 * NR + r] = best_leaves[r];
+    }
+    if (threadIdx.x == 0) {
+        occupied[k] = 1;
+        active[k] = 0;
+        cps[t] = k;
+        y[t] = 0.f;
+        ctl[CTL_NAP] = t + 1;
+    }
+}
 
 } // namespace vmat

@@ -576,20 +576,18 @@ __device__ void solve_take_step(const MPArgs &a, const SolveSmem &S, double delt
     __syncwarp();
 }
 
+// The whole solve as CTA `cta` of the n_cta CTAs working on this problem (sm:
+// the 128-byte aligned dynamic shared memory).
 template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
-    if (a.skip && *a.skip) return; // the same flag for every CTA: all return together
+__device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned cta, const unsigned n_cta, int stages,
+                                              int keep_in_l2, unsigned char *sm) {
     constexpr int GMAX = NMAX / 4;
-    extern __shared__ __align__(128) unsigned char sm_raw[];
     __shared__ PState ps;
     __shared__ FF shff[MP_NW];
     __shared__ int abort_s;
-    // align the staging area explicitly: static shared memory may shift the dynamic region
-    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
     const int n = a.n;
     const uint32_t cbytes = (uint32_t)wt_copy_bytes(n);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned n_cta = gridDim.x, cta = blockIdx.x;
     SolveSmem S;
     S.stage0 = sm;
     S.sy4 = reinterpret_cast<float4 *>(sm + (size_t)MP_NW * stages * cbytes);
@@ -769,6 +767,60 @@ __global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stag
         a.st->done = 1;
         a.st->stop = VMAT_STOP_MAXIT;
         a.st->iters = ps.t + 1;
+    }
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
+    if (a.skip && *a.skip) return; // the same flag for every CTA: all return together
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    // align the staging area explicitly: static shared memory may shift the dynamic region
+    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
+    mp_solve_body<NMAX>(a, blockIdx.x, gridDim.x, stages, keep_in_l2, sm);
+}
+
+// Several independent problems in one persistent launch: CTAs cta_start[p] ..
+// cta_start[p + 1] - 1 solve problem p (its own grid barrier and workspace);
+// every problem has n apertures.  CTAs of a skipped problem return at once.
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS)
+    mp_solve_batched_kernel(const MPArgs *__restrict__ args, const int32_t *__restrict__ cta_start, int32_t n_plans,
+                            int32_t n, int stages, int keep_in_l2) {
+    __shared__ MPArgs sa;
+    __shared__ int sp;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_plans; // cta_start[lo] <= blockIdx.x < cta_start[hi]
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (cta_start[m] <= (int)blockIdx.x) lo = m;
+            else hi = m;
+        }
+        sp = lo;
+    }
+    __syncthreads();
+    const int p = sp;
+    for (int i = threadIdx.x; i < (int)(sizeof(MPArgs) / 4); i += MP_THREADS)
+        reinterpret_cast<int32_t *>(&sa)[i] = reinterpret_cast<const int32_t *>(args + p)[i];
+    __syncthreads();
+    if (threadIdx.x == 0) sa.n = n;
+    __syncthreads();
+    if (sa.skip && *sa.skip) return;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
+    mp_solve_body<NMAX>(sa, blockIdx.x - cta_start[p], cta_start[p + 1] - cta_start[p], stages, keep_in_l2, sm);
+}
+
+// Per-problem set-up of the batched solver (one block per problem).
+__global__ void mp_init_batched_kernel(const MPArgs *__restrict__ args, int32_t n) {
+    MPArgs a = args[blockIdx.x];
+    a.n = n;
+    if (a.skip && *a.skip) return;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) a.y[k] = fminf(fmaxf(a.y[k], lo_of(a, k)), hi_of(a, k));
+    if (threadIdx.x == 0) {
+        BBState st = {};
+        *a.st = st;
+        *a.bar_count = 0u;
+        *a.bar_gen = 0u;
     }
 }
 
@@ -954,6 +1006,24 @@ static SolveFn solve_kernel_for(int n) {
     default: return nullptr;
     }
 }
+using SolveBatchFn = void (*)(const MPArgs *, const int32_t *, int32_t, int32_t, int, int);
+static SolveBatchFn solve_batched_kernel_for(int n) {
+    switch ((n + 7) / 8) {
+    case 1: return mp_solve_batched_kernel<8>;
+    case 2: return mp_solve_batched_kernel<16>;
+    case 3: return mp_solve_batched_kernel<24>;
+    case 4: return mp_solve_batched_kernel<32>;
+    case 5: return mp_solve_batched_kernel<40>;
+    case 6: return mp_solve_batched_kernel<48>;
+    case 7: return mp_solve_batched_kernel<56>;
+    case 8: return mp_solve_batched_kernel<64>;
+    case 9: return mp_solve_batched_kernel<72>;
+    case 10: return mp_solve_batched_kernel<80>;
+    case 11: return mp_solve_batched_kernel<88>;
+    case 12: return mp_solve_batched_kernel<96>;
+    default: return nullptr;
+    }
+}
 static size_t ldg_smem(int n) { return (size_t)((n + 3) & ~3) * 4 + (size_t)n * 8 + MP_THREADS * 4 + 3 * 256 * 4; }
 
 int64_t mp_wtile_stride(int32_t n_cap) { return MP_HEAD + (int64_t)((n_cap + 3) / 4) * 128; }
@@ -969,9 +1039,12 @@ struct MPLaunch {
 static vmat_status mp_set_attributes() {
     static bool attr = false;
     if (attr) return VMAT_OK;
-    for (int q = 1; q <= MP_NMAX / 8; ++q)
+    for (int q = 1; q <= MP_NMAX / 8; ++q) {
         VMAT_CUDA(cudaFuncSetAttribute(solve_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        MP_SMEM_LIMIT));
+        VMAT_CUDA(cudaFuncSetAttribute(solve_batched_kernel_for(8 * q), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       MP_SMEM_LIMIT));
+    }
     VMAT_CUDA(cudaFuncSetAttribute(mp_iter_ldg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
     VMAT_CUDA(cudaFuncSetAttribute(mp_cauchy_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM_LIMIT));
     attr = true;
@@ -1082,6 +1155,82 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
     a.skip = skip;
     a.iters_acc = iters_acc;
     return mp_launch_persistent(a, L, s);
+}
+
+size_t mp_args_bytes() { return sizeof(MPArgs); }
+
+vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
+                              const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
+                              const vmat_bb_opts *opts_in, double F_offset, const int32_t *skip, int32_t *iters_acc) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
+    if (opts_in) opts = *opts_in;
+    if (opts.max_iter < 1) return set_error(VMAT_EINVAL, "mp_bb_solve: max_iter must be >= 1");
+    MPLaunch L = {};
+    L.P = 1;
+    MPArgs a;
+    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_cap, struct_id, vox, nullptr, nullptr, y, z, opts,
+                 F_offset, L, ctx);
+    a.skip = skip;
+    a.iters_acc = iters_acc;
+    memcpy(out, &a, sizeof(MPArgs));
+    return VMAT_OK;
+}
+
+vmat_status mp_batched_grid(int32_t n, const int64_t *V_list, int32_t n_plans, int32_t *cta_start, int32_t *grid,
+                            int32_t *stages, size_t *smem) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    VMAT_TRY(mp_set_attributes());
+    if (n < 1 || n > MP_NMAX) return set_error(VMAT_EUNSUPPORTED, "batched master problem: %d apertures (max %d)", n, MP_NMAX);
+    const int st = solve_stages(n);
+    const size_t sm = solve_smem(n, st);
+    if (st < 2 || sm > MP_SMEM_LIMIT) return set_error(VMAT_EUNSUPPORTED, "batched master problem: no fit for %d", n);
+    int bps = 0;
+    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, solve_batched_kernel_for(n), MP_THREADS, sm));
+    if (bps < 1) return set_error(VMAT_ECUDA, "batched master problem: kernel does not fit on an SM");
+    const int64_t P = (int64_t)ctx->n_sm * bps;
+    if (P < n_plans) return set_error(VMAT_EUNSUPPORTED, "batched master problem: more plans than resident CTAs");
+    // CTAs in proportion to each problem's warp tiles, at least one, at most one per 8 tiles
+    double wsum = 0.0;
+    std::vector<int64_t> cap(n_plans);
+    for (int p = 0; p < n_plans; ++p) {
+        const int64_t wt = (std::max<int64_t>(V_list[p], 1) + MP_WT - 1) / MP_WT;
+        cap[p] = (wt + MP_NW - 1) / MP_NW;
+        wsum += (double)wt;
+    }
+    int64_t used = 0;
+    cta_start[0] = 0;
+    for (int p = 0; p < n_plans; ++p) {
+        const int64_t wt = (std::max<int64_t>(V_list[p], 1) + MP_WT - 1) / MP_WT;
+        const int64_t left_plans = n_plans - p - 1;
+        int64_t c = (int64_t)((double)(P - n_plans) * (double)wt / wsum) + 1;
+        c = std::min<int64_t>(c, std::min<int64_t>(cap[p], P - used - left_plans));
+        c = std::max<int64_t>(c, 1);
+        used += c;
+        cta_start[p + 1] = (int32_t)used;
+    }
+    *grid = (int32_t)used;
+    *stages = st;
+    *smem = sm;
+    return VMAT_OK;
+}
+
+vmat_status mp_bb_enqueue_batched(const void *args, const int32_t *cta_start, int32_t n_plans, int32_t n,
+                                  int32_t grid, int32_t stages, size_t smem, int keep_in_l2, cudaStream_t s) {
+    mp_init_batched_kernel<<<n_plans, 128, 0, s>>>(static_cast<const MPArgs *>(args), n);
+    VMAT_LAUNCH_CHECK();
+    SolveBatchFn fn = solve_batched_kernel_for(n);
+    if (!fn) return set_error(VMAT_EUNSUPPORTED, "batched master problem: %d apertures", n);
+    const MPArgs *a = static_cast<const MPArgs *>(args);
+    int32_t np = n_plans, nn = n;
+    int st = stages, l2 = keep_in_l2;
+    void *kargs[] = {&a, &cta_start, &np, &nn, &st, &l2};
+    VMAT_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3(MP_THREADS), kargs, smem,
+                                          s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return VMAT_OK;
 }
 
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,

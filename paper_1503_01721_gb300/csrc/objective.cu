@@ -75,6 +75,44 @@ __global__ void __launch_bounds__(OBJ_THREADS)
     }
 }
 
+// Batched g = -grad F (no F): global voxel g is compact voxel i = g - off[p] of plan p,
+// whose voxel index is idx[i]; g is written at g_scatter[idx[i]].
+__global__ void __launch_bounds__(OBJ_THREADS)
+    objective_grad_batched_kernel(const ObjPlan *__restrict__ plans, const int64_t *__restrict__ off, int32_t n_plans,
+                                  int64_t total) {
+    __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n_plans; i += blockDim.x) soff[i] = off[i];
+    __syncthreads();
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        int a = 0, b = n_plans;
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if (soff[m] <= gi) a = m;
+            else b = m;
+        }
+        const ObjPlan &P = plans[a];
+        if (P.skip && *P.skip) continue;
+        const int64_t i = gi - soff[a];
+        const int32_t v = P.idx[i];
+        const int k = P.sid[v];
+        const float zi = P.z[i], t = P.T[k];
+        P.g_scatter[v] = -2.f * P.wo[k] * fmaxf(0.f, zi - t) + 2.f * P.wu[k] * fmaxf(0.f, t - zi);
+    }
+}
+
+vmat_status objective_grad_batched(const ObjPlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
+                                   cudaStream_t s) {
+    if (total <= 0) return VMAT_OK;
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + OBJ_THREADS - 1) / OBJ_THREADS,
+                                                                  (int64_t)ctx->n_sm * 8));
+    objective_grad_batched_kernel<<<grid, OBJ_THREADS, 0, s>>>(plans, off, n_plans, total);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
 // F_i(0) summed over voxels outside every row of CSR(D) (their dose is always 0).
 __global__ void __launch_bounds__(OBJ_THREADS)
     inactive_objective_kernel(int32_t V, const int32_t *vox2act, const uint8_t *sid, const float *T, const float *wo,

@@ -18,13 +18,7 @@
 
 namespace vmat {
 
-constexpr int MAX_ARCS = 64;
 constexpr int PR_WARPS = 8;
-
-struct PricingGeom {
-    int32_t K, n_rows, n_cols, travel, n_arcs;
-    int32_t arc_first[MAX_ARCS + 1];
-};
 
 struct RowBest {
     double v;
@@ -55,15 +49,12 @@ __device__ int nearest_occupied(const PricingGeom &g, const uint8_t *occupied, i
     return -1;
 }
 
-__global__ void __launch_bounds__(PR_WARPS * 32)
-    price_rows_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
-                      const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok,
-                      const int32_t *skip) {
-    if (skip && *skip) return;
-    extern __shared__ double sP[]; // PR_WARPS x (n_cols + 1)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
-    if (gw >= (int64_t)g.K * g.n_rows) return;
+// Best opening of MLC row r of CP k (one warp; P: n_cols + 1 doubles of shared
+// memory for this warp).  Writes the row's entry gw of rb_*.
+__device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float *__restrict__ pi,
+                                               const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
+                                               int64_t gw, double *P, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok) {
+    const int lane = threadIdx.x & 31;
     const int k = (int)(gw / g.n_rows), r = (int)(gw % g.n_rows);
     if (occupied[k]) return;
     const int N = g.n_cols;
@@ -79,7 +70,6 @@ __global__ void __launch_bounds__(PR_WARPS * 32)
             Rmax = min(Rmax, Rn + reach);
         }
     }
-    double *P = sP + wid * (N + 1);
     if (lane == 0) {
         const float *row = pi + ((int64_t)k * g.n_rows + r) * N;
         double acc = 0.0;
@@ -124,13 +114,26 @@ __global__ void __launch_bounds__(PR_WARPS * 32)
     }
 }
 
+__global__ void __launch_bounds__(PR_WARPS * 32)
+    price_rows_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
+                      const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok,
+                      const int32_t *skip) {
+    if (skip && *skip) return;
+    extern __shared__ double sP[]; // PR_WARPS x (n_cols + 1)
+    const int wid = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
+    if (gw >= (int64_t)g.K * g.n_rows) return;
+    price_row_warp(g, pi, occupied, leaves, gw, sP + wid * (g.n_cols + 1), rb_v, rb_lr, rb_ok);
+}
+
 constexpr int CP_THREADS = 1024;
 
-__global__ void __launch_bounds__(CP_THREADS)
-    price_cps_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const double *__restrict__ rb_v,
-                     const int16_t *__restrict__ rb_lr, const uint8_t *__restrict__ rb_ok, int32_t *best_cp,
-                     int16_t *best_leaves, double *best_price, const int32_t *skip) {
-    if (skip && *skip) return;
+// The CP with the largest price (sum of its row bests, in row order), smallest k
+// on ties, and its leaves (one block).
+__device__ __forceinline__ void price_cps_block(const PricingGeom &g, const uint8_t *__restrict__ occupied,
+                                                const double *__restrict__ rb_v, const int16_t *__restrict__ rb_lr,
+                                                const uint8_t *__restrict__ rb_ok, int32_t *best_cp,
+                                                int16_t *best_leaves, double *best_price) {
     __shared__ double sv[CP_THREADS / 32];
     __shared__ int sk[CP_THREADS / 32];
     __shared__ int kwin;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(CP_THREADS)
     if (threadIdx.x == 0) {
         double v = -INFINITY;
         int kb = -1;
-        for (int w = 0; w < CP_THREADS / 32; ++w)
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
             if (sk[w] >= 0 && (kb < 0 || sv[w] > v || (sv[w] == v && sk[w] < kb))) {
                 v = sv[w];
                 kb = sk[w];
@@ -186,18 +189,80 @@ __global__ void __launch_bounds__(CP_THREADS)
         }
 }
 
+__global__ void __launch_bounds__(CP_THREADS)
+    price_cps_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const double *__restrict__ rb_v,
+                     const int16_t *__restrict__ rb_lr, const uint8_t *__restrict__ rb_ok, int32_t *best_cp,
+                     int16_t *best_leaves, double *best_price, const int32_t *skip) {
+    if (skip && *skip) return;
+    price_cps_block(g, occupied, rb_v, rb_lr, rb_ok, best_cp, best_leaves, best_price);
+}
+
+// Batched pricing: global row g of plan p is (CP, MLC row) pair g - off[p].
+__global__ void __launch_bounds__(PR_WARPS * 32)
+    price_rows_batched_kernel(const PricePlan *__restrict__ plans, const int64_t *__restrict__ off, int32_t n_plans,
+                              int64_t total, int32_t max_cols) {
+    extern __shared__ double sP[]; // PR_WARPS x (max_cols + 1)
+    __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n_plans; i += blockDim.x) soff[i] = off[i];
+    __syncthreads();
+    const int wid = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
+    if (gw >= total) return;
+    int a = 0, b = n_plans;
+    while (b - a > 1) {
+        const int m = (a + b) >> 1;
+        if (soff[m] <= gw) a = m;
+        else b = m;
+    }
+    const PricePlan &P = plans[a];
+    if (P.skip && *P.skip) return;
+    price_row_warp(P.g, P.pi, P.occupied, P.leaves, gw - soff[a], sP + wid * (max_cols + 1), P.rb_v, P.rb_lr,
+                   P.rb_ok);
+}
+
+__global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const PricePlan *__restrict__ plans) {
+    const PricePlan &P = plans[blockIdx.x];
+    if (P.skip && *P.skip) return;
+    price_cps_block(P.g, P.occupied, P.rb_v, P.rb_lr, P.rb_ok, P.best_cp, P.best_leaves, P.best_price);
+}
+
+vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g) {
+    if (mlc->n_arcs > MAX_ARCS) return set_error(VMAT_EUNSUPPORTED, "price_apertures: more than %d arcs", MAX_ARCS);
+    g->K = mlc->K;
+    g->n_rows = mlc->n_rows;
+    g->n_cols = mlc->n_cols;
+    g->travel = mlc->travel_cols;
+    g->n_arcs = mlc->n_arcs;
+    for (int a = 0; a < mlc->n_arcs; ++a) g->arc_first[a] = mlc->arc_first_cp[a];
+    g->arc_first[mlc->n_arcs] = mlc->K;
+    return VMAT_OK;
+}
+
+vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
+                                    int32_t max_cols, cudaStream_t s) {
+    if (n_plans < 1 || n_plans > VMAT_MAX_BATCH) return set_error(VMAT_EINVAL, "price_apertures_batched: bad plan count");
+    static bool attr_set = false;
+    if (!attr_set) {
+        VMAT_CUDA(cudaFuncSetAttribute(price_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(PR_WARPS * 1025 * sizeof(double))));
+        attr_set = true;
+    }
+    if (total > 0) {
+        const int64_t blocks = (total + PR_WARPS - 1) / PR_WARPS;
+        price_rows_batched_kernel<<<(unsigned)blocks, PR_WARPS * 32, (size_t)PR_WARPS * (max_cols + 1) * sizeof(double),
+                                    s>>>(plans, off, n_plans, total, max_cols);
+        VMAT_LAUNCH_CHECK();
+    }
+    price_cps_batched_kernel<<<n_plans, CP_THREADS, 0, s>>>(plans);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                                  int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws,
                                  cudaStream_t s, const int32_t *skip) {
-    if (mlc->n_arcs > MAX_ARCS) return set_error(VMAT_EUNSUPPORTED, "price_apertures: more than %d arcs", MAX_ARCS);
     PricingGeom g;
-    g.K = mlc->K;
-    g.n_rows = mlc->n_rows;
-    g.n_cols = mlc->n_cols;
-    g.travel = mlc->travel_cols;
-    g.n_arcs = mlc->n_arcs;
-    for (int a = 0; a < mlc->n_arcs; ++a) g.arc_first[a] = mlc->arc_first_cp[a];
-    g.arc_first[mlc->n_arcs] = mlc->K;
+    VMAT_TRY(pricing_geom(mlc, &g));
     const int64_t rows = (int64_t)g.K * g.n_rows;
     double *rb_v = static_cast<double *>(ws);
     int16_t *rb_lr = reinterpret_cast<int16_t *>(rb_v + rows);

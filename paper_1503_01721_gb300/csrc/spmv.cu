@@ -364,6 +364,55 @@ struct RowParams {
     const int32_t *skip; // when non-null and set, the kernel does nothing
 };
 
+// Sum of row r (all lanes of a warp; the result is valid in every lane): 4-entry
+// chunks per lane with 128-bit streaming loads, 4 accumulators per lane, a fixed
+// butterfly.  The head (< 4 entries before the first 4-aligned one) and the tail
+// take one entry per lane.
+template <int UNROLL, typename VT>
+__device__ __forceinline__ float warp_row_sum(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                              const void *__restrict__ val, const float *__restrict__ x, int64_t r,
+                                              int lane, uint64_t pol) {
+    const int64_t s = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+    const int64_t a = min((s + 3) & ~(int64_t)3, e); // first 4-aligned entry
+    const int64_t b = max(a, e & ~(int64_t)3);        // end of the aligned body
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (lane < a - s) {
+        const int64_t i = s + lane;
+        acc[0] = StreamVals<VT>::load1(val, i) * __ldg(x + __ldg(col + i));
+    }
+    if (lane < e - b) {
+        const int64_t i = b + lane;
+        acc[1] = StreamVals<VT>::load1(val, i) * __ldg(x + __ldg(col + i));
+    }
+    const int64_t nch = (b - a) >> 2;
+    for (int64_t c = lane; c < nch; c += 32 * UNROLL) {
+        float v[UNROLL][4];
+        int4 cc[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t cu = c + 32 * u;
+            if (cu < nch) {
+                const int64_t e0 = a + 4 * cu;
+                StreamVals<VT>::load4(val, e0, pol, v[u]);
+                cc[u] = ldg_stream_i4(col + e0, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (c + 32 * u < nch) {
+                acc[0] = fmaf(v[u][0], __ldg(x + cc[u].x), acc[0]);
+                acc[1] = fmaf(v[u][1], __ldg(x + cc[u].y), acc[1]);
+                acc[2] = fmaf(v[u][2], __ldg(x + cc[u].z), acc[2]);
+                acc[3] = fmaf(v[u][3], __ldg(x + cc[u].w), acc[3]);
+            }
+        }
+    }
+    float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    return sum;
+}
+
 template <int THREADS, int UNROLL, typename VT>
 __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
@@ -373,48 +422,51 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     const uint64_t pol = l2_evict_first_policy();
     for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
         if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
-        const int64_t s = __ldg(p.rowptr + r), e = __ldg(p.rowptr + r + 1);
-        const int64_t a = min((s + 3) & ~(int64_t)3, e); // first 4-aligned entry
-        const int64_t b = max(a, e & ~(int64_t)3);        // end of the aligned body
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        // head (< 4 entries) and tail (< 4 entries): one entry per lane
-        if (lane < a - s) {
-            const int64_t i = s + lane;
-            acc[0] = StreamVals<VT>::load1(p.val, i) * __ldg(p.x + __ldg(p.col + i));
-        }
-        if (lane < e - b) {
-            const int64_t i = b + lane;
-            acc[1] = StreamVals<VT>::load1(p.val, i) * __ldg(p.x + __ldg(p.col + i));
-        }
-        const int64_t nch = (b - a) >> 2;
-        for (int64_t c = lane; c < nch; c += 32 * UNROLL) {
-            float v[UNROLL][4];
-            int4 cc[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                const int64_t cu = c + 32 * u;
-                if (cu < nch) {
-                    const int64_t e0 = a + 4 * cu;
-                    StreamVals<VT>::load4(p.val, e0, pol, v[u]);
-                    cc[u] = ldg_stream_i4(p.col + e0, pol);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                if (c + 32 * u < nch) {
-                    acc[0] = fmaf(v[u][0], __ldg(p.x + cc[u].x), acc[0]);
-                    acc[1] = fmaf(v[u][1], __ldg(p.x + cc[u].y), acc[1]);
-                    acc[2] = fmaf(v[u][2], __ldg(p.x + cc[u].z), acc[2]);
-                    acc[3] = fmaf(v[u][3], __ldg(p.x + cc[u].w), acc[3]);
-                }
-            }
-        }
-        float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        float sum = warp_row_sum<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
             p.y[p.row_ids ? p.row_ids[r] : r] = sum;
+        }
+    }
+}
+
+// Several plans' matrices in one launch: global row g belongs to plan p with
+// row_off[p] <= g < row_off[p + 1] (row g - row_off[p] of that plan).  A warp
+// looks its plan up when it crosses into another plan's range.
+template <int THREADS, int UNROLL, typename VT>
+__global__ void __launch_bounds__(THREADS)
+    spmv_rows_batched_kernel(const SpmvPlan *__restrict__ plans, const int64_t *__restrict__ row_off, int32_t n_plans,
+                             int64_t total_rows) {
+    __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
+    for (int i = threadIdx.x; i <= n_plans; i += THREADS) soff[i] = row_off[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    const uint64_t pol = l2_evict_first_policy();
+    int64_t lo = 0, hi = 0;
+    SpmvPlan P;
+    bool skip = true;
+    for (int64_t gr = warp0; gr < total_rows; gr += n_warps) {
+        if (gr < lo || gr >= hi) {
+            int a = 0, b = n_plans; // soff[a] <= gr < soff[b]
+            while (b - a > 1) {
+                const int m = (a + b) >> 1;
+                if (soff[m] <= gr) a = m;
+                else b = m;
+            }
+            P = plans[a];
+            lo = soff[a];
+            hi = soff[a + 1];
+            skip = P.skip && *P.skip;
+        }
+        if (skip) continue;
+        const int64_t r = gr - lo;
+        if (P.cp_active && !P.cp_active[r / P.bpc]) continue;
+        float sum = warp_row_sum<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol);
+        if (lane == 0) {
+            if (P.row_scale) sum *= P.row_scale[r];
+            P.y[P.row_ids ? P.row_ids[r] : r] = sum;
         }
     }
 }
@@ -495,6 +547,7 @@ constexpr int N_CFG = 9;
 
 using TileFn = void (*)(SpmvParams);
 using RowFn = void (*)(RowParams);
+using RowBatchFn = void (*)(const SpmvPlan *, const int64_t *, int32_t, int64_t);
 
 template <typename VT> TileFn tile_kernel_for(int cfg) {
     switch (cfg) {
@@ -671,6 +724,39 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
     const int gf = std::max(1, std::min(ctx->n_sm * 4, (m.n_tiles + 255) / 256));
     spmv_fixup<<<gf, 256, 0, s>>>(m.tile_row, m.carry_val, m.n_tiles, list, n_list, m.n_rows, y, m.row_ids,
                                   row_scale, cp_active, bpc);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+template <typename VT> static RowBatchFn batched_kernel_for(int cfg) {
+    switch (cfg) {
+    case 4: return spmv_rows_batched_kernel<256, 2, VT>;
+    case 5: return spmv_rows_batched_kernel<256, 1, VT>;
+    case 6: return spmv_rows_batched_kernel<512, 4, VT>;
+    case 7: return spmv_rows_batched_kernel<256, 4, VT>;
+    case 8: return spmv_rows_batched_kernel<256, 8, VT>;
+    default: return nullptr;
+    }
+}
+
+bool spmv_batched_config(int cfg) { return cfg >= 0 && cfg < N_CFG && kCfgs[cfg].family == 1; }
+
+vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
+                              int64_t total_rows, cudaStream_t s) {
+    if (!spmv_batched_config(cfg)) return set_error(VMAT_EINVAL, "spmv_rows_batched: configuration %d is not warp-row", cfg);
+    if (n_plans < 1 || n_plans > VMAT_MAX_BATCH) return set_error(VMAT_EINVAL, "spmv_rows_batched: bad plan count");
+    if (total_rows <= 0) return VMAT_OK;
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    RowBatchFn fn = dt == VMAT_F32 ? batched_kernel_for<float>(cfg)
+                    : dt == VMAT_BF16 ? batched_kernel_for<__nv_bfloat16>(cfg)
+                                      : batched_kernel_for<__nv_fp8_e4m3>(cfg);
+    const int threads = kCfgs[cfg].threads;
+    int bps = 1;
+    VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, 0));
+    const int64_t want = (total_rows * 32 + threads - 1) / threads;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * std::max(bps, 1)));
+    fn<<<grid, threads, 0, s>>>(plans, row_off, n_plans, total_rows);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

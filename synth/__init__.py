@@ -17,6 +17,11 @@ Workload recipes (voxel units unless noted):
   (737,280), three ellipsoidal targets (1.0/0.9/0.8, semi-axes U[6,16]) and
   six ellipsoidal OARs (limit 0.5, semi-axes U[4,10]); 60 apertures.
 * ``cfg3``  cfg2 geometry with two arcs (360 CPs, second arc offset by 1 deg).
+* ``cfg5``  a batch of 24 prostate-like plans of uneven size (``batch_specs``):
+  grids from 80x80x60 to 160x160x120, 90-360 CPs (one arc up to 180, else two),
+  40-80 leaf pairs, 16-80 columns chosen so that each DDC has 2e8-1.2e9
+  nonzeros (1.14e10 in all); 60 apertures each.  ``cfg5q`` is the same batch
+  with a quarter of the CPs (profiling), ``batch_small`` four small plans.
 
 Pencil-beam value exp(-0.05 * depth) * exp(-rho^2/2), depth and lateral
 distance rho both in voxel units (sigma = 1 voxel), dropped below 1% of the
@@ -184,6 +189,55 @@ GEOMETRIES = {
 APERTURES = {"tiny": 3, "ragged": 4, "cfg1": 20, "cfg2": 60, "cfg3": 60, "cfg2q": 30}
 
 
+@dataclasses.dataclass(frozen=True)
+class PlanSpec:
+    """One plan of a batch workload: geometry, aperture count, structure recipe and seed."""
+    name: str
+    geom: Geometry
+    n_apertures: int
+    structures: str
+    seed: int
+
+
+def _cfg5_geometry(p: int, cp_div: int = 1) -> Geometry:
+    """Plan p of the 24-plan batch: sizes grow with p; CP count, leaf pairs and the
+    column count (set from a target beamlet count of 154e3 * 7.5^(u^2)) cycle so
+    that small and large DDCs are mixed.  About 1300 nonzeros per beamlet."""
+    s = p / 23.0
+    nx = 80 + 8 * round(10 * s)
+    nz = 60 + 4 * round(15 * s)
+    n_rows = 40 + 8 * round(5 * ((p * 7) % 24) / 23.0)
+    K = [90, 120, 180, 240, 360][(p * 3) % 5]
+    u = ((p * 5) % 24) / 23.0
+    beamlets = 154e3 * 7.5 ** (u * u)
+    n_cols = int(min(max(round(beamlets / (K * n_rows)), 16), 80))
+    n_arcs = 1 if K <= 180 else 2
+    n_cp = max(K // n_arcs // cp_div, 2)
+    return Geometry(nx, nx, nz, 2.5, n_cp, n_rows, n_cols, n_arcs=n_arcs, arc_offset_deg=1.0)
+
+
+def batch_specs(name: str) -> list:
+    """Plans of a batch workload (see the module docstring)."""
+    if name in ("cfg5", "cfg5q"):
+        div = 1 if name == "cfg5" else 4
+        geoms = [_cfg5_geometry(p, div) for p in range(24)]
+        return [PlanSpec(f"{name}_{p:02d}", g, min(60 if div == 1 else 30, g.K), "prostate", p)
+                for p, g in enumerate(geoms)]
+    if name == "batch_small":
+        return [PlanSpec("bs_0", GEOMETRIES["tiny"], 3, "tiny", 0),
+                PlanSpec("bs_1", GEOMETRIES["ragged"], 4, "ragged", 0),
+                PlanSpec("bs_2", Geometry(24, 20, 16, 5.0, 12, 8, 10), 6, "prostate", 2),
+                PlanSpec("bs_3", GEOMETRIES["cfg1"], 12, "cfg1", 3)]
+    raise KeyError(name)
+
+
+def make_plan_case(spec: PlanSpec) -> "Case":
+    """Generate one plan of a batch (not cached: batches can exceed host memory if kept)."""
+    vox, blt, val = generate_coo(spec.geom)
+    return Case(spec.name, spec.geom, make_mlc(spec.geom), vox, blt, val,
+                make_structures(spec.structures, spec.geom, spec.seed), spec.n_apertures)
+
+
 def generate_coo(geom: Geometry):
     """Return (vox int32, blt int32, val float32) COO arrays, beamlet-major."""
     lib = _load()
@@ -244,7 +298,18 @@ def make_structures(name: str, geom: Geometry, seed: int) -> Structures:
     T, wo, wu, names = [], [], [], []
     if name == "cfg2q":
         name = "cfg2"
-    if name in ("cfg1", "tiny", "ragged"):
+    if name == "prostate":
+        # target ellipsoid near the centre; rectum behind it (elongated along z),
+        # bladder above and in front; sizes in proportion to the grid
+        n = np.array([geom.nx, geom.ny, geom.nz], float)
+        ct = rng.uniform(-0.03, 0.03, size=3) * n
+        at = np.array([0.11, 0.09, 0.10]) * n * rng.uniform(0.9, 1.1, size=3)
+        ar = np.array([0.06, 0.06, 0.20]) * n
+        ab = np.array([0.14, 0.11, 0.09]) * n
+        targets = [(ct, at, 1.0)]
+        oars = [(ct - np.array([0.0, at[1] + ar[1] + 1.0, 0.0]), ar, 0.5),
+                (ct + np.array([0.0, 0.4 * at[1], at[2] + ab[2] + 1.0]), ab, 0.5)]
+    elif name in ("cfg1", "tiny", "ragged"):
         r_t = {"cfg1": 8.0, "tiny": 2.5, "ragged": 2.5}[name]
         r_o = {"cfg1": 5.0, "tiny": 1.5, "ragged": 1.5}[name]
         # continuous centre offsets: a sphere centred on a grid point is mirror
