@@ -39,6 +39,15 @@ DESCS = {
              "20 apertures (L2-resident)"),
 }
 WORKLOAD_DESC = DESCS[WORKLOAD]
+# SpMV configurations as the library builds them (csrc/spmv.cu, kCfgs)
+SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>", 2: "spmv_tile_kernel<512,8,2>",
+                3: "spmv_tile_kernel<128,16,3>", 4: "spmv_warp_row_kernel<256,2>", 5: "spmv_warp_row_kernel<256,1>",
+                6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>"}
+# DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
+# configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
+# (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.
+TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
+                 ("f32", 8): 1.0008, ("bf16", 5): 1.0083, ("fp8", 5): 1.0082}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
@@ -271,12 +280,19 @@ def run_ours(args, rank, world, local):
     spmv_bytes = sum(s["pp1_spmv_bytes"] for s in stats_all)
     peaks = roofline.measured_peaks()
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    kname = ("spmv_tile_kernel + spmv_fixup" if info["tile_nnz_Dt"] else "spmv_warp_row_kernel") + \
-        " (beamlet price D^T g over the unoccupied CPs)"
+    cfg_dt = int(info["cfg_Dt"])
+    kname = SPMV_KERNELS.get(cfg_dt, f"spmv configuration {cfg_dt}") + \
+        (" + spmv_fixup" if info["tile_nnz_Dt"] else "") + " (beamlet price D^T g over the unoccupied CPs)"
+    bytes_launch = spmv_bytes / max(spmv_n, 1)
+    ratio = TRAFFIC_RATIO.get((args.dtype, cfg_dt))
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-            "peak_source": peaks["source"], "bytes_per_launch": round(spmv_bytes / max(spmv_n, 1)),
+            "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "traffic": None if ratio is None else round(ratio * bytes_launch),
+            "traffic_source": None if ratio is None else
+            f"ncu dram bytes / algorithmic bytes = {ratio} for this kernel on the full D^T pass, times this "
+            "launch's algorithmic bytes",
+            "peak_source": peaks["source"], "bytes_per_launch": round(bytes_launch),
             "avg_launch_ms": round(spmv_ms / max(spmv_n, 1), 4)}
 
     # isolated full passes: D^T g and D x over the whole matrix

@@ -112,6 +112,7 @@ typedef struct {
     int32_t tile_nnz_D, tile_nnz_Dt; /* nonzeros per SpMV tile */
     int64_t bytes_D, bytes_Dt;       /* device bytes of each CSR (values, columns, row pointers) */
     double build_ms;                 /* device time of the last ddc_build */
+    int32_t cfg_D, cfg_Dt;           /* SpMV configuration of each CSR (see vmat_spmv_config_count) */
 } vmat_ddc_info;
 
 /* Per-phase device times of cg_plan, named as the paper's Table 2 phases. */

@@ -44,7 +44,7 @@ class BBReport(ctypes.Structure):
 class DdcInfo(ctypes.Structure):
     _fields_ = [("V", c_i32), ("J", c_i32), ("nnz", c_i64), ("n_active_vox", c_i32), ("dtype", c_i32),
                 ("built_D", c_i32), ("built_Dt", c_i32), ("tile_nnz_D", c_i32), ("tile_nnz_Dt", c_i32),
-                ("bytes_D", c_i64), ("bytes_Dt", c_i64), ("build_ms", c_f64)]
+                ("bytes_D", c_i64), ("bytes_Dt", c_i64), ("build_ms", c_f64), ("cfg_D", c_i32), ("cfg_Dt", c_i32)]
 
 
 class PlanStats(ctypes.Structure):

@@ -299,6 +299,8 @@ vmat_status ddc_info(vmat_ddc hd, vmat_ddc_info *out) {
     if (h->built_D) out->bytes_D = h->D.nnz * (int64_t)(vb + 4) + (int64_t)(h->D.n_rows + 1) * 8;
     if (h->built_Dt) out->bytes_Dt = h->Dt.nnz * (int64_t)(vb + 4) + (int64_t)(h->Dt.n_rows + 1) * 8;
     out->build_ms = h->build_ms;
+    out->cfg_D = h->D.cfg;
+    out->cfg_Dt = h->Dt.cfg;
     return VMAT_OK;
 }
 
