@@ -37,12 +37,16 @@ DESCS = {
     "cfg2q": ("profiling case: the H&N-like geometry with 45 CPs at 8 deg (184,320 beamlets), 30 apertures"),
     "cfg1": ("tiny FP32 case: 40^3 voxels @5 mm, one sphere target + 2 OARs, 36 CPs, 20x20 beamlets, "
              "20 apertures (L2-resident)"),
+    "cfg3": ("precision case: the H&N-like geometry with two arcs (360 CPs, second arc offset by 1 deg), "
+             "64x64 beamlets (1,474,560), 60 apertures"),
 }
 WORKLOAD_DESC = DESCS[WORKLOAD]
 # SpMV configurations as the library builds them (csrc/spmv.cu, kCfgs)
 SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>", 2: "spmv_tile_kernel<512,8,2>",
                 3: "spmv_tile_kernel<128,16,3>", 4: "spmv_warp_row_kernel<256,2>", 5: "spmv_warp_row_kernel<256,1>",
-                6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>"}
+                6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>",
+                9: "spmv_warp_row_c_kernel<256,4>", 10: "spmv_warp_row_c_kernel<256,8>",
+                11: "spmv_warp_row_c_kernel<512,4>"}
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
 # configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
 # (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.

@@ -112,7 +112,8 @@ struct Batch {
     int64_t *d_na_off = nullptr, tot_na = 0;
     CommitPlan *d_commit = nullptr;
     void *d_mpargs = nullptr;
-    int32_t *d_cta = nullptr; // [T][n + 1]
+    int64_t *d_weight = nullptr; // [n] warp tiles of each plan (the solver's CTA split)
+    unsigned *d_gctl = nullptr;  // [8] batch barrier, epoch and active-set words
     std::vector<int32_t> grid_t, stages_t, keep_t;
     std::vector<size_t> smem_t;
     int32_t *d_ctl = nullptr, *d_targets = nullptr, *h_ctl = nullptr;
@@ -168,7 +169,7 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
         batch_commit<<<n, 128, 0, s>>>(t, b.d_commit);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(aperture_dose_batched(b.dt, b.d_da, b.d_na_off, n, b.tot_na, t, s));
-        VMAT_TRY(mp_bb_enqueue_batched(b.d_mpargs, b.d_cta + (size_t)t * (n + 1), n, t + 1, b.grid_t[t], b.stages_t[t],
+        VMAT_TRY(mp_bb_enqueue_batched(b.d_mpargs, b.d_weight, b.d_gctl, n, t + 1, b.grid_t[t], b.stages_t[t],
                                        b.smem_t[t], b.keep_t[t], s));
     }
     for (BPlan &p : b.P) { // final dose D (A y) in FP32 and F (apertures not placed have cps = -1)
@@ -225,7 +226,6 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaStreamCreateWithFlags(&b.cs, cudaStreamNonBlocking));
     VMAT_TRY(b.get(&b.d_ctl, (size_t)n_plans * CTL_N));
     VMAT_TRY(b.get(&b.d_targets, n_plans));
-    const int n_cap_all = std::max(std::min(b.T, 96), 1);
 
     // ---- per-plan device state and set-up
     std::vector<int64_t *> cpo_dev(n_plans);
@@ -290,7 +290,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     std::vector<DaPlan> da(n_plans);
     std::vector<ObjPlan> obj(n_plans);
     std::vector<CommitPlan> com(n_plans);
-    std::vector<int64_t> rows_off(n_plans + 1, 0), price_off(n_plans + 1, 0), na_off(n_plans + 1, 0), na_list(n_plans);
+    std::vector<int64_t> rows_off(n_plans + 1, 0), price_off(n_plans + 1, 0), na_off(n_plans + 1, 0);
     std::vector<int32_t> targets(n_plans);
     const size_t argb = mp_args_bytes();
     std::vector<unsigned char> mpargs((size_t)n_plans * argb);
@@ -321,7 +321,6 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         rows_off[i + 1] = rows_off[i] + h.Dt.n_rows;
         price_off[i + 1] = price_off[i] + prow;
         na_off[i + 1] = na_off[i] + p.NA;
-        na_list[i] = p.NA;
         targets[i] = p.n_ap;
         VMAT_TRY(mp_fill_plan_args(mpargs.data() + (size_t)i * argb, p.mp_ws, std::min(std::max(p.n_ap, 1), 96), p.DA,
                                    p.wstride, p.NA, p.sid_c, &p.vox_c, p.y, p.z_c, &b.opts, p.F_offset, p.ctl,
@@ -350,16 +349,17 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaMemcpy(b.d_mpargs, mpargs.data(), (size_t)n_plans * argb, cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_targets, targets.data(), n_plans * 4, cudaMemcpyHostToDevice));
 
-    // ---- master-problem grids: CTAs split among the plans, for every aperture count
-    std::vector<int32_t> cta((size_t)std::max(b.T, 1) * (n_plans + 1), 0);
+    // ---- master-problem launch shapes for every aperture count (the kernel splits the CTAs)
     b.grid_t.assign(std::max(b.T, 1), 1);
     b.stages_t.assign(std::max(b.T, 1), 2);
     b.smem_t.assign(std::max(b.T, 1), 0);
     b.keep_t.assign(std::max(b.T, 1), 0);
+    std::vector<int64_t> weight(n_plans);
+    for (int i = 0; i < n_plans; ++i) weight[i] = b.P[i].n_wtiles;
     for (int t = 0; t < b.T; ++t) {
         int32_t g = 0, st = 0;
         size_t sm = 0;
-        VMAT_TRY(mp_batched_grid(t + 1, na_list.data(), n_plans, cta.data() + (size_t)t * (n_plans + 1), &g, &st, &sm));
+        VMAT_TRY(mp_batched_grid(t + 1, n_plans, &g, &st, &sm));
         b.grid_t[t] = g;
         b.stages_t[t] = st;
         b.smem_t[t] = sm;
@@ -368,9 +368,10 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
             da_bytes += (double)b.P[i].n_wtiles * (128.0 + 512.0 * ((t + 1 + 3) / 4));
         b.keep_t[t] = da_bytes <= 64.0 * 1024 * 1024 ? 1 : 0;
     }
-    VMAT_TRY(b.get(&b.d_cta, cta.size()));
-    VMAT_CUDA(cudaMemcpy(b.d_cta, cta.data(), cta.size() * 4, cudaMemcpyHostToDevice));
-    (void)n_cap_all;
+    VMAT_TRY(b.get(&b.d_weight, n_plans));
+    VMAT_TRY(b.get(&b.d_gctl, 8));
+    VMAT_CUDA(cudaMemcpy(b.d_weight, weight.data(), n_plans * sizeof(int64_t), cudaMemcpyHostToDevice));
+    VMAT_CUDA(cudaMemset(b.d_gctl, 0, 32));
 
     // ---- autotune the batched D^T g over every warp-row configuration (all CPs active)
     {
@@ -378,7 +379,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         VMAT_CUDA(cudaEventCreate(&e0));
         VMAT_CUDA(cudaEventCreate(&e1));
         float best = 1e30f;
-        for (int cfg = 0; cfg < spmv_n_configs() && cfg < 16; ++cfg) {
+        for (int cfg = 0; cfg < spmv_n_configs() && cfg < 16; ++cfg) {  // warp-row families only
             if (!spmv_batched_config(cfg)) continue;
             VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s)); // warm-up
             VMAT_CUDA(cudaEventRecord(e0, s));

@@ -230,15 +230,16 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
                           int32_t *iters_acc, cudaStream_t s);
 // Batched master problems (persistent solver, one cooperative launch for all plans).
 // Per-plan arguments are an opaque mp_args_bytes() record filled by mp_fill_plan_args
-// (ws: mp_workspace_bytes(n_cap) bytes); mp_batched_grid splits the resident CTAs
-// among plans of V_list[p] compact voxels for n apertures.
+// (ws: mp_workspace_bytes(n_cap) bytes); mp_batched_grid gives the launch shape for
+// n apertures (every resident CTA; the kernel splits them among the plans).
 size_t mp_args_bytes();
 vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
                               const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
                               const vmat_bb_opts *opts, double F_offset, const int32_t *skip, int32_t *iters_acc);
-vmat_status mp_batched_grid(int32_t n, const int64_t *V_list, int32_t n_plans, int32_t *cta_start, int32_t *grid,
-                            int32_t *stages, size_t *smem);
-vmat_status mp_bb_enqueue_batched(const void *args, const int32_t *cta_start, int32_t n_plans, int32_t n,
+vmat_status mp_batched_grid(int32_t n, int32_t n_plans, int32_t *grid, int32_t *stages, size_t *smem);
+// weight: device [n_plans] (warp tiles of each plan); gctl: device [8] batch barrier, epoch and
+// active-set words.
+vmat_status mp_bb_enqueue_batched(const void *args, const int64_t *weight, unsigned *gctl, int32_t n_plans, int32_t n,
                                   int32_t grid, int32_t stages, size_t smem, int keep_in_l2, cudaStream_t s);
 vmat_status mp_bb_impl(const float *DA, int32_t V, int32_t n_ap, int64_t ld, const uint8_t *struct_id,
                        int64_t wstride, const vmat_voxels *vox, const float *lo, const float *hi, float *y,

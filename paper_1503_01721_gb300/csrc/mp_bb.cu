@@ -57,7 +57,8 @@ struct BBState {
     int32_t stop;
     int32_t iters;
     int32_t need_cauchy;
-    uint32_t ticket; // CTAs of the current pass that have written their partials
+    uint32_t ticket;  // CTAs of the current pass that have written their partials
+    int32_t started;  // elastic batched solver: the state below t was saved by a previous epoch
 };
 
 struct MPArgs {
@@ -79,6 +80,7 @@ struct MPArgs {
     int64_t n_wtiles; // 32-voxel warp tiles
     BBState *st;
     unsigned *bar_count, *bar_gen; // grid barrier of the persistent solver
+    unsigned *epoch_snap;          // elastic batched solver: the batch epoch seen at this problem's last barrier
     const int32_t *skip;           // when non-null and set, the solve is skipped (device-driven plans)
     int32_t *iters_acc;            // when non-null, the persistent solver adds its iteration count
     int32_t *status;
@@ -335,7 +337,10 @@ __device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (do
 
 // Grid barrier over n_cta co-resident CTAs (cooperative launch): arrival counter
 // plus a generation word.  Gives up after WAIT_LIMIT_CYCLES; returns false then.
-__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta) {
+// When snap_dst is given, the last CTA to arrive copies *snap_src there before it
+// releases the others, so every CTA of the barrier reads the same value after it.
+__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta, unsigned *snap_dst = nullptr,
+                          const unsigned *snap_src = nullptr) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -344,6 +349,7 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta) {
         __threadfence();
         int ok = 1;
         if (atomicAdd(count, 1u) == n_cta - 1) {
+            if (snap_dst) *(volatile unsigned *)snap_dst = *(const volatile unsigned *)snap_src;
             atomicExch(count, 0u);
             __threadfence();
             atomicAdd(gen, 1u);
@@ -363,6 +369,13 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta) {
     __syncthreads();
     return ok_s != 0;
 }
+
+// Barrier of the whole batched grid.  The last CTA to arrive records the batch
+// epoch (gctl[3]) and the set of problems still iterating (gctl[4..5]) before it
+// releases the others: the CTA split that follows reads only these words, which
+// no CTA changes until every CTA has arrived at the next batch barrier.
+struct MPArgs;
+__device__ bool batch_sync(unsigned *gctl, unsigned n_cta, const MPArgs *args, int n_plans);
 
 // Solver state every CTA keeps in shared memory (identical in all CTAs).
 struct PState {
@@ -393,12 +406,13 @@ struct WarpPipe {
     uint64_t *mb;
     const unsigned char *src;
     int64_t tile_bytes, w0, W, n_my;
+    int64_t it_base; // pipeline slot of this tile set's first tile
     uint32_t cbytes;
     int stages;
     uint64_t pol;
     __device__ __forceinline__ void issue(int64_t it) const {
         const int s = (int)(it % stages);
-        const int64_t wt = w0 + (it % n_my) * W;
+        const int64_t wt = w0 + ((it - it_base) % n_my) * W;
         mbar_arrive_expect_tx(&mb[s], cbytes);
         bulk_g2s(my + (size_t)s * cbytes, src + wt * tile_bytes, cbytes, &mb[s], pol);
     }
@@ -576,18 +590,9 @@ __device__ void solve_take_step(const MPArgs &a, const SolveSmem &S, double delt
     __syncwarp();
 }
 
-// The whole solve as CTA `cta` of the n_cta CTAs working on this problem (sm:
-// the 128-byte aligned dynamic shared memory).
-template <int NMAX>
-__device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned cta, const unsigned n_cta, int stages,
-                                              int keep_in_l2, unsigned char *sm) {
+// Shared-memory layout of the solver for NMAX apertures and `stages` tiles per warp.
+template <int NMAX> __device__ __forceinline__ SolveSmem solve_layout(unsigned char *sm, int stages, uint32_t cbytes) {
     constexpr int GMAX = NMAX / 4;
-    __shared__ PState ps;
-    __shared__ FF shff[MP_NW];
-    __shared__ int abort_s;
-    const int n = a.n;
-    const uint32_t cbytes = (uint32_t)wt_copy_bytes(n);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     SolveSmem S;
     S.stage0 = sm;
     S.sy4 = reinterpret_cast<float4 *>(sm + (size_t)MP_NW * stages * cbytes);
@@ -600,8 +605,17 @@ __device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned ct
     S.sO = S.sT + 256;
     S.sU = S.sO + 256;
     S.bars = reinterpret_cast<uint64_t *>(S.sU + 256);
+    return S;
+}
+
+// Loads one problem's tables and state into shared memory: a fresh start (y from
+// a.y, clamped by the init kernel) or, for the elastic solver, the state a
+// previous epoch saved (t, F history, step scale, y, y_prev, G_prev).
+template <int NMAX> __device__ void solve_load(const MPArgs &a, const SolveSmem &S, PState &ps, bool resume) {
+    constexpr int GMAX = NMAX / 4;
+    const int n = a.n, tid = threadIdx.x;
     for (int k = tid; k < 4 * GMAX; k += MP_THREADS) {
-        reinterpret_cast<float *>(S.sy4)[k] = k < n ? a.y[k] : 0.f; // clamped by mp_init_kernel
+        reinterpret_cast<float *>(S.sy4)[k] = k < n ? a.y[k] : 0.f;
         reinterpret_cast<float *>(S.sg4)[k] = 0.f;
     }
     for (int k = tid; k < a.n_struct; k += MP_THREADS) {
@@ -609,35 +623,80 @@ __device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned ct
         S.sO[k] = a.wo[k];
         S.sU[k] = a.wu[k];
     }
+    if (resume)
+        for (int k = tid; k < n; k += MP_THREADS) {
+            S.sYp[k] = a.yprev[k];
+            S.sGp[k] = a.Gprev[k];
+        }
     if (tid == 0) {
         PState z = {};
         ps = z;
-        abort_s = 0;
-    }
-    WarpPipe P;
-    P.my = S.stage0 + (size_t)wid * stages * cbytes;
-    P.mb = S.bars + wid * stages;
-    P.src = reinterpret_cast<const unsigned char *>(a.DA);
-    P.tile_bytes = a.wstride * 4;
-    P.W = (int64_t)n_cta * MP_NW;
-    P.w0 = (int64_t)cta * MP_NW + wid;
-    P.n_my = P.w0 < a.n_wtiles ? (a.n_wtiles - 1 - P.w0) / P.W + 1 : 0;
-    P.cbytes = cbytes;
-    P.stages = stages;
-    // DA is read again by every iteration: keep it in L2 when it fits there
-    P.pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
-    if (lane == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&P.mb[s], 1);
-        fence_mbar_init();
+        if (resume) {
+            for (int i = 0; i < 6; ++i) ps.F_hist[i] = a.st->F_hist[i];
+            ps.F = a.st->F;
+            ps.delta0 = a.st->delta0;
+            ps.gg = a.st->gg;
+            ps.t = a.st->t;
+        }
     }
     __syncthreads();
-    if (lane == 0 && P.n_my > 0)
-        for (int s = 0; s < stages; ++s) P.issue(s);
-    int64_t it = 0; // pipeline slots consumed by this warp
+}
+
+// The state a later epoch resumes from (one CTA writes it).
+template <int NMAX> __device__ void solve_save(const MPArgs &a, const SolveSmem &S, const PState &ps) {
+    const float *y = reinterpret_cast<const float *>(S.sy4);
+    for (int k = threadIdx.x; k < a.n; k += MP_THREADS) {
+        a.y[k] = y[k];
+        a.yprev[k] = S.sYp[k];
+        a.Gprev[k] = S.sGp[k];
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 6; ++i) a.st->F_hist[i] = ps.F_hist[i];
+        a.st->F = ps.F;
+        a.st->delta0 = ps.delta0;
+        a.st->gg = ps.gg;
+        a.st->t = ps.t;
+        a.st->started = 1;
+    }
+    __threadfence();
+}
+
+// The end of a solve (one CTA): y, the report and the iteration count.
+template <int NMAX> __device__ void solve_finish(const MPArgs &a, const SolveSmem &S, const PState &ps, bool ok) {
+    const float *y = reinterpret_cast<const float *>(S.sy4);
+    if (ok)
+        for (int k = threadIdx.x; k < a.n; k += MP_THREADS) a.y[k] = y[k];
+    if (threadIdx.x == 0) {
+        a.st->F = ps.F;
+        a.st->t = ps.t;
+        a.st->done = 1;
+        a.st->stop = ok ? ps.stop : VMAT_STOP_MAXIT;
+        a.st->iters = ps.t + 1;
+        a.st->delta0 = ps.delta0;
+        if (ok && a.iters_acc) *a.iters_acc += ps.t + 1;
+    }
+    __threadfence();
+}
+
+enum { LOOP_DONE = 0, LOOP_ABORT = 1, LOOP_REBALANCE = 2 };
+
+// BB iterations of one problem as CTA `cta` of n_cta, until a stopping rule
+// (LOOP_DONE), a wait that ran out (LOOP_ABORT) or, for the elastic solver
+// (epoch_src non-null), a change of the batch epoch seen at the second barrier of
+// an iteration (LOOP_REBALANCE, after this CTA has saved the state if cta == 0).
+template <int NMAX>
+__device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PState &ps, int64_t &it,
+                          const unsigned cta, const unsigned n_cta, const unsigned *epoch_src, unsigned epoch_local) {
+    constexpr int GMAX = NMAX / 4;
+    __shared__ FF shff[MP_NW];
+    __shared__ int abort_s;
+    const int n = a.n;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) abort_s = 0;
+    __syncthreads();
     float gacc[NMAX];
     FF *part = reinterpret_cast<FF *>(a.part);
     FF *cpart = reinterpret_cast<FF *>(a.cpart);
-    bool ok = true;
     while (true) {
         // ---- pass: z = DA y, g, F and this CTA's shares of G = -DA^T g
 #pragma unroll
@@ -661,34 +720,27 @@ __device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned ct
             part[(int64_t)cta * (n + 1) + k] = sum;
         }
         if (tid == 0) part[(int64_t)cta * (n + 1) + n] = fb;
-        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) {
-            ok = false;
-            break;
-        }
+        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) return LOOP_ABORT;
         // ---- column reduction: warp w of CTA c sums columns c * MP_NW + w, + MP_NW * n_cta, ...
         for (int k = (int)cta * MP_NW + wid; k <= n; k += MP_NW * (int)n_cta) {
-            {
-                FF v{0.f, 0.f};
-                for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) { // eight loads in flight per lane
-                    float2 q[8];
+            FF v{0.f, 0.f};
+            for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) { // eight loads in flight per lane
+                float2 q[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const unsigned b = b0 + 32u * u;
-                        q[u] = b < n_cta ? __ldcg(reinterpret_cast<const float2 *>(part) + (int64_t)b * (n + 1) + k)
-                                         : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
+                for (int u = 0; u < 8; ++u) {
+                    const unsigned b = b0 + 32u * u;
+                    q[u] = b < n_cta ? __ldcg(reinterpret_cast<const float2 *>(part) + (int64_t)b * (n + 1) + k)
+                                     : make_float2(0.f, 0.f);
                 }
 #pragma unroll
-                for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
-                if (lane == 0) a.G[k] = ff_to_double(v);
+                for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
             }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
+            if (lane == 0) a.G[k] = ff_to_double(v);
         }
-        if (!grid_sync(a.bar_count, a.bar_gen, n_cta)) {
-            ok = false;
-            break;
-        }
+        if (!grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
+            return LOOP_ABORT;
         for (int k = tid; k < n; k += MP_THREADS) S.sG[k] = -__ldcg(a.G + k);
         if (tid == 0) ps.F = __ldcg(a.G + n) + a.F_offset;
         __syncthreads();
@@ -707,10 +759,7 @@ __device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned ct
             if (!c_ok && lane == 0) atomicOr(&abort_s, 1);
             const FF cb = block_ff(FF{cs, -cc}, shff);
             if (tid == 0) cpart[cta] = cb;
-            if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) {
-                ok = false;
-                break;
-            }
+            if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) return LOOP_ABORT;
             if (wid == 0) {
                 FF v{0.f, 0.f};
                 for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) {
@@ -739,34 +788,49 @@ __device__ __forceinline__ void mp_solve_body(const MPArgs &a, const unsigned ct
             }
             __syncthreads();
         }
-        if (ps.done) break;
+        if (ps.done) return LOOP_DONE;
         if (tid == 0) ++ps.t;
         __syncthreads();
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(a.status, DEV_TIMEOUT);
-    }
-    // copies issued ahead for a pass that will not run: let them land before exit
-    if (lane == 0 && P.n_my > 0)
-        for (int s = 0; s < stages; ++s) P.wait(it + s);
-    __syncwarp();
-    if (cta == 0 && ok) {
-        const float *y = reinterpret_cast<const float *>(S.sy4);
-        for (int k = tid; k < n; k += MP_THREADS) a.y[k] = y[k];
-        if (tid == 0) {
-            a.st->F = ps.F;
-            a.st->t = ps.t;
-            a.st->done = 1;
-            a.st->stop = ps.stop;
-            a.st->iters = ps.t + 1;
-            a.st->delta0 = ps.delta0;
-            if (a.iters_acc) *a.iters_acc += ps.t + 1;
+        if (epoch_src && __ldcg(a.epoch_snap) != epoch_local) { // the same word for every CTA of the problem
+            if (cta == 0) solve_save<NMAX>(a, S, ps);
+            return LOOP_REBALANCE;
         }
     }
-    if (cta == 0 && !ok && tid == 0) {
-        a.st->done = 1;
-        a.st->stop = VMAT_STOP_MAXIT;
-        a.st->iters = ps.t + 1;
+}
+
+// Sets up a warp's pipeline for tiles w0, w0 + W, ... of problem a, starting at slot it.
+__device__ __forceinline__ void pipe_start(WarpPipe &P, const MPArgs &a, unsigned cta, unsigned n_cta, int64_t it) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    P.src = reinterpret_cast<const unsigned char *>(a.DA);
+    P.tile_bytes = a.wstride * 4;
+    P.W = (int64_t)n_cta * MP_NW;
+    P.w0 = (int64_t)cta * MP_NW + wid;
+    P.n_my = P.w0 < a.n_wtiles ? (a.n_wtiles - 1 - P.w0) / P.W + 1 : 0;
+    P.it_base = it;
+    if (lane == 0 && P.n_my > 0)
+        for (int s = 0; s < P.stages; ++s) P.issue(it + s);
+}
+
+// Copies issued ahead for a pass that will not run: let them land (this warp's slots it ..).
+__device__ __forceinline__ void pipe_drain(const WarpPipe &P, int64_t it) {
+    if ((threadIdx.x & 31) == 0 && P.n_my > 0)
+        for (int s = 0; s < P.stages; ++s) P.wait(it + s);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void pipe_init(WarpPipe &P, const SolveSmem &S, int stages, uint32_t cbytes,
+                                          int keep_in_l2) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    P.my = S.stage0 + (size_t)wid * stages * cbytes;
+    P.mb = S.bars + wid * stages;
+    P.cbytes = cbytes;
+    P.stages = stages;
+    // DA is read again by every iteration: keep it in L2 when it fits there
+    P.pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
+    P.n_my = 0;
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&P.mb[s], 1);
+        fence_mbar_init();
     }
 }
 
@@ -774,44 +838,166 @@ template <int NMAX>
 __global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
     if (a.skip && *a.skip) return; // the same flag for every CTA: all return together
     extern __shared__ __align__(128) unsigned char sm_raw[];
+    __shared__ PState ps;
     // align the staging area explicitly: static shared memory may shift the dynamic region
     unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
-    mp_solve_body<NMAX>(a, blockIdx.x, gridDim.x, stages, keep_in_l2, sm);
+    const uint32_t cbytes = (uint32_t)wt_copy_bytes(a.n);
+    const SolveSmem S = solve_layout<NMAX>(sm, stages, cbytes);
+    WarpPipe P;
+    pipe_init(P, S, stages, cbytes, keep_in_l2);
+    solve_load<NMAX>(a, S, ps, false); // ends with a __syncthreads (barriers initialised)
+    int64_t it = 0;
+    pipe_start(P, a, blockIdx.x, gridDim.x, it);
+    const int r = solve_loop<NMAX>(a, S, P, ps, it, blockIdx.x, gridDim.x, nullptr, 0u);
+    if (r == LOOP_ABORT && threadIdx.x == 0) atomicOr(a.status, DEV_TIMEOUT);
+    pipe_drain(P, it);
+    if (blockIdx.x == 0) solve_finish<NMAX>(a, S, ps, r != LOOP_ABORT);
 }
 
-// Several independent problems in one persistent launch: CTAs cta_start[p] ..
-// cta_start[p + 1] - 1 solve problem p (its own grid barrier and workspace);
-// every problem has n apertures.  CTAs of a skipped problem return at once.
-template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS)
-    mp_solve_batched_kernel(const MPArgs *__restrict__ args, const int32_t *__restrict__ cta_start, int32_t n_plans,
-                            int32_t n, int stages, int keep_in_l2) {
-    __shared__ MPArgs sa;
-    __shared__ int sp;
+__device__ bool batch_sync(unsigned *gctl, unsigned n_cta, const MPArgs *args, int n_plans) {
+    __shared__ int ok_s;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int lo = 0, hi = n_plans; // cta_start[lo] <= blockIdx.x < cta_start[hi]
-        while (hi - lo > 1) {
-            const int m = (lo + hi) >> 1;
-            if (cta_start[m] <= (int)blockIdx.x) lo = m;
-            else hi = m;
+        volatile unsigned *vg = gctl + 1;
+        const unsigned g0 = *vg;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(gctl, 1u) == n_cta - 1) {
+            unsigned long long mask = 0ull;
+            for (int p = 0; p < n_plans; ++p) {
+                const MPArgs &q = args[p];
+                const bool act = !(q.skip && *(volatile const int32_t *)q.skip) && !*(volatile int32_t *)&q.st->done;
+                if (act) mask |= 1ull << p;
+            }
+            gctl[4] = (unsigned)(mask & 0xffffffffu);
+            gctl[5] = (unsigned)(mask >> 32);
+            gctl[3] = *(volatile unsigned *)(gctl + 2);
+            atomicExch(gctl, 0u);
+            __threadfence();
+            atomicAdd(gctl + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vg == g0) {
+                if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
-        sp = lo;
+        __threadfence();
+        ok_s = ok;
     }
     __syncthreads();
-    const int p = sp;
-    for (int i = threadIdx.x; i < (int)(sizeof(MPArgs) / 4); i += MP_THREADS)
-        reinterpret_cast<int32_t *>(&sa)[i] = reinterpret_cast<const int32_t *>(args + p)[i];
-    __syncthreads();
-    if (threadIdx.x == 0) sa.n = n;
-    __syncthreads();
-    if (sa.skip && *sa.skip) return;
+    return ok_s != 0;
+}
+
+// Several independent problems in one persistent launch.  All CTAs are split
+// among the problems still iterating, in proportion to their warp tiles (the same
+// computation in every CTA); each problem has its own grid barrier.  When a
+// problem stops it bumps the batch epoch (gctl[2]); every other problem sees the
+// change at its next second barrier, saves its state and joins a barrier of the
+// whole grid (gctl[0..1]), after which the CTAs are split again among the
+// problems left.  Every problem has n apertures.
+template <int NMAX>
+__global__ void __launch_bounds__(MP_THREADS)
+    mp_solve_batched_kernel(const MPArgs *__restrict__ args, const int64_t *__restrict__ weight, int32_t n_plans,
+                            int32_t n, unsigned *gctl, int stages, int keep_in_l2) {
     extern __shared__ __align__(128) unsigned char sm_raw[];
+    __shared__ MPArgs sa;
+    __shared__ PState ps;
+    __shared__ int sp, sc, sn, resume_s;
+    __shared__ unsigned epoch_s;
     unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
-    mp_solve_body<NMAX>(sa, blockIdx.x - cta_start[p], cta_start[p + 1] - cta_start[p], stages, keep_in_l2, sm);
+    const uint32_t cbytes = (uint32_t)wt_copy_bytes(n);
+    const SolveSmem S = solve_layout<NMAX>(sm, stages, cbytes);
+    WarpPipe P;
+    pipe_init(P, S, stages, cbytes, keep_in_l2);
+    __syncthreads();
+    int64_t it = 0;
+    unsigned epoch_local = 0;
+    bool ok = true;
+    while (true) {
+        if (threadIdx.x == 0) { // CTA split among the problems still iterating (identical in every CTA)
+            const unsigned long long mask =
+                (unsigned long long)__ldcg(gctl + 4) | ((unsigned long long)__ldcg(gctl + 5) << 32);
+            double wsum = 0.0;
+            int n_act = 0;
+            for (int q = 0; q < n_plans; ++q)
+                if ((mask >> q) & 1ull) {
+                    wsum += (double)weight[q];
+                    ++n_act;
+                }
+            sp = -1;
+            if (n_act > 0) {
+                const int G = (int)gridDim.x;
+                int start = 0, seen = 0;
+                for (int q = 0; q < n_plans && sp < 0; ++q) {
+                    if (!((mask >> q) & 1ull)) continue;
+                    ++seen;
+                    int cnt = seen == n_act ? G - start
+                                            : 1 + (int)((double)(G - n_act) * (double)weight[q] / wsum);
+                    cnt = max(1, min(cnt, G - start - (n_act - seen)));
+                    if ((int)blockIdx.x < start + cnt) {
+                        sp = q;
+                        sc = (int)blockIdx.x - start;
+                        sn = cnt;
+                    }
+                    start += cnt;
+                }
+            }
+            epoch_s = __ldcg(gctl + 3); // the epoch at the last batch barrier
+        }
+        __syncthreads();
+        const int p = sp;
+        if (p < 0) break;
+        epoch_local = epoch_s;
+        for (int i = threadIdx.x; i < (int)(sizeof(MPArgs) / 4); i += MP_THREADS)
+            reinterpret_cast<int32_t *>(&sa)[i] = reinterpret_cast<const int32_t *>(args + p)[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sa.n = n;
+            resume_s = *(volatile int32_t *)&args[p].st->started;
+        }
+        __syncthreads();
+        const unsigned c = (unsigned)sc, nc = (unsigned)sn;
+        solve_load<NMAX>(sa, S, ps, resume_s != 0);
+        pipe_start(P, sa, c, nc, it);
+        const int r = solve_loop<NMAX>(sa, S, P, ps, it, c, nc, gctl + 2, epoch_local);
+        pipe_drain(P, it);
+        if (P.n_my > 0) it += stages; // the drained slots were issued (a warp without tiles issued none)
+        if (r == LOOP_ABORT) {
+            ok = false;
+            if (threadIdx.x == 0) atomicOr(sa.status, DEV_TIMEOUT);
+            if (c == 0) solve_finish<NMAX>(sa, S, ps, false);
+            break;
+        }
+        if (r == LOOP_DONE && c == 0) {
+            solve_finish<NMAX>(sa, S, ps, true);
+            if (threadIdx.x == 0) atomicAdd(gctl + 2, 1u);
+        }
+        if (!batch_sync(gctl, gridDim.x, args, n_plans)) {
+            ok = false;
+            if (threadIdx.x == 0) atomicOr(sa.status, DEV_TIMEOUT);
+            break;
+        }
+    }
+    (void)ok;
 }
 
 // Per-problem set-up of the batched solver (one block per problem).
-__global__ void mp_init_batched_kernel(const MPArgs *__restrict__ args, int32_t n) {
+// gctl words: [0] arrivals, [1] generation of the batch barrier, [2] the batch
+// epoch (bumped when a problem stops), [3] the epoch seen at the last batch
+// barrier, [4..5] the problems still iterating then (a 64-bit mask).
+__global__ void mp_init_batched_kernel(const MPArgs *__restrict__ args, int32_t n_plans, int32_t n, unsigned *gctl) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long mask = 0ull;
+        for (int p = 0; p < n_plans; ++p)
+            if (!(args[p].skip && *args[p].skip)) mask |= 1ull << p;
+        gctl[0] = gctl[1] = gctl[2] = gctl[3] = 0u;
+        gctl[4] = (unsigned)(mask & 0xffffffffu);
+        gctl[5] = (unsigned)(mask >> 32);
+    }
     MPArgs a = args[blockIdx.x];
     a.n = n;
     if (a.skip && *a.skip) return;
@@ -821,6 +1007,7 @@ __global__ void mp_init_batched_kernel(const MPArgs *__restrict__ args, int32_t 
         *a.st = st;
         *a.bar_count = 0u;
         *a.bar_gen = 0u;
+        *a.epoch_snap = 0u;
     }
 }
 
@@ -1006,7 +1193,7 @@ static SolveFn solve_kernel_for(int n) {
     default: return nullptr;
     }
 }
-using SolveBatchFn = void (*)(const MPArgs *, const int32_t *, int32_t, int32_t, int, int);
+using SolveBatchFn = void (*)(const MPArgs *, const int64_t *, int32_t, int32_t, unsigned *, int, int);
 static SolveBatchFn solve_batched_kernel_for(int n) {
     switch ((n + 7) / 8) {
     case 1: return mp_solve_batched_kernel<8>;
@@ -1095,6 +1282,7 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.st = reinterpret_cast<BBState *>(p);
     a.bar_count = reinterpret_cast<unsigned *>(p + 192);
     a.bar_gen = reinterpret_cast<unsigned *>(p + 224);
+    a.epoch_snap = reinterpret_cast<unsigned *>(p + 240);
     p += 256;
     a.G = reinterpret_cast<double *>(p); // [n + 1]: G, then F in the persistent solver
     a.Gprev = a.G + n_cap + 1;
@@ -1178,8 +1366,7 @@ vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *D
     return VMAT_OK;
 }
 
-vmat_status mp_batched_grid(int32_t n, const int64_t *V_list, int32_t n_plans, int32_t *cta_start, int32_t *grid,
-                            int32_t *stages, size_t *smem) {
+vmat_status mp_batched_grid(int32_t n, int32_t n_plans, int32_t *grid, int32_t *stages, size_t *smem) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     VMAT_TRY(mp_set_attributes());
@@ -1190,43 +1377,24 @@ vmat_status mp_batched_grid(int32_t n, const int64_t *V_list, int32_t n_plans, i
     int bps = 0;
     VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, solve_batched_kernel_for(n), MP_THREADS, sm));
     if (bps < 1) return set_error(VMAT_ECUDA, "batched master problem: kernel does not fit on an SM");
-    const int64_t P = (int64_t)ctx->n_sm * bps;
+    const int64_t P = (int64_t)ctx->n_sm * bps; // every CTA resident at once (grid barriers)
     if (P < n_plans) return set_error(VMAT_EUNSUPPORTED, "batched master problem: more plans than resident CTAs");
-    // CTAs in proportion to each problem's warp tiles, at least one, at most one per 8 tiles
-    double wsum = 0.0;
-    std::vector<int64_t> cap(n_plans);
-    for (int p = 0; p < n_plans; ++p) {
-        const int64_t wt = (std::max<int64_t>(V_list[p], 1) + MP_WT - 1) / MP_WT;
-        cap[p] = (wt + MP_NW - 1) / MP_NW;
-        wsum += (double)wt;
-    }
-    int64_t used = 0;
-    cta_start[0] = 0;
-    for (int p = 0; p < n_plans; ++p) {
-        const int64_t wt = (std::max<int64_t>(V_list[p], 1) + MP_WT - 1) / MP_WT;
-        const int64_t left_plans = n_plans - p - 1;
-        int64_t c = (int64_t)((double)(P - n_plans) * (double)wt / wsum) + 1;
-        c = std::min<int64_t>(c, std::min<int64_t>(cap[p], P - used - left_plans));
-        c = std::max<int64_t>(c, 1);
-        used += c;
-        cta_start[p + 1] = (int32_t)used;
-    }
-    *grid = (int32_t)used;
+    *grid = (int32_t)P;
     *stages = st;
     *smem = sm;
     return VMAT_OK;
 }
 
-vmat_status mp_bb_enqueue_batched(const void *args, const int32_t *cta_start, int32_t n_plans, int32_t n,
+vmat_status mp_bb_enqueue_batched(const void *args, const int64_t *weight, unsigned *gctl, int32_t n_plans, int32_t n,
                                   int32_t grid, int32_t stages, size_t smem, int keep_in_l2, cudaStream_t s) {
-    mp_init_batched_kernel<<<n_plans, 128, 0, s>>>(static_cast<const MPArgs *>(args), n);
+    mp_init_batched_kernel<<<n_plans, 128, 0, s>>>(static_cast<const MPArgs *>(args), n_plans, n, gctl);
     VMAT_LAUNCH_CHECK();
     SolveBatchFn fn = solve_batched_kernel_for(n);
     if (!fn) return set_error(VMAT_EUNSUPPORTED, "batched master problem: %d apertures", n);
     const MPArgs *a = static_cast<const MPArgs *>(args);
     int32_t np = n_plans, nn = n;
     int st = stages, l2 = keep_in_l2;
-    void *kargs[] = {&a, &cta_start, &np, &nn, &st, &l2};
+    void *kargs[] = {&a, &weight, &np, &nn, &gctl, &st, &l2};
     VMAT_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3(MP_THREADS), kargs, smem,
                                           s));
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -306,6 +306,37 @@ __device__ __forceinline__ uint32_t ldg_stream_u1(const void *p, uint64_t pol) {
     return r;
 }
 
+__device__ __forceinline__ uint32_t ldg_stream_b16(const void *p, uint64_t pol) {
+    unsigned short r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ldg_stream_b8(const void *p, uint64_t pol) {
+    unsigned short r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+// One stored value, streamed (consecutive-lane kernel).
+template <typename VT> struct StreamVal1;
+template <> struct StreamVal1<float> {
+    static __device__ __forceinline__ float load(const void *val, int64_t e, uint64_t pol) {
+        return __uint_as_float(ldg_stream_u1(static_cast<const float *>(val) + e, pol));
+    }
+};
+template <> struct StreamVal1<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const void *val, int64_t e, uint64_t pol) {
+        return __uint_as_float(ldg_stream_b16(static_cast<const uint16_t *>(val) + e, pol) << 16);
+    }
+};
+template <> struct StreamVal1<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float load(const void *val, int64_t e, uint64_t pol) {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)ldg_stream_b8(static_cast<const uint8_t *>(val) + e, pol),
+                                               __NV_E4M3);
+        return __half2float(*reinterpret_cast<__half *>(&h));
+    }
+};
+
 template <typename VT> struct StreamVals;
 template <> struct StreamVals<float> {
     static __device__ __forceinline__ void load4(const void *val, int64_t e0, uint64_t pol, float v[4]) {
@@ -413,6 +444,55 @@ __device__ __forceinline__ float warp_row_sum(const int64_t *__restrict__ rowptr
     return sum;
 }
 
+// The same row sum with consecutive entries across the lanes: chunk m of 32 U
+// entries gives lane l the entries base + 32 u + l (u < U), so each gather of x
+// by the warp covers 32 consecutive (sorted) column indices and touches fewer
+// cache lines.  Scalar streaming loads of the values and columns; entry
+// base + 32 u + l goes to accumulator u % 4 of lane l, in a fixed order.
+template <int UNROLL, typename VT>
+__device__ __forceinline__ float warp_row_sum_c(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                const void *__restrict__ val, const float *__restrict__ x, int64_t r,
+                                                int lane, uint64_t pol) {
+    const int64_t s = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t b = s; b < e; b += 32 * UNROLL) {
+        float v[UNROLL];
+        int32_t c[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t i = b + 32 * u + lane;
+            if (i < e) {
+                v[u] = StreamVal1<VT>::load(val, i, pol);
+                c[u] = (int32_t)ldg_stream_u1(col + i, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (b + 32 * u + lane < e) acc[u & 3] = fmaf(v[u], __ldg(x + c[u]), acc[u & 3]);
+    }
+    float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    return sum;
+}
+
+template <int THREADS, int UNROLL, typename VT>
+__global__ void __launch_bounds__(THREADS) spmv_warp_row_c_kernel(RowParams p) {
+    if (p.skip && *p.skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    const uint64_t pol = l2_evict_first_policy();
+    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
+        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+        float sum = warp_row_sum_c<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
+        if (lane == 0) {
+            if (p.row_scale) sum *= p.row_scale[r];
+            p.y[p.row_ids ? p.row_ids[r] : r] = sum;
+        }
+    }
+}
+
 template <int THREADS, int UNROLL, typename VT>
 __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
@@ -433,7 +513,7 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
 // Several plans' matrices in one launch: global row g belongs to plan p with
 // row_off[p] <= g < row_off[p + 1] (row g - row_off[p] of that plan).  A warp
 // looks its plan up when it crosses into another plan's range.
-template <int THREADS, int UNROLL, typename VT>
+template <int THREADS, int UNROLL, typename VT, bool CONSEC>
 __global__ void __launch_bounds__(THREADS)
     spmv_rows_batched_kernel(const SpmvPlan *__restrict__ plans, const int64_t *__restrict__ row_off, int32_t n_plans,
                              int64_t total_rows) {
@@ -463,7 +543,8 @@ __global__ void __launch_bounds__(THREADS)
         if (skip) continue;
         const int64_t r = gr - lo;
         if (P.cp_active && !P.cp_active[r / P.bpc]) continue;
-        float sum = warp_row_sum<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol);
+        float sum = CONSEC ? warp_row_sum_c<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol)
+                           : warp_row_sum<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol);
         if (lane == 0) {
             if (P.row_scale) sum *= P.row_scale[r];
             P.y[P.row_ids ? P.row_ids[r] : r] = sum;
@@ -537,13 +618,13 @@ __global__ void scale_vector(const float *x, const float *s, float *out, int32_t
 // Configurations and dispatch
 // ---------------------------------------------------------------------------
 struct Cfg {
-    int family; // 0 = tile-segmented, 1 = warp per row
+    int family; // 0 = tile-segmented, 1 = warp per row (4-entry lane chunks), 2 = warp per row (consecutive lanes)
     int threads, e, stages; // tile: E entries per thread, STAGES bulk-copy stages; warp-row: e = unroll
 };
 static const Cfg kCfgs[] = {{0, 256, 16, 2}, {0, 256, 8, 3}, {0, 512, 8, 2}, {0, 128, 16, 3},
                             {1, 256, 2, 0},  {1, 256, 1, 0}, {1, 512, 4, 0}, {1, 256, 4, 0},
-                            {1, 256, 8, 0}};
-constexpr int N_CFG = 9;
+                            {1, 256, 8, 0}, {2, 256, 4, 0}, {2, 256, 8, 0}, {2, 512, 4, 0}};
+constexpr int N_CFG = 12;
 
 using TileFn = void (*)(SpmvParams);
 using RowFn = void (*)(RowParams);
@@ -564,6 +645,9 @@ template <typename VT> RowFn row_kernel_for(int cfg) {
     case 5: return spmv_warp_row_kernel<256, 1, VT>;
     case 7: return spmv_warp_row_kernel<256, 4, VT>;
     case 8: return spmv_warp_row_kernel<256, 8, VT>;
+    case 9: return spmv_warp_row_c_kernel<256, 4, VT>;
+    case 10: return spmv_warp_row_c_kernel<256, 8, VT>;
+    case 11: return spmv_warp_row_c_kernel<512, 4, VT>;
     default: return spmv_warp_row_kernel<512, 4, VT>;
     }
 }
@@ -730,16 +814,19 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
 
 template <typename VT> static RowBatchFn batched_kernel_for(int cfg) {
     switch (cfg) {
-    case 4: return spmv_rows_batched_kernel<256, 2, VT>;
-    case 5: return spmv_rows_batched_kernel<256, 1, VT>;
-    case 6: return spmv_rows_batched_kernel<512, 4, VT>;
-    case 7: return spmv_rows_batched_kernel<256, 4, VT>;
-    case 8: return spmv_rows_batched_kernel<256, 8, VT>;
+    case 4: return spmv_rows_batched_kernel<256, 2, VT, false>;
+    case 5: return spmv_rows_batched_kernel<256, 1, VT, false>;
+    case 6: return spmv_rows_batched_kernel<512, 4, VT, false>;
+    case 7: return spmv_rows_batched_kernel<256, 4, VT, false>;
+    case 8: return spmv_rows_batched_kernel<256, 8, VT, false>;
+    case 9: return spmv_rows_batched_kernel<256, 4, VT, true>;
+    case 10: return spmv_rows_batched_kernel<256, 8, VT, true>;
+    case 11: return spmv_rows_batched_kernel<512, 4, VT, true>;
     default: return nullptr;
     }
 }
 
-bool spmv_batched_config(int cfg) { return cfg >= 0 && cfg < N_CFG && kCfgs[cfg].family == 1; }
+bool spmv_batched_config(int cfg) { return cfg >= 0 && cfg < N_CFG && kCfgs[cfg].family != 0; }
 
 vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
                               int64_t total_rows, cudaStream_t s) {

@@ -11,7 +11,7 @@ U32 = 2.0 ** -24  # float32 unit roundoff
 # of roundoff bound both, for every row length.
 SPMV_C = 64
 # SpMV configurations the library offers (tile_cfg 0 .. N_SPMV_CFG - 1)
-N_SPMV_CFG = 9
+N_SPMV_CFG = 12
 
 
 def require_cuda():
