@@ -51,7 +51,8 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
 # configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
 # (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
-                 ("f32", 8): 1.0008, ("bf16", 5): 1.0083, ("fp8", 5): 1.0082}
+                 ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
+                 ("bf16", 5): 1.0083, ("fp8", 5): 1.0082}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5

@@ -225,7 +225,9 @@ vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float *pi, const 
 
 /* DA(A) = sum_{j in A} D_{:,j} (Eq. 5) for the aperture at CP `cp` with
  * leaves (device int16 [n_rows][2]).  da: device float [V], fully written.
- * Needs build_D. */
+ * Needs build_D.  The first call for an MLC shape keeps in the handle a table
+ * of where each CP's entries start in every CSR(D) row ((K + 1) x rows 16-bit
+ * offsets; cg_plan and batches build it too); it allocates device memory. */
 vmat_status aperture_dose(vmat_ddc h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
                           void *stream);
 

@@ -3,9 +3,9 @@
 // aperture_dose (Eq. 5): DA_i(A) = sum of D_ij over the beamlets j of the
 // aperture.  The paper sums COO columns on the CPU (Section 2.2.2) because its
 // GPUs only hold D^T.  Here the rows of CSR(D) are sorted by beamlet and the
-// beamlets of one CP are a contiguous index range, so each voxel row finds the
-// CP's slice with a binary search and adds the entries whose column lies
-// between the row's leaves, in beamlet order (deterministic, no atomics).
+// beamlets of one CP are a contiguous index range, so one warp per voxel row
+// finds the CP's slice (a guessed window, else a binary search) and adds the
+// entries whose column lies between the row's leaves (deterministic, no atomics).
 //
 // aperture_fluence: x = A y (beamlet fluence of a set of weighted apertures).
 // aperture_grad:    A^T pi (summed price of each aperture's beamlets).
@@ -14,17 +14,6 @@
 #include "internal.cuh"
 
 namespace vmat {
-
-__device__ __forceinline__ float load_val(const void *val, int64_t e, vmat_dtype dt) {
-    if (dt == VMAT_F32) return static_cast<const float *>(val)[e];
-    if (dt == VMAT_BF16) {
-        const uint16_t b = static_cast<const uint16_t *>(val)[e];
-        return __uint_as_float((uint32_t)b << 16);
-    }
-    const uint8_t q = static_cast<const uint8_t *>(val)[e];
-    __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
-    return __half2float(*reinterpret_cast<__half *>(&hr));
-}
 
 template <typename VT> struct StoredVal;
 template <> struct StoredVal<float> {
@@ -42,10 +31,92 @@ template <> struct StoredVal<__nv_fp8_e4m3> {
     }
 };
 
+// Start of CP cp's run in row `row` (the row's entries are sorted by beamlet):
+// from the offset table when there is one, else a binary search.
+__device__ __forceinline__ int64_t cp_run_start(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                const uint16_t *__restrict__ tab, int32_t n_rows, int32_t row,
+                                                int32_t cp, int32_t j0) {
+    const int64_t s = rowptr[row];
+    if (tab) return s + tab[(int64_t)cp * n_rows + row];
+    int64_t lo = s, hi = rowptr[row + 1];
+    while (lo < hi) { // first entry with column >= j0
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < j0) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Sum of D_ij over the beamlets j in [j0, j1) between the leaves of their MLC
+// row, in entry order (one thread per voxel row).
+template <typename VT>
+__device__ __forceinline__ float aperture_row(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                              const void *__restrict__ val, const float *__restrict__ scale,
+                                              const uint16_t *__restrict__ tab, int32_t n_rows, int32_t row,
+                                              int32_t cp, int32_t n_cols, int32_t j0, int32_t j1,
+                                              const int16_t *__restrict__ leaves) {
+    float acc = 0.f;
+    const int64_t end = rowptr[row + 1];
+    for (int64_t e = cp_run_start(rowptr, col, tab, n_rows, row, cp, j0); e < end; ++e) {
+        const int32_t j = col[e];
+        if (j >= j1) break;
+        const int32_t loc = j - j0, r = loc / n_cols, c = loc - r * n_cols;
+        if (c >= leaves[2 * r] && c < leaves[2 * r + 1]) {
+            float v = StoredVal<VT>::get(val, e);
+            if (scale) v *= scale[j];
+            acc += v;
+        }
+    }
+    return acc;
+}
+
+// Offsets of each CP's first entry in each row (one thread per row, entries in order).
+__global__ void build_cp_table(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n_rows,
+                               int32_t K, int32_t bpc, uint16_t *__restrict__ tab) {
+    for (int32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < n_rows; row += gridDim.x * blockDim.x) {
+        const int64_t s = rowptr[row], e = rowptr[row + 1];
+        int32_t k = 0;
+        for (int64_t q = s; q < e; ++q) {
+            const int32_t cpq = col[q] / bpc;
+            for (; k <= cpq && k <= K; ++k) tab[(int64_t)k * n_rows + row] = (uint16_t)(q - s);
+        }
+        for (; k <= K; ++k) tab[(int64_t)k * n_rows + row] = (uint16_t)(e - s);
+    }
+}
+
+vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s) {
+    if (!h.built_D || h.D.n_rows == 0) return VMAT_OK;
+    if (h.cp_tab && h.cp_tab_K == K && h.cp_tab_bpc == bpc) return VMAT_OK;
+    if (h.cp_tab) {
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        cudaFree(h.cp_tab);
+        h.cp_tab = nullptr;
+        h.cp_tab_K = h.cp_tab_bpc = 0;
+    }
+    if (h.D.max_row > 65535) return VMAT_OK; // offsets would not fit 16 bits: search instead
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    uint16_t *tab = nullptr;
+    const cudaError_t e = cudaMalloc(&tab, (size_t)(K + 1) * h.D.n_rows * sizeof(uint16_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VMAT_OK; // no room for the table: the aperture dose searches
+    }
+    const int grid = std::max(1, std::min(ctx->n_sm * 8, (h.D.n_rows + 255) / 256));
+    build_cp_table<<<grid, 256, 0, s>>>(h.D.rowptr, h.D.col, h.D.n_rows, K, bpc, tab);
+    VMAT_LAUNCH_CHECK();
+    h.cp_tab = tab;
+    h.cp_tab_K = K;
+    h.cp_tab_bpc = bpc;
+    return VMAT_OK;
+}
+
+template <typename VT>
 __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                     const void *__restrict__ val, vmat_dtype dt, const float *__restrict__ scale,
-                                     int32_t n_rows, const int32_t *__restrict__ row_ids, int32_t cp_arg,
-                                     const int32_t *cp_dev, const int32_t *skip, int32_t n_rrows, int32_t n_cols,
+                                     const void *__restrict__ val, const float *__restrict__ scale,
+                                     const uint16_t *__restrict__ tab, int32_t n_rows,
+                                     const int32_t *__restrict__ row_ids, int32_t cp_arg, const int32_t *cp_dev,
+                                     const int32_t *skip, int32_t n_rrows, int32_t n_cols,
                                      const int16_t *__restrict__ leaves, float *__restrict__ da, int64_t wstride) {
     if (skip && *skip) return;
     const int32_t cp = cp_dev ? *cp_dev : cp_arg;
@@ -55,30 +126,38 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
     const int32_t bpc = n_rrows * n_cols;
     const int32_t j0 = cp * bpc, j1 = j0 + bpc;
     for (int32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < n_rows; row += gridDim.x * blockDim.x) {
-        int64_t lo = rowptr[row], hi = rowptr[row + 1];
-        while (lo < hi) { // first entry with column >= j0
-            const int64_t mid = (lo + hi) >> 1;
-            if (col[mid] < j0) lo = mid + 1;
-            else hi = mid;
-        }
-        float acc = 0.f;
-        const int64_t end = rowptr[row + 1];
-        for (int64_t e = lo; e < end; ++e) {
-            const int32_t j = col[e];
-            if (j >= j1) break;
-            const int32_t loc = j - j0, r = loc / n_cols, c = loc - r * n_cols;
-            if (c >= sl[2 * r] && c < sl[2 * r + 1]) {
-                float v = load_val(val, e, dt);
-                if (scale) v *= scale[j];
-                acc += v;
-            }
-        }
+        const float acc = aperture_row<VT>(rowptr, col, val, scale, tab, n_rows, row, cp, n_cols, j0, j1, sl);
         // output: voxel space, compact row space, or the master problem's warp-tile
         // layout (row r at (r / 32) * wstride + (r % 32) * 4 from da, the column's base)
         const int64_t o =
             row_ids ? row_ids[row] : (wstride ? (int64_t)(row >> 5) * wstride + ((row & 31) << 2) : row);
         da[o] = acc;
     }
+}
+
+using DaFn = void (*)(const int64_t *, const int32_t *, const void *, const float *, const uint16_t *, int32_t,
+                      const int32_t *, int32_t, const int32_t *, const int32_t *, int32_t, int32_t, const int16_t *,
+                      float *, int64_t);
+static DaFn da_kernel_for(vmat_dtype dt) {
+    return dt == VMAT_F32 ? aperture_dose_kernel<float>
+           : dt == VMAT_BF16 ? aperture_dose_kernel<__nv_bfloat16>
+                             : aperture_dose_kernel<__nv_fp8_e4m3>;
+}
+
+static vmat_status launch_da(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int32_t *cp_dev, const int32_t *skip,
+                             const int16_t *leaves, float *da, const int32_t *row_ids, int64_t wstride, cudaStream_t s) {
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int32_t n = h.D.n_rows;
+    if (n == 0) return VMAT_OK;
+    const int32_t bpc = mlc->n_rows * mlc->n_cols;
+    const uint16_t *tab = h.cp_tab && h.cp_tab_K == mlc->K && h.cp_tab_bpc == bpc ? h.cp_tab : nullptr;
+    const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
+    da_kernel_for(h.dtype)<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
+        h.D.rowptr, h.D.col, h.D.val, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, tab, n, row_ids, cp, cp_dev, skip,
+        mlc->n_rows, mlc->n_cols, leaves, da, wstride);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
 }
 
 // Batched Eq. 5 for aperture t of every plan: global row g is compact row g - off[p]
@@ -101,27 +180,12 @@ __global__ void aperture_dose_batched_kernel(const DaPlan *__restrict__ plans, c
         const DaPlan &P = plans[a];
         if (P.skip && *P.skip) continue;
         const int32_t row = (int32_t)(gr - soff[a]);
+        const int32_t n_rows = (int32_t)(soff[a + 1] - soff[a]);
         const int32_t bpc = P.n_rrows * P.n_cols;
         const int32_t cp = P.cps[t];
-        const int32_t j0 = cp * bpc, j1 = j0 + bpc;
-        int64_t lo = P.rowptr[row], hi = P.rowptr[row + 1];
-        while (lo < hi) { // first entry with column >= j0
-            const int64_t mid = (lo + hi) >> 1;
-            if (P.col[mid] < j0) lo = mid + 1;
-            else hi = mid;
-        }
-        float acc = 0.f;
-        const int64_t end = P.rowptr[row + 1];
-        for (int64_t e = lo; e < end; ++e) {
-            const int32_t j = P.col[e];
-            if (j >= j1) break;
-            const int32_t loc = j - j0, r = loc / P.n_cols, c = loc - r * P.n_cols;
-            if (c >= P.leaves[2 * r] && c < P.leaves[2 * r + 1]) {
-                float v = StoredVal<VT>::get(P.val, e);
-                if (P.scale) v *= P.scale[j];
-                acc += v;
-            }
-        }
+        const int32_t j0 = cp * bpc;
+        const float acc = aperture_row<VT>(P.rowptr, P.col, P.val, P.scale, P.cp_tab, n_rows, row, cp, P.n_cols, j0,
+                                           j0 + bpc, P.leaves);
         P.DA[32 + (int64_t)(t >> 2) * 128 + (t & 3) + (int64_t)(row >> 5) * P.wstride + ((row & 31) << 2)] = acc;
     }
 }
@@ -142,32 +206,13 @@ vmat_status aperture_dose_batched(vmat_dtype dt, const DaPlan *plans, const int6
 
 vmat_status aperture_dose_impl(const Ddc &h, const vmat_mlc *mlc, int32_t cp, const int16_t *leaves, float *da,
                                bool compact, cudaStream_t s, int64_t wstride) {
-    DeviceCtx *ctx;
-    VMAT_TRY(device_ctx(&ctx));
     if (!compact) VMAT_CUDA(cudaMemsetAsync(da, 0, (size_t)h.V * 4, s));
-    const int32_t n = h.D.n_rows;
-    if (n == 0) return VMAT_OK;
-    const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
-    aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
-        h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n,
-        compact ? nullptr : h.D.row_ids, cp, nullptr, nullptr, mlc->n_rows, mlc->n_cols, leaves, da,
-        compact ? wstride : 0);
-    VMAT_LAUNCH_CHECK();
-    return VMAT_OK;
+    return launch_da(h, mlc, cp, nullptr, nullptr, leaves, da, compact ? nullptr : h.D.row_ids, compact ? wstride : 0, s);
 }
 
 vmat_status aperture_dose_dev(const Ddc &h, const vmat_mlc *mlc, const int32_t *cp_dev, const int16_t *leaves,
                               float *da, int64_t wstride, const int32_t *skip, cudaStream_t s) {
-    DeviceCtx *ctx;
-    VMAT_TRY(device_ctx(&ctx));
-    const int32_t n = h.D.n_rows;
-    if (n == 0) return VMAT_OK;
-    const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
-    aperture_dose_kernel<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
-        h.D.rowptr, h.D.col, h.D.val, h.dtype, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, n, nullptr, 0, cp_dev,
-        skip, mlc->n_rows, mlc->n_cols, leaves, da, wstride);
-    VMAT_LAUNCH_CHECK();
-    return VMAT_OK;
+    return launch_da(h, mlc, 0, cp_dev, skip, leaves, da, nullptr, wstride, s);
 }
 
 // x_j = sum over apertures n (in order) containing beamlet j of y_n.
@@ -237,6 +282,7 @@ vmat_status aperture_dose(vmat_ddc hd, const vmat_mlc *mlc, int32_t cp, const in
         return set_error(VMAT_EINVAL, "aperture_dose: K*n_rows*n_cols (%lld) != J (%d)",
                          (long long)mlc->K * mlc->n_rows * mlc->n_cols, h->J);
     if (cp < 0 || cp >= mlc->K) return set_error(VMAT_EINVAL, "aperture_dose: cp %d out of range", cp);
+    VMAT_TRY(ddc_cp_table(*h, mlc->K, mlc->n_rows * mlc->n_cols, as_stream(stream)));
     return aperture_dose_impl(*h, mlc, cp, leaves, da, false, as_stream(stream));
 }
 

@@ -272,6 +272,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         p.vox_c = p.vox;
         p.vox_c.struct_id = p.sid_c;
         VMAT_TRY(inactive_objective(*p.h, &p.vox, p.F0, s));
+        VMAT_TRY(ddc_cp_table(*p.h, p.K, p.bpc, s));
         batch_cp_offsets<<<std::max(1, (p.K + 256) / 256), 256, 0, s>>>(p.h->Dt.rowptr, p.K, p.bpc, cpo_dev[i]);
         VMAT_LAUNCH_CHECK();
     }
@@ -313,7 +314,9 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         q.best_leaves = p.best_leaves;
         q.best_price = p.best_price;
         q.skip = p.ctl;
-        da[i] = DaPlan{h.D.rowptr, h.D.col, h.D.val, fp8 ? h.scale : nullptr, p.NR, p.mlc.n_cols, p.cps,
+        const bool tab_ok = h.cp_tab && h.cp_tab_K == p.K && h.cp_tab_bpc == p.bpc;
+        da[i] = DaPlan{h.D.rowptr, h.D.col, h.D.val, fp8 ? h.scale : nullptr, tab_ok ? h.cp_tab : nullptr, p.K, p.NR,
+                       p.mlc.n_cols, p.cps,
                        p.best_leaves, p.DA, p.wstride, p.ctl};
         obj[i] = ObjPlan{p.z_c, h.act_vox, p.vox.struct_id, p.vox.T, p.vox.w_over, p.vox.w_under, p.g_full, p.ctl};
         com[i] = CommitPlan{p.NR, p.best_cp, p.best_price, p.best_leaves, p.occupied, p.active, p.leaves_all,

@@ -194,6 +194,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         VMAT_TRY(mp_write_labels(sid_c, NA, wstride, DA, s));
     }
     VMAT_TRY(inactive_objective(h, vox, F0, s));
+    VMAT_TRY(ddc_cp_table(h, K, bpc, s)); // CP offsets of CSR(D) rows for the aperture dose
     double F_offset = 0.0;
     VMAT_CUDA(cudaMemcpyAsync(&F_offset, F0, sizeof(double), cudaMemcpyDeviceToHost, s));
     // nonzeros per CP in CSR(D^T): algorithmic bytes of each pricing pass

@@ -80,6 +80,9 @@ void Ddc::free_all() {
     f(vox2act);
     f(scale);
     f(xs);
+    f(cp_tab);
+    cp_tab = nullptr;
+    cp_tab_K = cp_tab_bpc = 0;
     act_vox = vox2act = nullptr;
     scale = xs = nullptr;
 }

@@ -253,7 +253,8 @@ int64_t round_pad(int64_t nnz) { return ((std::max<int64_t>(nnz, 1) + NNZ_PAD - 
 
 // Sort each row of a CSR by column, check duplicates.
 vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows, int32_t *col, float *val,
-                      int32_t *bad, int n_sm, cudaStream_t s) {
+                      int32_t *bad, int n_sm, cudaStream_t s, int32_t *max_row) {
+    *max_row = 0;
     if (n_rows == 0) return VMAT_OK;
     int32_t *dmax = nullptr;
     DevBuf bmax;
@@ -265,6 +266,7 @@ vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows,
     int32_t maxlen = 0;
     VMAT_CUDA(cudaMemcpyAsync(&maxlen, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
+    *max_row = maxlen;
     if (maxlen < 2) return VMAT_OK;
     int cap_max = sort_smem_cap();
     int cap = 32;
@@ -410,11 +412,13 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
             (float *)b_val_d.p);
         VMAT_LAUNCH_CHECK();
     }
+    int32_t max_row_t = 0, max_row_d = 0;
     if (opts.build_Dt)
-        VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s));
+        VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s,
+                           &max_row_t));
     if (opts.build_D)
         VMAT_TRY(sort_rows((int64_t *)b_rp_d.p, (int32_t *)b_cnt_act.p, n_active, (int32_t *)b_col_d.p,
-                           (float *)b_val_d.p, bad, n_sm, s));
+                           (float *)b_val_d.p, bad, n_sm, s, &max_row_d));
     VMAT_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
     if (hbad & DEV_DUPLICATE) return set_error(VMAT_EINVAL, "ddc_build: duplicate (voxel, beamlet) entry in the COO input");
@@ -460,6 +464,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         m.rowptr = (int64_t *)b_rp_t.release();
         m.col = (int32_t *)b_col_t.release();
         m.row_ids = nullptr;
+        m.max_row = max_row_t;
         VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
         h->built_Dt = true;
     }
@@ -476,6 +481,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         h->vox2act = (int32_t *)b_v2a.release();
         h->n_active = n_active;
         m.row_ids = h->act_vox;
+        m.max_row = max_row_d;
         VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
         h->built_D = true;
     }

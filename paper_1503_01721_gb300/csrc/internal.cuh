@@ -73,6 +73,7 @@ constexpr int64_t NNZ_PAD = 8192; // value/column arrays padded to a multiple of
 
 struct CsrMat {
     int32_t n_rows = 0, n_cols = 0;
+    int32_t max_row = 0; // longest row
     int64_t nnz = 0, nnz_pad = 0;
     int64_t *rowptr = nullptr;   // [n_rows + 1]
     int32_t *col = nullptr;      // [nnz_pad], padding 0
@@ -103,9 +104,18 @@ struct Ddc {
     int32_t *vox2act = nullptr; // [V] voxel -> compact row or -1
     float *scale = nullptr;     // [J] FP8 per-beamlet scale
     float *xs = nullptr;        // [J] scratch: scaled x for FP8 CSR(D)
+    // Offsets of each CP's first entry in each CSR(D) row, [K + 1][n_active], for the
+    // aperture dose; built on demand for one MLC shape (cp_tab_bpc beamlets per CP).
+    uint16_t *cp_tab = nullptr;
+    int32_t cp_tab_K = 0, cp_tab_bpc = 0;
     double build_ms = 0.0;
     void free_all();
 };
+
+// Builds (or keeps) the CP offset table of CSR(D) for K CPs of bpc beamlets.  No
+// table (and VMAT_OK) when a row is longer than 16-bit offsets reach; the aperture
+// dose then searches.  Allocates device memory: not for use while capturing.
+vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s);
 
 inline Ddc *as_ddc(vmat_ddc h) { return reinterpret_cast<Ddc *>(h); }
 
@@ -172,7 +182,8 @@ struct DaPlan { // one plan's CSR(D) and warp-tile DA for the batched aperture d
     const int32_t *col;
     const void *val;
     const float *scale; // FP8 column scale, or null
-    int32_t n_rrows, n_cols;
+    const uint16_t *cp_tab; // CP offset table of CSR(D) (ddc_cp_table), or null
+    int32_t K, n_rrows, n_cols;
     const int32_t *cps;         // the aperture's CP is cps[t]
     const int16_t *leaves;      // its leaves [n_rrows][2]
     float *DA;

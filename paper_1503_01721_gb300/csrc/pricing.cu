@@ -20,16 +20,28 @@ namespace vmat {
 
 constexpr int PR_WARPS = 8;
 
+// A candidate opening: v = P_R - P_L as a double, also as an order-preserving
+// unsigned key (v is never -0: the prefix sums start at +0 and x - x = +0).
 struct RowBest {
-    double v;
+    uint64_t key;
     int32_t w, cd, L;
     bool has;
 };
 
+__device__ __forceinline__ uint64_t order_key(double v) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(uint64_t k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// The exact tie-break order (value desc, width asc, |L + R - n_cols| asc, L asc)
+// with integer compares only.
 __device__ __forceinline__ bool better(const RowBest &a, const RowBest &b) {
     if (!a.has) return false;
     if (!b.has) return true;
-    if (a.v != b.v) return a.v > b.v;
+    if (a.key != b.key) return a.key > b.key;
     if (a.w != b.w) return a.w < b.w;
     if (a.cd != b.cd) return a.cd < b.cd;
     return a.L < b.L;
@@ -49,15 +61,32 @@ __device__ int nearest_occupied(const PricingGeom &g, const uint8_t *occupied, i
     return -1;
 }
 
-// Best opening of MLC row r of CP k (one warp; P: n_cols + 1 doubles of shared
-// memory for this warp).  Writes the row's entry gw of rb_*.
+// Shared memory per warp of the row kernel: the float64 prefix sums and their
+// float32 roundings, n_cols + 1 of each.
+__host__ __device__ constexpr size_t row_smem_stride(int n_cols) { return (((size_t)(n_cols + 1) * 12) + 15) & ~15; }
+
+// Best opening of MLC row r of CP k (one warp; ws: row_smem_stride(n_cols) bytes of
+// shared memory for this warp).  Writes the row's entry gw of rb_*.
+//
+// The float64 prefix sums P_c are formed sequentially in column order (lane 0),
+// exactly as the definition.  Every feasible pair is first valued in float32 from
+// the rounded prefix sums; only the pairs whose float32 value lies within 3E of
+// the float32 maximum are valued in float64 (E = 2^-20 max|P| bounds the
+// difference between a pair's float32 value and its float64 value P_R - P_L:
+// two roundings of P to float32, one float32 and one float64 subtraction, each at
+// most 2^-24 or 2^-53 relative, with a factor 4 to spare).  The pairs that attain
+// the float64 maximum are always among them, so the choice, ties included, is the
+// one the exhaustive float64 search makes.
 __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float *__restrict__ pi,
                                                const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
-                                               int64_t gw, double *P, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok) {
+                                               int64_t gw, unsigned char *ws, double *rb_v, int16_t *rb_lr,
+                                               uint8_t *rb_ok) {
     const int lane = threadIdx.x & 31;
     const int k = (int)(gw / g.n_rows), r = (int)(gw % g.n_rows);
     if (occupied[k]) return;
     const int N = g.n_cols;
+    double *P = reinterpret_cast<double *>(ws);
+    float *P32 = reinterpret_cast<float *>(ws + (size_t)(N + 1) * 8);
     int Lmin = 0, Lmax = N, Rmin = 0, Rmax = N;
     for (int dir = -1; dir <= 1; dir += 2) {
         const int kk = nearest_occupied(g, occupied, k, dir, lane);
@@ -80,16 +109,41 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
         }
     }
     __syncwarp();
+    float pmax = 0.f;
+    for (int c = lane; c <= N; c += 32) {
+        const float q = (float)P[c];
+        P32[c] = q;
+        pmax = fmaxf(pmax, fabsf(q));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, d));
+    __syncwarp();
+    // float32 maximum over the feasible pairs
+    float m32 = -INFINITY;
+    for (int L = Lmin + lane; L <= Lmax; L += 32) {
+        const float pl = P32[L];
+        for (int R = max(L, Rmin); R <= Rmax; ++R) m32 = fmaxf(m32, P32[R] - pl);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) m32 = fmaxf(m32, __shfl_xor_sync(0xffffffffu, m32, d));
+    const float E = pmax * 0x1p-20f + 0x1p-140f;
+    // (prefix sums beyond the float32 range: every pair is a candidate)
+    const float thr = isfinite(pmax) ? m32 - 3.f * E : -INFINITY;
+    // float64 values of the candidates, exact key order
     RowBest best;
     best.has = false;
-    best.v = 0.0;
+    best.key = 0;
     best.w = best.cd = best.L = 0;
     for (int L = Lmin + lane; L <= Lmax; L += 32) {
-        const double PL = P[L];
+        const float pl = P32[L];
+        const long long bl = __double_as_longlong(P[L]);
         for (int R = max(L, Rmin); R <= Rmax; ++R) {
+            if (P32[R] - pl < thr) continue;
+            const long long br = __double_as_longlong(P[R]);
+            const double v = br == bl ? 0.0 : P[R] - P[L];
             RowBest c;
             c.has = true;
-            c.v = P[R] - PL;
+            c.key = order_key(v);
             c.w = R - L;
             c.cd = abs(L + R - N);
             c.L = L;
@@ -99,7 +153,7 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         RowBest o;
-        o.v = __shfl_down_sync(0xffffffffu, best.v, d);
+        o.key = __shfl_down_sync(0xffffffffu, best.key, d);
         o.w = __shfl_down_sync(0xffffffffu, best.w, d);
         o.cd = __shfl_down_sync(0xffffffffu, best.cd, d);
         o.L = __shfl_down_sync(0xffffffffu, best.L, d);
@@ -107,7 +161,7 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
         if (lane + d < 32 && better(o, best)) best = o;
     }
     if (lane == 0) {
-        rb_v[gw] = best.v;
+        rb_v[gw] = best.has ? key_value(best.key) : 0.0;
         rb_lr[2 * gw] = (int16_t)best.L;
         rb_lr[2 * gw + 1] = (int16_t)(best.L + best.w);
         rb_ok[gw] = best.has ? 1 : 0;
@@ -119,11 +173,11 @@ __global__ void __launch_bounds__(PR_WARPS * 32)
                       const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok,
                       const int32_t *skip) {
     if (skip && *skip) return;
-    extern __shared__ double sP[]; // PR_WARPS x (n_cols + 1)
+    extern __shared__ __align__(16) unsigned char sP[]; // PR_WARPS x row_smem_stride(n_cols)
     const int wid = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
     if (gw >= (int64_t)g.K * g.n_rows) return;
-    price_row_warp(g, pi, occupied, leaves, gw, sP + wid * (g.n_cols + 1), rb_v, rb_lr, rb_ok);
+    price_row_warp(g, pi, occupied, leaves, gw, sP + wid * row_smem_stride(g.n_cols), rb_v, rb_lr, rb_ok);
 }
 
 constexpr int CP_THREADS = 1024;
@@ -201,7 +255,7 @@ __global__ void __launch_bounds__(CP_THREADS)
 __global__ void __launch_bounds__(PR_WARPS * 32)
     price_rows_batched_kernel(const PricePlan *__restrict__ plans, const int64_t *__restrict__ off, int32_t n_plans,
                               int64_t total, int32_t max_cols) {
-    extern __shared__ double sP[]; // PR_WARPS x (max_cols + 1)
+    extern __shared__ __align__(16) unsigned char sP[]; // PR_WARPS x row_smem_stride(max_cols)
     __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
     for (int i = threadIdx.x; i <= n_plans; i += blockDim.x) soff[i] = off[i];
     __syncthreads();
@@ -216,8 +270,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32)
     }
     const PricePlan &P = plans[a];
     if (P.skip && *P.skip) return;
-    price_row_warp(P.g, P.pi, P.occupied, P.leaves, gw - soff[a], sP + wid * (max_cols + 1), P.rb_v, P.rb_lr,
-                   P.rb_ok);
+    price_row_warp(P.g, P.pi, P.occupied, P.leaves, gw - soff[a], sP + wid * row_smem_stride(max_cols), P.rb_v,
+                   P.rb_lr, P.rb_ok);
 }
 
 __global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const PricePlan *__restrict__ plans) {
@@ -244,13 +298,13 @@ vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, 
     static bool attr_set = false;
     if (!attr_set) {
         VMAT_CUDA(cudaFuncSetAttribute(price_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(PR_WARPS * 1025 * sizeof(double))));
+                                       (int)(PR_WARPS * row_smem_stride(1024))));
         attr_set = true;
     }
     if (total > 0) {
         const int64_t blocks = (total + PR_WARPS - 1) / PR_WARPS;
-        price_rows_batched_kernel<<<(unsigned)blocks, PR_WARPS * 32, (size_t)PR_WARPS * (max_cols + 1) * sizeof(double),
-                                    s>>>(plans, off, n_plans, total, max_cols);
+        price_rows_batched_kernel<<<(unsigned)blocks, PR_WARPS * 32, PR_WARPS * row_smem_stride(max_cols), s>>>(
+            plans, off, n_plans, total, max_cols);
         VMAT_LAUNCH_CHECK();
     }
     price_cps_batched_kernel<<<n_plans, CP_THREADS, 0, s>>>(plans);
@@ -267,11 +321,11 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
     double *rb_v = static_cast<double *>(ws);
     int16_t *rb_lr = reinterpret_cast<int16_t *>(rb_v + rows);
     uint8_t *rb_ok = reinterpret_cast<uint8_t *>(rb_lr + 2 * rows);
-    const size_t smem = (size_t)PR_WARPS * (g.n_cols + 1) * sizeof(double);
+    const size_t smem = PR_WARPS * row_smem_stride(g.n_cols);
     static bool attr_set = false;
     if (!attr_set) {
         VMAT_CUDA(cudaFuncSetAttribute(price_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(PR_WARPS * 1025 * sizeof(double))));
+                                       (int)(PR_WARPS * row_smem_stride(1024))));
         attr_set = true;
     }
     const int64_t blocks = (rows + PR_WARPS - 1) / PR_WARPS;
