@@ -43,6 +43,15 @@ R8  Ties: a row opening [L, R) is chosen by (value desc, width asc,
     prices, the CP price the sequential float64 sum over rows.
 R9  The loop stops when the best CP price is <= 0 (no aperture lowers F) or
     when n_apertures have been generated.
+R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
+    not pass the right leaf of an adjacent row, L_r <= min(R_{r-1}, R_{r+1}).
+    The best aperture of a CP is then a chain over the rows: the sequential
+    float64 sum of row values, maximised by dynamic programming over the row
+    states (L, R) in row order (the sum is monotone in the partial sum, so the
+    optimum of each prefix extends to the optimum of the next).  A state's
+    predecessor is the compatible state of the previous row with the largest
+    partial sum, ties by the row key of R8; the last row's state likewise.
+    Backtracking from it gives the aperture.
 """
 from __future__ import annotations
 
@@ -185,6 +194,87 @@ def price_cp(mlc, pi, occupied, leaves, k: int):
     return price, out
 
 
+def _state_order(val, L, R, N):
+    """Sort key arrays for 'better first': value desc, width asc, centredness asc, L asc."""
+    return (L, np.abs(L + R - N), R - L, -val)
+
+
+def _better(va, La, Ra, vb, Lb, Rb, N):
+    """Elementwise: is state a strictly better than state b (R8 order on the partial sums)?"""
+    wa, wb = Ra - La, Rb - Lb
+    ca, cb = np.abs(La + Ra - N), np.abs(Lb + Rb - N)
+    return (va > vb) | ((va == vb) & ((wa < wb) | ((wa == wb) & ((ca < cb) | ((ca == cb) & (La < Lb))))))
+
+
+def price_cp_interdig(mlc, pi, occupied, leaves, k: int, with_leaves: bool = True):
+    """Best aperture at CP k under the interdigitation constraint (reading R10).
+
+    Row states are the feasible (L, R) of R7 with L <= R; S_r(L, R) = S_{r-1}(pred)
+    + (P_R - P_L) in float64, S_0 = P_R - P_L.  Compatible predecessors of (L', R')
+    are the states (L, R) with L <= R' and L' <= R.  Returns (price, leaves) or
+    (None, None) when no chain is feasible.
+    """
+    Lmin, Lmax, Rmin, Rmax = leaf_windows(mlc, occupied, leaves, k)
+    N = mlc.n_cols
+    base = k * mlc.n_rows * N
+    Lg, Rg = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    NEG = -np.inf
+    S = None
+    preds = []
+    for r in range(mlc.n_rows):
+        P = prefix_sums(pi[base + r * N: base + (r + 1) * N])
+        feas = (Lg <= Rg) & (Lg >= Lmin[r]) & (Lg <= Lmax[r]) & (Rg >= Rmin[r]) & (Rg <= Rmax[r])
+        v = np.where(feas, P[Rg] - P[Lg], NEG)
+        if S is None:
+            S_new = v
+            preds.append(None)
+        else:
+            # C[L][b]: best state (L, R) with R >= b (suffix over R), then M[a][b]: best of
+            # C[L][b] over L <= a (prefix over L); pred of (L', R') = M[R'][L']
+            bestL = np.tile(np.arange(N + 1)[:, None], (1, N + 1))
+            bestR = np.full((N + 1, N + 1), N, np.int64)
+            bestV = S[:, N].copy()[:, None].repeat(N + 1, axis=1)
+            cL = np.arange(N + 1)
+            cR = np.full(N + 1, N, np.int64)
+            cV = S[:, N].copy()
+            for b in range(N, -1, -1):
+                if b < N:
+                    cand = _better(S[:, b], cL, np.full(N + 1, b), cV, cL, cR, N)
+                    cV = np.where(cand, S[:, b], cV)
+                    cR = np.where(cand, b, cR)
+                bestV[:, b], bestR[:, b] = cV, cR
+            mV = np.empty((N + 1, N + 1))
+            mL = np.empty((N + 1, N + 1), np.int64)
+            mR = np.empty((N + 1, N + 1), np.int64)
+            pV, pL, pR = bestV[0].copy(), np.zeros(N + 1, np.int64), bestR[0].copy()
+            for a in range(N + 1):
+                if a > 0:
+                    cand = _better(bestV[a], np.full(N + 1, a), bestR[a], pV, pL, pR, N)
+                    pV = np.where(cand, bestV[a], pV)
+                    pL = np.where(cand, a, pL)
+                    pR = np.where(cand, bestR[a], pR)
+                mV[a], mL[a], mR[a] = pV, pL, pR
+            predV, predL, predR = mV[Rg, Lg], mL[Rg, Lg], mR[Rg, Lg]
+            S_new = np.where(feas & (predV > NEG), predV + v, NEG)
+            preds.append((predL, predR))
+        S = S_new
+    flat = np.argwhere(S > NEG)
+    if len(flat) == 0:
+        return None, None
+    Lf, Rf = flat[:, 0], flat[:, 1]
+    o = np.lexsort(_state_order(S[Lf, Rf], Lf, Rf, N))
+    L, R = int(Lf[o[0]]), int(Rf[o[0]])
+    price = float(S[L, R])
+    if not with_leaves:
+        return price, None
+    out = np.zeros((mlc.n_rows, 2), np.int64)
+    for r in range(mlc.n_rows - 1, -1, -1):
+        out[r] = (L, R)
+        if r > 0:
+            L, R = int(preds[r][0][L, R]), int(preds[r][1][L, R])
+    return price, out
+
+
 def price_apertures(mlc, pi, occupied, leaves):
     """Best CP over the unoccupied ones and its aperture (Section 2.2.2).
 
@@ -193,10 +283,14 @@ def price_apertures(mlc, pi, occupied, leaves):
     """
     pi = np.asarray(pi)
     best_k, best_leaves, best_price = -1, None, -np.inf
+    interdig = bool(getattr(mlc, "interdigitation", False))
     for k in range(mlc.K):
         if occupied[k]:
             continue
-        price, lv = price_cp(mlc, pi, occupied, leaves, k)
+        if interdig:
+            price, lv = price_cp_interdig(mlc, pi, occupied, leaves, k)
+        else:
+            price, lv = price_cp(mlc, pi, occupied, leaves, k)
         if price is None:
             continue
         if best_k < 0 or price > best_price:

@@ -137,6 +137,7 @@ class MLC:
     n_cols: int
     arc_first_cp: np.ndarray  # int32 [n_arcs]; arc a spans [first[a], first[a+1] or K)
     travel_cols: int = 3
+    interdigitation: bool = False  # adjacent rows: L_r <= R_{r-1} and L_r <= R_{r+1}
 
     @property
     def n_arcs(self) -> int:

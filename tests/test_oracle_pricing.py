@@ -141,3 +141,103 @@ def test_best_cp_ties_pick_smallest_index():
     k, lv, price = oracle.price_apertures(mlc, pi, occupied, leaves)
     # CP 1 (distance 1, travel 1): L in [0, 1], R in [1, 3] -> [1, 2) = 2; CP 2: [0, 1) = 2
     assert (k, price) == (1, 2.0) and list(lv[0]) == [1, 2]
+
+
+# ---------------------------------------------------------------------------- interdigitation (reading R10)
+
+def _interdig_ok(lv):
+    """L_r <= min(R_{r-1}, R_{r+1}) for every row."""
+    for r in range(len(lv)):
+        for q in (r - 1, r + 1):
+            if 0 <= q < len(lv) and lv[r][0] > lv[q][1]:
+                return False
+    return True
+
+
+def _brute_interdig(mlc, pi, occupied, leaves, k):
+    """Every combination of feasible row openings obeying the constraint; the
+    largest sequential float64 sum of the row values."""
+    Lmin, Lmax, Rmin, Rmax = oracle.leaf_windows(mlc, occupied, leaves, k)
+    N = mlc.n_cols
+    states, vals = [], []
+    for r in range(mlc.n_rows):
+        row = pi[(k * mlc.n_rows + r) * N:(k * mlc.n_rows + r + 1) * N]
+        P = [0.0]
+        for p in row:
+            P.append(P[-1] + float(p))
+        st = [(L, R) for L in range(N + 1) for R in range(L, N + 1)
+              if Lmin[r] <= L <= Lmax[r] and Rmin[r] <= R <= Rmax[r]]
+        states.append(st)
+        vals.append({s: P[s[1]] - P[s[0]] for s in st})
+    best = None
+    for combo in itertools.product(*states):
+        if not _interdig_ok(combo):
+            continue
+        tot = 0.0
+        for r, s in enumerate(combo):
+            tot = tot + vals[r][s]
+        if best is None or tot > best:
+            best = tot
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_interdig_dp_matches_exhaustive_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    mlc = synth.MLC(4, 3, 4, np.array([0], np.int32), 1, interdigitation=True)
+    # small integers make exact ties common; some rows strongly negative
+    pi = rng.integers(-3, 4, size=mlc.K * mlc.n_rows * mlc.n_cols).astype(np.float32)
+    if seed % 2:
+        pi = (pi * rng.uniform(0.1, 1.0, size=pi.shape)).astype(np.float32)
+    occupied = np.zeros(mlc.K, bool)
+    leaves = np.zeros((mlc.K, mlc.n_rows, 2), np.int64)
+    if seed >= 3:  # a neighbour CP with interdigitated leaves narrows the windows
+        occupied[1] = True
+        leaves[1] = [[1, 3], [0, 2], [2, 4]]
+    for k in range(mlc.K):
+        if occupied[k]:
+            continue
+        ref = _brute_interdig(mlc, pi, occupied, leaves, k)
+        price, lv = oracle.price_cp_interdig(mlc, pi, occupied, leaves, k)
+        if ref is None:
+            assert price is None
+            continue
+        assert price == ref
+        assert _interdig_ok(lv)
+        Lmin, Lmax, Rmin, Rmax = oracle.leaf_windows(mlc, occupied, leaves, k)
+        tot = 0.0
+        for r in range(mlc.n_rows):
+            assert Lmin[r] <= lv[r][0] <= Lmax[r] and Rmin[r] <= lv[r][1] <= Rmax[r] and lv[r][0] <= lv[r][1]
+            P = oracle.prefix_sums(pi[(k * mlc.n_rows + r) * 4:(k * mlc.n_rows + r + 1) * 4])
+            tot = tot + (P[lv[r][1]] - P[lv[r][0]])
+        assert tot == price
+
+
+def test_interdig_equals_independent_rows_when_unconstrained():
+    # openings that already interlock (every row open over the same columns): the
+    # constraint is inactive and the chain price is the row-by-row price
+    mlc_free = synth.MLC(3, 4, 6, np.array([0], np.int32), 3)
+    mlc_id = synth.MLC(3, 4, 6, np.array([0], np.int32), 3, interdigitation=True)
+    pi = np.full(3 * 4 * 6, -1.0, np.float32)
+    pi.reshape(3, 4, 6)[:, :, 2:4] = 2.0
+    occupied = np.zeros(3, bool)
+    leaves = np.zeros((3, 4, 2), np.int64)
+    for k in range(3):
+        p_free, lv_free = oracle.price_cp(mlc_free, pi, occupied, leaves, k)
+        p_id, lv_id = oracle.price_cp_interdig(mlc_id, pi, occupied, leaves, k)
+        assert p_id == p_free == 16.0
+        assert np.array_equal(lv_id, lv_free)
+
+
+def test_interdig_constraint_binds():
+    # row 0 wants [0, 1), row 1 wants [5, 6): they do not interlock, so the chain
+    # gives up value; the row-by-row optimum is infeasible under the constraint
+    mlc_id = synth.MLC(1, 2, 6, np.array([0], np.int32), 3, interdigitation=True)
+    mlc_free = synth.MLC(1, 2, 6, np.array([0], np.int32), 3)
+    pi = np.float32([5, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 5])
+    occupied = np.zeros(1, bool)
+    leaves = np.zeros((1, 2, 2), np.int64)
+    p_free, lv_free = oracle.price_cp(mlc_free, pi, occupied, leaves, 0)
+    assert p_free == 10.0 and not _interdig_ok(lv_free)
+    p_id, lv_id = oracle.price_cp_interdig(mlc_id, pi, occupied, leaves, 0)
+    assert _interdig_ok(lv_id) and p_id == _brute_interdig(mlc_id, pi, occupied, leaves, 0) and p_id < 10.0
