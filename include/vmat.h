@@ -48,12 +48,16 @@ typedef struct vmat_ddc_s *vmat_ddc;
 /* MLC geometry.  arc_first_cp is HOST memory: n_arcs ascending CP indices,
  * arc_first_cp[0] == 0; arc a spans [arc_first_cp[a], arc_first_cp[a+1]) (the
  * last arc ends at K).  travel_cols: columns a leaf may travel per CP step
- * (the neighbour-compatibility reading of Eq. 2). */
+ * (the neighbour-compatibility reading of Eq. 2).  interdigitation != 0: the
+ * left leaf of a row may not pass the right leaf of an adjacent row,
+ * L_r <= min(R_{r-1}, R_{r+1}) (Section 2.2.2, second pricing variant;
+ * n_cols <= 88; not in batches). */
 typedef struct {
     int32_t K, n_rows, n_cols;
     int32_t n_arcs;
     const int32_t *arc_first_cp;
     int32_t travel_cols;
+    int32_t interdigitation;
 } vmat_mlc;
 
 /* Voxel penalty parameters of Eq. 1: per-voxel structure label (device uint8

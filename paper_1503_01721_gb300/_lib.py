@@ -20,7 +20,7 @@ STOP_NAMES = {1: "rel", 2: "step", 3: "maxit", 4: "grad0", 5: "flat", 10: "price
 
 class Mlc(ctypes.Structure):
     _fields_ = [("K", c_i32), ("n_rows", c_i32), ("n_cols", c_i32), ("n_arcs", c_i32),
-                ("arc_first_cp", ctypes.POINTER(c_i32)), ("travel_cols", c_i32)]
+                ("arc_first_cp", ctypes.POINTER(c_i32)), ("travel_cols", c_i32), ("interdigitation", c_i32)]
 
 
 class Voxels(ctypes.Structure):

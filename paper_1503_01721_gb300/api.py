@@ -72,7 +72,8 @@ class _MlcC:
         arcs = np.ascontiguousarray(np.asarray(mlc.arc_first_cp, np.int32))
         self._arcs = (ctypes.c_int32 * len(arcs))(*arcs.tolist())
         self.s = _lib.Mlc(int(mlc.K), int(mlc.n_rows), int(mlc.n_cols), len(arcs),
-                          ctypes.cast(self._arcs, ctypes.POINTER(ctypes.c_int32)), int(mlc.travel_cols))
+                          ctypes.cast(self._arcs, ctypes.POINTER(ctypes.c_int32)), int(mlc.travel_cols),
+                          int(bool(getattr(mlc, "interdigitation", False))))
 
 
 def _bb_opts(opts):

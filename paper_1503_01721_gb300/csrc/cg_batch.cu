@@ -200,6 +200,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
             return set_error(VMAT_ESTATE, "vmat_batch_create: plan %d needs both CSR(D) and CSR(D^T)", i);
         if ((int64_t)d.mlc->K * d.mlc->n_rows * d.mlc->n_cols != h->J)
             return set_error(VMAT_EINVAL, "vmat_batch_create: plan %d: K*n_rows*n_cols != J", i);
+        if (d.mlc->interdigitation)
+            return set_error(VMAT_EUNSUPPORTED, "vmat_batch_create: plan %d: interdigitation is not batched", i);
         if (d.n_apertures < 0 || d.n_apertures > std::min(d.mlc->K, 96))
             return set_error(VMAT_EINVAL, "vmat_batch_create: plan %d: n_apertures must be in [0, min(K, 96)]", i);
         if (i == 0) b.dt = h->dtype;

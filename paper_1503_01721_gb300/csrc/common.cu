@@ -194,6 +194,8 @@ vmat_status validate_mlc(const vmat_mlc *mlc) {
                          mlc->K, mlc->n_rows, mlc->n_cols, mlc->travel_cols);
     if ((int64_t)mlc->K * mlc->n_rows * mlc->n_cols > INT32_MAX)
         return set_error(VMAT_EINVAL, "mlc has more than 2^31-1 beamlets");
+    if (mlc->interdigitation && mlc->n_cols > INTERDIG_MAX_COLS)
+        return set_error(VMAT_EUNSUPPORTED, "mlc: interdigitation needs n_cols <= %d", INTERDIG_MAX_COLS);
     if (mlc->n_arcs <= 0 || !mlc->arc_first_cp || mlc->arc_first_cp[0] != 0)
         return set_error(VMAT_EINVAL, "mlc arcs invalid: need n_arcs >= 1 and arc_first_cp[0] == 0");
     for (int a = 1; a < mlc->n_arcs; ++a)

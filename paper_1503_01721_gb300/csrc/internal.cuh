@@ -159,8 +159,10 @@ bool spmv_batched_config(int cfg);
 constexpr int MAX_ARCS = 64;
 struct PricingGeom {
     int32_t K, n_rows, n_cols, travel, n_arcs;
+    int32_t interdig; // adjacent rows: L_r <= R_{r-1} and L_r <= R_{r+1}
     int32_t arc_first[MAX_ARCS + 1];
 };
+constexpr int INTERDIG_MAX_COLS = 88; // the chain DP holds (n_cols + 1)^2 states of a row in shared memory
 vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g);
 size_t pricing_scratch_bytes(const vmat_mlc *mlc);
 

@@ -280,12 +280,229 @@ __global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const Pri
     price_cps_block(P.g, P.occupied, P.rb_v, P.rb_lr, P.rb_ok, P.best_cp, P.best_leaves, P.best_price);
 }
 
+// ---------------------------------------------------------------------------
+// Interdigitation (Section 2.2.2, second variant): L_r <= min(R_{r-1}, R_{r+1}).
+// The best aperture of a CP is a chain over the rows: S_r(L, R) = S_{r-1}(pred) +
+// (P_R - P_L) in float64 (S_0 = P_R - P_L), where pred is the compatible state of
+// row r - 1 (L <= R' and L' <= R) with the largest S_{r-1}, ties by the row key
+// (width asc, |L + R - n_cols| asc, L asc).  The dominance maximum over
+// {L <= a, R >= b} is formed by a suffix pass over R (a thread per L) and a prefix
+// pass over L (a thread per b).  One block per CP; every compare is an integer
+// compare of order keys, every value the float64 of the sequential definition.
+// ---------------------------------------------------------------------------
+constexpr int ID_THREADS = 256;
+
+__device__ __forceinline__ bool state_better(uint64_t ka, int La, int Ra, uint64_t kb, int Lb, int Rb, int N) {
+    if (ka != kb) return ka > kb;
+    const int wa = Ra - La, wb = Rb - Lb;
+    if (wa != wb) return wa < wb;
+    const int ca = abs(La + Ra - N), cb = abs(Lb + Rb - N);
+    if (ca != cb) return ca < cb;
+    return La < Lb;
+}
+
+__host__ __device__ constexpr size_t interdig_smem(int N) {
+    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4) + (size_t)(N + 1) * 8 + 64;
+}
+
+// One CP's chain: its best price (cp_val/cp_ok) or, with pred_tab, also the leaves.
+__device__ void interdig_chain(const PricingGeom &g, const float *__restrict__ pi,
+                               const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves, int k,
+                               unsigned char *sm, int32_t *pred_tab, double *out_val, uint8_t *out_ok,
+                               int16_t *out_leaves) {
+    const int N = g.n_cols, NS = (N + 1) * (N + 1);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double *Sp = reinterpret_cast<double *>(sm);
+    double *Sn = Sp + NS;
+    int32_t *CM = reinterpret_cast<int32_t *>(Sn + NS);
+    double *P = reinterpret_cast<double *>(CM + NS + (NS & 1));
+    __shared__ int kk_s[2];
+    __shared__ uint64_t wk[ID_THREADS / 32];
+    __shared__ int ws[ID_THREADS / 32];
+    if (wid == 0) {
+        const int left = nearest_occupied(g, occupied, k, -1, lane);
+        const int right = nearest_occupied(g, occupied, k, 1, lane);
+        if (lane == 0) {
+            kk_s[0] = left;
+            kk_s[1] = right;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < g.n_rows; ++r) {
+        int Lmin = 0, Lmax = N, Rmin = 0, Rmax = N;
+        for (int side = 0; side < 2; ++side) {
+            const int kk = kk_s[side];
+            if (kk >= 0) {
+                const int reach = abs(k - kk) * g.travel;
+                const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
+                Lmin = max(Lmin, Ln - reach);
+                Lmax = min(Lmax, Ln + reach);
+                Rmin = max(Rmin, Rn - reach);
+                Rmax = min(Rmax, Rn + reach);
+            }
+        }
+        if (tid == 0) {
+            const float *row = pi + ((int64_t)k * g.n_rows + r) * N;
+            double acc = 0.0;
+            P[0] = 0.0;
+            for (int c = 0; c < N; ++c) {
+                acc = acc + (double)row[c];
+                P[c + 1] = acc;
+            }
+        }
+        if (r > 0) {
+            // C[L][b] = best state (L, R), R >= b (suffix over R, a thread per L)
+            for (int L = tid; L <= N; L += ID_THREADS) {
+                int bR = N;
+                uint64_t bk = order_key(Sp[L * (N + 1) + N]);
+                CM[L * (N + 1) + N] = L * (N + 1) + N;
+                for (int b = N - 1; b >= 0; --b) {
+                    const uint64_t kb = order_key(Sp[L * (N + 1) + b]);
+                    if (state_better(kb, L, b, bk, L, bR, N)) {
+                        bk = kb;
+                        bR = b;
+                    }
+                    CM[L * (N + 1) + b] = L * (N + 1) + bR;
+                }
+            }
+            __syncthreads();
+            // M[a][b] = best of C[L][b], L <= a (prefix over L, a thread per b), in place
+            for (int b = tid; b <= N; b += ID_THREADS) {
+                int best = CM[b];
+                uint64_t bk = order_key(Sp[best]);
+                for (int a = 1; a <= N; ++a) {
+                    const int c = CM[a * (N + 1) + b];
+                    const uint64_t kc = order_key(Sp[c]);
+                    if (state_better(kc, c / (N + 1), c % (N + 1), bk, best / (N + 1), best % (N + 1), N)) {
+                        best = c;
+                        bk = kc;
+                    }
+                    CM[a * (N + 1) + b] = best;
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NS; idx += ID_THREADS) {
+            const int L = idx / (N + 1), R = idx % (N + 1);
+            const bool feas = L <= R && L >= Lmin && L <= Lmax && R >= Rmin && R <= Rmax;
+            double sv = -INFINITY;
+            if (feas) {
+                const double v = P[R] - P[L];
+                if (r == 0) {
+                    sv = v;
+                } else {
+                    const int pred = CM[R * (N + 1) + L]; // M[R'][L']
+                    const double ps = Sp[pred];
+                    if (ps > -INFINITY) sv = ps + v;
+                    if (pred_tab) pred_tab[(int64_t)r * NS + idx] = pred;
+                }
+            }
+            Sn[idx] = sv;
+        }
+        __syncthreads();
+        double *t = Sp;
+        Sp = Sn;
+        Sn = t;
+    }
+    // best final state
+    int bi = -1;
+    uint64_t bk = 0;
+    for (int idx = tid; idx < NS; idx += ID_THREADS) {
+        const double sv = Sp[idx];
+        if (!(sv > -INFINITY)) continue;
+        const uint64_t kv = order_key(sv);
+        if (bi < 0 || state_better(kv, idx / (N + 1), idx % (N + 1), bk, bi / (N + 1), bi % (N + 1), N)) {
+            bi = idx;
+            bk = kv;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+        const uint64_t ok = __shfl_down_sync(0xffffffffu, bk, d);
+        if (lane + d < 32 && oi >= 0 &&
+            (bi < 0 || state_better(ok, oi / (N + 1), oi % (N + 1), bk, bi / (N + 1), bi % (N + 1), N))) {
+            bi = oi;
+            bk = ok;
+        }
+    }
+    if (lane == 0) {
+        ws[wid] = bi;
+        wk[wid] = bk;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int b = -1;
+        uint64_t kb = 0;
+        for (int w = 0; w < ID_THREADS / 32; ++w) {
+            const int oi = ws[w];
+            if (oi >= 0 && (b < 0 || state_better(wk[w], oi / (N + 1), oi % (N + 1), kb, b / (N + 1), b % (N + 1), N))) {
+                b = oi;
+                kb = wk[w];
+            }
+        }
+        if (out_val) {
+            out_val[k] = b >= 0 ? Sp[b] : -INFINITY;
+            out_ok[k] = b >= 0 ? 1 : 0;
+        }
+        if (out_leaves && b >= 0) {
+            int cur = b;
+            for (int r = g.n_rows - 1; r >= 0; --r) {
+                out_leaves[2 * r] = (int16_t)(cur / (N + 1));
+                out_leaves[2 * r + 1] = (int16_t)(cur % (N + 1));
+                if (r > 0) cur = pred_tab[(int64_t)r * NS + cur];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ID_THREADS)
+    price_cps_interdig_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
+                              const int16_t *__restrict__ leaves, double *cp_val, uint8_t *cp_ok, const int32_t *skip) {
+    if (skip && *skip) return;
+    const int k = blockIdx.x;
+    if (occupied[k]) {
+        if (threadIdx.x == 0) cp_ok[k] = 0;
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smi[];
+    interdig_chain(g, pi, occupied, leaves, k, smi, nullptr, cp_val, cp_ok, nullptr);
+}
+
+// The best CP (price desc, smallest k on ties) and, re-running its chain with the
+// predecessor table, its leaves.
+__global__ void __launch_bounds__(ID_THREADS)
+    price_pick_interdig_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
+                               const int16_t *__restrict__ leaves, const double *cp_val, const uint8_t *cp_ok,
+                               int32_t *pred_tab, int32_t *best_cp, int16_t *best_leaves, double *best_price,
+                               const int32_t *skip) {
+    if (skip && *skip) return;
+    __shared__ int kwin;
+    if (threadIdx.x == 0) {
+        int kb = -1;
+        double v = -INFINITY;
+        for (int k = 0; k < g.K; ++k) // k ascending: a strict > keeps the smallest k
+            if (!occupied[k] && cp_ok[k] && (kb < 0 || cp_val[k] > v)) {
+                v = cp_val[k];
+                kb = k;
+            }
+        *best_cp = kb;
+        *best_price = kb >= 0 ? v : -INFINITY;
+        kwin = kb;
+    }
+    __syncthreads();
+    if (kwin < 0) return;
+    extern __shared__ __align__(16) unsigned char smi[];
+    interdig_chain(g, pi, occupied, leaves, kwin, smi, pred_tab, nullptr, nullptr, best_leaves);
+}
+
 vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g) {
     if (mlc->n_arcs > MAX_ARCS) return set_error(VMAT_EUNSUPPORTED, "price_apertures: more than %d arcs", MAX_ARCS);
     g->K = mlc->K;
     g->n_rows = mlc->n_rows;
     g->n_cols = mlc->n_cols;
     g->travel = mlc->travel_cols;
+    g->interdig = mlc->interdigitation ? 1 : 0;
     g->n_arcs = mlc->n_arcs;
     for (int a = 0; a < mlc->n_arcs; ++a) g->arc_first[a] = mlc->arc_first_cp[a];
     g->arc_first[mlc->n_arcs] = mlc->K;
@@ -321,6 +538,27 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
     double *rb_v = static_cast<double *>(ws);
     int16_t *rb_lr = reinterpret_cast<int16_t *>(rb_v + rows);
     uint8_t *rb_ok = reinterpret_cast<uint8_t *>(rb_lr + 2 * rows);
+    if (g.interdig) {
+        // scratch: per-CP prices, then the chosen CP's predecessor table
+        double *cp_val = rb_v;
+        uint8_t *cp_ok = reinterpret_cast<uint8_t *>(cp_val + g.K);
+        int32_t *pred_tab = reinterpret_cast<int32_t *>(cp_ok + ((g.K + 15) & ~15));
+        const size_t sm = interdig_smem(g.n_cols);
+        static bool attr_id = false;
+        if (!attr_id) {
+            VMAT_CUDA(cudaFuncSetAttribute(price_cps_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)interdig_smem(INTERDIG_MAX_COLS)));
+            VMAT_CUDA(cudaFuncSetAttribute(price_pick_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)interdig_smem(INTERDIG_MAX_COLS)));
+            attr_id = true;
+        }
+        price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, pi, occupied, leaves, cp_val, cp_ok, skip);
+        VMAT_LAUNCH_CHECK();
+        price_pick_interdig_kernel<<<1, ID_THREADS, sm, s>>>(g, pi, occupied, leaves, cp_val, cp_ok, pred_tab,
+                                                               best_cp, best_leaves, best_price, skip);
+        VMAT_LAUNCH_CHECK();
+        return VMAT_OK;
+    }
     const size_t smem = PR_WARPS * row_smem_stride(g.n_cols);
     static bool attr_set = false;
     if (!attr_set) {
@@ -338,7 +576,12 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
 
 size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
     const size_t rows = (size_t)mlc->K * mlc->n_rows;
-    return rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
+    size_t b = rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
+    if (mlc->interdigitation) {
+        const size_t ns = (size_t)(mlc->n_cols + 1) * (mlc->n_cols + 1);
+        b = std::max(b, (size_t)mlc->K * 9 + 16 + (size_t)mlc->n_rows * ns * 4 + 64);
+    }
+    return b;
 }
 
 // Scratch of price_apertures_noalloc: per-row bests for up to VMAT_NOALLOC_MAX_ROWS
@@ -398,6 +641,9 @@ extern "C" vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float 
     VMAT_TRY(validate_mlc(mlc));
     if (!pi || !occupied || !leaves || !best_cp || !best_leaves || !best_price)
         return set_error(VMAT_EINVAL, "price_apertures_noalloc: NULL argument");
+    if ((int64_t)mlc->K * mlc->n_rows <= VMAT_NOALLOC_MAX_ROWS && pricing_scratch_bytes(mlc) > NOALLOC_BYTES)
+        return set_error(VMAT_EINVAL, "price_apertures_noalloc: this MLC needs %zu bytes of scratch, over the fixed "
+                         "scratch limit of %zu bytes; use price_apertures", pricing_scratch_bytes(mlc), NOALLOC_BYTES);
     if ((int64_t)mlc->K * mlc->n_rows > VMAT_NOALLOC_MAX_ROWS)
         return set_error(VMAT_EINVAL,
                          "price_apertures_noalloc: K * n_rows = %lld exceeds the fixed scratch limit of %d "

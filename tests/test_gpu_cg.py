@@ -57,7 +57,8 @@ def near_tie_at(ddc, c, D, t, k_gpu, opts=None):
     _, g = oracle.objective_grad(z, s.struct_id, s.T, s.w_over, s.w_under)
     pi = oracle.beamlet_price(D, g)
     _, _, p_ref = oracle.price_apertures(c.mlc, pi, occupied, leaves_all)
-    p_gpu, _ = oracle.price_cp(c.mlc, pi, occupied, leaves_all, int(k_gpu))
+    price_cp = oracle.price_cp_interdig if getattr(c.mlc, "interdigitation", False) else oracle.price_cp
+    p_gpu, _ = price_cp(c.mlc, pi, occupied, leaves_all, int(k_gpu))
     return p_gpu is not None and p_ref - p_gpu <= 1e-4 * abs(p_ref)
 
 
@@ -84,6 +85,30 @@ def test_plan_matches_oracle(name, n, tight):
     else:
         t = next(i for i, (a, b) in enumerate(zip(list(cps), ref.cps)) if a != b)
         assert near_tie_at(ddc, c, D, t, cps[t], opts), \
+            f"aperture sequence differs at step {t}: gpu {list(cps)} oracle {ref.cps}"
+
+
+@pytest.mark.parametrize("name,n", [("tiny", 3), ("ragged", 4), ("cfg1", 12)])
+def test_plan_interdigitation_matches_oracle(name, n):
+    """The CG loop with the interdigitation constraint on every aperture."""
+    import dataclasses
+    c = synth.make_case(name, seed=0)
+    c = dataclasses.replace(c, mlc=dataclasses.replace(c.mlc, interdigitation=True))
+    ddc = make_ddc(c)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    s = c.structs
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, n, TIGHT)
+    for a in lv:
+        assert all(a[r][0] <= min(a[q][1] for q in (r - 1, r + 1) if 0 <= q < len(a)) for r in range(len(a)))
+    x = oracle.aperture_fluence(c.mlc, cps, lv, y)
+    d_ref = oracle.dose_forward(D, x)
+    assert np.max(np.abs(dose - d_ref)) <= 1e-5 * max(np.max(np.abs(d_ref)), 1e-30)
+    ref = oracle.cg_plan(D, c.mlc, s, n, oracle.BBOptions(**TIGHT))
+    if list(cps) == ref.cps:
+        assert abs(F - ref.F) <= 1e-4 * ref.F
+    else:
+        t = next(i for i, (a, b) in enumerate(zip(list(cps), ref.cps)) if a != b)
+        assert near_tie_at(ddc, c, D, t, cps[t], TIGHT), \
             f"aperture sequence differs at step {t}: gpu {list(cps)} oracle {ref.cps}"
 
 

@@ -84,6 +84,31 @@ def test_price_apertures_bit_exact(geom, seed, ints):
             assert np.array_equal(lv, np.asarray(lv_ref))
 
 
+@pytest.mark.parametrize("geom,seed,ints", [((5, 3, 4, 1, (0,)), 10, True), ((12, 4, 9, 2, (0, 6)), 11, True),
+                                            ((36, 20, 20, 3, (0,)), 12, False), ((36, 20, 20, 3, (0,)), 13, True),
+                                            ((40, 8, 80, 2, (0, 20)), 14, False)])
+def test_price_apertures_interdigitation_bit_exact(geom, seed, ints):
+    """Interdigitation (Section 2.2.2): the GPU chain DP and the oracle's give the
+    same CP, the same float64 price and the same leaves."""
+    K, nr, nc, travel, arcs = geom
+    mlc = synth.MLC(K, nr, nc, np.array(arcs, np.int32), travel, interdigitation=True)
+    rng = np.random.default_rng(seed)
+    for frac in (0.0, 0.3, 0.8):
+        if ints:
+            pi = rng.integers(-3, 4, K * nr * nc).astype(np.float32)
+        else:
+            pi = (rng.normal(size=K * nr * nc) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
+            pi[rng.random(pi.size) < 0.2] = 0.0
+        occupied, leaves = random_state(mlc, rng, frac)
+        k, lv, price = gpu_price(mlc, pi, occupied, leaves)
+        k_ref, lv_ref, price_ref = oracle.price_apertures(mlc, pi, occupied, leaves)
+        assert k == k_ref
+        if k_ref >= 0:
+            assert price == price_ref
+            assert np.array_equal(lv, np.asarray(lv_ref))
+            assert all(lv[r][0] <= min(lv[q][1] for q in (r - 1, r + 1) if 0 <= q < nr) for r in range(nr))
+
+
 def test_price_all_occupied():
     mlc = synth.MLC(4, 2, 3, np.array([0], np.int32), 1)
     occupied = np.ones(4, np.uint8)
