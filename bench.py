@@ -234,6 +234,9 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     t0 = time.time()
     case = synth.make_case(args.workload, seed=rank, cache=False)
+    if args.interdig:
+        import dataclasses
+        case = dataclasses.replace(case, mlc=dataclasses.replace(case.mlc, interdigitation=True))
     log(f"[rank {rank}] generated {case.nnz} nonzeros in {time.time() - t0:.1f}s")
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
     vox_h, blt_h, val_h = pin(case.vox, torch.int32), pin(case.blt, torch.int32), pin(case.val, torch.float32)
@@ -358,6 +361,7 @@ def run_ours(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else args.dtype, "data": "synthetic",
             "config": {"workload": f"{args.workload} {DESCS[args.workload]}", "V": case.V, "J": case.J, "nnz": case.nnz,
                        "n_active_vox": info["n_active_vox"], "n_apertures": n_ap, "storage": args.dtype,
+                       "interdigitation": bool(args.interdig),
                        "l2": "inputs larger than L2 (CSR D + D^T %.1f GB)" % ((info["bytes_D"] + info["bytes_Dt"]) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
@@ -532,6 +536,73 @@ def run_batch(args):
     return out
 
 
+def run_truncation(args):
+    """The paper's method S1 (Section 2.4): plan on a DDC truncated to a radius about
+    each beamlet axis (1.25 voxels keeps about a quarter of the entries, as the
+    paper's 2.5 cm against 6 cm did), then evaluate that plan's dose on the full
+    DDC, beside the plan optimised on the full DDC."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1503_01721_gb300 import api
+    import __graft_entry__
+
+    __graft_entry__.build()
+    radius = 1.25
+    full = synth.make_case(args.workload, seed=0, cache=False)
+    tr = synth.make_truncated_case(args.workload, radius, seed=0)
+    n = full.n_apertures
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+    ddcs = {}
+    for tag, c in (("full", full), ("trunc", tr)):
+        ddcs[tag] = api.Ddc(c.V, c.J, dev(c.vox, torch.int32), dev(c.blt, torch.int32), dev(c.val, torch.float32),
+                            dtype=args.dtype, autotune=True)
+    vox = api.VoxelParams.from_numpy(full.structs)
+    out = {"mode": "truncation", "workload": args.workload, "radius_vox": radius, "dtype": args.dtype,
+           "nnz_full": full.nnz, "nnz_trunc": tr.nnz, "nnz_ratio": round(tr.nnz / full.nnz, 4)}
+    res = {}
+    for tag, c in (("full", full), ("trunc", tr)):
+        cps = torch.empty(n, dtype=torch.int32)
+        lv = torch.empty(n * c.mlc.n_rows * 2, dtype=torch.int16)
+        y = torch.empty(n, dtype=torch.float32)
+        dose = torch.empty(c.V, device="cuda")
+        for _ in range(max(args.warmup, 1)):
+            api.cg_plan(ddcs[tag].h, c.mlc, vox, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            F, st = api.cg_plan(ddcs[tag].h, c.mlc, vox, n, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        res[tag] = (F, st, cps.clone(), lv.clone(), y.clone(), dose.clone(), ms)
+    # the truncated plan's dose on the full matrix
+    _, st_t, cps, lv, y, dose_model, _ = res["trunc"]
+    m = st_t["n_apertures"]
+    x = torch.empty(full.J, device="cuda")
+    api.aperture_fluence(full.mlc, cps[:m].cuda(), lv[:m * full.mlc.n_rows * 2].cuda(), y[:m].cuda(), x)
+    dose_true = torch.empty(full.V, device="cuda")
+    api.dose_forward(ddcs["full"].h, x, dose_true)
+    F_true = torch.empty(1, dtype=torch.float64, device="cuda")
+    api.objective_grad(dose_true, vox, None, F_true)
+    s = full.structs
+    targets = [k for k in range(len(s.T)) if s.w_under[k] > 0]
+    ptv = np.isin(s.struct_id, targets)
+    T = s.T[s.struct_id]
+    dm, dt, df = dose_model.cpu().numpy(), dose_true.cpu().numpy(), res["full"][5].cpu().numpy()
+    out.update({
+        "full_plan": {"F": res["full"][0], "ms": round(res["full"][6], 2), "bb_iters": res["full"][1]["bb_iters_total"],
+                      "ptv_frac_over_110pct": round(float(np.mean(df[ptv] > 1.1 * T[ptv])), 4)},
+        "trunc_plan": {"F_on_truncated": res["trunc"][0], "F_on_full": F_true.item(), "ms": round(res["trunc"][6], 2),
+                       "bb_iters": st_t["bb_iters_total"],
+                       "ptv_mean_dose_increase": round(float(np.mean((dt[ptv] - dm[ptv]) / T[ptv])), 4),
+                       "ptv_frac_over_110pct": round(float(np.mean(dt[ptv] > 1.1 * T[ptv])), 4)},
+        "speedup_trunc_over_full": round(res["full"][6] / res["trunc"][6], 3),
+    })
+    for d in ddcs.values():
+        d.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -557,12 +628,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS) + ["cfg5", "cfg5q", "batch_small"])
-    ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp", "batch"],
+    ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp", "batch", "truncation"],
                     help="spmv: only build and run D^T g and D x a few times (profiling driver); "
                          "mp: fixed-length master-problem solves; batch: a batch workload (cfg5, cfg5q, "
-                         "batch_small) batched against one by one")
+                         "batch_small) batched against one by one; truncation: the paper's truncated-matrix "
+                         "plan evaluated on the full matrix")
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
+    ap.add_argument("--interdig", action="store_true", help="plan mode: price with the interdigitation constraint")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.mode == "plan":
         log("note: fewer than 3 warm-up steps")
@@ -573,6 +646,8 @@ def main():
         out = run_mp_only(args) if rank == 0 else None
     elif args.mode == "batch":
         out = run_batch(args) if rank == 0 else None
+    elif args.mode == "truncation":
+        out = run_truncation(args) if rank == 0 else None
     else:
         out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

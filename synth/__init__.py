@@ -56,6 +56,7 @@ class _Geom(ctypes.Structure):
         ("mu_per_vox", ctypes.c_double),
         ("sigma_vox", ctypes.c_double),
         ("cutoff", ctypes.c_double),
+        ("trunc_vox", ctypes.c_double),
     ]
 
 
@@ -110,6 +111,7 @@ class Geometry:
     mu_per_vox: float = 0.05
     sigma_vox: float = 1.0
     cutoff: float = 0.01
+    trunc_vox: float = 0.0  # > 0: truncation radius about each beamlet axis (the paper's S1 matrix)
 
     @property
     def V(self) -> int:
@@ -126,7 +128,7 @@ class Geometry:
     def _c(self) -> _Geom:
         return _Geom(self.nx, self.ny, self.nz, self.h_mm, self.n_cp, self.n_arcs,
                      self.arc_offset_deg, self.n_rows, self.n_cols, self.pitch_vox,
-                     self.mu_per_vox, self.sigma_vox, self.cutoff)
+                     self.mu_per_vox, self.sigma_vox, self.cutoff, self.trunc_vox)
 
 
 @dataclasses.dataclass
@@ -230,6 +232,15 @@ def batch_specs(name: str) -> list:
                 PlanSpec("bs_2", Geometry(24, 20, 16, 5.0, 12, 8, 10), 6, "prostate", 2),
                 PlanSpec("bs_3", GEOMETRIES["cfg1"], 12, "cfg1", 3)]
     raise KeyError(name)
+
+
+def make_truncated_case(name: str, trunc_vox: float, seed: int = 0) -> "Case":
+    """The named workload with its DDC truncated to trunc_vox voxels about each
+    beamlet axis (same geometry, structures and MLC)."""
+    geom = dataclasses.replace(GEOMETRIES[name], trunc_vox=float(trunc_vox))
+    vox, blt, val = generate_coo(geom)
+    return Case(f"{name}_trunc{trunc_vox:g}", geom, make_mlc(geom), vox, blt, val,
+                make_structures(name, geom, seed), APERTURES[name])
 
 
 def make_plan_case(spec: PlanSpec) -> "Case":

@@ -23,7 +23,10 @@
  * t_entry being where the beamlet axis enters the grid box.  Entries with
  * q > ln(1/cutoff) (value below cutoff times the beamlet's unit peak) and
  * voxels upstream of the entry point are dropped.  The keep test is done on q,
- * so no libm call decides which entries exist.
+ * so no libm call decides which entries exist.  With trunc_vox > 0 the entries
+ * farther than trunc_vox from the beamlet axis are dropped too (the paper's
+ * truncated matrix of its method S1: a cone of radius gamma about each
+ * beamlet's axis, a cylinder for these parallel beamlets).
  *
  * Output is COO, beamlet-major, voxel index ascending within each beamlet.
  * Every beamlet is generated independently, so the result does not depend on
@@ -44,6 +47,7 @@ typedef struct {
     double mu_per_vox;
     double sigma_vox;
     double cutoff;
+    double trunc_vox; /* > 0: also drop entries farther than this from the beamlet axis */
 } synth_geom;
 
 typedef struct {
@@ -132,6 +136,7 @@ static int64_t beamlet_entries(const synth_geom *g, int64_t j, int32_t *vox, flo
                 if (t < ax.t_entry) continue;
                 double l0 = w0 - t * ax.b[0], l1 = w1 - t * ax.b[1], l2 = w2 - t * ax.b[2];
                 double rho2 = l0 * l0 + l1 * l1 + l2 * l2;
+                if (g->trunc_vox > 0.0 && rho2 > g->trunc_vox * g->trunc_vox) continue;
                 double q = att * (t - ax.t_entry) + rho2 * inv2s2;
                 if (q > qmax) continue;
                 if (vox) {

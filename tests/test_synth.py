@@ -69,3 +69,21 @@ def test_structures_seeded():
     assert np.array_equal(s1.struct_id, s2.struct_id)
     assert s1.names == ["tissue", "oar0", "oar1", "ptv0"]
     assert (s1.struct_id == 3).sum() > 1500      # sphere r=8: ~2145 voxels
+
+
+def test_truncated_ddc_is_a_subset_of_the_full_one():
+    """The truncated matrix (the paper's S1: entries outside a radius about each
+    beamlet axis dropped) keeps exactly the full matrix's entries near the axis."""
+    g = synth.GEOMETRIES["ragged"]
+    full = synth.generate_coo(g)
+    import dataclasses
+    for radius, expect_all in ((1.25, False), (2.0, False), (3.1, True)):
+        tr = synth.generate_coo(dataclasses.replace(g, trunc_vox=radius))
+        key_full = {(int(v), int(b)): float(x) for v, b, x in zip(*full)}
+        assert all(key_full[(int(v), int(b))] == float(x) for v, b, x in zip(*tr))
+        assert (len(tr[2]) == len(full[2])) == expect_all
+        # dropped entries are off-axis: their values are at most exp(-radius^2 / 2) of the peak
+        kept = {(int(v), int(b)) for v, b in zip(tr[0], tr[1])}
+        dropped = [x for (v, b), x in key_full.items() if (v, b) not in kept]
+        if dropped:
+            assert max(dropped) <= np.exp(-radius ** 2 / 2) * (1 + 1e-6)
