@@ -290,35 +290,124 @@ __global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const Pri
 // pass over L (a thread per b).  One block per CP; every compare is an integer
 // compare of order keys, every value the float64 of the sequential definition.
 // ---------------------------------------------------------------------------
-constexpr int ID_THREADS = 256;
+constexpr int ID_THREADS = 512;
 
-__device__ __forceinline__ bool state_better(uint64_t ka, int La, int Ra, uint64_t kb, int Lb, int Rb, int N) {
-    if (ka != kb) return ka > kb;
-    const int wa = Ra - La, wb = Rb - Lb;
-    if (wa != wb) return wa < wb;
-    const int ca = abs(La + Ra - N), cb = abs(Lb + Rb - N);
-    if (ca != cb) return ca < cb;
-    return La < Lb;
+// A state's tie key (width, |L + R - n_cols|, L, each below 1024) in one word:
+// smaller is better among equal values.
+__device__ __forceinline__ uint32_t state_sec(int L, int R, int N) {
+    return ((uint32_t)(R - L) << 20) | ((uint32_t)abs(L + R - N) << 10) | (uint32_t)L;
+}
+// a strictly better than b: larger value key, then smaller tie key.
+__device__ __forceinline__ bool key_better(uint64_t ka, uint32_t sa, uint64_t kb, uint32_t sb) {
+    return ka > kb || (ka == kb && sa < sb);
 }
 
 __host__ __device__ constexpr size_t interdig_smem(int N) {
-    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4) + (size_t)(N + 1) * 8 + 64;
+    // S_{r-1}, S_r (double), CM (int32), tie keys (uint32), (L, R) of each state (uint16)
+    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4 + 4 + 2) + 64;
 }
 
-// One CP's chain: its best price (cp_val/cp_ok) or, with pred_tab, also the leaves.
-__device__ void interdig_chain(const PricingGeom &g, const float *__restrict__ pi,
+// Prefix sums of every MLC row of every unoccupied CP (a thread per row, float64
+// in column order, as the definition), for the chain kernels.
+__global__ void interdig_prefix_kernel(PricingGeom g, const float *__restrict__ pi,
+                                       const uint8_t *__restrict__ occupied, double *__restrict__ Pall,
+                                       const int32_t *skip) {
+    if (skip && *skip) return;
+    const int N = g.n_cols;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < (int64_t)g.K * g.n_rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        if (occupied[row / g.n_rows]) continue;
+        const float *src = pi + row * N;
+        double *P = Pall + row * (N + 1);
+        double acc = 0.0;
+        P[0] = 0.0;
+        for (int c = 0; c < N; ++c) {
+            acc = acc + (double)src[c];
+            P[c + 1] = acc;
+        }
+    }
+}
+
+// Inclusive "best so far" scans of n_lines lines of n = N + 1 states each, four
+// threads per line: each scans a segment of about n/4 consecutive states in scan
+// order, the segments' bests pass along the line by two shuffles, and each thread
+// rescans its segment from that carry, writing the best state so far to CM.
+// SUFFIX: line L is (L, R) for R = N .. 0 (state index = position); otherwise line
+// b is CM[a][b] for a = 0 .. N (the state index stored there), rewritten in place.
+template <bool SUFFIX>
+__device__ __forceinline__ void seg_best_scans(const double *Sp, const uint32_t *sec, int32_t *CM, int N) {
+    const int n = N + 1, seglen = (n + 3) >> 2, lane = threadIdx.x & 31;
+    for (int base = 0; base < n * 4; base += ID_THREADS) { // warp-uniform trip count
+        const int t = base + (int)threadIdx.x;
+        const bool act = t < n * 4;
+        const int line = t >> 2, sg = t & 3;
+        const int e0 = sg * seglen, e1 = act ? min(e0 + seglen, n) : e0;
+        auto pos_of = [&](int e) { return SUFFIX ? line * n + (N - e) : e * n + line; };
+        int bi = -1;
+        uint64_t bk = 0;
+        uint32_t bs = 0xffffffffu;
+        for (int e = e0; e < e1; ++e) {
+            const int pos = pos_of(e);
+            const int id = SUFFIX ? pos : CM[pos];
+            const uint64_t kk = order_key(Sp[id]);
+            const uint32_t ss = sec[id];
+            if (bi < 0 || key_better(kk, ss, bk, bs)) {
+                bi = id;
+                bk = kk;
+                bs = ss;
+            }
+        }
+        // carry: the best of the line's earlier segments (lanes sg - 1, sg - 2, sg - 3 of this group)
+        int ci = -1;
+        uint64_t ck = 0;
+        uint32_t cs = 0xffffffffu;
+#pragma unroll
+        for (int d = 1; d <= 3; ++d) {
+            const int oi = __shfl_up_sync(0xffffffffu, bi, d);
+            const uint64_t ok = __shfl_up_sync(0xffffffffu, bk, d);
+            const uint32_t os = __shfl_up_sync(0xffffffffu, bs, d);
+            if (sg >= d && lane >= d && oi >= 0 && (ci < 0 || key_better(ok, os, ck, cs))) {
+                ci = oi;
+                ck = ok;
+                cs = os;
+            }
+        }
+        for (int e = e0; e < e1; ++e) {
+            const int pos = pos_of(e);
+            const int id = SUFFIX ? pos : CM[pos];
+            const uint64_t kk = order_key(Sp[id]);
+            const uint32_t ss = sec[id];
+            if (ci < 0 || key_better(kk, ss, ck, cs)) {
+                ci = id;
+                ck = kk;
+                cs = ss;
+            }
+            CM[pos] = ci;
+        }
+    }
+}
+
+// One CP's chain: its best price (cp_val/cp_ok) and its predecessor table (the
+// feasible states' predecessors per row, then the best final state) for the backtrack.
+__device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ Pall,
                                const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves, int k,
-                               unsigned char *sm, int32_t *pred_tab, double *out_val, uint8_t *out_ok,
-                               int16_t *out_leaves) {
+                               unsigned char *sm, int16_t *pred_tab, double *out_val, uint8_t *out_ok) {
     const int N = g.n_cols, NS = (N + 1) * (N + 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double *Sp = reinterpret_cast<double *>(sm);
     double *Sn = Sp + NS;
     int32_t *CM = reinterpret_cast<int32_t *>(Sn + NS);
-    double *P = reinterpret_cast<double *>(CM + NS + (NS & 1));
+    uint32_t *sec = reinterpret_cast<uint32_t *>(CM + NS);
+    uint16_t *lr = reinterpret_cast<uint16_t *>(sec + NS);
     __shared__ int kk_s[2];
     __shared__ uint64_t wk[ID_THREADS / 32];
+    __shared__ uint32_t wsec[ID_THREADS / 32];
     __shared__ int ws[ID_THREADS / 32];
+    for (int idx = tid; idx < NS; idx += ID_THREADS) {
+        const int L = idx / (N + 1), R = idx - L * (N + 1);
+        sec[idx] = state_sec(L, R, N);
+        lr[idx] = (uint16_t)((L << 8) | R);
+    }
     if (wid == 0) {
         const int left = nearest_occupied(g, occupied, k, -1, lane);
         const int right = nearest_occupied(g, occupied, k, 1, lane);
@@ -341,49 +430,17 @@ __device__ void interdig_chain(const PricingGeom &g, const float *__restrict__ p
                 Rmax = min(Rmax, Rn + reach);
             }
         }
-        if (tid == 0) {
-            const float *row = pi + ((int64_t)k * g.n_rows + r) * N;
-            double acc = 0.0;
-            P[0] = 0.0;
-            for (int c = 0; c < N; ++c) {
-                acc = acc + (double)row[c];
-                P[c + 1] = acc;
-            }
-        }
+        const double *P = Pall + ((int64_t)k * g.n_rows + r) * (N + 1);
         if (r > 0) {
-            // C[L][b] = best state (L, R), R >= b (suffix over R, a thread per L)
-            for (int L = tid; L <= N; L += ID_THREADS) {
-                int bR = N;
-                uint64_t bk = order_key(Sp[L * (N + 1) + N]);
-                CM[L * (N + 1) + N] = L * (N + 1) + N;
-                for (int b = N - 1; b >= 0; --b) {
-                    const uint64_t kb = order_key(Sp[L * (N + 1) + b]);
-                    if (state_better(kb, L, b, bk, L, bR, N)) {
-                        bk = kb;
-                        bR = b;
-                    }
-                    CM[L * (N + 1) + b] = L * (N + 1) + bR;
-                }
-            }
+            // C[L][b] = best state (L, R), R >= b (suffix over R), then in place
+            // M[a][b] = best of C[L][b], L <= a (prefix over L)
+            seg_best_scans<true>(Sp, sec, CM, N);
             __syncthreads();
-            // M[a][b] = best of C[L][b], L <= a (prefix over L, a thread per b), in place
-            for (int b = tid; b <= N; b += ID_THREADS) {
-                int best = CM[b];
-                uint64_t bk = order_key(Sp[best]);
-                for (int a = 1; a <= N; ++a) {
-                    const int c = CM[a * (N + 1) + b];
-                    const uint64_t kc = order_key(Sp[c]);
-                    if (state_better(kc, c / (N + 1), c % (N + 1), bk, best / (N + 1), best % (N + 1), N)) {
-                        best = c;
-                        bk = kc;
-                    }
-                    CM[a * (N + 1) + b] = best;
-                }
-            }
+            seg_best_scans<false>(Sp, sec, CM, N);
         }
         __syncthreads();
         for (int idx = tid; idx < NS; idx += ID_THREADS) {
-            const int L = idx / (N + 1), R = idx % (N + 1);
+            const int L = lr[idx] >> 8, R = lr[idx] & 255;
             const bool feas = L <= R && L >= Lmin && L <= Lmax && R >= Rmin && R <= Rmax;
             double sv = -INFINITY;
             if (feas) {
@@ -394,7 +451,7 @@ __device__ void interdig_chain(const PricingGeom &g, const float *__restrict__ p
                     const int pred = CM[R * (N + 1) + L]; // M[R'][L']
                     const double ps = Sp[pred];
                     if (ps > -INFINITY) sv = ps + v;
-                    if (pred_tab) pred_tab[(int64_t)r * NS + idx] = pred;
+                    pred_tab[(int64_t)r * NS + idx] = (int16_t)pred;
                 }
             }
             Sn[idx] = sv;
@@ -407,58 +464,56 @@ __device__ void interdig_chain(const PricingGeom &g, const float *__restrict__ p
     // best final state
     int bi = -1;
     uint64_t bk = 0;
+    uint32_t bs = 0xffffffffu;
     for (int idx = tid; idx < NS; idx += ID_THREADS) {
         const double sv = Sp[idx];
         if (!(sv > -INFINITY)) continue;
         const uint64_t kv = order_key(sv);
-        if (bi < 0 || state_better(kv, idx / (N + 1), idx % (N + 1), bk, bi / (N + 1), bi % (N + 1), N)) {
+        if (bi < 0 || key_better(kv, sec[idx], bk, bs)) {
             bi = idx;
             bk = kv;
+            bs = sec[idx];
         }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         const int oi = __shfl_down_sync(0xffffffffu, bi, d);
         const uint64_t ok = __shfl_down_sync(0xffffffffu, bk, d);
-        if (lane + d < 32 && oi >= 0 &&
-            (bi < 0 || state_better(ok, oi / (N + 1), oi % (N + 1), bk, bi / (N + 1), bi % (N + 1), N))) {
+        const uint32_t os = __shfl_down_sync(0xffffffffu, bs, d);
+        if (lane + d < 32 && oi >= 0 && (bi < 0 || key_better(ok, os, bk, bs))) {
             bi = oi;
             bk = ok;
+            bs = os;
         }
     }
     if (lane == 0) {
         ws[wid] = bi;
         wk[wid] = bk;
+        wsec[wid] = bs;
     }
     __syncthreads();
     if (tid == 0) {
         int b = -1;
         uint64_t kb = 0;
+        uint32_t sb = 0xffffffffu;
         for (int w = 0; w < ID_THREADS / 32; ++w) {
             const int oi = ws[w];
-            if (oi >= 0 && (b < 0 || state_better(wk[w], oi / (N + 1), oi % (N + 1), kb, b / (N + 1), b % (N + 1), N))) {
+            if (oi >= 0 && (b < 0 || key_better(wk[w], wsec[w], kb, sb))) {
                 b = oi;
                 kb = wk[w];
+                sb = wsec[w];
             }
         }
-        if (out_val) {
-            out_val[k] = b >= 0 ? Sp[b] : -INFINITY;
-            out_ok[k] = b >= 0 ? 1 : 0;
-        }
-        if (out_leaves && b >= 0) {
-            int cur = b;
-            for (int r = g.n_rows - 1; r >= 0; --r) {
-                out_leaves[2 * r] = (int16_t)(cur / (N + 1));
-                out_leaves[2 * r + 1] = (int16_t)(cur % (N + 1));
-                if (r > 0) cur = pred_tab[(int64_t)r * NS + cur];
-            }
-        }
+        out_val[k] = b >= 0 ? Sp[b] : -INFINITY;
+        out_ok[k] = b >= 0 ? 1 : 0;
+        pred_tab[(int64_t)g.n_rows * NS] = (int16_t)max(b, 0); // the final state, for the backtrack
     }
 }
 
 __global__ void __launch_bounds__(ID_THREADS)
-    price_cps_interdig_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
-                              const int16_t *__restrict__ leaves, double *cp_val, uint8_t *cp_ok, const int32_t *skip) {
+    price_cps_interdig_kernel(PricingGeom g, const double *__restrict__ Pall, const uint8_t *__restrict__ occupied,
+                              const int16_t *__restrict__ leaves, double *cp_val, uint8_t *cp_ok, int16_t *pred_all,
+                              const int32_t *skip) {
     if (skip && *skip) return;
     const int k = blockIdx.x;
     if (occupied[k]) {
@@ -466,34 +521,37 @@ __global__ void __launch_bounds__(ID_THREADS)
         return;
     }
     extern __shared__ __align__(16) unsigned char smi[];
-    interdig_chain(g, pi, occupied, leaves, k, smi, nullptr, cp_val, cp_ok, nullptr);
+    const int64_t NS = (int64_t)(g.n_cols + 1) * (g.n_cols + 1);
+    interdig_chain(g, Pall, occupied, leaves, k, smi, pred_all + (int64_t)k * (g.n_rows * NS + 1), cp_val, cp_ok);
 }
 
-// The best CP (price desc, smallest k on ties) and, re-running its chain with the
-// predecessor table, its leaves.
-__global__ void __launch_bounds__(ID_THREADS)
-    price_pick_interdig_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
-                               const int16_t *__restrict__ leaves, const double *cp_val, const uint8_t *cp_ok,
-                               int32_t *pred_tab, int32_t *best_cp, int16_t *best_leaves, double *best_price,
-                               const int32_t *skip) {
+// The best CP (price desc, smallest k on ties) and its leaves, backtracked through
+// the predecessor table its chain stored.
+__global__ void price_pick_interdig_kernel(PricingGeom g, const uint8_t *__restrict__ occupied,
+                                           const double *cp_val, const uint8_t *cp_ok, const int16_t *pred_all,
+                                           int32_t *best_cp, int16_t *best_leaves, double *best_price,
+                                           const int32_t *skip) {
     if (skip && *skip) return;
-    __shared__ int kwin;
-    if (threadIdx.x == 0) {
-        int kb = -1;
-        double v = -INFINITY;
-        for (int k = 0; k < g.K; ++k) // k ascending: a strict > keeps the smallest k
-            if (!occupied[k] && cp_ok[k] && (kb < 0 || cp_val[k] > v)) {
-                v = cp_val[k];
-                kb = k;
-            }
-        *best_cp = kb;
-        *best_price = kb >= 0 ? v : -INFINITY;
-        kwin = kb;
+    if (threadIdx.x != 0) return;
+    int kb = -1;
+    double v = -INFINITY;
+    for (int k = 0; k < g.K; ++k) // k ascending: a strict > keeps the smallest k
+        if (!occupied[k] && cp_ok[k] && (kb < 0 || cp_val[k] > v)) {
+            v = cp_val[k];
+            kb = k;
+        }
+    *best_cp = kb;
+    *best_price = kb >= 0 ? v : -INFINITY;
+    if (kb < 0) return;
+    const int N = g.n_cols;
+    const int64_t NS = (int64_t)(N + 1) * (N + 1);
+    const int16_t *pt = pred_all + (int64_t)kb * (g.n_rows * NS + 1);
+    int cur = pt[g.n_rows * NS];
+    for (int r = g.n_rows - 1; r >= 0; --r) {
+        best_leaves[2 * r] = (int16_t)(cur / (N + 1));
+        best_leaves[2 * r + 1] = (int16_t)(cur % (N + 1));
+        if (r > 0) cur = pt[(int64_t)r * NS + cur];
     }
-    __syncthreads();
-    if (kwin < 0) return;
-    extern __shared__ __align__(16) unsigned char smi[];
-    interdig_chain(g, pi, occupied, leaves, kwin, smi, pred_tab, nullptr, nullptr, best_leaves);
 }
 
 vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g) {
@@ -542,20 +600,24 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         // scratch: per-CP prices, then the chosen CP's predecessor table
         double *cp_val = rb_v;
         uint8_t *cp_ok = reinterpret_cast<uint8_t *>(cp_val + g.K);
-        int32_t *pred_tab = reinterpret_cast<int32_t *>(cp_ok + ((g.K + 15) & ~15));
+        double *Pall = reinterpret_cast<double *>(cp_ok + ((g.K + 15) & ~15));
+        int16_t *pred_all = reinterpret_cast<int16_t *>(Pall + (int64_t)g.K * g.n_rows * (g.n_cols + 1));
         const size_t sm = interdig_smem(g.n_cols);
         static bool attr_id = false;
         if (!attr_id) {
             VMAT_CUDA(cudaFuncSetAttribute(price_cps_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)interdig_smem(INTERDIG_MAX_COLS)));
-            VMAT_CUDA(cudaFuncSetAttribute(price_pick_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)interdig_smem(INTERDIG_MAX_COLS)));
             attr_id = true;
         }
-        price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, pi, occupied, leaves, cp_val, cp_ok, skip);
+        const int64_t rows = (int64_t)g.K * g.n_rows;
+        interdig_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
+                                 s>>>(g, pi, occupied, Pall, skip);
         VMAT_LAUNCH_CHECK();
-        price_pick_interdig_kernel<<<1, ID_THREADS, sm, s>>>(g, pi, occupied, leaves, cp_val, cp_ok, pred_tab,
-                                                               best_cp, best_leaves, best_price, skip);
+        price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, Pall, occupied, leaves, cp_val, cp_ok, pred_all,
+                                                               skip);
+        VMAT_LAUNCH_CHECK();
+        price_pick_interdig_kernel<<<1, 32, 0, s>>>(g, occupied, cp_val, cp_ok, pred_all, best_cp, best_leaves,
+                                                    best_price, skip);
         VMAT_LAUNCH_CHECK();
         return VMAT_OK;
     }
@@ -578,8 +640,10 @@ size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
     const size_t rows = (size_t)mlc->K * mlc->n_rows;
     size_t b = rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
     if (mlc->interdigitation) {
+        // per-CP prices, every row's prefix sums, every CP's predecessor table (16-bit)
         const size_t ns = (size_t)(mlc->n_cols + 1) * (mlc->n_cols + 1);
-        b = std::max(b, (size_t)mlc->K * 9 + 16 + (size_t)mlc->n_rows * ns * 4 + 64);
+        b = std::max(b, (size_t)mlc->K * 9 + 16 + (size_t)mlc->K * mlc->n_rows * (mlc->n_cols + 1) * 8 +
+                            (size_t)mlc->K * ((size_t)mlc->n_rows * ns + 1) * 2 + 64);
     }
     return b;
 }
