@@ -16,6 +16,7 @@ implementation of a VMAT treatment plan optimization algorithm"
 * Eq. 5            aperture dose vector DA = sum of D's columns in the aperture
 * Eq. 6-10         master problem by Barzilai-Borwein steps with the
                    subspace (bound) scheme; Section 2.1 stopping rules
+* Eq. 2, 6         fluence-rate bounds from gantry-speed, dose-rate and leaf-speed limits
 * Section 2.1      column-generation loop (PP <-> MP)
 
 Readings where the paper is silent or ambiguous (each is repeated where used):
@@ -43,6 +44,20 @@ R8  Ties: a row opening [L, R) is chosen by (value desc, width asc,
     prices, the CP price the sequential float64 sum over rows.
 R9  The loop stops when the best CP price is <= 0 (no aperture lowers F) or
     when n_apertures have been generated.
+R11 Delivery limits (Eq. 2, 6).  Gantry speed s_k of an occupied CP is the
+    speed over the interval that starts at k and ends at the next occupied CP
+    k' of the same arc, m = k' - k CP steps of cp_step degrees.  Its leaves move
+    at most d = max over rows of |L_k - L_k'|, |R_k - R_k'| columns in that
+    interval, so s_k <= S^U_{k,k'} = m cp_step leaf_speed / d (no limit when
+    d = 0 or k is the last occupied CP of its arc).  Speed changes between
+    consecutive occupied CPs are at most m Delta S.  The updated bounds of
+    Eq. 6 are the extreme speeds these constraints allow at k:
+    S^U_k = min over occupied j of the arc of (min(S^U, S^U_{j,j'}) + Delta S |k - j|),
+    S^L_k = S^L; then R^L / S^U_k <= y_k <= R^U / S^L_k, in float64, rounded to
+    float32 for the master problem.  Bounds are recomputed after every new
+    aperture.  The travel window (R7) must not exceed what the leaves can do at
+    the slowest gantry speed (travel_cols S^L <= cp_step leaf_speed), which
+    keeps S^U_k >= S^L.
 R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
     not pass the right leaf of an adjacent row, L_r <= min(R_{r-1}, R_{r+1}).
     The best aperture of a CP is then a chain over the rows: the sequential
@@ -338,6 +353,50 @@ def aperture_grad(mlc, cps, leaves, pi):
 
 
 # ----------------------------------------------------------------------------
+# Fluence-rate bounds from the delivery limits (Eq. 2, 6; reading R11)
+# ----------------------------------------------------------------------------
+
+def gantry_speed_bounds(mlc, machine, cps, leaves):
+    """Largest gantry speed S^U_k allowed at each placed CP (reading R11).
+
+    Returns (S_hat, S_U) per placed aperture, in the order of ``cps``: S_hat is
+    min(S^U, S^U_{k,k'}) of the aperture's own interval, S_U the updated bound
+    after the speed-change limit."""
+    n = len(cps)
+    cps = [int(k) for k in cps]
+    lv = [np.asarray(l, np.int64).reshape(mlc.n_rows, 2) for l in leaves]
+    S_hat = np.full(n, float(machine.speed_max), F64)
+    for t, k in enumerate(cps):
+        a0, a1 = arc_of(mlc, k)
+        later = [(kk, u) for u, kk in enumerate(cps) if k < kk < a1]
+        if not later:
+            continue
+        k2, u = min(later)
+        d = int(np.max(np.abs(lv[t] - lv[u])))
+        if d > 0:
+            m = k2 - k
+            S_hat[t] = min(S_hat[t], (float(m) * machine.cp_step_deg) * machine.leaf_speed_cols / float(d))
+    S_U = np.empty(n, F64)
+    for t, k in enumerate(cps):
+        a0, a1 = arc_of(mlc, k)
+        S_U[t] = min(S_hat[u] + machine.speed_step_max * float(abs(k - kk))
+                     for u, kk in enumerate(cps) if a0 <= kk < a1)
+    return S_hat, S_U
+
+
+def fluence_bounds(mlc, machine, cps, leaves):
+    """Eq. 6 bounds R^L / S^U_k <= y_k <= R^U / S^L of each placed aperture, as
+    float32 (reading R11).  Without a machine: [0, +inf)."""
+    n = len(cps)
+    if machine is None:
+        return np.zeros(n, np.float32), np.full(n, np.inf, np.float32)
+    _, S_U = gantry_speed_bounds(mlc, machine, cps, leaves)
+    lo = machine.rate_min / S_U
+    hi = np.full(n, machine.rate_max / machine.speed_min if machine.speed_min > 0 else np.inf, F64)
+    return lo.astype(np.float32), hi.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
 # Master problem (Eq. 6-10; readings R1-R6)
 # ----------------------------------------------------------------------------
 
@@ -463,7 +522,8 @@ def cg_plan(D, mlc, structs, n_apertures: int, opts: BBOptions | None = None, pr
         prices.append(price)
         cols.append(aperture_dose(D, mlc, k, lv))
         y = np.concatenate([y, [0.0]])
-        y, z, _, it, _, _ = mp_bb_solve(np.stack(cols, axis=1), sid, T, wo, wu, y, opts=opts)
+        lo, hi = fluence_bounds(mlc, getattr(mlc, "machine", None), cps, lvs)
+        y, z, _, it, _, _ = mp_bb_solve(np.stack(cols, axis=1), sid, T, wo, wu, y, lo, hi, opts=opts)
         iters.append(it)
     x = aperture_fluence(mlc, cps, lvs, y) if cps else np.zeros(J, F64)
     dose = dose_forward(D, x)

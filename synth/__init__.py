@@ -132,6 +132,20 @@ class Geometry:
 
 
 @dataclasses.dataclass
+class Machine:
+    """Delivery limits of Eq. 2: gantry speed, its change between CPs, dose rate
+    and leaf speed.  Angles in degrees, times in seconds, leaf travel in MLC
+    columns (the paper gives no values; these are parameters)."""
+    cp_step_deg: float      # gantry angle between adjacent CPs of an arc
+    speed_min: float        # S^L (deg/s)
+    speed_max: float        # S^U (deg/s)
+    speed_step_max: float   # Delta S: largest change of gantry speed per CP step (deg/s)
+    rate_min: float         # R^L (MU/s)
+    rate_max: float         # R^U (MU/s)
+    leaf_speed_cols: float  # largest leaf speed (columns/s)
+
+
+@dataclasses.dataclass
 class MLC:
     """Beamlet layout j = (k*n_rows + r)*n_cols + c; arcs are CP ranges."""
     K: int
@@ -140,6 +154,7 @@ class MLC:
     arc_first_cp: np.ndarray  # int32 [n_arcs]; arc a spans [first[a], first[a+1] or K)
     travel_cols: int = 3
     interdigitation: bool = False  # adjacent rows: L_r <= R_{r-1} and L_r <= R_{r+1}
+    machine: Machine | None = None  # None: every aperture's fluence rate in [0, +inf)
 
     @property
     def n_arcs(self) -> int:
@@ -363,6 +378,17 @@ def make_mlc(geom: Geometry, travel_cols: int = 3) -> MLC:
 
 
 _CACHE: dict = {}
+
+
+def make_machine(mlc: MLC, speed_min: float = 0.5, speed_max: float = 4.0, speed_step_max: float = 0.5,
+                 rate_min: float = 0.02, rate_max: float = 0.025) -> Machine:
+    """A delivery machine for an MLC: CPs evenly spaced over each arc's 360
+    degrees, and a leaf speed 1.25x what the MLC's travel window needs at the
+    slowest gantry speed (so the travel window never asks for more than the
+    leaves can do).  Defaults make both fluence bounds bind on the test plans."""
+    step = 360.0 * mlc.n_arcs / mlc.K
+    return Machine(step, speed_min, speed_max, speed_step_max, rate_min, rate_max,
+                   1.25 * max(mlc.travel_cols, 1) * speed_min / step)
 
 
 def make_case(name: str, seed: int = 0, cache: bool = True) -> Case:
