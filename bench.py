@@ -58,6 +58,11 @@ SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
 
 
+def dataclasses_asdict(x):
+    import dataclasses
+    return None if x is None else dataclasses.asdict(x)
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -234,9 +239,12 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     t0 = time.time()
     case = synth.make_case(args.workload, seed=rank, cache=False)
-    if args.interdig:
+    if args.interdig or args.machine:
         import dataclasses
-        case = dataclasses.replace(case, mlc=dataclasses.replace(case.mlc, interdigitation=True))
+        mlc = dataclasses.replace(case.mlc, interdigitation=bool(args.interdig))
+        if args.machine:
+            mlc.machine = synth.make_machine(mlc)
+        case = dataclasses.replace(case, mlc=mlc)
     log(f"[rank {rank}] generated {case.nnz} nonzeros in {time.time() - t0:.1f}s")
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
     vox_h, blt_h, val_h = pin(case.vox, torch.int32), pin(case.blt, torch.int32), pin(case.val, torch.float32)
@@ -362,6 +370,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": f"{args.workload} {DESCS[args.workload]}", "V": case.V, "J": case.J, "nnz": case.nnz,
                        "n_active_vox": info["n_active_vox"], "n_apertures": n_ap, "storage": args.dtype,
                        "interdigitation": bool(args.interdig),
+                       "machine": dataclasses_asdict(case.mlc.machine),
                        "l2": "inputs larger than L2 (CSR D + D^T %.1f GB)" % ((info["bytes_D"] + info["bytes_Dt"]) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
@@ -636,6 +645,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     ap.add_argument("--interdig", action="store_true", help="plan mode: price with the interdigitation constraint")
+    ap.add_argument("--machine", action="store_true",
+                    help="plan mode: fluence-rate bounds from gantry-speed, dose-rate and leaf-speed limits")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.mode == "plan":
         log("note: fewer than 3 warm-up steps")

@@ -45,19 +45,38 @@ typedef enum { VMAT_F32 = 0, VMAT_BF16 = 1, VMAT_FP8E4M3 = 2 } vmat_dtype;
  * library-owned device memory. */
 typedef struct vmat_ddc_s *vmat_ddc;
 
+/* Delivery limits of Eq. 2 (HOST struct; the paper gives no values, so they
+ * are parameters).  All finite: cp_step_deg > 0 (gantry angle between adjacent
+ * CPs of an arc), 0 <= speed_min <= speed_max, speed_max > 0 (gantry speed
+ * bounds S^L, S^U, deg/s), speed_step_max >= 0 (Delta S: the largest change of
+ * gantry speed per CP step, deg/s), 0 <= rate_min <= rate_max (dose-rate bounds
+ * R^L, R^U, MU/s), leaf_speed_cols > 0 (largest leaf speed, MLC columns/s).
+ * The MLC's travel window must be reachable at the slowest gantry speed:
+ * travel_cols * speed_min <= cp_step_deg * leaf_speed_cols (else VMAT_EINVAL). */
+typedef struct {
+    double cp_step_deg;
+    double speed_min, speed_max;
+    double speed_step_max;
+    double rate_min, rate_max;
+    double leaf_speed_cols;
+} vmat_machine;
+
 /* MLC geometry.  arc_first_cp is HOST memory: n_arcs ascending CP indices,
  * arc_first_cp[0] == 0; arc a spans [arc_first_cp[a], arc_first_cp[a+1]) (the
  * last arc ends at K).  travel_cols: columns a leaf may travel per CP step
  * (the neighbour-compatibility reading of Eq. 2).  interdigitation != 0: the
  * left leaf of a row may not pass the right leaf of an adjacent row,
  * L_r <= min(R_{r-1}, R_{r+1}) (Section 2.2.2, second pricing variant;
- * n_cols <= 88; not in batches). */
+ * n_cols <= 88; not in batches).  machine: HOST, or NULL for fixed fluence
+ * bounds [0, +inf); with a machine, cg_plan and batches bound every aperture's
+ * fluence rate by fluence_bounds before each master problem (Eq. 6). */
 typedef struct {
     int32_t K, n_rows, n_cols;
     int32_t n_arcs;
     const int32_t *arc_first_cp;
     int32_t travel_cols;
     int32_t interdigitation;
+    const vmat_machine *machine;
 } vmat_mlc;
 
 /* Voxel penalty parameters of Eq. 1: per-voxel structure label (device uint8
@@ -261,12 +280,30 @@ vmat_status mp_bb_solve(const float *DA, int32_t V, int32_t n_ap, int64_t ld, co
                         const float *lo, const float *hi, float *y, float *z, const vmat_bb_opts *opts,
                         vmat_bb_report *rep, void *stream);
 
+/* Fluence-rate bounds of Eq. 6 from the delivery limits of Eq. 2, for the
+ * apertures placed so far: cps (device int32 [n_ap], distinct CPs; entries < 0
+ * are slots not yet placed, which get [0, +inf) and are ignored) and their
+ * leaves (device int16 [n_ap][n_rows][2], in the same order).  The gantry speed
+ * s_k of a placed CP is the speed from k to the next placed CP k' of its arc,
+ * m = k' - k steps: with d the largest leaf move (columns) between the two
+ * apertures, s_k <= S^U_{k,k'} = m cp_step_deg leaf_speed_cols / d (no limit if
+ * d = 0 or k is the arc's last placed CP).  Speeds of consecutive placed CPs
+ * differ by at most m speed_step_max.  S^U_k = min over placed j of the arc of
+ * (min(S^U, S^U_{j,j'}) + speed_step_max |k - j|) is the largest speed these
+ * constraints allow at k, S^L the smallest; then lo[n] = R^L / S^U_k and
+ * hi[n] = R^U / S^L (+inf when S^L = 0), each the float64 quotient rounded to
+ * float32.  lo, hi: device float [n_ap].  mlc->machine NULL: [0, +inf).
+ * n_ap <= 8192.  Asynchronous on stream. */
+vmat_status fluence_bounds(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps, const int16_t *leaves, float *lo,
+                           float *hi, void *stream);
+
 /* ---- Column generation (Section 2.1, Fig. 1a) ---------------------------- */
 
 /* Generate up to n_apertures apertures: repeat { g = -grad F(z); pi = D^T g
  * over unoccupied CPs; best aperture; DA column (Eq. 5); master problem over
- * all apertures (warm start, new y = 0) } until n_apertures are generated or
- * the best price is <= 0.  Finally dose = D (A y) in FP32 and F(dose).
+ * all apertures (warm start, new y = 0; with mlc->machine, within the bounds
+ * fluence_bounds gives for the apertures placed so far) } until n_apertures
+ * are generated or the best price is <= 0.  Finally dose = D (A y) in FP32 and F(dose).
  * Outputs may be host or device memory (copied with cudaMemcpyDefault), any
  * may be NULL: cps_out int32 [n_apertures] (unused slots -1), leaves_out
  * int16 [n_apertures][n_rows][2], y_out float [n_apertures], dose_out float

@@ -18,9 +18,15 @@ DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 STOP_NAMES = {1: "rel", 2: "step", 3: "maxit", 4: "grad0", 5: "flat", 10: "price", 11: "count"}
 
 
+class Machine(ctypes.Structure):
+    _fields_ = [("cp_step_deg", c_f64), ("speed_min", c_f64), ("speed_max", c_f64), ("speed_step_max", c_f64),
+                ("rate_min", c_f64), ("rate_max", c_f64), ("leaf_speed_cols", c_f64)]
+
+
 class Mlc(ctypes.Structure):
     _fields_ = [("K", c_i32), ("n_rows", c_i32), ("n_cols", c_i32), ("n_arcs", c_i32),
-                ("arc_first_cp", ctypes.POINTER(c_i32)), ("travel_cols", c_i32), ("interdigitation", c_i32)]
+                ("arc_first_cp", ctypes.POINTER(c_i32)), ("travel_cols", c_i32), ("interdigitation", c_i32),
+                ("machine", ctypes.POINTER(Machine))]
 
 
 class Voxels(ctypes.Structure):
@@ -77,6 +83,7 @@ SIGNATURES = {
     "aperture_dose": (c_i32, [c_vp, ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp]),
     "aperture_fluence": (c_i32, [ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "aperture_grad": (c_i32, [ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "fluence_bounds": (c_i32, [ctypes.POINTER(Mlc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "mp_bb_solve": (c_i32, [c_vp, c_i32, c_i32, c_i64, ctypes.POINTER(Voxels), c_vp, c_vp, c_vp, c_vp,
                             ctypes.POINTER(BBOpts), ctypes.POINTER(BBReport), c_vp]),
     "cg_plan": (c_i32, [c_vp, ctypes.POINTER(Mlc), ctypes.POINTER(Voxels), c_i32, ctypes.POINTER(BBOpts),

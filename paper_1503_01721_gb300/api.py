@@ -66,14 +66,19 @@ class VoxelParams:
 
 
 class _MlcC:
-    """Holds the ctypes MLC struct and its host arc array alive for a call."""
+    """Holds the ctypes MLC struct, its host arc array and machine limits alive for a call."""
 
     def __init__(self, mlc):
         arcs = np.ascontiguousarray(np.asarray(mlc.arc_first_cp, np.int32))
         self._arcs = (ctypes.c_int32 * len(arcs))(*arcs.tolist())
+        m = getattr(mlc, "machine", None)
+        self._machine = None if m is None else _lib.Machine(
+            float(m.cp_step_deg), float(m.speed_min), float(m.speed_max), float(m.speed_step_max),
+            float(m.rate_min), float(m.rate_max), float(m.leaf_speed_cols))
         self.s = _lib.Mlc(int(mlc.K), int(mlc.n_rows), int(mlc.n_cols), len(arcs),
                           ctypes.cast(self._arcs, ctypes.POINTER(ctypes.c_int32)), int(mlc.travel_cols),
-                          int(bool(getattr(mlc, "interdigitation", False))))
+                          int(bool(getattr(mlc, "interdigitation", False))),
+                          ctypes.pointer(self._machine) if self._machine is not None else None)
 
 
 def _bb_opts(opts):
@@ -183,6 +188,17 @@ def aperture_grad(mlc, cps, leaves, pi, gy, stream=None) -> None:
     check("aperture_grad", _lib.load().aperture_grad(
         ctypes.byref(m.s), n, _ptr(cps, torch.int32, n, "cps"), _ptr(leaves, torch.int16, n * mlc.n_rows * 2, "leaves"),
         _ptr(pi, torch.float32, None, "pi"), _ptr(gy, torch.float32, n, "gy"), _stream(stream)))
+
+
+def fluence_bounds(mlc, cps: torch.Tensor, leaves: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor,
+                   stream=None) -> None:
+    """Fluence-rate bounds of Eq. 6 from the delivery limits of Eq. 2 (``mlc.machine``)
+    for the placed apertures (cps < 0: slots not placed)."""
+    m = _MlcC(mlc)
+    n = cps.numel()
+    check("fluence_bounds", _lib.load().fluence_bounds(
+        ctypes.byref(m.s), n, _ptr(cps, torch.int32, n, "cps"), _ptr(leaves, torch.int16, n * mlc.n_rows * 2, "leaves"),
+        _ptr(lo, torch.float32, n, "lo"), _ptr(hi, torch.float32, n, "hi"), _stream(stream)))
 
 
 def mp_bb_solve(DA: torch.Tensor, vox: VoxelParams, y: torch.Tensor, z: torch.Tensor, lo=None, hi=None,

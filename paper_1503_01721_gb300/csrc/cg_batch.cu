@@ -5,6 +5,7 @@
 //   pricing rows of every plan, then one block per plan picks CPs  (two)
 //   the commit (or the stop) of every plan                        (one)
 //   the new aperture's dose column of every plan (Eq. 5)           (one)
+//   the fluence-rate bounds of plans with delivery limits (Eq. 2, 6)  (one)
 //   the master problems: one persistent cooperative launch whose
 //   CTAs are split among the plans in proportion to their voxels   (two)
 // A plan that has all its apertures, or whose best price is <= 0, sets its
@@ -77,12 +78,13 @@ __global__ void batch_cp_offsets(const int64_t *rowptr, int32_t K, int32_t bpc, 
 struct BPlan {
     Ddc *h = nullptr;
     vmat_mlc mlc = {};
+    vmat_machine machine = {}; // the plan's own copy (mlc.machine points here when set)
     std::vector<int32_t> arcs;
     vmat_voxels vox = {}, vox_c = {};
     int32_t n_ap = 0, V = 0, J = 0, K = 0, NR = 0, bpc = 0, NA = 0;
     int64_t n_wtiles = 0, wstride = 0;
     float *z_c = nullptr, *g_full = nullptr, *pi = nullptr, *DA = nullptr, *y = nullptr, *x = nullptr,
-          *dose = nullptr;
+          *dose = nullptr, *lo = nullptr, *hi = nullptr;
     uint8_t *occupied = nullptr, *active = nullptr, *sid_c = nullptr;
     int16_t *leaves_all = nullptr, *best_leaves = nullptr, *leaves_seq = nullptr;
     int32_t *best_cp = nullptr, *cps = nullptr, *ctl = nullptr;
@@ -111,6 +113,7 @@ struct Batch {
     ObjPlan *d_obj = nullptr;
     int64_t *d_na_off = nullptr, tot_na = 0;
     CommitPlan *d_commit = nullptr;
+    BoundsPlan *d_bounds = nullptr; // null when no plan has a machine
     void *d_mpargs = nullptr;
     int64_t *d_weight = nullptr; // [n] warp tiles of each plan (the solver's CTA split)
     unsigned *d_gctl = nullptr;  // [8] batch barrier, epoch and active-set words
@@ -169,6 +172,7 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
         batch_commit<<<n, 128, 0, s>>>(t, b.d_commit);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(aperture_dose_batched(b.dt, b.d_da, b.d_na_off, n, b.tot_na, t, s));
+        if (b.d_bounds) VMAT_TRY(fluence_bounds_batched(b.d_bounds, n, t + 1, s));
         VMAT_TRY(mp_bb_enqueue_batched(b.d_mpargs, b.d_weight, b.d_gctl, n, t + 1, b.grid_t[t], b.stages_t[t],
                                        b.smem_t[t], b.keep_t[t], s));
     }
@@ -212,6 +216,10 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         p.mlc = *d.mlc;
         p.arcs.assign(d.mlc->arc_first_cp, d.mlc->arc_first_cp + d.mlc->n_arcs);
         p.mlc.arc_first_cp = p.arcs.data();
+        if (d.mlc->machine) {
+            p.machine = *d.mlc->machine;
+            p.mlc.machine = &p.machine;
+        }
         p.vox = *d.vox;
         p.n_ap = d.n_apertures;
         p.V = h->V;
@@ -241,6 +249,10 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         VMAT_TRY(b.get(&p.pi, p.J));
         VMAT_TRY(b.get(&p.DA, (size_t)p.n_wtiles * p.wstride));
         VMAT_TRY(b.get(&p.y, nap));
+        if (p.mlc.machine) {
+            VMAT_TRY(b.get(&p.lo, nap));
+            VMAT_TRY(b.get(&p.hi, nap));
+        }
         VMAT_TRY(b.get(&p.x, p.J));
         VMAT_TRY(b.get(&p.dose, p.V));
         VMAT_TRY(b.get(&p.occupied, p.K));
@@ -328,8 +340,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         na_off[i + 1] = na_off[i] + p.NA;
         targets[i] = p.n_ap;
         VMAT_TRY(mp_fill_plan_args(mpargs.data() + (size_t)i * argb, p.mp_ws, std::min(std::max(p.n_ap, 1), 96), p.DA,
-                                   p.wstride, p.NA, p.sid_c, &p.vox_c, p.y, p.z_c, &b.opts, p.F_offset, p.ctl,
-                                   p.ctl + CTL_BBITERS));
+                                   p.wstride, p.NA, p.sid_c, &p.vox_c, p.lo, p.hi, p.y, p.z_c, &b.opts, p.F_offset,
+                                   p.ctl, p.ctl + CTL_BBITERS));
     }
     b.tot_rows = rows_off[n_plans];
     b.tot_price = price_off[n_plans];
@@ -353,6 +365,24 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaMemcpy(b.d_na_off, na_off.data(), (n_plans + 1) * 8, cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_mpargs, mpargs.data(), (size_t)n_plans * argb, cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_targets, targets.data(), n_plans * 4, cudaMemcpyHostToDevice));
+    bool any_machine = false;
+    std::vector<BoundsPlan> bounds(n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        BPlan &p = b.P[i];
+        bounds[i] = BoundsPlan{};
+        if (!p.mlc.machine) continue; // lo == NULL: the kernel skips this plan
+        VMAT_TRY(bounds_geom(&p.mlc, &bounds[i].g));
+        bounds[i].cps = p.cps;
+        bounds[i].leaves = p.leaves_seq;
+        bounds[i].lo = p.lo;
+        bounds[i].hi = p.hi;
+        bounds[i].skip = p.ctl;
+        any_machine = true;
+    }
+    if (any_machine) {
+        VMAT_TRY(b.get(&b.d_bounds, n_plans));
+        VMAT_CUDA(cudaMemcpy(b.d_bounds, bounds.data(), n_plans * sizeof(BoundsPlan), cudaMemcpyHostToDevice));
+    }
 
     // ---- master-problem launch shapes for every aperture count (the kernel splits the CTAs)
     b.grid_t.assign(std::max(b.T, 1), 1);

@@ -130,6 +130,8 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         return set_error(VMAT_EINVAL, "cg_plan: K*n_rows*n_cols != J");
     if (n_apertures < 0 || n_apertures > mlc->K)
         return set_error(VMAT_EINVAL, "cg_plan: n_apertures must be in [0, K] (each CP holds one aperture)");
+    if (mlc->machine && n_apertures > BOUNDS_MAX_AP)
+        return set_error(VMAT_EINVAL, "cg_plan: at most %d apertures with a machine", BOUNDS_MAX_AP);
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     cudaStream_t s = as_stream(stream);
@@ -209,6 +211,14 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     vox_c.struct_id = sid_c;
     int bb_extra = 0;
 
+    // fluence-rate bounds of the apertures placed so far (Eq. 2, 6), with a machine
+    BoundsGeom bg;
+    VMAT_TRY(bounds_geom(mlc, &bg));
+    float *lo = nullptr, *hi = nullptr;
+    if (bg.has_machine) {
+        VMAT_TRY(ar.get(&lo, nap_max));
+        VMAT_TRY(ar.get(&hi, nap_max));
+    }
     int32_t *ctl;
     VMAT_TRY(ar.get(&ctl, CTL_N));
     VMAT_CUDA(cudaMemsetAsync(ctl, 0, CTL_N * sizeof(int32_t), s));
@@ -251,17 +261,18 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
                                    wstride, ctl, s));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
+        if (lo) VMAT_TRY(fluence_bounds_enqueue(bg, t + 1, cps_dev, leaves_seq, lo, hi, ctl, s));
         if (NA > 0) {
             if (t + 1 <= n_cap) {
-                VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, y, z_c, opts, F_offset, mp_ws,
-                                       ctl, ctl + CTL_BBITERS, s));
+                VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, F_offset,
+                                       mp_ws, ctl, ctl + CTL_BBITERS, s));
             } else {
                 VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 VMAT_CUDA(cudaStreamSynchronize(s));
                 if (!hctl[CTL_STOPPED]) {
                     vmat_bb_report rep;
-                    VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, nullptr, nullptr, y, z_c, opts,
-                                        F_offset, &rep, s));
+                    VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, lo, hi, y, z_c, opts, F_offset,
+                                        &rep, s));
                     bb_extra += rep.iters;
                 }
             }

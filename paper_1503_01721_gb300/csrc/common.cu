@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -201,6 +202,24 @@ vmat_status validate_mlc(const vmat_mlc *mlc) {
     for (int a = 1; a < mlc->n_arcs; ++a)
         if (mlc->arc_first_cp[a] <= mlc->arc_first_cp[a - 1] || mlc->arc_first_cp[a] >= mlc->K)
             return set_error(VMAT_EINVAL, "mlc arc_first_cp must be strictly increasing and < K");
+    if (const vmat_machine *m = mlc->machine) {
+        const double v[7] = {m->cp_step_deg, m->speed_min, m->speed_max, m->speed_step_max,
+                             m->rate_min, m->rate_max, m->leaf_speed_cols};
+        for (double x : v)
+            if (!std::isfinite(x)) return set_error(VMAT_EINVAL, "machine: every limit must be finite");
+        if (!(m->cp_step_deg > 0.0) || !(m->speed_max > 0.0) || !(m->leaf_speed_cols > 0.0))
+            return set_error(VMAT_EINVAL, "machine: cp_step_deg, speed_max and leaf_speed_cols must be > 0");
+        if (!(m->speed_min >= 0.0 && m->speed_min <= m->speed_max) || !(m->speed_step_max >= 0.0) ||
+            !(m->rate_min >= 0.0 && m->rate_min <= m->rate_max))
+            return set_error(VMAT_EINVAL, "machine: need 0 <= speed_min <= speed_max, speed_step_max >= 0 and "
+                                          "0 <= rate_min <= rate_max");
+        // the travel window must be reachable at the slowest gantry speed, so every
+        // interval cap is >= speed_min and the bounds stay ordered
+        if ((double)mlc->travel_cols * m->speed_min > m->cp_step_deg * m->leaf_speed_cols)
+            return set_error(VMAT_EINVAL, "machine: travel_cols * speed_min (%g) exceeds cp_step_deg * "
+                                          "leaf_speed_cols (%g)",
+                             (double)mlc->travel_cols * m->speed_min, m->cp_step_deg * m->leaf_speed_cols);
+    }
     return VMAT_OK;
 }
 

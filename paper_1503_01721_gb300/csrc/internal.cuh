@@ -179,6 +179,27 @@ struct PricePlan { // one plan's pricing inputs, per-row scratch and results
     double *best_price;
     const int32_t *skip;
 };
+// Fluence-rate bounds of Eq. 6 from the delivery limits of Eq. 2 (bounds.cu).
+constexpr int BOUNDS_MAX_AP = 8192;
+struct BoundsGeom {
+    int32_t K, n_rows, n_arcs, has_machine;
+    int32_t arc_first[MAX_ARCS + 1];
+    double step, s_min, s_max, ds, r_min, r_max, v_leaf;
+};
+struct BoundsPlan { // one plan's bounds inputs and outputs for the batched kernel
+    BoundsGeom g;
+    const int32_t *cps;
+    const int16_t *leaves;
+    float *lo, *hi;
+    const int32_t *skip;
+};
+vmat_status bounds_geom(const vmat_mlc *mlc, BoundsGeom *g);
+// lo/hi of the first n slots of (cps, leaves); nothing when *skip != 0.
+vmat_status fluence_bounds_enqueue(const BoundsGeom &g, int32_t n, const int32_t *cps, const int16_t *leaves,
+                                   float *lo, float *hi, const int32_t *skip, cudaStream_t s);
+// One block per plan, the first n slots of each (plans: device array).
+vmat_status fluence_bounds_batched(const BoundsPlan *plans, int32_t n_plans, int32_t n, cudaStream_t s);
+
 struct DaPlan { // one plan's CSR(D) and warp-tile DA for the batched aperture dose
     const int64_t *rowptr;
     const int32_t *col;
@@ -238,8 +259,8 @@ vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, floa
 // ws holds mp_workspace_bytes(n_cap) bytes; skip and iters_acc as in the solver's arguments.
 size_t mp_workspace_bytes(int32_t n_cap);
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
-                          const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
-                          const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
+                          const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                          float *z, const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
                           int32_t *iters_acc, cudaStream_t s);
 // Batched master problems (persistent solver, one cooperative launch for all plans).
 // Per-plan arguments are an opaque mp_args_bytes() record filled by mp_fill_plan_args
@@ -247,8 +268,9 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
 // n apertures (every resident CTA; the kernel splits them among the plans).
 size_t mp_args_bytes();
 vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
-                              const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
-                              const vmat_bb_opts *opts, double F_offset, const int32_t *skip, int32_t *iters_acc);
+                              const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi,
+                              float *y, float *z, const vmat_bb_opts *opts, double F_offset, const int32_t *skip,
+                              int32_t *iters_acc);
 vmat_status mp_batched_grid(int32_t n, int32_t n_plans, int32_t *grid, int32_t *stages, size_t *smem);
 // weight: device [n_plans] (warp tiles of each plan); gctl: device [8] batch barrier, epoch and
 // active-set words.

@@ -1324,8 +1324,8 @@ static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream
 }
 
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
-                          const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
-                          const vmat_bb_opts *opts_in, double F_offset, void *ws, const int32_t *skip,
+                          const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
+                          float *z, const vmat_bb_opts *opts_in, double F_offset, void *ws, const int32_t *skip,
                           int32_t *iters_acc, cudaStream_t s) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
@@ -1338,8 +1338,8 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
     if (!L.persistent)
         return set_error(VMAT_EUNSUPPORTED, "mp_bb_enqueue: %d apertures need the host-driven solver", n_ap);
     MPArgs a;
-    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_ap, struct_id, vox, nullptr, nullptr, y, z, opts,
-                 F_offset, L, ctx);
+    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_ap, struct_id, vox, lo, hi, y, z, opts, F_offset, L,
+                 ctx);
     a.skip = skip;
     a.iters_acc = iters_acc;
     return mp_launch_persistent(a, L, s);
@@ -1348,8 +1348,9 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
 size_t mp_args_bytes() { return sizeof(MPArgs); }
 
 vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
-                              const uint8_t *struct_id, const vmat_voxels *vox, float *y, float *z,
-                              const vmat_bb_opts *opts_in, double F_offset, const int32_t *skip, int32_t *iters_acc) {
+                              const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi,
+                              float *y, float *z, const vmat_bb_opts *opts_in, double F_offset, const int32_t *skip,
+                              int32_t *iters_acc) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
@@ -1358,8 +1359,8 @@ vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *D
     MPLaunch L = {};
     L.P = 1;
     MPArgs a;
-    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_cap, struct_id, vox, nullptr, nullptr, y, z, opts,
-                 F_offset, L, ctx);
+    mp_fill_args(a, ws, n_cap, mp_p_max(ctx), DA, wstride, V, n_cap, struct_id, vox, lo, hi, y, z, opts, F_offset, L,
+                 ctx);
     a.skip = skip;
     a.iters_acc = iters_acc;
     memcpy(out, &a, sizeof(MPArgs));

@@ -67,6 +67,23 @@ def test_host_validation_errors(lib):
     m = _lib.Mlc(6, 2, 2000, 2, ctypes.cast(arcs, ctypes.POINTER(ctypes.c_int32)), 1)
     assert lib.price_apertures(ctypes.byref(m), None, None, None, None, None, None, None) == _lib.VMAT_EINVAL
     assert b"n_cols" in lib.vmat_last_error()
+    # machine checks (Eq. 2 limits): finite, ordered, travel window reachable at the slowest speed
+    arcs = (ctypes.c_int32 * 1)(0)
+    good = dict(cp_step_deg=10.0, speed_min=0.5, speed_max=4.0, speed_step_max=0.5, rate_min=0.02,
+                rate_max=0.025, leaf_speed_cols=0.1875)
+    for bad, msg in (({"speed_min": 5.0}, b"speed_min <= speed_max"), ({"rate_min": 0.03}, b"rate_min <= rate_max"),
+                     ({"leaf_speed_cols": 0.1}, b"travel_cols * speed_min"), ({"cp_step_deg": 0.0}, b"> 0"),
+                     ({"speed_step_max": float("inf")}, b"finite"), ({"speed_step_max": -1.0}, b"speed_step_max")):
+        mach = _lib.Machine(**{**good, **bad})
+        m = _lib.Mlc(6, 2, 4, 1, ctypes.cast(arcs, ctypes.POINTER(ctypes.c_int32)), 3, 0, ctypes.pointer(mach))
+        assert lib.fluence_bounds(ctypes.byref(m), 1, 8, 8, 8, 8, None) == _lib.VMAT_EINVAL, bad
+        assert msg in lib.vmat_last_error(), (bad, lib.vmat_last_error())
+    mach = _lib.Machine(**good)
+    m = _lib.Mlc(6, 2, 4, 1, ctypes.cast(arcs, ctypes.POINTER(ctypes.c_int32)), 3, 0, ctypes.pointer(mach))
+    assert lib.fluence_bounds(ctypes.byref(m), -1, None, None, None, None, None) == _lib.VMAT_EINVAL
+    assert lib.fluence_bounds(ctypes.byref(m), 9000, 8, 8, 8, 8, None) == _lib.VMAT_EINVAL
+    assert lib.fluence_bounds(ctypes.byref(m), 2, None, 8, 8, 8, None) == _lib.VMAT_EINVAL
+    assert lib.fluence_bounds(ctypes.byref(m), 0, None, None, None, None, None) == _lib.VMAT_OK
     # voxel parameter checks
     v = _lib.Voxels(None, 0, None, None, None)
     assert lib.objective_grad(10, None, ctypes.byref(v), None, None, None) == _lib.VMAT_EINVAL
