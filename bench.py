@@ -46,7 +46,10 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
                 3: "spmv_tile_kernel<128,16,3>", 4: "spmv_warp_row_kernel<256,2>", 5: "spmv_warp_row_kernel<256,1>",
                 6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>",
                 9: "spmv_warp_row_c_kernel<256,4>", 10: "spmv_warp_row_c_kernel<256,8>",
-                11: "spmv_warp_row_c_kernel<512,4>"}
+                11: "spmv_warp_row_c_kernel<512,4>", 12: "spmv_warp_row_z_kernel<256,4>",
+                13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>"}
+# configurations that read the 16-bit column index (built with index16)
+INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
 # configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
 # (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.
@@ -253,7 +256,7 @@ def run_ours(args, rank, world, local):
 
     # resident DDC
     h = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0)
+    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0, index16=args.index16)
     info = api.ddc_info(h)
     log(f"[rank {rank}] build {info['build_ms']:.1f} ms, active voxels {info['n_active_vox']}")
 
@@ -346,7 +349,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         h2 = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-        api.ddc_build(h2, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0)
+        api.ddc_build(h2, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0, index16=args.index16)
         F2, st2 = api.cg_plan(h2, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose_h)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t_a)
@@ -408,12 +411,25 @@ def run_spmv_only(args):
     pi = torch.empty(case.J, device="cuda")
     dd = torch.empty(case.V, device="cuda")
     out = {"mode": "spmv", "workload": args.workload, "nnz": case.nnz, "dtype": args.dtype, "configs": {}}
+    from paper_1503_01721_gb300 import _lib
     for cfg in (range(api.spmv_config_count()) if args.sweep else [args.tile_cfg]):
-        ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg)
+        z = cfg in INDEX16_CFGS
+        try:
+            ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=z or args.index16)
+        except _lib.VmatError:
+            if not z:
+                raise
+            try:  # CSR(D) without a 16-bit index: time D^T g alone
+                ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=True, build_D=False)
+            except _lib.VmatError as e:
+                out["configs"][cfg] = {"unavailable": str(e)}
+                continue
         info = ddc.info()
+        has_d = bool(info["built_D"])
         for _ in range(3):
             api.beamlet_price(ddc.h, g, pi)
-            api.dose_forward(ddc.h, x, dd)
+            if has_d:
+                api.dose_forward(ddc.h, x, dd)
         torch.cuda.synchronize()
         if args.sweep:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -421,16 +437,32 @@ def run_spmv_only(args):
             for _ in range(10):
                 api.beamlet_price(ddc.h, g, pi)
             ev[1].record()
-            for _ in range(10):
+            for _ in range(10 if has_d else 0):
                 api.dose_forward(ddc.h, x, dd)
             ev[2].record()
             torch.cuda.synchronize()
             sc = case.J if args.dtype == "fp8" else 0
-            b_t = roofline.spmv_bytes(case.nnz, case.J, case.V, case.J, args.dtype, sc)
-            b_d = roofline.spmv_bytes(case.nnz, info["n_active_vox"], case.J, case.V, args.dtype, sc)
-            t_t, t_d = ev[0].elapsed_time(ev[1]) / 10, ev[1].elapsed_time(ev[2]) / 10
-            out["configs"][cfg] = {"dt_g_gbs": round(b_t / t_t / 1e6, 1), "d_x_gbs": round(b_d / t_d / 1e6, 1),
-                                   "dt_g_ms": round(t_t, 4), "d_x_ms": round(t_d, 4)}
+            # chunk counts from the index sizes (2 bytes per nonzero, 4 per chunk, 8 per row pointer)
+            chunks = lambda b16, rows: (b16 - 2 * case.nnz - 8 * (rows + 1)) // 4
+            if z:
+                b_t = roofline.spmv_bytes_index16(case.nnz, chunks(info["bytes16_Dt"], case.J), case.J, case.V,
+                                                  case.J, args.dtype, sc)
+            else:
+                b_t = roofline.spmv_bytes(case.nnz, case.J, case.V, case.J, args.dtype, sc)
+            t_t = ev[0].elapsed_time(ev[1]) / 10
+            rec = {"dt_g_gbs": round(b_t / t_t / 1e6, 1), "dt_g_ms": round(t_t, 4), "dt_g_bytes": b_t}
+            if has_d:
+                if z:
+                    nr = info["n_active_vox"]
+                    b_d = roofline.spmv_bytes_index16(case.nnz, chunks(info["bytes16_D"], nr), nr, case.J, case.V,
+                                                      args.dtype, sc)
+                else:
+                    b_d = roofline.spmv_bytes(case.nnz, info["n_active_vox"], case.J, case.V, args.dtype, sc)
+                t_d = ev[1].elapsed_time(ev[2]) / 10
+                rec.update({"d_x_gbs": round(b_d / t_d / 1e6, 1), "d_x_ms": round(t_d, 4)})
+            else:
+                rec["d_x"] = "CSR(D) holds no 16-bit index (a chunk spans 65,536 columns or more)"
+            out["configs"][cfg] = rec
         ddc.close()
     return out
 
@@ -645,6 +677,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     ap.add_argument("--interdig", action="store_true", help="plan mode: price with the interdigitation constraint")
+    ap.add_argument("--no-index16", dest="index16", action="store_false",
+                    help="build without the 16-bit column index (32-bit indices only)")
     ap.add_argument("--machine", action="store_true",
                     help="plan mode: fluence-rate bounds from gantry-speed, dose-rate and leaf-speed limits")
     args = ap.parse_args()

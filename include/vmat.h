@@ -98,6 +98,10 @@ typedef struct {
     int32_t tile_cfg;   /* SpMV tile configuration index, -1 = library default */
     int32_t autotune;   /* nonzero: time every tile configuration and keep the fastest */
     int32_t keep_coo;   /* nonzero: keep the COO copy after the build */
+    int32_t index16;    /* nonzero: also store 16-bit column indices (rows cut into 128-entry
+                           chunks, each with a 32-bit base column) for every CSR whose chunks all
+                           span fewer than 65,536 columns; the autotuner then also times the
+                           configurations that read them (2 bytes per nonzero instead of 4) */
 } vmat_build_opts;
 
 /* Master-problem (Eq. 6-10) options.  Stopping rules of Section 2.1:
@@ -136,6 +140,8 @@ typedef struct {
     int64_t bytes_D, bytes_Dt;       /* device bytes of each CSR (values, columns, row pointers) */
     double build_ms;                 /* device time of the last ddc_build */
     int32_t cfg_D, cfg_Dt;           /* SpMV configuration of each CSR (see vmat_spmv_config_count) */
+    int32_t index16_D, index16_Dt;   /* 1: that CSR holds the 16-bit column index */
+    int64_t bytes16_D, bytes16_Dt;   /* device bytes of the 16-bit index (offsets, bases, chunk pointers) */
 } vmat_ddc_info;
 
 /* Per-phase device times of cg_plan, named as the paper's Table 2 phases. */
@@ -334,7 +340,7 @@ typedef struct {
     int32_t graph;            /* 1: the run is one CUDA graph launch */
     int64_t graph_nodes;      /* nodes of that graph (0 without a graph) */
     int64_t device_bytes;     /* device memory the batch holds (plan state, tables) */
-    double autotune_ms[16];   /* D^T g time of each configuration tried (0 = not a candidate) */
+    double autotune_ms[32];   /* D^T g time of each configuration tried (0 = not a candidate) */
 } vmat_batch_info;
 
 /* Column generation (as cg_plan) for n_plans independent plans (1 .. 64)
@@ -378,7 +384,9 @@ const char *vmat_version(void);
 int64_t vmat_launch_count(void);
 
 /* Number of SpMV configurations (valid vmat_build_opts.tile_cfg values are
- * 0 .. count - 1). */
+ * 0 .. count - 1): 0-3 nonzero tiles, 4-8 a warp per row with 4-entry lane
+ * chunks, 9-11 a warp per row with consecutive lanes, 12-14 the same reading
+ * the 16-bit column index (only where vmat_build_opts.index16 built it). */
 int32_t vmat_spmv_config_count(void);
 
 #ifdef __cplusplus

@@ -35,7 +35,7 @@ class Voxels(ctypes.Structure):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("dtype", c_i32), ("build_D", c_i32), ("build_Dt", c_i32), ("tile_cfg", c_i32),
-                ("autotune", c_i32), ("keep_coo", c_i32)]
+                ("autotune", c_i32), ("keep_coo", c_i32), ("index16", c_i32)]
 
 
 class BBOpts(ctypes.Structure):
@@ -50,7 +50,8 @@ class BBReport(ctypes.Structure):
 class DdcInfo(ctypes.Structure):
     _fields_ = [("V", c_i32), ("J", c_i32), ("nnz", c_i64), ("n_active_vox", c_i32), ("dtype", c_i32),
                 ("built_D", c_i32), ("built_Dt", c_i32), ("tile_nnz_D", c_i32), ("tile_nnz_Dt", c_i32),
-                ("bytes_D", c_i64), ("bytes_Dt", c_i64), ("build_ms", c_f64), ("cfg_D", c_i32), ("cfg_Dt", c_i32)]
+                ("bytes_D", c_i64), ("bytes_Dt", c_i64), ("build_ms", c_f64), ("cfg_D", c_i32), ("cfg_Dt", c_i32),
+                ("index16_D", c_i32), ("index16_Dt", c_i32), ("bytes16_D", c_i64), ("bytes16_Dt", c_i64)]
 
 
 class PlanStats(ctypes.Structure):
@@ -66,7 +67,7 @@ class PlanDesc(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_plans", c_i32), ("max_apertures", c_i32), ("spmv_cfg", c_i32), ("graph", c_i32),
-                ("graph_nodes", c_i64), ("device_bytes", c_i64), ("autotune_ms", c_f64 * 16)]
+                ("graph_nodes", c_i64), ("device_bytes", c_i64), ("autotune_ms", c_f64 * 32)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/vmat.h

@@ -121,7 +121,7 @@ struct Batch {
     std::vector<size_t> smem_t;
     int32_t *d_ctl = nullptr, *d_targets = nullptr, *h_ctl = nullptr;
     int spmv_cfg = 4;
-    double autotune_ms[16] = {0};
+    double autotune_ms[32] = {0};
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -414,7 +414,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         VMAT_CUDA(cudaEventCreate(&e0));
         VMAT_CUDA(cudaEventCreate(&e1));
         float best = 1e30f;
-        for (int cfg = 0; cfg < spmv_n_configs() && cfg < 16; ++cfg) {  // warp-row families only
+        for (int cfg = 0; cfg < spmv_n_configs() && cfg < 32; ++cfg) {  // warp-row families only
             if (!spmv_batched_config(cfg)) continue;
             VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s)); // warm-up
             VMAT_CUDA(cudaEventRecord(e0, s));
@@ -538,8 +538,8 @@ vmat_status vmat_batch_run(vmat_batch hb, double *F_out, vmat_plan_stats *stats,
         st.t_total_ms = ms;
         st.pp1_spmv_launches = n_pp1;
         st.pp1_spmv_bytes = pp1;
-        st.other_spmv_bytes = (double)h.D.nnz * (vb + 4) + 8.0 * (h.D.n_rows + 1) + 4.0 * p.J + 4.0 * p.V +
-                              (fp8 ? 4.0 * p.J : 0.0);
+        st.other_spmv_bytes = csr_pass_bytes(h.D.cfg, vb, (double)h.D.nnz, h.D.n_rows + 1.0, (double)h.D.n_chunks) +
+                              4.0 * p.J + 4.0 * p.V + (fp8 ? 4.0 * p.J : 0.0);
         st.n_apertures = n_ap;
         st.bb_iters_total = c[CTL_BBITERS];
         st.stop_reason = stop;
@@ -584,7 +584,7 @@ vmat_status vmat_batch_info_get(vmat_batch hb, vmat_batch_info *info) {
     info->graph = b.exec ? 1 : 0;
     info->graph_nodes = b.graph_nodes;
     info->device_bytes = b.device_bytes;
-    for (int i = 0; i < 16; ++i) info->autotune_ms[i] = b.autotune_ms[i];
+    for (int i = 0; i < 32; ++i) info->autotune_ms[i] = b.autotune_ms[i];
     return VMAT_OK;
 }
 

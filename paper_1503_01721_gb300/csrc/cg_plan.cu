@@ -204,8 +204,15 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&cpo_dev, (size_t)K + 1));
     cp_offsets<<<std::max(1, (K + 256) / 256), 256, 0, s>>>(h.Dt.rowptr, K, bpc, cpo_dev);
     VMAT_LAUNCH_CHECK();
-    std::vector<int64_t> cpo(K + 1);
+    std::vector<int64_t> cpo(K + 1), cco(K + 1, 0); // nonzeros and 16-bit-index chunks before each CP
     VMAT_CUDA(cudaMemcpyAsync(cpo.data(), cpo_dev, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
+    const bool z_dt = spmv_config_index16(h.Dt.cfg);
+    if (z_dt) {
+        VMAT_CUDA(cudaStreamSynchronize(s)); // cpo_dev is reused
+        cp_offsets<<<std::max(1, (K + 256) / 256), 256, 0, s>>>(h.Dt.cptr, K, bpc, cpo_dev);
+        VMAT_LAUNCH_CHECK();
+        VMAT_CUDA(cudaMemcpyAsync(cco.data(), cpo_dev, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
+    }
     VMAT_CUDA(cudaStreamSynchronize(s));
     vmat_voxels vox_c = *vox;
     vox_c.struct_id = sid_c;
@@ -227,8 +234,8 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get((char **)&mp_ws, mp_workspace_bytes(n_cap)));
     int64_t spmv_launches = 0;
     const int vb = value_bytes(h.dtype);
-    const double bytes_D_full = (double)h.D.nnz * (vb + 4) + 8.0 * (h.D.n_rows + 1) + 4.0 * J + 4.0 * V +
-                                (h.dtype == VMAT_FP8E4M3 ? 4.0 * J : 0.0);
+    const double bytes_D_full = csr_pass_bytes(h.D.cfg, vb, (double)h.D.nnz, h.D.n_rows + 1.0, (double)h.D.n_chunks) +
+                                4.0 * J + 4.0 * V + (h.dtype == VMAT_FP8E4M3 ? 4.0 * J : 0.0);
     int32_t *hctl;
     VMAT_CUDA(cudaMallocHost(&hctl, CTL_N * sizeof(int32_t)));
     struct FreeCtl {
@@ -303,8 +310,9 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
             double b = 4.0 * V;
             for (int kk = 0; kk < K; ++kk)
                 if (!occ[kk])
-                    b += (double)(cpo[kk + 1] - cpo[kk]) * (vb + 4) + bpc * (8.0 + 4.0) +
-                         (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
+                    b += csr_pass_bytes(h.Dt.cfg, vb, (double)(cpo[kk + 1] - cpo[kk]), (double)bpc,
+                                        (double)(cco[kk + 1] - cco[kk])) +
+                         4.0 * bpc + (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
             pp1_bytes += b;
             if (t < n_ap) occ[cps_host[t]] = 1;
         }

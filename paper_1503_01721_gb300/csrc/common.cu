@@ -75,6 +75,9 @@ void Ddc::free_all() {
         f(m->tile_flag);
         f(m->tile_list);
         f(m->n_list);
+        f(m->col16);
+        f(m->cbase);
+        f(m->cptr);
         *m = CsrMat();
     }
     f(act_vox);
@@ -325,6 +328,12 @@ vmat_status ddc_info(vmat_ddc hd, vmat_ddc_info *out) {
     out->build_ms = h->build_ms;
     out->cfg_D = h->D.cfg;
     out->cfg_Dt = h->Dt.cfg;
+    out->index16_D = h->D.col16 ? 1 : 0;
+    out->index16_Dt = h->Dt.col16 ? 1 : 0;
+    for (const CsrMat *m : {&h->D, &h->Dt}) {
+        const int64_t b = m->col16 ? m->nnz * 2 + m->n_chunks * 4 + (int64_t)(m->n_rows + 1) * 8 : 0;
+        (m == &h->D ? out->bytes16_D : out->bytes16_Dt) = b;
+    }
     return VMAT_OK;
 }
 

@@ -299,7 +299,65 @@ vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows,
     return VMAT_OK;
 }
 
+// Chunks of ZCHUNK entries per row (the last one ragged).
+__global__ void chunk_counts(const int64_t *__restrict__ rowptr, int32_t n_rows, int32_t *cnt) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += gridDim.x * blockDim.x)
+        cnt[r] = (int32_t)((rowptr[r + 1] - rowptr[r] + ZCHUNK - 1) / ZCHUNK);
+}
+
+// A warp per row: each chunk's base is its first column (rows are sorted), each
+// entry stores its offset from that base; bad is set when an offset needs more
+// than 16 bits.
+__global__ void fill_index16(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                             const int64_t *__restrict__ cptr, int32_t n_rows, int32_t *cbase, uint16_t *col16,
+                             int32_t *bad) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += (gridDim.x * blockDim.x) >> 5) {
+        const int64_t s = rowptr[r], e = rowptr[r + 1], c0 = cptr[r];
+        bool ok = true;
+        for (int64_t i = s + lane; i < e; i += 32) {
+            const int64_t t = (i - s) / ZCHUNK;
+            const int32_t base = col[s + t * ZCHUNK];
+            const int32_t off = col[i] - base;
+            ok = ok && off >= 0 && off <= 65535;
+            col16[i] = (uint16_t)off;
+            if (i - s == t * ZCHUNK) cbase[c0 + t] = base;
+        }
+        if (__any_sync(0xffffffffu, !ok) && lane == 0) *bad = 1;
+    }
+}
+
 } // namespace
+
+vmat_status csr_build_index16(CsrMat &m, int n_sm, cudaStream_t s) {
+    if (m.n_rows <= 0 || m.nnz <= 0) return VMAT_OK;
+    DevBuf b_cnt, b_cptr, b_base, b_c16, b_bad;
+    VMAT_CUDA(b_cnt.alloc((size_t)m.n_rows * 4));
+    VMAT_CUDA(b_cptr.alloc((size_t)(m.n_rows + 1) * 8));
+    VMAT_CUDA(b_bad.alloc(4));
+    chunk_counts<<<grid_for(m.n_rows, n_sm), BUILD_THREADS, 0, s>>>(m.rowptr, m.n_rows, (int32_t *)b_cnt.p);
+    VMAT_LAUNCH_CHECK();
+    VMAT_TRY(scan_counts((int32_t *)b_cnt.p, (int64_t *)b_cptr.p, m.n_rows, s));
+    int64_t n_chunks = 0;
+    VMAT_CUDA(cudaMemcpyAsync(&n_chunks, (int64_t *)b_cptr.p + m.n_rows, 8, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaMemsetAsync(b_bad.p, 0, 4, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    VMAT_CUDA(b_base.alloc((size_t)std::max<int64_t>(n_chunks, 1) * 4));
+    VMAT_CUDA(b_c16.alloc((size_t)m.nnz * 2));
+    fill_index16<<<grid_for((int64_t)m.n_rows * 32, n_sm), BUILD_THREADS, 0, s>>>(
+        m.rowptr, m.col, (const int64_t *)b_cptr.p, m.n_rows, (int32_t *)b_base.p, (uint16_t *)b_c16.p,
+        (int32_t *)b_bad.p);
+    VMAT_LAUNCH_CHECK();
+    int32_t bad = 0;
+    VMAT_CUDA(cudaMemcpyAsync(&bad, b_bad.p, 4, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    if (bad) return VMAT_OK; // some chunk spans 65536 columns or more: this matrix keeps 32-bit indices only
+    m.cptr = (int64_t *)b_cptr.release();
+    m.cbase = (int32_t *)b_base.release();
+    m.col16 = (uint16_t *)b_c16.release();
+    m.n_chunks = n_chunks;
+    return VMAT_OK;
+}
 
 } // namespace vmat
 
@@ -309,7 +367,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     clear_error();
     if (!hd) return set_error(VMAT_EINVAL, "ddc_build: handle is NULL");
     Ddc *h = as_ddc(hd);
-    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0};
+    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0};
     if (opts_in) opts = *opts_in;
     if (opts.dtype != VMAT_F32 && opts.dtype != VMAT_BF16 && opts.dtype != VMAT_FP8E4M3)
         return set_error(VMAT_EINVAL, "ddc_build: unknown dtype %d", (int)opts.dtype);
@@ -465,6 +523,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         m.col = (int32_t *)b_col_t.release();
         m.row_ids = nullptr;
         m.max_row = max_row_t;
+        if (opts.index16) VMAT_TRY(csr_build_index16(m, n_sm, s));
         VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
         h->built_Dt = true;
     }
@@ -482,6 +541,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         h->n_active = n_active;
         m.row_ids = h->act_vox;
         m.max_row = max_row_d;
+        if (opts.index16) VMAT_TRY(csr_build_index16(m, n_sm, s));
         VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
         h->built_D = true;
     }

@@ -71,6 +71,8 @@ struct Scratch {
 // ---------------------------------------------------------------------------
 constexpr int64_t NNZ_PAD = 8192; // value/column arrays padded to a multiple of this
 
+constexpr int ZCHUNK = 128; // entries per chunk of the 16-bit column index
+
 struct CsrMat {
     int32_t n_rows = 0, n_cols = 0;
     int32_t max_row = 0; // longest row
@@ -79,6 +81,13 @@ struct CsrMat {
     int32_t *col = nullptr;      // [nnz_pad], padding 0
     void *val = nullptr;         // [nnz_pad] of the stored type, padding 0
     const int32_t *row_ids = nullptr; // output index of each row (CSR(D): compact -> voxel), or null
+    // 16-bit column indices, when built: each row is cut into ZCHUNK-entry chunks (from the
+    // row's first entry); a chunk stores its first (smallest) column in cbase and every
+    // entry its offset from it in col16.  Built only when every chunk spans < 65536 columns.
+    uint16_t *col16 = nullptr;   // [nnz_pad], padding 0
+    int32_t *cbase = nullptr;    // [n_chunks]
+    int64_t *cptr = nullptr;     // [n_rows + 1] first chunk of each row
+    int64_t n_chunks = 0;
     // tiles
     int cfg = 0;                 // tile configuration index
     int32_t tile = 0;            // nonzeros per tile
@@ -129,11 +138,25 @@ int value_bytes(vmat_dtype t);
 vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
                      const uint8_t *cp_active, int32_t bpc, cudaStream_t s, const int32_t *skip = nullptr);
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s);
+// Does configuration cfg read the 16-bit column index (and so need m.col16)?
+bool spmv_config_index16(int cfg);
+// Builds m.col16 / cbase / cptr when every chunk fits 16 bits (else leaves them null).
+vmat_status csr_build_index16(CsrMat &m, int n_sm, cudaStream_t s);
 int spmv_n_configs();
 int spmv_default_config();
 int32_t spmv_config_tile(int cfg);
 
 vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compact, cudaStream_t s);
+
+// Algorithmic bytes of the matrix part of one SpMV pass over `rows` rows holding
+// `nnz` nonzeros and `chunks` 16-bit-index chunks, in the format configuration
+// cfg reads: each value (vb bytes) and column index (4, or 2 plus a 4-byte base
+// per chunk and an 8-byte chunk pointer per row) once, an 8-byte row pointer
+// per row.  Dense inputs, outputs and scales are the caller's.
+inline double csr_pass_bytes(int cfg, int vb, double nnz, double rows, double chunks) {
+    if (spmv_config_index16(cfg)) return nnz * (vb + 2) + 4.0 * chunks + 16.0 * rows;
+    return nnz * (vb + 4) + 8.0 * rows;
+}
 
 // ---------------------------------------------------------------------------
 // Batched phases: one launch covers every plan of a batch.  Work item g of a

@@ -393,6 +393,9 @@ struct RowParams {
     int32_t bpc;
     int32_t n_rows;
     const int32_t *skip; // when non-null and set, the kernel does nothing
+    const uint16_t *col16; // 16-bit column index (configurations that read it)
+    const int32_t *cbase;
+    const int64_t *cptr;
 };
 
 // Sum of row r (all lanes of a warp; the result is valid in every lane): 4-entry
@@ -474,6 +477,58 @@ __device__ __forceinline__ float warp_row_sum_c(const int64_t *__restrict__ rowp
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
     return sum;
+}
+
+// The consecutive-lane row sum reading the 16-bit column index: entry i of chunk
+// t (i - s in [t ZCHUNK, (t + 1) ZCHUNK)) has column cbase[cptr[r] + t] + col16[i].
+// The chunk base is the same for all lanes of a load (one broadcast load, one per
+// iteration); the products and their order are those of warp_row_sum_c, so the
+// sums are identical.
+template <int UNROLL, typename VT>
+__device__ __forceinline__ float warp_row_sum_z(const int64_t *__restrict__ rowptr, const int64_t *__restrict__ cptr,
+                                                const int32_t *__restrict__ cbase, const uint16_t *__restrict__ col16,
+                                                const void *__restrict__ val, const float *__restrict__ x, int64_t r,
+                                                int lane, uint64_t pol) {
+    static_assert((32 * UNROLL) % ZCHUNK == 0, "an iteration covers whole chunks");
+    const int64_t s = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+    const int32_t *cb = cbase + __ldg(cptr + r);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t b = s; b < e; b += 32 * UNROLL, cb += 32 * UNROLL / ZCHUNK) {
+        float v[UNROLL];
+        int32_t c[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t i = b + 32 * u + lane;
+            if (i < e) {
+                v[u] = StreamVal1<VT>::load(val, i, pol);
+                c[u] = __ldg(cb + (32 * u) / ZCHUNK) + (int32_t)ldg_stream_b16(col16 + i, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (b + 32 * u + lane < e) acc[u & 3] = fmaf(v[u], __ldg(x + c[u]), acc[u & 3]);
+    }
+    float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    return sum;
+}
+
+template <int THREADS, int UNROLL, typename VT>
+__global__ void __launch_bounds__(THREADS) spmv_warp_row_z_kernel(RowParams p) {
+    if (p.skip && *p.skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    const uint64_t pol = l2_evict_first_policy();
+    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
+        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+        float sum = warp_row_sum_z<UNROLL, VT>(p.rowptr, p.cptr, p.cbase, p.col16, p.val, p.x, r, lane, pol);
+        if (lane == 0) {
+            if (p.row_scale) sum *= p.row_scale[r];
+            p.y[p.row_ids ? p.row_ids[r] : r] = sum;
+        }
+    }
 }
 
 template <int THREADS, int UNROLL, typename VT>
@@ -618,13 +673,15 @@ __global__ void scale_vector(const float *x, const float *s, float *out, int32_t
 // Configurations and dispatch
 // ---------------------------------------------------------------------------
 struct Cfg {
-    int family; // 0 = tile-segmented, 1 = warp per row (4-entry lane chunks), 2 = warp per row (consecutive lanes)
+    int family; // 0 = tile-segmented, 1 = warp per row (4-entry lane chunks), 2 = warp per row (consecutive
+                // lanes), 3 = as 2 reading the 16-bit column index
     int threads, e, stages; // tile: E entries per thread, STAGES bulk-copy stages; warp-row: e = unroll
 };
 static const Cfg kCfgs[] = {{0, 256, 16, 2}, {0, 256, 8, 3}, {0, 512, 8, 2}, {0, 128, 16, 3},
                             {1, 256, 2, 0},  {1, 256, 1, 0}, {1, 512, 4, 0}, {1, 256, 4, 0},
-                            {1, 256, 8, 0}, {2, 256, 4, 0}, {2, 256, 8, 0}, {2, 512, 4, 0}};
-constexpr int N_CFG = 12;
+                            {1, 256, 8, 0}, {2, 256, 4, 0}, {2, 256, 8, 0}, {2, 512, 4, 0},
+                            {3, 256, 4, 0}, {3, 256, 8, 0}, {3, 512, 4, 0}};
+constexpr int N_CFG = 15;
 
 using TileFn = void (*)(SpmvParams);
 using RowFn = void (*)(RowParams);
@@ -648,6 +705,9 @@ template <typename VT> RowFn row_kernel_for(int cfg) {
     case 9: return spmv_warp_row_c_kernel<256, 4, VT>;
     case 10: return spmv_warp_row_c_kernel<256, 8, VT>;
     case 11: return spmv_warp_row_c_kernel<512, 4, VT>;
+    case 12: return spmv_warp_row_z_kernel<256, 4, VT>;
+    case 13: return spmv_warp_row_z_kernel<256, 8, VT>;
+    case 14: return spmv_warp_row_z_kernel<512, 4, VT>;
     default: return spmv_warp_row_kernel<512, 4, VT>;
     }
 }
@@ -707,10 +767,14 @@ static vmat_status launch_info(vmat_dtype dt, int cfg, Launch *out) {
 }
 
 int spmv_n_configs() { return N_CFG; }
+bool spmv_config_index16(int cfg) { return cfg >= 0 && cfg < N_CFG && kCfgs[cfg].family == 3; }
 int spmv_default_config() { return 4; }
 int32_t spmv_config_tile(int cfg) { return kCfgs[cfg].family == 0 ? kCfgs[cfg].threads * kCfgs[cfg].e : 0; }
 
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s) {
+    if (kCfgs[cfg].family == 3 && !m.col16 && m.nnz > 0)
+        return set_error(VMAT_EUNSUPPORTED, "spmv: configuration %d reads the 16-bit column index, which this matrix "
+                                            "does not hold (build with index16, chunks spanning < 65536 columns)", cfg);
     if (kCfgs[cfg].family != 0) { // warp per row: no tile structure needed
         m.cfg = cfg;
         m.tile = 0;
@@ -764,6 +828,11 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
         p.bpc = bpc;
         p.n_rows = m.n_rows;
         p.skip = skip;
+        p.col16 = m.col16;
+        p.cbase = m.cbase;
+        p.cptr = m.cptr;
+        if (kCfgs[m.cfg].family == 3 && !m.col16 && m.n_rows > 0)
+            return set_error(VMAT_ESTATE, "spmv: configuration %d needs the 16-bit column index", m.cfg);
         const int64_t warps = std::max<int64_t>(1, m.n_rows);
         const int64_t want = (warps * 32 + L.threads - 1) / L.threads;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * L.blocks_per_sm));
@@ -826,7 +895,9 @@ template <typename VT> static RowBatchFn batched_kernel_for(int cfg) {
     }
 }
 
-bool spmv_batched_config(int cfg) { return cfg >= 0 && cfg < N_CFG && kCfgs[cfg].family != 0; }
+bool spmv_batched_config(int cfg) {
+    return cfg >= 0 && cfg < N_CFG && (kCfgs[cfg].family == 1 || kCfgs[cfg].family == 2);
+}
 
 vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
                               int64_t total_rows, cudaStream_t s) {
@@ -883,6 +954,7 @@ vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
         int best = m->cfg;
         float best_ms = 1e30f;
         for (int cfg = 0; cfg < N_CFG; ++cfg) {
+            if (kCfgs[cfg].family == 3 && !m->col16) continue;
             vmat_status st = spmv_prepare_tiles(*m, cfg, s);
             if (st != VMAT_OK) break;
             float ms_total = 0.f;

@@ -30,6 +30,15 @@ def spmv_bytes(nnz: int, n_rows: int, n_in: int, n_out: int, dtype: str = "f32",
             + 4 * n_in + 4 * n_out + 4 * n_scales)
 
 
+def spmv_bytes_index16(nnz: int, n_chunks: int, n_rows: int, n_in: int, n_out: int, dtype: str = "f32",
+                       n_scales: int = 0) -> int:
+    """Algorithmic bytes of y = M x reading the 16-bit column index: 2 bytes per
+    nonzero, a 4-byte base per 128-entry chunk and an 8-byte chunk pointer per row
+    replace the 4-byte index."""
+    return (nnz * (VAL_BYTES[dtype] + 2) + 4 * n_chunks + 2 * PTR_BYTES * (n_rows + 1)
+            + 4 * n_in + 4 * n_out + 4 * n_scales)
+
+
 def measured_peaks(path: str | None = None) -> dict:
     """Peaks measured on this GPU model (copy bandwidth, bf16 GEMM), if recorded."""
     if path is None:

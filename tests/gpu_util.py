@@ -11,7 +11,10 @@ U32 = 2.0 ** -24  # float32 unit roundoff
 # of roundoff bound both, for every row length.
 SPMV_C = 64
 # SpMV configurations the library offers (tile_cfg 0 .. N_SPMV_CFG - 1)
-N_SPMV_CFG = 12
+N_SPMV_CFG = 15
+# configurations that read the 16-bit column index, and their consecutive-lane twins (same products,
+# same order)
+INDEX16_TWIN = {12: 9, 13: 10, 14: 11}
 
 
 def require_cuda():
@@ -32,12 +35,15 @@ def spmv_bound(abs_terms_sum, row_len=0):
     return (SPMV_C + np.asarray(row_len, np.float64) / 64.0) * U32 * abs_terms_sum + 1e-37
 
 
-def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None):
+def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None, index16=None):
+    """index16 None: build the 16-bit column index when tile_cfg reads it."""
     from paper_1503_01721_gb300 import api
     if hasattr(case_or_coo, "vox"):
         c = case_or_coo
         V, J, vox, blt, val = c.V, c.J, c.vox, c.blt, c.val
     else:
         vox, blt, val = case_or_coo
+    if index16 is None:
+        index16 = tile_cfg in INDEX16_TWIN
     return api.Ddc(V, J, dev(vox, torch.int32), dev(blt, torch.int32), dev(val, torch.float32), dtype=dtype,
-                   tile_cfg=tile_cfg)
+                   tile_cfg=tile_cfg, index16=index16)

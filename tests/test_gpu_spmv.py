@@ -15,7 +15,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import N_SPMV_CFG, dev, host, make_ddc, require_cuda, spmv_bound
+from gpu_util import INDEX16_TWIN, N_SPMV_CFG, dev, host, make_ddc, require_cuda, spmv_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +68,67 @@ def test_every_tile_config(cfg):
     check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg)
     c = synth.make_case("cfg1", seed=0)
     check_products(c.V, c.J, c.vox, c.blt, c.val, tile_cfg=cfg, seed=5)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_index16_configs_match_their_32bit_twins_bit_for_bit(dtype):
+    """The 16-bit column index changes the bytes read, not the arithmetic: each
+    configuration that reads it gives the same bits as the consecutive-lane
+    configuration with the same launch shape."""
+    cases = [synth.make_case("ragged", seed=1), synth.make_case("cfg1", seed=0)]
+    for c in cases:
+        g = synth.random_vector(c.V, 11)
+        x = synth.random_vector(c.J, 12, 0.0, 1.0)
+        for z, twin in INDEX16_TWIN.items():
+            dz = make_ddc(c, dtype, z)
+            info = dz.info()
+            assert info["index16_Dt"] == 1 and info["index16_D"] == 1 and info["cfg_Dt"] == z
+            assert info["bytes16_Dt"] == 2 * c.nnz + 4 * _chunks(c.blt, c.J) + 8 * (c.J + 1)
+            dc = make_ddc(c, dtype, twin)
+            a = run_products(dz, c.V, c.J, g, x)
+            b = run_products(dc, c.V, c.J, g, x)
+            assert all(np.array_equal(u.view(np.uint32), v.view(np.uint32)) for u, v in zip(a, b))
+
+
+def _chunks(rows, n_rows):
+    return int(np.sum((np.bincount(rows, minlength=n_rows) + 127) // 128))
+
+
+def test_index16_chunk_span_limit():
+    """A chunk whose columns span 65,535 fits 16 bits; 65,537 does not, and then the
+    matrix keeps 32-bit indices only (the 16-bit configurations are refused)."""
+    from paper_1503_01721_gb300 import _lib
+    V = 140000
+    rows = [np.array([0, 65535]),                                         # span 65,535: fits
+            np.concatenate([np.arange(128), 100000 + np.arange(172)]),    # 3 chunks, a jump between chunks
+            np.arange(7, 7 + 128 * 40, 40)]                               # 128 entries spanning 5,080
+    def coo(rs):
+        vox = np.concatenate(rs).astype(np.int32)
+        blt = np.concatenate([np.full(len(r), j) for j, r in enumerate(rs)]).astype(np.int32)
+        val = np.random.default_rng(1).uniform(0.1, 1.0, len(vox)).astype(np.float32)
+        return vox, blt, val
+    vox, blt, val = coo(rows)
+    ddc, _, _ = check_products(V, len(rows), vox, blt, val, tile_cfg=12)
+    assert ddc.info()["index16_Dt"] == 1
+    bad = rows + [np.array([5, 65542])]                                  # span 65,537: does not fit
+    vox, blt, val = coo(bad)
+    with pytest.raises(_lib.VmatError) as e:
+        make_ddc((vox, blt, val), "f32", 12, V, len(bad))
+    assert e.value.status == _lib.VMAT_EUNSUPPORTED
+    ddc = make_ddc((vox, blt, val), "f32", -1, V, len(bad), index16=True)
+    info = ddc.info()
+    assert info["index16_Dt"] == 0 and info["bytes16_Dt"] == 0 and info["index16_D"] == 1
+    # the autotuner times the 16-bit configurations only where the index exists
+    from paper_1503_01721_gb300 import api
+    ddc = api.Ddc(V, len(bad), dev(vox, torch.int32), dev(blt, torch.int32), dev(val, torch.float32),
+                  autotune=True, index16=True)
+    assert ddc.info()["cfg_Dt"] not in INDEX16_TWIN
+    g = synth.random_vector(V, 1)
+    pi, _ = run_products(ddc, V, len(bad), g, np.ones(len(bad), np.float32))
+    D = oracle.ddc_matrix(V, len(bad), vox, blt, val)
+    pi_ref = oracle.beamlet_price(D, g)
+    assert np.all(np.abs(pi - pi_ref) <= spmv_bound(abs(D).T @ np.abs(g.astype(np.float64)),
+                                                     np.bincount(blt, minlength=len(bad))))
 
 
 def test_shuffled_coo_gives_identical_bits():
