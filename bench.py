@@ -55,7 +55,9 @@ INDEX16_CFGS = (12, 13, 14)
 # (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
                  ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
-                 ("bf16", 5): 1.0083, ("fp8", 5): 1.0082}
+                 ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
+                 # 16-bit index, on the 45-CP case (profiles/spmv_warp_row_z_kernel_cfg2q_f32.md)
+                 ("f32", 12): 1.0044}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
@@ -677,8 +679,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
     ap.add_argument("--interdig", action="store_true", help="plan mode: price with the interdigitation constraint")
-    ap.add_argument("--no-index16", dest="index16", action="store_false",
-                    help="build without the 16-bit column index (32-bit indices only)")
+    ap.add_argument("--index16", action="store_true",
+                    help="also build the 16-bit column index (the autotuner then times configurations 12-14)")
     ap.add_argument("--machine", action="store_true",
                     help="plan mode: fluence-rate bounds from gantry-speed, dose-rate and leaf-speed limits")
     args = ap.parse_args()
