@@ -4,25 +4,27 @@
 //
 // The paper runs four steps per iteration on one GPU (aperture gradient, step
 // length with cuBLAS dot products, subspace update, dose update).  Here one
-// kernel does a whole iteration.  DA is kept in a warp-tile layout: blocks of
-// 32 voxels, each block a 128-byte head holding the 32 voxels' structure
-// labels, then the apertures in groups of four with the four values of a voxel
-// side by side,
+// persistent cooperative kernel runs a whole solve.  DA is kept in a warp-tile
+// layout: blocks of 32 voxels, each block a 128-byte head holding the 32 voxels'
+// structure labels, then the apertures in groups of four with the four values
+// of a voxel side by side,
 //     DA(i, k) = DA[(i / 32) * wstride + 32 + (k / 4) * 128 + (i % 32) * 4 + k % 4],
 // so the labels and the first n columns of a block are one contiguous run of
 // 128 + 512 ceil(n / 4) bytes.  Every warp streams its own blocks into shared
 // memory with one bulk copy each (several in flight on the warp's own mbarrier
-// ring; no CTA-wide barrier in the loop); each lane owns a voxel, reads its
-// four-aperture groups with 128-bit shared loads, forms z = DA y with four
-// independent chains, the objective term and g = -grad F, and adds DA_ik g_i
-// to its register-resident shares of G = grad_y F = -DA^T g.  DA is read from
-// HBM once per iteration.  Objective terms w d^2 are formed in FP32 and summed
-// per lane with compensation (Kahan), then in FP64 across lanes and CTAs: the
+// ring, continuing across iterations; no CTA-wide barrier in the loop); each
+// lane owns a voxel, reads its four-aperture groups with 128-bit shared loads,
+// forms z = DA y with four independent chains, the objective term and
+// g = -grad F, and adds DA_ik g_i to its register-resident shares of
+// G = grad_y F = -DA^T g.  DA is read from HBM (or L2, when it fits there) once
+// per iteration.  Objective terms w d^2 are formed in FP32 and summed per lane
+// with compensation (Kahan), then as float pairs across lanes and CTAs: the
 // voxel loop runs no FP64 instruction (FP64 issues at a small fraction of the
-// FP32 rate on this GPU).  The last CTA to finish (a ticket counter) reduces
-// the partials in a fixed order (FP64) and takes the step: the Eq. 9-10 freeze,
-// the stopping tests, the BB step length and the projected update.  The first
-// iteration's Cauchy step needs DA G and takes two more kernels.
+// FP32 rate on this GPU).  After a grid barrier one warp per column reduces the
+// CTA partials in a fixed order; after a second barrier every CTA takes the
+// same step in shared memory: the Eq. 9-10 freeze, the stopping tests, the BB
+// step length (FP64) and the projected update.  The first iteration's Cauchy
+// step needs DA G and one more pass.
 //
 // Readings (where the paper is silent): G is the gradient of F, so both BB
 // step lengths are positive and Eq. 9-10 freeze at lo when G > 0 and at hi when
