@@ -95,13 +95,16 @@ typedef struct {
     vmat_dtype dtype;   /* stored value type; FP8 uses per-beamlet power-of-two scales */
     int32_t build_D;    /* nonzero: build CSR(D), voxel rows (dose_forward, aperture_dose) */
     int32_t build_Dt;   /* nonzero: build CSR(D^T), beamlet rows (beamlet_price) */
-    int32_t tile_cfg;   /* SpMV tile configuration index, -1 = library default */
+    int32_t tile_cfg;   /* SpMV configuration index of CSR(D) (and of CSR(D^T) when tile_cfg_Dt < 0),
+                           -1 = library default */
     int32_t autotune;   /* nonzero: time every tile configuration and keep the fastest */
     int32_t keep_coo;   /* nonzero: keep the COO copy after the build */
     int32_t index16;    /* nonzero: also store 16-bit column indices (rows cut into 128-entry
                            chunks, each with a 32-bit base column) for every CSR whose chunks all
                            span fewer than 65,536 columns; the autotuner then also times the
                            configurations that read them (2 bytes per nonzero instead of 4) */
+    int32_t tile_cfg_Dt; /* SpMV configuration index of CSR(D^T), -1 = as tile_cfg (a pair found by
+                            the autotuner once, see vmat_ddc_info, can be reused without tuning again) */
 } vmat_build_opts;
 
 /* Master-problem (Eq. 6-10) options.  Stopping rules of Section 2.1:

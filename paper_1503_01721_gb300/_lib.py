@@ -35,7 +35,7 @@ class Voxels(ctypes.Structure):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("dtype", c_i32), ("build_D", c_i32), ("build_Dt", c_i32), ("tile_cfg", c_i32),
-                ("autotune", c_i32), ("keep_coo", c_i32), ("index16", c_i32)]
+                ("autotune", c_i32), ("keep_coo", c_i32), ("index16", c_i32), ("tile_cfg_Dt", c_i32)]
 
 
 class BBOpts(ctypes.Structure):

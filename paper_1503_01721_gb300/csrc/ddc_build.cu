@@ -367,12 +367,13 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     clear_error();
     if (!hd) return set_error(VMAT_EINVAL, "ddc_build: handle is NULL");
     Ddc *h = as_ddc(hd);
-    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0};
+    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0, -1};
     if (opts_in) opts = *opts_in;
     if (opts.dtype != VMAT_F32 && opts.dtype != VMAT_BF16 && opts.dtype != VMAT_FP8E4M3)
         return set_error(VMAT_EINVAL, "ddc_build: unknown dtype %d", (int)opts.dtype);
     if (!opts.build_D && !opts.build_Dt) return set_error(VMAT_EINVAL, "ddc_build: nothing to build");
-    if (opts.tile_cfg >= spmv_n_configs()) return set_error(VMAT_EINVAL, "ddc_build: tile_cfg out of range");
+    if (opts.tile_cfg >= spmv_n_configs() || opts.tile_cfg_Dt >= spmv_n_configs())
+        return set_error(VMAT_EINVAL, "ddc_build: tile_cfg / tile_cfg_Dt out of range");
     if (!h->coo_vox) return set_error(VMAT_ESTATE, "ddc_build: the COO copy was released by an earlier build");
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
@@ -512,6 +513,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     };
 
     int cfg = opts.tile_cfg >= 0 ? opts.tile_cfg : spmv_default_config();
+    const int cfg_dt = opts.tile_cfg_Dt >= 0 ? opts.tile_cfg_Dt : cfg;
     if (opts.build_Dt) {
         CsrMat &m = h->Dt;
         m.n_rows = J;
@@ -524,7 +526,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         m.row_ids = nullptr;
         m.max_row = max_row_t;
         if (opts.index16) VMAT_TRY(csr_build_index16(m, n_sm, s));
-        VMAT_TRY(spmv_prepare_tiles(m, cfg, s));
+        VMAT_TRY(spmv_prepare_tiles(m, cfg_dt, s));
         h->built_Dt = true;
     }
     if (opts.build_D) {
