@@ -46,6 +46,20 @@ __global__ void coo_check_hist(const int32_t *__restrict__ vox, const int32_t *_
     }
 }
 
+// Is the COO in column order (beamlets nondecreasing, voxels strictly increasing
+// within a beamlet, the order a dose engine writes per-beamlet columns in)?  Sets
+// *unordered otherwise.
+__global__ void coo_csc_check(const int32_t *__restrict__ vox, const int32_t *__restrict__ blt, int64_t nnz,
+                              int32_t *unordered) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e + 1 < nnz; e += stride) {
+        const int32_t b0 = blt[e], b1 = blt[e + 1];
+        bad = bad || b1 < b0 || (b1 == b0 && vox[e + 1] <= vox[e]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(unordered, 1);
+}
+
 __global__ void flag_nonzero(const int32_t *cnt, int32_t n, int32_t *flag) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flag[i] = cnt[i] > 0 ? 1 : 0;
@@ -252,6 +266,19 @@ int grid_for(int64_t n, int n_sm) {
 int64_t round_pad(int64_t nnz) { return ((std::max<int64_t>(nnz, 1) + NNZ_PAD - 1) / NNZ_PAD) * NNZ_PAD; }
 
 // Sort each row of a CSR by column, check duplicates.
+vmat_status longest_row(const int32_t *cnt, int32_t n_rows, int n_sm, cudaStream_t s, int32_t *max_row) {
+    *max_row = 0;
+    if (n_rows == 0) return VMAT_OK;
+    DevBuf bmax;
+    VMAT_CUDA(bmax.alloc(sizeof(int32_t)));
+    VMAT_CUDA(cudaMemsetAsync(bmax.p, 0, sizeof(int32_t), s));
+    max_count<<<grid_for(n_rows, n_sm), BUILD_THREADS, 0, s>>>(cnt, n_rows, (int32_t *)bmax.p);
+    VMAT_LAUNCH_CHECK();
+    VMAT_CUDA(cudaMemcpyAsync(max_row, bmax.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    return VMAT_OK;
+}
+
 vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows, int32_t *col, float *val,
                       int32_t *bad, int n_sm, cudaStream_t s, int32_t *max_row) {
     *max_row = 0;
@@ -334,7 +361,7 @@ vmat_status csr_build_index16(CsrMat &m, int n_sm, cudaStream_t s) {
     DevBuf b_cnt, b_cptr, b_base, b_c16, b_bad;
     VMAT_CUDA(b_cnt.alloc((size_t)m.n_rows * 4));
     VMAT_CUDA(b_cptr.alloc((size_t)(m.n_rows + 1) * 8));
-    VMAT_CUDA(b_bad.alloc(4));
+    VMAT_CUDA(b_bad.alloc(8)); // [0]: invalid or duplicate entries, [1]: not in column order
     chunk_counts<<<grid_for(m.n_rows, n_sm), BUILD_THREADS, 0, s>>>(m.rowptr, m.n_rows, (int32_t *)b_cnt.p);
     VMAT_LAUNCH_CHECK();
     VMAT_TRY(scan_counts((int32_t *)b_cnt.p, (int64_t *)b_cptr.p, m.n_rows, s));
@@ -404,23 +431,27 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     DevBuf b_rp_t, b_col_t, b_val_t, b_rp_d, b_col_d, b_val_d, b_act, b_v2a, b_scale;
     VMAT_CUDA(b_cnt_vox.alloc((size_t)V * 4));
     VMAT_CUDA(b_cnt_blt.alloc((size_t)J * 4));
-    VMAT_CUDA(b_bad.alloc(4));
+    VMAT_CUDA(b_bad.alloc(8)); // [0]: invalid or duplicate entries, [1]: not in column order
     const bool fp8 = opts.dtype == VMAT_FP8E4M3;
     if (fp8) VMAT_CUDA(b_colmax.alloc((size_t)J * 4));
     int32_t *cnt_vox = (int32_t *)b_cnt_vox.p, *cnt_blt = (int32_t *)b_cnt_blt.p, *bad = (int32_t *)b_bad.p;
     VMAT_CUDA(cudaMemsetAsync(cnt_vox, 0, (size_t)V * 4, s));
     VMAT_CUDA(cudaMemsetAsync(cnt_blt, 0, (size_t)J * 4, s));
-    VMAT_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+    VMAT_CUDA(cudaMemsetAsync(bad, 0, 8, s));
     if (fp8) VMAT_CUDA(cudaMemsetAsync(b_colmax.p, 0, (size_t)J * 4, s));
     if (nnz > 0) {
         coo_check_hist<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(h->coo_vox, h->coo_blt, h->coo_val, nnz, V, J,
                                                                       cnt_vox, cnt_blt, (unsigned *)b_colmax.p, bad);
         VMAT_LAUNCH_CHECK();
+        coo_csc_check<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(h->coo_vox, h->coo_blt, nnz, bad + 1);
+        VMAT_LAUNCH_CHECK();
     }
-    int32_t hbad = 0;
-    VMAT_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+    int32_t hbad[2] = {0, 0};
+    VMAT_CUDA(cudaMemcpyAsync(hbad, bad, 8, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
-    if (hbad) return set_error(VMAT_EINVAL, "ddc_build: COO entry with voxel/beamlet index out of range or a non-finite value");
+    if (hbad[0]) return set_error(VMAT_EINVAL, "ddc_build: COO entry with voxel/beamlet index out of range or a non-finite value");
+    // column-ordered input: CSR(D^T) is the COO's voxel and value arrays as they are
+    const bool csc = nnz > 0 && hbad[1] == 0;
 
     const int64_t pad = round_pad(nnz);
     const int vb = value_bytes(opts.dtype);
@@ -431,10 +462,16 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         VMAT_TRY(scan_counts(cnt_blt, (int64_t *)b_rp_t.p, J, s));
         VMAT_CUDA(b_col_t.alloc((size_t)pad * 4));
         VMAT_CUDA(b_val_t.alloc((size_t)pad * 4));
-        VMAT_CUDA(cudaMemsetAsync(b_col_t.p, 0, (size_t)pad * 4, s));
-        VMAT_CUDA(cudaMemsetAsync(b_val_t.p, 0, (size_t)pad * 4, s));
-        VMAT_CUDA(b_cur_t.alloc((size_t)J * 4));
-        VMAT_CUDA(cudaMemsetAsync(b_cur_t.p, 0, (size_t)J * 4, s));
+        // every entry is written below; only the padding needs zeros
+        VMAT_CUDA(cudaMemsetAsync((int32_t *)b_col_t.p + nnz, 0, (size_t)(pad - nnz) * 4, s));
+        VMAT_CUDA(cudaMemsetAsync((float *)b_val_t.p + nnz, 0, (size_t)(pad - nnz) * 4, s));
+        if (csc) {
+            VMAT_CUDA(cudaMemcpyAsync(b_col_t.p, h->coo_vox, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+            VMAT_CUDA(cudaMemcpyAsync(b_val_t.p, h->coo_val, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+        } else {
+            VMAT_CUDA(b_cur_t.alloc((size_t)J * 4));
+            VMAT_CUDA(cudaMemsetAsync(b_cur_t.p, 0, (size_t)J * 4, s));
+        }
     }
     // ---- CSR(D): rows = voxels with at least one entry
     int32_t n_active = 0;
@@ -459,28 +496,31 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         VMAT_TRY(scan_counts((int32_t *)b_cnt_act.p, (int64_t *)b_rp_d.p, n_active, s));
         VMAT_CUDA(b_col_d.alloc((size_t)pad * 4));
         VMAT_CUDA(b_val_d.alloc((size_t)pad * 4));
-        VMAT_CUDA(cudaMemsetAsync(b_col_d.p, 0, (size_t)pad * 4, s));
-        VMAT_CUDA(cudaMemsetAsync(b_val_d.p, 0, (size_t)pad * 4, s));
+        VMAT_CUDA(cudaMemsetAsync((int32_t *)b_col_d.p + nnz, 0, (size_t)(pad - nnz) * 4, s));
+        VMAT_CUDA(cudaMemsetAsync((float *)b_val_d.p + nnz, 0, (size_t)(pad - nnz) * 4, s));
         VMAT_CUDA(b_cur_d.alloc((size_t)std::max(n_active, 1) * 4));
         VMAT_CUDA(cudaMemsetAsync(b_cur_d.p, 0, (size_t)std::max(n_active, 1) * 4, s));
     }
-    if (nnz > 0) {
+    const bool scatter_t = opts.build_Dt && !csc;
+    if (nnz > 0 && (scatter_t || opts.build_D)) {
         coo_scatter<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(
-            h->coo_vox, h->coo_blt, h->coo_val, nnz, (int64_t *)b_rp_t.p, (int32_t *)b_cur_t.p, (int32_t *)b_col_t.p,
-            (float *)b_val_t.p, (int64_t *)b_rp_d.p, (int32_t *)b_v2a.p, (int32_t *)b_cur_d.p, (int32_t *)b_col_d.p,
-            (float *)b_val_d.p);
+            h->coo_vox, h->coo_blt, h->coo_val, nnz, (int64_t *)b_rp_t.p, (int32_t *)b_cur_t.p,
+            scatter_t ? (int32_t *)b_col_t.p : nullptr, (float *)b_val_t.p, (int64_t *)b_rp_d.p, (int32_t *)b_v2a.p,
+            (int32_t *)b_cur_d.p, opts.build_D ? (int32_t *)b_col_d.p : nullptr, (float *)b_val_d.p);
         VMAT_LAUNCH_CHECK();
     }
     int32_t max_row_t = 0, max_row_d = 0;
-    if (opts.build_Dt)
+    if (scatter_t)
         VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s,
                            &max_row_t));
+    else if (opts.build_Dt)
+        VMAT_TRY(longest_row(cnt_blt, J, n_sm, s, &max_row_t)); // already in order: nothing to sort
     if (opts.build_D)
         VMAT_TRY(sort_rows((int64_t *)b_rp_d.p, (int32_t *)b_cnt_act.p, n_active, (int32_t *)b_col_d.p,
                            (float *)b_val_d.p, bad, n_sm, s, &max_row_d));
-    VMAT_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
-    if (hbad & DEV_DUPLICATE) return set_error(VMAT_EINVAL, "ddc_build: duplicate (voxel, beamlet) entry in the COO input");
+    if (hbad[0] & DEV_DUPLICATE) return set_error(VMAT_EINVAL, "ddc_build: duplicate (voxel, beamlet) entry in the COO input");
 
     // ---- quantisation
     if (fp8) {
