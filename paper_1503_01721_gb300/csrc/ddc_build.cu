@@ -29,35 +29,37 @@ int sort_smem_cap() {
     return SORT_SMEM_CAP_MAX;
 }
 
+// Validates the COO, counts entries per voxel and per beamlet, and sets bad[1]
+// unless the entries are in column order (beamlets nondecreasing, voxels strictly
+// increasing within a beamlet: the order a dose engine writes per-beamlet columns
+// in).  Lanes with the same beamlet add their count with one atomic (column-ordered
+// input has runs of equal beamlets).
 __global__ void coo_check_hist(const int32_t *__restrict__ vox, const int32_t *__restrict__ blt,
                                const float *__restrict__ val, int64_t nnz, int32_t V, int32_t J, int32_t *cnt_vox,
                                int32_t *cnt_blt, unsigned *colmax_bits, int32_t *bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-        int32_t i = vox[e], j = blt[e];
-        float v = val[e];
-        if (i < 0 || i >= V || j < 0 || j >= J || !isfinite(v)) {
-            atomicOr(bad, DEV_INDEX);
-            continue;
+    const int lane = threadIdx.x & 31;
+    bool unordered = false;
+    // every lane runs the same number of rounds (warp-wide matches inside)
+    const int64_t rounds = (nnz + stride - 1) / stride;
+    for (int64_t q = 0; q < rounds; ++q) {
+        const int64_t e = q * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const bool in = e < nnz;
+        int32_t i = in ? vox[e] : 0, j = in ? blt[e] : -1;
+        const float v = in ? val[e] : 0.f;
+        const bool ok = in && i >= 0 && i < V && j >= 0 && j < J && isfinite(v);
+        if (in && !ok) atomicOr(bad, DEV_INDEX);
+        if (in && e + 1 < nnz) {
+            const int32_t j1 = blt[e + 1];
+            unordered = unordered || j1 < j || (j1 == j && vox[e + 1] <= i);
         }
-        atomicAdd(&cnt_vox[i], 1);
-        atomicAdd(&cnt_blt[j], 1);
-        if (colmax_bits) atomicMax(&colmax_bits[j], __float_as_uint(fabsf(v)));
+        if (ok) atomicAdd(&cnt_vox[i], 1);
+        const int key = ok ? j : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&cnt_blt[j], __popc(peers));
+        if (ok && colmax_bits) atomicMax(&colmax_bits[j], __float_as_uint(fabsf(v)));
     }
-}
-
-// Is the COO in column order (beamlets nondecreasing, voxels strictly increasing
-// within a beamlet, the order a dose engine writes per-beamlet columns in)?  Sets
-// *unordered otherwise.
-__global__ void coo_csc_check(const int32_t *__restrict__ vox, const int32_t *__restrict__ blt, int64_t nnz,
-                              int32_t *unordered) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    bool bad = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e + 1 < nnz; e += stride) {
-        const int32_t b0 = blt[e], b1 = blt[e + 1];
-        bad = bad || b1 < b0 || (b1 == b0 && vox[e + 1] <= vox[e]);
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(unordered, 1);
+    if (__any_sync(0xffffffffu, unordered) && lane == 0) atomicOr(bad + 1, 1);
 }
 
 __global__ void flag_nonzero(const int32_t *cnt, int32_t n, int32_t *flag) {
@@ -99,6 +101,111 @@ __global__ void coo_scatter(const int32_t *__restrict__ vox, const int32_t *__re
             col_d[q] = j;
             val_d[q] = v;
         }
+    }
+}
+
+// ---- Stable LSD radix sort by compact voxel index (CSR(D) of a column-ordered COO).
+// Sorting the column-ordered entries by voxel with a stable sort leaves each voxel's
+// entries in beamlet order: no per-row sort.  7-bit digits; a block sorts a tile of
+// RS_TILE entries: per-tile digit counts, one exclusive scan over (digit, tile), then
+// a scatter whose in-tile ranks keep the input order (warp match per 32 entries,
+// warp counters, a prefix over the warps).
+constexpr int RS_BITS = 7, RS_BUCKETS = 1 << RS_BITS, RS_THREADS = 256, RS_ITEMS = 8;
+constexpr int RS_WARPS = RS_THREADS / 32, RS_TILE = RS_THREADS * RS_ITEMS;
+
+// Key of entry e: the pass-0 input is the COO (key = compact index of its voxel),
+// later passes read the previous pass's keys.
+__device__ __forceinline__ int32_t rs_key(const int32_t *keys, const int32_t *vox, const int32_t *vox2act, int64_t e) {
+    return keys ? keys[e] : vox2act[vox[e]];
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    rs_hist(const int32_t *__restrict__ keys, const int32_t *__restrict__ vox, const int32_t *__restrict__ vox2act,
+            int64_t n, int shift, int64_t n_tiles, int32_t *__restrict__ hist) {
+    __shared__ int32_t c[RS_BUCKETS];
+    for (int d = threadIdx.x; d < RS_BUCKETS; d += RS_THREADS) c[d] = 0;
+    __syncthreads();
+    const int64_t t = blockIdx.x, base = t * RS_TILE;
+    for (int u = 0; u < RS_ITEMS; ++u) {
+        const int64_t e = base + (int64_t)u * RS_THREADS + threadIdx.x;
+        if (e < n) atomicAdd(&c[(rs_key(keys, vox, vox2act, e) >> shift) & (RS_BUCKETS - 1)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_BUCKETS; d += RS_THREADS) hist[(int64_t)d * n_tiles + t] = c[d];
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    rs_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vox, const int32_t *__restrict__ vox2act,
+               const int32_t *__restrict__ pay, const float *__restrict__ val, int64_t n, int shift,
+               const int64_t *__restrict__ off, int64_t n_tiles, int32_t *keys_out, int32_t *pay_out,
+               float *val_out) {
+    __shared__ int32_t wcnt[RS_WARPS][RS_BUCKETS];
+    __shared__ int32_t woff[RS_WARPS][RS_BUCKETS];
+    __shared__ int32_t bstart[RS_BUCKETS + 1];
+    extern __shared__ __align__(16) int32_t rs_dyn[]; // the tile in sorted order: keys, payloads, values
+    int32_t *sk = rs_dyn, *sp = rs_dyn + RS_TILE;
+    float *sv = reinterpret_cast<float *>(rs_dyn + 2 * RS_TILE);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BUCKETS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    // warp w takes entries [base, base + 32 RS_ITEMS) of the tile, 32 consecutive per round
+    const int64_t t = blockIdx.x, base = t * RS_TILE + (int64_t)wid * 32 * RS_ITEMS;
+    const unsigned below = (1u << lane) - 1u;
+    int32_t key[RS_ITEMS], pj[RS_ITEMS], rk[RS_ITEMS];
+    float pv[RS_ITEMS];
+#pragma unroll
+    for (int u = 0; u < RS_ITEMS; ++u) {
+        const int64_t e = base + (int64_t)u * 32 + lane;
+        const bool ok = e < n;
+        key[u] = ok ? rs_key(keys, vox, vox2act, e) : 0;
+        pj[u] = ok ? pay[e] : 0;
+        pv[u] = ok ? val[e] : 0.f;
+        const int d = ok ? (key[u] >> shift) & (RS_BUCKETS - 1) : RS_BUCKETS; // past the end: no digit
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int lower = __popc(peers & below);
+        const int cur = ok ? wcnt[wid][d] : 0;
+        __syncwarp();
+        rk[u] = cur + lower;
+        if (ok && lower == 0) wcnt[wid][d] = cur + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_BUCKETS; d += RS_THREADS) {
+        int32_t acc = 0;
+        for (int w = 0; w < RS_WARPS; ++w) {
+            woff[w][d] = acc;
+            acc += wcnt[w][d];
+        }
+        bstart[d + 1] = acc; // the bucket's size in this tile, scanned below
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bstart[0] = 0;
+        for (int d = 0; d < RS_BUCKETS; ++d) bstart[d + 1] += bstart[d];
+    }
+    __syncthreads();
+    // the tile in sorted order in shared memory, then written out with consecutive
+    // threads on consecutive positions (each bucket's run is contiguous in the output)
+#pragma unroll
+    for (int u = 0; u < RS_ITEMS; ++u) {
+        const int64_t e = base + (int64_t)u * 32 + lane;
+        if (e < n) {
+            const int d = (key[u] >> shift) & (RS_BUCKETS - 1);
+            const int li = bstart[d] + woff[wid][d] + rk[u];
+            sk[li] = key[u];
+            sp[li] = pj[u];
+            sv[li] = pv[u];
+        }
+    }
+    __syncthreads();
+    const int cnt = bstart[RS_BUCKETS];
+    for (int li = threadIdx.x; li < cnt; li += RS_THREADS) {
+        const int32_t kk = sk[li];
+        const int d = (kk >> shift) & (RS_BUCKETS - 1);
+        const int64_t pos = off[(int64_t)d * n_tiles + t] + (li - bstart[d]);
+        if (keys_out) keys_out[pos] = kk;
+        pay_out[pos] = sp[li];
+        val_out[pos] = sv[li];
     }
 }
 
@@ -266,6 +373,52 @@ int grid_for(int64_t n, int n_sm) {
 int64_t round_pad(int64_t nnz) { return ((std::max<int64_t>(nnz, 1) + NNZ_PAD - 1) / NNZ_PAD) * NNZ_PAD; }
 
 // Sort each row of a CSR by column, check duplicates.
+// CSR(D) of a column-ordered COO: entries sorted by compact voxel index (stable), the
+// beamlet into col, the value into val.  Passes of RS_BITS bits over the key's width.
+vmat_status radix_by_voxel(const int32_t *vox, const int32_t *blt, const float *cval, const int32_t *vox2act,
+                           int64_t nnz, int32_t n_keys, int32_t *col, float *val, cudaStream_t s) {
+    if (nnz == 0) return VMAT_OK;
+    int bits = 1;
+    while (bits < 31 && (1 << bits) < n_keys) ++bits;
+    const int passes = (bits + RS_BITS - 1) / RS_BITS;
+    const int64_t n_tiles = (nnz + RS_TILE - 1) / RS_TILE;
+    if (n_tiles > INT32_MAX) return set_error(VMAT_EUNSUPPORTED, "ddc_build: too many nonzeros for the radix pass");
+    DevBuf hist, off, ka, kb, pa, va;
+    VMAT_CUDA(hist.alloc((size_t)RS_BUCKETS * n_tiles * 4));
+    VMAT_CUDA(off.alloc(((size_t)RS_BUCKETS * n_tiles + 1) * 8));
+    // ping-pong through the outputs: pass q writes to (col, val) when passes - 1 - q is even,
+    // else to the temporaries (pa, va), so the last pass lands in (col, val)
+    if (passes > 1) {
+        VMAT_CUDA(ka.alloc((size_t)nnz * 4));
+        VMAT_CUDA(pa.alloc((size_t)nnz * 4));
+        VMAT_CUDA(va.alloc((size_t)nnz * 4));
+    }
+    if (passes > 2) VMAT_CUDA(kb.alloc((size_t)nnz * 4));
+    // the sorted tile (48 KB) comes on top of the static counters: above the default per-block limit
+    VMAT_CUDA(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * RS_TILE * 4));
+    const int32_t *kin = nullptr, *pin = blt;
+    const float *vin = cval;
+    for (int q = 0; q < passes; ++q) {
+        const int shift = q * RS_BITS;
+        const bool last = q == passes - 1, to_out = ((passes - 1 - q) & 1) == 0;
+        int32_t *kout = last ? nullptr : (to_out ? (int32_t *)kb.p : (int32_t *)ka.p);
+        int32_t *pout = to_out ? col : (int32_t *)pa.p;
+        float *vout = to_out ? val : (float *)va.p;
+        rs_hist<<<(unsigned)n_tiles, RS_THREADS, 0, s>>>(kin, vox, vox2act, nnz, shift, n_tiles, (int32_t *)hist.p);
+        VMAT_LAUNCH_CHECK();
+        VMAT_TRY(scan_counts((const int32_t *)hist.p, (int64_t *)off.p, (int64_t)RS_BUCKETS * n_tiles, s));
+        rs_scatter<<<(unsigned)n_tiles, RS_THREADS, 3 * RS_TILE * 4, s>>>(kin, vox, vox2act, pin, vin, nnz, shift,
+                                                                          (const int64_t *)off.p, n_tiles, kout,
+                                                                          pout, vout);
+        VMAT_LAUNCH_CHECK();
+        kin = kout;
+        pin = pout;
+        vin = vout;
+    }
+    VMAT_CUDA(cudaStreamSynchronize(s)); // the ping-pong buffers are freed on return
+    return VMAT_OK;
+}
+
 vmat_status longest_row(const int32_t *cnt, int32_t n_rows, int n_sm, cudaStream_t s, int32_t *max_row) {
     *max_row = 0;
     if (n_rows == 0) return VMAT_OK;
@@ -443,8 +596,6 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         coo_check_hist<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(h->coo_vox, h->coo_blt, h->coo_val, nnz, V, J,
                                                                       cnt_vox, cnt_blt, (unsigned *)b_colmax.p, bad);
         VMAT_LAUNCH_CHECK();
-        coo_csc_check<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(h->coo_vox, h->coo_blt, nnz, bad + 1);
-        VMAT_LAUNCH_CHECK();
     }
     int32_t hbad[2] = {0, 0};
     VMAT_CUDA(cudaMemcpyAsync(hbad, bad, 8, cudaMemcpyDeviceToHost, s));
@@ -501,12 +652,14 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         VMAT_CUDA(b_cur_d.alloc((size_t)std::max(n_active, 1) * 4));
         VMAT_CUDA(cudaMemsetAsync(b_cur_d.p, 0, (size_t)std::max(n_active, 1) * 4, s));
     }
-    const bool scatter_t = opts.build_Dt && !csc;
-    if (nnz > 0 && (scatter_t || opts.build_D)) {
+    // column-ordered input: CSR(D^T) was copied, CSR(D) is a stable sort by voxel (rows come out in
+    // beamlet order); otherwise an atomic scatter into rows, then a sort of each row by column
+    const bool scatter_t = opts.build_Dt && !csc, scatter_d = opts.build_D && !csc;
+    if (nnz > 0 && (scatter_t || scatter_d)) {
         coo_scatter<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>(
             h->coo_vox, h->coo_blt, h->coo_val, nnz, (int64_t *)b_rp_t.p, (int32_t *)b_cur_t.p,
             scatter_t ? (int32_t *)b_col_t.p : nullptr, (float *)b_val_t.p, (int64_t *)b_rp_d.p, (int32_t *)b_v2a.p,
-            (int32_t *)b_cur_d.p, opts.build_D ? (int32_t *)b_col_d.p : nullptr, (float *)b_val_d.p);
+            (int32_t *)b_cur_d.p, scatter_d ? (int32_t *)b_col_d.p : nullptr, (float *)b_val_d.p);
         VMAT_LAUNCH_CHECK();
     }
     int32_t max_row_t = 0, max_row_d = 0;
@@ -515,9 +668,14 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
                            &max_row_t));
     else if (opts.build_Dt)
         VMAT_TRY(longest_row(cnt_blt, J, n_sm, s, &max_row_t)); // already in order: nothing to sort
-    if (opts.build_D)
+    if (scatter_d) {
         VMAT_TRY(sort_rows((int64_t *)b_rp_d.p, (int32_t *)b_cnt_act.p, n_active, (int32_t *)b_col_d.p,
                            (float *)b_val_d.p, bad, n_sm, s, &max_row_d));
+    } else if (opts.build_D) {
+        VMAT_TRY(radix_by_voxel(h->coo_vox, h->coo_blt, h->coo_val, (const int32_t *)b_v2a.p, nnz, n_active,
+                                (int32_t *)b_col_d.p, (float *)b_val_d.p, s));
+        VMAT_TRY(longest_row((int32_t *)b_cnt_act.p, n_active, n_sm, s, &max_row_d));
+    }
     VMAT_CUDA(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
     if (hbad[0] & DEV_DUPLICATE) return set_error(VMAT_EINVAL, "ddc_build: duplicate (voxel, beamlet) entry in the COO input");
