@@ -126,18 +126,6 @@ __device__ double block_reduce_sum(double v, double *sh) {
     return t;
 }
 
-__device__ double block_reduce_max(double v, double *sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, d));
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = sh[0];
-    for (int w = 1; w < MP_NW; ++w) t = fmax(t, sh[w]);
-    return t;
-}
-
 __device__ void finish(BBState *st, int reason, int t) {
     st->done = 1;
     st->stop = reason;
