@@ -375,8 +375,11 @@ int64_t round_pad(int64_t nnz) { return ((std::max<int64_t>(nnz, 1) + NNZ_PAD - 
 // Sort each row of a CSR by column, check duplicates.
 // CSR(D) of a column-ordered COO: entries sorted by compact voxel index (stable), the
 // beamlet into col, the value into val.  Passes of RS_BITS bits over the key's width.
+// reuse (optional): three nnz-entry device arrays the call may overwrite after the first
+// pass has read the input (the COO itself, when it is not kept), used as ping-pong space.
 vmat_status radix_by_voxel(const int32_t *vox, const int32_t *blt, const float *cval, const int32_t *vox2act,
-                           int64_t nnz, int32_t n_keys, int32_t *col, float *val, cudaStream_t s) {
+                           int64_t nnz, int32_t n_keys, int32_t *col, float *val, cudaStream_t s,
+                           int32_t *reuse_k = nullptr, int32_t *reuse_p = nullptr, float *reuse_v = nullptr) {
     if (nnz == 0) return VMAT_OK;
     int bits = 1;
     while (bits < 31 && (1 << bits) < n_keys) ++bits;
@@ -388,12 +391,17 @@ vmat_status radix_by_voxel(const int32_t *vox, const int32_t *blt, const float *
     VMAT_CUDA(off.alloc(((size_t)RS_BUCKETS * n_tiles + 1) * 8));
     // ping-pong through the outputs: pass q writes to (col, val) when passes - 1 - q is even,
     // else to the temporaries (pa, va), so the last pass lands in (col, val)
-    if (passes > 1) {
+    // The input is read only by pass 0, so the A set may be the input's own arrays when pass 0
+    // writes to the outputs instead (passes - 1 even: an odd number of passes, at least 3).
+    const bool reuse = reuse_k && reuse_p && reuse_v && passes >= 3 && (passes & 1);
+    if (passes > 1 && !reuse) {
         VMAT_CUDA(ka.alloc((size_t)nnz * 4));
         VMAT_CUDA(pa.alloc((size_t)nnz * 4));
         VMAT_CUDA(va.alloc((size_t)nnz * 4));
     }
     if (passes > 2) VMAT_CUDA(kb.alloc((size_t)nnz * 4));
+    int32_t *A_k = reuse ? reuse_k : (int32_t *)ka.p, *A_p = reuse ? reuse_p : (int32_t *)pa.p;
+    float *A_v = reuse ? reuse_v : (float *)va.p;
     // the sorted tile (48 KB) comes on top of the static counters: above the default per-block limit
     VMAT_CUDA(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * RS_TILE * 4));
     const int32_t *kin = nullptr, *pin = blt;
@@ -401,9 +409,9 @@ vmat_status radix_by_voxel(const int32_t *vox, const int32_t *blt, const float *
     for (int q = 0; q < passes; ++q) {
         const int shift = q * RS_BITS;
         const bool last = q == passes - 1, to_out = ((passes - 1 - q) & 1) == 0;
-        int32_t *kout = last ? nullptr : (to_out ? (int32_t *)kb.p : (int32_t *)ka.p);
-        int32_t *pout = to_out ? col : (int32_t *)pa.p;
-        float *vout = to_out ? val : (float *)va.p;
+        int32_t *kout = last ? nullptr : (to_out ? (int32_t *)kb.p : A_k);
+        int32_t *pout = to_out ? col : A_p;
+        float *vout = to_out ? val : A_v;
         rs_hist<<<(unsigned)n_tiles, RS_THREADS, 0, s>>>(kin, vox, vox2act, nnz, shift, n_tiles, (int32_t *)hist.p);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(scan_counts((const int32_t *)hist.p, (int64_t *)off.p, (int64_t)RS_BUCKETS * n_tiles, s));
@@ -673,7 +681,9 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
                            (float *)b_val_d.p, bad, n_sm, s, &max_row_d));
     } else if (opts.build_D) {
         VMAT_TRY(radix_by_voxel(h->coo_vox, h->coo_blt, h->coo_val, (const int32_t *)b_v2a.p, nnz, n_active,
-                                (int32_t *)b_col_d.p, (float *)b_val_d.p, s));
+                                (int32_t *)b_col_d.p, (float *)b_val_d.p, s,
+                                opts.keep_coo ? nullptr : h->coo_vox, opts.keep_coo ? nullptr : h->coo_blt,
+                                opts.keep_coo ? nullptr : h->coo_val));
         VMAT_TRY(longest_row((int32_t *)b_cnt_act.p, n_active, n_sm, s, &max_row_d));
     }
     VMAT_CUDA(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, s));
