@@ -12,6 +12,7 @@ import json
 import os
 
 VAL_BYTES = {"f32": 4, "bf16": 2, "fp8": 1}
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline denominator)
 IDX_BYTES = 4
 PTR_BYTES = 8
 
