@@ -141,3 +141,24 @@ def test_batch_with_machines():
         if list(cps1) == list(cps):
             assert abs(F1 - F[i]) <= 1e-4 * F1
     batch.close()
+
+
+def test_plan_with_machine_and_interdigitation():
+    """Both constraints at once: the delivery-limit bounds on y and the interdigitation
+    constraint on the apertures, against the oracle with the same two."""
+    c = _machine_case("cfg1")
+    c = dataclasses.replace(c, mlc=dataclasses.replace(c.mlc, interdigitation=True))
+    ddc = make_ddc(c)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, 12, TIGHT)
+    lo, hi = oracle.fluence_bounds(c.mlc, c.mlc.machine, list(cps), list(lv))
+    assert np.all(y >= lo) and np.all(y <= hi)
+    for t in range(len(cps)):  # adjacent rows never interdigitate
+        L, R = lv[t, :, 0], lv[t, :, 1]
+        assert np.all(L[1:] <= R[:-1]) and np.all(L[:-1] <= R[1:])
+    ref = oracle.cg_plan(D, c.mlc, c.structs, 12, oracle.BBOptions(**TIGHT))
+    if list(cps) == ref.cps:
+        assert abs(F - ref.F) <= 1e-4 * ref.F
+    else:
+        t = next(i for i, (a, b) in enumerate(zip(list(cps), ref.cps)) if a != b)
+        assert near_tie_at(ddc, c, D, t, cps[t], TIGHT), f"sequence differs at {t}: gpu {list(cps)} oracle {ref.cps}"
