@@ -350,7 +350,10 @@ typedef struct {
  * advanced together: iteration t of every plan runs in shared launches (the
  * gradient, D^T g, pricing, the commit, the aperture dose and a persistent
  * master-problem solver whose CTAs are split among the plans), and the whole run
- * is recorded once as a CUDA graph.  The batched D^T g configuration is chosen
+ * is recorded once as a CUDA graph.  Plans with interdigitation set are priced
+ * by their own row-chain launches inside that graph; the other plans share one
+ * pricing launch.  Plans may differ in MLC, DDC, machine and aperture count, not
+ * in the DDC's value type.  The batched D^T g configuration is chosen
  * by timing every warp-row configuration on the batch.  The handles and the
  * descriptors' arrays must stay valid until vmat_batch_free.  opts NULL =
  * defaults.  Synchronises. */

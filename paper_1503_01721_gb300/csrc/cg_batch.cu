@@ -120,6 +120,8 @@ struct Batch {
     std::vector<int32_t> grid_t, stages_t, keep_t;
     std::vector<size_t> smem_t;
     int32_t *d_ctl = nullptr, *d_targets = nullptr, *h_ctl = nullptr;
+    int32_t *d_one = nullptr; // a word holding 1: the batched pricing's skip word of interdigitation plans
+    bool any_interdig = false;
     int spmv_cfg = 4;
     double autotune_ms[32] = {0};
     cudaStream_t cs = nullptr;
@@ -169,6 +171,11 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
         VMAT_TRY(objective_grad_batched(b.d_obj, b.d_na_off, n, b.tot_na, s));
         VMAT_TRY(spmv_rows_batched(b.dt, b.spmv_cfg, b.d_spmv, b.d_rows_off, n, b.tot_rows, s));
         VMAT_TRY(price_apertures_batched(b.d_price, b.d_price_off, n, b.tot_price, b.max_cols, s));
+        if (b.any_interdig) // the chain DP over rows (Section 2.2.2), each such plan on its own scratch
+            for (BPlan &p : b.P)
+                if (p.mlc.interdigitation)
+                    VMAT_TRY(price_apertures_impl(&p.mlc, p.pi, p.occupied, p.leaves_all, p.best_cp, p.best_leaves,
+                                                  p.best_price, p.pr_ws, s, p.ctl));
         batch_commit<<<n, 128, 0, s>>>(t, b.d_commit);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(aperture_dose_batched(b.dt, b.d_da, b.d_na_off, n, b.tot_na, t, s));
@@ -204,8 +211,6 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
             return set_error(VMAT_ESTATE, "vmat_batch_create: plan %d needs both CSR(D) and CSR(D^T)", i);
         if ((int64_t)d.mlc->K * d.mlc->n_rows * d.mlc->n_cols != h->J)
             return set_error(VMAT_EINVAL, "vmat_batch_create: plan %d: K*n_rows*n_cols != J", i);
-        if (d.mlc->interdigitation)
-            return set_error(VMAT_EUNSUPPORTED, "vmat_batch_create: plan %d: interdigitation is not batched", i);
         if (d.n_apertures < 0 || d.n_apertures > std::min(d.mlc->K, 96))
             return set_error(VMAT_EINVAL, "vmat_batch_create: plan %d: n_apertures must be in [0, min(K, 96)]", i);
         if (i == 0) b.dt = h->dtype;
@@ -228,6 +233,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         p.NR = d.mlc->n_rows;
         p.bpc = d.mlc->n_rows * d.mlc->n_cols;
         p.NA = h->n_active;
+        b.any_interdig = b.any_interdig || d.mlc->interdigitation;
         b.T = std::max(b.T, p.n_ap);
         b.max_cols = std::max(b.max_cols, d.mlc->n_cols);
     }
@@ -236,6 +242,9 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaStreamCreateWithFlags(&b.cs, cudaStreamNonBlocking));
     VMAT_TRY(b.get(&b.d_ctl, (size_t)n_plans * CTL_N));
     VMAT_TRY(b.get(&b.d_targets, n_plans));
+    VMAT_TRY(b.get(&b.d_one, 1));
+    batch_fill_i32<<<1, 32, 0, s>>>(b.d_one, 1, 1);
+    VMAT_LAUNCH_CHECK();
 
     // ---- per-plan device state and set-up
     std::vector<int64_t *> cpo_dev(n_plans);
@@ -317,7 +326,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
                            p.active, p.ctl, p.bpc, h.Dt.n_rows};
         PricePlan &q = price[i];
         VMAT_TRY(pricing_geom(&p.mlc, &q.g));
-        const int64_t prow = (int64_t)p.K * p.NR;
+        const bool interdig = p.mlc.interdigitation != 0; // no rows in the shared launch, skipped by its CP kernel
+        const int64_t prow = interdig ? 0 : (int64_t)p.K * p.NR;
         q.pi = p.pi;
         q.occupied = p.occupied;
         q.leaves = p.leaves_all;
@@ -327,7 +337,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         q.best_cp = p.best_cp;
         q.best_leaves = p.best_leaves;
         q.best_price = p.best_price;
-        q.skip = p.ctl;
+        q.skip = interdig ? b.d_one : p.ctl;
         const bool tab_ok = h.cp_tab && h.cp_tab_K == p.K && h.cp_tab_bpc == p.bpc;
         da[i] = DaPlan{h.D.rowptr, h.D.col, h.D.val, fp8 ? h.scale : nullptr, tab_ok ? h.cp_tab : nullptr, p.K, p.NR,
                        p.mlc.n_cols, p.cps,
@@ -436,6 +446,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     // ---- record the run as a CUDA graph (on a private stream); without it, runs enqueue directly
     {
         cudaGraph_t g = nullptr;
+        VMAT_TRY(pricing_attributes()); // function attributes are set outside the capture
         VMAT_CUDA(cudaStreamBeginCapture(b.cs, cudaStreamCaptureModeThreadLocal));
         const vmat_status st = enqueue_run(b, b.cs);
         const cudaError_t ec = cudaStreamEndCapture(b.cs, &g);

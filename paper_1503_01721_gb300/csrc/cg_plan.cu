@@ -30,10 +30,6 @@ vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, con
                               const int32_t *skip);
 size_t objective_scratch_bytes(int n_sm);
 vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);
-vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
-                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s,
-                                 const int32_t *skip);
-size_t pricing_scratch_bytes(const vmat_mlc *mlc);
 
 __global__ void gather_u8(const uint8_t *src, const int32_t *idx, int32_t n, uint8_t *dst) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];

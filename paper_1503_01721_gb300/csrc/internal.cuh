@@ -188,6 +188,12 @@ struct PricingGeom {
 constexpr int INTERDIG_MAX_COLS = 88; // the chain DP holds (n_cols + 1)^2 states of a row in shared memory
 vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g);
 size_t pricing_scratch_bytes(const vmat_mlc *mlc);
+vmat_status pricing_attributes(); // raises the kernels' shared-memory limits (not a stream operation)
+// One plan's pricing (either variant) with scratch ws of pricing_scratch_bytes(mlc);
+// skip (may be null): a device word, nonzero = leave the outputs untouched.
+vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
+                                 int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s,
+                                 const int32_t *skip);
 
 struct PricePlan { // one plan's pricing inputs, per-row scratch and results
     PricingGeom g;
@@ -252,6 +258,8 @@ vmat_status objective_grad_batched(const ObjPlan *plans, const int64_t *off, int
                                    cudaStream_t s);
 
 // off: prefix of K * n_rows over the plans (total entries); max_cols: largest n_cols.
+// A plan whose skip word is nonzero, or whose entry range is empty, is left alone
+// (interdigitation plans of a batch are priced on their own).
 vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
                                     int32_t max_cols, cudaStream_t s);
 vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,

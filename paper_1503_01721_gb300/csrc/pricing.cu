@@ -567,15 +567,31 @@ vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g) {
     return VMAT_OK;
 }
 
+// Dynamic shared-memory limits of the pricing kernels, raised once per process for
+// their largest MLC (1024 columns; the interdigitation kernel's own column limit).
+// Not a stream operation: callers that record a CUDA graph call it before capture.
+vmat_status pricing_attributes() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(price_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(PR_WARPS * row_smem_stride(1024)));
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(price_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(PR_WARPS * row_smem_stride(1024)));
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(price_cps_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)interdig_smem(INTERDIG_MAX_COLS));
+    });
+    if (err != cudaSuccess)
+        return set_error(VMAT_ECUDA, "pricing: cudaFuncSetAttribute failed: %s", cudaGetErrorString(err));
+    return VMAT_OK;
+}
+
 vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
                                     int32_t max_cols, cudaStream_t s) {
     if (n_plans < 1 || n_plans > VMAT_MAX_BATCH) return set_error(VMAT_EINVAL, "price_apertures_batched: bad plan count");
-    static bool attr_set = false;
-    if (!attr_set) {
-        VMAT_CUDA(cudaFuncSetAttribute(price_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(PR_WARPS * row_smem_stride(1024))));
-        attr_set = true;
-    }
+    VMAT_TRY(pricing_attributes());
     if (total > 0) {
         const int64_t blocks = (total + PR_WARPS - 1) / PR_WARPS;
         price_rows_batched_kernel<<<(unsigned)blocks, PR_WARPS * 32, PR_WARPS * row_smem_stride(max_cols), s>>>(
@@ -603,12 +619,7 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         double *Pall = reinterpret_cast<double *>(cp_ok + ((g.K + 15) & ~15));
         int16_t *pred_all = reinterpret_cast<int16_t *>(Pall + (int64_t)g.K * g.n_rows * (g.n_cols + 1));
         const size_t sm = interdig_smem(g.n_cols);
-        static bool attr_id = false;
-        if (!attr_id) {
-            VMAT_CUDA(cudaFuncSetAttribute(price_cps_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)interdig_smem(INTERDIG_MAX_COLS)));
-            attr_id = true;
-        }
+        VMAT_TRY(pricing_attributes());
         const int64_t rows = (int64_t)g.K * g.n_rows;
         interdig_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
                                  s>>>(g, pi, occupied, Pall, skip);
@@ -622,12 +633,7 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         return VMAT_OK;
     }
     const size_t smem = PR_WARPS * row_smem_stride(g.n_cols);
-    static bool attr_set = false;
-    if (!attr_set) {
-        VMAT_CUDA(cudaFuncSetAttribute(price_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(PR_WARPS * row_smem_stride(1024))));
-        attr_set = true;
-    }
+    VMAT_TRY(pricing_attributes());
     const int64_t blocks = (rows + PR_WARPS - 1) / PR_WARPS;
     price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok, skip);
     VMAT_LAUNCH_CHECK();

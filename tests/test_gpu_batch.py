@@ -45,24 +45,18 @@ def _batch_outputs(batch, cases):
     return out
 
 
-@pytest.mark.parametrize("tight", [False, True])
-def test_batch_matches_oracle_and_single_plans(tight):
-    from paper_1503_01721_gb300 import api
-    cases = _cases()
-    ddcs = [make_ddc(c) for c, _ in cases]
-    voxs = [api.VoxelParams.from_numpy(c.structs) for c, _ in cases]
-    opts = api.BBOptions(**TIGHT) if tight else None
-    batch = api.Batch([(d.h, c.mlc, v, n) for d, v, (c, n) in zip(ddcs, voxs, cases)], opts)
-    info = batch.info()
-    assert info["n_plans"] == len(cases) and info["max_apertures"] == 20
-    assert info["graph"] == 1 and info["graph_nodes"] > 0
-    assert info["spmv_cfg"] in info["autotune_ms"]
+def _check_batch(batch, ddcs, cases, tight):
+    """Every plan against the oracle and against cg_plan alone; a second replay of
+    the graph equal bit for bit."""
     F, stats = batch.run()
     outs = _batch_outputs(batch, cases)
     for i, (c, n) in enumerate(cases):
         cps, lv, y, dose = outs[i]
         st = stats[i]
         assert st["n_apertures"] == n and st["stop"] == "count" and st["bb_iters_total"] > 0
+        if c.mlc.interdigitation:  # the left leaf of a row never passes an adjacent row's right leaf
+            for a in lv:
+                assert np.all(a[1:, 0] <= a[:-1, 1]) and np.all(a[:-1, 0] <= a[1:, 1])
         D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
         s = c.structs
         x = oracle.aperture_fluence(c.mlc, cps, lv, y)
@@ -88,6 +82,40 @@ def test_batch_matches_oracle_and_single_plans(tight):
     for a, b in zip(outs, outs2):
         for u, v in zip(a, b):
             assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_batch_matches_oracle_and_single_plans(tight):
+    from paper_1503_01721_gb300 import api
+    cases = _cases()
+    ddcs = [make_ddc(c) for c, _ in cases]
+    voxs = [api.VoxelParams.from_numpy(c.structs) for c, _ in cases]
+    opts = api.BBOptions(**TIGHT) if tight else None
+    batch = api.Batch([(d.h, c.mlc, v, n) for d, v, (c, n) in zip(ddcs, voxs, cases)], opts)
+    info = batch.info()
+    assert info["n_plans"] == len(cases) and info["max_apertures"] == 20
+    assert info["graph"] == 1 and info["graph_nodes"] > 0
+    assert info["spmv_cfg"] in info["autotune_ms"]
+    _check_batch(batch, ddcs, cases, tight)
+    batch.close()
+
+
+def test_batch_with_interdigitation_plans():
+    """Plans with the interdigitation constraint (Section 2.2.2) mixed with plain ones
+    in one batch: each priced by the row-chain program on its own, the others by the
+    shared pricing launch, all in the same graph."""
+    import dataclasses
+    from paper_1503_01721_gb300 import api
+
+    def interdig(c):
+        return dataclasses.replace(c, mlc=dataclasses.replace(c.mlc, interdigitation=True))
+    cases = [(interdig(synth.make_case("tiny", seed=0)), 3), (synth.make_case("cfg1", seed=0), 8),
+             (interdig(synth.make_case("ragged", seed=0)), 4), (interdig(synth.make_case("cfg1", seed=2)), 10)]
+    ddcs = [make_ddc(c) for c, _ in cases]
+    voxs = [api.VoxelParams.from_numpy(c.structs) for c, _ in cases]
+    batch = api.Batch([(d.h, c.mlc, v, n) for d, v, (c, n) in zip(ddcs, voxs, cases)], api.BBOptions(**TIGHT))
+    assert batch.info()["graph"] == 1
+    _check_batch(batch, ddcs, cases, True)
     batch.close()
 
 
