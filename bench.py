@@ -7,8 +7,12 @@ FP32 dose).  The DDC (CSR of D and of D^T) is resident in HBM before timing.
 
 value = effective DDC bandwidth of the plan: the algorithmic bytes of every
 D x and D^T g pass the plan makes, divided by the plan's wall time (GB/s).
-ms_per_step = plan wall time.  roofline = the beamlet-price SpMV, timed by the
-library's CUDA events on its launch stream during the timed plans.
+The D^T g passes read only the beamlet rows inside the leaf-travel windows of
+the unoccupied CPs (the prices that pricing reads), so their bytes are those
+rows' bytes; plan.pp1_window_frac = those bytes over the bytes of passes over
+every row of the unoccupied CPs.  ms_per_step = plan wall time.  roofline =
+the beamlet-price SpMV, timed by the library's CUDA events on its launch
+stream during the timed plans.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -52,7 +56,10 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
 INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
 # configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
-# (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  A configuration without a capture reports null.
+# (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  The plan's passes are windowed: their ratio is
+# WINDOWED_TRAFFIC_RATIO, measured on a windowed launch of the plan; a configuration without such a
+# capture reports null.
+WINDOWED_TRAFFIC_RATIO = {("f32", 11): 1.0103}  # profiles/spmv_warp_row_c_kernel_cfg2_windowed_traffic.md
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
                  ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
                  ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
@@ -319,14 +326,14 @@ def run_ours(args, rank, world, local):
     kname = SPMV_KERNELS.get(cfg_dt, f"spmv configuration {cfg_dt}") + \
         (" + spmv_fixup" if info["tile_nnz_Dt"] else "") + " (beamlet price D^T g over the unoccupied CPs)"
     bytes_launch = spmv_bytes / max(spmv_n, 1)
-    ratio = TRAFFIC_RATIO.get((args.dtype, cfg_dt))
+    ratio = WINDOWED_TRAFFIC_RATIO.get((args.dtype, cfg_dt))
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4),
             "traffic": None if ratio is None else round(ratio * bytes_launch),
             "traffic_source": None if ratio is None else
-            f"ncu dram bytes / algorithmic bytes = {ratio} for this kernel on the full D^T pass, times this "
-            "launch's algorithmic bytes",
+            f"ncu dram bytes / algorithmic bytes = {ratio} for this kernel on a windowed D^T g launch of the "
+            "plan, times this launch's algorithmic bytes",
             "peak_source": peaks["source"], "frac_of_nominal": round(achieved / roofline.HBM_NOMINAL_GBS, 4),
             "nominal_peak": roofline.HBM_NOMINAL_GBS, "bytes_per_launch": round(bytes_launch),
             "avg_launch_ms": round(spmv_ms / max(spmv_n, 1), 4)}
@@ -417,6 +424,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plan": {"F": Fs[-1], "F_spread": max(Fs) - min(Fs), "apertures": st["n_apertures"],
                      "stop": st["stop"], "bb_iters": st["bb_iters_total"],
+                     "pp1_window_frac": round(st["pp1_spmv_bytes"] / max(st["pp1_full_bytes"], 1.0), 4),
                      "phases_ms": {k: round(st[k], 3) for k in
                                    ("t_pp1_ms", "t_pp2_ms", "t_da_ms", "t_mp_ms", "t_final_ms", "t_total_ms")},
                      "build_ms": round(info["build_ms"], 1)},

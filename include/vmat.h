@@ -157,12 +157,13 @@ typedef struct {
     double t_final_ms;  /* final dose D (A y) and objective */
     double pp1_spmv_ms; /* the D^T g kernels alone */
     int64_t pp1_spmv_launches;
-    double pp1_spmv_bytes;  /* algorithmic bytes of those launches */
+    double pp1_spmv_bytes;  /* algorithmic bytes of those launches (rows inside the leaf-travel windows) */
     double other_spmv_bytes; /* algorithmic bytes of the D x / aperture-dose passes */
     int32_t n_apertures;
     int32_t bb_iters_total;
     int32_t stop_reason;
     int64_t kernel_launches; /* kernels this call launched */
+    double pp1_full_bytes;   /* bytes of the same passes over every row of the unoccupied CPs */
 } vmat_plan_stats;
 
 /* ---- DDC matrix ---------------------------------------------------------- */
@@ -208,6 +209,18 @@ vmat_status dose_forward(vmat_ddc h, const float *x, float *d, void *stream);
  * Needs build_Dt. */
 vmat_status beamlet_price(vmat_ddc h, const float *g, float *pi, const uint8_t *cp_active,
                           int32_t beamlets_per_cp, void *stream);
+
+/* pi = D^T g (Eq. 3) on the beamlets that pricing can read: for every CP k with
+ * occupied[k] == 0 and MLC row r, the columns [Lmin, Rmax) of the row's
+ * leaf-travel window (Section 2.2.2 with the neighbour compatibility of Eq. 2:
+ * each leaf within m * travel_cols columns of its position at the nearest
+ * occupied CP m steps away in the same arc).  price_apertures reads no other
+ * entry; they are left unspecified.  mlc: host; occupied: device uint8 [K];
+ * leaves: device int16 [K][n_rows][2], (L, R) of the occupied CPs; g: device
+ * float [V]; pi: device float [J] with J = K * n_rows * n_cols.  Needs
+ * build_Dt.  Allocates K * n_rows * 4 bytes of device scratch (stream-ordered). */
+vmat_status beamlet_price_windowed(vmat_ddc h, const vmat_mlc *mlc, const uint8_t *occupied, const int16_t *leaves,
+                                   const float *g, float *pi, void *stream);
 
 /* ---- Objective ------------------------------------------------------------ */
 

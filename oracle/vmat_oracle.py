@@ -41,7 +41,11 @@ R7  Neighbour compatibility (Eq. 2, Section 2.1): for the nearest occupied CP
 R8  Ties: a row opening [L, R) is chosen by (value desc, width asc,
     |L + R - n_cols| asc, L asc); CPs by (price desc, index asc).  Row values
     are P_R - P_L with P the sequential float64 prefix sum of the float32
-    prices, the CP price the sequential float64 sum over rows.
+    prices over the row's window [Lmin, Rmax) of R7 (P_c = 0 up to Lmin,
+    constant after Rmax): the price of an opening is the sum of its
+    beamlets' prices, and only beamlets inside the window can be in an
+    opening, so prices outside it never enter a value.  The CP price is the
+    sequential float64 sum over rows.
 R9  The loop stops when the best CP price is <= 0 (no aperture lowers F) or
     when n_apertures have been generated.
 R11 Delivery limits (Eq. 2, 6).  Gantry speed s_k of an occupied CP is the
@@ -166,10 +170,16 @@ def leaf_windows(mlc, occupied, leaves, k: int):
     return Lmin, Lmax, Rmin, Rmax
 
 
-def prefix_sums(pi_row):
-    """P_0 = 0, P_{c+1} = P_c + pi_c in float64, accumulated in column order."""
-    P = np.zeros(len(pi_row) + 1, F64)
-    np.cumsum(np.asarray(pi_row, F64), out=P[1:])
+def prefix_sums(pi_row, lo: int = 0, hi=None):
+    """Float64 prefix sums over the columns [lo, hi) of a row (reading R8):
+    P_c = 0 for c <= lo, P_{c+1} = P_c + pi_c for lo <= c < hi, accumulated in
+    column order, and P_c = P_hi for c > hi.  Entries outside [lo, hi) are not read."""
+    N = len(pi_row)
+    hi = N if hi is None else hi
+    P = np.zeros(N + 1, F64)
+    if hi > lo:
+        np.cumsum(np.asarray(pi_row[lo:hi], F64), out=P[lo + 1:hi + 1])
+        P[hi + 1:] = P[hi]
     return P
 
 
@@ -180,7 +190,7 @@ def best_opening(pi_row, Lmin: int, Lmax: int, Rmin: int, Rmax: int):
     Returns (value, L, R), or (None, -1, -1) if no pair is feasible.
     """
     N = len(pi_row)
-    P = prefix_sums(pi_row)
+    P = prefix_sums(pi_row, Lmin, Rmax)
     L, R = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
     feas = (L <= R) & (L >= Lmin) & (L <= Lmax) & (R >= Rmin) & (R <= Rmax)
     if not feas.any():
@@ -237,7 +247,7 @@ def price_cp_interdig(mlc, pi, occupied, leaves, k: int, with_leaves: bool = Tru
     S = None
     preds = []
     for r in range(mlc.n_rows):
-        P = prefix_sums(pi[base + r * N: base + (r + 1) * N])
+        P = prefix_sums(pi[base + r * N: base + (r + 1) * N], int(Lmin[r]), int(Rmax[r]))
         feas = (Lg <= Rg) & (Lg >= Lmin[r]) & (Lg <= Lmax[r]) & (Rg >= Rmin[r]) & (Rg <= Rmax[r])
         v = np.where(feas, P[Rg] - P[Lg], NEG)
         if S is None:

@@ -58,7 +58,8 @@ class PlanStats(ctypes.Structure):
     _fields_ = [("t_total_ms", c_f64), ("t_pp1_ms", c_f64), ("t_pp2_ms", c_f64), ("t_da_ms", c_f64),
                 ("t_mp_ms", c_f64), ("t_final_ms", c_f64), ("pp1_spmv_ms", c_f64), ("pp1_spmv_launches", c_i64),
                 ("pp1_spmv_bytes", c_f64), ("other_spmv_bytes", c_f64), ("n_apertures", c_i32),
-                ("bb_iters_total", c_i32), ("stop_reason", c_i32), ("kernel_launches", c_i64)]
+                ("bb_iters_total", c_i32), ("stop_reason", c_i32), ("kernel_launches", c_i64),
+                ("pp1_full_bytes", c_f64)]
 
 
 class PlanDesc(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "ddc_info": (c_i32, [c_vp, ctypes.POINTER(DdcInfo)]),
     "dose_forward": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "beamlet_price": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
+    "beamlet_price_windowed": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "objective_grad": (c_i32, [c_i32, c_vp, ctypes.POINTER(Voxels), c_vp, c_vp, c_vp]),
     "price_apertures": (c_i32, [ctypes.POINTER(Mlc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "price_apertures_noalloc": (c_i32, [ctypes.POINTER(Mlc), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

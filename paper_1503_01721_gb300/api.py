@@ -149,6 +149,17 @@ def beamlet_price(h: int, g: torch.Tensor, pi: torch.Tensor, cp_active: torch.Te
         _ptr(cp_active, torch.uint8, None, "cp_active", allow_none=True), int(beamlets_per_cp), _stream(stream)))
 
 
+def beamlet_price_windowed(h: int, mlc, occupied: torch.Tensor, leaves: torch.Tensor, g: torch.Tensor,
+                           pi: torch.Tensor, stream=None) -> None:
+    """pi = D^T g (Eq. 3) on the beamlets inside the leaf-travel windows of the
+    unoccupied CPs (the entries price_apertures reads); other entries unspecified."""
+    m = _MlcC(mlc)
+    check("beamlet_price_windowed", _lib.load().beamlet_price_windowed(
+        ctypes.c_void_p(h), ctypes.byref(m.s), _ptr(occupied, torch.uint8, mlc.K, "occupied"),
+        _ptr(leaves, torch.int16, mlc.K * mlc.n_rows * 2, "leaves"), _ptr(g, torch.float32, None, "g"),
+        _ptr(pi, torch.float32, None, "pi"), _stream(stream)))
+
+
 def objective_grad(z: torch.Tensor, vox: VoxelParams, g: torch.Tensor | None = None,
                    F: torch.Tensor | None = None, stream=None) -> None:
     """F(z) (Eq. 1) into F (float64 [1]) and g = -grad F (Eq. 4) into g."""

@@ -90,6 +90,8 @@ struct BPlan {
     int32_t *best_cp = nullptr, *cps = nullptr, *ctl = nullptr;
     double *best_price = nullptr, *F_dev = nullptr, *F0 = nullptr;
     void *obj_ws = nullptr, *pr_ws = nullptr, *mp_ws = nullptr;
+    short2 *win = nullptr;                 // [K * NR] leaf-travel windows of the current iteration
+    unsigned long long *wcount = nullptr;  // [iterations][3]: rows, nonzeros (and 0) inside the windows
     double F_offset = 0.0;
     std::vector<int64_t> cpo; // CSR(D^T) rowptr at each CP boundary
 };
@@ -114,6 +116,9 @@ struct Batch {
     int64_t *d_na_off = nullptr, tot_na = 0;
     CommitPlan *d_commit = nullptr;
     BoundsPlan *d_bounds = nullptr; // null when no plan has a machine
+    WinPlan *d_win = nullptr;
+    int32_t max_K = 1;
+    std::vector<int32_t> cols; // the distinct MLC column counts of the plans
     void *d_mpargs = nullptr;
     int64_t *d_weight = nullptr; // [n] warp tiles of each plan (the solver's CTA split)
     unsigned *d_gctl = nullptr;  // [8] batch barrier, epoch and active-set words
@@ -157,6 +162,7 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
     const int n = b.n;
     for (BPlan &p : b.P) {
         if (p.NA > 0) VMAT_CUDA(cudaMemsetAsync(p.z_c, 0, (size_t)p.NA * 4, s));
+        VMAT_CUDA(cudaMemsetAsync(p.wcount, 0, (size_t)3 * std::max(b.T, 1) * 8, s));
         VMAT_CUDA(cudaMemsetAsync(p.occupied, 0, p.K, s));
         VMAT_CUDA(cudaMemsetAsync(p.leaves_all, 0, (size_t)p.K * p.NR * 4, s));
         batch_fill_u8<<<std::max(1, (p.K + 255) / 256), 256, 0, s>>>(p.active, p.K, 1);
@@ -169,7 +175,9 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
         batch_begin<<<1, 64, 0, s>>>(t, b.d_targets, b.d_ctl, n);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(objective_grad_batched(b.d_obj, b.d_na_off, n, b.tot_na, s));
-        VMAT_TRY(spmv_rows_batched(b.dt, b.spmv_cfg, b.d_spmv, b.d_rows_off, n, b.tot_rows, s));
+        VMAT_TRY(price_windows_batched(b.d_win, n, b.max_K, t, s));
+        VMAT_TRY(spmv_rows_batched(b.dt, b.spmv_cfg, b.d_spmv, b.d_rows_off, n, b.tot_rows, s, b.cols.data(),
+                                   (int)b.cols.size()));
         VMAT_TRY(price_apertures_batched(b.d_price, b.d_price_off, n, b.tot_price, b.max_cols, s));
         if (b.any_interdig) // the chain DP over rows (Section 2.2.2), each such plan on its own scratch
             for (BPlan &p : b.P)
@@ -236,6 +244,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         b.any_interdig = b.any_interdig || d.mlc->interdigitation;
         b.T = std::max(b.T, p.n_ap);
         b.max_cols = std::max(b.max_cols, d.mlc->n_cols);
+        b.max_K = std::max(b.max_K, d.mlc->K);
+        if (std::find(b.cols.begin(), b.cols.end(), d.mlc->n_cols) == b.cols.end()) b.cols.push_back(d.mlc->n_cols);
     }
     if (b.max_cols > 1024) return set_error(VMAT_EUNSUPPORTED, "vmat_batch_create: more than 1024 MLC columns");
     VMAT_CUDA(cudaMallocHost(&b.h_ctl, (size_t)n_plans * CTL_N * sizeof(int32_t)));
@@ -279,6 +289,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         VMAT_TRY(b.get((char **)&p.pr_ws, pricing_scratch_bytes(&p.mlc)));
         VMAT_TRY(b.get((char **)&p.mp_ws, mp_workspace_bytes(std::min(nap, 96))));
         VMAT_TRY(b.get(&cpo_dev[i], (size_t)p.K + 1));
+        VMAT_TRY(b.get(&p.win, (size_t)p.K * p.NR));
+        VMAT_TRY(b.get(&p.wcount, (size_t)3 * std::max(b.T, 1)));
         p.ctl = b.d_ctl + (size_t)i * CTL_N;
         // columns not yet generated must read as 0 (later runs overwrite only columns they generate)
         VMAT_CUDA(cudaMemsetAsync(p.DA, 0, (size_t)p.n_wtiles * p.wstride * 4, s));
@@ -311,6 +323,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     // ---- descriptor tables
     std::vector<SpmvPlan> spmv(n_plans);
     std::vector<PricePlan> price(n_plans);
+    std::vector<WinPlan> wins(n_plans);
     std::vector<DaPlan> da(n_plans);
     std::vector<ObjPlan> obj(n_plans);
     std::vector<CommitPlan> com(n_plans);
@@ -323,9 +336,10 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         const Ddc &h = *p.h;
         const bool fp8 = h.dtype == VMAT_FP8E4M3;
         spmv[i] = SpmvPlan{h.Dt.rowptr, h.Dt.col, h.Dt.val, p.g_full, p.pi, fp8 ? h.scale : nullptr, nullptr,
-                           p.active, p.ctl, p.bpc, h.Dt.n_rows};
+                           RowMask{nullptr, p.win, p.bpc, p.mlc.n_cols}, p.ctl, h.Dt.n_rows};
         PricePlan &q = price[i];
         VMAT_TRY(pricing_geom(&p.mlc, &q.g));
+        wins[i] = WinPlan{q.g, p.occupied, p.leaves_all, p.win, h.Dt.rowptr, p.wcount, p.ctl};
         const bool interdig = p.mlc.interdigitation != 0; // no rows in the shared launch, skipped by its CP kernel
         const int64_t prow = interdig ? 0 : (int64_t)p.K * p.NR;
         q.pi = p.pi;
@@ -358,6 +372,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     b.tot_na = na_off[n_plans];
     VMAT_TRY(b.get(&b.d_spmv, n_plans));
     VMAT_TRY(b.get(&b.d_price, n_plans));
+    VMAT_TRY(b.get(&b.d_win, n_plans));
     VMAT_TRY(b.get(&b.d_da, n_plans));
     VMAT_TRY(b.get(&b.d_obj, n_plans));
     VMAT_TRY(b.get(&b.d_commit, n_plans));
@@ -367,6 +382,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_TRY(b.get((char **)&b.d_mpargs, (size_t)n_plans * argb));
     VMAT_CUDA(cudaMemcpy(b.d_spmv, spmv.data(), n_plans * sizeof(SpmvPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_price, price.data(), n_plans * sizeof(PricePlan), cudaMemcpyHostToDevice));
+    VMAT_CUDA(cudaMemcpy(b.d_win, wins.data(), n_plans * sizeof(WinPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_da, da.data(), n_plans * sizeof(DaPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_obj, obj.data(), n_plans * sizeof(ObjPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_commit, com.data(), n_plans * sizeof(CommitPlan), cudaMemcpyHostToDevice));
@@ -418,7 +434,13 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaMemcpy(b.d_weight, weight.data(), n_plans * sizeof(int64_t), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemset(b.d_gctl, 0, 32));
 
-    // ---- autotune the batched D^T g over every warp-row configuration (all CPs active)
+    // ---- autotune the batched D^T g over every warp-row configuration (all CPs active:
+    // the windows of the empty state cover every row)
+    for (BPlan &p : b.P) {
+        VMAT_CUDA(cudaMemsetAsync(p.occupied, 0, p.K, s));
+        VMAT_CUDA(cudaMemsetAsync(p.ctl, 0, CTL_N * sizeof(int32_t), s));
+    }
+    VMAT_TRY(price_windows_batched(b.d_win, n_plans, b.max_K, 0, s));
     {
         cudaEvent_t e0, e1;
         VMAT_CUDA(cudaEventCreate(&e0));
@@ -426,9 +448,11 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         float best = 1e30f;
         for (int cfg = 0; cfg < spmv_n_configs() && cfg < 32; ++cfg) {  // warp-row families only
             if (!spmv_batched_config(cfg)) continue;
-            VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s)); // warm-up
+            VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s, b.cols.data(),
+                                       (int)b.cols.size())); // warm-up
             VMAT_CUDA(cudaEventRecord(e0, s));
-            VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s));
+            VMAT_TRY(spmv_rows_batched(b.dt, cfg, b.d_spmv, b.d_rows_off, n_plans, b.tot_rows, s, b.cols.data(),
+                                       (int)b.cols.size()));
             VMAT_CUDA(cudaEventRecord(e1, s));
             VMAT_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -535,20 +559,27 @@ vmat_status vmat_batch_run(vmat_batch hb, double *F_out, vmat_plan_stats *stats,
         const Ddc &h = *p.h;
         const int vb = value_bytes(h.dtype);
         const bool fp8 = h.dtype == VMAT_FP8E4M3;
+        std::vector<unsigned long long> wc((size_t)3 * std::max(p.n_ap, 1));
+        VMAT_CUDA(cudaMemcpy(wc.data(), p.wcount, wc.size() * 8, cudaMemcpyDeviceToHost));
         std::vector<char> occ(p.K, 0);
         const int n_pp1 = n_ap + (stop == VMAT_STOP_PRICE ? 1 : 0);
-        double pp1 = 0.0;
+        double pp1 = 0.0, pp1_full = 0.0;
         for (int t = 0; t < n_pp1; ++t) {
             double bb = 4.0 * p.V;
             for (int k = 0; k < p.K; ++k)
                 if (!occ[k])
                     bb += (double)(p.cpo[k + 1] - p.cpo[k]) * (vb + 4) + p.bpc * (8.0 + 4.0) + (fp8 ? 4.0 * p.bpc : 0.0);
-            pp1 += bb;
+            pp1_full += bb;
+            if (t < std::max(p.n_ap, 1)) {
+                const double rows = (double)wc[3 * t], nnz = (double)wc[3 * t + 1];
+                pp1 += 4.0 * p.V + 4.0 * p.K * p.NR + nnz * (vb + 4) + rows * (8.0 + 4.0) + (fp8 ? 4.0 * rows : 0.0);
+            }
             if (t < n_ap) occ[cps[t]] = 1;
         }
         st.t_total_ms = ms;
         st.pp1_spmv_launches = n_pp1;
         st.pp1_spmv_bytes = pp1;
+        st.pp1_full_bytes = pp1_full;
         st.other_spmv_bytes = csr_pass_bytes(h.D.cfg, vb, (double)h.D.nnz, h.D.n_rows + 1.0, (double)h.D.n_chunks) +
                               4.0 * p.J + 4.0 * p.V + (fp8 ? 4.0 * p.J : 0.0);
         st.n_apertures = n_ap;

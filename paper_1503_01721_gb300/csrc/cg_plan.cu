@@ -168,6 +168,14 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&F0, 2));
     VMAT_TRY(ar.get((char **)&obj_ws, objective_scratch_bytes(ctx->n_sm)));
     VMAT_TRY(ar.get((char **)&pr_ws, pricing_scratch_bytes(mlc)));
+    // leaf-travel windows of every (CP, MLC row) before each D^T g, and the rows,
+    // nonzeros and 16-bit-index chunks inside them per pass
+    PricingGeom pg;
+    VMAT_TRY(pricing_geom(mlc, &pg));
+    short2 *win;
+    unsigned long long *wcount;
+    VMAT_TRY(ar.get(&win, (size_t)K * NR));
+    VMAT_TRY(ar.get(&wcount, (size_t)3 * nap_max));
     const long long launches0 = g_launches.load();
     PhaseTimer tm(stats != nullptr, s);
     cudaEvent_t t0, t1;
@@ -182,6 +190,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_CUDA(cudaMemsetAsync(occupied, 0, K, s));
     VMAT_CUDA(cudaMemsetAsync(leaves_all, 0, (size_t)K * NR * 4, s));
     VMAT_CUDA(cudaMemsetAsync(obj_ws, 0, 64, s));
+    VMAT_CUDA(cudaMemsetAsync(wcount, 0, (size_t)3 * nap_max * 8, s));
     fill_u8<<<std::max(1, (K + 255) / 256), 256, 0, s>>>(active, K, 1);
     VMAT_LAUNCH_CHECK();
     fill_i32<<<1, 256, 0, s>>>(cps_dev, nap_max, -1);
@@ -249,8 +258,12 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         tm.mark(PH_PP1);
         if (NA > 0)
             VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s, ctl));
+        // prices only where pricing reads them: the columns of each row's window
+        VMAT_TRY(price_windows(pg, occupied, leaves_all, win, h.Dt.rowptr, z_dt ? h.Dt.cptr : nullptr,
+                               t < nap_max ? wcount + 3 * t : nullptr, ctl, s));
         tm.mark(PH_SPMV);
-        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, active, bpc, s, ctl));
+        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr,
+                          RowMask{nullptr, win, bpc, mlc->n_cols}, s, ctl));
         ++spmv_launches;
         // ---- PP2, and the commit (or the stop) on the device
         tm.mark(PH_PP2);
@@ -296,10 +309,14 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     const int bb_total = hctl[CTL_BBITERS] + bb_extra;
     std::vector<int32_t> cps_host(std::max(n_ap, 1));
     if (n_ap > 0) VMAT_CUDA(cudaMemcpy(cps_host.data(), cps_dev, (size_t)n_ap * 4, cudaMemcpyDeviceToHost));
-    // the format's own bytes of each pricing pass (rows of the CPs unoccupied at that
-    // pass, plus g once) and of the final D x
-    double pp1_bytes = 0.0, other_bytes = bytes_D_full;
+    // the format's own bytes of each pricing pass (the rows inside the windows, the
+    // window table, g once) and of the final D x; pp1_full_bytes: the same passes over
+    // every row of the CPs unoccupied at that pass
+    double pp1_bytes = 0.0, pp1_full = 0.0, other_bytes = bytes_D_full;
     {
+        std::vector<unsigned long long> wc((size_t)3 * nap_max);
+        VMAT_CUDA(cudaMemcpy(wc.data(), wcount, wc.size() * 8, cudaMemcpyDeviceToHost));
+        const double fp8_row = h.dtype == VMAT_FP8E4M3 ? 4.0 : 0.0;
         std::vector<char> occ(K, 0);
         const int n_pp1 = n_ap + (stop == VMAT_STOP_PRICE ? 1 : 0);
         for (int t = 0; t < n_pp1; ++t) {
@@ -308,8 +325,13 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
                 if (!occ[kk])
                     b += csr_pass_bytes(h.Dt.cfg, vb, (double)(cpo[kk + 1] - cpo[kk]), (double)bpc,
                                         (double)(cco[kk + 1] - cco[kk])) +
-                         4.0 * bpc + (h.dtype == VMAT_FP8E4M3 ? 4.0 * bpc : 0.0);
-            pp1_bytes += b;
+                         (4.0 + fp8_row) * bpc;
+            pp1_full += b;
+            if (t < nap_max) {
+                const double rows = (double)wc[3 * t], nnz = (double)wc[3 * t + 1], ch = (double)wc[3 * t + 2];
+                pp1_bytes += 4.0 * V + 4.0 * K * NR + csr_pass_bytes(h.Dt.cfg, vb, nnz, rows, ch) +
+                             (4.0 + fp8_row) * rows;
+            }
             if (t < n_ap) occ[cps_host[t]] = 1;
         }
         spmv_launches = n_pp1;
@@ -346,6 +368,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         stats->t_final_ms = acc[PH_FINAL];
         stats->pp1_spmv_launches = spmv_launches;
         stats->pp1_spmv_bytes = pp1_bytes;
+        stats->pp1_full_bytes = pp1_full;
         stats->other_spmv_bytes = other_bytes;
         stats->n_apertures = n_ap;
         stats->bb_iters_total = bb_total;

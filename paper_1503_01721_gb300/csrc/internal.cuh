@@ -133,10 +133,34 @@ inline Ddc *as_ddc(vmat_ddc h) { return reinterpret_cast<Ddc *>(h); }
 // ---------------------------------------------------------------------------
 int value_bytes(vmat_dtype t);
 
-// SpMV on one CSR; x/y device.  cp_active/bpc restrict to rows of active CPs (may be null).
+// The rows of a CSR(D^T) pass a caller needs (every row when both pointers are null).
+// cp_active: row r belongs to CP r / bpc and is needed only when that CP's flag is set.
+// win: row r is beamlet column c = r % n_cols of MLC-row segment q = r / n_cols (CP
+// q / n_rows, MLC row q % n_rows) and is needed only when win[q].x <= c < win[q].y:
+// the columns that the leaf-travel windows let pricing read (price_windows).
+// Rows not needed are not computed: y holds unspecified values there (the tile
+// configurations write every row of a tile that holds a needed row).
+struct RowMask {
+    const uint8_t *cp_active;
+    const short2 *win;
+    int32_t bpc;
+    int32_t n_cols;
+};
+inline RowMask all_rows() { return RowMask{nullptr, nullptr, 1, 1}; }
+__device__ __forceinline__ bool row_needed(const RowMask &m, int64_t r) {
+    if (m.cp_active && !m.cp_active[r / m.bpc]) return false;
+    if (m.win) {
+        const int32_t q = (int32_t)r / m.n_cols, c = (int32_t)r - q * m.n_cols;
+        const short2 w = __ldg(m.win + q);
+        return c >= w.x && c < w.y;
+    }
+    return true;
+}
+
+// SpMV on one CSR; x/y device.  mask: the rows to compute (all_rows(): every row).
 // skip (may be null): a device flag; when set at run time the kernels do nothing.
-vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
-                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s, const int32_t *skip = nullptr);
+vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale, RowMask mask,
+                     cudaStream_t s, const int32_t *skip = nullptr);
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s);
 // Does configuration cfg read the 16-bit column index (and so need m.col16)?
 bool spmv_config_index16(int cfg);
@@ -170,11 +194,10 @@ struct SpmvPlan { // one plan's matrix and vectors in a batched warp-row SpMV
     const void *val;
     const float *x;
     float *y;
-    const float *row_scale;   // or null
-    const int32_t *row_ids;   // or null
-    const uint8_t *cp_active; // or null
-    const int32_t *skip;      // or null
-    int32_t bpc;
+    const float *row_scale; // or null
+    const int32_t *row_ids; // or null
+    RowMask mask;           // the rows to compute
+    const int32_t *skip;    // or null
     int32_t n_rows;
 };
 bool spmv_batched_config(int cfg);
@@ -189,6 +212,25 @@ constexpr int INTERDIG_MAX_COLS = 88; // the chain DP holds (n_cols + 1)^2 state
 vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g);
 size_t pricing_scratch_bytes(const vmat_mlc *mlc);
 vmat_status pricing_attributes(); // raises the kernels' shared-memory limits (not a stream operation)
+// Leaf-travel windows of every MLC row of every CP (Section 2.2.2, reading R7): win[k *
+// n_rows + r] = [Lmin, max(Lmin, Rmax)), the columns any feasible opening of that row
+// covers, empty for occupied CPs.  counts (may be null): adds the rows, CSR(D^T)
+// nonzeros (rowptr) and 16-bit-index chunks (cptr, may be null) inside the windows to
+// counts[0..2].  skip as for the pricing kernels.
+vmat_status price_windows(const PricingGeom &g, const uint8_t *occupied, const int16_t *leaves, short2 *win,
+                          const int64_t *rowptr, const int64_t *cptr, unsigned long long *counts,
+                          const int32_t *skip, cudaStream_t s);
+struct WinPlan { // one plan's window inputs and outputs in a batched launch
+    PricingGeom g;
+    const uint8_t *occupied;
+    const int16_t *leaves;
+    short2 *win;
+    const int64_t *rowptr;
+    unsigned long long *counts; // [iterations][3], iteration t at counts + 3 t
+    const int32_t *skip;
+};
+// Iteration t of every plan of a batch (max_K: largest K).
+vmat_status price_windows_batched(const WinPlan *plans, int32_t n_plans, int32_t max_K, int32_t t, cudaStream_t s);
 // One plan's pricing (either variant) with scratch ws of pricing_scratch_bytes(mlc);
 // skip (may be null): a device word, nonzero = leave the outputs untouched.
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
@@ -262,8 +304,10 @@ vmat_status objective_grad_batched(const ObjPlan *plans, const int64_t *off, int
 // (interdigitation plans of a batch are priced on their own).
 vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
                                     int32_t max_cols, cudaStream_t s);
+// cols (host, may be null): the plans' MLC column counts (n_cols entries); the row
+// stride is chosen coprime with each so that windowed passes stay balanced.
 vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
-                              int64_t total_rows, cudaStream_t s);
+                              int64_t total_rows, cudaStream_t s, const int32_t *cols = nullptr, int n_cols = 0);
 
 // Objective over n voxels.  idx (may be null): voxel i of z is voxel idx[i] of struct_id.
 // g_scatter (may be null): write g[i] to g_scatter[idx[i]] instead of g[i].

@@ -61,6 +61,50 @@ __device__ int nearest_occupied(const PricingGeom &g, const uint8_t *occupied, i
     return -1;
 }
 
+// The same search by one thread.
+__device__ int nearest_occupied_seq(const PricingGeom &g, const uint8_t *occupied, int k, int dir) {
+    int a = 0;
+    while (a + 1 < g.n_arcs && g.arc_first[a + 1] <= k) ++a;
+    const int lo = g.arc_first[a], hi = g.arc_first[a + 1];
+    for (int kk = k + dir; kk >= lo && kk < hi; kk += dir)
+        if (occupied[kk]) return kk;
+    return -1;
+}
+
+// Leaf-travel window of MLC row r at CP k (reading R7): each leaf moves at most
+// travel columns per CP step from its position at the nearest occupied CP on each
+// side (kl, kr; -1: none).
+struct RowWindow {
+    int Lmin, Lmax, Rmin, Rmax;
+};
+__device__ __forceinline__ RowWindow row_window(const PricingGeom &g, const int16_t *__restrict__ leaves, int k,
+                                                int r, int kl, int kr) {
+    RowWindow w{0, g.n_cols, 0, g.n_cols};
+    for (int side = 0; side < 2; ++side) {
+        const int kk = side ? kr : kl;
+        if (kk < 0) continue;
+        const int reach = abs(k - kk) * g.travel;
+        const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
+        w.Lmin = max(w.Lmin, Ln - reach);
+        w.Lmax = min(w.Lmax, Ln + reach);
+        w.Rmin = max(w.Rmin, Rn - reach);
+        w.Rmax = min(w.Rmax, Rn + reach);
+    }
+    return w;
+}
+
+// Float64 prefix sums of one MLC row's prices over its window (reading R8): P_c = 0
+// for c <= Lmin, P_{c+1} = P_c + pi_c for Lmin <= c < Rmax, constant after Rmax, in
+// column order.  Prices outside [Lmin, Rmax) are never read.
+__device__ __forceinline__ void window_prefix(const float *__restrict__ row, int N, int Lmin, int Rmax, double *P) {
+    double acc = 0.0;
+    P[0] = 0.0;
+    for (int c = 0; c < N; ++c) {
+        if (c >= Lmin && c < Rmax) acc = acc + (double)row[c];
+        P[c + 1] = acc;
+    }
+}
+
 // Shared memory per warp of the row kernel: the float64 prefix sums and their
 // float32 roundings, n_cols + 1 of each.
 __host__ __device__ constexpr size_t row_smem_stride(int n_cols) { return (((size_t)(n_cols + 1) * 12) + 15) & ~15; }
@@ -87,27 +131,10 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
     const int N = g.n_cols;
     double *P = reinterpret_cast<double *>(ws);
     float *P32 = reinterpret_cast<float *>(ws + (size_t)(N + 1) * 8);
-    int Lmin = 0, Lmax = N, Rmin = 0, Rmax = N;
-    for (int dir = -1; dir <= 1; dir += 2) {
-        const int kk = nearest_occupied(g, occupied, k, dir, lane);
-        if (kk >= 0) {
-            const int reach = abs(k - kk) * g.travel;
-            const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
-            Lmin = max(Lmin, Ln - reach);
-            Lmax = min(Lmax, Ln + reach);
-            Rmin = max(Rmin, Rn - reach);
-            Rmax = min(Rmax, Rn + reach);
-        }
-    }
-    if (lane == 0) {
-        const float *row = pi + ((int64_t)k * g.n_rows + r) * N;
-        double acc = 0.0;
-        P[0] = 0.0;
-        for (int c = 0; c < N; ++c) {
-            acc = acc + (double)row[c];
-            P[c + 1] = acc;
-        }
-    }
+    const int kl = nearest_occupied(g, occupied, k, -1, lane), kr = nearest_occupied(g, occupied, k, 1, lane);
+    const RowWindow win = row_window(g, leaves, k, r, kl, kr);
+    const int Lmin = win.Lmin, Lmax = win.Lmax, Rmin = win.Rmin, Rmax = win.Rmax;
+    if (lane == 0) window_prefix(pi + ((int64_t)k * g.n_rows + r) * N, N, Lmin, Rmax, P);
     __syncwarp();
     float pmax = 0.f;
     for (int c = lane; c <= N; c += 32) {
@@ -307,25 +334,86 @@ __host__ __device__ constexpr size_t interdig_smem(int N) {
     return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4 + 4 + 2) + 64;
 }
 
-// Prefix sums of every MLC row of every unoccupied CP (a thread per row, float64
-// in column order, as the definition), for the chain kernels.
+// Window prefix sums of every MLC row of every unoccupied CP (a thread per row,
+// float64 in column order, as the definition), for the chain kernels.
 __global__ void interdig_prefix_kernel(PricingGeom g, const float *__restrict__ pi,
-                                       const uint8_t *__restrict__ occupied, double *__restrict__ Pall,
-                                       const int32_t *skip) {
+                                       const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
+                                       double *__restrict__ Pall, const int32_t *skip) {
     if (skip && *skip) return;
     const int N = g.n_cols;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < (int64_t)g.K * g.n_rows;
          row += (int64_t)gridDim.x * blockDim.x) {
-        if (occupied[row / g.n_rows]) continue;
-        const float *src = pi + row * N;
-        double *P = Pall + row * (N + 1);
-        double acc = 0.0;
-        P[0] = 0.0;
-        for (int c = 0; c < N; ++c) {
-            acc = acc + (double)src[c];
-            P[c + 1] = acc;
+        const int k = (int)(row / g.n_rows), r = (int)(row % g.n_rows);
+        if (occupied[k]) continue;
+        const RowWindow w = row_window(g, leaves, k, r, nearest_occupied_seq(g, occupied, k, -1),
+                                       nearest_occupied_seq(g, occupied, k, 1));
+        window_prefix(pi + row * N, N, w.Lmin, w.Rmax, Pall + row * (N + 1));
+    }
+}
+
+// Windows of one CP (a warp): [Lmin, max(Lmin, Rmax)) per MLC row, empty when the CP
+// is occupied; the rows, nonzeros and chunks inside them added to counts.
+__device__ __forceinline__ void cp_windows_warp(const PricingGeom &g, const uint8_t *__restrict__ occupied,
+                                                const int16_t *__restrict__ leaves, int k, short2 *win,
+                                                const int64_t *__restrict__ rowptr, const int64_t *__restrict__ cptr,
+                                                unsigned long long *counts) {
+    const int lane = threadIdx.x & 31;
+    const bool occ = occupied[k] != 0;
+    int kl = -1, kr = -1;
+    if (!occ) {
+        kl = nearest_occupied(g, occupied, k, -1, lane);
+        kr = nearest_occupied(g, occupied, k, 1, lane);
+    }
+    unsigned long long rows = 0, nnz = 0, chunks = 0;
+    for (int r = lane; r < g.n_rows; r += 32) {
+        int lo = 0, hi = 0;
+        if (!occ) {
+            const RowWindow w = row_window(g, leaves, k, r, kl, kr);
+            lo = w.Lmin;
+            hi = max(w.Lmin, w.Rmax);
+        }
+        const int64_t q = (int64_t)k * g.n_rows + r;
+        win[q] = make_short2((short)lo, (short)hi);
+        if (counts && hi > lo) {
+            const int64_t b = q * g.n_cols;
+            rows += (unsigned long long)(hi - lo);
+            nnz += (unsigned long long)(rowptr[b + hi] - rowptr[b + lo]);
+            if (cptr) chunks += (unsigned long long)(cptr[b + hi] - cptr[b + lo]);
         }
     }
+    if (!counts) return;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        rows += __shfl_xor_sync(0xffffffffu, rows, d);
+        nnz += __shfl_xor_sync(0xffffffffu, nnz, d);
+        chunks += __shfl_xor_sync(0xffffffffu, chunks, d);
+    }
+    if (lane == 0 && rows > 0) {
+        atomicAdd(counts, rows);
+        atomicAdd(counts + 1, nnz);
+        atomicAdd(counts + 2, chunks);
+    }
+}
+
+constexpr int WIN_WARPS = 4;
+
+__global__ void __launch_bounds__(WIN_WARPS * 32)
+    price_windows_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
+                         short2 *win, const int64_t *__restrict__ rowptr, const int64_t *__restrict__ cptr,
+                         unsigned long long *counts, const int32_t *skip) {
+    if (skip && *skip) return;
+    const int k = blockIdx.x * WIN_WARPS + (threadIdx.x >> 5);
+    if (k >= g.K) return; // warp-uniform
+    cp_windows_warp(g, occupied, leaves, k, win, rowptr, cptr, counts);
+}
+
+__global__ void __launch_bounds__(WIN_WARPS * 32)
+    price_windows_batched_kernel(const WinPlan *__restrict__ plans, int32_t t) {
+    const WinPlan &P = plans[blockIdx.y];
+    if (P.skip && *P.skip) return;
+    const int k = blockIdx.x * WIN_WARPS + (threadIdx.x >> 5);
+    if (k >= P.g.K) return; // warp-uniform
+    cp_windows_warp(P.g, P.occupied, P.leaves, k, P.win, P.rowptr, nullptr, P.counts ? P.counts + 3 * (int64_t)t : nullptr);
 }
 
 // Inclusive "best so far" scans of n_lines lines of n = N + 1 states each, four
@@ -418,18 +506,8 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
     }
     __syncthreads();
     for (int r = 0; r < g.n_rows; ++r) {
-        int Lmin = 0, Lmax = N, Rmin = 0, Rmax = N;
-        for (int side = 0; side < 2; ++side) {
-            const int kk = kk_s[side];
-            if (kk >= 0) {
-                const int reach = abs(k - kk) * g.travel;
-                const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
-                Lmin = max(Lmin, Ln - reach);
-                Lmax = min(Lmax, Ln + reach);
-                Rmin = max(Rmin, Rn - reach);
-                Rmax = min(Rmax, Rn + reach);
-            }
-        }
+        const RowWindow w = row_window(g, leaves, k, r, kk_s[0], kk_s[1]);
+        const int Lmin = w.Lmin, Lmax = w.Lmax, Rmin = w.Rmin, Rmax = w.Rmax;
         const double *P = Pall + ((int64_t)k * g.n_rows + r) * (N + 1);
         if (r > 0) {
             // C[L][b] = best state (L, R), R >= b (suffix over R), then in place
@@ -567,6 +645,25 @@ vmat_status pricing_geom(const vmat_mlc *mlc, PricingGeom *g) {
     return VMAT_OK;
 }
 
+vmat_status price_windows(const PricingGeom &g, const uint8_t *occupied, const int16_t *leaves, short2 *win,
+                          const int64_t *rowptr, const int64_t *cptr, unsigned long long *counts,
+                          const int32_t *skip, cudaStream_t s) {
+    if (g.K < 1) return VMAT_OK;
+    price_windows_kernel<<<(g.K + WIN_WARPS - 1) / WIN_WARPS, WIN_WARPS * 32, 0, s>>>(g, occupied, leaves, win, rowptr,
+                                                                                   cptr, counts, skip);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status price_windows_batched(const WinPlan *plans, int32_t n_plans, int32_t max_K, int32_t t, cudaStream_t s) {
+    if (n_plans < 1 || n_plans > VMAT_MAX_BATCH || max_K < 1)
+        return set_error(VMAT_EINVAL, "price_windows_batched: bad plan count or K");
+    price_windows_batched_kernel<<<dim3((max_K + WIN_WARPS - 1) / WIN_WARPS, n_plans), WIN_WARPS * 32, 0, s>>>(plans,
+                                                                                                            t);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
 // Dynamic shared-memory limits of the pricing kernels, raised once per process for
 // their largest MLC (1024 columns; the interdigitation kernel's own column limit).
 // Not a stream operation: callers that record a CUDA graph call it before capture.
@@ -622,7 +719,7 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         VMAT_TRY(pricing_attributes());
         const int64_t rows = (int64_t)g.K * g.n_rows;
         interdig_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
-                                 s>>>(g, pi, occupied, Pall, skip);
+                                 s>>>(g, pi, occupied, leaves, Pall, skip);
         VMAT_LAUNCH_CHECK();
         price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, Pall, occupied, leaves, cp_val, cp_ok, pred_all,
                                                                skip);

@@ -389,9 +389,9 @@ struct RowParams {
     float *y;
     const float *row_scale;
     const int32_t *row_ids;
-    const uint8_t *cp_active; // skip rows r with !cp_active[r / bpc], or null
-    int32_t bpc;
+    RowMask mask; // the rows to compute
     int32_t n_rows;
+    int64_t stride; // rows between a warp's consecutive rows (<= the launch's warps; warps past it idle)
     const int32_t *skip; // when non-null and set, the kernel does nothing
     const uint16_t *col16; // 16-bit column index (configurations that read it)
     const int32_t *cbase;
@@ -519,10 +519,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_z_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
-        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
+        if (!row_needed(p.mask, r)) continue;
         float sum = warp_row_sum_z<UNROLL, VT>(p.rowptr, p.cptr, p.cbase, p.col16, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -536,10 +536,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_c_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
-        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
+        if (!row_needed(p.mask, r)) continue;
         float sum = warp_row_sum_c<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -553,10 +553,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += n_warps) {
-        if (p.cp_active && !p.cp_active[r / p.bpc]) continue;
+    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
+        if (!row_needed(p.mask, r)) continue;
         float sum = warp_row_sum<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -571,18 +571,18 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
 template <int THREADS, int UNROLL, typename VT, bool CONSEC>
 __global__ void __launch_bounds__(THREADS)
     spmv_rows_batched_kernel(const SpmvPlan *__restrict__ plans, const int64_t *__restrict__ row_off, int32_t n_plans,
-                             int64_t total_rows) {
+                             int64_t total_rows, int64_t stride) {
     __shared__ int64_t soff[VMAT_MAX_BATCH + 1];
     for (int i = threadIdx.x; i <= n_plans; i += THREADS) soff[i] = row_off[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * THREADS) >> 5;
+    if (warp0 >= stride) return; // warp-uniform, after the block's only barrier
     const uint64_t pol = l2_evict_first_policy();
     int64_t lo = 0, hi = 0;
     SpmvPlan P;
     bool skip = true;
-    for (int64_t gr = warp0; gr < total_rows; gr += n_warps) {
+    for (int64_t gr = warp0; gr < total_rows; gr += stride) {
         if (gr < lo || gr >= hi) {
             int a = 0, b = n_plans; // soff[a] <= gr < soff[b]
             while (b - a > 1) {
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(THREADS)
         }
         if (skip) continue;
         const int64_t r = gr - lo;
-        if (P.cp_active && !P.cp_active[r / P.bpc]) continue;
+        if (!row_needed(P.mask, r)) continue;
         float sum = CONSEC ? warp_row_sum_c<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol)
                            : warp_row_sum<UNROLL, VT>(P.rowptr, P.col, P.val, P.x, r, lane, pol);
         if (lane == 0) {
@@ -608,17 +608,17 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // Adds tile carries to their rows.  Tile b's carry belongs to row tile_row[b + 1];
-// the first tile of each run of equal keys sums the run left to right.  Rows of
-// inactive CPs are skipped (their tiles may not have run).
+// the first tile of each run of equal keys sums the run left to right.  Rows not in
+// the mask are skipped (their tiles may not have run).
 __global__ void spmv_fixup(const int32_t *tile_row, const float *carry_val, int32_t n_tiles,
                            const int32_t *tile_list, const int32_t *n_list, int32_t n_rows, float *y,
-                           const int32_t *row_ids, const float *row_scale, const uint8_t *cp_active, int32_t bpc) {
+                           const int32_t *row_ids, const float *row_scale, RowMask mask) {
     const int32_t n_work = tile_list ? *n_list : n_tiles;
     for (int32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
         const int32_t b = tile_list ? tile_list[w] : w;
         const int32_t key = tile_row[b + 1];
         if (key >= n_rows) continue;
-        if (cp_active && !cp_active[key / bpc]) continue;
+        if (!row_needed(mask, key)) continue;
         if (b > 0 && tile_row[b] == key) continue;
         float sum = carry_val[b];
         for (int32_t bb = b + 1; bb < n_tiles && tile_row[bb + 1] == key; ++bb) sum += carry_val[bb];
@@ -646,14 +646,18 @@ __global__ void compute_tile_rows(const int64_t *rowptr, int32_t n_rows, int32_t
     }
 }
 
-// A tile is active when its row range [tile_row[b], tile_row[b+1]] meets a row of an active CP.
-__global__ void flag_active_tiles(const int32_t *tile_row, int32_t n_tiles, int32_t n_rows, const uint8_t *cp_active,
-                                  int32_t bpc, int32_t *flag) {
+// A tile is active when its row range [tile_row[b], tile_row[b+1]] meets a row in the mask.
+__global__ void flag_active_tiles(const int32_t *tile_row, int32_t n_tiles, int32_t n_rows, RowMask mask,
+                                  int32_t *flag) {
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_tiles; b += gridDim.x * blockDim.x) {
         const int32_t r0 = tile_row[b];
         const int32_t r1 = min(tile_row[b + 1], n_rows - 1);
         int32_t f = 0;
-        for (int32_t k = r0 / bpc; k <= r1 / bpc && !f; ++k) f = cp_active[k] != 0;
+        if (mask.win) {
+            for (int32_t r = r0; r <= r1 && !f; ++r) f = row_needed(mask, r) ? 1 : 0;
+        } else {
+            for (int32_t k = r0 / mask.bpc; k <= r1 / mask.bpc && !f; ++k) f = mask.cp_active[k] != 0;
+        }
         flag[b] = f;
     }
 }
@@ -685,7 +689,30 @@ constexpr int N_CFG = 15;
 
 using TileFn = void (*)(SpmvParams);
 using RowFn = void (*)(RowParams);
-using RowBatchFn = void (*)(const SpmvPlan *, const int64_t *, int32_t, int64_t);
+using RowBatchFn = void (*)(const SpmvPlan *, const int64_t *, int32_t, int64_t, int64_t);
+
+static int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Row stride of a warp-row launch with n_warps warps: the largest s <= n_warps that
+// is coprime with every MLC column count in cols[0..n).  A warp's rows r, r + s, ...
+// then cycle through every beamlet column instead of keeping one (n_warps is a
+// multiple of the warps per block, and so often of n_cols), which keeps the warps
+// balanced when the leaf-travel windows leave whole columns out of a pass.
+static int64_t coprime_stride(int64_t n_warps, const int32_t *cols, int n) {
+    for (int64_t st = n_warps; st > n_warps / 2 && st > 1; --st) {
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) ok = cols[i] <= 1 || gcd64(st, cols[i]) == 1;
+        if (ok) return st;
+    }
+    return std::max<int64_t>(n_warps, 1);
+}
 
 template <typename VT> TileFn tile_kernel_for(int cfg) {
     switch (cfg) {
@@ -809,8 +836,8 @@ vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s) {
     return VMAT_OK;
 }
 
-vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale,
-                     const uint8_t *cp_active, int32_t bpc, cudaStream_t s, const int32_t *skip) {
+vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale, RowMask mask,
+                     cudaStream_t s, const int32_t *skip) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     Launch L;
@@ -824,8 +851,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
         p.y = y;
         p.row_scale = row_scale;
         p.row_ids = m.row_ids;
-        p.cp_active = cp_active;
-        p.bpc = bpc;
+        p.mask = mask;
         p.n_rows = m.n_rows;
         p.skip = skip;
         p.col16 = m.col16;
@@ -836,17 +862,19 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
         const int64_t warps = std::max<int64_t>(1, m.n_rows);
         const int64_t want = (warps * 32 + L.threads - 1) / L.threads;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * L.blocks_per_sm));
+        const int64_t n_warps = (int64_t)grid * L.threads / 32;
+        p.stride = mask.win ? coprime_stride(n_warps, &mask.n_cols, 1) : n_warps;
         L.row<<<grid, L.threads, 0, s>>>(p);
         VMAT_LAUNCH_CHECK();
         return VMAT_OK;
     }
     const int32_t *list = nullptr;
     int32_t *n_list = nullptr;
-    if (cp_active) {
+    if (mask.cp_active || mask.win) {
         // ordered list of active tiles: flags, exclusive scan, compaction
         int64_t *off = reinterpret_cast<int64_t *>(m.n_list + 2);
         int g = std::max(1, std::min(ctx->n_sm * 8, (m.n_tiles + 255) / 256));
-        flag_active_tiles<<<g, 256, 0, s>>>(m.tile_row, m.n_tiles, m.n_rows, cp_active, bpc, m.tile_flag);
+        flag_active_tiles<<<g, 256, 0, s>>>(m.tile_row, m.n_tiles, m.n_rows, mask, m.tile_flag);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(scan_counts(m.tile_flag, off, m.n_tiles, s));
         compact_tiles<<<g, 256, 0, s>>>(m.tile_flag, off, m.n_tiles, m.tile_list, m.n_list);
@@ -876,7 +904,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
     VMAT_LAUNCH_CHECK();
     const int gf = std::max(1, std::min(ctx->n_sm * 4, (m.n_tiles + 255) / 256));
     spmv_fixup<<<gf, 256, 0, s>>>(m.tile_row, m.carry_val, m.n_tiles, list, n_list, m.n_rows, y, m.row_ids,
-                                  row_scale, cp_active, bpc);
+                                  row_scale, mask);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }
@@ -900,7 +928,7 @@ bool spmv_batched_config(int cfg) {
 }
 
 vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, const int64_t *row_off, int32_t n_plans,
-                              int64_t total_rows, cudaStream_t s) {
+                              int64_t total_rows, cudaStream_t s, const int32_t *cols, int n_cols) {
     if (!spmv_batched_config(cfg)) return set_error(VMAT_EINVAL, "spmv_rows_batched: configuration %d is not warp-row", cfg);
     if (n_plans < 1 || n_plans > VMAT_MAX_BATCH) return set_error(VMAT_EINVAL, "spmv_rows_batched: bad plan count");
     if (total_rows <= 0) return VMAT_OK;
@@ -914,7 +942,8 @@ vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, con
     VMAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, 0));
     const int64_t want = (total_rows * 32 + threads - 1) / threads;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * std::max(bps, 1)));
-    fn<<<grid, threads, 0, s>>>(plans, row_off, n_plans, total_rows);
+    fn<<<grid, threads, 0, s>>>(plans, row_off, n_plans, total_rows,
+                                coprime_stride((int64_t)grid * threads / 32, cols, cols ? n_cols : 0));
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }
@@ -931,10 +960,10 @@ vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compa
     if (compact) {
         CsrMat m = h.D;
         m.row_ids = nullptr;
-        return spmv_run(h, m, xin, d, nullptr, nullptr, 1, s);
+        return spmv_run(h, m, xin, d, nullptr, all_rows(), s);
     }
     VMAT_CUDA(cudaMemsetAsync(d, 0, (size_t)h.V * 4, s));
-    return spmv_run(h, h.D, xin, d, nullptr, nullptr, 1, s);
+    return spmv_run(h, h.D, xin, d, nullptr, all_rows(), s);
 }
 
 vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
@@ -960,7 +989,7 @@ vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
             float ms_total = 0.f;
             for (int rep = 0; rep < 6; ++rep) {
                 cudaEventRecord(a, s);
-                st = isDt ? spmv_run(h, *m, x, y, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, nullptr, 1, s)
+                st = isDt ? spmv_run(h, *m, x, y, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, all_rows(), s)
                           : dose_forward_impl(h, x, y, false, s);
                 cudaEventRecord(b, s);
                 cudaEventSynchronize(b);
@@ -1006,8 +1035,28 @@ vmat_status beamlet_price(vmat_ddc hd, const float *g, float *pi, const uint8_t 
     if (!h->built_Dt) return set_error(VMAT_ESTATE, "beamlet_price: CSR(D^T) not built");
     if (cp_active && (beamlets_per_cp <= 0 || h->J % beamlets_per_cp != 0))
         return set_error(VMAT_EINVAL, "beamlet_price: beamlets_per_cp (%d) must divide J (%d)", beamlets_per_cp, h->J);
-    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr, cp_active,
-                    cp_active ? beamlets_per_cp : 1, as_stream(stream));
+    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
+                    RowMask{cp_active, nullptr, cp_active ? beamlets_per_cp : 1, 1}, as_stream(stream));
+}
+
+vmat_status beamlet_price_windowed(vmat_ddc hd, const vmat_mlc *mlc, const uint8_t *occupied, const int16_t *leaves,
+                                   const float *g, float *pi, void *stream) {
+    clear_error();
+    if (!hd || !g || !pi || !occupied || !leaves) return set_error(VMAT_EINVAL, "beamlet_price_windowed: NULL argument");
+    VMAT_TRY(validate_mlc(mlc));
+    Ddc *h = as_ddc(hd);
+    if (!h->built_Dt) return set_error(VMAT_ESTATE, "beamlet_price_windowed: CSR(D^T) not built");
+    if ((int64_t)mlc->K * mlc->n_rows * mlc->n_cols != h->J)
+        return set_error(VMAT_EINVAL, "beamlet_price_windowed: K*n_rows*n_cols != J");
+    PricingGeom pg;
+    VMAT_TRY(pricing_geom(mlc, &pg));
+    cudaStream_t s = as_stream(stream);
+    Scratch ws;
+    VMAT_TRY(ws.alloc((size_t)mlc->K * mlc->n_rows * sizeof(short2), s));
+    short2 *win = static_cast<short2 *>(ws.ptr);
+    VMAT_TRY(price_windows(pg, occupied, leaves, win, h->Dt.rowptr, nullptr, nullptr, nullptr, s));
+    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
+                    RowMask{nullptr, win, mlc->n_rows * mlc->n_cols, mlc->n_cols}, s);
 }
 
 } // extern "C"

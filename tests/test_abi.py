@@ -57,6 +57,7 @@ def test_host_validation_errors(lib):
     assert lib.ddc_build(None, None, None) == _lib.VMAT_EINVAL
     assert lib.dose_forward(None, None, None, None) == _lib.VMAT_EINVAL
     assert lib.beamlet_price(None, None, None, None, 0, None) == _lib.VMAT_EINVAL
+    assert lib.beamlet_price_windowed(None, None, None, None, None, None, None) == _lib.VMAT_EINVAL
     assert lib.ddc_free(None) == _lib.VMAT_OK
     # MLC checks: arcs must start at CP 0 and increase
     arcs = (ctypes.c_int32 * 2)(1, 3)

@@ -225,6 +225,50 @@ def test_cp_active_restricts_rows():
     assert np.all(np.abs(pi[rows] - pi_ref[rows]) <= bound[rows])
 
 
+def _placed_state(mlc, rng, n_placed):
+    """n_placed occupied CPs with random openings (L <= R) on every row."""
+    occupied = np.zeros(mlc.K, bool)
+    occupied[rng.choice(mlc.K, n_placed, replace=False)] = True
+    L = rng.integers(0, mlc.n_cols + 1, size=(mlc.K, mlc.n_rows))
+    W = rng.integers(0, mlc.n_cols // 2 + 1, size=(mlc.K, mlc.n_rows))
+    leaves = np.stack([L, np.minimum(L + W, mlc.n_cols)], axis=2) * occupied[:, None, None]
+    return occupied, leaves.astype(np.int64)
+
+
+@pytest.mark.parametrize("cfg", list(range(N_SPMV_CFG)))
+def test_windowed_price_every_config(cfg):
+    """beamlet_price_windowed: inside the leaf-travel windows of the unoccupied CPs
+    (the oracle's windows) bit-identical to the full pass of the same
+    configuration; the row configurations leave every other entry unwritten."""
+    from paper_1503_01721_gb300 import api
+    for name, seed, n_placed in (("ragged", 1, 3), ("cfg1", 0, 9)):
+        c = synth.make_case(name, seed=seed)
+        m = c.mlc
+        ddc = make_ddc(c, tile_cfg=cfg)
+        rng = np.random.default_rng(40 + cfg)
+        occupied, leaves = _placed_state(m, rng, n_placed)
+        need = np.zeros((m.K, m.n_rows, m.n_cols), bool)
+        for k in range(m.K):
+            if occupied[k]:
+                continue
+            Lmin, _, _, Rmax = oracle.leaf_windows(m, occupied, leaves, k)
+            for r in range(m.n_rows):
+                need[k, r, Lmin[r]:max(Rmax[r], Lmin[r])] = True
+        need = need.reshape(-1)
+        assert 0 < need.sum() < c.J
+        g = dev(synth.random_vector(c.V, 7 + cfg), torch.float32)
+        full = torch.empty(c.J, device="cuda")
+        api.beamlet_price(ddc.h, g, full)
+        pw = torch.full((c.J,), float("nan"), device="cuda")
+        api.beamlet_price_windowed(ddc.h, m, dev(occupied, torch.uint8), dev(leaves, torch.int16), g, pw)
+        torch.cuda.synchronize()
+        full, pw = host(full), host(pw)
+        assert np.array_equal(pw[need].view(np.uint32), full[need].view(np.uint32)), f"{name} cfg {cfg}"
+        if cfg >= 4:  # warp-row families: rows outside the windows are skipped
+            assert np.all(np.isnan(pw[~need])), f"{name} cfg {cfg}"
+        ddc.close()
+
+
 def test_empty_matrix():
     V, J = 7, 12
     e = np.zeros(0, np.int32)

@@ -9,12 +9,18 @@ import oracle
 import synth
 
 
+def window_prefix(row, lo, hi):
+    """Running float64 sum over the columns lo .. hi - 1 only, by an explicit loop."""
+    P = [0.0]
+    for c, p in enumerate(row):
+        P.append(P[-1] + float(p) if lo <= c < hi else P[-1])
+    return P
+
+
 def brute_best_opening(row, Lmin, Lmax, Rmin, Rmax):
     """All feasible [L, R) by explicit loops; key (v desc, width, centredness, L)."""
     N = len(row)
-    P = [0.0]
-    for p in row:
-        P.append(P[-1] + float(p))
+    P = window_prefix(row, Lmin, Rmax)
     best = None
     for L in range(N + 1):
         for R in range(L, N + 1):
@@ -58,6 +64,62 @@ def test_prefix_sum_is_sequential():
     for c, p in enumerate(row):
         acc = acc + float(p)
         assert P[c + 1] == acc  # bitwise: same order of float64 additions
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 97), (13, 60), (40, 41), (50, 50), (70, 20), (96, 97)])
+def test_window_prefix_sum(lo, hi):
+    """Zero up to the window, sequential inside it, constant after it; nothing
+    outside the window is read (NaN there changes nothing)."""
+    rng = np.random.default_rng(2)
+    row = (rng.normal(size=97) * 10.0 ** rng.integers(-6, 6, size=97)).astype(np.float32)
+    P = oracle.prefix_sums(row, lo, hi)
+    assert list(P) == window_prefix(row, lo, hi)
+    assert np.all(P[:lo + 1] == 0.0)
+    if hi > lo:
+        assert np.all(P[hi:] == P[hi])
+    poisoned = row.copy()
+    poisoned[:lo] = np.nan
+    poisoned[max(hi, lo):] = np.nan
+    assert np.array_equal(oracle.prefix_sums(poisoned, lo, hi), P)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_prices_outside_the_window_never_matter(seed):
+    """A row's choice, and a CP's aperture with neighbours placed, are unchanged
+    when every price outside the leaf-travel windows is replaced by NaN."""
+    rng = np.random.default_rng(10 + seed)
+    N = 16
+    for _ in range(30):
+        row = (rng.normal(size=N) * 10.0 ** rng.integers(-7, 7, size=N)).astype(np.float32)
+        a, b = sorted(rng.integers(0, N + 1, 2))
+        c, d = sorted(rng.integers(0, N + 1, 2))
+        got = oracle.best_opening(row, a, b, c, d)
+        poisoned = row.copy()
+        poisoned[:a] = np.nan
+        poisoned[max(d, a):] = np.nan
+        assert oracle.best_opening(poisoned, a, b, c, d) == got
+    mlc = synth.MLC(9, 4, 12, np.array([0], np.int32), 2)
+    mlc_id = synth.MLC(9, 4, 12, np.array([0], np.int32), 2, interdigitation=True)
+    pi = (rng.normal(size=mlc.K * 4 * 12) * 10.0 ** rng.integers(-5, 5, size=mlc.K * 4 * 12)).astype(np.float32)
+    occupied = np.zeros(mlc.K, bool)
+    leaves = np.zeros((mlc.K, 4, 2), np.int64)
+    for k in (2, 6):
+        occupied[k] = True
+        Ls = rng.integers(0, 9, size=4)
+        leaves[k] = np.stack([Ls, Ls + rng.integers(0, 4, size=4)], axis=1)
+    for k in range(mlc.K):
+        if occupied[k]:
+            continue
+        Lmin, _, _, Rmax = oracle.leaf_windows(mlc, occupied, leaves, k)
+        poisoned = pi.copy()
+        for r in range(4):
+            seg = poisoned[(k * 4 + r) * 12:(k * 4 + r + 1) * 12]
+            seg[:Lmin[r]] = np.nan
+            seg[max(Rmax[r], Lmin[r]):] = np.nan
+        for m, price_cp in ((mlc, oracle.price_cp), (mlc_id, oracle.price_cp_interdig)):
+            p0, l0 = price_cp(m, pi, occupied, leaves, k)
+            p1, l1 = price_cp(m, poisoned, occupied, leaves, k)
+            assert p0 == p1 and ((l0 is None and l1 is None) or np.array_equal(l0, l1))
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -162,9 +224,7 @@ def _brute_interdig(mlc, pi, occupied, leaves, k):
     states, vals = [], []
     for r in range(mlc.n_rows):
         row = pi[(k * mlc.n_rows + r) * N:(k * mlc.n_rows + r + 1) * N]
-        P = [0.0]
-        for p in row:
-            P.append(P[-1] + float(p))
+        P = window_prefix(row, Lmin[r], Rmax[r])
         st = [(L, R) for L in range(N + 1) for R in range(L, N + 1)
               if Lmin[r] <= L <= Lmax[r] and Rmin[r] <= R <= Rmax[r]]
         states.append(st)
@@ -208,7 +268,7 @@ def test_interdig_dp_matches_exhaustive_enumeration(seed):
         tot = 0.0
         for r in range(mlc.n_rows):
             assert Lmin[r] <= lv[r][0] <= Lmax[r] and Rmin[r] <= lv[r][1] <= Rmax[r] and lv[r][0] <= lv[r][1]
-            P = oracle.prefix_sums(pi[(k * mlc.n_rows + r) * 4:(k * mlc.n_rows + r + 1) * 4])
+            P = window_prefix(pi[(k * mlc.n_rows + r) * 4:(k * mlc.n_rows + r + 1) * 4], Lmin[r], Rmax[r])
             tot = tot + (P[lv[r][1]] - P[lv[r][0]])
         assert tot == price
 
