@@ -91,6 +91,10 @@ struct BPlan {
     double *best_price = nullptr, *F_dev = nullptr, *F0 = nullptr;
     void *obj_ws = nullptr, *pr_ws = nullptr, *mp_ws = nullptr;
     short2 *win = nullptr;                 // [K * NR] leaf-travel windows of the current iteration
+    uint8_t *live_flag = nullptr;          // master-problem live tiles (MpLive)
+    double *c_tile = nullptr, *F_off = nullptr;
+    int32_t *live_tiles = nullptr, *n_live = nullptr, *live_bcnt = nullptr;
+    double *live_bpart = nullptr;
     unsigned long long *wcount = nullptr;  // [iterations][3]: rows, nonzeros (and 0) inside the windows
     double F_offset = 0.0;
     std::vector<int64_t> cpo; // CSR(D^T) rowptr at each CP boundary
@@ -117,6 +121,8 @@ struct Batch {
     CommitPlan *d_commit = nullptr;
     BoundsPlan *d_bounds = nullptr; // null when no plan has a machine
     WinPlan *d_win = nullptr;
+    MpLive *d_live = nullptr;
+    int64_t max_wtiles = 1;
     int32_t max_K = 1;
     std::vector<int32_t> cols; // the distinct MLC column counts of the plans
     void *d_mpargs = nullptr;
@@ -163,6 +169,7 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
     for (BPlan &p : b.P) {
         if (p.NA > 0) VMAT_CUDA(cudaMemsetAsync(p.z_c, 0, (size_t)p.NA * 4, s));
         VMAT_CUDA(cudaMemsetAsync(p.wcount, 0, (size_t)3 * std::max(b.T, 1) * 8, s));
+        VMAT_CUDA(cudaMemsetAsync(p.live_flag, 0, (size_t)p.n_wtiles, s));
         VMAT_CUDA(cudaMemsetAsync(p.occupied, 0, p.K, s));
         VMAT_CUDA(cudaMemsetAsync(p.leaves_all, 0, (size_t)p.K * p.NR * 4, s));
         batch_fill_u8<<<std::max(1, (p.K + 255) / 256), 256, 0, s>>>(p.active, p.K, 1);
@@ -187,6 +194,7 @@ static vmat_status enqueue_run(Batch &b, cudaStream_t s) {
         batch_commit<<<n, 128, 0, s>>>(t, b.d_commit);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(aperture_dose_batched(b.dt, b.d_da, b.d_na_off, n, b.tot_na, t, s));
+        VMAT_TRY(mp_live_update_batched(b.d_live, n, b.max_wtiles, t, s));
         if (b.d_bounds) VMAT_TRY(fluence_bounds_batched(b.d_bounds, n, t + 1, s));
         VMAT_TRY(mp_bb_enqueue_batched(b.d_mpargs, b.d_weight, b.d_gctl, n, t + 1, b.grid_t[t], b.stages_t[t],
                                        b.smem_t[t], b.keep_t[t], s));
@@ -290,6 +298,14 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         VMAT_TRY(b.get((char **)&p.mp_ws, mp_workspace_bytes(std::min(nap, 96))));
         VMAT_TRY(b.get(&cpo_dev[i], (size_t)p.K + 1));
         VMAT_TRY(b.get(&p.win, (size_t)p.K * p.NR));
+        VMAT_TRY(b.get(&p.live_flag, (size_t)p.n_wtiles));
+        VMAT_TRY(b.get(&p.c_tile, (size_t)p.n_wtiles));
+        VMAT_TRY(b.get(&p.live_tiles, (size_t)p.n_wtiles));
+        VMAT_TRY(b.get(&p.n_live, 1));
+        VMAT_TRY(b.get(&p.F_off, 1));
+        VMAT_TRY(b.get(&p.live_bcnt, (size_t)mp_live_blocks(p.n_wtiles)));
+        VMAT_TRY(b.get(&p.live_bpart, (size_t)mp_live_blocks(p.n_wtiles)));
+        b.max_wtiles = std::max(b.max_wtiles, p.n_wtiles);
         VMAT_TRY(b.get(&p.wcount, (size_t)3 * std::max(b.T, 1)));
         p.ctl = b.d_ctl + (size_t)i * CTL_N;
         // columns not yet generated must read as 0 (later runs overwrite only columns they generate)
@@ -304,6 +320,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
             VMAT_LAUNCH_CHECK();
             VMAT_TRY(mp_write_labels(p.sid_c, p.NA, p.wstride, p.DA, s));
         }
+        VMAT_TRY(mp_tile_consts(p.sid_c, p.NA, &p.vox, p.n_wtiles, p.c_tile, s));
         p.vox_c = p.vox;
         p.vox_c.struct_id = p.sid_c;
         VMAT_TRY(inactive_objective(*p.h, &p.vox, p.F0, s));
@@ -324,6 +341,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     std::vector<SpmvPlan> spmv(n_plans);
     std::vector<PricePlan> price(n_plans);
     std::vector<WinPlan> wins(n_plans);
+    std::vector<MpLive> lives(n_plans);
     std::vector<DaPlan> da(n_plans);
     std::vector<ObjPlan> obj(n_plans);
     std::vector<CommitPlan> com(n_plans);
@@ -363,9 +381,12 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         price_off[i + 1] = price_off[i] + prow;
         na_off[i + 1] = na_off[i] + p.NA;
         targets[i] = p.n_ap;
+        lives[i] = MpLive{p.DA, p.wstride, p.n_wtiles, p.live_flag, p.c_tile, p.live_tiles, p.n_live, p.F_off, p.F0,
+                          p.ctl, p.live_bcnt, p.live_bpart};
+        // over the live tiles; F_off holds F0 and the constant of the other tiles
         VMAT_TRY(mp_fill_plan_args(mpargs.data() + (size_t)i * argb, p.mp_ws, std::min(std::max(p.n_ap, 1), 96), p.DA,
-                                   p.wstride, p.NA, p.sid_c, &p.vox_c, p.lo, p.hi, p.y, p.z_c, &b.opts, p.F_offset,
-                                   p.ctl, p.ctl + CTL_BBITERS));
+                                   p.wstride, p.NA, p.sid_c, &p.vox_c, p.lo, p.hi, p.y, p.z_c, &b.opts, 0.0, p.ctl,
+                                   p.ctl + CTL_BBITERS, &lives[i]));
     }
     b.tot_rows = rows_off[n_plans];
     b.tot_price = price_off[n_plans];
@@ -373,6 +394,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_TRY(b.get(&b.d_spmv, n_plans));
     VMAT_TRY(b.get(&b.d_price, n_plans));
     VMAT_TRY(b.get(&b.d_win, n_plans));
+    VMAT_TRY(b.get(&b.d_live, n_plans));
     VMAT_TRY(b.get(&b.d_da, n_plans));
     VMAT_TRY(b.get(&b.d_obj, n_plans));
     VMAT_TRY(b.get(&b.d_commit, n_plans));
@@ -383,6 +405,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
     VMAT_CUDA(cudaMemcpy(b.d_spmv, spmv.data(), n_plans * sizeof(SpmvPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_price, price.data(), n_plans * sizeof(PricePlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_win, wins.data(), n_plans * sizeof(WinPlan), cudaMemcpyHostToDevice));
+    VMAT_CUDA(cudaMemcpy(b.d_live, lives.data(), n_plans * sizeof(MpLive), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_da, da.data(), n_plans * sizeof(DaPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_obj, obj.data(), n_plans * sizeof(ObjPlan), cudaMemcpyHostToDevice));
     VMAT_CUDA(cudaMemcpy(b.d_commit, com.data(), n_plans * sizeof(CommitPlan), cudaMemcpyHostToDevice));

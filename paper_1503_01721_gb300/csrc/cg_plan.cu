@@ -176,6 +176,28 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     unsigned long long *wcount;
     VMAT_TRY(ar.get(&win, (size_t)K * NR));
     VMAT_TRY(ar.get(&wcount, (size_t)3 * nap_max));
+    // live tiles of the master problem (the 32-voxel tiles some placed aperture reaches)
+    MpLive live;
+    uint8_t *live_flag;
+    double *c_tile, *F_off;
+    int32_t *live_tiles, *n_live;
+    VMAT_TRY(ar.get(&live_flag, (size_t)n_wtiles));
+    VMAT_TRY(ar.get(&c_tile, (size_t)n_wtiles));
+    VMAT_TRY(ar.get(&live_tiles, (size_t)n_wtiles));
+    VMAT_TRY(ar.get(&n_live, 1));
+    VMAT_TRY(ar.get(&F_off, 1));
+    VMAT_TRY(ar.get(&live.bcnt, (size_t)mp_live_blocks(n_wtiles)));
+    VMAT_TRY(ar.get(&live.bpart, (size_t)mp_live_blocks(n_wtiles)));
+    live.DA = DA;
+    live.wstride = wstride;
+    live.n_wtiles = n_wtiles;
+    live.flag = live_flag;
+    live.c_tile = c_tile;
+    live.tiles = live_tiles;
+    live.n_live = n_live;
+    live.F_off = F_off;
+    live.F0 = F0;
+    live.skip = nullptr;
     const long long launches0 = g_launches.load();
     PhaseTimer tm(stats != nullptr, s);
     cudaEvent_t t0, t1;
@@ -199,7 +221,9 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         gather_u8<<<std::max(1, std::min(g256, (NA + 255) / 256)), 256, 0, s>>>(vox->struct_id, h.act_vox, NA, sid_c);
         VMAT_LAUNCH_CHECK();
         VMAT_TRY(mp_write_labels(sid_c, NA, wstride, DA, s));
+        VMAT_TRY(mp_tile_consts(sid_c, NA, vox, n_wtiles, c_tile, s));
     }
+    VMAT_CUDA(cudaMemsetAsync(live_flag, 0, (size_t)n_wtiles, s));
     VMAT_TRY(inactive_objective(h, vox, F0, s));
     VMAT_TRY(ddc_cp_table(h, K, bpc, s)); // CP offsets of CSR(D) rows for the aperture dose
     double F_offset = 0.0;
@@ -233,6 +257,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     }
     int32_t *ctl;
     VMAT_TRY(ar.get(&ctl, CTL_N));
+    live.skip = ctl;
     VMAT_CUDA(cudaMemsetAsync(ctl, 0, CTL_N * sizeof(int32_t), s));
     const int n_cap = std::min(std::max(n_apertures, 1), 96);
     void *mp_ws;
@@ -275,13 +300,15 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         tm.mark(PH_DA);
         VMAT_TRY(aperture_dose_dev(h, mlc, cps_dev + t, best_leaves, DA + 32 + (size_t)(t >> 2) * 128 + (t & 3),
                                    wstride, ctl, s));
+        if (NA > 0) VMAT_TRY(mp_live_update(live, t, s));
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
         if (lo) VMAT_TRY(fluence_bounds_enqueue(bg, t + 1, cps_dev, leaves_seq, lo, hi, ctl, s));
         if (NA > 0) {
             if (t + 1 <= n_cap) {
-                VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, F_offset,
-                                       mp_ws, ctl, ctl + CTL_BBITERS, s));
+                // over the live tiles; F_off holds F0 and the constant of the other tiles
+                VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, 0.0, mp_ws,
+                                       ctl, ctl + CTL_BBITERS, s, &live));
             } else {
                 VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 VMAT_CUDA(cudaStreamSynchronize(s));

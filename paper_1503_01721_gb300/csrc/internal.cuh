@@ -333,10 +333,39 @@ vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, floa
 // Device-driven solve (persistent solver only, n_ap <= n_cap <= 96): no host synchronisation;
 // ws holds mp_workspace_bytes(n_cap) bytes; skip and iters_acc as in the solver's arguments.
 size_t mp_workspace_bytes(int32_t n_cap);
+// Live warp tiles of a plan's master problem.  A voxel that no placed aperture
+// reaches has an all-zero row of DA: its dose is 0 whatever y is, and its penalty a
+// constant (Eq. 1 at z = 0).  The solver runs over the 32-voxel tiles that some
+// placed aperture reaches (in ascending order) and adds the constant of the others.
+struct MpLive {
+    const float *DA; // the plan's warp-tile DA
+    int64_t wstride, n_wtiles;
+    uint8_t *flag;        // [n_wtiles] sticky: a placed aperture reaches a voxel of the tile
+    const double *c_tile; // [n_wtiles] penalty at zero dose of the tile's voxels (mp_tile_consts)
+    int32_t *tiles;       // [n_wtiles] the live tiles, ascending
+    int32_t *n_live;      // [1] their number
+    double *F_off;        // [1] *F0 + the c_tile of the tiles not live
+    const double *F0;     // penalty of the voxels without entries
+    const int32_t *skip;  // as for the solver
+    int32_t *bcnt;        // [mp_live_blocks(n_wtiles)] scratch: live tiles per block of 1024
+    double *bpart;        // [mp_live_blocks(n_wtiles)] scratch: constants of the others per block
+};
+constexpr int MP_LIVE_BLOCK = 1024; // tiles per block of the list kernels
+__host__ __device__ inline int64_t mp_live_blocks(int64_t n_wtiles) {
+    return (n_wtiles + MP_LIVE_BLOCK - 1) / MP_LIVE_BLOCK;
+}
+vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *vox, int64_t n_wtiles, double *c_tile,
+                           cudaStream_t s);
+// After column t of DA is written: mark the tiles it reaches, rebuild the list and F_off
+// (per-block counts, then ordered writes: the list and the sums are reproducible).
+vmat_status mp_live_update(const MpLive &L, int32_t t, cudaStream_t s);
+vmat_status mp_live_update_batched(const MpLive *plans, int32_t n_plans, int64_t max_wtiles, int32_t t,
+                                   cudaStream_t s);
+// live (may be null): solve over the live tiles only, F offset F_offset + *live->F_off.
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
                           const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                           float *z, const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
-                          int32_t *iters_acc, cudaStream_t s);
+                          int32_t *iters_acc, cudaStream_t s, const MpLive *live = nullptr);
 // Batched master problems (persistent solver, one cooperative launch for all plans).
 // Per-plan arguments are an opaque mp_args_bytes() record filled by mp_fill_plan_args
 // (ws: mp_workspace_bytes(n_cap) bytes); mp_batched_grid gives the launch shape for
@@ -345,7 +374,7 @@ size_t mp_args_bytes();
 vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
                               const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi,
                               float *y, float *z, const vmat_bb_opts *opts, double F_offset, const int32_t *skip,
-                              int32_t *iters_acc);
+                              int32_t *iters_acc, const MpLive *live = nullptr);
 vmat_status mp_batched_grid(int32_t n, int32_t n_plans, int32_t *grid, int32_t *stages, size_t *smem);
 // weight: device [n_plans] (warp tiles of each plan); gctl: device [8] batch barrier, epoch and
 // active-set words.

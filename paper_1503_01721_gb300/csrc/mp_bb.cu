@@ -88,6 +88,12 @@ struct MPArgs {
     int32_t *status;
     vmat_bb_opts opts;
     double F_offset;
+    // Live-tile solves (tiles may be null: every tile): only the warp tiles
+    // tiles[0 .. *n_live) of DA are in the problem (the tiles some placed aperture
+    // reaches), and *F_off_dev, the constant penalty of the others, is added to F.
+    const int32_t *tiles;
+    const int32_t *n_live;
+    const double *F_off_dev;
 };
 
 __device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
@@ -157,7 +163,7 @@ __device__ void reduce_partials(const MPArgs &a, int P) {
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
         if (lane == 0) {
             if (k < n) a.G[k] = -s;
-            else a.st->F = s + a.F_offset;
+            else a.st->F = s + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
         }
     }
     __syncthreads();
@@ -396,13 +402,15 @@ struct WarpPipe {
     uint64_t *mb;
     const unsigned char *src;
     int64_t tile_bytes, w0, W, n_my;
+    const int32_t *tiles; // warp tile of list entry q (null: tile q)
     int64_t it_base; // pipeline slot of this tile set's first tile
     uint32_t cbytes;
     int stages;
     uint64_t pol;
+    __device__ __forceinline__ int64_t tile_of(int64_t q) const { return tiles ? (int64_t)__ldg(tiles + q) : q; }
     __device__ __forceinline__ void issue(int64_t it) const {
         const int s = (int)(it % stages);
-        const int64_t wt = w0 + ((it - it_base) % n_my) * W;
+        const int64_t wt = tile_of(w0 + ((it - it_base) % n_my) * W);
         mbar_arrive_expect_tx(&mb[s], cbytes);
         bulk_g2s(my + (size_t)s * cbytes, src + wt * tile_bytes, cbytes, &mb[s], pol);
     }
@@ -440,7 +448,7 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
                 z3 = fmaf(v.w, w.w, z3);
             }
         const float zi = (z0 + z1) + (z2 + z3);
-        const int64_t i = (P.w0 + j * P.W) * MP_WT + lane;
+        const int64_t i = P.tile_of(P.w0 + j * P.W) * MP_WT + lane;
         float gi = 0.f;
         if (i < a.V) {
             const int sid = blk[lane];
@@ -732,7 +740,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
         if (!grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
             return LOOP_ABORT;
         for (int k = tid; k < n; k += MP_THREADS) S.sG[k] = -__ldcg(a.G + k);
-        if (tid == 0) ps.F = __ldcg(a.G + n) + a.F_offset;
+        if (tid == 0) ps.F = __ldcg(a.G + n) + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
         __syncthreads();
         if (wid == 0) {
             solve_step<NMAX>(a, S, ps);
@@ -795,7 +803,11 @@ __device__ __forceinline__ void pipe_start(WarpPipe &P, const MPArgs &a, unsigne
     P.tile_bytes = a.wstride * 4;
     P.W = (int64_t)n_cta * MP_NW;
     P.w0 = (int64_t)cta * MP_NW + wid;
-    P.n_my = P.w0 < a.n_wtiles ? (a.n_wtiles - 1 - P.w0) / P.W + 1 : 0;
+    P.tiles = a.tiles;
+    int64_t n_wt = a.n_wtiles;
+    if (a.tiles) // the live list: written by earlier kernels of the stream, fixed during the solve
+        n_wt = min64((int64_t)max(__ldcg(a.n_live), 0), a.n_wtiles);
+    P.n_my = P.w0 < n_wt ? (n_wt - 1 - P.w0) / P.W + 1 : 0;
     P.it_base = it;
     if (lane == 0 && P.n_my > 0)
         for (int s = 0; s < P.stages; ++s) P.issue(it + s);
@@ -1136,6 +1148,171 @@ __global__ void write_label_heads(const uint8_t *sid, int32_t V, int64_t wstride
     }
 }
 
+// ---------------------------------------------------------------------------
+// Live tiles (MpLive): the 32-voxel tiles that some placed aperture reaches.
+// ---------------------------------------------------------------------------
+
+// Penalty at zero dose of each tile's voxels (a warp per tile, fixed butterfly).
+__global__ void mp_tile_const_kernel(const uint8_t *sid, int32_t NA, const float *T, const float *wo,
+                                     const float *wu, int64_t n_wtiles, double *c_tile) {
+    const int64_t wt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wt >= n_wtiles) return; // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int64_t i = wt * MP_WT + lane;
+    double f = 0.0;
+    if (i < NA) {
+        const int k = sid[i];
+        const double d = -(double)T[k]; // z - T at z = 0
+        const double w = d > 0.0 ? (double)wo[k] : (double)wu[k];
+        f = w * d * d;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) f += __shfl_xor_sync(0xffffffffu, f, d);
+    if (lane == 0) c_tile[wt] = f;
+}
+
+// Marks the tiles that column t of DA reaches (a warp per tile; the flag stays set).
+__device__ __forceinline__ void live_mark(const MpLive &L, int32_t t, int64_t wt) {
+    const int lane = threadIdx.x & 31;
+    const float v = L.DA[wt * L.wstride + MP_HEAD + (int64_t)(t >> 2) * 128 + (lane << 2) + (t & 3)];
+    if (__any_sync(0xffffffffu, v != 0.f) && lane == 0) L.flag[wt] = 1;
+}
+
+__global__ void mp_live_mark_kernel(MpLive L, int32_t t) {
+    if (L.skip && *L.skip) return;
+    const int64_t wt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wt < L.n_wtiles) live_mark(L, t, wt); // warp-uniform
+}
+
+__global__ void mp_live_mark_batched_kernel(const MpLive *plans, int32_t t) {
+    const MpLive &L = plans[blockIdx.y];
+    if (L.skip && *L.skip) return;
+    const int64_t wt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wt < L.n_wtiles) live_mark(L, t, wt);
+}
+
+constexpr int LV_THREADS = MP_LIVE_BLOCK; // a thread per tile
+
+// Block b of the list: the live count of tiles b * 1024 .. and the sum of the
+// others' constants (a fixed tree).
+__device__ void live_count(const MpLive &L) {
+    __shared__ double sums[LV_THREADS];
+    const int tid = threadIdx.x;
+    const int64_t q = (int64_t)blockIdx.x * LV_THREADS + tid;
+    const bool in = q < L.n_wtiles;
+    const int f = in && L.flag[q];
+    sums[tid] = in && !f ? L.c_tile[q] : 0.0;
+    const int c = __syncthreads_count(f);
+    for (int st = LV_THREADS / 2; st > 0; st >>= 1) {
+        if (tid < st) sums[tid] += sums[tid + st];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        L.bcnt[blockIdx.x] = c;
+        L.bpart[blockIdx.x] = sums[0];
+    }
+}
+
+// Block b writes its live tiles after those of blocks 0 .. b-1 (ballot ranks within
+// a warp, warp offsets by a scan of the 32 warp counts); block 0 also forms the
+// count and F_off = F0 + the block sums in block order.
+__device__ void live_write(const MpLive &L, int64_t n_blocks) {
+    __shared__ int32_t woff[32];
+    __shared__ int32_t base_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t q = (int64_t)blockIdx.x * LV_THREADS + tid;
+    const bool f = q < L.n_wtiles && L.flag[q];
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) woff[wid] = __popc(m);
+    if (tid == 0) {
+        int32_t b = 0;
+        for (int64_t k = 0; k < blockIdx.x; ++k) b += L.bcnt[k];
+        base_s = b;
+    }
+    __syncthreads();
+    if (wid == 0) { // exclusive scan of the warp counts
+        const int32_t v = woff[lane];
+        int32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        woff[lane] = x - v;
+    }
+    __syncthreads();
+    if (f) L.tiles[base_s + woff[wid] + __popc(m & ((1u << lane) - 1u))] = (int32_t)q;
+    if (blockIdx.x == 0 && tid == 0) {
+        int32_t n = 0;
+        double acc = 0.0;
+        for (int64_t k = 0; k < n_blocks; ++k) {
+            n += L.bcnt[k];
+            acc += L.bpart[k];
+        }
+        *L.n_live = n;
+        *L.F_off = *L.F0 + acc;
+    }
+}
+
+__global__ void __launch_bounds__(LV_THREADS) mp_live_count_kernel(MpLive L) {
+    if (L.skip && *L.skip) return;
+    if ((int64_t)blockIdx.x < mp_live_blocks(L.n_wtiles)) live_count(L);
+}
+
+__global__ void __launch_bounds__(LV_THREADS) mp_live_write_kernel(MpLive L) {
+    if (L.skip && *L.skip) return;
+    const int64_t nb = mp_live_blocks(L.n_wtiles);
+    if ((int64_t)blockIdx.x < nb) live_write(L, nb);
+}
+
+__global__ void __launch_bounds__(LV_THREADS) mp_live_count_batched_kernel(const MpLive *plans) {
+    const MpLive &L = plans[blockIdx.y];
+    if (L.skip && *L.skip) return;
+    if ((int64_t)blockIdx.x < mp_live_blocks(L.n_wtiles)) live_count(L);
+}
+
+__global__ void __launch_bounds__(LV_THREADS) mp_live_write_batched_kernel(const MpLive *plans) {
+    const MpLive &L = plans[blockIdx.y];
+    if (L.skip && *L.skip) return;
+    const int64_t nb = mp_live_blocks(L.n_wtiles);
+    if ((int64_t)blockIdx.x < nb) live_write(L, nb);
+}
+
+vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *vox, int64_t n_wtiles, double *c_tile,
+                           cudaStream_t s) {
+    if (n_wtiles < 1) return VMAT_OK;
+    const int64_t blocks = (n_wtiles * 32 + 255) / 256;
+    mp_tile_const_kernel<<<(unsigned)blocks, 256, 0, s>>>(sid_c, NA, vox->T, vox->w_over, vox->w_under, n_wtiles,
+                                                          c_tile);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status mp_live_update(const MpLive &L, int32_t t, cudaStream_t s) {
+    if (L.n_wtiles < 1) return VMAT_OK;
+    mp_live_mark_kernel<<<(unsigned)((L.n_wtiles * 32 + 255) / 256), 256, 0, s>>>(L, t);
+    VMAT_LAUNCH_CHECK();
+    const unsigned nb = (unsigned)mp_live_blocks(L.n_wtiles);
+    mp_live_count_kernel<<<nb, LV_THREADS, 0, s>>>(L);
+    VMAT_LAUNCH_CHECK();
+    mp_live_write_kernel<<<nb, LV_THREADS, 0, s>>>(L);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status mp_live_update_batched(const MpLive *plans, int32_t n_plans, int64_t max_wtiles, int32_t t,
+                                   cudaStream_t s) {
+    if (n_plans < 1 || max_wtiles < 1) return VMAT_OK;
+    mp_live_mark_batched_kernel<<<dim3((unsigned)((max_wtiles * 32 + 255) / 256), n_plans), 256, 0, s>>>(plans, t);
+    VMAT_LAUNCH_CHECK();
+    const dim3 g((unsigned)mp_live_blocks(max_wtiles), (unsigned)n_plans);
+    mp_live_count_batched_kernel<<<g, LV_THREADS, 0, s>>>(plans);
+    VMAT_LAUNCH_CHECK();
+    mp_live_write_batched_kernel<<<g, LV_THREADS, 0, s>>>(plans);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
 vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, float *DA, cudaStream_t s) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
@@ -1300,6 +1477,9 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.F_offset = F_offset;
     a.skip = nullptr;
     a.iters_acc = nullptr;
+    a.tiles = nullptr;
+    a.n_live = nullptr;
+    a.F_off_dev = nullptr;
 }
 
 static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream_t s) {
@@ -1316,7 +1496,7 @@ static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
                           const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                           float *z, const vmat_bb_opts *opts_in, double F_offset, void *ws, const int32_t *skip,
-                          int32_t *iters_acc, cudaStream_t s) {
+                          int32_t *iters_acc, cudaStream_t s, const MpLive *live) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
@@ -1332,6 +1512,11 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
                  ctx);
     a.skip = skip;
     a.iters_acc = iters_acc;
+    if (live) {
+        a.tiles = live->tiles;
+        a.n_live = live->n_live;
+        a.F_off_dev = live->F_off;
+    }
     return mp_launch_persistent(a, L, s);
 }
 
@@ -1340,7 +1525,7 @@ size_t mp_args_bytes() { return sizeof(MPArgs); }
 vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *DA, int64_t wstride, int32_t V,
                               const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi,
                               float *y, float *z, const vmat_bb_opts *opts_in, double F_offset, const int32_t *skip,
-                              int32_t *iters_acc) {
+                              int32_t *iters_acc, const MpLive *live) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
@@ -1353,6 +1538,11 @@ vmat_status mp_fill_plan_args(void *out, void *ws, int32_t n_cap, const float *D
                  ctx);
     a.skip = skip;
     a.iters_acc = iters_acc;
+    if (live) {
+        a.tiles = live->tiles;
+        a.n_live = live->n_live;
+        a.F_off_dev = live->F_off;
+    }
     memcpy(out, &a, sizeof(MPArgs));
     return VMAT_OK;
 }

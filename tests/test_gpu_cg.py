@@ -159,3 +159,27 @@ def test_plan_stats_and_stop_rule():
     zero = synth.Structures(s.struct_id, np.zeros_like(s.T), s.w_over, s.w_under, s.names)
     F0, st0 = api.cg_plan(ddc.h, c.mlc, api.VoxelParams.from_numpy(zero), 3)
     assert st0["n_apertures"] == 0 and st0["stop"] == "price" and F0 == 0.0
+
+
+def test_plan_past_the_persistent_solver_limit():
+    """100 apertures: the master problems past the persistent solver's 96 columns run
+    in the host-driven solver, over the covered voxels like the others.  Tight
+    delivery limits (Eq. 6) keep a positive price at every step, so the plan
+    reaches the count."""
+    import dataclasses
+    spec = synth.PlanSpec("long", synth.Geometry(16, 16, 12, 5.0, 110, 4, 6), 100, "prostate", 1)
+    c = synth.make_plan_case(spec)
+    machine = synth.make_machine(c.mlc, rate_min=0.0016, rate_max=0.002)
+    c = dataclasses.replace(c, mlc=dataclasses.replace(c.mlc, machine=machine))
+    ddc = make_ddc(c)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    F, st, cps, lv, y, dose = gpu_plan(ddc, c, 100)
+    assert st["n_apertures"] == 100 and st["stop"] == "count"
+    d_ref = oracle.dose_forward(D, oracle.aperture_fluence(c.mlc, cps, lv, y))
+    assert np.max(np.abs(dose - d_ref)) <= 1e-5 * np.max(np.abs(d_ref))
+    ref = oracle.cg_plan(D, c.mlc, c.structs, 100)
+    if list(cps) == ref.cps:
+        assert abs(F - ref.F) <= 1e-2 * ref.F
+    else:
+        t = next(i for i, (a, b) in enumerate(zip(list(cps), ref.cps)) if a != b)
+        assert near_tie_at(ddc, c, D, t, cps[t], None), f"sequence differs at {t}: gpu {list(cps)} oracle {ref.cps}"
