@@ -25,11 +25,6 @@
 
 namespace vmat {
 
-vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
-                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
-                              const int32_t *skip);
-size_t objective_scratch_bytes(int n_sm);
-vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);
 
 __global__ void gather_u8(const uint8_t *src, const int32_t *idx, int32_t n, uint8_t *dst) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];

@@ -313,6 +313,13 @@ vmat_status spmv_rows_batched(vmat_dtype dt, int cfg, const SpmvPlan *plans, con
 // g_scatter (may be null): write g[i] to g_scatter[idx[i]] instead of g[i].
 vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                            float *g_scatter, double *F, double F_offset, cudaStream_t s);
+// The same with caller-owned scratch ws (objective_scratch_bytes) and a skip word.
+vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
+                              float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
+                              const int32_t *skip);
+size_t objective_scratch_bytes(int n_sm);
+// F0 = the penalty at zero dose of the voxels without DDC entries (their dose is always 0).
+vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);
 
 // compact: write row r of CSR(D) (wstride == 0: at da[r]; else at da[(r / 32) * wstride + (r % 32) * 4],
 // the master problem's warp-tile layout with da pointing at the column's first slot);
