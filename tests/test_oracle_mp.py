@@ -102,3 +102,26 @@ def test_zero_gradient_stops_immediately():
     T = np.array([0.0], np.float32)
     y, z, F, it, reason, _ = oracle.mp_bb_solve(DA, sid, T, np.float32([1]), np.float32([1]), [0.0, 0.0])
     assert reason == oracle.STOP_GRAD0 and it == 1 and F == 0.0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_unreached_voxels_only_shift_F(seed):
+    """A voxel whose row of DA is zero keeps zero dose for every y: it adds nothing
+    to G and the constant F_i(0) to F.  Solving without those rows, with their
+    zero-dose penalty as the F offset, gives the same iterates and the same F
+    (the property that lets a solver skip voxels no placed aperture reaches)."""
+    DA, sid, T, wo, wu = random_mp(seed, V=400, n=5)
+    rng = np.random.default_rng(100 + seed)
+    unreached = rng.random(DA.shape[0]) < 0.4
+    DA[unreached] = 0.0
+    y0 = np.zeros(DA.shape[1])
+    y_a, z_a, F_a, it_a, r_a, h_a = oracle.mp_bb_solve(DA, sid, T, wo, wu, y0, opts=TIGHT)
+    F0, _ = oracle.objective_grad(np.zeros(int(unreached.sum())), sid[unreached], T, wo, wu)
+    assert F0 > 0.0  # some unreached voxels are underdosed targets
+    keep = ~unreached
+    y_b, z_b, F_b, it_b, r_b, h_b = oracle.mp_bb_solve(DA[keep], sid[keep], T, wo, wu, y0, opts=TIGHT, F_offset=F0)
+    assert np.all(z_a[unreached] == 0.0)
+    assert np.allclose(y_a, y_b, rtol=1e-9, atol=1e-12)
+    assert abs(F_a - F_b) <= 1e-12 * F_a
+    n = min(len(h_a), len(h_b), 50)
+    assert np.allclose(h_a[:n], h_b[:n], rtol=1e-12, atol=0.0)
