@@ -207,9 +207,7 @@ def run_oracle_steps(steps, warmup):
     V, J, vox, blt, val, structs, mlc = sample_case()
     D = oracle.ddc_matrix(V, J, vox, blt, val)
     nnz = len(val)
-    bpc = mlc.n_rows * mlc.n_cols
     n_rows_D = int(np.count_nonzero(np.bincount(vox, minlength=V)))
-    per_cp = np.bincount(blt // bpc, minlength=mlc.K)
     times, gbytes = [], 0.0
     for it in range(warmup + steps):
         t0 = time.perf_counter()
@@ -217,15 +215,26 @@ def run_oracle_steps(steps, warmup):
         dt = time.perf_counter() - t0
         if it >= warmup:
             times.append(dt)
-    # bytes moved by the plan's sparse passes, in the same FP32-CSR byte model as the GPU
+    # bytes of the plan's sparse passes in the GPU's FP32-CSR byte model: each pricing pass counts
+    # the beamlet rows inside the leaf-travel windows of the unoccupied CPs (the prices pricing reads),
+    # as the GPU's windowed pass does, plus g and the window table; then the final D x
+    per_blt = np.bincount(blt, minlength=J).reshape(mlc.K, mlc.n_rows, mlc.n_cols)
+    col = np.arange(mlc.n_cols)[None, :]
     n_price = len(plan.cps) + (plan.stop == "price")
     b = 0.0
-    occupied = set()
+    occupied = np.zeros(mlc.K, bool)
+    leaves_all = np.zeros((mlc.K, mlc.n_rows, 2), np.int64)
     for t in range(n_price):
-        act = [k for k in range(mlc.K) if k not in occupied]
-        b += sum(int(per_cp[k]) for k in act) * roofline.csr_bytes_per_nnz("f32") + len(act) * bpc * 12 + 4 * V
+        nz = rows = 0
+        for k in np.flatnonzero(~occupied):
+            Lmin, _, _, Rmax = oracle.leaf_windows(mlc, occupied, leaves_all, int(k))
+            inw = (col >= np.asarray(Lmin)[:, None]) & (col < np.asarray(Rmax)[:, None])
+            nz += int(per_blt[k][inw].sum())
+            rows += int(inw.sum())
+        b += nz * roofline.csr_bytes_per_nnz("f32") + rows * 12 + 4 * V + 4 * mlc.K * mlc.n_rows
         if t < len(plan.cps):
-            occupied.add(plan.cps[t])
+            occupied[plan.cps[t]] = True
+            leaves_all[plan.cps[t]] = plan.leaves[t]
     b += roofline.spmv_bytes(nnz, n_rows_D, J, V)
     per_step = sum(times) / len(times)
     return {"value": b / per_step / 1e9, "sec_per_plan": per_step, "nnz": nnz, "J": J, "V": V,
@@ -248,7 +257,8 @@ def cpu_baseline_subprocess(steps=1, warmup=0):
 
 def sample_desc(res):
     return (f"FP64 oracle cg_plan, {SAMPLE_APERTURES} apertures, on every {SAMPLE_CP_STRIDE}th CP of the "
-            f"{WORKLOAD} geometry ({res['J']} beamlets, {res['nnz']} nonzeros); same byte model")
+            f"{WORKLOAD} geometry ({res['J']} beamlets, {res['nnz']} nonzeros); same byte model (rows inside "
+            f"the leaf-travel windows per pricing pass)")
 
 
 # ----------------------------------------------------------------------------- GPU arm
