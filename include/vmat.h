@@ -329,7 +329,7 @@ vmat_status fluence_bounds(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps
  * pi is formed only inside the leaf-travel windows (as beamlet_price_windowed),
  * the only prices pricing reads.  The master problem runs over the 32-voxel
  * tiles that some placed aperture reaches; the other voxels have zero dose for
- * every y, and their penalty enters F as a constant. */
+ * every y, and their penalty enters F as a constant.
  * Outputs may be host or device memory (copied with cudaMemcpyDefault), any
  * may be NULL: cps_out int32 [n_apertures] (unused slots -1), leaves_out
  * int16 [n_apertures][n_rows][2], y_out float [n_apertures], dose_out float
