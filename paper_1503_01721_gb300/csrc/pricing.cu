@@ -4,8 +4,10 @@
 //
 // The paper uses one thread per row for the first kernel and one thread per CP
 // for the second.  Here one warp handles a row: lane 0 builds the float64
-// prefix sums P_c sequentially in column order, the lanes evaluate every
-// feasible pair (P_R - P_L) and the warp reduces with the full tie-break key
+// prefix sums P_c sequentially in column order over the row's leaf-travel
+// window [Lmin, Rmax) (no price outside it is read, so the beamlet price pass
+// may skip those beamlets), the lanes evaluate every feasible pair
+// (P_R - P_L) and the warp reduces with the full tie-break key
 // (value desc, width asc, |L + R - n_cols| asc, L asc).  Every compared value is
 // produced by the same float64 operations in the same order as the sequential
 // definition, and the key is a total order, so the choice is bit-exact.
