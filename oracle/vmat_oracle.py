@@ -70,7 +70,14 @@ R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
     optimum of each prefix extends to the optimum of the next).  A state's
     predecessor is the compatible state of the previous row with the largest
     partial sum, ties by the row key of R8; the last row's state likewise.
-    Backtracking from it gives the aperture.
+    Backtracking from it gives the aperture.  ``price_cp_interdig_plain``
+    is this reading written out state by state (every compatible pair of
+    states visited); ``price_cp_interdig`` reaches the same states, sums and
+    predecessors with prefix/suffix passes over the row states and is the
+    form used at clinical sizes.  Both are checked against an enumeration of
+    every interlocking aperture under R10's order on whole apertures (total,
+    then the last row's key, then the partial sum before it and that row's
+    key, down to the first row), prices and leaves.
 """
 from __future__ import annotations
 
@@ -238,6 +245,12 @@ def price_cp_interdig(mlc, pi, occupied, leaves, k: int, with_leaves: bool = Tru
     + (P_R - P_L) in float64, S_0 = P_R - P_L.  Compatible predecessors of (L', R')
     are the states (L, R) with L <= R' and L' <= R.  Returns (price, leaves) or
     (None, None) when no chain is feasible.
+
+    The best compatible predecessor of every state is found with two sweeps
+    instead of a scan per state: over R from n_cols down (the best state with
+    R >= b for each L), then over L upward (the best of those with L <= a), so
+    M[a][b] is the best state with L <= a and R >= b, and the predecessor of
+    (L', R') is M[R'][L'].  The result equals ``price_cp_interdig_plain``.
     """
     Lmin, Lmax, Rmin, Rmax = leaf_windows(mlc, occupied, leaves, k)
     N = mlc.n_cols
@@ -297,6 +310,59 @@ def price_cp_interdig(mlc, pi, occupied, leaves, k: int, with_leaves: bool = Tru
         out[r] = (L, R)
         if r > 0:
             L, R = int(preds[r][0][L, R]), int(preds[r][1][L, R])
+    return price, out
+
+
+def price_cp_interdig_plain(mlc, pi, occupied, leaves, k: int):
+    """Reading R10 written out state by state: the reference form of
+    ``price_cp_interdig``, slow (every pair of states of adjacent rows is
+    visited), for small MLCs and for checking the fast form.
+
+    Row r's states are its feasible openings (L, R) of R7 with value P_R - P_L
+    (R8 prefix sums).  For each state of row r, every state (L, R) of row r - 1
+    that has a chain and is compatible with it (L <= R' and L' <= R: each left
+    leaf stays left of the neighbouring right leaf) is visited, and the best by
+    (partial sum desc, R - L asc, |L + R - n_cols| asc, L asc) becomes its
+    predecessor; its partial sum is that predecessor's plus its own value, in
+    float64.  The last row's state is chosen by the same key; the aperture is
+    read back through the predecessors.  Returns (price, leaves [n_rows, 2]) or
+    (None, None) when no chain is feasible.
+    """
+    Lmin, Lmax, Rmin, Rmax = leaf_windows(mlc, occupied, leaves, k)
+    N = mlc.n_cols
+    base = k * mlc.n_rows * N
+
+    def key(st):  # st = (L, R, partial sum, predecessor index)
+        L, R, S = st[0], st[1], st[2]
+        return (-S, R - L, abs(L + R - N), L)
+
+    rows = []  # per row: the list of states that have a chain
+    for r in range(mlc.n_rows):
+        P = prefix_sums(pi[base + r * N: base + (r + 1) * N], int(Lmin[r]), int(Rmax[r]))
+        cur = []
+        for L in range(int(Lmin[r]), int(Lmax[r]) + 1):
+            for R in range(max(L, int(Rmin[r])), int(Rmax[r]) + 1):
+                v = float(P[R] - P[L])
+                if r == 0:
+                    cur.append((L, R, v, -1))
+                    continue
+                best = -1
+                for q, prev in enumerate(rows[r - 1]):
+                    if prev[0] <= R and L <= prev[1]:
+                        if best < 0 or key(prev) < key(rows[r - 1][best]):
+                            best = q
+                if best >= 0:
+                    cur.append((L, R, rows[r - 1][best][2] + v, best))
+        if not cur:
+            return None, None
+        rows.append(cur)
+    last = min(range(len(rows[-1])), key=lambda q: key(rows[-1][q]))
+    price = rows[-1][last][2]
+    out = np.zeros((mlc.n_rows, 2), np.int64)
+    q = last
+    for r in range(mlc.n_rows - 1, -1, -1):
+        out[r] = rows[r][q][:2]
+        q = rows[r][q][3]
     return price, out
 
 

@@ -301,3 +301,167 @@ def test_interdig_constraint_binds():
     assert p_free == 10.0 and not _interdig_ok(lv_free)
     p_id, lv_id = oracle.price_cp_interdig(mlc_id, pi, occupied, leaves, 0)
     assert _interdig_ok(lv_id) and p_id == _brute_interdig(mlc_id, pi, occupied, leaves, 0) and p_id < 10.0
+
+
+# ------------------------------------------------ interdigitation: the chosen leaves (reading R10's order)
+
+def _chains(states, n_rows):
+    """Every combination of one state per row in which adjacent rows interlock
+    (L_r <= R_{r-1} and L_{r-1} <= R_r), by depth-first extension row by row."""
+    out = []
+
+    def extend(prefix):
+        if len(prefix) == n_rows:
+            out.append(tuple(prefix))
+            return
+        for s in states[len(prefix)]:
+            if prefix and not (s[0] <= prefix[-1][1] and prefix[-1][0] <= s[1]):
+                continue
+            extend(prefix + [s])
+
+    extend([])
+    return out
+
+
+def _brute_interdig_aperture(mlc, pi, occupied, leaves, k):
+    """The aperture R10 selects, by enumeration: of every feasible interlocking
+    combination of row openings, the first in R10's order on whole apertures.
+    That order compares the total (the sequential float64 sum of the row values),
+    larger first; then the last row's opening by the R8 key (width, |L + R - N|,
+    L); then the partial sum through the row before it, larger first, and that
+    row's opening by the R8 key; and so on down to the first row.
+    Returns (price, leaves) or (None, None)."""
+    Lmin, Lmax, Rmin, Rmax = oracle.leaf_windows(mlc, occupied, leaves, k)
+    N = mlc.n_cols
+    states, vals = [], []
+    for r in range(mlc.n_rows):
+        row = pi[(k * mlc.n_rows + r) * N:(k * mlc.n_rows + r + 1) * N]
+        P = window_prefix(row, Lmin[r], Rmax[r])
+        st = [(L, R) for L in range(N + 1) for R in range(L, N + 1)
+              if Lmin[r] <= L <= Lmax[r] and Rmin[r] <= R <= Rmax[r]]
+        states.append(st)
+        vals.append({s: P[s[1]] - P[s[0]] for s in st})
+    best = None
+    for combo in _chains(states, mlc.n_rows):
+        assert _interdig_ok(combo)
+        partial, tot = [], 0.0
+        for r, s in enumerate(combo):
+            tot = tot + vals[r][s]
+            partial.append(tot)
+        key = []
+        for r in range(mlc.n_rows - 1, -1, -1):
+            L, R = combo[r]
+            key += [-partial[r], R - L, abs(L + R - N), L]
+        key = tuple(key)
+        if best is None or key < best[0]:
+            best = (key, tot, combo)
+    if best is None:
+        return None, None
+    return best[1], np.array(best[2], np.int64)
+
+
+def _interdig_case(seed, n_rows, n_cols, K=4):
+    """Prices with many exact ties (small integers), or ties broken by rounding
+    (values of very different size), and an occupied neighbour on some seeds."""
+    rng = np.random.default_rng(seed)
+    mlc = synth.MLC(K, n_rows, n_cols, np.array([0], np.int32), 1 + seed % 2, interdigitation=True)
+    J = K * n_rows * n_cols
+    kind = seed % 3
+    if kind == 0:
+        pi = rng.integers(-2, 3, size=J).astype(np.float32)
+    elif kind == 1:
+        pi = (rng.integers(-3, 4, size=J) * rng.uniform(0.1, 1.0, size=J)).astype(np.float32)
+    else:  # 2^25 + small: partial sums round, so distinct chains reach equal totals
+        pi = np.where(rng.random(J) < 0.3, 2.0 ** 25, rng.integers(-2, 3, size=J)).astype(np.float32)
+    occupied = np.zeros(K, bool)
+    leaves = np.zeros((K, n_rows, 2), np.int64)
+    if seed % 4 >= 2:
+        occupied[1] = True
+        L = rng.integers(0, n_cols + 1, size=n_rows)
+        R = np.minimum(n_cols, L + rng.integers(0, n_cols + 1, size=n_rows))
+        leaves[1] = np.stack([L, R], axis=1)
+    return mlc, pi, occupied, leaves
+
+
+# 5 x 6 only with an occupied neighbour (seed % 4 >= 2), whose windows keep the enumeration short
+@pytest.mark.parametrize("n_rows,n_cols,seed", [(3, 6, s) for s in range(6)] + [(4, 5, s) for s in range(6)] +
+                         [(5, 4, s) for s in range(6)] + [(5, 6, s) for s in (2, 3, 6, 7)])
+def test_interdig_plain_dp_leaves_match_enumeration(n_rows, n_cols, seed):
+    mlc, pi, occupied, leaves = _interdig_case(seed, n_rows, n_cols, K=3 if n_rows * n_cols >= 30 else 4)
+    for k in range(mlc.K):
+        if occupied[k]:
+            continue
+        p_ref, lv_ref = _brute_interdig_aperture(mlc, pi, occupied, leaves, k)
+        price, lv = oracle.price_cp_interdig_plain(mlc, pi, occupied, leaves, k)
+        if p_ref is None:
+            assert price is None
+            continue
+        assert np.float64(price).view(np.uint64) == np.float64(p_ref).view(np.uint64)
+        assert np.array_equal(lv, lv_ref), (k, lv, lv_ref)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_interdig_fast_form_matches_plain_dp(seed):
+    """price_cp_interdig (prefix/suffix dominance passes) against the plain DP,
+    leaves and price, on 12 x 12 rows with occupied neighbours and ties."""
+    rng = np.random.default_rng(100 + seed)
+    K, NR, N = 10, 12, 12
+    mlc = synth.MLC(K, NR, N, np.array([0, 6], np.int32), 2 + seed % 3, interdigitation=True)
+    J = K * NR * N
+    if seed % 2:
+        pi = rng.integers(-2, 3, size=J).astype(np.float32)
+    else:
+        pi = (rng.normal(size=J) * 5.0).astype(np.float32)
+        pi[rng.random(J) < 0.4] = 0.0
+    occupied = np.zeros(K, bool)
+    occupied[[2, 7]] = True
+    leaves = np.zeros((K, NR, 2), np.int64)
+    for kk in (2, 7):
+        L = rng.integers(0, N // 2 + 1, size=NR)
+        leaves[kk] = np.stack([L, np.minimum(N, L + rng.integers(0, N // 2 + 1, size=NR))], axis=1)
+    for k in range(K):
+        if occupied[k]:
+            continue
+        p_ref, lv_ref = oracle.price_cp_interdig_plain(mlc, pi, occupied, leaves, k)
+        price, lv = oracle.price_cp_interdig(mlc, pi, occupied, leaves, k)
+        if p_ref is None:
+            assert price is None
+            continue
+        assert np.float64(price).view(np.uint64) == np.float64(p_ref).view(np.uint64)
+        assert np.array_equal(lv, lv_ref), (k, lv, lv_ref)
+
+
+def _planted(monkeypatch, which):
+    """Plant one mistake in the oracle's interdigitation order (CPU only)."""
+    if which == "tie_L":  # L ascending flipped in the dominance passes
+        def bad(va, La, Ra, vb, Lb, Rb, N):
+            wa, wb = Ra - La, Rb - Lb
+            ca, cb = np.abs(La + Ra - N), np.abs(Lb + Rb - N)
+            return (va > vb) | ((va == vb) & ((wa < wb) | ((wa == wb) & ((ca < cb) | ((ca == cb) & (La > Lb))))))
+        monkeypatch.setattr(oracle.vmat_oracle, "_better", bad)
+    elif which == "tie_width":  # wider first
+        def bad(va, La, Ra, vb, Lb, Rb, N):
+            wa, wb = Ra - La, Rb - Lb
+            ca, cb = np.abs(La + Ra - N), np.abs(Lb + Rb - N)
+            return (va > vb) | ((va == vb) & ((wa > wb) | ((wa == wb) & ((ca < cb) | ((ca == cb) & (La < Lb))))))
+        monkeypatch.setattr(oracle.vmat_oracle, "_better", bad)
+    elif which == "final_key":  # the last row's state chosen without the centredness term
+        monkeypatch.setattr(oracle.vmat_oracle, "_state_order", lambda val, L, R, N: (L, R - L, -val))
+
+
+@pytest.mark.parametrize("which", ["tie_L", "tie_width", "final_key"])
+def test_interdig_planted_order_mistakes_are_caught(monkeypatch, which):
+    """Each planted mistake in the fast form's order changes a chosen aperture on
+    the tie-heavy cases above, so the pins would fail."""
+    _planted(monkeypatch, which)
+    caught = False
+    for seed in range(6):
+        mlc, pi, occupied, leaves = _interdig_case(seed, 4, 5)
+        for k in range(mlc.K):
+            if occupied[k]:
+                continue
+            p_ref, lv_ref = oracle.price_cp_interdig_plain(mlc, pi, occupied, leaves, k)
+            price, lv = oracle.price_cp_interdig(mlc, pi, occupied, leaves, k)
+            if p_ref is not None and (price != p_ref or not np.array_equal(lv, lv_ref)):
+                caught = True
+    assert caught
