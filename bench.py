@@ -55,15 +55,14 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
 # configurations that read the 16-bit column index (built with index16)
 INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
-# configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel
-# (profiles/spmv_warp_row_kernel_cfg2_traffic.md).  The plan's passes are windowed: their ratio is
-# WINDOWED_TRAFFIC_RATIO, measured on a windowed launch of the plan; a configuration without such a
-# capture reports null.
-WINDOWED_TRAFFIC_RATIO = {("f32", 11): 1.0103}  # profiles/spmv_warp_row_c_kernel_cfg2_windowed_traffic.md
+# configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel.
+# The plan's passes are windowed: their ratio is WINDOWED_TRAFFIC_RATIO, measured on a windowed
+# launch of the plan; a configuration without such a capture reports null.
+WINDOWED_TRAFFIC_RATIO = {("f32", 11): 1.0103}
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
                  ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
                  ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
-                 # 16-bit index, on the 45-CP case (profiles/spmv_warp_row_z_kernel_cfg2q_f32.md)
+                 # 16-bit index, on the 45-CP case
                  ("f32", 12): 1.0044}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12

@@ -24,6 +24,7 @@
 #ifndef VMAT_H
 #define VMAT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -253,15 +254,24 @@ vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, const uint8_t 
  * while they plan: a service that hands all of its GPU memory to its own pool at
  * start-up (an allocation behind that pool's back can fail or fragment it), or
  * a loop that must not touch the allocator after initialisation.
- * Its per-row scratch is one fixed device array inside libvmat with room for
- * VMAT_NOALLOC_MAX_ROWS (CP, MLC row) pairs (about 0.85 MB), which every GPU
- * that loads the library keeps until the process exits.  K * n_rows above the
- * limit returns VMAT_EINVAL (use price_apertures).  The first call on a device
- * looks up the array's device address, so make that first call outside any
- * stream capture.  All calls share the one array: calls whose work overlaps
- * on the GPU (other streams, other host threads) race on it, so callers must
- * order them.  Nothing needs zeroing between calls. */
+ * Its scratch is one fixed device array inside libvmat of
+ * VMAT_NOALLOC_SCRATCH_BYTES (about 0.85 MB), which every GPU that loads the
+ * library keeps until the process exits.  Two limits follow from its size:
+ *   - K * n_rows at most VMAT_NOALLOC_MAX_ROWS (CP, MLC row) pairs;
+ *   - with interdigitation, the chain search also keeps per-CP prices, every
+ *     row's prefix sums and every CP's predecessor table there:
+ *     K * (9 + 8 n_rows (n_cols + 1) + 2 (n_rows (n_cols + 1)^2 + 1)) + 80
+ *     bytes must fit (36 CPs x 20 rows x 20 columns does; the 180 x 64 x 64
+ *     geometry does not).
+ * Beyond either limit the call returns VMAT_EINVAL (use price_apertures).
+ * Every call looks up the array's device address on the current device (a host
+ * lookup; the first one on a device also loads the library's device code
+ * there, so make that first call outside any stream capture).  All calls share
+ * the one array: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it, so callers must order them.  Nothing needs zeroing
+ * between calls. */
 #define VMAT_NOALLOC_MAX_ROWS 65536
+#define VMAT_NOALLOC_SCRATCH_BYTES ((size_t)VMAT_NOALLOC_MAX_ROWS * 13 + 64)
 vmat_status price_apertures_noalloc(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied,
                                     const int16_t *leaves, int32_t *best_cp, int16_t *best_leaves,
                                     double *best_price, void *stream);

@@ -753,32 +753,22 @@ size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
     return b;
 }
 
-// Scratch of price_apertures_noalloc: per-row bests for up to VMAT_NOALLOC_MAX_ROWS
-// (CP, MLC row) pairs, in one fixed device array that every GPU loading the library
-// keeps until the process exits.  Host code must not use the symbol as a pointer:
-// its device address is looked up once per device with cudaGetSymbolAddress.
-constexpr size_t NOALLOC_BYTES = (size_t)VMAT_NOALLOC_MAX_ROWS * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
+// Scratch of price_apertures_noalloc: one fixed device array that every GPU loading
+// the library keeps until the process exits.  Host code must not use the symbol as a
+// pointer: its device address on the current device comes from cudaGetSymbolAddress.
+constexpr size_t NOALLOC_BYTES = VMAT_NOALLOC_SCRATCH_BYTES;
+static_assert(NOALLOC_BYTES == (size_t)VMAT_NOALLOC_MAX_ROWS * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64,
+              "the fixed scratch holds the per-row bests of VMAT_NOALLOC_MAX_ROWS rows");
 static __device__ __align__(256) unsigned char g_noalloc_price_scratch[NOALLOC_BYTES];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
+// Looked up on every call rather than cached: a cached address would outlive a
+// cudaDeviceReset or a re-created primary context.
 static vmat_status noalloc_scratch(void **out) {
-    int dev = -1;
-    VMAT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
-        return set_error(VMAT_EUNSUPPORTED, "price_apertures_noalloc: device ordinal %d not supported", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_price_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(VMAT_ECUDA, "price_apertures_noalloc: cudaGetSymbolAddress failed: %s",
-                             cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_price_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(VMAT_ECUDA, "price_apertures_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    *out = p;
     return VMAT_OK;
 }
 
