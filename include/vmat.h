@@ -106,6 +106,9 @@ typedef struct {
                            configurations that read them (2 bytes per nonzero instead of 4) */
     int32_t tile_cfg_Dt; /* SpMV configuration index of CSR(D^T), -1 = as tile_cfg (a pair found by
                             the autotuner once, see vmat_ddc_info, can be reused without tuning again) */
+    int32_t refine_f32; /* BF16 / FP8 builds: nonzero keeps CSR(D)'s values in FP32 as well (4 more
+                           bytes per nonzero), and cg_plan ends with the FP32 refinement described
+                           there.  Ignored for F32 builds. */
 } vmat_build_opts;
 
 /* Master-problem (Eq. 6-10) options.  Stopping rules of Section 2.1:
@@ -146,6 +149,7 @@ typedef struct {
     int32_t cfg_D, cfg_Dt;           /* SpMV configuration of each CSR (see vmat_spmv_config_count) */
     int32_t index16_D, index16_Dt;   /* 1: that CSR holds the 16-bit column index */
     int64_t bytes16_D, bytes16_Dt;   /* device bytes of the 16-bit index (offsets, bases, chunk pointers) */
+    int32_t refine_f32;              /* 1: CSR(D) also holds FP32 values (build option refine_f32) */
 } vmat_ddc_info;
 
 /* Per-phase device times of cg_plan, named as the paper's Table 2 phases. */
@@ -165,6 +169,14 @@ typedef struct {
     int32_t stop_reason;
     int64_t kernel_launches; /* kernels this call launched */
     double pp1_full_bytes;   /* bytes of the same passes over every row of the unoccupied CPs */
+    int32_t refined;         /* 1: the plan ended with the FP32 refinement (see cg_plan) */
+    int32_t refine_bb_iters; /* BB iterations of the refinement's master problem */
+    double t_refine_ms;      /* refinement: FP32 aperture dose vectors and master problem */
+    double F_before_refine;  /* objective of the low-precision master problem's dose before it */
+    double mp_bytes;         /* bytes the master problems' passes over DA moved (t_mp_ms's work):
+                                per pass, each 32-voxel tile in the solve reads its 128-byte label
+                                head and its ceil(n/4) four-aperture groups (512 bytes each) and
+                                writes (or reads) its 32 doses */
 } vmat_plan_stats;
 
 /* ---- DDC matrix ---------------------------------------------------------- */
@@ -344,7 +356,14 @@ vmat_status fluence_bounds(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps
  * may be NULL: cps_out int32 [n_apertures] (unused slots -1), leaves_out
  * int16 [n_apertures][n_rows][2], y_out float [n_apertures], dose_out float
  * [V].  F_out: host double.  stats: host struct or NULL.  Needs build_D and
- * build_Dt.  Synchronises. */
+ * build_Dt.  Synchronises.
+ * FP32 refinement (BF16 / FP8 handles built with refine_f32): after the last
+ * aperture, every placed aperture's dose vector DA (Eq. 5) is recomputed from
+ * the FP32 values, the master problem is solved again on those columns (warm
+ * start from the plan's y, the same options and bounds), and the final dose
+ * D (A y) and F come from the FP32 values.  Pricing stays in the stored type.
+ * stats->F_before_refine holds the objective the low-precision master problem
+ * reached. */
 vmat_status cg_plan(vmat_ddc h, const vmat_mlc *mlc, const vmat_voxels *vox, int32_t n_apertures,
                     const vmat_bb_opts *opts, int32_t *cps_out, int16_t *leaves_out, float *y_out, float *dose_out,
                     double *F_out, vmat_plan_stats *stats, void *stream);

@@ -62,6 +62,10 @@ R11 Delivery limits (Eq. 2, 6).  Gantry speed s_k of an occupied CP is the
     aperture.  The travel window (R7) must not exceed what the leaves can do at
     the slowest gantry speed (travel_cols S^L <= cp_step leaf_speed), which
     keeps S^U_k >= S^L.
+R12 FP32 refinement of a BF16 / FP8 plan (the precision form): the apertures
+    stay as chosen on the stored values; their dose vectors are recomputed from
+    the float32 values, the master problem is solved again from the plan's y,
+    and the final dose comes from the float32 values.
 R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
     not pass the right leaf of an adjacent row, L_r <= min(R_{r-1}, R_{r+1}).
     The best aperture of a CP is then a chain over the rows: the sequential
@@ -605,6 +609,22 @@ def cg_plan(D, mlc, structs, n_apertures: int, opts: BBOptions | None = None, pr
     dose = dose_forward(D, x)
     F, _ = objective_grad(dose, sid, T, wo, wu)
     return PlanResult(cps, lvs, y, dose, F, prices, iters, stop)
+
+
+def refine_plan(D, mlc, structs, cps, leaves, y, opts: BBOptions | None = None):
+    """FP32 refinement of a plan chosen on lower-precision values (reading R12):
+    with D holding the float32 values, each placed aperture's dose vector
+    DA = sum of D's columns in the aperture (Eq. 5), the master problem of
+    Eq. 6-10 again from the plan's y, and the final dose D (A y).
+
+    Returns (y, dose, F, bb_iters).
+    """
+    s = structs
+    DA = np.stack([aperture_dose(D, mlc, int(k), lv) for k, lv in zip(cps, leaves)], axis=1)
+    yr, _, _, iters, _, _ = mp_bb_solve(DA, s.struct_id, s.T, s.w_over, s.w_under, np.asarray(y, F64), opts=opts)
+    dose = dose_forward(D, aperture_fluence(mlc, cps, leaves, yr))
+    F, _ = objective_grad(dose, s.struct_id, s.T, s.w_over, s.w_under)
+    return yr, dose, F, iters
 
 
 # ----------------------------------------------------------------------------

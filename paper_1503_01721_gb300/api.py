@@ -115,11 +115,12 @@ def ddc_load_coo(V: int, J: int, vox: torch.Tensor, blt: torch.Tensor, val: torc
 
 def ddc_build(h: int, dtype: str = "f32", build_D: bool = True, build_Dt: bool = True, tile_cfg: int = -1,
               autotune: bool = False, keep_coo: bool = False, stream=None, index16: bool = False,
-              tile_cfg_Dt: int = -1) -> None:
+              tile_cfg_Dt: int = -1, refine: bool = False) -> None:
     """Build CSR(D) / CSR(D^T); index16 also stores 16-bit chunk-relative column indices where they fit.
-    tile_cfg sets the SpMV configuration of CSR(D) (and of CSR(D^T) unless tile_cfg_Dt >= 0)."""
+    tile_cfg sets the SpMV configuration of CSR(D) (and of CSR(D^T) unless tile_cfg_Dt >= 0).
+    refine (BF16 / FP8): keep CSR(D)'s FP32 values too, for cg_plan's FP32 refinement."""
     o = _lib.BuildOpts(_lib.DTYPES[dtype], int(build_D), int(build_Dt), int(tile_cfg), int(autotune), int(keep_coo),
-                       int(index16), int(tile_cfg_Dt))
+                       int(index16), int(tile_cfg_Dt), int(refine))
     check("ddc_build", _lib.load().ddc_build(ctypes.c_void_p(h), ctypes.byref(o), _stream(stream)))
 
 
@@ -344,11 +345,12 @@ class Ddc:
     """Owning wrapper of a DDC handle (frees it when garbage-collected)."""
 
     def __init__(self, V, J, vox, blt, val, dtype="f32", build_D=True, build_Dt=True, tile_cfg=-1,
-                 autotune=False, stream=None, index16=False, tile_cfg_Dt=-1):
+                 autotune=False, stream=None, index16=False, tile_cfg_Dt=-1, refine=False):
         self.V, self.J = int(V), int(J)
         self.h = ddc_load_coo(V, J, vox, blt, val, stream)
         try:
-            ddc_build(self.h, dtype, build_D, build_Dt, tile_cfg, autotune, False, stream, index16, tile_cfg_Dt)
+            ddc_build(self.h, dtype, build_D, build_Dt, tile_cfg, autotune, False, stream, index16, tile_cfg_Dt,
+                      refine)
         except Exception:
             ddc_free(self.h)
             self.h = None

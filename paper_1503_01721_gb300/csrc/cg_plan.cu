@@ -100,7 +100,7 @@ struct PhaseTimer {
     }
 };
 
-enum { PH_PP1 = 0, PH_SPMV, PH_PP2, PH_DA, PH_MP, PH_FINAL, PH_N };
+enum { PH_PP1 = 0, PH_SPMV, PH_PP2, PH_DA, PH_MP, PH_FINAL, PH_REFINE, PH_N };
 
 } // namespace
 
@@ -257,6 +257,10 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     const int n_cap = std::min(std::max(n_apertures, 1), 96);
     void *mp_ws;
     VMAT_TRY(ar.get((char **)&mp_ws, mp_workspace_bytes(n_cap)));
+    double *mp_bytes_dev; // bytes the persistent master-problem passes moved
+    VMAT_TRY(ar.get(&mp_bytes_dev, 1));
+    VMAT_CUDA(cudaMemsetAsync(mp_bytes_dev, 0, sizeof(double), s));
+    double mp_bytes_host = 0.0; // the same for host-driven solves (column-major DA, every active voxel)
     int64_t spmv_launches = 0;
     const int vb = value_bytes(h.dtype);
     const double bytes_D_full = csr_pass_bytes(h.D.cfg, vb, (double)h.D.nnz, h.D.n_rows + 1.0, (double)h.D.n_chunks) +
@@ -303,7 +307,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
             if (t + 1 <= n_cap) {
                 // over the live tiles; F_off holds F0 and the constant of the other tiles
                 VMAT_TRY(mp_bb_enqueue(DA, NA, t + 1, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, 0.0, mp_ws,
-                                       ctl, ctl + CTL_BBITERS, s, &live));
+                                       ctl, ctl + CTL_BBITERS, s, &live, mp_bytes_dev));
             } else {
                 VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 VMAT_CUDA(cudaStreamSynchronize(s));
@@ -312,7 +316,51 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
                     VMAT_TRY(mp_bb_impl(DA, NA, t + 1, ld, sid_c, wstride, &vox_c, lo, hi, y, z_c, opts, F_offset,
                                         &rep, s));
                     bb_extra += rep.iters;
+                    mp_bytes_host += (double)rep.iters * (double)NA * (4.0 * (t + 1) + 9.0);
                 }
+            }
+        }
+        tm.end();
+    }
+    // ---- FP32 refinement of a BF16 / FP8 plan: every placed aperture's DA column from the
+    // FP32 values of CSR(D), the master problem again from the plan's y, then the final dose
+    // from the same values.  hf reads the handle's CSR(D) through those values.
+    const bool refine = h.D_val_f32 != nullptr && h.dtype != VMAT_F32 && NA > 0;
+    Ddc hf = h;
+    if (refine) {
+        hf.dtype = VMAT_F32;
+        hf.D.val = h.D_val_f32;
+        hf.scale = nullptr;
+    }
+    int refine_extra = 0;
+    int32_t *refine_iters = nullptr;
+    if (refine) {
+        VMAT_TRY(ar.get(&refine_iters, 1));
+        VMAT_CUDA(cudaMemsetAsync(refine_iters, 0, sizeof(int32_t), s));
+        VMAT_CUDA(cudaMemcpyAsync(hctl, ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaStreamSynchronize(s));
+        const int n_placed = hctl[CTL_NAP];
+        MpLive live_r = live; // runs whether or not the plan stopped on its prices
+        live_r.skip = nullptr;
+        tm.mark(PH_REFINE);
+        // the objective the low-precision master problem reached (its compact dose, plus
+        // the constant penalty of the voxels without entries)
+        VMAT_TRY(objective_impl(NA, z_c, h.act_vox, vox, nullptr, nullptr, F_dev + 1, F_offset, s));
+        for (int t = 0; t < n_placed; ++t) {
+            VMAT_TRY(aperture_dose_dev(hf, mlc, cps_dev + t, leaves_seq + (size_t)t * NR * 2,
+                                       DA + 32 + (size_t)(t >> 2) * 128 + (t & 3), wstride, nullptr, s));
+            VMAT_TRY(mp_live_mark(live_r, t, s)); // FP32 columns can reach tiles an FP8 column rounded to 0
+        }
+        if (n_placed > 0) {
+            VMAT_TRY(mp_live_rebuild(live_r, s));
+            if (n_placed <= n_cap) {
+                VMAT_TRY(mp_bb_enqueue(DA, NA, n_placed, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, 0.0,
+                                       mp_ws, nullptr, refine_iters, s, &live_r));
+            } else {
+                vmat_bb_report rep;
+                VMAT_TRY(mp_bb_impl(DA, NA, n_placed, ld, sid_c, wstride, &vox_c, lo, hi, y, z_c, opts, F_offset,
+                                    &rep, s));
+                refine_extra = rep.iters;
             }
         }
         tm.end();
@@ -320,7 +368,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     // ---- final dose D (A y) in FP32 and its objective (apertures not placed have cps = -1)
     tm.mark(PH_FINAL);
     VMAT_TRY(aperture_fluence(mlc, n_apertures, cps_dev, leaves_seq, y, x, s));
-    VMAT_TRY(dose_forward_impl(h, x, dose, false, s));
+    VMAT_TRY(dose_forward_impl(refine ? hf : h, x, dose, false, s));
     VMAT_TRY(objective_impl(V, dose, nullptr, vox, nullptr, nullptr, F_dev, 0.0, s));
     tm.end();
     VMAT_CUDA(cudaEventRecord(t1, s));
@@ -371,10 +419,13 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         VMAT_CUDA(cudaMemcpyAsync(y_out, y, (size_t)n_apertures * 4, cudaMemcpyDefault, s));
     }
     if (dose_out) VMAT_CUDA(cudaMemcpyAsync(dose_out, dose, (size_t)V * 4, cudaMemcpyDefault, s));
-    double Fh = 0.0;
-    VMAT_CUDA(cudaMemcpyAsync(&Fh, F_dev, 8, cudaMemcpyDeviceToHost, s));
+    double Fh[2] = {0.0, 0.0}, mp_bytes = 0.0;
+    int32_t refine_it = 0;
+    VMAT_CUDA(cudaMemcpyAsync(Fh, F_dev, 16, cudaMemcpyDeviceToHost, s));
+    VMAT_CUDA(cudaMemcpyAsync(&mp_bytes, mp_bytes_dev, 8, cudaMemcpyDeviceToHost, s));
+    if (refine_iters) VMAT_CUDA(cudaMemcpyAsync(&refine_it, refine_iters, 4, cudaMemcpyDeviceToHost, s));
     VMAT_CUDA(cudaStreamSynchronize(s));
-    if (F_out) *F_out = Fh;
+    if (F_out) *F_out = Fh[0];
     if (stats) {
         double acc[PH_N] = {0};
         tm.accumulate(acc);
@@ -396,6 +447,11 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         stats->bb_iters_total = bb_total;
         stats->stop_reason = stop;
         stats->kernel_launches = g_launches.load() - launches0;
+        stats->refined = refine ? 1 : 0;
+        stats->refine_bb_iters = refine_it + refine_extra;
+        stats->t_refine_ms = acc[PH_REFINE];
+        stats->F_before_refine = refine ? Fh[1] : Fh[0];
+        stats->mp_bytes = mp_bytes + mp_bytes_host;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);

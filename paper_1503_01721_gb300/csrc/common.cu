@@ -82,6 +82,8 @@ void Ddc::free_all() {
     }
     f(act_vox);
     f(vox2act);
+    f(D_val_f32);
+    D_val_f32 = nullptr;
     f(scale);
     f(xs);
     f(cp_tab);
@@ -334,6 +336,7 @@ vmat_status ddc_info(vmat_ddc hd, vmat_ddc_info *out) {
         const int64_t b = m->col16 ? m->nnz * 2 + m->n_chunks * 4 + (int64_t)(m->n_rows + 1) * 8 : 0;
         (m == &h->D ? out->bytes16_D : out->bytes16_Dt) = b;
     }
+    out->refine_f32 = h->D_val_f32 ? 1 : 0;
     return VMAT_OK;
 }
 

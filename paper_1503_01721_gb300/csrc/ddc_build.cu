@@ -555,7 +555,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     clear_error();
     if (!hd) return set_error(VMAT_EINVAL, "ddc_build: handle is NULL");
     Ddc *h = as_ddc(hd);
-    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0, -1};
+    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0, -1, 0};
     if (opts_in) opts = *opts_in;
     if (opts.dtype != VMAT_F32 && opts.dtype != VMAT_BF16 && opts.dtype != VMAT_FP8E4M3)
         return set_error(VMAT_EINVAL, "ddc_build: unknown dtype %d", (int)opts.dtype);
@@ -744,6 +744,8 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         m.nnz = nnz;
         m.nnz_pad = pad;
         VMAT_TRY(quantise(b_val_d, (int32_t *)b_col_d.p, (int64_t *)b_rp_d.p, n_active, false, &m.val));
+        // FP32 refinement: the FP32 values stay beside the stored ones
+        if (opts.refine_f32 && opts.dtype != VMAT_F32) h->D_val_f32 = (float *)b_val_d.release();
         m.rowptr = (int64_t *)b_rp_d.release();
         m.col = (int32_t *)b_col_d.release();
         h->act_vox = (int32_t *)b_act.release();

@@ -111,6 +111,9 @@ struct Ddc {
     int32_t n_active = 0;
     int32_t *act_vox = nullptr; // [n_active] compact row -> voxel
     int32_t *vox2act = nullptr; // [V] voxel -> compact row or -1
+    // FP32 values of CSR(D) beside the stored BF16 / FP8 ones (build option refine_f32),
+    // same order and padding; the FP32 refinement at the end of cg_plan reads them
+    float *D_val_f32 = nullptr;
     float *scale = nullptr;     // [J] FP8 per-beamlet scale
     float *xs = nullptr;        // [J] scratch: scaled x for FP8 CSR(D)
     // Offsets of each CP's first entry in each CSR(D) row, [K + 1][n_active], for the
@@ -366,13 +369,18 @@ vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *
 // After column t of DA is written: mark the tiles it reaches, rebuild the list and F_off
 // (per-block counts, then ordered writes: the list and the sums are reproducible).
 vmat_status mp_live_update(const MpLive &L, int32_t t, cudaStream_t s);
+// The two halves of mp_live_update: mark the tiles column t reaches; rebuild the list and F_off.
+vmat_status mp_live_mark(const MpLive &L, int32_t t, cudaStream_t s);
+vmat_status mp_live_rebuild(const MpLive &L, cudaStream_t s);
 vmat_status mp_live_update_batched(const MpLive *plans, int32_t n_plans, int64_t max_wtiles, int32_t t,
                                    cudaStream_t s);
 // live (may be null): solve over the live tiles only, F offset F_offset + *live->F_off.
+// bytes_acc (may be null): device double, += the bytes of the solve's passes over DA.
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
                           const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                           float *z, const vmat_bb_opts *opts, double F_offset, void *ws, const int32_t *skip,
-                          int32_t *iters_acc, cudaStream_t s, const MpLive *live = nullptr);
+                          int32_t *iters_acc, cudaStream_t s, const MpLive *live = nullptr,
+                          double *bytes_acc = nullptr);
 // Batched master problems (persistent solver, one cooperative launch for all plans).
 // Per-plan arguments are an opaque mp_args_bytes() record filled by mp_fill_plan_args
 // (ws: mp_workspace_bytes(n_cap) bytes); mp_batched_grid gives the launch shape for

