@@ -75,9 +75,11 @@ struct MPArgs {
     const float *lo, *hi; // may be null
     double *G, *Gprev;
     float *yprev;
-    double *part;  // [P][n + 1]
+    double *part;  // fallback solver: [P][n + 1] doubles; persistent solver: two buffers (by iteration
+                   // parity) of float pairs, [2][n + 1][pstride] (column k of CTA c at k * pstride + c)
     double *cpart; // [P]
     int32_t P;
+    int32_t pstride; // CTAs a persistent partial buffer has room for
     int32_t n_tiles;  // 256-voxel tiles (fallback and Cauchy kernels)
     int64_t n_wtiles; // 32-voxel warp tiles
     BBState *st;
@@ -85,6 +87,7 @@ struct MPArgs {
     unsigned *epoch_snap;          // elastic batched solver: the batch epoch seen at this problem's last barrier
     const int32_t *skip;           // when non-null and set, the solve is skipped (device-driven plans)
     int32_t *iters_acc;            // when non-null, the persistent solver adds its iteration count
+    double *bytes_acc;             // when non-null, the persistent solver adds the bytes its passes moved
     int32_t *status;
     vmat_bb_opts opts;
     double F_offset;
@@ -378,6 +381,7 @@ struct PState {
     double F_hist[6];
     double F, delta0, gg, delta;
     int t, done, stop, decided;
+    int passes; // passes over DA (iterations and the Cauchy pass)
 };
 
 struct SolveSmem {
@@ -672,6 +676,10 @@ template <int NMAX> __device__ void solve_finish(const MPArgs &a, const SolveSme
         a.st->iters = ps.t + 1;
         a.st->delta0 = ps.delta0;
         if (ok && a.iters_acc) *a.iters_acc += ps.t + 1;
+        if (ok && a.bytes_acc) { // each pass reads the tiles' labels and columns and writes (or reads) their dose
+            const int64_t tiles = a.tiles ? min64((int64_t)max(__ldcg(a.n_live), 0), a.n_wtiles) : a.n_wtiles;
+            *a.bytes_acc += (double)ps.passes * (double)tiles * (double)(wt_copy_bytes(a.n) + 4 * MP_WT);
+        }
     }
     __threadfence();
 }
@@ -701,6 +709,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
         for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
         float fs = 0.f, fc = 0.f;
         const bool pass_ok = P.n_my == 0 || solve_pass<NMAX, PASS_ITER>(a, S, P, it, gacc, fs, fc);
+        if (tid == 0) ++ps.passes;
         if (!pass_ok && lane == 0) atomicOr(&abort_s, 1);
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
@@ -712,35 +721,42 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             }
         }
         const FF fb = block_ff(FF{fs, -fc}, shff); // includes a __syncthreads after wred
+        // this CTA's partials, column-major by CTA, in the buffer of this iteration's parity: a CTA
+        // writes buffer b again two iterations later, after the barrier that every CTA reaches only
+        // once it has read buffer b
+        FF *pb = part + (size_t)(ps.t & 1) * (n + 1) * a.pstride;
         for (int k = tid; k < n; k += MP_THREADS) {
             FF sum{S.wred[k], 0.f};
             for (int w = 1; w < MP_NW; ++w) sum = ff_add(sum, FF{S.wred[w * NMAX + k], 0.f});
-            part[(int64_t)cta * (n + 1) + k] = sum;
+            pb[(size_t)k * a.pstride + cta] = sum;
         }
-        if (tid == 0) part[(int64_t)cta * (n + 1) + n] = fb;
-        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) return LOOP_ABORT;
-        // ---- column reduction: warp w of CTA c sums columns c * MP_NW + w, + MP_NW * n_cta, ...
-        for (int k = (int)cta * MP_NW + wid; k <= n; k += MP_NW * (int)n_cta) {
+        if (tid == 0) pb[(size_t)n * a.pstride + cta] = fb;
+        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
+            return LOOP_ABORT;
+        // ---- every CTA reduces every column itself (warp w: columns w, w + MP_NW, ...), lane l
+        // summing CTAs l, l + 32, ... in order and then a fixed butterfly: the same G and F in
+        // every CTA, with no second barrier
+        for (int k = wid; k <= n; k += MP_NW) {
+            const float2 *col = reinterpret_cast<const float2 *>(pb + (size_t)k * a.pstride);
             FF v{0.f, 0.f};
             for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) { // eight loads in flight per lane
                 float2 q[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const unsigned b = b0 + 32u * u;
-                    q[u] = b < n_cta ? __ldcg(reinterpret_cast<const float2 *>(part) + (int64_t)b * (n + 1) + k)
-                                     : make_float2(0.f, 0.f);
+                    q[u] = b < n_cta ? __ldcg(col + b) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
-            if (lane == 0) a.G[k] = ff_to_double(v);
+            if (lane == 0) {
+                const double sum = ff_to_double(v);
+                if (k < n) S.sG[k] = -sum;
+                else ps.F = sum + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
+            }
         }
-        if (!grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
-            return LOOP_ABORT;
-        for (int k = tid; k < n; k += MP_THREADS) S.sG[k] = -__ldcg(a.G + k);
-        if (tid == 0) ps.F = __ldcg(a.G + n) + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
         __syncthreads();
         if (wid == 0) {
             solve_step<NMAX>(a, S, ps);
@@ -754,6 +770,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             __syncthreads();
             float cs = 0.f, cc = 0.f;
             const bool c_ok = P.n_my == 0 || solve_pass<NMAX, PASS_CAUCHY>(a, S, P, it, gacc, cs, cc);
+            if (tid == 0) ++ps.passes;
             if (!c_ok && lane == 0) atomicOr(&abort_s, 1);
             const FF cb = block_ff(FF{cs, -cc}, shff);
             if (tid == 0) cpart[cta] = cb;
@@ -1288,6 +1305,23 @@ vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *
     return VMAT_OK;
 }
 
+vmat_status mp_live_mark(const MpLive &L, int32_t t, cudaStream_t s) {
+    if (L.n_wtiles < 1) return VMAT_OK;
+    mp_live_mark_kernel<<<(unsigned)((L.n_wtiles * 32 + 255) / 256), 256, 0, s>>>(L, t);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+vmat_status mp_live_rebuild(const MpLive &L, cudaStream_t s) {
+    if (L.n_wtiles < 1) return VMAT_OK;
+    const unsigned nb = (unsigned)mp_live_blocks(L.n_wtiles);
+    mp_live_count_kernel<<<nb, LV_THREADS, 0, s>>>(L);
+    VMAT_LAUNCH_CHECK();
+    mp_live_write_kernel<<<nb, LV_THREADS, 0, s>>>(L);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
 vmat_status mp_live_update(const MpLive &L, int32_t t, cudaStream_t s) {
     if (L.n_wtiles < 1) return VMAT_OK;
     mp_live_mark_kernel<<<(unsigned)((L.n_wtiles * 32 + 255) / 256), 256, 0, s>>>(L, t);
@@ -1432,7 +1466,7 @@ static int mp_p_max(const DeviceCtx *ctx) { return ctx->n_sm * (2048 / MP_THREAD
 
 static size_t mp_ws_bytes(int n_cap, int p_max) {
     return 256 + (size_t)(n_cap + 1) * sizeof(double) + (size_t)n_cap * (sizeof(double) + sizeof(float)) +
-           (size_t)p_max * (n_cap + 1) * sizeof(double) + (size_t)p_max * sizeof(double) + 256;
+           2 * (size_t)p_max * (n_cap + 1) * sizeof(double) + (size_t)p_max * sizeof(double) + 256;
 }
 
 size_t mp_workspace_bytes(int32_t n_cap) {
@@ -1454,7 +1488,7 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.G = reinterpret_cast<double *>(p); // [n + 1]: G, then F in the persistent solver
     a.Gprev = a.G + n_cap + 1;
     a.part = a.Gprev + n_cap;
-    a.cpart = a.part + (size_t)p_max * (n_cap + 1);
+    a.cpart = a.part + 2 * (size_t)p_max * (n_cap + 1);
     a.yprev = reinterpret_cast<float *>(a.cpart + p_max);
     a.DA = DA;
     a.wstride = wstride;
@@ -1470,6 +1504,7 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.lo = lo;
     a.hi = hi;
     a.P = L.P;
+    a.pstride = p_max;
     a.n_tiles = (int32_t)((V + MP_THREADS - 1) / MP_THREADS);
     a.n_wtiles = ((int64_t)V + MP_WT - 1) / MP_WT;
     a.status = ctx->status;
@@ -1477,6 +1512,7 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.F_offset = F_offset;
     a.skip = nullptr;
     a.iters_acc = nullptr;
+    a.bytes_acc = nullptr;
     a.tiles = nullptr;
     a.n_live = nullptr;
     a.F_off_dev = nullptr;
@@ -1496,7 +1532,7 @@ static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream
 vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_cap, int64_t wstride,
                           const uint8_t *struct_id, const vmat_voxels *vox, const float *lo, const float *hi, float *y,
                           float *z, const vmat_bb_opts *opts_in, double F_offset, void *ws, const int32_t *skip,
-                          int32_t *iters_acc, cudaStream_t s, const MpLive *live) {
+                          int32_t *iters_acc, cudaStream_t s, const MpLive *live, double *bytes_acc) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     vmat_bb_opts opts = {500, 1e-6, 1e-9, 1e-12, 1e12};
@@ -1512,6 +1548,7 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
                  ctx);
     a.skip = skip;
     a.iters_acc = iters_acc;
+    a.bytes_acc = bytes_acc;
     if (live) {
         a.tiles = live->tiles;
         a.n_live = live->n_live;
