@@ -51,7 +51,9 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
                 6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>",
                 9: "spmv_warp_row_c_kernel<256,4>", 10: "spmv_warp_row_c_kernel<256,8>",
                 11: "spmv_warp_row_c_kernel<512,4>", 12: "spmv_warp_row_z_kernel<256,4>",
-                13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>"}
+                13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>",
+                15: "spmv_warp_row_t_kernel<256,512,4>", 16: "spmv_warp_row_t_kernel<512,256,3>",
+                17: "spmv_warp_row_t_kernel<256,1024,3>", 18: "spmv_warp_row_t_kernel<384,512,3>"}
 # configurations that read the 16-bit column index (built with index16)
 INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
@@ -198,26 +200,49 @@ def sample_case():
     return geom.V, len(keep_cp) * bpc, vox, blt, val, structs, mlc
 
 
-def run_oracle_steps(steps, warmup):
-    """Time the FP64 oracle's column generation on the CPU sample (one thread)."""
+def _sample_dir():
+    import tempfile
+    base = "/dev/shm" if os.path.isdir("/dev/shm") and os.access("/dev/shm", os.W_OK) else None
+    return tempfile.mkdtemp(prefix="vmat_oracle_sample_", dir=base)
+
+
+def prepare_cpu_sample(path):
+    """Generate the CPU sample once and store the oracle's float64 CSR of D (and the
+    plan inputs) under path, so that every oracle process maps the same arrays."""
+    import numpy as np
+    import oracle
+    V, J, vox, blt, val, structs, mlc = sample_case()
+    D = oracle.ddc_matrix(V, J, vox, blt, val)
+    for nm in ("data", "indices", "indptr"):
+        np.save(os.path.join(path, nm + ".npy"), getattr(D, nm))
+    np.savez(os.path.join(path, "meta.npz"), V=V, J=J, nnz=len(val), K=mlc.K, n_rows=mlc.n_rows,
+             n_cols=mlc.n_cols, per_blt=np.bincount(blt, minlength=J),
+             n_rows_D=int(np.count_nonzero(np.bincount(vox, minlength=V))), struct_id=structs.struct_id,
+             T=structs.T, w_over=structs.w_over, w_under=structs.w_under)
+
+
+def _load_cpu_sample(path):
+    import numpy as np
+    import scipy.sparse as sp
+    import synth
+    m = np.load(os.path.join(path, "meta.npz"))
+    ld = lambda nm: np.load(os.path.join(path, nm + ".npy"), mmap_mode="r")
+    D = sp.csr_matrix((ld("data"), ld("indices"), ld("indptr")), shape=(int(m["V"]), int(m["J"])), copy=False)
+    structs = synth.Structures(m["struct_id"], m["T"], m["w_over"], m["w_under"], [])
+    mlc = synth.MLC(int(m["K"]), int(m["n_rows"]), int(m["n_cols"]), np.array([0], np.int32), 3)
+    return D, structs, mlc, m
+
+
+def _plan_bytes(plan, mlc, m):
+    """Bytes of a sample plan's sparse passes in the GPU's FP32-CSR byte model: each pricing
+    pass counts the beamlet rows inside the leaf-travel windows of the unoccupied CPs (the
+    prices pricing reads), as the GPU's windowed pass does, plus g and the window table;
+    then the final D x."""
     import numpy as np
     import oracle
     from paper_1503_01721_gb300 import roofline
-    V, J, vox, blt, val, structs, mlc = sample_case()
-    D = oracle.ddc_matrix(V, J, vox, blt, val)
-    nnz = len(val)
-    n_rows_D = int(np.count_nonzero(np.bincount(vox, minlength=V)))
-    times, gbytes = [], 0.0
-    for it in range(warmup + steps):
-        t0 = time.perf_counter()
-        plan = oracle.cg_plan(D, mlc, structs, SAMPLE_APERTURES)
-        dt = time.perf_counter() - t0
-        if it >= warmup:
-            times.append(dt)
-    # bytes of the plan's sparse passes in the GPU's FP32-CSR byte model: each pricing pass counts
-    # the beamlet rows inside the leaf-travel windows of the unoccupied CPs (the prices pricing reads),
-    # as the GPU's windowed pass does, plus g and the window table; then the final D x
-    per_blt = np.bincount(blt, minlength=J).reshape(mlc.K, mlc.n_rows, mlc.n_cols)
+    V, J = int(m["V"]), int(m["J"])
+    per_blt = m["per_blt"].reshape(mlc.K, mlc.n_rows, mlc.n_cols)
     col = np.arange(mlc.n_cols)[None, :]
     n_price = len(plan.cps) + (plan.stop == "price")
     b = 0.0
@@ -234,33 +259,199 @@ def run_oracle_steps(steps, warmup):
         if t < len(plan.cps):
             occupied[plan.cps[t]] = True
             leaves_all[plan.cps[t]] = plan.leaves[t]
-    b += roofline.spmv_bytes(nnz, n_rows_D, J, V)
-    per_step = sum(times) / len(times)
-    return {"value": b / per_step / 1e9, "sec_per_plan": per_step, "nnz": nnz, "J": J, "V": V,
-            "apertures": len(plan.cps), "F": plan.F}
+    return b + roofline.spmv_bytes(int(m["nnz"]), int(m["n_rows_D"]), J, V)
 
 
-def cpu_baseline_subprocess(steps=1, warmup=0):
-    """Run the oracle sample in a fresh single-threaded process (no CUDA in it)."""
-    # the timed oracle is single-threaded (scipy sparse products, BLAS pinned to one
-    # thread); the untimed input generator keeps its OpenMP threads
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="",
-               VMAT_ORACLE_SUBPROCESS="1")
-    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"print(json.dumps(bench.run_oracle_steps({steps}, {warmup})))")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def oracle_worker(path, steps, warmup, barrier, queue):
+    """One oracle process (one thread): `warmup` + `steps` sample plans, then D^T g and
+    D x passes over the sample, each phase started together with the other processes."""
+    import numpy as np
+    import oracle
+    from paper_1503_01721_gb300 import roofline
+    try:
+        D, structs, mlc, m = _load_cpu_sample(path)
+        V, J = int(m["V"]), int(m["J"])
+        rng = np.random.default_rng(0)
+        g, x = rng.standard_normal(V), rng.random(J)
+        times = []
+        for it in range(warmup + steps):
+            barrier.wait()
+            t0 = time.perf_counter()
+            plan = oracle.cg_plan(D, mlc, structs, SAMPLE_APERTURES)
+            if it >= warmup:
+                times.append(time.perf_counter() - t0)
+        pt = {}
+        for nm, fn, arg in (("dt_g", oracle.beamlet_price, g), ("d_x", oracle.dose_forward, x)):
+            ts = []
+            for _ in range(3):
+                barrier.wait()
+                t0 = time.perf_counter()
+                fn(D, arg)
+                ts.append(time.perf_counter() - t0)
+            pt[nm] = float(np.median(ts))
+        nnz = int(m["nnz"])
+        queue.put({"sec_per_plan": sum(times) / len(times), "plan_bytes": _plan_bytes(plan, mlc, m),
+                   "dt_g_s": pt["dt_g"], "d_x_s": pt["d_x"],
+                   "dt_g_bytes": roofline.spmv_bytes(nnz, J, V, J), "d_x_bytes": roofline.spmv_bytes(nnz,
+                   int(m["n_rows_D"]), J, V), "nnz": nnz, "J": J, "V": V, "apertures": len(plan.cps),
+                   "F": plan.F})
+    except BaseException as e:  # report instead of leaving the others at the barrier
+        barrier.abort()
+        queue.put({"error": repr(e)})
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_procs(path, n_proc, steps, warmup):
+    """n_proc single-threaded oracle processes on the same sample, in step.  Whole-job
+    rates: the bytes of every process over the slowest process's time."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")  # the parent may hold a CUDA context
+    barrier, queue = ctx.Barrier(n_proc), ctx.Queue()
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                               "CUDA_VISIBLE_DEVICES")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        procs = [ctx.Process(target=oracle_worker, args=(path, steps, warmup, barrier, queue)) for _ in range(n_proc)]
+        for p in procs:
+            p.start()
+        res = [queue.get(timeout=1800) for _ in range(n_proc)]
+        for p in procs:
+            p.join(timeout=60)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    bad = [r["error"] for r in res if "error" in r]
+    if bad:
+        raise RuntimeError("oracle process failed: " + bad[0])
+    r0 = res[0]
+    t_plan = max(r["sec_per_plan"] for r in res)
+    t_dt, t_d = max(r["dt_g_s"] for r in res), max(r["d_x_s"] for r in res)
+    return {"value": sum(r["plan_bytes"] for r in res) / t_plan / 1e9, "sec_per_plan": t_plan, "procs": n_proc,
+            "dt_g_gbs": n_proc * r0["dt_g_bytes"] / t_dt / 1e9, "d_x_gbs": n_proc * r0["d_x_bytes"] / t_d / 1e9,
+            "nnz": r0["nnz"], "J": r0["J"], "V": r0["V"], "apertures": r0["apertures"], "F": r0["F"]}
+
+
+def cpu_baseline(steps=1, warmup=0):
+    """The FP64 oracle on the CPU sample: one process per host core, and one alone."""
+    import shutil
+    path = _sample_dir()
+    try:
+        prepare_cpu_sample(path)
+        n = host_cores()
+        single = run_oracle_procs(path, 1, steps, warmup)
+        allc = run_oracle_procs(path, n, steps, warmup) if n > 1 else single
+    finally:
+        shutil.rmtree(path, ignore_errors=True)
+    allc["single_thread"] = {k: single[k] for k in ("value", "sec_per_plan", "dt_g_gbs", "d_x_gbs")}
+    return allc
 
 
 def sample_desc(res):
     return (f"FP64 oracle cg_plan, {SAMPLE_APERTURES} apertures, on every {SAMPLE_CP_STRIDE}th CP of the "
-            f"{WORKLOAD} geometry ({res['J']} beamlets, {res['nnz']} nonzeros); same byte model (rows inside "
-            f"the leaf-travel windows per pricing pass)")
+            f"{WORKLOAD} geometry ({res['J']} beamlets, {res['nnz']} nonzeros), one single-threaded process per "
+            f"host core ({res['procs']}) on the same sample, whole-job bytes over the slowest process's time; "
+            f"same byte model (rows inside the leaf-travel windows per pricing pass)")
+
+
+def cpu_block(res):
+    return {"value": round(res["value"], 4), "unit": "GB/s", "cores": res["procs"], "kind": "oracle",
+            "sample": sample_desc(res), "sec_per_plan": round(res["sec_per_plan"], 3),
+            "spmv_passes": {"dt_g_gbs": round(res["dt_g_gbs"], 3), "d_x_gbs": round(res["d_x_gbs"], 3)},
+            "single_thread": {k: round(v, 4) for k, v in res["single_thread"].items()}}
 
 
 # ----------------------------------------------------------------------------- GPU arm
+
+def sampled_dose_error(case, cps, lv, y, dose, n_ap, n=4096, seed=5):
+    """Final dose against the float64 sum over the COO's float32 entries of D (A y), at
+    n sampled voxels: max |d - d_ref| / max |d_ref| over the sample."""
+    import numpy as np
+    m = case.mlc
+    cps = np.asarray(cps)[:n_ap].astype(np.int64)
+    lv = np.asarray(lv).reshape(-1, m.n_rows, 2)[:n_ap].astype(np.int64)
+    y = np.asarray(y)[:n_ap].astype(np.float64)
+    x = np.zeros(case.J)  # x = A y: each aperture's fluence on its beamlets
+    for a, k in enumerate(cps):
+        for r in range(m.n_rows):
+            base = (int(k) * m.n_rows + r) * m.n_cols
+            x[base + lv[a, r, 0]: base + lv[a, r, 1]] += y[a]
+    voxels = np.random.default_rng(seed).choice(case.V, n, replace=False)
+    flag = np.zeros(case.V, bool)
+    flag[voxels] = True
+    sel = np.flatnonzero(flag[case.vox])
+    ref = np.bincount(case.vox[sel], weights=case.val[sel].astype(np.float64) * x[case.blt[sel]],
+                      minlength=case.V)[voxels]
+    err = float(np.max(np.abs(np.asarray(dose)[voxels] - ref)) / max(float(np.max(np.abs(ref))), 1e-300))
+    return {"rel_linf": err, "voxels": n,
+            "against": "float64 sum of D (A y) over the float32 COO entries, at seeded sampled voxels"}
+
+
+def precision_form(dev, steps=3, warmup=1):
+    """The precision form on the two-arc case (1.93e9 nonzeros): the same 60-aperture plan
+    with the DDC stored as FP32, BF16 and FP8 E4M3 (the low-precision handles also keep
+    FP32 values of CSR(D) for the end-of-plan refinement)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1503_01721_gb300 import api
+    t0 = time.time()
+    case = synth.make_case("cfg3", seed=0, cache=False)
+    log(f"[forms] cfg3: {case.nnz} nonzeros in {time.time() - t0:.1f}s")
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+    coo = (pin(case.vox, torch.int32), pin(case.blt, torch.int32), pin(case.val, torch.float32))
+    vox = api.VoxelParams.from_numpy(case.structs, dev)
+    n_ap = case.n_apertures
+    stream = torch.cuda.current_stream()
+    res = {}
+    for dt in ("f32", "bf16", "fp8"):
+        h = api.ddc_load_coo(case.V, case.J, *coo)
+        api.ddc_build(h, dt, autotune=True, refine=dt != "f32")
+        cps = torch.empty(n_ap, dtype=torch.int32)
+        lv = torch.empty(n_ap * case.mlc.n_rows * 2, dtype=torch.int16)
+        y = torch.empty(n_ap, dtype=torch.float32)
+        dose = torch.empty(case.V, dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            api.cg_plan(h, case.mlc, vox, n_ap)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sts = []
+        for _ in range(steps):
+            F, st = api.cg_plan(h, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose)
+            sts.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = api.ddc_info(h)
+        api.ddc_free(h)
+        st = sts[-1]
+        res[dt] = {"ms_per_plan": round(e0.elapsed_time(e1) / steps, 3), "F": F,
+                   "pp1_spmv_ms": round(sum(x["pp1_spmv_ms"] for x in sts) / steps, 3),
+                   "pp1_spmv_gbs": round(sum(x["pp1_spmv_bytes"] for x in sts) / sum(x["pp1_spmv_ms"] for x in sts)
+                                         / 1e6, 1),
+                   "t_refine_ms": round(st["t_refine_ms"], 3), "F_before_refine": st["F_before_refine"],
+                   "refine_bb_iters": st["refine_bb_iters"], "cfg_Dt": int(info["cfg_Dt"]),
+                   "dose_err": sampled_dose_error(case, cps.numpy(), lv.numpy(), y.numpy(), dose.cpu().numpy(),
+                                                  int(st["n_apertures"]))}
+    f32 = res["f32"]
+    return {"workload": "cfg3 " + DESCS["cfg3"] + f", {case.nnz} nonzeros", "plans": res,
+            "bf16_speedup": round(f32["ms_per_plan"] / res["bf16"]["ms_per_plan"], 3),
+            "fp8_speedup": round(f32["ms_per_plan"] / res["fp8"]["ms_per_plan"], 3),
+            "pp1_speedup": {d: round(f32["pp1_spmv_ms"] / res[d]["pp1_spmv_ms"], 3) for d in ("bf16", "fp8")},
+            "F_rel_err": {d: (res[d]["F"] - f32["F"]) / f32["F"] for d in ("bf16", "fp8")},
+            "dose_rel_err": {d: res[d]["dose_err"]["rel_linf"] for d in ("f32", "bf16", "fp8")},
+            "notes": "speedups and F_rel_err against the FP32 plan on the same GPU; the BF16 / FP8 plans end "
+                     "with the FP32 refinement (DA of the placed apertures and the final dose from FP32 values)"}
+
+
 
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -347,6 +538,19 @@ def run_ours(args, rank, world, local):
             "nominal_peak": roofline.HBM_NOMINAL_GBS, "bytes_per_launch": round(bytes_launch),
             "avg_launch_ms": round(spmv_ms / max(spmv_n, 1), 4)}
 
+    # the last timed plan's final dose against float64 sums over the COO at sampled voxels
+    dose_err = sampled_dose_error(case, cps.numpy(), lv.numpy(), y.numpy(), dose.cpu().numpy(),
+                                  int(stats_all[-1]["n_apertures"]))
+    # master problem: the bytes its passes moved over the time of the MP phase
+    mp_bytes = sum(s["mp_bytes"] for s in stats_all)
+    mp_ms = sum(s["t_mp_ms"] for s in stats_all)
+    mp_roof = {"bound": "hbm", "kernel": "mp_solve_kernel (persistent BB master problem over the live tiles)",
+               "achieved": round(mp_bytes / (mp_ms * 1e-3) / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": round(mp_bytes / (mp_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+               "bytes_per_step": round(mp_bytes / args.steps), "ms_per_step": round(mp_ms / args.steps, 3),
+               "bb_iters_per_step": stats_all[-1]["bb_iters_total"],
+               "timing": "library CUDA events around each plan's master-problem phase"}
+
     # isolated full passes: D^T g and D x over the whole matrix
     g = torch.rand(case.V, device=dev)
     x = torch.rand(case.J, device=dev)
@@ -413,8 +617,24 @@ def run_ours(args, rank, world, local):
                        "cg_plan, results device->host"}
 
     out = None
+    forms = None
+    if rank == 0 and world == 1 and args.forms != "none":
+        api.ddc_free(h)  # room for the forms' matrices
+        h = None
+        forms = {}
+        try:
+            forms["precision"] = precision_form(dev)
+        except Exception as e:  # the headline line stands without it
+            forms["precision"] = {"error": repr(e)[:400]}
+        if args.forms == "full":
+            try:
+                b = batch_measure("cfg5", "bf16", 1, 1)
+                forms["batching"] = {k: b[k] for k in ("workload", "n_plans", "nnz", "dtype", "batched",
+                                                       "one_by_one", "speedup", "F_rel_diff_max")}
+            except Exception as e:
+                forms["batching"] = {"error": repr(e)[:400]}
     if rank == 0:
-        cpu = cpu_baseline_subprocess(1, 0) if world == 1 and not args.no_cpu else None
+        cpu = cpu_baseline(1, 0) if world == 1 and not args.no_cpu else None
         st = stats_all[-1]
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -427,9 +647,7 @@ def run_ours(args, rank, world, local):
                        "l2": "inputs larger than L2 (CSR D + D^T %.1f GB)" % ((info["bytes_D"] + info["bytes_Dt"]) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
-            "cpu_baseline": None if cpu is None else {
-                "value": round(cpu["value"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                "sample": sample_desc(cpu), "sec_per_plan": round(cpu["sec_per_plan"], 3)},
+            "cpu_baseline": None if cpu is None else cpu_block(cpu),
             "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plan": {"F": Fs[-1], "F_spread": max(Fs) - min(Fs), "apertures": st["n_apertures"],
                      "stop": st["stop"], "bb_iters": st["bb_iters_total"],
@@ -438,8 +656,12 @@ def run_ours(args, rank, world, local):
                                    ("t_pp1_ms", "t_pp2_ms", "t_da_ms", "t_mp_ms", "t_final_ms", "t_total_ms")},
                      "build_ms": round(info["build_ms"], 1)},
             "spmv_pair": pair,
+            "mp_roofline": mp_roof,
+            "forms": forms,
         }
-    api.ddc_free(h)
+        out["plan"]["dose_err"] = dose_err
+    if h is not None:
+        api.ddc_free(h)
     return out
 
 
@@ -559,6 +781,12 @@ def run_mp_only(args):
 
 
 def run_batch(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    return batch_measure(args.workload, args.dtype, args.steps, args.warmup)
+
+
+def batch_measure(workload, dtype, steps, warmup):
     """Batched plans: every plan of a batch workload resident in HBM, then timed
     runs of the whole batch (one CUDA graph per run) against the same plans run one
     after another through cg_plan.  Aggregate GB/s = the algorithmic bytes of every
@@ -567,11 +795,8 @@ def run_batch(args):
     import torch
     import synth
     from paper_1503_01721_gb300 import api, roofline
-    import __graft_entry__
 
-    __graft_entry__.build()
-    dtype = args.dtype
-    specs = synth.batch_specs(args.workload)
+    specs = synth.batch_specs(workload)
     plans, keep, nnz = [], [], 0
     t0 = time.time()
     for sp in specs:
@@ -587,23 +812,23 @@ def run_batch(args):
     batch = api.Batch(plans)
     info = batch.info()
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         Fb, stb = batch.run()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / args.steps
+    ms_batch = e0.elapsed_time(e1) / steps
     bytes_run = sum(s["pp1_spmv_bytes"] + s["other_spmv_bytes"] for s in stb)
     # the same plans one after another
     for h, mlc, vox, n in plans:
         api.cg_plan(h, mlc, vox, n)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         Fs, sts = [], []
         for h, mlc, vox, n in plans:
             F, st = api.cg_plan(h, mlc, vox, n)
@@ -611,11 +836,11 @@ def run_batch(args):
             sts.append(st)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1) / args.steps
+    ms_seq = e0.elapsed_time(e1) / steps
     bytes_seq = sum(s["pp1_spmv_bytes"] + s["other_spmv_bytes"] for s in sts)
     rel = [abs(a - b) / max(abs(b), 1e-30) for a, b in zip(Fb, Fs)]
     peaks = roofline.measured_peaks()
-    out = {"mode": "batch", "workload": args.workload, "n_plans": len(specs), "nnz": nnz, "dtype": dtype,
+    out = {"mode": "batch", "workload": workload, "n_plans": len(specs), "nnz": nnz, "dtype": dtype,
            "batched": {"ms_per_run": round(ms_batch, 3), "gbs": round(bytes_run / ms_batch / 1e6, 1),
                        "frac_of_hbm": round(bytes_run / ms_batch / 1e6 / peaks["hbm_gbs"], 4)},
            "one_by_one": {"ms_per_run": round(ms_seq, 3), "gbs": round(bytes_seq / ms_seq / 1e6, 1)},
@@ -696,16 +921,24 @@ def run_truncation(args):
 
 
 def run_reference(args, rank, world):
+    """The FP64 CPU oracle (the only reference that exists) on the machine's host cores: each
+    step is one sample plan in every one of host_cores() single-threaded processes."""
     if rank != 0:
         return None
-    res = cpu_baseline_subprocess(args.steps, args.warmup)
+    import shutil
+    path = _sample_dir()
+    try:
+        prepare_cpu_sample(path)
+        res = run_oracle_procs(path, host_cores(), args.steps, args.warmup)
+    finally:
+        shutil.rmtree(path, ignore_errors=True)
     return {"impl": "reference", "metric": METRIC, "value": round(res["value"], 4), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(res["sec_per_plan"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{WORKLOAD} {WORKLOAD_DESC}", "sample": sample_desc(res)},
-            "cpu_baseline": {"value": round(res["value"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": sample_desc(res)},
+            "cpu_baseline": {"value": round(res["value"], 4), "unit": "GB/s", "cores": res["procs"],
+                             "kind": "oracle", "sample": sample_desc(res)},
             "e2e": {"value": round(res["value"], 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -719,6 +952,9 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--forms", default="full", choices=["full", "precision", "none"],
+                    help="after the headline plan (one GPU): the precision form on the two-arc case and, with "
+                         "full, the 24-plan BF16 batch against the same plans one by one")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(DESCS) + ["cfg5", "cfg5q", "batch_small"])
     ap.add_argument("--mode", default="plan", choices=["plan", "spmv", "mp", "batch", "truncation"],
                     help="spmv: only build and run D^T g and D x a few times (profiling driver); "

@@ -389,6 +389,8 @@ struct SolveSmem {
     float4 *sy4;           // [GMAX]   y, zero-padded
     float4 *sg4;           // [GMAX]   G as float (Cauchy pass), zero-padded
     double *sG, *sGp;      // [NMAX]   G_t, G_{t-1}
+    double *sS, *sR;       // [NMAX]   s = y_t - y_{t-1}, r = G_t - G_{t-1} (the step's inputs)
+    double *sRed;          // [8]      the step's sums and maxima
     float *sYp;            // [NMAX]   y_{t-1}
     float *wred;           // [MP_NW][NMAX]
     float *sT, *sO, *sU;   // [256]
@@ -396,7 +398,7 @@ struct SolveSmem {
 };
 
 template <int NMAX> __host__ __device__ constexpr size_t solve_fixed_smem() {
-    return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 2 * (size_t)NMAX * 8 + (size_t)NMAX * 4 +
+    return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 4 * (size_t)NMAX * 8 + 8 * 8 + (size_t)NMAX * 4 +
            (size_t)MP_NW * NMAX * 4 + 3 * 256 * 4;
 }
 
@@ -506,15 +508,19 @@ __device__ FF block_ff(FF v, FF *sh) {
     return t;
 }
 
-// Warp 0: Eq. 9-10 freeze, stopping tests, BB step length, projected update, all
-// on the shared-memory copy of the state.  Every CTA runs it on identical inputs.
+// Eq. 9-10 freeze, stopping tests, BB step length (FP64) and projected update, on the
+// shared-memory copy of the state, run by the whole CTA.  FP64 issues at a small
+// fraction of the FP32 rate on this GPU and one warp's chain of FP64 operations was
+// the step's cost, so the work is spread: one aperture per thread (freeze, s, r),
+// then one warp per sum or maximum (each lane over apertures l, l + 32, ... in
+// order, then a fixed butterfly), then thread 0 decides.  Every CTA runs it on
+// identical inputs.  Ends synchronised.
 template <int NMAX>
-__device__ void solve_step(const MPArgs &a, const SolveSmem &S, PState &ps) {
-    const int lane = threadIdx.x & 31;
+__device__ void solve_step_cta(const MPArgs &a, const SolveSmem &S, PState &ps) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = a.n, t = ps.t;
     float *y = reinterpret_cast<float *>(S.sy4);
-    double dy = 0.0, ymax = 0.0, gg = 0.0, ss = 0.0, sr = 0.0, rr = 0.0;
-    for (int k = lane; k < n; k += 32) {
+    for (int k = tid; k < n; k += MP_THREADS) {
         float yk = y[k];
         const float l = lo_of(a, k), h = hi_of(a, k);
         double g = S.sG[k];
@@ -527,26 +533,44 @@ __device__ void solve_step(const MPArgs &a, const SolveSmem &S, PState &ps) {
         }
         y[k] = yk;
         S.sG[k] = g;
-        ymax = fmax(ymax, fabs((double)yk));
-        gg += g * g;
         if (t > 0) {
-            const double sk = (double)yk - (double)S.sYp[k], rk = g - S.sGp[k];
-            dy = fmax(dy, fabs(sk));
-            ss += sk * sk;
-            sr += sk * rk;
-            rr += rk * rk;
+            S.sS[k] = (double)yk - (double)S.sYp[k];
+            S.sR[k] = g - S.sGp[k];
         }
     }
+    __syncthreads();
+    // warp q: 0 G.G, 1 s.s, 2 s.r, 3 r.r, 4 max |s|, 5 max |y|
+    if (wid < 6 && (wid == 0 || wid == 5 || t > 0)) {
+        double v = 0.0;
+        for (int k = lane; k < n; k += 32) {
+            if (wid == 0) {
+                const double g = S.sG[k];
+                v += g * g;
+            } else if (wid == 1) {
+                const double sk = S.sS[k];
+                v += sk * sk;
+            } else if (wid == 2) {
+                v += S.sS[k] * S.sR[k];
+            } else if (wid == 3) {
+                const double rk = S.sR[k];
+                v += rk * rk;
+            } else if (wid == 4) {
+                v = fmax(v, fabs(S.sS[k]));
+            } else {
+                v = fmax(v, fabs((double)y[k]));
+            }
+        }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        dy = fmax(dy, __shfl_xor_sync(0xffffffffu, dy, d));
-        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, d));
-        gg += __shfl_xor_sync(0xffffffffu, gg, d);
-        ss += __shfl_xor_sync(0xffffffffu, ss, d);
-        sr += __shfl_xor_sync(0xffffffffu, sr, d);
-        rr += __shfl_xor_sync(0xffffffffu, rr, d);
+        for (int d = 16; d > 0; d >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, v, d);
+            v = wid < 4 ? v + o : fmax(v, o);
+        }
+        if (lane == 0) S.sRed[wid] = v;
     }
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
+        const double gg = S.sRed[0], ss = S.sRed[1], sr = S.sRed[2], rr = S.sRed[3], dy = S.sRed[4],
+                     ymax = S.sRed[5];
         const double F = ps.F;
         ps.decided = 1;
         ps.F_hist[t % 6] = F;
@@ -576,20 +600,21 @@ __device__ void solve_step(const MPArgs &a, const SolveSmem &S, PState &ps) {
             ps.decided = 0;
         }
     }
-    __syncwarp();
+    __syncthreads();
 }
 
-// y <- clamp(y - delta G) after saving (y, G) as the previous iterate (warp 0).
-__device__ void solve_take_step(const MPArgs &a, const SolveSmem &S, double delta) {
+// y <- clamp(y - delta G) after saving (y, G) as the previous iterate, one aperture
+// per thread (the whole CTA).  Ends synchronised.
+__device__ void solve_take_step_cta(const MPArgs &a, const SolveSmem &S, double delta) {
     float *y = reinterpret_cast<float *>(S.sy4);
-    for (int k = threadIdx.x & 31; k < a.n; k += 32) {
+    for (int k = threadIdx.x; k < a.n; k += MP_THREADS) {
         const float yk = y[k];
         S.sYp[k] = yk;
         S.sGp[k] = S.sG[k];
         const double yn = (double)yk - delta * S.sG[k];
         y[k] = fminf(fmaxf((float)yn, lo_of(a, k)), hi_of(a, k));
     }
-    __syncwarp();
+    __syncthreads();
 }
 
 // Shared-memory layout of the solver for NMAX apertures and `stages` tiles per warp.
@@ -601,7 +626,10 @@ template <int NMAX> __device__ __forceinline__ SolveSmem solve_layout(unsigned c
     S.sg4 = S.sy4 + GMAX;
     S.sG = reinterpret_cast<double *>(S.sg4 + GMAX);
     S.sGp = S.sG + NMAX;
-    S.sYp = reinterpret_cast<float *>(S.sGp + NMAX);
+    S.sS = S.sGp + NMAX;
+    S.sR = S.sS + NMAX;
+    S.sRed = S.sR + NMAX;
+    S.sYp = reinterpret_cast<float *>(S.sRed + 8);
     S.wred = S.sYp + NMAX;
     S.sT = S.wred + MP_NW * NMAX;
     S.sO = S.sT + 256;
@@ -758,11 +786,8 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             }
         }
         __syncthreads();
-        if (wid == 0) {
-            solve_step<NMAX>(a, S, ps);
-            if (ps.decided == 0) solve_take_step(a, S, ps.delta);
-        }
-        __syncthreads();
+        solve_step_cta<NMAX>(a, S, ps);
+        if (ps.decided == 0) solve_take_step_cta(a, S, ps.delta);
         if (ps.decided == 2) {
             // ---- Cauchy step: delta0 = G.G / (2 sum_i w_i (DA G)_i^2)
             for (int k = tid; k < 4 * GMAX; k += MP_THREADS)
@@ -798,10 +823,9 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
                         ps.delta0 = ps.gg / curv;
                     }
                 }
-                __syncwarp();
-                if (!ps.done) solve_take_step(a, S, ps.delta0);
             }
             __syncthreads();
+            if (!ps.done) solve_take_step_cta(a, S, ps.delta0);
         }
         if (ps.done) return LOOP_DONE;
         if (tid == 0) ++ps.t;
@@ -1360,8 +1384,8 @@ vmat_status mp_write_labels(const uint8_t *sid, int32_t V, int64_t wstride, floa
 static int solve_nmax(int n) { return ((n + 7) / 8) * 8; }
 static size_t solve_fixed(int n) {
     const int nmax = solve_nmax(n);
-    return 128 /* alignment slack */ + 2 * (size_t)(nmax / 4) * 16 + 2 * (size_t)nmax * 8 + (size_t)nmax * 4 +
-           (size_t)MP_NW * nmax * 4 + 3 * 256 * 4;
+    return 128 /* alignment slack */ + 2 * (size_t)(nmax / 4) * 16 + 4 * (size_t)nmax * 8 + 8 * 8 +
+           (size_t)nmax * 4 + (size_t)MP_NW * nmax * 4 + 3 * 256 * 4;
 }
 static size_t solve_smem(int n, int stages) {
     return solve_fixed(n) + (size_t)stages * (MP_NW * wt_copy_bytes(n) + MP_NW * 8);
