@@ -51,9 +51,7 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
                 6: "spmv_warp_row_kernel<512,4>", 7: "spmv_warp_row_kernel<256,4>", 8: "spmv_warp_row_kernel<256,8>",
                 9: "spmv_warp_row_c_kernel<256,4>", 10: "spmv_warp_row_c_kernel<256,8>",
                 11: "spmv_warp_row_c_kernel<512,4>", 12: "spmv_warp_row_z_kernel<256,4>",
-                13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>",
-                15: "spmv_warp_row_t_kernel<256,512,4>", 16: "spmv_warp_row_t_kernel<512,256,3>",
-                17: "spmv_warp_row_t_kernel<256,1024,3>", 18: "spmv_warp_row_t_kernel<384,512,3>"}
+                13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>"}
 # configurations that read the 16-bit column index (built with index16)
 INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,

@@ -168,8 +168,10 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     PricingGeom pg;
     VMAT_TRY(pricing_geom(mlc, &pg));
     short2 *win;
+    int32_t *woff; // the rows inside the windows as one list (window_offsets)
     unsigned long long *wcount;
     VMAT_TRY(ar.get(&win, (size_t)K * NR));
+    VMAT_TRY(ar.get(&woff, (size_t)K * NR + 1));
     VMAT_TRY(ar.get(&wcount, (size_t)3 * nap_max));
     // live tiles of the master problem (the 32-voxel tiles some placed aperture reaches)
     MpLive live;
@@ -285,9 +287,10 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         // prices only where pricing reads them: the columns of each row's window
         VMAT_TRY(price_windows(pg, occupied, leaves_all, win, h.Dt.rowptr, z_dt ? h.Dt.cptr : nullptr,
                                t < nap_max ? wcount + 3 * t : nullptr, ctl, s));
+        VMAT_TRY(window_offsets(win, K * NR, woff, ctl, s));
         tm.mark(PH_SPMV);
         VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr,
-                          RowMask{nullptr, win, bpc, mlc->n_cols}, s, ctl));
+                          RowMask{nullptr, win, bpc, mlc->n_cols, woff, K * NR}, s, ctl));
         ++spmv_launches;
         // ---- PP2, and the commit (or the stop) on the device
         tm.mark(PH_PP2);

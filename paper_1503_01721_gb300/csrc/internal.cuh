@@ -143,11 +143,17 @@ int value_bytes(vmat_dtype t);
 // the columns that the leaf-travel windows let pricing read (price_windows).
 // Rows not needed are not computed: y holds unspecified values there (the tile
 // configurations write every row of a tile that holds a needed row).
+// woff (may be null, with win): the windows' rows as one list, woff[q] = the rows inside the
+// windows of segments 0 .. q - 1 (nseg + 1 entries, window_offsets); the row kernels then
+// take list entries in order instead of visiting every row and skipping, so that the
+// warps of a launch read neighbouring rows at the same time, as in a full pass.
 struct RowMask {
     const uint8_t *cp_active;
     const short2 *win;
     int32_t bpc;
     int32_t n_cols;
+    const int32_t *woff;
+    int32_t nseg;
 };
 inline RowMask all_rows() { return RowMask{nullptr, nullptr, 1, 1}; }
 __device__ __forceinline__ bool row_needed(const RowMask &m, int64_t r) {
@@ -159,6 +165,23 @@ __device__ __forceinline__ bool row_needed(const RowMask &m, int64_t r) {
     }
     return true;
 }
+
+// Row of list entry i of a windowed pass (mask.woff set): the segment q with woff[q] <= i <
+// woff[q + 1] (binary search; empty segments are never found), then column win[q].x +
+// (i - woff[q]) of that segment.
+__device__ __forceinline__ int64_t window_row(const RowMask &m, int64_t i) {
+    int lo = 0, hi = m.nseg; // woff[lo] <= i < woff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m.woff + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return (int64_t)lo * m.n_cols + __ldg(m.win + lo).x + (i - __ldg(m.woff + lo));
+}
+
+// Exclusive scan of the windows' lengths (win[q].y - win[q].x) into woff (nseg + 1
+// entries, one block); skip as for the pricing kernels.
+vmat_status window_offsets(const short2 *win, int32_t nseg, int32_t *woff, const int32_t *skip, cudaStream_t s);
 
 // SpMV on one CSR; x/y device.  mask: the rows to compute (all_rows(): every row).
 // skip (may be null): a device flag; when set at run time the kernels do nothing.

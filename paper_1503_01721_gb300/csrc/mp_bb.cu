@@ -761,28 +761,43 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
         if (tid == 0) pb[(size_t)n * a.pstride + cta] = fb;
         if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
             return LOOP_ABORT;
-        // ---- every CTA reduces every column itself (warp w: columns w, w + MP_NW, ...), lane l
-        // summing CTAs l, l + 32, ... in order and then a fixed butterfly: the same G and F in
-        // every CTA, with no second barrier
-        for (int k = wid; k <= n; k += MP_NW) {
-            const float2 *col = reinterpret_cast<const float2 *>(pb + (size_t)k * a.pstride);
-            FF v{0.f, 0.f};
-            for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) { // eight loads in flight per lane
-                float2 q[8];
+        // ---- every CTA reduces every column itself: warp w takes columns w, w + MP_NW, ...,
+        // four at a time with eight loads per column in flight per lane (every load of the
+        // group issued before the first add); lane l sums CTAs l, l + 32, ... in order, then
+        // a fixed butterfly: the same G and F in every CTA, with no second barrier
+        for (int k0 = wid; k0 <= n; k0 += MP_NW * 4) {
+            FF v[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const unsigned b = b0 + 32u * u;
-                    q[u] = b < n_cta ? __ldcg(col + b) : make_float2(0.f, 0.f);
+            for (int j = 0; j < 4; ++j) v[j] = FF{0.f, 0.f};
+            for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) {
+                float2 q[4][8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + MP_NW * j;
+                    const float2 *col = reinterpret_cast<const float2 *>(pb + (size_t)min(k, n) * a.pstride);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const unsigned b = b0 + 32u * u;
+                        q[j][u] = k <= n && b < n_cta ? __ldcg(col + b) : make_float2(0.f, 0.f);
+                    }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v = ff_add(v, FF{q[u].x, q[u].y});
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[j] = ff_add(v[j], FF{q[j][u].x, q[j][u].y});
             }
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_xor(v, d));
+            for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = ff_add(v[j], ff_shfl_xor(v[j], d));
             if (lane == 0) {
-                const double sum = ff_to_double(v);
-                if (k < n) S.sG[k] = -sum;
-                else ps.F = sum + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + MP_NW * j;
+                    const double sum = ff_to_double(v[j]);
+                    if (k < n) S.sG[k] = -sum;
+                    else if (k == n) ps.F = sum + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
+                }
             }
         }
         __syncthreads();

@@ -315,9 +315,10 @@ __global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const Pri
 // (P_R - P_L) in float64 (S_0 = P_R - P_L), where pred is the compatible state of
 // row r - 1 (L <= R' and L' <= R) with the largest S_{r-1}, ties by the row key
 // (width asc, |L + R - n_cols| asc, L asc).  The dominance maximum over
-// {L <= a, R >= b} is formed by a suffix pass over R (a thread per L) and a prefix
-// pass over L (a thread per b).  One block per CP; every compare is an integer
-// compare of order keys, every value the float64 of the sequential definition.
+// {L <= a, R >= b} is formed by a suffix pass over R and a prefix pass over L, both
+// restricted to the window rectangle of the previous row (the only states with a
+// chain).  One block per CP; every compare is an integer compare of order keys,
+// every value the float64 of the sequential definition.
 // ---------------------------------------------------------------------------
 constexpr int ID_THREADS = 512;
 
@@ -332,8 +333,8 @@ __device__ __forceinline__ bool key_better(uint64_t ka, uint32_t sa, uint64_t kb
 }
 
 __host__ __device__ constexpr size_t interdig_smem(int N) {
-    // S_{r-1}, S_r (double), CM (int32), tie keys (uint32), (L, R) of each state (uint16)
-    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4 + 4 + 2) + 64;
+    // S_{r-1}, S_r (double), CM (int32), tie keys (uint32)
+    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4 + 4) + 64;
 }
 
 // Window prefix sums of every MLC row of every unoccupied CP (a thread per row,
@@ -418,21 +419,27 @@ __global__ void __launch_bounds__(WIN_WARPS * 32)
     cp_windows_warp(P.g, P.occupied, P.leaves, k, P.win, P.rowptr, nullptr, P.counts ? P.counts + 3 * (int64_t)t : nullptr);
 }
 
-// Inclusive "best so far" scans of n_lines lines of n = N + 1 states each, four
-// threads per line: each scans a segment of about n/4 consecutive states in scan
-// order, the segments' bests pass along the line by two shuffles, and each thread
-// rescans its segment from that carry, writing the best state so far to CM.
-// SUFFIX: line L is (L, R) for R = N .. 0 (state index = position); otherwise line
-// b is CM[a][b] for a = 0 .. N (the state index stored there), rewritten in place.
+// Inclusive "best so far" scans over the previous row's feasible rectangle
+// [pL0, pL1] x [pR0, pR1] of states (L, R), four threads per line: each scans a
+// segment of about a quarter of the line in scan order, the segments' bests pass
+// along the line by two shuffles, and each thread rescans its segment from that
+// carry, writing the best state so far to CM.  SUFFIX: line L is (L, R) for R = pR1
+// down to pR0, C[L][R] written at CM[L (N + 1) + R]; otherwise line b is CM[a (N + 1)
+// + b] for a = pL0 .. pL1 (the state index stored there), rewritten in place with
+// M[a][b], the best state with L <= a and R >= b.
 template <bool SUFFIX>
-__device__ __forceinline__ void seg_best_scans(const double *Sp, const uint32_t *sec, int32_t *CM, int N) {
-    const int n = N + 1, seglen = (n + 3) >> 2, lane = threadIdx.x & 31;
-    for (int base = 0; base < n * 4; base += ID_THREADS) { // warp-uniform trip count
+__device__ __forceinline__ void rect_best_scans(const double *Sp, const uint32_t *sec, int32_t *CM, int N, int pL0,
+                                                int pL1, int pR0, int pR1) {
+    const int n = N + 1, lane = threadIdx.x & 31;
+    const int n_lines = SUFFIX ? pL1 - pL0 + 1 : pR1 - pR0 + 1;
+    const int len = SUFFIX ? pR1 - pR0 + 1 : pL1 - pL0 + 1;
+    const int seglen = (len + 3) >> 2;
+    for (int base = 0; base < n_lines * 4; base += ID_THREADS) { // warp-uniform trip count
         const int t = base + (int)threadIdx.x;
-        const bool act = t < n * 4;
+        const bool act = t < n_lines * 4;
         const int line = t >> 2, sg = t & 3;
-        const int e0 = sg * seglen, e1 = act ? min(e0 + seglen, n) : e0;
-        auto pos_of = [&](int e) { return SUFFIX ? line * n + (N - e) : e * n + line; };
+        const int e0 = min(sg * seglen, len), e1 = act ? min(e0 + seglen, len) : e0;
+        auto pos_of = [&](int e) { return SUFFIX ? (pL0 + line) * n + (pR1 - e) : (pL0 + e) * n + (pR0 + line); };
         int bi = -1;
         uint64_t bk = 0;
         uint32_t bs = 0xffffffffu;
@@ -488,7 +495,6 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
     double *Sn = Sp + NS;
     int32_t *CM = reinterpret_cast<int32_t *>(Sn + NS);
     uint32_t *sec = reinterpret_cast<uint32_t *>(CM + NS);
-    uint16_t *lr = reinterpret_cast<uint16_t *>(sec + NS);
     __shared__ int kk_s[2];
     __shared__ uint64_t wk[ID_THREADS / 32];
     __shared__ uint32_t wsec[ID_THREADS / 32];
@@ -496,7 +502,6 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
     for (int idx = tid; idx < NS; idx += ID_THREADS) {
         const int L = idx / (N + 1), R = idx - L * (N + 1);
         sec[idx] = state_sec(L, R, N);
-        lr[idx] = (uint16_t)((L << 8) | R);
     }
     if (wid == 0) {
         const int left = nearest_occupied(g, occupied, k, -1, lane);
@@ -507,28 +512,34 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
         }
     }
     __syncthreads();
+    // Only the states inside a row's leaf-travel window can be in a chain: the scans run
+    // over the previous row's window rectangle and the update over the current one.
+    // Every cell of a rectangle is written (-inf where L > R), and no cell outside the
+    // current and previous rectangles is read.
+    int pL0 = 0, pL1 = -1, pR0 = 0, pR1 = -1; // the previous row's rectangle (none yet)
     for (int r = 0; r < g.n_rows; ++r) {
         const RowWindow w = row_window(g, leaves, k, r, kk_s[0], kk_s[1]);
-        const int Lmin = w.Lmin, Lmax = w.Lmax, Rmin = w.Rmin, Rmax = w.Rmax;
+        const int L0 = w.Lmin, L1 = w.Lmax, R0 = w.Rmin, R1 = w.Rmax;
         const double *P = Pall + ((int64_t)k * g.n_rows + r) * (N + 1);
-        if (r > 0) {
+        const bool prev = pL0 <= pL1 && pR0 <= pR1;
+        if (r > 0 && prev) {
             // C[L][b] = best state (L, R), R >= b (suffix over R), then in place
             // M[a][b] = best of C[L][b], L <= a (prefix over L)
-            seg_best_scans<true>(Sp, sec, CM, N);
+            rect_best_scans<true>(Sp, sec, CM, N, pL0, pL1, pR0, pR1);
             __syncthreads();
-            seg_best_scans<false>(Sp, sec, CM, N);
+            rect_best_scans<false>(Sp, sec, CM, N, pL0, pL1, pR0, pR1);
         }
         __syncthreads();
-        for (int idx = tid; idx < NS; idx += ID_THREADS) {
-            const int L = lr[idx] >> 8, R = lr[idx] & 255;
-            const bool feas = L <= R && L >= Lmin && L <= Lmax && R >= Rmin && R <= Rmax;
+        const int wR = R1 - R0 + 1, cells = (L1 >= L0 && R1 >= R0) ? (L1 - L0 + 1) * wR : 0;
+        for (int t = tid; t < cells; t += ID_THREADS) {
+            const int L = L0 + t / wR, R = R0 + t % wR, idx = L * (N + 1) + R;
             double sv = -INFINITY;
-            if (feas) {
+            if (L <= R) {
                 const double v = P[R] - P[L];
                 if (r == 0) {
                     sv = v;
-                } else {
-                    const int pred = CM[R * (N + 1) + L]; // M[R'][L']
+                } else if (prev && R >= pL0 && L <= pR1) {
+                    const int pred = CM[min(R, pL1) * (N + 1) + max(L, pR0)]; // M[R'][L'] clamped to the rectangle
                     const double ps = Sp[pred];
                     if (ps > -INFINITY) sv = ps + v;
                     pred_tab[(int64_t)r * NS + idx] = (int16_t)pred;
@@ -540,12 +551,18 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
         double *t = Sp;
         Sp = Sn;
         Sn = t;
+        pL0 = L0;
+        pL1 = cells ? L1 : -1;
+        pR0 = R0;
+        pR1 = R1;
     }
     // best final state
     int bi = -1;
     uint64_t bk = 0;
     uint32_t bs = 0xffffffffu;
-    for (int idx = tid; idx < NS; idx += ID_THREADS) {
+    const int fwR = pR1 - pR0 + 1, fcells = (pL1 >= pL0 && pR1 >= pR0) ? (pL1 - pL0 + 1) * fwR : 0;
+    for (int t = tid; t < fcells; t += ID_THREADS) {
+        const int idx = (pL0 + t / fwR) * (N + 1) + pR0 + t % fwR;
         const double sv = Sp[idx];
         if (!(sv > -INFINITY)) continue;
         const uint64_t kv = order_key(sv);
@@ -653,6 +670,57 @@ vmat_status price_windows(const PricingGeom &g, const uint8_t *occupied, const i
     if (g.K < 1) return VMAT_OK;
     price_windows_kernel<<<(g.K + WIN_WARPS - 1) / WIN_WARPS, WIN_WARPS * 32, 0, s>>>(g, occupied, leaves, win, rowptr,
                                                                                    cptr, counts, skip);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+// Exclusive scan of the window lengths (one block of WO_THREADS): each thread sums a
+// contiguous run of segments, a block scan of the run totals (warp scans, then the warp
+// totals), then each thread writes its run's offsets.
+constexpr int WO_THREADS = 1024;
+__global__ void __launch_bounds__(WO_THREADS)
+    window_offsets_kernel(const short2 *__restrict__ win, int32_t nseg, int32_t *__restrict__ woff,
+                          const int32_t *skip) {
+    if (skip && *skip) return;
+    __shared__ int32_t wsum[WO_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (nseg + WO_THREADS - 1) / WO_THREADS;
+    const int q0 = min(tid * per, nseg), q1 = min(q0 + per, nseg);
+    int32_t run = 0;
+    for (int q = q0; q < q1; ++q) {
+        const short2 w = win[q];
+        run += max(0, (int)w.y - (int)w.x);
+    }
+    int32_t incl = run; // inclusive scan of the run totals within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t v = wsum[lane], x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t o = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += o;
+        }
+        wsum[lane] = x - v; // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    int32_t off = wsum[wid] + incl - run;
+    for (int q = q0; q < q1; ++q) {
+        woff[q] = off;
+        const short2 w = win[q];
+        off += max(0, (int)w.y - (int)w.x);
+    }
+    if (tid == WO_THREADS - 1) woff[nseg] = off;
+}
+
+vmat_status window_offsets(const short2 *win, int32_t nseg, int32_t *woff, const int32_t *skip, cudaStream_t s) {
+    if (nseg < 1) return VMAT_OK;
+    window_offsets_kernel<<<1, WO_THREADS, 0, s>>>(win, nseg, woff, skip);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

@@ -521,8 +521,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_z_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
-        if (!row_needed(p.mask, r)) continue;
+    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
+    for (int64_t i = warp0; i < n_items; i += p.stride) {
+        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
+        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
         float sum = warp_row_sum_z<UNROLL, VT>(p.rowptr, p.cptr, p.cbase, p.col16, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -538,8 +540,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_c_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
-        if (!row_needed(p.mask, r)) continue;
+    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
+    for (int64_t i = warp0; i < n_items; i += p.stride) {
+        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
+        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
         float sum = warp_row_sum_c<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -555,8 +559,10 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    for (int64_t r = warp0; r < p.n_rows; r += p.stride) {
-        if (!row_needed(p.mask, r)) continue;
+    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
+    for (int64_t i = warp0; i < n_items; i += p.stride) {
+        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
+        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
         float sum = warp_row_sum<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
@@ -863,7 +869,7 @@ vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, co
         const int64_t want = (warps * 32 + L.threads - 1) / L.threads;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * L.blocks_per_sm));
         const int64_t n_warps = (int64_t)grid * L.threads / 32;
-        p.stride = mask.win ? coprime_stride(n_warps, &mask.n_cols, 1) : n_warps;
+        p.stride = mask.win && !mask.woff ? coprime_stride(n_warps, &mask.n_cols, 1) : n_warps;
         L.row<<<grid, L.threads, 0, s>>>(p);
         VMAT_LAUNCH_CHECK();
         return VMAT_OK;
@@ -1051,12 +1057,15 @@ vmat_status beamlet_price_windowed(vmat_ddc hd, const vmat_mlc *mlc, const uint8
     PricingGeom pg;
     VMAT_TRY(pricing_geom(mlc, &pg));
     cudaStream_t s = as_stream(stream);
+    const int32_t nseg = mlc->K * mlc->n_rows;
     Scratch ws;
-    VMAT_TRY(ws.alloc((size_t)mlc->K * mlc->n_rows * sizeof(short2), s));
+    VMAT_TRY(ws.alloc((size_t)nseg * sizeof(short2) + (size_t)(nseg + 1) * sizeof(int32_t), s));
     short2 *win = static_cast<short2 *>(ws.ptr);
+    int32_t *woff = reinterpret_cast<int32_t *>(win + nseg);
     VMAT_TRY(price_windows(pg, occupied, leaves, win, h->Dt.rowptr, nullptr, nullptr, nullptr, s));
+    VMAT_TRY(window_offsets(win, nseg, woff, nullptr, s));
     return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
-                    RowMask{nullptr, win, mlc->n_rows * mlc->n_cols, mlc->n_cols}, s);
+                    RowMask{nullptr, win, mlc->n_rows * mlc->n_cols, mlc->n_cols, woff, nseg}, s);
 }
 
 } // extern "C"
