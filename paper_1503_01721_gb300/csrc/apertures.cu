@@ -84,6 +84,113 @@ __global__ void build_cp_table(const int64_t *__restrict__ rowptr, const int32_t
     }
 }
 
+// Entries of CP k in the 32 rows of group g (a warp per (k, g); lane = row).
+__global__ void cpm_group_sizes(const uint16_t *__restrict__ tab, int32_t n_rows, int32_t K, int32_t n_grp,
+                                int32_t *__restrict__ gsum) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)K * n_grp) return; // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int32_t k = (int32_t)(w / n_grp), g = (int32_t)(w - (int64_t)k * n_grp), row = g * 32 + lane;
+    int32_t len = row < n_rows ? (int32_t)tab[(int64_t)(k + 1) * n_rows + row] - (int32_t)tab[(int64_t)k * n_rows + row]
+                               : 0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) len += __shfl_xor_sync(0xffffffffu, len, d);
+    if (lane == 0) gsum[w] = len;
+}
+
+// Copies CP k's run of each row of group g to the group's place in the CP-major block
+// (a warp per (k, g)): the runs of the 32 rows follow each other there; lane l writes
+// destination entries l, l + 32, ... (coalesced) and finds each one's row among the
+// 32 inclusive run-length prefixes by a 5-step search over the lanes' values.
+template <typename VT>
+__global__ void cpm_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                         const VT *__restrict__ val, const uint16_t *__restrict__ tab, int32_t n_rows, int32_t K,
+                         int32_t bpc, int32_t n_grp, const int64_t *__restrict__ base, uint16_t *__restrict__ loc,
+                         VT *__restrict__ cval) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)K * n_grp) return; // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int32_t k = (int32_t)(w / n_grp), g = (int32_t)(w - (int64_t)k * n_grp), row = g * 32 + lane;
+    int32_t len = 0;
+    int64_t src = 0; // where this lane's run starts in CSR(D)
+    if (row < n_rows) {
+        const int32_t a = tab[(int64_t)k * n_rows + row];
+        len = (int32_t)tab[(int64_t)(k + 1) * n_rows + row] - a;
+        src = rowptr[row] + a;
+    }
+    int32_t incl = len; // inclusive scan of the run lengths over the lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const int64_t dst0 = base[w];
+    for (int32_t e0 = 0; e0 < total; e0 += 32) { // warp-uniform trip count
+        const int32_t e = e0 + lane;
+        int r = 0; // the first lane whose inclusive prefix exceeds e
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int32_t v = __shfl_sync(0xffffffffu, incl, r + st - 1);
+            if (v <= e) r += st;
+        }
+        const int32_t start = __shfl_sync(0xffffffffu, incl - len, r);
+        const int64_t s0 = __shfl_sync(0xffffffffu, src, r);
+        if (e < total) {
+            const int64_t i = s0 + (e - start);
+            loc[dst0 + e] = (uint16_t)(col[i] - k * bpc);
+            cval[dst0 + e] = val[i];
+        }
+    }
+}
+
+// Builds the CP-major copy (VMAT_OK without one when memory is short).
+static vmat_status ddc_cpm_build(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s) {
+    if (bpc > 65536) return VMAT_OK; // a beamlet's index within its CP must fit 16 bits
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int32_t n = h.D.n_rows, n_grp = (n + 31) / 32;
+    const int64_t n_w = (int64_t)K * n_grp;
+    const int vb = value_bytes(h.dtype);
+    uint16_t *loc = nullptr;
+    void *cval = nullptr;
+    int64_t *base = nullptr;
+    int32_t *gsum = nullptr;
+    auto fail = [&]() {
+        cudaGetLastError();
+        cudaFree(loc);
+        cudaFree(cval);
+        cudaFree(base);
+        cudaFree(gsum);
+        return VMAT_OK; // no room: the aperture dose reads CSR(D) itself
+    };
+    if (cudaMalloc(&loc, (size_t)std::max<int64_t>(h.D.nnz, 1) * 2) != cudaSuccess) return fail();
+    if (cudaMalloc(&cval, (size_t)std::max<int64_t>(h.D.nnz, 1) * vb) != cudaSuccess) return fail();
+    if (cudaMalloc(&base, (size_t)(n_w + 1) * 8) != cudaSuccess) return fail();
+    if (cudaMalloc(&gsum, (size_t)std::max<int64_t>(n_w, 1) * 4) != cudaSuccess) return fail();
+    const unsigned blocks = (unsigned)((n_w * 32 + 255) / 256);
+    cpm_group_sizes<<<blocks, 256, 0, s>>>(h.cp_tab, n, K, n_grp, gsum);
+    VMAT_LAUNCH_CHECK();
+    VMAT_TRY(scan_counts(gsum, base, n_w, s));
+    if (h.dtype == VMAT_F32)
+        cpm_fill<float><<<blocks, 256, 0, s>>>(h.D.rowptr, h.D.col, static_cast<const float *>(h.D.val), h.cp_tab, n,
+                                               K, bpc, n_grp, base, loc, static_cast<float *>(cval));
+    else if (h.dtype == VMAT_BF16)
+        cpm_fill<uint16_t><<<blocks, 256, 0, s>>>(h.D.rowptr, h.D.col, static_cast<const uint16_t *>(h.D.val),
+                                                  h.cp_tab, n, K, bpc, n_grp, base, loc,
+                                                  static_cast<uint16_t *>(cval));
+    else
+        cpm_fill<uint8_t><<<blocks, 256, 0, s>>>(h.D.rowptr, h.D.col, static_cast<const uint8_t *>(h.D.val), h.cp_tab,
+                                                 n, K, bpc, n_grp, base, loc, static_cast<uint8_t *>(cval));
+    VMAT_LAUNCH_CHECK();
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    cudaFree(gsum);
+    h.cpm_loc = loc;
+    h.cpm_val = cval;
+    h.cpm_base = base;
+    return VMAT_OK;
+}
+
 vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s) {
     if (!h.built_D || h.D.n_rows == 0) return VMAT_OK;
     if (h.cp_tab && h.cp_tab_K == K && h.cp_tab_bpc == bpc) return VMAT_OK;
@@ -92,6 +199,12 @@ vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s) {
         cudaFree(h.cp_tab);
         h.cp_tab = nullptr;
         h.cp_tab_K = h.cp_tab_bpc = 0;
+        cudaFree(h.cpm_loc);
+        cudaFree(h.cpm_val);
+        cudaFree(h.cpm_base);
+        h.cpm_loc = nullptr;
+        h.cpm_val = nullptr;
+        h.cpm_base = nullptr;
     }
     if (h.D.max_row > 65535) return VMAT_OK; // offsets would not fit 16 bits: search instead
     DeviceCtx *ctx;
@@ -108,7 +221,7 @@ vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s) {
     h.cp_tab = tab;
     h.cp_tab_K = K;
     h.cp_tab_bpc = bpc;
-    return VMAT_OK;
+    return ddc_cpm_build(h, K, bpc, s);
 }
 
 template <typename VT>
@@ -135,6 +248,54 @@ __global__ void aperture_dose_kernel(const int64_t *__restrict__ rowptr, const i
     }
 }
 
+// The same sums from the CP-major copy: a warp per group of 32 rows, lane = row; the
+// group's runs of CP cp are one contiguous block (cpm_base), each lane reads its own run
+// (the warp's entries share a few cache lines).  Entries in beamlet order, as above: the
+// same bits as aperture_dose_kernel.
+template <typename VT>
+__global__ void aperture_dose_cpm_kernel(const uint16_t *__restrict__ loc, const void *__restrict__ val,
+                                         const int64_t *__restrict__ base, const float *__restrict__ scale,
+                                         const uint16_t *__restrict__ tab, int32_t n_rows, int32_t n_grp,
+                                         const int32_t *__restrict__ row_ids, int32_t cp_arg, const int32_t *cp_dev,
+                                         const int32_t *skip, int32_t n_rrows, int32_t n_cols,
+                                         const int16_t *__restrict__ leaves, float *__restrict__ da, int64_t wstride) {
+    if (skip && *skip) return;
+    const int32_t cp = cp_dev ? *cp_dev : cp_arg;
+    extern __shared__ int16_t sl[]; // [n_rrows][2]
+    for (int i = threadIdx.x; i < 2 * n_rrows; i += blockDim.x) sl[i] = leaves[i];
+    __syncthreads();
+    const int32_t bpc = n_rrows * n_cols;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_grp; g += n_warps) {
+        const int32_t row = (int32_t)g * 32 + lane;
+        int32_t len = 0;
+        if (row < n_rows) len = (int32_t)tab[(int64_t)(cp + 1) * n_rows + row] - (int32_t)tab[(int64_t)cp * n_rows + row];
+        int32_t incl = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int64_t start = base[(int64_t)cp * n_grp + g] + (incl - len);
+        float acc = 0.f;
+        for (int32_t e = 0; e < len; ++e) {
+            const int32_t lc = loc[start + e];
+            const int32_t r = lc / n_cols, c = lc - r * n_cols;
+            if (c >= sl[2 * r] && c < sl[2 * r + 1]) {
+                float v = StoredVal<VT>::get(val, start + e);
+                if (scale) v *= scale[(int64_t)cp * bpc + lc];
+                acc += v;
+            }
+        }
+        if (row < n_rows) {
+            const int64_t o =
+                row_ids ? row_ids[row] : (wstride ? (int64_t)(row >> 5) * wstride + ((row & 31) << 2) : row);
+            da[o] = acc;
+        }
+    }
+}
+
 using DaFn = void (*)(const int64_t *, const int32_t *, const void *, const float *, const uint16_t *, int32_t,
                       const int32_t *, int32_t, const int32_t *, const int32_t *, int32_t, int32_t, const int16_t *,
                       float *, int64_t);
@@ -152,8 +313,28 @@ static vmat_status launch_da(const Ddc &h, const vmat_mlc *mlc, int32_t cp, cons
     if (n == 0) return VMAT_OK;
     const int32_t bpc = mlc->n_rows * mlc->n_cols;
     const uint16_t *tab = h.cp_tab && h.cp_tab_K == mlc->K && h.cp_tab_bpc == bpc ? h.cp_tab : nullptr;
+    const size_t sl_bytes = (size_t)mlc->n_rows * 2 * sizeof(int16_t);
+    if (tab && h.cpm_val) { // the CP-major copy, built with this table
+        const int32_t n_grp = (n + 31) / 32;
+        const int g = std::max(1, std::min(ctx->n_sm * 16, (n_grp * 32 + 255) / 256));
+        const float *sc = h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr;
+        if (h.dtype == VMAT_F32)
+            aperture_dose_cpm_kernel<float><<<g, 256, sl_bytes, s>>>(h.cpm_loc, h.cpm_val, h.cpm_base, sc, tab, n,
+                                                                     n_grp, row_ids, cp, cp_dev, skip, mlc->n_rows,
+                                                                     mlc->n_cols, leaves, da, wstride);
+        else if (h.dtype == VMAT_BF16)
+            aperture_dose_cpm_kernel<__nv_bfloat16><<<g, 256, sl_bytes, s>>>(
+                h.cpm_loc, h.cpm_val, h.cpm_base, sc, tab, n, n_grp, row_ids, cp, cp_dev, skip, mlc->n_rows,
+                mlc->n_cols, leaves, da, wstride);
+        else
+            aperture_dose_cpm_kernel<__nv_fp8_e4m3><<<g, 256, sl_bytes, s>>>(
+                h.cpm_loc, h.cpm_val, h.cpm_base, sc, tab, n, n_grp, row_ids, cp, cp_dev, skip, mlc->n_rows,
+                mlc->n_cols, leaves, da, wstride);
+        VMAT_LAUNCH_CHECK();
+        return VMAT_OK;
+    }
     const int grid = std::max(1, std::min(ctx->n_sm * 8, (n + 255) / 256));
-    da_kernel_for(h.dtype)<<<grid, 256, (size_t)mlc->n_rows * 2 * sizeof(int16_t), s>>>(
+    da_kernel_for(h.dtype)<<<grid, 256, sl_bytes, s>>>(
         h.D.rowptr, h.D.col, h.D.val, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, tab, n, row_ids, cp, cp_dev, skip,
         mlc->n_rows, mlc->n_cols, leaves, da, wstride);
     VMAT_LAUNCH_CHECK();

@@ -185,6 +185,11 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&F_off, 1));
     VMAT_TRY(ar.get(&live.bcnt, (size_t)mp_live_blocks(n_wtiles)));
     VMAT_TRY(ar.get(&live.bpart, (size_t)mp_live_blocks(n_wtiles)));
+    // the live tiles packed (heads and the four-aperture groups that hold a nonzero)
+    VMAT_TRY(ar.get(&live.gmask, (size_t)n_wtiles));
+    VMAT_TRY(ar.get(&live.packed, (size_t)n_wtiles * wstride));
+    VMAT_TRY(ar.get(&live.poff, (size_t)n_wtiles + 1));
+    VMAT_TRY(ar.get(&live.bsize, (size_t)mp_live_blocks(n_wtiles)));
     live.DA = DA;
     live.wstride = wstride;
     live.n_wtiles = n_wtiles;
@@ -221,6 +226,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         VMAT_TRY(mp_tile_consts(sid_c, NA, vox, n_wtiles, c_tile, s));
     }
     VMAT_CUDA(cudaMemsetAsync(live_flag, 0, (size_t)n_wtiles, s));
+    VMAT_CUDA(cudaMemsetAsync(live.gmask, 0, (size_t)n_wtiles * sizeof(uint32_t), s));
     VMAT_TRY(inactive_objective(h, vox, F0, s));
     VMAT_TRY(ddc_cp_table(h, K, bpc, s)); // CP offsets of CSR(D) rows for the aperture dose
     double F_offset = 0.0;
@@ -302,7 +308,10 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         tm.mark(PH_DA);
         VMAT_TRY(aperture_dose_dev(h, mlc, cps_dev + t, best_leaves, DA + 32 + (size_t)(t >> 2) * 128 + (t & 3),
                                    wstride, ctl, s));
-        if (NA > 0) VMAT_TRY(mp_live_update(live, t, s));
+        if (NA > 0) {
+            VMAT_TRY(mp_live_update(live, t, s));
+            VMAT_TRY(mp_pack(live, t + 1, s));
+        }
         // ---- MP (Eq. 6-10)
         tm.mark(PH_MP);
         if (lo) VMAT_TRY(fluence_bounds_enqueue(bg, t + 1, cps_dev, leaves_seq, lo, hi, ctl, s));
@@ -334,6 +343,9 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         hf.dtype = VMAT_F32;
         hf.D.val = h.D_val_f32;
         hf.scale = nullptr;
+        hf.cpm_loc = nullptr; // the CP-major copy holds the stored values
+        hf.cpm_val = nullptr;
+        hf.cpm_base = nullptr;
     }
     int refine_extra = 0;
     int32_t *refine_iters = nullptr;
@@ -356,6 +368,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         }
         if (n_placed > 0) {
             VMAT_TRY(mp_live_rebuild(live_r, s));
+            VMAT_TRY(mp_pack(live_r, n_placed, s));
             if (n_placed <= n_cap) {
                 VMAT_TRY(mp_bb_enqueue(DA, NA, n_placed, n_cap, wstride, sid_c, &vox_c, lo, hi, y, z_c, opts, 0.0,
                                        mp_ws, nullptr, refine_iters, s, &live_r));

@@ -88,6 +88,12 @@ void Ddc::free_all() {
     f(xs);
     f(cp_tab);
     cp_tab = nullptr;
+    f(cpm_loc);
+    f(cpm_val);
+    f(cpm_base);
+    cpm_loc = nullptr;
+    cpm_val = nullptr;
+    cpm_base = nullptr;
     cp_tab_K = cp_tab_bpc = 0;
     act_vox = vox2act = nullptr;
     scale = xs = nullptr;

@@ -120,6 +120,14 @@ struct Ddc {
     // aperture dose; built on demand for one MLC shape (cp_tab_bpc beamlets per CP).
     uint16_t *cp_tab = nullptr;
     int32_t cp_tab_K = 0, cp_tab_bpc = 0;
+    // CP-major copy of CSR(D) for the aperture dose, built with the CP table: block k holds
+    // every compact row's run of CP k's entries, rows in order, each entry as its beamlet's
+    // index within the CP (uint16) and its stored value; cpm_base[k * n_grp + g] is the
+    // entry where the runs of rows 32 g .. 32 g + 31 start (n_grp = ceil(rows / 32)).  One
+    // aperture's dose then reads one contiguous block.  Null when it does not fit in memory.
+    uint16_t *cpm_loc = nullptr;
+    void *cpm_val = nullptr;
+    int64_t *cpm_base = nullptr;
     double build_ms = 0.0;
     void free_all();
 };
@@ -382,6 +390,16 @@ struct MpLive {
     const int32_t *skip;  // as for the solver
     int32_t *bcnt;        // [mp_live_blocks(n_wtiles)] scratch: live tiles per block of 1024
     double *bpart;        // [mp_live_blocks(n_wtiles)] scratch: constants of the others per block
+    // Packed tiles (all null: the solver reads DA's tiles whole).  gmask[q] bit g: group g
+    // (apertures 4g .. 4g + 3) has a nonzero in tile q (sticky).  packed holds every live tile
+    // as its 128-byte head (the labels, the group mask at byte 32) followed by its marked
+    // groups only (512 bytes each, ascending), live tile i at 128-byte unit poff[i], in list
+    // order; poff[n_live] is the total.  Groups left out hold only zeros, whose products
+    // add nothing, so the solver's sums are the same bits either way.
+    uint32_t *gmask;      // [n_wtiles]
+    float *packed;        // [n_wtiles * wstride]
+    int32_t *poff;        // [n_wtiles + 1]
+    int32_t *bsize;       // [mp_live_blocks(n_wtiles)] scratch: packed units per block
 };
 constexpr int MP_LIVE_BLOCK = 1024; // tiles per block of the list kernels
 __host__ __device__ inline int64_t mp_live_blocks(int64_t n_wtiles) {
@@ -392,6 +410,9 @@ vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *
 // After column t of DA is written: mark the tiles it reaches, rebuild the list and F_off
 // (per-block counts, then ordered writes: the list and the sums are reproducible).
 vmat_status mp_live_update(const MpLive &L, int32_t t, cudaStream_t s);
+// Copies the live tiles' heads and marked groups into L.packed (L.packed non-null; after
+// the list is rebuilt).  The apertures are the first n columns.
+vmat_status mp_pack(const MpLive &L, int32_t n, cudaStream_t s);
 // The two halves of mp_live_update: mark the tiles column t reaches; rebuild the list and F_off.
 vmat_status mp_live_mark(const MpLive &L, int32_t t, cudaStream_t s);
 vmat_status mp_live_rebuild(const MpLive &L, cudaStream_t s);

@@ -97,6 +97,10 @@ struct MPArgs {
     const int32_t *tiles;
     const int32_t *n_live;
     const double *F_off_dev;
+    // Packed live tiles (null: read DA's tiles whole): list entry i at 128-byte unit poff[i] of
+    // packed, its head (labels, group mask at byte 32) then its marked groups.
+    const float *packed;
+    const int32_t *poff;
 };
 
 __device__ __forceinline__ int64_t min64(int64_t x, int64_t y) { return x < y ? x : y; }
@@ -394,12 +398,22 @@ struct SolveSmem {
     float *sYp;            // [NMAX]   y_{t-1}
     float *wred;           // [MP_NW][NMAX]
     float *sT, *sO, *sU;   // [256]
-    uint64_t *bars;        // [MP_NW][stages]
+    uint64_t *bars;        // [MP_NW][PQ]
+    uint32_t *ring_meta;   // [MP_NW][PQ][2] packed tiles: ring offset, bytes held
+    int32_t *wlist;        // [MP_NW][WL_CAP][3] the warp's first tiles: tile, packed unit offset, units
 };
+
+// Copies in flight per warp at most (mbarriers per warp): the tile stages of whole tiles, or
+// the packed tiles that fit in the warp's byte ring.
+constexpr int PQ = 8;
+// Tiles of a warp whose index and packed place are kept in shared memory (loaded once per
+// solve, so that issuing a copy and placing a tile's voxels wait on no global load); a
+// warp's tiles past the first WL_CAP are looked up in global memory.
+constexpr int WL_CAP = 64;
 
 template <int NMAX> __host__ __device__ constexpr size_t solve_fixed_smem() {
     return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 4 * (size_t)NMAX * 8 + 8 * 8 + (size_t)NMAX * 4 +
-           (size_t)MP_NW * NMAX * 4 + 3 * 256 * 4;
+           (size_t)MP_NW * NMAX * 4 + 3 * 256 * 4 + (size_t)MP_NW * PQ * (8 + 8) + (size_t)MP_NW * WL_CAP * 12;
 }
 
 // Bulk copy of the warp's pipeline slot `it` (global tile-use index across passes).
@@ -413,15 +427,65 @@ struct WarpPipe {
     uint32_t cbytes;
     int stages;
     uint64_t pol;
+    // Packed tiles (poff non-null): each is copied whole into the warp's byte ring (stages *
+    // cbytes bytes, the tiles in issue order, a tile that would cross the end starting again
+    // at 0), up to PQ copies in flight, as many as the ring holds.  Lane 0 is the producer.
+    const unsigned char *packed; // packed live tiles
+    const int32_t *poff;         // list entry q at 128-byte unit poff[q] of packed
+    uint32_t *moff, *mspan;      // [PQ] per slot: ring offset of its tile, ring bytes it holds
+    int32_t *wl;                 // [WL_CAP][3] this warp's tile j: tile, packed unit offset, units
+    uint32_t ring_bytes;
+    int64_t iss;                 // lane 0: the next tile to issue
+    uint32_t pos, span;          // lane 0: ring write position, ring bytes held by tiles in flight
     __device__ __forceinline__ int64_t tile_of(int64_t q) const { return tiles ? (int64_t)__ldg(tiles + q) : q; }
+    // the warp's tile j (0 <= j < n_my): tile index, from the shared list when it holds it
+    __device__ __forceinline__ int64_t my_tile(int64_t j) const {
+        return j < WL_CAP ? (int64_t)wl[3 * j] : tile_of(w0 + j * W);
+    }
     __device__ __forceinline__ void issue(int64_t it) const {
         const int s = (int)(it % stages);
-        const int64_t wt = tile_of(w0 + ((it - it_base) % n_my) * W);
+        const int64_t wt = my_tile((it - it_base) % n_my);
         mbar_arrive_expect_tx(&mb[s], cbytes);
         bulk_g2s(my + (size_t)s * cbytes, src + wt * tile_bytes, cbytes, &mb[s], pol);
     }
     __device__ __forceinline__ bool wait(int64_t it) const {
         return mbar_wait_bounded(&mb[it % stages], (uint32_t)((it / stages) & 1), WAIT_LIMIT_CYCLES);
+    }
+    // packed: issue tiles iss, iss + 1, ... while fewer than PQ are in flight past tile `it`
+    // (the next to be consumed) and the ring has room (lane 0)
+    __device__ __forceinline__ void fill(int64_t it) {
+        if (span == 0) pos = 0; // an empty ring: any tile fits from its start
+        while (iss - it < PQ) {
+            const int64_t j = (iss - it_base) % n_my;
+            int64_t u0;
+            uint32_t units;
+            if (j < WL_CAP) {
+                u0 = wl[3 * j + 1];
+                units = (uint32_t)wl[3 * j + 2];
+            } else {
+                const int64_t q = w0 + j * W;
+                u0 = __ldg(poff + q);
+                units = (uint32_t)(__ldg(poff + q + 1) - u0);
+            }
+            const uint32_t bytes = units * 128u; // at most cbytes <= ring_bytes
+            uint32_t start = pos, gap = 0;
+            if (pos + bytes > ring_bytes) { // the ring's end: skip the rest, start at 0
+                gap = ring_bytes - pos;
+                start = 0;
+            }
+            if (span + gap + bytes > ring_bytes) break;
+            const int s = (int)(iss % PQ);
+            moff[s] = start;
+            mspan[s] = gap + bytes;
+            mbar_arrive_expect_tx(&mb[s], bytes);
+            bulk_g2s(my + start, packed + u0 * 128, bytes, &mb[s], pol);
+            pos = start + bytes;
+            span += gap + bytes;
+            ++iss;
+        }
+    }
+    __device__ __forceinline__ bool wait_packed(int64_t it) const {
+        return mbar_wait_bounded(&mb[it % PQ], (uint32_t)((it / PQ) & 1), WAIT_LIMIT_CYCLES);
     }
 };
 
@@ -431,30 +495,34 @@ enum { PASS_ITER = 0, PASS_CAUCHY = 1 };
 // shares; PASS_CAUCHY: q = DA G and the curvature terms w q^2.  Consumes
 // pipeline slots it .. it + n_my - 1 (advancing it) and issues slot + stages
 // after each.  Returns false (it at the slot) if a copy never landed.
-template <int NMAX, int MODE>
-__device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, const WarpPipe &P, int64_t &it,
+template <int NMAX, int MODE, bool PACKED>
+__device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, WarpPipe &P, int64_t &it,
                                            float *gacc, float &fs, float &fc) {
     constexpr int GMAX = NMAX / 4;
     const int G = (a.n + 3) >> 2;
     const int lane = threadIdx.x & 31;
     for (int64_t j = 0; j < P.n_my; ++j, ++it) {
-        const bool ok = P.wait(it);
+        const bool ok = PACKED ? P.wait_packed(it) : P.wait(it);
         if (!__all_sync(0xffffffffu, ok)) return false;
-        const unsigned char *blk = P.my + (size_t)(it % P.stages) * P.cbytes;
+        const unsigned char *blk =
+            PACKED ? P.my + P.moff[it % PQ] : P.my + (size_t)(it % P.stages) * P.cbytes;
         const float4 *D4 = reinterpret_cast<const float4 *>(blk + 128) + lane; // group g at D4[32 g]
         const float4 *w4 = MODE == PASS_ITER ? S.sy4 : S.sg4;
+        // packed: the marked groups only, in order (a group left out holds zeros, which add nothing)
+        const uint32_t gm = PACKED ? reinterpret_cast<const uint32_t *>(blk)[8] : 0u;
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+        int slot = 0;
 #pragma unroll
         for (int g = 0; g < GMAX; ++g)
-            if (g < G) {
-                const float4 v = D4[32 * g], w = w4[g];
+            if (g < G && (!PACKED || ((gm >> g) & 1u))) {
+                const float4 v = D4[32 * (PACKED ? slot++ : g)], w = w4[g];
                 z0 = fmaf(v.x, w.x, z0);
                 z1 = fmaf(v.y, w.y, z1);
                 z2 = fmaf(v.z, w.z, z2);
                 z3 = fmaf(v.w, w.w, z3);
             }
         const float zi = (z0 + z1) + (z2 + z3);
-        const int64_t i = P.tile_of(P.w0 + j * P.W) * MP_WT + lane;
+        const int64_t i = P.my_tile(j) * MP_WT + lane;
         float gi = 0.f;
         if (i < a.V) {
             const int sid = blk[lane];
@@ -478,10 +546,11 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
             }
         }
         if (MODE == PASS_ITER) {
+            slot = 0;
 #pragma unroll
             for (int g = 0; g < GMAX; ++g)
-                if (g < G) {
-                    const float4 v = D4[32 * g];
+                if (g < G && (!PACKED || ((gm >> g) & 1u))) {
+                    const float4 v = D4[32 * (PACKED ? slot++ : g)];
                     gacc[4 * g + 0] = fmaf(v.x, gi, gacc[4 * g + 0]);
                     gacc[4 * g + 1] = fmaf(v.y, gi, gacc[4 * g + 1]);
                     gacc[4 * g + 2] = fmaf(v.z, gi, gacc[4 * g + 2]);
@@ -489,7 +558,14 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
                 }
         }
         __syncwarp(); // every lane's reads of this slot are done before its next copy
-        if (lane == 0) P.issue(it + P.stages);
+        if (lane == 0) {
+            if (PACKED) {
+                P.span -= P.mspan[it % PQ];
+                P.fill(it + 1);
+            } else {
+                P.issue(it + P.stages);
+            }
+        }
     }
     return true;
 }
@@ -635,6 +711,8 @@ template <int NMAX> __device__ __forceinline__ SolveSmem solve_layout(unsigned c
     S.sO = S.sT + 256;
     S.sU = S.sO + 256;
     S.bars = reinterpret_cast<uint64_t *>(S.sU + 256);
+    S.ring_meta = reinterpret_cast<uint32_t *>(S.bars + MP_NW * PQ);
+    S.wlist = reinterpret_cast<int32_t *>(S.ring_meta + MP_NW * PQ * 2);
     return S;
 }
 
@@ -706,7 +784,9 @@ template <int NMAX> __device__ void solve_finish(const MPArgs &a, const SolveSme
         if (ok && a.iters_acc) *a.iters_acc += ps.t + 1;
         if (ok && a.bytes_acc) { // each pass reads the tiles' labels and columns and writes (or reads) their dose
             const int64_t tiles = a.tiles ? min64((int64_t)max(__ldcg(a.n_live), 0), a.n_wtiles) : a.n_wtiles;
-            *a.bytes_acc += (double)ps.passes * (double)tiles * (double)(wt_copy_bytes(a.n) + 4 * MP_WT);
+            const double per_tile_read = a.poff ? 0.0 : (double)wt_copy_bytes(a.n);
+            const double packed_read = a.poff ? 128.0 * (double)__ldcg(a.poff + tiles) : 0.0;
+            *a.bytes_acc += (double)ps.passes * ((double)tiles * (per_tile_read + 4.0 * MP_WT) + packed_read);
         }
     }
     __threadfence();
@@ -736,7 +816,8 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) gacc[k] = 0.f;
         float fs = 0.f, fc = 0.f;
-        const bool pass_ok = P.n_my == 0 || solve_pass<NMAX, PASS_ITER>(a, S, P, it, gacc, fs, fc);
+        const bool pass_ok = P.n_my == 0 || (P.poff ? solve_pass<NMAX, PASS_ITER, true>(a, S, P, it, gacc, fs, fc)
+                                                    : solve_pass<NMAX, PASS_ITER, false>(a, S, P, it, gacc, fs, fc));
         if (tid == 0) ++ps.passes;
         if (!pass_ok && lane == 0) atomicOr(&abort_s, 1);
 #pragma unroll
@@ -762,17 +843,20 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
         if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
             return LOOP_ABORT;
         // ---- every CTA reduces every column itself: warp w takes columns w, w + MP_NW, ...,
-        // four at a time with eight loads per column in flight per lane (every load of the
-        // group issued before the first add); lane l sums CTAs l, l + 32, ... in order, then
-        // a fixed butterfly: the same G and F in every CTA, with no second barrier
-        for (int k0 = wid; k0 <= n; k0 += MP_NW * 4) {
-            FF v[4];
+        // CB at a time with eight loads per column in flight per lane (every load of the group
+        // issued before the first add; CB grows with NMAX, whose kernels have fewer CTAs per SM
+        // and more columns per warp, and stays 1 where registers set the CTAs per SM); lane l
+        // sums CTAs l, l + 32, ... in order, then a fixed butterfly: the same G and F in every
+        // CTA, with no second barrier
+        constexpr int CB = NMAX >= 56 ? 4 : (NMAX >= 32 ? 2 : 1);
+        for (int k0 = wid; k0 <= n; k0 += MP_NW * CB) {
+            FF v[CB];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = FF{0.f, 0.f};
+            for (int j = 0; j < CB; ++j) v[j] = FF{0.f, 0.f};
             for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) {
-                float2 q[4][8];
+                float2 q[CB][8];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < CB; ++j) {
                     const int k = k0 + MP_NW * j;
                     const float2 *col = reinterpret_cast<const float2 *>(pb + (size_t)min(k, n) * a.pstride);
 #pragma unroll
@@ -782,17 +866,17 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < CB; ++j)
 #pragma unroll
                     for (int u = 0; u < 8; ++u) v[j] = ff_add(v[j], FF{q[j][u].x, q[j][u].y});
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] = ff_add(v[j], ff_shfl_xor(v[j], d));
+                for (int j = 0; j < CB; ++j) v[j] = ff_add(v[j], ff_shfl_xor(v[j], d));
             if (lane == 0) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < CB; ++j) {
                     const int k = k0 + MP_NW * j;
                     const double sum = ff_to_double(v[j]);
                     if (k < n) S.sG[k] = -sum;
@@ -809,7 +893,8 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
                 reinterpret_cast<float *>(S.sg4)[k] = k < n ? (float)S.sG[k] : 0.f;
             __syncthreads();
             float cs = 0.f, cc = 0.f;
-            const bool c_ok = P.n_my == 0 || solve_pass<NMAX, PASS_CAUCHY>(a, S, P, it, gacc, cs, cc);
+            const bool c_ok = P.n_my == 0 || (P.poff ? solve_pass<NMAX, PASS_CAUCHY, true>(a, S, P, it, gacc, cs, cc)
+                                                      : solve_pass<NMAX, PASS_CAUCHY, false>(a, S, P, it, gacc, cs, cc));
             if (tid == 0) ++ps.passes;
             if (!c_ok && lane == 0) atomicOr(&abort_s, 1);
             const FF cb = block_ff(FF{cs, -cc}, shff);
@@ -860,19 +945,42 @@ __device__ __forceinline__ void pipe_start(WarpPipe &P, const MPArgs &a, unsigne
     P.W = (int64_t)n_cta * MP_NW;
     P.w0 = (int64_t)cta * MP_NW + wid;
     P.tiles = a.tiles;
+    P.packed = reinterpret_cast<const unsigned char *>(a.packed);
+    P.poff = a.packed ? a.poff : nullptr;
+    P.iss = it;
+    P.pos = 0;
+    P.span = 0;
     int64_t n_wt = a.n_wtiles;
     if (a.tiles) // the live list: written by earlier kernels of the stream, fixed during the solve
         n_wt = min64((int64_t)max(__ldcg(a.n_live), 0), a.n_wtiles);
     P.n_my = P.w0 < n_wt ? (n_wt - 1 - P.w0) / P.W + 1 : 0;
     P.it_base = it;
-    if (lane == 0 && P.n_my > 0)
-        for (int s = 0; s < P.stages; ++s) P.issue(it + s);
+    // the warp's first WL_CAP tiles: index, and the packed place when packed (lane per tile)
+    for (int64_t j = lane; j < min64(P.n_my, (int64_t)WL_CAP); j += 32) {
+        const int64_t q = P.w0 + j * P.W;
+        P.wl[3 * j] = (int32_t)P.tile_of(q);
+        if (P.poff) {
+            const int32_t u0 = __ldg(P.poff + q);
+            P.wl[3 * j + 1] = u0;
+            P.wl[3 * j + 2] = __ldg(P.poff + q + 1) - u0;
+        }
+    }
+    __syncwarp();
+    if (lane == 0 && P.n_my > 0) {
+        if (P.poff) P.fill(it);
+        else
+            for (int s = 0; s < P.stages; ++s) P.issue(it + s);
+    }
 }
 
 // Copies issued ahead for a pass that will not run: let them land (this warp's slots it ..).
 __device__ __forceinline__ void pipe_drain(const WarpPipe &P, int64_t it) {
-    if ((threadIdx.x & 31) == 0 && P.n_my > 0)
-        for (int s = 0; s < P.stages; ++s) P.wait(it + s);
+    if ((threadIdx.x & 31) == 0 && P.n_my > 0) {
+        if (P.poff)
+            for (int64_t k = it; k < P.iss; ++k) P.wait_packed(k);
+        else
+            for (int s = 0; s < P.stages; ++s) P.wait(it + s);
+    }
     __syncwarp();
 }
 
@@ -880,14 +988,18 @@ __device__ __forceinline__ void pipe_init(WarpPipe &P, const SolveSmem &S, int s
                                           int keep_in_l2) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     P.my = S.stage0 + (size_t)wid * stages * cbytes;
-    P.mb = S.bars + wid * stages;
+    P.mb = S.bars + wid * PQ;
+    P.ring_bytes = (uint32_t)stages * cbytes;
+    P.moff = S.ring_meta + wid * PQ * 2;
+    P.mspan = P.moff + PQ;
+    P.wl = S.wlist + wid * WL_CAP * 3;
     P.cbytes = cbytes;
     P.stages = stages;
     // DA is read again by every iteration: keep it in L2 when it fits there
     P.pol = keep_in_l2 ? l2_evict_last_policy() : l2_evict_first_policy();
     P.n_my = 0;
     if (lane == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&P.mb[s], 1);
+        for (int s = 0; s < PQ; ++s) mbar_init(&P.mb[s], 1);
         fence_mbar_init();
     }
 }
@@ -1231,7 +1343,10 @@ __global__ void mp_tile_const_kernel(const uint8_t *sid, int32_t NA, const float
 __device__ __forceinline__ void live_mark(const MpLive &L, int32_t t, int64_t wt) {
     const int lane = threadIdx.x & 31;
     const float v = L.DA[wt * L.wstride + MP_HEAD + (int64_t)(t >> 2) * 128 + (lane << 2) + (t & 3)];
-    if (__any_sync(0xffffffffu, v != 0.f) && lane == 0) L.flag[wt] = 1;
+    if (__any_sync(0xffffffffu, v != 0.f) && lane == 0) {
+        L.flag[wt] = 1;
+        if (L.gmask) L.gmask[wt] |= 1u << (t >> 2); // one writer per tile and launch
+    }
 }
 
 __global__ void mp_live_mark_kernel(MpLive L, int32_t t) {
@@ -1262,6 +1377,19 @@ __device__ void live_count(const MpLive &L) {
     for (int st = LV_THREADS / 2; st > 0; st >>= 1) {
         if (tid < st) sums[tid] += sums[tid + st];
         __syncthreads();
+    }
+    if (L.gmask) { // packed units of the block's live tiles: a head and 4 per marked group
+        int32_t u = f ? 1 + 4 * __popc(L.gmask[q]) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) u += __shfl_xor_sync(0xffffffffu, u, d);
+        __shared__ int32_t wu[LV_THREADS / 32];
+        if ((tid & 31) == 0) wu[tid >> 5] = u;
+        __syncthreads();
+        if (tid == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < LV_THREADS / 32; ++w) tot += wu[w];
+            L.bsize[blockIdx.x] = tot;
+        }
     }
     if (tid == 0) {
         L.bcnt[blockIdx.x] = c;
@@ -1297,16 +1425,49 @@ __device__ void live_write(const MpLive &L, int64_t n_blocks) {
         woff[lane] = x - v;
     }
     __syncthreads();
-    if (f) L.tiles[base_s + woff[wid] + __popc(m & ((1u << lane) - 1u))] = (int32_t)q;
+    const int32_t li = base_s + woff[wid] + __popc(m & ((1u << lane) - 1u)); // list index of a live tile
+    if (f) L.tiles[li] = (int32_t)q;
+    if (L.gmask) { // packed offsets in list order: earlier blocks' units, then a block scan
+        __shared__ int32_t su[32];
+        __shared__ int32_t ubase_s;
+        const int32_t u = f ? 1 + 4 * __popc(L.gmask[q]) : 0;
+        int32_t x = u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) su[wid] = x;
+        if (tid == 0) {
+            int32_t b = 0;
+            for (int64_t k = 0; k < blockIdx.x; ++k) b += L.bsize[k];
+            ubase_s = b;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const int32_t v = su[lane];
+            int32_t y = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t o = __shfl_up_sync(0xffffffffu, y, d);
+                if (lane >= d) y += o;
+            }
+            su[lane] = y - v;
+        }
+        __syncthreads();
+        if (f) L.poff[li] = ubase_s + su[wid] + x - u;
+    }
     if (blockIdx.x == 0 && tid == 0) {
-        int32_t n = 0;
+        int32_t n = 0, units = 0;
         double acc = 0.0;
         for (int64_t k = 0; k < n_blocks; ++k) {
             n += L.bcnt[k];
             acc += L.bpart[k];
+            if (L.gmask) units += L.bsize[k];
         }
         *L.n_live = n;
         *L.F_off = *L.F0 + acc;
+        if (L.gmask) L.poff[n] = units;
     }
 }
 
@@ -1340,6 +1501,41 @@ vmat_status mp_tile_consts(const uint8_t *sid_c, int32_t NA, const vmat_voxels *
     const int64_t blocks = (n_wtiles * 32 + 255) / 256;
     mp_tile_const_kernel<<<(unsigned)blocks, 256, 0, s>>>(sid_c, NA, vox->T, vox->w_over, vox->w_under, n_wtiles,
                                                           c_tile);
+    VMAT_LAUNCH_CHECK();
+    return VMAT_OK;
+}
+
+// A warp per live list entry: the tile's labels and group mask, then its marked groups
+// of the first G groups, ascending (float4 per lane; the group's 512 bytes per warp).
+__global__ void mp_pack_kernel(MpLive L, int32_t G) {
+    if (L.skip && *L.skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_live = min64((int64_t)max(__ldcg(L.n_live), 0), L.n_wtiles);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_live;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t q = __ldcg(L.tiles + i);
+        const float *src = L.DA + q * L.wstride;
+        float *dst = L.packed + (int64_t)__ldcg(L.poff + i) * 32;
+        const uint32_t mask = __ldcg(L.gmask + q);
+        if (lane < 8) dst[lane] = src[lane]; // the 32 labels
+        if (lane == 8) dst[8] = __uint_as_float(mask);
+        int slot = 0;
+        for (int g = 0; g < G; ++g) {
+            if (!((mask >> g) & 1u)) continue; // warp-uniform
+            const float4 v = reinterpret_cast<const float4 *>(src + MP_HEAD + g * 128)[lane];
+            reinterpret_cast<float4 *>(dst + MP_HEAD + slot * 128)[lane] = v;
+            ++slot;
+        }
+    }
+}
+
+vmat_status mp_pack(const MpLive &L, int32_t n, cudaStream_t s) {
+    if (L.n_wtiles < 1 || !L.packed) return VMAT_OK;
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    const int64_t want = (L.n_wtiles * 32 + 255) / 256;
+    mp_pack_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * 8)), 256, 0, s>>>(
+        L, (n + 3) / 4);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }
@@ -1400,15 +1596,14 @@ static int solve_nmax(int n) { return ((n + 7) / 8) * 8; }
 static size_t solve_fixed(int n) {
     const int nmax = solve_nmax(n);
     return 128 /* alignment slack */ + 2 * (size_t)(nmax / 4) * 16 + 4 * (size_t)nmax * 8 + 8 * 8 +
-           (size_t)nmax * 4 + (size_t)MP_NW * nmax * 4 + 3 * 256 * 4;
+           (size_t)nmax * 4 + (size_t)MP_NW * nmax * 4 + 3 * 256 * 4 + (size_t)MP_NW * PQ * (8 + 8) +
+           (size_t)MP_NW * WL_CAP * 12;
 }
-static size_t solve_smem(int n, int stages) {
-    return solve_fixed(n) + (size_t)stages * (MP_NW * wt_copy_bytes(n) + MP_NW * 8);
-}
+static size_t solve_smem(int n, int stages) { return solve_fixed(n) + (size_t)stages * MP_NW * wt_copy_bytes(n); }
 // Tiles in flight per warp: as many as fit (up to 8) in ~110 KB, so that two CTAs
 // share an SM; where not even two fit there, up to the per-CTA limit (one CTA per SM).
 static int solve_stages(int n) {
-    const size_t per = MP_NW * wt_copy_bytes(n) + MP_NW * 8;
+    const size_t per = MP_NW * wt_copy_bytes(n);
     const size_t small = 110 * 1024;
     const size_t st = solve_fixed(n) + 2 * per <= small ? (small - solve_fixed(n)) / per
                                                         : (MP_SMEM_LIMIT - solve_fixed(n)) / per;
@@ -1555,6 +1750,8 @@ static void mp_fill_args(MPArgs &a, void *ws, int n_cap, int p_max, const float 
     a.tiles = nullptr;
     a.n_live = nullptr;
     a.F_off_dev = nullptr;
+    a.packed = nullptr;
+    a.poff = nullptr;
 }
 
 static vmat_status mp_launch_persistent(MPArgs &a, const MPLaunch &L, cudaStream_t s) {
@@ -1592,6 +1789,8 @@ vmat_status mp_bb_enqueue(const float *DA, int32_t V, int32_t n_ap, int32_t n_ca
         a.tiles = live->tiles;
         a.n_live = live->n_live;
         a.F_off_dev = live->F_off;
+        a.packed = live->packed;
+        a.poff = live->poff;
     }
     return mp_launch_persistent(a, L, s);
 }
