@@ -56,9 +56,12 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
 INDEX16_CFGS = (12, 13, 14)
 # DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
 # configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel.
-# The plan's passes are windowed: their ratio is WINDOWED_TRAFFIC_RATIO, measured on a windowed
-# launch of the plan; a configuration without such a capture reports null.
-WINDOWED_TRAFFIC_RATIO = {("f32", 11): 1.0103}
+# The plan's passes are windowed (the rows inside the leaf-travel windows, taken as one list): their
+# ratio is WINDOWED_TRAFFIC_RATIO, the sum over the 30 windowed launches of the 45-CP plan (the same
+# kernels on a quarter of the CPs) over their algorithmic bytes; a configuration without such a
+# capture reports null.
+WINDOWED_TRAFFIC_RATIO = {("f32", 5): 0.9988, ("f32", 9): 1.0010, ("f32", 11): 1.0009}
+TRAFFIC_RATIO = {("f32", 11): 1.0103}
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
                  ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
                  ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
@@ -530,8 +533,8 @@ def run_ours(args, rank, world, local):
             "frac": round(achieved / peaks["hbm_gbs"], 4),
             "traffic": None if ratio is None else round(ratio * bytes_launch),
             "traffic_source": None if ratio is None else
-            f"ncu dram bytes / algorithmic bytes = {ratio} for this kernel on a windowed D^T g launch of the "
-            "plan, times this launch's algorithmic bytes",
+            f"ncu dram bytes / algorithmic bytes = {ratio} for this kernel over the windowed D^T g launches of "
+            "the 45-CP plan, times this launch's algorithmic bytes",
             "peak_source": peaks["source"], "frac_of_nominal": round(achieved / roofline.HBM_NOMINAL_GBS, 4),
             "nominal_peak": roofline.HBM_NOMINAL_GBS, "bytes_per_launch": round(bytes_launch),
             "avg_launch_ms": round(spmv_ms / max(spmv_n, 1), 4)}

@@ -403,6 +403,10 @@ struct SolveSmem {
     int32_t *wlist;        // [MP_NW][WL_CAP][3] the warp's first tiles: tile, packed unit offset, units
 };
 
+// Resident CTAs per SM the persistent solvers are compiled for (a register budget): more
+// CTAs for fewer apertures, whose tiles are small and whose warps wait on copies.
+__host__ __device__ constexpr int mp_min_ctas(int nmax) { return nmax <= 8 ? 4 : (nmax <= 24 ? 3 : (nmax <= 48 ? 2 : 1)); }
+
 // Copies in flight per warp at most (mbarriers per warp): the tile stages of whole tiles, or
 // the packed tiles that fit in the warp's byte ring.
 constexpr int PQ = 8;
@@ -436,6 +440,7 @@ struct WarpPipe {
     int32_t *wl;                 // [WL_CAP][3] this warp's tile j: tile, packed unit offset, units
     uint32_t ring_bytes;
     int64_t iss;                 // lane 0: the next tile to issue
+    int64_t jiss;                // lane 0: its place in the warp's tile cycle, (iss - it_base) mod n_my
     uint32_t pos, span;          // lane 0: ring write position, ring bytes held by tiles in flight
     __device__ __forceinline__ int64_t tile_of(int64_t q) const { return tiles ? (int64_t)__ldg(tiles + q) : q; }
     // the warp's tile j (0 <= j < n_my): tile index, from the shared list when it holds it
@@ -443,20 +448,21 @@ struct WarpPipe {
         return j < WL_CAP ? (int64_t)wl[3 * j] : tile_of(w0 + j * W);
     }
     __device__ __forceinline__ void issue(int64_t it) const {
-        const int s = (int)(it % stages);
-        const int64_t wt = my_tile((it - it_base) % n_my);
+        const int s = (int)((uint32_t)it % (uint32_t)stages);
+        const int64_t wt = my_tile((uint32_t)(it - it_base) % (uint32_t)n_my);
         mbar_arrive_expect_tx(&mb[s], cbytes);
         bulk_g2s(my + (size_t)s * cbytes, src + wt * tile_bytes, cbytes, &mb[s], pol);
     }
     __device__ __forceinline__ bool wait(int64_t it) const {
-        return mbar_wait_bounded(&mb[it % stages], (uint32_t)((it / stages) & 1), WAIT_LIMIT_CYCLES);
+        return mbar_wait_bounded(&mb[(uint32_t)it % (uint32_t)stages], ((uint32_t)it / (uint32_t)stages) & 1u,
+                                 WAIT_LIMIT_CYCLES);
     }
     // packed: issue tiles iss, iss + 1, ... while fewer than PQ are in flight past tile `it`
     // (the next to be consumed) and the ring has room (lane 0)
     __device__ __forceinline__ void fill(int64_t it) {
         if (span == 0) pos = 0; // an empty ring: any tile fits from its start
         while (iss - it < PQ) {
-            const int64_t j = (iss - it_base) % n_my;
+            const int64_t j = jiss;
             int64_t u0;
             uint32_t units;
             if (j < WL_CAP) {
@@ -482,6 +488,7 @@ struct WarpPipe {
             pos = start + bytes;
             span += gap + bytes;
             ++iss;
+            if (++jiss == n_my) jiss = 0;
         }
     }
     __device__ __forceinline__ bool wait_packed(int64_t it) const {
@@ -505,7 +512,7 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
         const bool ok = PACKED ? P.wait_packed(it) : P.wait(it);
         if (!__all_sync(0xffffffffu, ok)) return false;
         const unsigned char *blk =
-            PACKED ? P.my + P.moff[it % PQ] : P.my + (size_t)(it % P.stages) * P.cbytes;
+            PACKED ? P.my + P.moff[it % PQ] : P.my + (size_t)((uint32_t)it % (uint32_t)P.stages) * P.cbytes;
         const float4 *D4 = reinterpret_cast<const float4 *>(blk + 128) + lane; // group g at D4[32 g]
         const float4 *w4 = MODE == PASS_ITER ? S.sy4 : S.sg4;
         // packed: the marked groups only, in order (a group left out holds zeros, which add nothing)
@@ -568,6 +575,48 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
         }
     }
     return true;
+}
+
+// The warp's sums over its 32 lanes of the G shares gacc[0 .. n), written to out[0 .. n).
+// From 16 apertures on, by halving exchanges over 32-column chunks: at the exchange of
+// width w each lane keeps half of its remaining columns (the upper half when its lane bit
+// w is set), sends the other half to lane ^ w and adds what it receives; after five
+// exchanges lane l holds column l of the chunk.  31 shuffles per chunk instead of 5 per
+// column.  Columns at or past n hold zero (their DA groups are zero padding).  A fixed
+// order: every warp of every CTA adds the same way.
+template <int NMAX>
+__device__ __forceinline__ void warp_share_sums(const float *gacc, int n, float *out, int lane) {
+    if (NMAX < 16) {
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < n) {
+                float x = gacc[k];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+                if (lane == 0) out[k] = x;
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < (NMAX + 31) / 32; ++c) {
+        if (32 * c < n) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = 32 * c + i < NMAX ? gacc[32 * c + i] : 0.f;
+#pragma unroll
+            for (int w = 16; w >= 1; w >>= 1) {
+                const bool up = (lane & w) != 0;
+#pragma unroll
+                for (int i = 0; i < w; ++i) {
+                    const float send = up ? v[i] : v[i + w];
+                    const float keep = up ? v[i + w] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                }
+            }
+            if (32 * c + lane < n) out[32 * c + lane] = v[0];
+        }
+    }
 }
 
 // CTA sum of one float pair per thread (result in thread 0): warp butterflies, warps in order.
@@ -820,15 +869,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
                                                     : solve_pass<NMAX, PASS_ITER, false>(a, S, P, it, gacc, fs, fc));
         if (tid == 0) ++ps.passes;
         if (!pass_ok && lane == 0) atomicOr(&abort_s, 1);
-#pragma unroll
-        for (int k = 0; k < NMAX; ++k) {
-            if (k < n) {
-                float x = gacc[k];
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-                if (lane == 0) S.wred[wid * NMAX + k] = x;
-            }
-        }
+        warp_share_sums<NMAX>(gacc, n, S.wred + wid * NMAX, lane);
         const FF fb = block_ff(FF{fs, -fc}, shff); // includes a __syncthreads after wred
         // this CTA's partials, column-major by CTA, in the buffer of this iteration's parity: a CTA
         // writes buffer b again two iterations later, after the barrier that every CTA reaches only
@@ -948,6 +989,7 @@ __device__ __forceinline__ void pipe_start(WarpPipe &P, const MPArgs &a, unsigne
     P.packed = reinterpret_cast<const unsigned char *>(a.packed);
     P.poff = a.packed ? a.poff : nullptr;
     P.iss = it;
+    P.jiss = 0;
     P.pos = 0;
     P.span = 0;
     int64_t n_wt = a.n_wtiles;
@@ -1005,7 +1047,7 @@ __device__ __forceinline__ void pipe_init(WarpPipe &P, const SolveSmem &S, int s
 }
 
 template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
+__global__ void __launch_bounds__(MP_THREADS, mp_min_ctas(NMAX)) mp_solve_kernel(MPArgs a, int stages, int keep_in_l2) {
     if (a.skip && *a.skip) return; // the same flag for every CTA: all return together
     extern __shared__ __align__(128) unsigned char sm_raw[];
     __shared__ PState ps;
@@ -1070,7 +1112,7 @@ __device__ bool batch_sync(unsigned *gctl, unsigned n_cta, const MPArgs *args, i
 // whole grid (gctl[0..1]), after which the CTAs are split again among the
 // problems left.  Every problem has n apertures.
 template <int NMAX>
-__global__ void __launch_bounds__(MP_THREADS)
+__global__ void __launch_bounds__(MP_THREADS, mp_min_ctas(NMAX))
     mp_solve_batched_kernel(const MPArgs *__restrict__ args, const int64_t *__restrict__ weight, int32_t n_plans,
                             int32_t n, unsigned *gctl, int stages, int keep_in_l2) {
     extern __shared__ __align__(128) unsigned char sm_raw[];
