@@ -491,6 +491,16 @@ struct WarpPipe {
             if (++jiss == n_my) jiss = 0;
         }
     }
+    // after consuming tile `it` (lane 0): packed, release its ring bytes and top the ring up;
+    // whole tiles, reuse its slot for the tile `stages` ahead
+    __device__ __forceinline__ void refill(int64_t it, bool packed_mode) {
+        if (packed_mode) {
+            span -= mspan[it % PQ];
+            fill(it + 1);
+        } else {
+            issue(it + stages);
+        }
+    }
     __device__ __forceinline__ bool wait_packed(int64_t it) const {
         return mbar_wait_bounded(&mb[it % PQ], (uint32_t)((it / PQ) & 1), WAIT_LIMIT_CYCLES);
     }
@@ -506,6 +516,11 @@ template <int NMAX, int MODE, bool PACKED>
 __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, WarpPipe &P, int64_t &it,
                                            float *gacc, float &fs, float &fc) {
     constexpr int GMAX = NMAX / 4;
+    // From 56 to 72 apertures (one CTA per SM, registers to spare) a tile's groups stay in
+    // registers between the dose and the G shares, so its slot is refilled before the
+    // objective; the Cauchy pass reads the slot once and refills at the same point.
+    constexpr bool KEEP = NMAX >= 56 && NMAX <= 72 && MODE == PASS_ITER;
+    constexpr bool EARLY = KEEP || MODE == PASS_CAUCHY;
     const int G = (a.n + 3) >> 2;
     const int lane = threadIdx.x & 31;
     for (int64_t j = 0; j < P.n_my; ++j, ++it) {
@@ -517,22 +532,28 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
         const float4 *w4 = MODE == PASS_ITER ? S.sy4 : S.sg4;
         // packed: the marked groups only, in order (a group left out holds zeros, which add nothing)
         const uint32_t gm = PACKED ? reinterpret_cast<const uint32_t *>(blk)[8] : 0u;
+        float4 vk[KEEP ? GMAX : 1];
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
         int slot = 0;
 #pragma unroll
         for (int g = 0; g < GMAX; ++g)
             if (g < G && (!PACKED || ((gm >> g) & 1u))) {
                 const float4 v = D4[32 * (PACKED ? slot++ : g)], w = w4[g];
+                if (KEEP) vk[KEEP ? g : 0] = v;
                 z0 = fmaf(v.x, w.x, z0);
                 z1 = fmaf(v.y, w.y, z1);
                 z2 = fmaf(v.z, w.z, z2);
                 z3 = fmaf(v.w, w.w, z3);
             }
+        const int sid = blk[lane];
+        if (EARLY) {
+            __syncwarp(); // every lane's reads of this slot are done before its next copy
+            if (lane == 0) P.refill(it, PACKED);
+        }
         const float zi = (z0 + z1) + (z2 + z3);
         const int64_t i = P.my_tile(j) * MP_WT + lane;
         float gi = 0.f;
         if (i < a.V) {
-            const int sid = blk[lane];
             if (MODE == PASS_ITER) {
                 a.z[i] = zi;
                 const float d = zi - S.sT[sid];
@@ -557,21 +578,16 @@ __device__ __forceinline__ bool solve_pass(const MPArgs &a, const SolveSmem &S, 
 #pragma unroll
             for (int g = 0; g < GMAX; ++g)
                 if (g < G && (!PACKED || ((gm >> g) & 1u))) {
-                    const float4 v = D4[32 * (PACKED ? slot++ : g)];
+                    const float4 v = KEEP ? vk[KEEP ? g : 0] : D4[32 * (PACKED ? slot++ : g)];
                     gacc[4 * g + 0] = fmaf(v.x, gi, gacc[4 * g + 0]);
                     gacc[4 * g + 1] = fmaf(v.y, gi, gacc[4 * g + 1]);
                     gacc[4 * g + 2] = fmaf(v.z, gi, gacc[4 * g + 2]);
                     gacc[4 * g + 3] = fmaf(v.w, gi, gacc[4 * g + 3]);
                 }
         }
-        __syncwarp(); // every lane's reads of this slot are done before its next copy
-        if (lane == 0) {
-            if (PACKED) {
-                P.span -= P.mspan[it % PQ];
-                P.fill(it + 1);
-            } else {
-                P.issue(it + P.stages);
-            }
+        if (!EARLY) {
+            __syncwarp(); // every lane's reads of this slot are done before its next copy
+            if (lane == 0) P.refill(it, PACKED);
         }
     }
     return true;
