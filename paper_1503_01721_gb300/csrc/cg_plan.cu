@@ -162,7 +162,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_TRY(ar.get(&F_dev, 2));
     VMAT_TRY(ar.get(&F0, 2));
     VMAT_TRY(ar.get((char **)&obj_ws, objective_scratch_bytes(ctx->n_sm)));
-    VMAT_TRY(ar.get((char **)&pr_ws, pricing_scratch_bytes(mlc)));
+    VMAT_TRY(ar.get((char **)&pr_ws, pricing_scratch_bytes_prefix(mlc)));
     // leaf-travel windows of every (CP, MLC row) before each D^T g, and the rows,
     // nonzeros and 16-bit-index chunks inside them per pass
     PricingGeom pg;
@@ -300,7 +300,8 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         ++spmv_launches;
         // ---- PP2, and the commit (or the stop) on the device
         tm.mark(PH_PP2);
-        VMAT_TRY(price_apertures_impl(mlc, pi, occupied, leaves_all, best_cp, best_leaves, best_price, pr_ws, s, ctl));
+        VMAT_TRY(price_apertures_impl(mlc, pi, occupied, leaves_all, best_cp, best_leaves, best_price, pr_ws, s, ctl,
+                                      true));
         commit_aperture<<<1, 128, 0, s>>>(t, NR, best_cp, best_price, best_leaves, occupied, active, leaves_all,
                                          leaves_seq, cps_dev, y, ctl);
         VMAT_LAUNCH_CHECK();

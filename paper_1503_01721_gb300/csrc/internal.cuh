@@ -267,9 +267,12 @@ struct WinPlan { // one plan's window inputs and outputs in a batched launch
 vmat_status price_windows_batched(const WinPlan *plans, int32_t n_plans, int32_t max_K, int32_t t, cudaStream_t s);
 // One plan's pricing (either variant) with scratch ws of pricing_scratch_bytes(mlc);
 // skip (may be null): a device word, nonzero = leave the outputs untouched.
+// ws_has_prefix: ws holds pricing_scratch_bytes_prefix(mlc) bytes, and the row search
+// reads prefix sums formed a row per thread (the same values, fewer FP64 instructions).
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                                  int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws, cudaStream_t s,
-                                 const int32_t *skip);
+                                 const int32_t *skip, bool ws_has_prefix = false);
+size_t pricing_scratch_bytes_prefix(const vmat_mlc *mlc);
 
 struct PricePlan { // one plan's pricing inputs, per-row scratch and results
     PricingGeom g;

@@ -126,7 +126,7 @@ __host__ __device__ constexpr size_t row_smem_stride(int n_cols) { return (((siz
 __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float *__restrict__ pi,
                                                const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
                                                int64_t gw, unsigned char *ws, double *rb_v, int16_t *rb_lr,
-                                               uint8_t *rb_ok) {
+                                               uint8_t *rb_ok, const double *__restrict__ Pall = nullptr) {
     const int lane = threadIdx.x & 31;
     const int k = (int)(gw / g.n_rows), r = (int)(gw % g.n_rows);
     if (occupied[k]) return;
@@ -136,7 +136,11 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
     const int kl = nearest_occupied(g, occupied, k, -1, lane), kr = nearest_occupied(g, occupied, k, 1, lane);
     const RowWindow win = row_window(g, leaves, k, r, kl, kr);
     const int Lmin = win.Lmin, Lmax = win.Lmax, Rmin = win.Rmin, Rmax = win.Rmax;
-    if (lane == 0) window_prefix(pi + ((int64_t)k * g.n_rows + r) * N, N, Lmin, Rmax, P);
+    if (Pall) { // the same prefix sums, formed by window_prefix_kernel a thread per row
+        for (int c = lane; c <= N; c += 32) P[c] = Pall[gw * (N + 1) + c];
+    } else if (lane == 0) {
+        window_prefix(pi + ((int64_t)k * g.n_rows + r) * N, N, Lmin, Rmax, P);
+    }
     __syncwarp();
     float pmax = 0.f;
     for (int c = lane; c <= N; c += 32) {
@@ -200,13 +204,13 @@ __device__ __forceinline__ void price_row_warp(const PricingGeom &g, const float
 __global__ void __launch_bounds__(PR_WARPS * 32)
     price_rows_kernel(PricingGeom g, const float *__restrict__ pi, const uint8_t *__restrict__ occupied,
                       const int16_t *__restrict__ leaves, double *rb_v, int16_t *rb_lr, uint8_t *rb_ok,
-                      const int32_t *skip) {
+                      const int32_t *skip, const double *__restrict__ Pall) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sP[]; // PR_WARPS x row_smem_stride(n_cols)
     const int wid = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * PR_WARPS + wid;
     if (gw >= (int64_t)g.K * g.n_rows) return;
-    price_row_warp(g, pi, occupied, leaves, gw, sP + wid * row_smem_stride(g.n_cols), rb_v, rb_lr, rb_ok);
+    price_row_warp(g, pi, occupied, leaves, gw, sP + wid * row_smem_stride(g.n_cols), rb_v, rb_lr, rb_ok, Pall);
 }
 
 constexpr int CP_THREADS = 1024;
@@ -338,8 +342,11 @@ __host__ __device__ constexpr size_t interdig_smem(int N) {
 }
 
 // Window prefix sums of every MLC row of every unoccupied CP (a thread per row,
-// float64 in column order, as the definition), for the chain kernels.
-__global__ void interdig_prefix_kernel(PricingGeom g, const float *__restrict__ pi,
+// float64 in column order, as the definition), for the chain kernels and the row
+// kernel.  FP64 issues at a small fraction of the FP32 rate on this GPU: a row per
+// lane keeps 32 rows' sequential sums in one instruction stream, where a row per
+// warp spends a warp-wide FP64 instruction on every add of one row.
+__global__ void window_prefix_kernel(PricingGeom g, const float *__restrict__ pi,
                                        const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves,
                                        double *__restrict__ Pall, const int32_t *skip) {
     if (skip && *skip) return;
@@ -770,9 +777,14 @@ vmat_status price_apertures_batched(const PricePlan *plans, const int64_t *off, 
     return VMAT_OK;
 }
 
+// Bytes of the per-row bests (value, leaves, flag) of `rows` rows, rounded up to 16.
+static size_t row_best_bytes(int64_t rows) {
+    return ((size_t)rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 15) & ~(size_t)15;
+}
+
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                                  int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws,
-                                 cudaStream_t s, const int32_t *skip) {
+                                 cudaStream_t s, const int32_t *skip, bool ws_has_prefix) {
     PricingGeom g;
     VMAT_TRY(pricing_geom(mlc, &g));
     const int64_t rows = (int64_t)g.K * g.n_rows;
@@ -788,7 +800,7 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
         const size_t sm = interdig_smem(g.n_cols);
         VMAT_TRY(pricing_attributes());
         const int64_t rows = (int64_t)g.K * g.n_rows;
-        interdig_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
+        window_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
                                  s>>>(g, pi, occupied, leaves, Pall, skip);
         VMAT_LAUNCH_CHECK();
         price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, Pall, occupied, leaves, cp_val, cp_ok, pred_all,
@@ -802,11 +814,25 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
     const size_t smem = PR_WARPS * row_smem_stride(g.n_cols);
     VMAT_TRY(pricing_attributes());
     const int64_t blocks = (rows + PR_WARPS - 1) / PR_WARPS;
-    price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok, skip);
+    double *Pall = nullptr;
+    if (ws_has_prefix) { // after the row bests (pricing_scratch_bytes_prefix)
+        Pall = reinterpret_cast<double *>(static_cast<char *>(ws) + row_best_bytes(rows));
+        window_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
+                               s>>>(g, pi, occupied, leaves, Pall, skip);
+        VMAT_LAUNCH_CHECK();
+    }
+    price_rows_kernel<<<(unsigned)blocks, PR_WARPS * 32, smem, s>>>(g, pi, occupied, leaves, rb_v, rb_lr, rb_ok, skip,
+                                                                     Pall);
     VMAT_LAUNCH_CHECK();
     price_cps_kernel<<<1, CP_THREADS, 0, s>>>(g, occupied, rb_v, rb_lr, rb_ok, best_cp, best_leaves, best_price, skip);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
+}
+
+size_t pricing_scratch_bytes_prefix(const vmat_mlc *mlc) {
+    const size_t rows = (size_t)mlc->K * mlc->n_rows;
+    if (mlc->interdigitation) return pricing_scratch_bytes(mlc);
+    return std::max(pricing_scratch_bytes(mlc), row_best_bytes((int64_t)rows) + rows * (mlc->n_cols + 1) * 8 + 64);
 }
 
 size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
@@ -853,8 +879,8 @@ extern "C" vmat_status price_apertures(const vmat_mlc *mlc, const float *pi, con
         return set_error(VMAT_EINVAL, "price_apertures: NULL argument");
     cudaStream_t s = as_stream(stream);
     Scratch ws;
-    VMAT_TRY(ws.alloc(pricing_scratch_bytes(mlc), s));
-    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s, nullptr);
+    VMAT_TRY(ws.alloc(pricing_scratch_bytes_prefix(mlc), s));
+    return price_apertures_impl(mlc, pi, occupied, leaves, best_cp, best_leaves, best_price, ws.ptr, s, nullptr, true);
 }
 
 // Same computation as price_apertures with the fixed device scratch above: no
