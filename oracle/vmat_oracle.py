@@ -62,10 +62,6 @@ R11 Delivery limits (Eq. 2, 6).  Gantry speed s_k of an occupied CP is the
     aperture.  The travel window (R7) must not exceed what the leaves can do at
     the slowest gantry speed (travel_cols S^L <= cp_step leaf_speed), which
     keeps S^U_k >= S^L.
-R12 FP32 refinement of a BF16 / FP8 plan (the precision form): the apertures
-    stay as chosen on the stored values; their dose vectors are recomputed from
-    the float32 values, the master problem is solved again from the plan's y,
-    and the final dose comes from the float32 values.
 R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
     not pass the right leaf of an adjacent row, L_r <= min(R_{r-1}, R_{r+1}).
     The best aperture of a CP is then a chain over the rows: the sequential
@@ -82,6 +78,10 @@ R10 Interdigitation (Section 2.2.2, second variant): the left leaf of a row may
     every interlocking aperture under R10's order on whole apertures (total,
     then the last row's key, then the partial sum before it and that row's
     key, down to the first row), prices and leaves.
+R12 FP32 refinement of a BF16 / FP8 plan (the precision form): the apertures
+    stay as chosen on the stored values; their dose vectors are recomputed from
+    the float32 values, the master problem is solved again from the plan's y,
+    and the final dose comes from the float32 values.
 """
 from __future__ import annotations
 
