@@ -395,6 +395,7 @@ struct SolveSmem {
     double *sG, *sGp;      // [NMAX]   G_t, G_{t-1}
     double *sS, *sR;       // [NMAX]   s = y_t - y_{t-1}, r = G_t - G_{t-1} (the step's inputs)
     double *sRed;          // [8]      the step's sums and maxima
+    FF *sGff;              // [NMAX + 1] the reduced sums as float pairs: -G, then F (converted in the step)
     float *sYp;            // [NMAX]   y_{t-1}
     float *wred;           // [MP_NW][NMAX]
     float *sT, *sO, *sU;   // [256]
@@ -416,7 +417,8 @@ constexpr int PQ = 8;
 constexpr int WL_CAP = 64;
 
 template <int NMAX> __host__ __device__ constexpr size_t solve_fixed_smem() {
-    return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 4 * (size_t)NMAX * 8 + 8 * 8 + (size_t)NMAX * 4 +
+    return 128 /* alignment slack */ + 2 * (NMAX / 4) * 16 + 4 * (size_t)NMAX * 8 + 8 * 8 + 8 * (size_t)(NMAX + 1) +
+           (size_t)NMAX * 4 +
            (size_t)MP_NW * NMAX * 4 + 3 * 256 * 4 + (size_t)MP_NW * PQ * (8 + 8) + (size_t)MP_NW * WL_CAP * 12;
 }
 
@@ -661,10 +663,13 @@ __device__ void solve_step_cta(const MPArgs &a, const SolveSmem &S, PState &ps) 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = a.n, t = ps.t;
     float *y = reinterpret_cast<float *>(S.sy4);
+    // FP64 issues at a small fraction of the FP32 rate on this GPU: the reduced float pairs
+    // are converted here, one column per thread, not one column per warp instruction
+    if (tid == MP_THREADS - 1) ps.F = ff_to_double(S.sGff[n]) + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
     for (int k = tid; k < n; k += MP_THREADS) {
         float yk = y[k];
         const float l = lo_of(a, k), h = hi_of(a, k);
-        double g = S.sG[k];
+        double g = -ff_to_double(S.sGff[k]);
         if (yk <= l && g > 0.0) {
             yk = l;
             g = 0.0;
@@ -770,7 +775,8 @@ template <int NMAX> __device__ __forceinline__ SolveSmem solve_layout(unsigned c
     S.sS = S.sGp + NMAX;
     S.sR = S.sS + NMAX;
     S.sRed = S.sR + NMAX;
-    S.sYp = reinterpret_cast<float *>(S.sRed + 8);
+    S.sGff = reinterpret_cast<FF *>(S.sRed + 8);
+    S.sYp = reinterpret_cast<float *>(S.sGff + NMAX + 1);
     S.wred = S.sYp + NMAX;
     S.sT = S.wred + MP_NW * NMAX;
     S.sO = S.sT + 256;
@@ -931,13 +937,11 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             for (int d = 16; d > 0; d >>= 1)
 #pragma unroll
                 for (int j = 0; j < CB; ++j) v[j] = ff_add(v[j], ff_shfl_xor(v[j], d));
-            if (lane == 0) {
+            if (lane == 0) { // float pairs: the step converts them a column per thread
 #pragma unroll
                 for (int j = 0; j < CB; ++j) {
                     const int k = k0 + MP_NW * j;
-                    const double sum = ff_to_double(v[j]);
-                    if (k < n) S.sG[k] = -sum;
-                    else if (k == n) ps.F = sum + a.F_offset + (a.F_off_dev ? __ldcg(a.F_off_dev) : 0.0);
+                    if (k <= n) S.sGff[k] = v[j];
                 }
             }
         }
@@ -1654,7 +1658,7 @@ static int solve_nmax(int n) { return ((n + 7) / 8) * 8; }
 static size_t solve_fixed(int n) {
     const int nmax = solve_nmax(n);
     return 128 /* alignment slack */ + 2 * (size_t)(nmax / 4) * 16 + 4 * (size_t)nmax * 8 + 8 * 8 +
-           (size_t)nmax * 4 + (size_t)MP_NW * nmax * 4 + 3 * 256 * 4 + (size_t)MP_NW * PQ * (8 + 8) +
+           8 * (size_t)(nmax + 1) + (size_t)nmax * 4 + (size_t)MP_NW * nmax * 4 + 3 * 256 * 4 + (size_t)MP_NW * PQ * (8 + 8) +
            (size_t)MP_NW * WL_CAP * 12;
 }
 static size_t solve_smem(int n, int stages) { return solve_fixed(n) + (size_t)stages * MP_NW * wt_copy_bytes(n); }
