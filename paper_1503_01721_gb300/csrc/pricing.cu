@@ -336,9 +336,11 @@ __device__ __forceinline__ bool key_better(uint64_t ka, uint32_t sa, uint64_t kb
     return ka > kb || (ka == kb && sa < sb);
 }
 
+constexpr int INTERDIG_PSTRIDE = 96; // doubles per row of prefix sums in shared memory (>= INTERDIG_MAX_COLS + 1)
+static_assert(INTERDIG_PSTRIDE >= INTERDIG_MAX_COLS + 1 && INTERDIG_PSTRIDE % 2 == 0, "prefix-sum rows");
 __host__ __device__ constexpr size_t interdig_smem(int N) {
-    // S_{r-1}, S_r (double), CM (int32), tie keys (uint32)
-    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4 + 4) + 64;
+    // S_{r-1} and S_r as order keys, two rows of prefix sums, the scans' tie keys
+    return (size_t)(N + 1) * (N + 1) * (8 + 8 + 4) + 2 * INTERDIG_PSTRIDE * 8 + 64;
 }
 
 // Window prefix sums of every MLC row of every unoccupied CP (a thread per row,
@@ -426,195 +428,266 @@ __global__ void __launch_bounds__(WIN_WARPS * 32)
     cp_windows_warp(P.g, P.occupied, P.leaves, k, P.win, P.rowptr, nullptr, P.counts ? P.counts + 3 * (int64_t)t : nullptr);
 }
 
-// Inclusive "best so far" scans over the previous row's feasible rectangle
-// [pL0, pL1] x [pR0, pR1] of states (L, R), four threads per line: each scans a
-// segment of about a quarter of the line in scan order, the segments' bests pass
-// along the line by two shuffles, and each thread rescans its segment from that
-// carry, writing the best state so far to CM.  SUFFIX: line L is (L, R) for R = pR1
-// down to pR0, C[L][R] written at CM[L (N + 1) + R]; otherwise line b is CM[a (N + 1)
-// + b] for a = pL0 .. pL1 (the state index stored there), rewritten in place with
-// M[a][b], the best state with L <= a and R >= b.
+// Inclusive "best so far" scans over the previous row's window rectangle
+// [pL0, pL1] x [pR0, pR1], one pass per line with G threads per line (the largest
+// power of two up to 32 that fits every line into the block): each thread takes the
+// best of a contiguous segment of its line in scan order, the segment bests are
+// scanned across the line's G lanes by shuffles, and each thread rescans its segment
+// from the carry of the segments before it, writing every element's best so far.
+// A candidate is (order key of S_{r-1}, tie key); a state with L > R is no candidate
+// (key 0 and tie key SEC_NONE, below every state).
+//   SUFFIX: line L, elements R = pR1 down to pR0; C[L][R] = the best state (L, R'),
+//           R' >= R, written as its keys to CK and CM at L (N + 1) + R.
+//   else:   line b, elements a = pL0 up to pL1, read from CK and CM at a (N + 1) + b
+//           and rewritten in CM with M[a][b], the best state with L <= a, R >= b.
+constexpr uint32_t SEC_NONE = 0xffffffffu;
+constexpr uint64_t KEY_NEG_INF = 0x000fffffffffffffull; // order_key(-inf)
+constexpr uint64_t KEY_POS_INF = 0xfff0000000000000ull; // order_key(+inf)
+
 template <bool SUFFIX>
-__device__ __forceinline__ void rect_best_scans(const double *Sp, const uint32_t *sec, int32_t *CM, int N, int pL0,
-                                                int pL1, int pR0, int pR1) {
-    const int n = N + 1, lane = threadIdx.x & 31;
+__device__ __forceinline__ void rect_line_scans(const uint64_t *__restrict__ Kp, uint64_t *CK, uint32_t *CM, int N,
+                                                int pL0, int pL1, int pR0, int pR1) {
+    const int n1 = N + 1, tid = threadIdx.x;
     const int n_lines = SUFFIX ? pL1 - pL0 + 1 : pR1 - pR0 + 1;
     const int len = SUFFIX ? pR1 - pR0 + 1 : pL1 - pL0 + 1;
-    const int seglen = (len + 3) >> 2;
-    for (int base = 0; base < n_lines * 4; base += ID_THREADS) { // warp-uniform trip count
-        const int t = base + (int)threadIdx.x;
-        const bool act = t < n_lines * 4;
-        const int line = t >> 2, sg = t & 3;
-        const int e0 = min(sg * seglen, len), e1 = act ? min(e0 + seglen, len) : e0;
-        auto pos_of = [&](int e) { return SUFFIX ? (pL0 + line) * n + (pR1 - e) : (pL0 + e) * n + (pR0 + line); };
-        int bi = -1;
-        uint64_t bk = 0;
-        uint32_t bs = 0xffffffffu;
-        for (int e = e0; e < e1; ++e) {
-            const int pos = pos_of(e);
-            const int id = SUFFIX ? pos : CM[pos];
-            const uint64_t kk = order_key(Sp[id]);
-            const uint32_t ss = sec[id];
-            if (bi < 0 || key_better(kk, ss, bk, bs)) {
-                bi = id;
-                bk = kk;
-                bs = ss;
-            }
+    int lg = 5;
+    while (lg > 0 && (n_lines << lg) > ID_THREADS) --lg;
+    const int G = 1 << lg, seg = (len + G - 1) >> lg;
+    const int line = tid >> lg, sg = tid & (G - 1);
+    const bool act = line < n_lines;
+    const int e0 = act ? min(sg * seg, len) : 0, e1 = act ? min(e0 + seg, len) : 0;
+    auto load = [&](int e, uint64_t &kk, uint32_t &ss, int &pos) {
+        if (SUFFIX) {
+            const int L = pL0 + line, R = pR1 - e;
+            pos = L * n1 + R;
+            const bool ok = L <= R;
+            kk = ok ? Kp[pos] : 0ull;
+            ss = ok ? state_sec(L, R, N) : SEC_NONE;
+        } else {
+            pos = (pL0 + e) * n1 + pR0 + line;
+            kk = CK[pos];
+            ss = CM[pos];
         }
-        // carry: the best of the line's earlier segments (lanes sg - 1, sg - 2, sg - 3 of this group)
-        int ci = -1;
-        uint64_t ck = 0;
-        uint32_t cs = 0xffffffffu;
-#pragma unroll
-        for (int d = 1; d <= 3; ++d) {
-            const int oi = __shfl_up_sync(0xffffffffu, bi, d);
-            const uint64_t ok = __shfl_up_sync(0xffffffffu, bk, d);
-            const uint32_t os = __shfl_up_sync(0xffffffffu, bs, d);
-            if (sg >= d && lane >= d && oi >= 0 && (ci < 0 || key_better(ok, os, ck, cs))) {
-                ci = oi;
-                ck = ok;
-                cs = os;
-            }
+    };
+    uint64_t bk = 0;
+    uint32_t bs = SEC_NONE;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+        uint64_t kk;
+        uint32_t ss;
+        int pos;
+        load(e, kk, ss, pos);
+        if (key_better(kk, ss, bk, bs)) {
+            bk = kk;
+            bs = ss;
         }
-        for (int e = e0; e < e1; ++e) {
-            const int pos = pos_of(e);
-            const int id = SUFFIX ? pos : CM[pos];
-            const uint64_t kk = order_key(Sp[id]);
-            const uint32_t ss = sec[id];
-            if (ci < 0 || key_better(kk, ss, ck, cs)) {
-                ci = id;
-                ck = kk;
-                cs = ss;
-            }
-            CM[pos] = ci;
+    }
+    for (int d = 1; d < G; d <<= 1) { // inclusive scan of the segment bests along the line
+        const uint64_t ok = __shfl_up_sync(0xffffffffu, bk, d, G);
+        const uint32_t os = __shfl_up_sync(0xffffffffu, bs, d, G);
+        if (sg >= d && key_better(ok, os, bk, bs)) {
+            bk = ok;
+            bs = os;
         }
+    }
+    uint64_t ck = __shfl_up_sync(0xffffffffu, bk, 1, G); // carry: the segments before this one
+    uint32_t cs = __shfl_up_sync(0xffffffffu, bs, 1, G);
+    if (sg == 0) {
+        ck = 0;
+        cs = SEC_NONE;
+    }
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+        uint64_t kk;
+        uint32_t ss;
+        int pos;
+        load(e, kk, ss, pos);
+        if (key_better(kk, ss, ck, cs)) {
+            ck = kk;
+            cs = ss;
+        }
+        if (SUFFIX) CK[pos] = ck;
+        CM[pos] = cs;
     }
 }
 
+// The states L <= R of the window rectangle [L0, L1] x [R0, R1], numbered without
+// gaps: first the lines L <= R0 (every R of the rectangle), wR states each, then the
+// lines R0 < L <= min(L1, R1), whose states run from R = L to R1 (one fewer each).
+struct RectStates {
+    int L0, R0, R1, wR, nA, cellsA, Lb0, m, total;
+    float inv_wR;
+    __device__ __forceinline__ void init(int l0, int l1, int r0, int r1) {
+        L0 = l0;
+        R0 = r0;
+        R1 = r1;
+        wR = r1 - r0 + 1;
+        total = 0;
+        if (l1 < l0 || r1 < r0) return;
+        nA = max(0, min(l1, r0) - l0 + 1);
+        cellsA = nA * wR;
+        Lb0 = max(l0, r0 + 1);
+        const int nB = max(0, min(l1, r1) - Lb0 + 1);
+        m = r1 - Lb0 + 1;
+        total = cellsA + nB * m - nB * (nB - 1) / 2;
+        inv_wR = 1.0f / (float)wR;
+    }
+    // state u -> (L, R).  In the first part (u + 0.5) / wR is at least 0.5 / wR away
+    // from an integer and the float quotient is within 2^-22 of it (u < 8192, wR <= 89),
+    // so its floor is exact; in the second the line j solves j (2m + 1 - j) / 2 <= u'
+    // (float root, then at most a step either way to the exact integer answer).
+    __device__ __forceinline__ void at(int u, int &L, int &R) const {
+        if (u < cellsA) {
+            const int q = (int)(((float)u + 0.5f) * inv_wR);
+            L = L0 + q;
+            R = R0 + (u - q * wR);
+            return;
+        }
+        const int v = u - cellsA, b = 2 * m + 1;
+        int j = (int)(0.5f * ((float)b - sqrtf((float)(b * b - 8 * v))));
+        j = max(j, 0);
+        while (j > 0 && j * (b - j) > 2 * v) --j;
+        while ((j + 1) * (b - j - 1) <= 2 * v) ++j;
+        L = Lb0 + j;
+        R = L + (v - j * (b - j) / 2);
+    }
+};
+
 // One CP's chain: its best price (cp_val/cp_ok) and its predecessor table (the
 // feasible states' predecessors per row, then the best final state) for the backtrack.
+// Shared memory: S_{r-1} and S_r as order keys (the scans' key column CK aliases S_r,
+// which the update writes only after the scans), the prefix sums of the current and
+// the next row, and the scans' tie-key column CM.  The next row's prefix sums and
+// leaf-travel window are loaded while the current row is processed.
 __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ Pall,
                                const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves, int k,
                                unsigned char *sm, int16_t *pred_tab, double *out_val, uint8_t *out_ok) {
-    const int N = g.n_cols, NS = (N + 1) * (N + 1);
+    const int N = g.n_cols, n1 = N + 1, NS = n1 * n1;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double *Sp = reinterpret_cast<double *>(sm);
-    double *Sn = Sp + NS;
-    int32_t *CM = reinterpret_cast<int32_t *>(Sn + NS);
-    uint32_t *sec = reinterpret_cast<uint32_t *>(CM + NS);
+    uint64_t *Kp = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *Kn = Kp + NS;
+    double *Pb = reinterpret_cast<double *>(Kn + NS); // [2][INTERDIG_PSTRIDE]
+    uint32_t *CM = reinterpret_cast<uint32_t *>(Pb + 2 * INTERDIG_PSTRIDE);
     __shared__ int kk_s[2];
+    __shared__ int4 win_s[2];
     __shared__ uint64_t wk[ID_THREADS / 32];
     __shared__ uint32_t wsec[ID_THREADS / 32];
-    __shared__ int ws[ID_THREADS / 32];
-    for (int idx = tid; idx < NS; idx += ID_THREADS) {
-        const int L = idx / (N + 1), R = idx - L * (N + 1);
-        sec[idx] = state_sec(L, R, N);
-    }
+    const double *Pk = Pall + (int64_t)k * g.n_rows * n1;
     if (wid == 0) {
         const int left = nearest_occupied(g, occupied, k, -1, lane);
         const int right = nearest_occupied(g, occupied, k, 1, lane);
         if (lane == 0) {
             kk_s[0] = left;
             kk_s[1] = right;
+            const RowWindow w = row_window(g, leaves, k, 0, left, right);
+            win_s[0] = make_int4(w.Lmin, w.Lmax, w.Rmin, w.Rmax);
         }
     }
+    for (int c = tid; c < n1; c += ID_THREADS) Pb[c] = Pk[c];
     __syncthreads();
-    // Only the states inside a row's leaf-travel window can be in a chain: the scans run
-    // over the previous row's window rectangle and the update over the current one.
-    // Every cell of a rectangle is written (-inf where L > R), and no cell outside the
-    // current and previous rectangles is read.
     int pL0 = 0, pL1 = -1, pR0 = 0, pR1 = -1; // the previous row's rectangle (none yet)
     for (int r = 0; r < g.n_rows; ++r) {
-        const RowWindow w = row_window(g, leaves, k, r, kk_s[0], kk_s[1]);
-        const int L0 = w.Lmin, L1 = w.Lmax, R0 = w.Rmin, R1 = w.Rmax;
-        const double *P = Pall + ((int64_t)k * g.n_rows + r) * (N + 1);
+        const int4 w = win_s[r & 1];
+        const double *P = Pb + (r & 1) * INTERDIG_PSTRIDE;
+        // the next row's prefix sums and window, in flight during this row
+        const bool more = r + 1 < g.n_rows;
+        const double pn = more && tid < n1 ? Pk[(int64_t)(r + 1) * n1 + tid] : 0.0;
+        int4 wn = make_int4(0, 0, 0, 0);
+        if (more && tid == ID_THREADS - 1) {
+            const RowWindow x = row_window(g, leaves, k, r + 1, kk_s[0], kk_s[1]);
+            wn = make_int4(x.Lmin, x.Lmax, x.Rmin, x.Rmax);
+        }
         const bool prev = pL0 <= pL1 && pR0 <= pR1;
         if (r > 0 && prev) {
-            // C[L][b] = best state (L, R), R >= b (suffix over R), then in place
-            // M[a][b] = best of C[L][b], L <= a (prefix over L)
-            rect_best_scans<true>(Sp, sec, CM, N, pL0, pL1, pR0, pR1);
+            rect_line_scans<true>(Kp, Kn, CM, N, pL0, pL1, pR0, pR1);
             __syncthreads();
-            rect_best_scans<false>(Sp, sec, CM, N, pL0, pL1, pR0, pR1);
+            rect_line_scans<false>(Kp, Kn, CM, N, pL0, pL1, pR0, pR1);
+            __syncthreads();
         }
-        __syncthreads();
-        const int wR = R1 - R0 + 1, cells = (L1 >= L0 && R1 >= R0) ? (L1 - L0 + 1) * wR : 0;
-        for (int t = tid; t < cells; t += ID_THREADS) {
-            const int L = L0 + t / wR, R = R0 + t % wR, idx = L * (N + 1) + R;
-            double sv = -INFINITY;
-            if (L <= R) {
-                const double v = P[R] - P[L];
-                if (r == 0) {
-                    sv = v;
-                } else if (prev && R >= pL0 && L <= pR1) {
-                    const int pred = CM[min(R, pL1) * (N + 1) + max(L, pR0)]; // M[R'][L'] clamped to the rectangle
-                    const double ps = Sp[pred];
-                    if (ps > -INFINITY) sv = ps + v;
-                    pred_tab[(int64_t)r * NS + idx] = (int16_t)pred;
+        // S_r over the rectangle's states L <= R (the states with L > R are never read)
+        RectStates rs;
+        rs.init(w.x, w.y, w.z, w.w);
+        int16_t *pt = pred_tab + (int64_t)r * NS;
+        for (int u = tid; u < rs.total; u += ID_THREADS) {
+            int L, R;
+            rs.at(u, L, R);
+            const int idx = L * n1 + R;
+            const double v = P[R] - P[L];
+            double sv = v;
+            if (r > 0) {
+                sv = -INFINITY;
+                if (prev && R >= pL0 && L <= pR1) {
+                    const uint32_t s = CM[min(R, pL1) * n1 + max(L, pR0)]; // M[R'][L'] clamped to the rectangle
+                    if (s != SEC_NONE) {
+                        const int pl = (int)(s & 1023u), pid = pl * n1 + pl + (int)(s >> 20);
+                        const uint64_t pk = Kp[pid];
+                        if (pk > KEY_NEG_INF && pk <= KEY_POS_INF) sv = key_value(pk) + v; // S_{r-1} > -inf
+                        pt[idx] = (int16_t)pid;
+                    }
                 }
             }
-            Sn[idx] = sv;
+            Kn[idx] = order_key(sv);
         }
+        if (more && tid < n1) Pb[((r + 1) & 1) * INTERDIG_PSTRIDE + tid] = pn;
+        if (more && tid == ID_THREADS - 1) win_s[(r + 1) & 1] = wn;
         __syncthreads();
-        double *t = Sp;
-        Sp = Sn;
-        Sn = t;
-        pL0 = L0;
-        pL1 = cells ? L1 : -1;
-        pR0 = R0;
-        pR1 = R1;
+        uint64_t *t = Kp;
+        Kp = Kn;
+        Kn = t;
+        pL0 = w.x;
+        pL1 = rs.total ? w.y : -1;
+        pR0 = w.z;
+        pR1 = w.w;
     }
-    // best final state
-    int bi = -1;
+    // best final state (value > -inf; value desc, then tie key)
     uint64_t bk = 0;
-    uint32_t bs = 0xffffffffu;
-    const int fwR = pR1 - pR0 + 1, fcells = (pL1 >= pL0 && pR1 >= pR0) ? (pL1 - pL0 + 1) * fwR : 0;
-    for (int t = tid; t < fcells; t += ID_THREADS) {
-        const int idx = (pL0 + t / fwR) * (N + 1) + pR0 + t % fwR;
-        const double sv = Sp[idx];
-        if (!(sv > -INFINITY)) continue;
-        const uint64_t kv = order_key(sv);
-        if (bi < 0 || key_better(kv, sec[idx], bk, bs)) {
-            bi = idx;
-            bk = kv;
-            bs = sec[idx];
+    uint32_t bs = SEC_NONE;
+    {
+        RectStates rs;
+        rs.init(pL0, pL1, pR0, pR1);
+        for (int u = tid; u < rs.total; u += ID_THREADS) {
+            int L, R;
+            rs.at(u, L, R);
+            const uint64_t kv = Kp[L * n1 + R];
+            if (!(kv > KEY_NEG_INF && kv <= KEY_POS_INF)) continue;
+            const uint32_t sv = state_sec(L, R, N);
+            if (key_better(kv, sv, bk, bs)) {
+                bk = kv;
+                bs = sv;
+            }
         }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        const int oi = __shfl_down_sync(0xffffffffu, bi, d);
         const uint64_t ok = __shfl_down_sync(0xffffffffu, bk, d);
         const uint32_t os = __shfl_down_sync(0xffffffffu, bs, d);
-        if (lane + d < 32 && oi >= 0 && (bi < 0 || key_better(ok, os, bk, bs))) {
-            bi = oi;
+        if (lane + d < 32 && key_better(ok, os, bk, bs)) {
             bk = ok;
             bs = os;
         }
     }
     if (lane == 0) {
-        ws[wid] = bi;
         wk[wid] = bk;
         wsec[wid] = bs;
     }
     __syncthreads();
     if (tid == 0) {
-        int b = -1;
         uint64_t kb = 0;
-        uint32_t sb = 0xffffffffu;
-        for (int w = 0; w < ID_THREADS / 32; ++w) {
-            const int oi = ws[w];
-            if (oi >= 0 && (b < 0 || key_better(wk[w], wsec[w], kb, sb))) {
-                b = oi;
-                kb = wk[w];
-                sb = wsec[w];
+        uint32_t sb = SEC_NONE;
+        for (int x = 0; x < ID_THREADS / 32; ++x)
+            if (key_better(wk[x], wsec[x], kb, sb)) {
+                kb = wk[x];
+                sb = wsec[x];
             }
-        }
-        out_val[k] = b >= 0 ? Sp[b] : -INFINITY;
-        out_ok[k] = b >= 0 ? 1 : 0;
-        pred_tab[(int64_t)g.n_rows * NS] = (int16_t)max(b, 0); // the final state, for the backtrack
+        const bool found = sb != SEC_NONE;
+        const int L = (int)(sb & 1023u), id = found ? L * n1 + L + (int)(sb >> 20) : 0;
+        out_val[k] = found ? key_value(kb) : -INFINITY;
+        out_ok[k] = found ? 1 : 0;
+        pred_tab[(int64_t)g.n_rows * NS] = (int16_t)id; // the final state, for the backtrack
     }
 }
 
-__global__ void __launch_bounds__(ID_THREADS)
+__global__ void __launch_bounds__(ID_THREADS, 2)
     price_cps_interdig_kernel(PricingGeom g, const double *__restrict__ Pall, const uint8_t *__restrict__ occupied,
                               const int16_t *__restrict__ leaves, double *cp_val, uint8_t *cp_ok, int16_t *pred_all,
                               const int32_t *skip) {
@@ -629,21 +702,32 @@ __global__ void __launch_bounds__(ID_THREADS)
     interdig_chain(g, Pall, occupied, leaves, k, smi, pred_all + (int64_t)k * (g.n_rows * NS + 1), cp_val, cp_ok);
 }
 
-// The best CP (price desc, smallest k on ties) and its leaves, backtracked through
-// the predecessor table its chain stored.
+// The best CP (price desc, smallest k on ties, in k order as the sequential
+// definition: the warp loads 32 CPs at a time and every lane applies the same
+// comparisons in k order) and its leaves, backtracked through the predecessor table
+// its chain stored.
 __global__ void price_pick_interdig_kernel(PricingGeom g, const uint8_t *__restrict__ occupied,
                                            const double *cp_val, const uint8_t *cp_ok, const int16_t *pred_all,
                                            int32_t *best_cp, int16_t *best_leaves, double *best_price,
                                            const int32_t *skip) {
     if (skip && *skip) return;
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     int kb = -1;
     double v = -INFINITY;
-    for (int k = 0; k < g.K; ++k) // k ascending: a strict > keeps the smallest k
-        if (!occupied[k] && cp_ok[k] && (kb < 0 || cp_val[k] > v)) {
-            v = cp_val[k];
-            kb = k;
+    for (int base = 0; base < g.K; base += 32) {
+        const int k = base + lane;
+        const bool cand = k < g.K && !occupied[k] && cp_ok[k];
+        const double x = cand ? cp_val[k] : 0.0;
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        for (int j = 0; j < 32; ++j) {
+            const double xj = __shfl_sync(0xffffffffu, x, j);
+            if (((m >> j) & 1u) && (kb < 0 || xj > v)) { // a strict > keeps the smallest k
+                v = xj;
+                kb = base + j;
+            }
         }
+    }
+    if (lane != 0) return;
     *best_cp = kb;
     *best_price = kb >= 0 ? v : -INFINITY;
     if (kb < 0) return;
