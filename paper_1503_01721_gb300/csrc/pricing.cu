@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -79,18 +81,22 @@ __device__ int nearest_occupied_seq(const PricingGeom &g, const uint8_t *occupie
 struct RowWindow {
     int Lmin, Lmax, Rmin, Rmax;
 };
+// The window narrowed by the leaves (Ln, Rn) of the occupied CP kk.
+__device__ __forceinline__ void window_clip(RowWindow &w, int k, int kk, int travel, int Ln, int Rn) {
+    const int reach = abs(k - kk) * travel;
+    w.Lmin = max(w.Lmin, Ln - reach);
+    w.Lmax = min(w.Lmax, Ln + reach);
+    w.Rmin = max(w.Rmin, Rn - reach);
+    w.Rmax = min(w.Rmax, Rn + reach);
+}
 __device__ __forceinline__ RowWindow row_window(const PricingGeom &g, const int16_t *__restrict__ leaves, int k,
                                                 int r, int kl, int kr) {
     RowWindow w{0, g.n_cols, 0, g.n_cols};
     for (int side = 0; side < 2; ++side) {
         const int kk = side ? kr : kl;
         if (kk < 0) continue;
-        const int reach = abs(k - kk) * g.travel;
-        const int Ln = leaves[((int64_t)kk * g.n_rows + r) * 2], Rn = leaves[((int64_t)kk * g.n_rows + r) * 2 + 1];
-        w.Lmin = max(w.Lmin, Ln - reach);
-        w.Lmax = min(w.Lmax, Ln + reach);
-        w.Rmin = max(w.Rmin, Rn - reach);
-        w.Rmax = min(w.Rmax, Rn + reach);
+        window_clip(w, k, kk, g.travel, leaves[((int64_t)kk * g.n_rows + r) * 2],
+                    leaves[((int64_t)kk * g.n_rows + r) * 2 + 1]);
     }
     return w;
 }
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(CP_THREADS) price_cps_batched_kernel(const Pri
 // chain).  One block per CP; every compare is an integer compare of order keys,
 // every value the float64 of the sequential definition.
 // ---------------------------------------------------------------------------
-constexpr int ID_THREADS = 512;
+constexpr int ID_THREADS = 1024;
 
 // A state's tie key (width, |L + R - n_cols|, L, each below 1024) in one word:
 // smaller is better among equal values.
@@ -429,17 +435,19 @@ __global__ void __launch_bounds__(WIN_WARPS * 32)
 }
 
 // Inclusive "best so far" scans over the previous row's window rectangle
-// [pL0, pL1] x [pR0, pR1], one pass per line with G threads per line (the largest
-// power of two up to 32 that fits every line into the block): each thread takes the
-// best of a contiguous segment of its line in scan order, the segment bests are
-// scanned across the line's G lanes by shuffles, and each thread rescans its segment
-// from the carry of the segments before it, writing every element's best so far.
-// A candidate is (order key of S_{r-1}, tie key); a state with L > R is no candidate
-// (key 0 and tie key SEC_NONE, below every state).
-//   SUFFIX: line L, elements R = pR1 down to pR0; C[L][R] = the best state (L, R'),
-//           R' >= R, written as its keys to CK and CM at L (N + 1) + R.
-//   else:   line b, elements a = pL0 up to pL1, read from CK and CM at a (N + 1) + b
-//           and rewritten in CM with M[a][b], the best state with L <= a, R >= b.
+// [pL0, pL1] x [pR0, pR1], G threads per line (the largest power of two up to 32 that
+// fits every line into the block): each thread takes the best of a contiguous segment
+// of its line in scan order, the segment bests are scanned across the line's G lanes
+// by shuffles, and each thread rescans its segment from the carry of the segments
+// before it, writing every element's best so far as its two keys (order key of
+// S_{r-1}, tie key) to CK and CM.
+//   SUFFIX: line L, elements R = pR1 down to max(L, pR0) (the states of the line);
+//           C[L][R] = the best state (L, R'), R' >= R.  The columns R < L of the
+//           rectangle get the line's best state (every state of the line has R' >= L
+//           > R), or no state (key 0, tie key SEC_NONE, below every state) if the
+//           line has none.
+//   else:   line b, elements a = pL0 up to pL1, rewritten in place with M[a][b], the
+//           best state with L <= a, R >= b.
 constexpr uint32_t SEC_NONE = 0xffffffffu;
 constexpr uint64_t KEY_NEG_INF = 0x000fffffffffffffull; // order_key(-inf)
 constexpr uint64_t KEY_POS_INF = 0xfff0000000000000ull; // order_key(+inf)
@@ -449,34 +457,24 @@ __device__ __forceinline__ void rect_line_scans(const uint64_t *__restrict__ Kp,
                                                 int pL0, int pL1, int pR0, int pR1) {
     const int n1 = N + 1, tid = threadIdx.x;
     const int n_lines = SUFFIX ? pL1 - pL0 + 1 : pR1 - pR0 + 1;
-    const int len = SUFFIX ? pR1 - pR0 + 1 : pL1 - pL0 + 1;
     int lg = 5;
     while (lg > 0 && (n_lines << lg) > ID_THREADS) --lg;
-    const int G = 1 << lg, seg = (len + G - 1) >> lg;
+    const int G = 1 << lg;
     const int line = tid >> lg, sg = tid & (G - 1);
     const bool act = line < n_lines;
-    const int e0 = act ? min(sg * seg, len) : 0, e1 = act ? min(e0 + seg, len) : 0;
-    auto load = [&](int e, uint64_t &kk, uint32_t &ss, int &pos) {
-        if (SUFFIX) {
-            const int L = pL0 + line, R = pR1 - e;
-            pos = L * n1 + R;
-            const bool ok = L <= R;
-            kk = ok ? Kp[pos] : 0ull;
-            ss = ok ? state_sec(L, R, N) : SEC_NONE;
-        } else {
-            pos = (pL0 + e) * n1 + pR0 + line;
-            kk = CK[pos];
-            ss = CM[pos];
-        }
-    };
+    const int L = pL0 + line;                      // SUFFIX: the line's L
+    const int lo = SUFFIX ? max(L, pR0) : 0;       // SUFFIX: its first state's R
+    const int len = !act ? 0 : SUFFIX ? max(0, pR1 - lo + 1) : pL1 - pL0 + 1;
+    const int seg = (len + G - 1) >> lg;
+    const int e0 = min(sg * seg, len), e1 = min(e0 + seg, len);
+    auto pos_of = [&](int e) { return SUFFIX ? L * n1 + (pR1 - e) : (pL0 + e) * n1 + pR0 + line; };
     uint64_t bk = 0;
     uint32_t bs = SEC_NONE;
 #pragma unroll 4
     for (int e = e0; e < e1; ++e) {
-        uint64_t kk;
-        uint32_t ss;
-        int pos;
-        load(e, kk, ss, pos);
+        const int pos = pos_of(e);
+        const uint64_t kk = SUFFIX ? Kp[pos] : CK[pos];
+        const uint32_t ss = SUFFIX ? state_sec(L, pR1 - e, N) : CM[pos];
         if (key_better(kk, ss, bk, bs)) {
             bk = kk;
             bs = ss;
@@ -496,17 +494,25 @@ __device__ __forceinline__ void rect_line_scans(const uint64_t *__restrict__ Kp,
         ck = 0;
         cs = SEC_NONE;
     }
+    if (SUFFIX) { // the line's best, for the columns left of its states
+        const uint64_t tk = __shfl_sync(0xffffffffu, bk, G - 1, G);
+        const uint32_t ts = __shfl_sync(0xffffffffu, bs, G - 1, G);
+        if (act)
+            for (int b = pR0 + sg; b < min(lo, pR1 + 1); b += G) {
+                CK[L * n1 + b] = tk;
+                CM[L * n1 + b] = ts;
+            }
+    }
 #pragma unroll 4
     for (int e = e0; e < e1; ++e) {
-        uint64_t kk;
-        uint32_t ss;
-        int pos;
-        load(e, kk, ss, pos);
+        const int pos = pos_of(e);
+        const uint64_t kk = SUFFIX ? Kp[pos] : CK[pos];
+        const uint32_t ss = SUFFIX ? state_sec(L, pR1 - e, N) : CM[pos];
         if (key_better(kk, ss, ck, cs)) {
             ck = kk;
             cs = ss;
         }
-        if (SUFFIX) CK[pos] = ck;
+        CK[pos] = ck;
         CM[pos] = cs;
     }
 }
@@ -555,18 +561,18 @@ struct RectStates {
 
 // One CP's chain: its best price (cp_val/cp_ok) and its predecessor table (the
 // feasible states' predecessors per row, then the best final state) for the backtrack.
-// Shared memory: S_{r-1} and S_r as order keys (the scans' key column CK aliases S_r,
-// which the update writes only after the scans), the prefix sums of the current and
-// the next row, and the scans' tie-key column CM.  The next row's prefix sums and
-// leaf-travel window are loaded while the current row is processed.
+// Shared memory: S as order keys (S_{r-1} until the scans have read it, then S_r, in
+// place), the scans' key and tie-key columns CK and CM, and the prefix sums of the
+// current and the next row.  The next row's prefix sums and leaf-travel window are
+// loaded while the current row is processed.
 __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ Pall,
                                const uint8_t *__restrict__ occupied, const int16_t *__restrict__ leaves, int k,
                                unsigned char *sm, int16_t *pred_tab, double *out_val, uint8_t *out_ok) {
     const int N = g.n_cols, n1 = N + 1, NS = n1 * n1;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    uint64_t *Kp = reinterpret_cast<uint64_t *>(sm);
-    uint64_t *Kn = Kp + NS;
-    double *Pb = reinterpret_cast<double *>(Kn + NS); // [2][INTERDIG_PSTRIDE]
+    uint64_t *Ks = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *CK = Ks + NS;
+    double *Pb = reinterpret_cast<double *>(CK + NS); // [2][INTERDIG_PSTRIDE]
     uint32_t *CM = reinterpret_cast<uint32_t *>(Pb + 2 * INTERDIG_PSTRIDE);
     __shared__ int kk_s[2];
     __shared__ int4 win_s[2];
@@ -592,19 +598,25 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
         // the next row's prefix sums and window, in flight during this row
         const bool more = r + 1 < g.n_rows;
         const double pn = more && tid < n1 ? Pk[(int64_t)(r + 1) * n1 + tid] : 0.0;
-        int4 wn = make_int4(0, 0, 0, 0);
-        if (more && tid == ID_THREADS - 1) {
-            const RowWindow x = row_window(g, leaves, k, r + 1, kk_s[0], kk_s[1]);
-            wn = make_int4(x.Lmin, x.Lmax, x.Rmin, x.Rmax);
-        }
+        // (the leaves are loaded here and used at the end of the row, so that no warp
+        // waits for them before the scans)
+        int nb[4] = {0, 0, 0, 0};
+        if (more && tid == ID_THREADS - 1)
+            for (int side = 0; side < 2; ++side)
+                if (kk_s[side] >= 0) {
+                    const int16_t *q = leaves + ((int64_t)kk_s[side] * g.n_rows + r + 1) * 2;
+                    nb[2 * side] = q[0];
+                    nb[2 * side + 1] = q[1];
+                }
         const bool prev = pL0 <= pL1 && pR0 <= pR1;
         if (r > 0 && prev) {
-            rect_line_scans<true>(Kp, Kn, CM, N, pL0, pL1, pR0, pR1);
+            rect_line_scans<true>(Ks, CK, CM, N, pL0, pL1, pR0, pR1);
             __syncthreads();
-            rect_line_scans<false>(Kp, Kn, CM, N, pL0, pL1, pR0, pR1);
+            rect_line_scans<false>(Ks, CK, CM, N, pL0, pL1, pR0, pR1);
             __syncthreads();
         }
-        // S_r over the rectangle's states L <= R (the states with L > R are never read)
+        // S_r over the rectangle's states L <= R (the states with L > R are never read),
+        // from the best compatible state of row r - 1, M[R'][L'] clamped to its rectangle
         RectStates rs;
         rs.init(w.x, w.y, w.z, w.w);
         int16_t *pt = pred_tab + (int64_t)r * NS;
@@ -617,23 +629,26 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
             if (r > 0) {
                 sv = -INFINITY;
                 if (prev && R >= pL0 && L <= pR1) {
-                    const uint32_t s = CM[min(R, pL1) * n1 + max(L, pR0)]; // M[R'][L'] clamped to the rectangle
+                    const int q = min(R, pL1) * n1 + max(L, pR0);
+                    const uint32_t s = CM[q];
+                    const uint64_t pk = CK[q];
                     if (s != SEC_NONE) {
-                        const int pl = (int)(s & 1023u), pid = pl * n1 + pl + (int)(s >> 20);
-                        const uint64_t pk = Kp[pid];
+                        const int pl = (int)(s & 1023u);
                         if (pk > KEY_NEG_INF && pk <= KEY_POS_INF) sv = key_value(pk) + v; // S_{r-1} > -inf
-                        pt[idx] = (int16_t)pid;
+                        pt[idx] = (int16_t)(pl * n1 + pl + (int)(s >> 20));
                     }
                 }
             }
-            Kn[idx] = order_key(sv);
+            Ks[idx] = order_key(sv);
         }
         if (more && tid < n1) Pb[((r + 1) & 1) * INTERDIG_PSTRIDE + tid] = pn;
-        if (more && tid == ID_THREADS - 1) win_s[(r + 1) & 1] = wn;
+        if (more && tid == ID_THREADS - 1) {
+            RowWindow x{0, N, 0, N};
+            for (int side = 0; side < 2; ++side)
+                if (kk_s[side] >= 0) window_clip(x, k, kk_s[side], g.travel, nb[2 * side], nb[2 * side + 1]);
+            win_s[(r + 1) & 1] = make_int4(x.Lmin, x.Lmax, x.Rmin, x.Rmax);
+        }
         __syncthreads();
-        uint64_t *t = Kp;
-        Kp = Kn;
-        Kn = t;
         pL0 = w.x;
         pL1 = rs.total ? w.y : -1;
         pR0 = w.z;
@@ -648,7 +663,7 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
         for (int u = tid; u < rs.total; u += ID_THREADS) {
             int L, R;
             rs.at(u, L, R);
-            const uint64_t kv = Kp[L * n1 + R];
+            const uint64_t kv = Ks[L * n1 + R];
             if (!(kv > KEY_NEG_INF && kv <= KEY_POS_INF)) continue;
             const uint32_t sv = state_sec(L, R, N);
             if (key_better(kv, sv, bk, bs)) {
@@ -687,19 +702,183 @@ __device__ void interdig_chain(const PricingGeom &g, const double *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(ID_THREADS, 2)
+// CTA i runs the chain of CP cand[i], i < *n_cand.
+__global__ void __launch_bounds__(ID_THREADS, 1)
     price_cps_interdig_kernel(PricingGeom g, const double *__restrict__ Pall, const uint8_t *__restrict__ occupied,
                               const int16_t *__restrict__ leaves, double *cp_val, uint8_t *cp_ok, int16_t *pred_all,
-                              const int32_t *skip) {
+                              const int32_t *skip, const int32_t *__restrict__ cand, const int32_t *n_cand) {
     if (skip && *skip) return;
-    const int k = blockIdx.x;
-    if (occupied[k]) {
-        if (threadIdx.x == 0) cp_ok[k] = 0;
-        return;
-    }
+    if ((int)blockIdx.x >= *n_cand) return;
+    const int k = cand[blockIdx.x];
     extern __shared__ __align__(16) unsigned char smi[];
     const int64_t NS = (int64_t)(g.n_cols + 1) * (g.n_cols + 1);
     interdig_chain(g, Pall, occupied, leaves, k, smi, pred_all + (int64_t)k * (g.n_rows * NS + 1), cp_val, cp_ok);
+}
+
+// Which CPs run the chain.  The chain's price of a CP is at most its price without
+// the interdigitation constraint, the sum over rows (in row order, float64) of each
+// row's best opening in its window: every chain term P_R - P_L is at most its row's
+// best, and a float64 sum rounded at each step is monotone in each term.  So the
+// chains run in two rounds: first the CPs with the B largest unconstrained prices
+// (B = the CTAs that run at once; all unoccupied CPs when they are no more than B),
+// then every other CP whose unconstrained price could still reach the best chain
+// price of the first round (above it, or equal with a smaller k).  The CP the pick
+// chooses over the CPs that ran is the one it chooses over all CPs.
+enum { IDC_SKIP_ROWS = 0, IDC_N1 = 1, IDC_N2 = 2, IDC_UNOCC = 3, IDC_PRUNE = 4, IDC_WORDS = 8 };
+constexpr int ID_SEL_THREADS = 1024;
+constexpr int ID_PRUNE_MAX_K = 2048; // above this the ranking is skipped: every CP runs in the first round
+
+// Counts the unoccupied CPs, clears every cp_ok and decides whether the row bests
+// (the bounds) are needed: ctl[IDC_SKIP_ROWS] also skips the row kernel when the
+// plan is done.
+__global__ void __launch_bounds__(ID_SEL_THREADS)
+    interdig_setup_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, uint8_t *cp_ok, int32_t *ctl,
+                          int32_t B, const int32_t *skip) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const bool sk = skip && *skip;
+    int c = 0;
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+        cp_ok[k] = 0;
+        c += occupied[k] ? 0 : 1;
+    }
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool prune = cnt > B && g.K <= ID_PRUNE_MAX_K;
+        ctl[IDC_SKIP_ROWS] = (sk || !prune) ? 1 : 0;
+        ctl[IDC_UNOCC] = cnt;
+        ctl[IDC_PRUNE] = prune ? 1 : 0;
+        ctl[IDC_N1] = 0;
+        ctl[IDC_N2] = 0;
+    }
+}
+
+// The first round: every unoccupied CP (no pruning), or the B best by unconstrained
+// price (order key desc, k asc; a CP with a row without any opening has no chain and
+// runs in neither round).  bound[k] keeps the unconstrained price, feasible or -inf.
+__global__ void __launch_bounds__(ID_SEL_THREADS)
+    interdig_select_kernel(PricingGeom g, const uint8_t *__restrict__ occupied, const double *__restrict__ rb_v,
+                           const uint8_t *__restrict__ rb_ok, double *bound, uint64_t *bkey, uint8_t *in1,
+                           int32_t *cand1, int32_t *ctl, int32_t B, const int32_t *skip) {
+    if (skip && *skip) return;
+    __shared__ int n1;
+    if (threadIdx.x == 0) n1 = 0;
+    __syncthreads();
+    const bool prune = ctl[IDC_PRUNE] != 0;
+    if (!prune) {
+        for (int k = threadIdx.x; k < g.K; k += blockDim.x)
+            if (!occupied[k]) cand1[atomicAdd(&n1, 1)] = k;
+        __syncthreads();
+        if (threadIdx.x == 0) ctl[IDC_N1] = n1;
+        return;
+    }
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+        uint64_t key = 0; // 0: no chain (occupied, or a row without any opening)
+        double b = -INFINITY;
+        if (!occupied[k]) {
+            double price = 0.0;
+            bool ok = true;
+            for (int r = 0; r < g.n_rows; ++r) {
+                const int64_t i = (int64_t)k * g.n_rows + r;
+                ok = ok && rb_ok[i];
+                price = price + rb_v[i];
+            }
+            if (ok) {
+                b = price;
+                // nonzero (the low bit only orders the first round, which any order keeps exact)
+                key = order_key(price) | 1ull;
+            }
+        }
+        bound[k] = b;
+        bkey[k] = key;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+        const uint64_t kk = bkey[k];
+        int rank = B;
+        if (kk) {
+            rank = 0;
+            for (int j = 0; j < g.K; ++j) {
+                const uint64_t kj = bkey[j];
+                rank += (kj > kk || (kj == kk && j < k)) ? 1 : 0;
+            }
+        }
+        in1[k] = rank < B ? 1 : 0;
+        if (rank < B) {
+            cand1[rank] = k;
+            atomicAdd(&n1, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl[IDC_N1] = n1;
+}
+
+// The second round: the CPs outside the first whose bound can still reach the first
+// round's best chain price v* (at CP k*): bound > v*, or bound == v* and k < k*; every
+// one of them when v* or the bound is not finite, or when no first-round chain exists.
+__global__ void __launch_bounds__(ID_SEL_THREADS)
+    interdig_threshold_kernel(PricingGeom g, const double *__restrict__ bound, const uint64_t *__restrict__ bkey,
+                              const uint8_t *__restrict__ in1, const double *__restrict__ cp_val,
+                              const uint8_t *__restrict__ cp_ok, const int32_t *__restrict__ cand1, int32_t *cand2,
+                              int32_t *ctl, const int32_t *skip) {
+    if (skip && *skip) return;
+    if (!ctl[IDC_PRUNE]) return;
+    __shared__ double sv[ID_SEL_THREADS / 32];
+    __shared__ int sk[ID_SEL_THREADS / 32];
+    __shared__ int n2;
+    __shared__ double vs;
+    __shared__ int ks;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n1 = ctl[IDC_N1];
+    double v = -INFINITY;
+    int kb = -1;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        const int k = cand1[i];
+        if (cp_ok[k] && (kb < 0 || cp_val[k] > v || (cp_val[k] == v && k < kb))) {
+            v = cp_val[k];
+            kb = k;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, d);
+        const int ok = __shfl_down_sync(0xffffffffu, kb, d);
+        if (lane + d < 32 && ok >= 0 && (kb < 0 || ov > v || (ov == v && ok < kb))) {
+            v = ov;
+            kb = ok;
+        }
+    }
+    if (lane == 0) {
+        sv[wid] = v;
+        sk[wid] = kb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bv = -INFINITY;
+        int bk = -1;
+        for (int w = 0; w < ID_SEL_THREADS / 32; ++w)
+            if (sk[w] >= 0 && (bk < 0 || sv[w] > bv || (sv[w] == bv && sk[w] < bk))) {
+                bv = sv[w];
+                bk = sk[w];
+            }
+        vs = bv;
+        ks = bk;
+        n2 = 0;
+    }
+    __syncthreads();
+    const double vstar = vs;
+    const int kstar = ks;
+    const bool vfin = kstar >= 0 && isfinite(vstar);
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+        if (!bkey[k] || in1[k]) continue; // no chain, or ran in the first round
+        const double b = bound[k];
+        const bool prune = vfin && isfinite(b) && (b < vstar || (b == vstar && k > kstar));
+        if (!prune) cand2[atomicAdd(&n2, 1)] = k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl[IDC_N2] = n2;
 }
 
 // The best CP (price desc, smallest k on ties, in k order as the sequential
@@ -840,6 +1019,7 @@ vmat_status pricing_attributes() {
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(price_cps_interdig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)interdig_smem(INTERDIG_MAX_COLS));
+
     });
     if (err != cudaSuccess)
         return set_error(VMAT_ECUDA, "pricing: cudaFuncSetAttribute failed: %s", cudaGetErrorString(err));
@@ -866,6 +1046,71 @@ static size_t row_best_bytes(int64_t rows) {
     return ((size_t)rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 15) & ~(size_t)15;
 }
 
+// Scratch of the interdigitation pricing, carved from one array (8-byte arrays first,
+// then 4-, 2- and 1-byte ones): per-CP chain prices, bounds and their keys, the row
+// bests, every row's prefix sums, the control words and the two rounds' CP lists,
+// the row bests' leaves, every CP's predecessor table (16-bit), the flags.
+struct InterdigScratch {
+    double *cp_val, *bound, *rb_v, *Pall;
+    uint64_t *bkey;
+    int32_t *ctl, *cand1, *cand2;
+    int16_t *rb_lr, *pred_all;
+    uint8_t *cp_ok, *rb_ok, *in1;
+    size_t bytes;
+};
+static InterdigScratch interdig_scratch(void *ws, const PricingGeom &g) {
+    InterdigScratch x{};
+    const int64_t K = g.K, rows = K * g.n_rows, NS = (int64_t)(g.n_cols + 1) * (g.n_cols + 1);
+    char *p = static_cast<char *>(ws);
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        char *q = p ? p + off : nullptr;
+        off += n;
+        return q;
+    };
+    x.cp_val = reinterpret_cast<double *>(take(K * 8));
+    x.bound = reinterpret_cast<double *>(take(K * 8));
+    x.rb_v = reinterpret_cast<double *>(take(rows * 8));
+    x.Pall = reinterpret_cast<double *>(take(rows * (g.n_cols + 1) * 8));
+    x.bkey = reinterpret_cast<uint64_t *>(take(K * 8));
+    x.ctl = reinterpret_cast<int32_t *>(take(IDC_WORDS * 4));
+    x.cand1 = reinterpret_cast<int32_t *>(take(K * 4));
+    x.cand2 = reinterpret_cast<int32_t *>(take(K * 4));
+    x.rb_lr = reinterpret_cast<int16_t *>(take(rows * 4));
+    x.pred_all = reinterpret_cast<int16_t *>(take(K * (g.n_rows * NS + 1) * 2));
+    x.cp_ok = reinterpret_cast<uint8_t *>(take(K));
+    x.rb_ok = reinterpret_cast<uint8_t *>(take(rows));
+    x.in1 = reinterpret_cast<uint8_t *>(take(K));
+    x.bytes = off + 64;
+    return x;
+}
+
+// CTAs of the chain kernel that run at once on the current device (one round),
+// queried once per device and shared-memory size.
+static vmat_status interdig_wave(size_t smem, int *B) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, size_t>, int>> known;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(VMAT_ECUDA, "interdigitation pricing: cudaGetDevice failed: %s",
+                                           cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &x : known)
+        if (x.first.first == dev && x.first.second == smem) {
+            *B = x.second;
+            return VMAT_OK;
+        }
+    int sms = 0, per = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, price_cps_interdig_kernel, ID_THREADS, smem);
+    if (e != cudaSuccess) return set_error(VMAT_ECUDA, "interdigitation pricing: occupancy query failed: %s",
+                                           cudaGetErrorString(e));
+    *B = std::max(1, sms * std::max(per, 1));
+    known.push_back({{dev, smem}, *B});
+    return VMAT_OK;
+}
+
 vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uint8_t *occupied, const int16_t *leaves,
                                  int32_t *best_cp, int16_t *best_leaves, double *best_price, void *ws,
                                  cudaStream_t s, const int32_t *skip, bool ws_has_prefix) {
@@ -876,21 +1121,37 @@ vmat_status price_apertures_impl(const vmat_mlc *mlc, const float *pi, const uin
     int16_t *rb_lr = reinterpret_cast<int16_t *>(rb_v + rows);
     uint8_t *rb_ok = reinterpret_cast<uint8_t *>(rb_lr + 2 * rows);
     if (g.interdig) {
-        // scratch: per-CP prices, then the chosen CP's predecessor table
-        double *cp_val = rb_v;
-        uint8_t *cp_ok = reinterpret_cast<uint8_t *>(cp_val + g.K);
-        double *Pall = reinterpret_cast<double *>(cp_ok + ((g.K + 15) & ~15));
-        int16_t *pred_all = reinterpret_cast<int16_t *>(Pall + (int64_t)g.K * g.n_rows * (g.n_cols + 1));
+        const InterdigScratch x = interdig_scratch(ws, g);
         const size_t sm = interdig_smem(g.n_cols);
         VMAT_TRY(pricing_attributes());
-        const int64_t rows = (int64_t)g.K * g.n_rows;
+        int B = 0;
+        VMAT_TRY(interdig_wave(sm, &B));
         window_prefix_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, 4096)), 128, 0,
-                                 s>>>(g, pi, occupied, leaves, Pall, skip);
+                                 s>>>(g, pi, occupied, leaves, x.Pall, skip);
         VMAT_LAUNCH_CHECK();
-        price_cps_interdig_kernel<<<g.K, ID_THREADS, sm, s>>>(g, Pall, occupied, leaves, cp_val, cp_ok, pred_all,
-                                                               skip);
+        interdig_setup_kernel<<<1, ID_SEL_THREADS, 0, s>>>(g, occupied, x.cp_ok, x.ctl, B, skip);
         VMAT_LAUNCH_CHECK();
-        price_pick_interdig_kernel<<<1, 32, 0, s>>>(g, occupied, cp_val, cp_ok, pred_all, best_cp, best_leaves,
+        // the unconstrained row bests (the bounds), only when the CPs exceed one round
+        price_rows_kernel<<<(unsigned)((rows + PR_WARPS - 1) / PR_WARPS), PR_WARPS * 32,
+                            PR_WARPS * row_smem_stride(g.n_cols), s>>>(g, pi, occupied, leaves, x.rb_v, x.rb_lr,
+                                                                       x.rb_ok, x.ctl + IDC_SKIP_ROWS, x.Pall);
+        VMAT_LAUNCH_CHECK();
+        interdig_select_kernel<<<1, ID_SEL_THREADS, 0, s>>>(g, occupied, x.rb_v, x.rb_ok, x.bound, x.bkey, x.in1,
+                                                            x.cand1, x.ctl, B, skip);
+        VMAT_LAUNCH_CHECK();
+        const int grid1 = g.K > ID_PRUNE_MAX_K ? g.K : std::min(g.K, B);
+        price_cps_interdig_kernel<<<grid1, ID_THREADS, sm, s>>>(g, x.Pall, occupied, leaves, x.cp_val, x.cp_ok,
+                                                                 x.pred_all, skip, x.cand1, x.ctl + IDC_N1);
+        VMAT_LAUNCH_CHECK();
+        if (g.K > grid1) {
+            interdig_threshold_kernel<<<1, ID_SEL_THREADS, 0, s>>>(g, x.bound, x.bkey, x.in1, x.cp_val, x.cp_ok,
+                                                                   x.cand1, x.cand2, x.ctl, skip);
+            VMAT_LAUNCH_CHECK();
+            price_cps_interdig_kernel<<<g.K - grid1, ID_THREADS, sm, s>>>(
+                g, x.Pall, occupied, leaves, x.cp_val, x.cp_ok, x.pred_all, skip, x.cand2, x.ctl + IDC_N2);
+            VMAT_LAUNCH_CHECK();
+        }
+        price_pick_interdig_kernel<<<1, 32, 0, s>>>(g, occupied, x.cp_val, x.cp_ok, x.pred_all, best_cp, best_leaves,
                                                     best_price, skip);
         VMAT_LAUNCH_CHECK();
         return VMAT_OK;
@@ -923,10 +1184,11 @@ size_t pricing_scratch_bytes(const vmat_mlc *mlc) {
     const size_t rows = (size_t)mlc->K * mlc->n_rows;
     size_t b = rows * (sizeof(double) + 2 * sizeof(int16_t) + 1) + 64;
     if (mlc->interdigitation) {
-        // per-CP prices, every row's prefix sums, every CP's predecessor table (16-bit)
-        const size_t ns = (size_t)(mlc->n_cols + 1) * (mlc->n_cols + 1);
-        b = std::max(b, (size_t)mlc->K * 9 + 16 + (size_t)mlc->K * mlc->n_rows * (mlc->n_cols + 1) * 8 +
-                            (size_t)mlc->K * ((size_t)mlc->n_rows * ns + 1) * 2 + 64);
+        PricingGeom g{};
+        g.K = mlc->K;
+        g.n_rows = mlc->n_rows;
+        g.n_cols = mlc->n_cols;
+        b = std::max(b, interdig_scratch(nullptr, g).bytes);
     }
     return b;
 }

@@ -88,7 +88,9 @@ def test_price_apertures_bit_exact(geom, seed, ints):
                                             ((36, 20, 20, 3, (0,)), 12, False), ((36, 20, 20, 3, (0,)), 13, True),
                                             ((40, 8, 80, 2, (0, 20)), 14, False),
                                             # 64 rows of 65 x 65 windows (no CP occupied), and the 88-column limit
-                                            ((45, 64, 64, 3, (0,)), 15, True), ((24, 16, 88, 4, (0, 12)), 16, False)])
+                                            ((45, 64, 64, 3, (0,)), 15, True), ((24, 16, 88, 4, (0, 12)), 16, False),
+                                            # more unoccupied CPs than chains that run at once: two rounds
+                                            ((400, 4, 10, 2, (0, 200)), 17, True), ((300, 6, 14, 3, (0,)), 18, False)])
 def test_price_apertures_interdigitation_bit_exact(geom, seed, ints):
     """Interdigitation (Section 2.2.2): the GPU chain DP and the oracle's give the
     same CP, the same float64 price and the same leaves."""
