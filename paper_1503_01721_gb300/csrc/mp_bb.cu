@@ -386,6 +386,8 @@ struct PState {
     double F, delta0, gg, delta;
     int t, done, stop, decided;
     int passes; // passes over DA (iterations and the Cauchy pass)
+    int stop_rel, stop_step; // the step's stopping tests, formed in parallel
+    double delta_c;          // the step's BB step size, formed in parallel
 };
 
 struct SolveSmem {
@@ -669,11 +671,12 @@ __device__ void solve_step_cta(const MPArgs &a, const SolveSmem &S, PState &ps) 
     for (int k = tid; k < n; k += MP_THREADS) {
         float yk = y[k];
         const float l = lo_of(a, k), h = hi_of(a, k);
-        double g = -ff_to_double(S.sGff[k]);
-        if (yk <= l && g > 0.0) {
+        const FF gf = S.sGff[k]; // g = -(hi + lo): its sign from a float compare (the pair's sum is not rounded to 0)
+        double g = -ff_to_double(gf);
+        if (yk <= l && gf.hi < -gf.lo) {
             yk = l;
             g = 0.0;
-        } else if (yk >= h && g < 0.0) {
+        } else if (yk >= h && gf.hi > -gf.lo) {
             yk = h;
             g = 0.0;
         }
@@ -685,45 +688,63 @@ __device__ void solve_step_cta(const MPArgs &a, const SolveSmem &S, PState &ps) 
         }
     }
     __syncthreads();
-    // warp q: 0 G.G, 1 s.s, 2 s.r, 3 r.r, 4 max |s|, 5 max |y|
-    if (wid < 6 && (wid == 0 || wid == 5 || t > 0)) {
+    // Warp 0: the four sums, eight lanes each (lanes 8q .. 8q + 7: 0 G.G, 1 s.s, 2 s.r,
+    // 3 r.r), lane j of a group over apertures j, j + 8, ... in order, then a fixed
+    // butterfly of the group: one warp's FP64 instructions serve all four.  Warp 1: the
+    // maxima |s| (lanes 0-15) and |y| (lanes 16-31) as integer maxima of the bit
+    // patterns of non-negative values (the order of their values), off the FP64 pipe.
+    // (the group's operands come through selected pointers, so that the warp does not
+    // diverge; at t = 0 the groups other than G.G read stale values, never used)
+    if (wid == 0) {
+        const int q = lane >> 3, j = lane & 7;
+        const double *xa = q == 0 ? S.sG : (q == 3 ? S.sR : S.sS);
+        const double *za = q == 2 ? S.sR : xa;
         double v = 0.0;
-        for (int k = lane; k < n; k += 32) {
-            if (wid == 0) {
-                const double g = S.sG[k];
-                v += g * g;
-            } else if (wid == 1) {
-                const double sk = S.sS[k];
-                v += sk * sk;
-            } else if (wid == 2) {
-                v += S.sS[k] * S.sR[k];
-            } else if (wid == 3) {
-                const double rk = S.sR[k];
-                v += rk * rk;
-            } else if (wid == 4) {
-                v = fmax(v, fabs(S.sS[k]));
-            } else {
-                v = fmax(v, fabs((double)y[k]));
-            }
+        for (int k = j; k < n; k += 8) v += xa[k] * za[k];
+#pragma unroll
+        for (int d = 4; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        if (j == 0) S.sRed[q] = v;
+    } else if (wid == 1) {
+        const bool ys = lane >= 16;
+        const int j = lane & 15;
+        unsigned long long m = 0;
+        if (ys) {
+            for (int k = j; k < n; k += 16) m = max(m, (unsigned long long)(__float_as_uint(y[k]) & 0x7fffffffu));
+        } else if (t > 0) {
+            for (int k = j; k < n; k += 16)
+                m = max(m, (unsigned long long)__double_as_longlong(S.sS[k]) & 0x7fffffffffffffffull);
         }
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const double o = __shfl_xor_sync(0xffffffffu, v, d);
-            v = wid < 4 ? v + o : fmax(v, o);
+        for (int d = 8; d > 0; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+        if (j == 0) S.sRed[ys ? 5 : 4] = ys ? (double)__uint_as_float((unsigned)m) : __longlong_as_double((long long)m);
+    }
+    __syncthreads();
+    // the two stopping tests and the BB step size, each by lane 0 of its own warp (their
+    // FP64 chains run side by side); thread 0 then decides in the sequential order
+    if (lane == 0 && wid < 3) {
+        const double ss = S.sRed[1], sr = S.sRed[2], rr = S.sRed[3], dy = S.sRed[4], ymax = S.sRed[5];
+        if (wid == 0) {
+            const double F = ps.F;
+            ps.stop_rel = t >= 5 && fabs(ps.F_hist[(t - 5) % 6] - F) <= a.opts.rel_tol5 * F;
+        } else if (wid == 1) {
+            ps.stop_step = t >= 1 && dy <= a.opts.step_tol * fmax(1.0, ymax);
+        } else if (t > 0) {
+            double delta;
+            if (sr <= 0.0) delta = a.opts.delta_max * ps.delta0;
+            else if (t & 1) delta = sr / rr;
+            else delta = ss / sr;
+            ps.delta_c = fmin(fmax(delta, a.opts.delta_min * ps.delta0), a.opts.delta_max * ps.delta0);
         }
-        if (lane == 0) S.sRed[wid] = v;
     }
     __syncthreads();
     if (tid == 0) {
-        const double gg = S.sRed[0], ss = S.sRed[1], sr = S.sRed[2], rr = S.sRed[3], dy = S.sRed[4],
-                     ymax = S.sRed[5];
-        const double F = ps.F;
+        const double gg = S.sRed[0];
         ps.decided = 1;
-        ps.F_hist[t % 6] = F;
-        if (t >= 5 && fabs(ps.F_hist[(t - 5) % 6] - F) <= a.opts.rel_tol5 * F) {
+        ps.F_hist[t % 6] = ps.F;
+        if (ps.stop_rel) {
             ps.done = 1;
             ps.stop = VMAT_STOP_REL;
-        } else if (t >= 1 && dy <= a.opts.step_tol * fmax(1.0, ymax)) {
+        } else if (ps.stop_step) {
             ps.done = 1;
             ps.stop = VMAT_STOP_STEP;
         } else if (t == a.opts.max_iter - 1) {
@@ -738,11 +759,7 @@ __device__ void solve_step_cta(const MPArgs &a, const SolveSmem &S, PState &ps) 
                 ps.decided = 2; // the first step is the Cauchy step (needs DA G)
             }
         } else {
-            double delta;
-            if (sr <= 0.0) delta = a.opts.delta_max * ps.delta0;
-            else if (t & 1) delta = sr / rr;
-            else delta = ss / sr;
-            ps.delta = fmin(fmax(delta, a.opts.delta_min * ps.delta0), a.opts.delta_max * ps.delta0);
+            ps.delta = ps.delta_c;
             ps.decided = 0;
         }
     }
