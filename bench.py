@@ -61,7 +61,6 @@ INDEX16_CFGS = (12, 13, 14)
 # kernels on a quarter of the CPs) over their algorithmic bytes; a configuration without such a
 # capture reports null.
 WINDOWED_TRAFFIC_RATIO = {("f32", 5): 0.9988, ("f32", 9): 1.0010, ("f32", 11): 1.0009}
-TRAFFIC_RATIO = {("f32", 11): 1.0103}
 TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
                  ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
                  ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
