@@ -174,19 +174,6 @@ __device__ __forceinline__ bool row_needed(const RowMask &m, int64_t r) {
     return true;
 }
 
-// Row of list entry i of a windowed pass (mask.woff set): the segment q with woff[q] <= i <
-// woff[q + 1] (binary search; empty segments are never found), then column win[q].x +
-// (i - woff[q]) of that segment.
-__device__ __forceinline__ int64_t window_row(const RowMask &m, int64_t i) {
-    int lo = 0, hi = m.nseg; // woff[lo] <= i < woff[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(m.woff + mid) <= i) lo = mid;
-        else hi = mid;
-    }
-    return (int64_t)lo * m.n_cols + __ldg(m.win + lo).x + (i - __ldg(m.woff + lo));
-}
-
 // Exclusive scan of the windows' lengths (win[q].y - win[q].x) into woff (nseg + 1
 // entries, one block); skip as for the pricing kernels.
 vmat_status window_offsets(const short2 *win, int32_t nseg, int32_t *woff, const int32_t *skip, cudaStream_t s);

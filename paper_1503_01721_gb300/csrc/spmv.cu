@@ -514,6 +514,40 @@ __device__ __forceinline__ float warp_row_sum_z(const int64_t *__restrict__ rowp
     return sum;
 }
 
+// The rows of a warp-row launch, passed to f in order.  Without a list: rows
+// warp0, warp0 + stride, ... that the mask keeps.  With the window list (mask.woff):
+// list items in runs of WIN_RUN consecutive items, run warp0, warp0 + stride, ...; the
+// items of a run are consecutive rows of one window segment or of the next ones, so
+// the segment is searched once per run and then followed item by item.
+constexpr int WIN_RUN = 4;
+template <typename F> __device__ __forceinline__ void for_rows(const RowParams &p, int64_t warp0, F &&f) {
+    if (!p.mask.woff) {
+        for (int64_t r = warp0; r < p.n_rows; r += p.stride)
+            if (row_needed(p.mask, r)) f(r);
+        return;
+    }
+    const int64_t n_items = (int64_t)__ldg(p.mask.woff + p.mask.nseg);
+    for (int64_t c0 = warp0 * WIN_RUN; c0 < n_items; c0 += p.stride * WIN_RUN) {
+        int lo = 0, hi = p.mask.nseg; // woff[lo] <= c0 < woff[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(p.mask.woff + mid) <= c0) lo = mid;
+            else hi = mid;
+        }
+        int64_t seg_end = __ldg(p.mask.woff + lo + 1);
+        int64_t r = (int64_t)lo * p.mask.n_cols + __ldg(p.mask.win + lo).x + (c0 - __ldg(p.mask.woff + lo));
+        const int64_t c1 = min(c0 + WIN_RUN, n_items);
+        for (int64_t i = c0; i < c1; ++i, ++r) {
+            while (i == seg_end) { // the next segment with a row (empty windows have none)
+                ++lo;
+                seg_end = __ldg(p.mask.woff + lo + 1);
+                r = (int64_t)lo * p.mask.n_cols + __ldg(p.mask.win + lo).x;
+            }
+            f(r);
+        }
+    }
+}
+
 template <int THREADS, int UNROLL, typename VT>
 __global__ void __launch_bounds__(THREADS) spmv_warp_row_z_kernel(RowParams p) {
     if (p.skip && *p.skip) return;
@@ -521,16 +555,13 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_z_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
-    for (int64_t i = warp0; i < n_items; i += p.stride) {
-        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
-        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
+    for_rows(p, warp0, [&](int64_t r) {
         float sum = warp_row_sum_z<UNROLL, VT>(p.rowptr, p.cptr, p.cbase, p.col16, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
             p.y[p.row_ids ? p.row_ids[r] : r] = sum;
         }
-    }
+    });
 }
 
 template <int THREADS, int UNROLL, typename VT>
@@ -540,16 +571,13 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_c_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
-    for (int64_t i = warp0; i < n_items; i += p.stride) {
-        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
-        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
+    for_rows(p, warp0, [&](int64_t r) {
         float sum = warp_row_sum_c<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
             p.y[p.row_ids ? p.row_ids[r] : r] = sum;
         }
-    }
+    });
 }
 
 template <int THREADS, int UNROLL, typename VT>
@@ -559,16 +587,13 @@ __global__ void __launch_bounds__(THREADS) spmv_warp_row_kernel(RowParams p) {
     const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
     if (warp0 >= p.stride) return; // warp-uniform
     const uint64_t pol = l2_evict_first_policy();
-    const int64_t n_items = p.mask.woff ? (int64_t)__ldg(p.mask.woff + p.mask.nseg) : p.n_rows;
-    for (int64_t i = warp0; i < n_items; i += p.stride) {
-        const int64_t r = p.mask.woff ? window_row(p.mask, i) : i;
-        if (!p.mask.woff && !row_needed(p.mask, r)) continue;
+    for_rows(p, warp0, [&](int64_t r) {
         float sum = warp_row_sum<UNROLL, VT>(p.rowptr, p.col, p.val, p.x, r, lane, pol);
         if (lane == 0) {
             if (p.row_scale) sum *= p.row_scale[r];
             p.y[p.row_ids ? p.row_ids[r] : r] = sum;
         }
-    }
+    });
 }
 
 // Several plans' matrices in one launch: global row g belongs to plan p with
