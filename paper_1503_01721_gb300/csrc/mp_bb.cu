@@ -373,6 +373,37 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned n_cta, unsign
     return ok_s != 0;
 }
 
+// Grid barrier of a solve whose CTAs stay with it from start to end: one arrival
+// counter that only grows (zeroed by the init kernel before the launch); the e-th
+// barrier (e = 1, 2, ...) ends when the counter reaches e n_cta.  No CTA reads a word
+// before it arrives and no CTA resets one after the last arrival, so the barrier ends
+// one round trip after the last arrival.  Gives up after WAIT_LIMIT_CYCLES; returns
+// false then.
+__device__ bool grid_sync_count(unsigned *count, unsigned target) {
+    __shared__ int ok_c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 1;
+        const long long t0 = clock64();
+        while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        ok_c = ok;
+    }
+    __syncthreads();
+    return ok_c != 0;
+}
+
 // Barrier of the whole batched grid.  The last CTA to arrive records the batch
 // epoch (gctl[3]) and the set of problems still iterating (gctl[4..5]) before it
 // releases the others: the CTA split that follows reads only these words, which
@@ -896,6 +927,14 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) abort_s = 0;
     __syncthreads();
+    // the single-problem solve (no epochs) keeps its CTAs: its barriers count arrivals
+    // on one growing counter; the elastic solver's use the counter and generation pair
+    unsigned bar_e = 0;
+    auto sync_grid = [&](bool snap) -> bool {
+        if (!epoch_src) return grid_sync_count(a.bar_count, ++bar_e * n_cta);
+        return snap ? grid_sync(a.bar_count, a.bar_gen, n_cta, a.epoch_snap, epoch_src)
+                    : grid_sync(a.bar_count, a.bar_gen, n_cta);
+    };
     float gacc[NMAX];
     FF *part = reinterpret_cast<FF *>(a.part);
     FF *cpart = reinterpret_cast<FF *>(a.cpart);
@@ -920,8 +959,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             pb[(size_t)k * a.pstride + cta] = sum;
         }
         if (tid == 0) pb[(size_t)n * a.pstride + cta] = fb;
-        if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta, epoch_src ? a.epoch_snap : nullptr, epoch_src))
-            return LOOP_ABORT;
+        if (abort_s || !sync_grid(true)) return LOOP_ABORT;
         // ---- every CTA reduces every column itself: warp w takes columns w, w + MP_NW, ...,
         // CB at a time with eight loads per column in flight per lane (every load of the group
         // issued before the first add; CB grows with NMAX, whose kernels have fewer CTAs per SM
@@ -977,7 +1015,7 @@ __device__ int solve_loop(const MPArgs &a, const SolveSmem &S, WarpPipe &P, PSta
             if (!c_ok && lane == 0) atomicOr(&abort_s, 1);
             const FF cb = block_ff(FF{cs, -cc}, shff);
             if (tid == 0) cpart[cta] = cb;
-            if (abort_s || !grid_sync(a.bar_count, a.bar_gen, n_cta)) return LOOP_ABORT;
+            if (abort_s || !sync_grid(false)) return LOOP_ABORT;
             if (wid == 0) {
                 FF v{0.f, 0.f};
                 for (unsigned b0 = lane; b0 < n_cta; b0 += 32 * 8) {
