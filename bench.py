@@ -71,6 +71,12 @@ SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
 
 
+def vox_grid(case):
+    """(nx, ny, nz) of a case's voxel grid: CSR(D^T) columns in brick order."""
+    g = case.geom
+    return (g.nx, g.ny, g.nz)
+
+
 def dataclasses_asdict(x):
     import dataclasses
     return None if x is None else dataclasses.asdict(x)
@@ -414,7 +420,7 @@ def precision_form(dev, steps=3, warmup=1):
     res = {}
     for dt in ("f32", "bf16", "fp8"):
         h = api.ddc_load_coo(case.V, case.J, *coo)
-        api.ddc_build(h, dt, autotune=True, refine=dt != "f32")
+        api.ddc_build(h, dt, autotune=True, refine=dt != "f32", vox_grid=vox_grid(case))
         cps = torch.empty(n_ap, dtype=torch.int32)
         lv = torch.empty(n_ap * case.mlc.n_rows * 2, dtype=torch.int16)
         y = torch.empty(n_ap, dtype=torch.float32)
@@ -438,7 +444,7 @@ def precision_form(dev, steps=3, warmup=1):
                    "pp1_spmv_gbs": round(sum(x["pp1_spmv_bytes"] for x in sts) / sum(x["pp1_spmv_ms"] for x in sts)
                                          / 1e6, 1),
                    "t_refine_ms": round(st["t_refine_ms"], 3), "F_before_refine": st["F_before_refine"],
-                   "refine_bb_iters": st["refine_bb_iters"], "cfg_Dt": int(info["cfg_Dt"]),
+                   "refine_bb_iters": st["refine_bb_iters"], "cfg_Dt": int(st["pp1_spmv_cfg"]),
                    "dose_err": sampled_dose_error(case, cps.numpy(), lv.numpy(), y.numpy(), dose.cpu().numpy(),
                                                   int(st["n_apertures"]))}
     f32 = res["f32"]
@@ -480,7 +486,9 @@ def run_ours(args, rank, world, local):
 
     # resident DDC
     h = api.ddc_load_coo(case.V, case.J, vox_h, blt_h, val_h)
-    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0, index16=args.index16)
+    grid = vox_grid(case) if args.vox_order == "brick" else None
+    api.ddc_build(h, args.dtype, tile_cfg=args.tile_cfg, autotune=args.tile_cfg < 0, index16=args.index16,
+                  vox_grid=grid)
     info = api.ddc_info(h)
     log(f"[rank {rank}] build {info['build_ms']:.1f} ms, active voxels {info['n_active_vox']}")
 
@@ -522,9 +530,9 @@ def run_ours(args, rank, world, local):
     spmv_bytes = sum(s["pp1_spmv_bytes"] for s in stats_all)
     peaks = roofline.measured_peaks()
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    cfg_dt = int(info["cfg_Dt"])
+    cfg_dt = int(stats_all[-1]["pp1_spmv_cfg"])  # the windowed passes' configuration
     kname = SPMV_KERNELS.get(cfg_dt, f"spmv configuration {cfg_dt}") + \
-        (" + spmv_fixup" if info["tile_nnz_Dt"] else "") + " (beamlet price D^T g over the unoccupied CPs)"
+        (" + spmv_fixup" if cfg_dt < 4 else "") + " (beamlet price D^T g over the unoccupied CPs)"
     bytes_launch = spmv_bytes / max(spmv_n, 1)
     ratio = WINDOWED_TRAFFIC_RATIO.get((args.dtype, cfg_dt))
     roof = {"bound": "hbm", "kernel": kname,
@@ -592,8 +600,8 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t_b = time.perf_counter()
         # the SpMV configurations the autotuner chose for the resident handle (tuned once per machine)
-        api.ddc_build(h2, args.dtype, tile_cfg=int(info["cfg_D"]), tile_cfg_Dt=int(info["cfg_Dt"]),
-                      index16=args.index16)
+        api.ddc_build(h2, args.dtype, tile_cfg=int(info["cfg_D"]), tile_cfg_Dt=cfg_dt,
+                      index16=args.index16, vox_grid=grid)
         torch.cuda.synchronize()
         t_c = time.perf_counter()
         F2, st2 = api.cg_plan(h2, case.mlc, vox, n_ap, cps_out=cps, leaves_out=lv, y_out=y, dose_out=dose_h)
@@ -642,6 +650,7 @@ def run_ours(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else args.dtype, "data": "synthetic",
             "config": {"workload": f"{args.workload} {DESCS[args.workload]}", "V": case.V, "J": case.J, "nnz": case.nnz,
                        "n_active_vox": info["n_active_vox"], "n_apertures": n_ap, "storage": args.dtype,
+                       "dt_column_order": "4x4x2 voxel bricks" if info["vox_brick"] else "voxel",
                        "interdigitation": bool(args.interdig),
                        "machine": dataclasses_asdict(case.mlc.machine),
                        "l2": "inputs larger than L2 (CSR D + D^T %.1f GB)" % ((info["bytes_D"] + info["bytes_Dt"]) / 1e9),
@@ -679,21 +688,24 @@ def run_spmv_only(args):
     case = synth.make_case(args.workload, seed=0, cache=False)
     d = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
     coo = (d(case.vox, torch.int32), d(case.blt, torch.int32), d(case.val, torch.float32))
+    grid = vox_grid(case) if args.vox_order == "brick" else None
     g = torch.rand(case.V, device="cuda")
     x = torch.rand(case.J, device="cuda")
     pi = torch.empty(case.J, device="cuda")
     dd = torch.empty(case.V, device="cuda")
-    out = {"mode": "spmv", "workload": args.workload, "nnz": case.nnz, "dtype": args.dtype, "configs": {}}
+    out = {"mode": "spmv", "vox_order": args.vox_order, "workload": args.workload, "nnz": case.nnz, "dtype": args.dtype, "configs": {}}
     from paper_1503_01721_gb300 import _lib
     for cfg in (range(api.spmv_config_count()) if args.sweep else [args.tile_cfg]):
         z = cfg in INDEX16_CFGS
         try:
-            ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=z or args.index16)
+            ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=z or args.index16,
+                          vox_grid=grid)
         except _lib.VmatError:
             if not z:
                 raise
             try:  # CSR(D) without a 16-bit index: time D^T g alone
-                ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=True, build_D=False)
+                ddc = api.Ddc(case.V, case.J, *coo, dtype=args.dtype, tile_cfg=cfg, index16=True, build_D=False,
+                              vox_grid=grid)
             except _lib.VmatError as e:
                 out["configs"][cfg] = {"unavailable": str(e)}
                 continue
@@ -802,7 +814,7 @@ def batch_measure(workload, dtype, steps, warmup):
     for sp in specs:
         c = synth.make_plan_case(sp)
         h = api.ddc_load_coo(c.V, c.J, torch.from_numpy(c.vox), torch.from_numpy(c.blt), torch.from_numpy(c.val))
-        api.ddc_build(h, dtype)
+        api.ddc_build(h, dtype, vox_grid=vox_grid(c))
         vox = api.VoxelParams.from_numpy(c.structs)
         plans.append((h, c.mlc, vox, sp.n_apertures))
         keep.append(c.mlc)
@@ -873,7 +885,8 @@ def run_truncation(args):
     ddcs = {}
     for tag, c in (("full", full), ("trunc", tr)):
         ddcs[tag] = api.Ddc(c.V, c.J, dev(c.vox, torch.int32), dev(c.blt, torch.int32), dev(c.val, torch.float32),
-                            dtype=args.dtype, autotune=True)
+                            dtype=args.dtype, autotune=True,
+                            vox_grid=vox_grid(c) if args.vox_order == "brick" else None)
     vox = api.VoxelParams.from_numpy(full.structs)
     out = {"mode": "truncation", "workload": args.workload, "radius_vox": radius, "dtype": args.dtype,
            "nnz_full": full.nnz, "nnz_trunc": tr.nnz, "nnz_ratio": round(tr.nnz / full.nnz, 4)}
@@ -963,6 +976,8 @@ def main():
                          "plan evaluated on the full matrix")
     ap.add_argument("--sweep", action="store_true", help="spmv mode: time every SpMV configuration")
     ap.add_argument("--tile-cfg", type=int, default=-1, help="SpMV configuration (-1 = library default)")
+    ap.add_argument("--vox-order", default="brick", choices=["brick", "voxel"],
+                    help="column order of CSR(D^T): 4x4x2 voxel bricks (default) or the grid's voxel order")
     ap.add_argument("--interdig", action="store_true", help="plan mode: price with the interdigitation constraint")
     ap.add_argument("--index16", action="store_true",
                     help="also build the 16-bit column index (the autotuner then times configurations 12-14)")

@@ -109,6 +109,16 @@ typedef struct {
     int32_t refine_f32; /* BF16 / FP8 builds: nonzero keeps CSR(D)'s values in FP32 as well (4 more
                            bytes per nonzero), and cg_plan ends with the FP32 refinement described
                            there.  Ignored for F32 builds. */
+    int32_t vox_grid[3]; /* {nx, ny, nz} of the voxel grid when voxel i = (z ny + y) nx + x, else all 0.
+                            Given, CSR(D^T) numbers its columns in brick order: bricks of 4 x 4 x 2
+                            voxels (32 voxels, the 128 bytes of one cache line of g), bricks in x-fastest
+                            order, the grid padded up to whole bricks.  A beamlet's 32 consecutive
+                            entries then touch about half as many lines of g as in grid order, which
+                            the gathers of D^T g pay for (Eq. 3).  beamlet_price and
+                            beamlet_price_windowed still take and return vectors in voxel order: they
+                            reorder g on the stream first (stream-ordered scratch of 4 bytes per
+                            padded voxel); cg_plan and batches write g in brick order directly.
+                            nx ny nz must equal V (VMAT_EINVAL otherwise). */
 } vmat_build_opts;
 
 /* Master-problem (Eq. 6-10) options.  Stopping rules of Section 2.1:
@@ -150,6 +160,7 @@ typedef struct {
     int32_t index16_D, index16_Dt;   /* 1: that CSR holds the 16-bit column index */
     int64_t bytes16_D, bytes16_Dt;   /* device bytes of the 16-bit index (offsets, bases, chunk pointers) */
     int32_t refine_f32;              /* 1: CSR(D) also holds FP32 values (build option refine_f32) */
+    int32_t vox_brick;               /* 1: CSR(D^T) columns are in brick order (build option vox_grid) */
 } vmat_ddc_info;
 
 /* Per-phase device times of cg_plan, named as the paper's Table 2 phases. */
@@ -177,6 +188,9 @@ typedef struct {
                                 per pass, each 32-voxel tile in the solve reads its 128-byte label
                                 head and its ceil(n/4) four-aperture groups (512 bytes each) and
                                 writes (or reads) its 32 doses */
+    int32_t pp1_spmv_cfg;    /* SpMV configuration of the windowed D^T g passes: on an autotuned handle
+                                the fastest on a pass over half of every MLC row (timed once per
+                                handle and MLC shape), else the handle's CSR(D^T) configuration */
 } vmat_plan_stats;
 
 /* ---- DDC matrix ---------------------------------------------------------- */

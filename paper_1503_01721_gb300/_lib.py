@@ -36,7 +36,7 @@ class Voxels(ctypes.Structure):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("dtype", c_i32), ("build_D", c_i32), ("build_Dt", c_i32), ("tile_cfg", c_i32),
                 ("autotune", c_i32), ("keep_coo", c_i32), ("index16", c_i32), ("tile_cfg_Dt", c_i32),
-                ("refine_f32", c_i32)]
+                ("refine_f32", c_i32), ("vox_grid", c_i32 * 3)]
 
 
 class BBOpts(ctypes.Structure):
@@ -53,7 +53,7 @@ class DdcInfo(ctypes.Structure):
                 ("built_D", c_i32), ("built_Dt", c_i32), ("tile_nnz_D", c_i32), ("tile_nnz_Dt", c_i32),
                 ("bytes_D", c_i64), ("bytes_Dt", c_i64), ("build_ms", c_f64), ("cfg_D", c_i32), ("cfg_Dt", c_i32),
                 ("index16_D", c_i32), ("index16_Dt", c_i32), ("bytes16_D", c_i64), ("bytes16_Dt", c_i64),
-                ("refine_f32", c_i32)]
+                ("refine_f32", c_i32), ("vox_brick", c_i32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -62,7 +62,7 @@ class PlanStats(ctypes.Structure):
                 ("pp1_spmv_bytes", c_f64), ("other_spmv_bytes", c_f64), ("n_apertures", c_i32),
                 ("bb_iters_total", c_i32), ("stop_reason", c_i32), ("kernel_launches", c_i64),
                 ("pp1_full_bytes", c_f64), ("refined", c_i32), ("refine_bb_iters", c_i32), ("t_refine_ms", c_f64),
-                ("F_before_refine", c_f64), ("mp_bytes", c_f64)]
+                ("F_before_refine", c_f64), ("mp_bytes", c_f64), ("pp1_spmv_cfg", c_i32)]
 
 
 class PlanDesc(ctypes.Structure):

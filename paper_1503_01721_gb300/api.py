@@ -115,12 +115,14 @@ def ddc_load_coo(V: int, J: int, vox: torch.Tensor, blt: torch.Tensor, val: torc
 
 def ddc_build(h: int, dtype: str = "f32", build_D: bool = True, build_Dt: bool = True, tile_cfg: int = -1,
               autotune: bool = False, keep_coo: bool = False, stream=None, index16: bool = False,
-              tile_cfg_Dt: int = -1, refine: bool = False) -> None:
+              tile_cfg_Dt: int = -1, refine: bool = False, vox_grid=None) -> None:
     """Build CSR(D) / CSR(D^T); index16 also stores 16-bit chunk-relative column indices where they fit.
     tile_cfg sets the SpMV configuration of CSR(D) (and of CSR(D^T) unless tile_cfg_Dt >= 0).
-    refine (BF16 / FP8): keep CSR(D)'s FP32 values too, for cg_plan's FP32 refinement."""
+    refine (BF16 / FP8): keep CSR(D)'s FP32 values too, for cg_plan's FP32 refinement.
+    vox_grid (nx, ny, nz), voxel i = (z ny + y) nx + x: CSR(D^T) columns in 4x4x2 brick order."""
+    grid = (0, 0, 0) if vox_grid is None else tuple(int(v) for v in vox_grid)
     o = _lib.BuildOpts(_lib.DTYPES[dtype], int(build_D), int(build_Dt), int(tile_cfg), int(autotune), int(keep_coo),
-                       int(index16), int(tile_cfg_Dt), int(refine))
+                       int(index16), int(tile_cfg_Dt), int(refine), (ctypes.c_int32 * 3)(*grid))
     check("ddc_build", _lib.load().ddc_build(ctypes.c_void_p(h), ctypes.byref(o), _stream(stream)))
 
 
@@ -345,12 +347,12 @@ class Ddc:
     """Owning wrapper of a DDC handle (frees it when garbage-collected)."""
 
     def __init__(self, V, J, vox, blt, val, dtype="f32", build_D=True, build_Dt=True, tile_cfg=-1,
-                 autotune=False, stream=None, index16=False, tile_cfg_Dt=-1, refine=False):
+                 autotune=False, stream=None, index16=False, tile_cfg_Dt=-1, refine=False, vox_grid=None):
         self.V, self.J = int(V), int(J)
         self.h = ddc_load_coo(V, J, vox, blt, val, stream)
         try:
             ddc_build(self.h, dtype, build_D, build_Dt, tile_cfg, autotune, False, stream, index16, tile_cfg_Dt,
-                      refine)
+                      refine, vox_grid)
         except Exception:
             ddc_free(self.h)
             self.h = None

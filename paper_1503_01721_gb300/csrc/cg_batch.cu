@@ -267,7 +267,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         p.n_wtiles = ((int64_t)std::max(p.NA, 1) + 31) / 32;
         p.wstride = mp_wtile_stride(nap);
         VMAT_TRY(b.get(&p.z_c, std::max(p.NA, 1)));
-        VMAT_TRY(b.get(&p.g_full, p.V));
+        VMAT_TRY(b.get(&p.g_full, g_positions(*p.h))); // in CSR(D^T)'s column order
         VMAT_TRY(b.get(&p.pi, p.J));
         VMAT_TRY(b.get(&p.DA, (size_t)p.n_wtiles * p.wstride));
         VMAT_TRY(b.get(&p.y, nap));
@@ -305,7 +305,7 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         p.ctl = b.d_ctl + (size_t)i * CTL_N;
         // columns not yet generated must read as 0 (later runs overwrite only columns they generate)
         VMAT_CUDA(cudaMemsetAsync(p.DA, 0, (size_t)p.n_wtiles * p.wstride * 4, s));
-        VMAT_CUDA(cudaMemsetAsync(p.g_full, 0, (size_t)p.V * 4, s));
+        VMAT_CUDA(cudaMemsetAsync(p.g_full, 0, (size_t)g_positions(*p.h) * 4, s));
         VMAT_CUDA(cudaMemsetAsync(p.obj_ws, 0, 64, s));
         batch_fill_u8<<<std::max(1, (p.K + 255) / 256), 256, 0, s>>>(p.active, p.K, 1);
         VMAT_LAUNCH_CHECK();
@@ -369,7 +369,8 @@ static vmat_status make_batch(Batch &b, int32_t n_plans, const vmat_plan_desc *p
         da[i] = DaPlan{h.D.rowptr, h.D.col, h.D.val, fp8 ? h.scale : nullptr, tab_ok ? h.cp_tab : nullptr, p.K, p.NR,
                        p.mlc.n_cols, p.cps,
                        p.best_leaves, p.DA, p.wstride, p.ctl};
-        obj[i] = ObjPlan{p.z_c, h.act_vox, p.vox.struct_id, p.vox.T, p.vox.w_over, p.vox.w_under, p.g_full, p.ctl};
+        obj[i] = ObjPlan{p.z_c, h.act_vox, p.vox.struct_id, p.vox.T, p.vox.w_over, p.vox.w_under, p.g_full, p.ctl,
+                         h.act_gpos};
         com[i] = CommitPlan{p.NR, p.best_cp, p.best_price, p.best_leaves, p.occupied, p.active, p.leaves_all,
                             p.leaves_seq, p.cps, p.y, p.ctl};
         rows_off[i + 1] = rows_off[i] + h.Dt.n_rows;

@@ -144,7 +144,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     double *best_price, *F_dev, *F0;
     void *obj_ws, *pr_ws;
     VMAT_TRY(ar.get(&z_c, std::max(NA, 1)));
-    VMAT_TRY(ar.get(&g_full, V));
+    VMAT_TRY(ar.get(&g_full, g_positions(h))); // in CSR(D^T)'s column order
     VMAT_TRY(ar.get(&pi, J));
     VMAT_TRY(ar.get(&DA, (size_t)n_wtiles * wstride));
     VMAT_TRY(ar.get(&y, nap_max));
@@ -210,7 +210,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_CUDA(cudaMemsetAsync(z_c, 0, (size_t)std::max(NA, 1) * 4, s));
     // columns not yet generated (and voxel slots past the last one) must read as 0
     VMAT_CUDA(cudaMemsetAsync(DA, 0, (size_t)n_wtiles * wstride * 4, s));
-    VMAT_CUDA(cudaMemsetAsync(g_full, 0, (size_t)V * 4, s));
+    VMAT_CUDA(cudaMemsetAsync(g_full, 0, (size_t)g_positions(h) * 4, s));
     VMAT_CUDA(cudaMemsetAsync(occupied, 0, K, s));
     VMAT_CUDA(cudaMemsetAsync(leaves_all, 0, (size_t)K * NR * 4, s));
     VMAT_CUDA(cudaMemsetAsync(obj_ws, 0, 64, s));
@@ -238,7 +238,12 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     VMAT_LAUNCH_CHECK();
     std::vector<int64_t> cpo(K + 1), cco(K + 1, 0); // nonzeros and 16-bit-index chunks before each CP
     VMAT_CUDA(cudaMemcpyAsync(cpo.data(), cpo_dev, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
-    const bool z_dt = spmv_config_index16(h.Dt.cfg);
+    // the windowed passes' SpMV configuration (autotuned handles: timed once per MLC shape)
+    int dt_cfg = h.Dt.cfg;
+    VMAT_TRY(ddc_window_config(h, mlc->n_cols, K * NR, s, &dt_cfg));
+    CsrMat Dt_win = h.Dt;
+    Dt_win.cfg = dt_cfg;
+    const bool z_dt = spmv_config_index16(dt_cfg);
     if (z_dt) {
         VMAT_CUDA(cudaStreamSynchronize(s)); // cpo_dev is reused
         cp_offsets<<<std::max(1, (K + 256) / 256), 256, 0, s>>>(h.Dt.cptr, K, bpc, cpo_dev);
@@ -289,13 +294,14 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         // ---- PP1
         tm.mark(PH_PP1);
         if (NA > 0)
-            VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s, ctl));
+            VMAT_TRY(objective_impl_ws(NA, z_c, h.act_vox, vox, nullptr, g_full, nullptr, 0.0, obj_ws, s, ctl,
+                                       h.act_gpos));
         // prices only where pricing reads them: the columns of each row's window
         VMAT_TRY(price_windows(pg, occupied, leaves_all, win, h.Dt.rowptr, z_dt ? h.Dt.cptr : nullptr,
                                t < nap_max ? wcount + 3 * t : nullptr, ctl, s));
         VMAT_TRY(window_offsets(win, K * NR, woff, ctl, s));
         tm.mark(PH_SPMV);
-        VMAT_TRY(spmv_run(h, h.Dt, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr,
+        VMAT_TRY(spmv_run(h, Dt_win, g_full, pi, h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr,
                           RowMask{nullptr, win, bpc, mlc->n_cols, woff, K * NR}, s, ctl));
         ++spmv_launches;
         // ---- PP2, and the commit (or the stop) on the device
@@ -410,13 +416,13 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
             double b = 4.0 * V;
             for (int kk = 0; kk < K; ++kk)
                 if (!occ[kk])
-                    b += csr_pass_bytes(h.Dt.cfg, vb, (double)(cpo[kk + 1] - cpo[kk]), (double)bpc,
+                    b += csr_pass_bytes(dt_cfg, vb, (double)(cpo[kk + 1] - cpo[kk]), (double)bpc,
                                         (double)(cco[kk + 1] - cco[kk])) +
                          (4.0 + fp8_row) * bpc;
             pp1_full += b;
             if (t < nap_max) {
                 const double rows = (double)wc[3 * t], nnz = (double)wc[3 * t + 1], ch = (double)wc[3 * t + 2];
-                pp1_bytes += 4.0 * V + 4.0 * K * NR + csr_pass_bytes(h.Dt.cfg, vb, nnz, rows, ch) +
+                pp1_bytes += 4.0 * V + 4.0 * K * NR + csr_pass_bytes(dt_cfg, vb, nnz, rows, ch) +
                              (4.0 + fp8_row) * rows;
             }
             if (t < n_ap) occ[cps_host[t]] = 1;
@@ -469,6 +475,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
         stats->t_refine_ms = acc[PH_REFINE];
         stats->F_before_refine = refine ? Fh[1] : Fh[0];
         stats->mp_bytes = mp_bytes + mp_bytes_host;
+        stats->pp1_spmv_cfg = dt_cfg;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);

@@ -82,6 +82,12 @@ void Ddc::free_all() {
     }
     f(act_vox);
     f(vox2act);
+    f(act_gpos);
+    act_gpos = nullptr;
+    brick = BrickGrid();
+    tuned = false;
+    win_cfg = -1;
+    win_ncols = win_nseg = 0;
     f(D_val_f32);
     D_val_f32 = nullptr;
     f(scale);
@@ -343,6 +349,7 @@ vmat_status ddc_info(vmat_ddc hd, vmat_ddc_info *out) {
         (m == &h->D ? out->bytes16_D : out->bytes16_Dt) = b;
     }
     out->refine_f32 = h->D_val_f32 ? 1 : 0;
+    out->vox_brick = h->brick.on() ? 1 : 0;
     return VMAT_OK;
 }
 

@@ -209,21 +209,21 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
+// Bitonic network over P (a power of two) keys with their values; thread t of a stage
+// takes pair t: the lower index i = 2 t - (t mod stride) and i + stride.
 __device__ __forceinline__ void bitonic_smem(int32_t *k, float *v, int P) {
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                int j = i ^ stride;
-                if (j > i) {
-                    bool up = (i & size) == 0;
-                    int32_t a = k[i], b = k[j];
-                    if ((a > b) == up) {
-                        k[i] = b;
-                        k[j] = a;
-                        float t = v[i];
-                        v[i] = v[j];
-                        v[j] = t;
-                    }
+            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                const bool up = (i & size) == 0;
+                const int32_t a = k[i], b = k[j];
+                if ((a > b) == up) {
+                    k[i] = b;
+                    k[j] = a;
+                    const float w = v[i];
+                    v[i] = v[j];
+                    v[j] = w;
                 }
             }
             __syncthreads();
@@ -231,7 +231,138 @@ __device__ __forceinline__ void bitonic_smem(int32_t *k, float *v, int P) {
     }
 }
 
-__global__ void row_sort_smem(const int64_t *rowptr, int32_t *col, float *val, int32_t n_rows, int cap,
+// Column (voxel) of every entry to its brick position.
+__global__ void cols_to_brick(int32_t *col, int64_t n, BrickGrid b) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        col[e] = brick_pos(b, col[e]);
+}
+
+__global__ void map_to_brick(const int32_t *vox, int32_t n, BrickGrid b, int32_t *pos) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        pos[i] = brick_pos(b, vox[i]);
+}
+
+// Rows of up to RR_CAP entries: stable LSD radix sort by column in shared memory, a block
+// per row, 8-bit digits of (col - the row's least col), as many passes as the row's column
+// range needs.  Warp w holds entries [w RR_CAP / RR_WARPS, (w + 1) RR_CAP / RR_WARPS) of the
+// row, 32 consecutive per round; a warp's running digit counts (match_any ranks) and the
+// counts of the warps before it place each entry after every earlier entry of its digit,
+// so each pass is stable and the result is the row sorted by column (ties, which the
+// build rejects as duplicates, keep their order).  Sets DEV_DUPLICATE on equal neighbours.
+constexpr int RR_THREADS = 256, RR_WARPS = RR_THREADS / 32, RR_CAP = 2048, RR_ITEMS = RR_CAP / RR_THREADS;
+__global__ void __launch_bounds__(RR_THREADS)
+    row_radix_sort(const int64_t *rowptr, int32_t *col, float *val, int32_t n_rows, int32_t *bad) {
+    __shared__ int32_t wcnt[RR_WARPS][256];
+    __shared__ int32_t bstart[256];
+    __shared__ int32_t wsum[RR_WARPS];
+    __shared__ int32_t red_min[RR_WARPS], red_max[RR_WARPS];
+    extern __shared__ __align__(16) unsigned char rr_dyn[];
+    int32_t *const ka = reinterpret_cast<int32_t *>(rr_dyn), *const kz = ka + RR_CAP;
+    float *const va = reinterpret_cast<float *>(rr_dyn) + 2 * RR_CAP, *const vz = va + RR_CAP;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    for (int32_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
+        const int64_t s = rowptr[r];
+        const int n = (int)(rowptr[r + 1] - s);
+        if (n < 2 || n > RR_CAP) continue;
+        int32_t kmin = INT_MAX, kmax = INT_MIN;
+        for (int i = threadIdx.x; i < n; i += RR_THREADS) {
+            const int32_t k = col[s + i];
+            ka[i] = k;
+            va[i] = val[s + i];
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, d));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+        }
+        if (lane == 0) {
+            red_min[wid] = kmin;
+            red_max[wid] = kmax;
+        }
+        __syncthreads();
+        kmin = red_min[0];
+        kmax = red_max[0];
+        for (int w = 1; w < RR_WARPS; ++w) {
+            kmin = min(kmin, red_min[w]);
+            kmax = max(kmax, red_max[w]);
+        }
+        const uint32_t range = (uint32_t)(kmax - kmin);
+        int32_t *kin = ka, *kout = kz;
+        float *vin = va, *vout = vz;
+        for (int shift = 0; shift < 32 && (shift == 0 || (range >> shift) != 0); shift += 8) {
+            for (int i = threadIdx.x; i < RR_WARPS * 256; i += RR_THREADS) (&wcnt[0][0])[i] = 0;
+            __syncthreads();
+            int32_t key[RR_ITEMS], rk[RR_ITEMS];
+            float v[RR_ITEMS];
+#pragma unroll
+            for (int u = 0; u < RR_ITEMS; ++u) {
+                const int e = wid * (RR_CAP / RR_WARPS) + u * 32 + lane;
+                const bool ok = e < n;
+                key[u] = ok ? kin[e] : 0;
+                v[u] = ok ? vin[e] : 0.f;
+                const int d = ok ? (int)(((uint32_t)(key[u] - kmin) >> shift) & 255u) : 256;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int lower = __popc(peers & below);
+                const int c0 = ok ? wcnt[wid][d] : 0;
+                __syncwarp();
+                rk[u] = c0 + lower;
+                if (ok && lower == 0) wcnt[wid][d] = c0 + __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            // digit t: offsets of the warps within it, its total, then an exclusive scan of the totals
+            const int t = threadIdx.x; // RR_THREADS == 256 digits
+            int32_t acc = 0;
+            for (int w = 0; w < RR_WARPS; ++w) {
+                const int32_t c = wcnt[w][t];
+                wcnt[w][t] = acc;
+                acc += c;
+            }
+            int32_t inc = acc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += o;
+            }
+            if (lane == 31) wsum[wid] = inc;
+            __syncthreads();
+            int32_t before = 0;
+            for (int w = 0; w < wid; ++w) before += wsum[w];
+            bstart[t] = before + inc - acc;
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < RR_ITEMS; ++u) {
+                const int e = wid * (RR_CAP / RR_WARPS) + u * 32 + lane;
+                if (e < n) {
+                    const int d = (int)(((uint32_t)(key[u] - kmin) >> shift) & 255u);
+                    const int pos = bstart[d] + wcnt[wid][d] + rk[u];
+                    kout[pos] = key[u];
+                    vout[pos] = v[u];
+                }
+            }
+            __syncthreads();
+            int32_t *kt = kin;
+            kin = kout;
+            kout = kt;
+            float *vt = vin;
+            vin = vout;
+            vout = vt;
+        }
+        for (int i = threadIdx.x; i < n; i += RR_THREADS) {
+            const int32_t k = kin[i];
+            col[s + i] = k;
+            val[s + i] = vin[i];
+            if (i > 0 && k == kin[i - 1]) atomicOr(bad, DEV_DUPLICATE);
+        }
+        __syncthreads();
+    }
+}
+
+// Sorts the rows with lo < n <= cap entries (n >= 2), a block per row in shared memory.
+__global__ void row_sort_smem(const int64_t *rowptr, int32_t *col, float *val, int32_t n_rows, int lo, int cap,
                               int32_t *bad) {
     extern __shared__ __align__(16) unsigned char sm[];
     int32_t *k = reinterpret_cast<int32_t *>(sm);
@@ -239,7 +370,7 @@ __global__ void row_sort_smem(const int64_t *rowptr, int32_t *col, float *val, i
     for (int32_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
         int64_t s = rowptr[r];
         int n = (int)(rowptr[r + 1] - s);
-        if (n < 2 || n > cap) continue;
+        if (n < 2 || n <= lo || n > cap) continue;
         int P = 1;
         while (P < n) P <<= 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -352,19 +483,6 @@ __global__ void to_fp8_by_row(const float *in, const int64_t *rowptr, int32_t n_
     }
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
-    void *release() {
-        void *q = p;
-        p = nullptr;
-        return q;
-    }
-};
-
 int grid_for(int64_t n, int n_sm) {
     int64_t g = (n + BUILD_THREADS - 1) / BUILD_THREADS;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)n_sm * 16));
@@ -459,11 +577,22 @@ vmat_status sort_rows(const int64_t *rowptr, const int32_t *cnt, int32_t n_rows,
     int cap_max = sort_smem_cap();
     int cap = 32;
     while (cap < maxlen && cap < cap_max) cap <<= 1;
-    size_t smem = (size_t)cap * 8;
-    VMAT_CUDA(cudaFuncSetAttribute(row_sort_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // rows up to RR_CAP entries by the radix sort (unless a smaller cap is forced), the longer
+    // ones (up to cap) by the bitonic network in a second launch, so that a few long rows do not
+    // set every block's shared memory
     int grid = (int)std::min<int64_t>(n_rows, (int64_t)n_sm * 8);
-    row_sort_smem<<<grid, BUILD_THREADS, smem, s>>>(rowptr, col, val, n_rows, cap, bad);
-    VMAT_LAUNCH_CHECK();
+    int cap1 = 0;
+    if (cap_max >= RR_CAP) {
+        cap1 = RR_CAP;
+        VMAT_CUDA(cudaFuncSetAttribute(row_radix_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, RR_CAP * 16));
+        row_radix_sort<<<grid, RR_THREADS, (size_t)RR_CAP * 16, s>>>(rowptr, col, val, n_rows, bad);
+        VMAT_LAUNCH_CHECK();
+    }
+    if (cap > cap1) {
+        VMAT_CUDA(cudaFuncSetAttribute(row_sort_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, cap * 8));
+        row_sort_smem<<<grid, BUILD_THREADS, (size_t)cap * 8, s>>>(rowptr, col, val, n_rows, cap1, cap, bad);
+        VMAT_LAUNCH_CHECK();
+    }
     if (maxlen > cap) {
         DevBuf blist;
         VMAT_CUDA(blist.alloc((size_t)n_rows * 4));
@@ -555,8 +684,22 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     clear_error();
     if (!hd) return set_error(VMAT_EINVAL, "ddc_build: handle is NULL");
     Ddc *h = as_ddc(hd);
-    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0, -1, 0};
+    vmat_build_opts opts = {VMAT_F32, 1, 1, -1, 0, 0, 0, -1, 0, {0, 0, 0}};
     if (opts_in) opts = *opts_in;
+    BrickGrid brick;
+    if (opts.vox_grid[0] || opts.vox_grid[1] || opts.vox_grid[2]) {
+        const int32_t nx = opts.vox_grid[0], ny = opts.vox_grid[1], nz = opts.vox_grid[2];
+        if (nx <= 0 || ny <= 0 || nz <= 0 || (int64_t)nx * ny * nz != (int64_t)h->V)
+            return set_error(VMAT_EINVAL, "ddc_build: vox_grid {%d, %d, %d} does not give V = %d voxels", nx, ny, nz,
+                             h->V);
+        brick.nx = nx;
+        brick.ny = ny;
+        brick.nz = nz;
+        brick.nbx = (nx + 3) / 4;
+        brick.nby = (ny + 3) / 4;
+        brick.n_pos = (int64_t)brick.nbx * brick.nby * ((nz + 1) / 2) * 32;
+        if (brick.n_pos > INT32_MAX) return set_error(VMAT_EINVAL, "ddc_build: vox_grid padded to bricks exceeds 2^31 voxels");
+    }
     if (opts.dtype != VMAT_F32 && opts.dtype != VMAT_BF16 && opts.dtype != VMAT_FP8E4M3)
         return set_error(VMAT_EINVAL, "ddc_build: unknown dtype %d", (int)opts.dtype);
     if (!opts.build_D && !opts.build_Dt) return set_error(VMAT_EINVAL, "ddc_build: nothing to build");
@@ -674,8 +817,14 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     if (scatter_t)
         VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s,
                            &max_row_t));
-    else if (opts.build_Dt)
+    else if (opts.build_Dt && !brick.on())
         VMAT_TRY(longest_row(cnt_blt, J, n_sm, s, &max_row_t)); // already in order: nothing to sort
+    if (opts.build_Dt && brick.on() && nnz > 0) { // columns to brick positions, each row sorted again by them
+        cols_to_brick<<<grid_for(nnz, n_sm), BUILD_THREADS, 0, s>>>((int32_t *)b_col_t.p, nnz, brick);
+        VMAT_LAUNCH_CHECK();
+        VMAT_TRY(sort_rows((int64_t *)b_rp_t.p, cnt_blt, J, (int32_t *)b_col_t.p, (float *)b_val_t.p, bad, n_sm, s,
+                           &max_row_t));
+    }
     if (scatter_d) {
         VMAT_TRY(sort_rows((int64_t *)b_rp_d.p, (int32_t *)b_cnt_act.p, n_active, (int32_t *)b_col_d.p,
                            (float *)b_val_d.p, bad, n_sm, s, &max_row_d));
@@ -725,7 +874,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     if (opts.build_Dt) {
         CsrMat &m = h->Dt;
         m.n_rows = J;
-        m.n_cols = V;
+        m.n_cols = brick.on() ? (int32_t)brick.n_pos : V;
         m.nnz = nnz;
         m.nnz_pad = pad;
         VMAT_TRY(quantise(b_val_t, (int32_t *)b_col_t.p, (int64_t *)b_rp_t.p, J, true, &m.val));
@@ -751,6 +900,14 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         h->act_vox = (int32_t *)b_act.release();
         h->vox2act = (int32_t *)b_v2a.release();
         h->n_active = n_active;
+        if (brick.on()) {
+            VMAT_CUDA(cudaMalloc(&h->act_gpos, (size_t)std::max(n_active, 1) * 4));
+            if (n_active > 0) {
+                map_to_brick<<<grid_for(n_active, n_sm), BUILD_THREADS, 0, s>>>(h->act_vox, n_active, brick,
+                                                                                h->act_gpos);
+                VMAT_LAUNCH_CHECK();
+            }
+        }
         m.row_ids = h->act_vox;
         m.max_row = max_row_d;
         if (opts.index16) VMAT_TRY(csr_build_index16(m, n_sm, s));
@@ -762,6 +919,7 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
         VMAT_CUDA(cudaMalloc(&h->xs, (size_t)J * 4));
     }
     h->dtype = opts.dtype;
+    h->brick = brick;
     if (!opts.keep_coo) {
         VMAT_CUDA(cudaStreamSynchronize(s));
         cudaFree(h->coo_vox);

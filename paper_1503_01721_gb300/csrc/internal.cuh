@@ -66,6 +66,20 @@ struct Scratch {
     vmat_status alloc(size_t bytes, cudaStream_t s);
 };
 
+// Device buffer freed at scope exit unless released (build and set-up steps).
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
+    void *release() {
+        void *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // CSR matrix held by a handle
 // ---------------------------------------------------------------------------
@@ -99,6 +113,22 @@ struct CsrMat {
     int32_t *n_list = nullptr;   // [1]
 };
 
+// Brick order of the voxels (build option vox_grid): bricks of 4 x 4 x 2 voxels, one
+// 128-byte line of a float vector each, in x-fastest order over the grid padded up to
+// whole bricks; inside a brick x fastest, then y, then z.
+struct BrickGrid {
+    int32_t nx = 0, ny = 0, nz = 0; // 0: voxel order
+    int32_t nbx = 0, nby = 0;       // bricks along x and y
+    int64_t n_pos = 0;              // positions: whole bricks x 32
+    bool on() const { return nx > 0; }
+};
+__host__ __device__ __forceinline__ int32_t brick_pos(const BrickGrid &b, int32_t v) {
+    const int32_t x = v % b.nx, yz = v / b.nx;
+    const int32_t y = yz % b.ny, z = yz / b.ny;
+    const int32_t brick = ((z >> 1) * b.nby + (y >> 2)) * b.nbx + (x >> 2);
+    return brick * 32 + (((z & 1) << 4) | ((y & 3) << 2) | (x & 3));
+}
+
 struct Ddc {
     int32_t V = 0, J = 0;
     int64_t nnz = 0;
@@ -111,6 +141,15 @@ struct Ddc {
     int32_t n_active = 0;
     int32_t *act_vox = nullptr; // [n_active] compact row -> voxel
     int32_t *vox2act = nullptr; // [V] voxel -> compact row or -1
+    // Columns of CSR(D^T) in brick order (BrickGrid) when brick.on(): g vectors for it are
+    // indexed by brick_pos, act_gpos maps a compact row to its voxel's position (null: the
+    // columns are voxels and act_vox serves)
+    BrickGrid brick;
+    int32_t *act_gpos = nullptr; // [n_active]
+    // SpMV configuration of windowed D^T g passes (ddc_window_config): found for an MLC
+    // shape (win_ncols, win_nseg; 0 = none yet) on a handle whose configurations were autotuned
+    bool tuned = false;
+    int32_t win_cfg = -1, win_ncols = 0, win_nseg = 0;
     // FP32 values of CSR(D) beside the stored BF16 / FP8 ones (build option refine_f32),
     // same order and padding; the FP32 refinement at the end of cg_plan reads them
     float *D_val_f32 = nullptr;
@@ -138,6 +177,13 @@ struct Ddc {
 vmat_status ddc_cp_table(Ddc &h, int32_t K, int32_t bpc, cudaStream_t s);
 
 inline Ddc *as_ddc(vmat_ddc h) { return reinterpret_cast<Ddc *>(h); }
+
+// Length of a g vector in CSR(D^T)'s column space (act_gpos: where a compact row's g goes).
+inline int64_t g_positions(const Ddc &h) { return h.brick.on() ? h.brick.n_pos : (int64_t)h.V; }
+
+// g in CSR(D^T)'s column space: g itself in voxel order, else a brick-ordered copy in
+// stream-ordered scratch (ws) written on s.
+vmat_status g_for_dt(const Ddc &h, const float *g, Scratch &ws, const float **out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Cross-file entry points (host)
@@ -183,6 +229,12 @@ vmat_status window_offsets(const short2 *win, int32_t nseg, int32_t *woff, const
 vmat_status spmv_run(const Ddc &h, const CsrMat &m, const float *x, float *y, const float *row_scale, RowMask mask,
                      cudaStream_t s, const int32_t *skip = nullptr);
 vmat_status spmv_prepare_tiles(CsrMat &m, int cfg, cudaStream_t s);
+// The configuration for D^T g passes over leaf-travel windows of an MLC with n_cols columns and
+// nseg = K n_rows rows: the handle's own unless it was autotuned; then every warp-row
+// configuration (and the handle's) is timed once on a pass over the middle half of every MLC
+// row and the fastest kept for that shape.  Allocates device memory and synchronises the
+// first time for a shape: not for use while capturing.
+vmat_status ddc_window_config(Ddc &h, int32_t n_cols, int32_t nseg, cudaStream_t s, int *cfg);
 // Does configuration cfg read the 16-bit column index (and so need m.col16)?
 bool spmv_config_index16(int cfg);
 // Builds m.col16 / cbase / cptr when every chunk fits 16 bits (else leaves them null).
@@ -319,6 +371,7 @@ struct ObjPlan { // one plan's compact dose and labels for the batched gradient
     const float *T, *wo, *wu;
     float *g_scatter;
     const int32_t *skip;
+    const int32_t *gpos; // where g goes in g_scatter (null: at idx, the voxel)
 };
 vmat_status objective_grad_batched(const ObjPlan *plans, const int64_t *off, int32_t n_plans, int64_t total,
                                    cudaStream_t s);
@@ -340,7 +393,7 @@ vmat_status objective_impl(int32_t n, const float *z, const int32_t *idx, const 
 // The same with caller-owned scratch ws (objective_scratch_bytes) and a skip word.
 vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                               float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
-                              const int32_t *skip);
+                              const int32_t *skip, const int32_t *gpos = nullptr);
 size_t objective_scratch_bytes(int n_sm);
 // F0 = the penalty at zero dose of the voxels without DDC entries (their dose is always 0).
 vmat_status inactive_objective(const Ddc &h, const vmat_voxels *vox, double *F0, cudaStream_t s);

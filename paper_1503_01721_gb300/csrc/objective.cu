@@ -24,12 +24,13 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh) {
     return t; // valid in thread 0
 }
 
-// z[i] is the dose of voxel v = idx ? idx[i] : i.  Writes g[i] (or g_scatter[v]).
+// z[i] is the dose of voxel v = idx ? idx[i] : i.  Writes g[i] (or g_scatter[v], or
+// g_scatter[gpos[i]] when gpos is given: g in brick order).
 __global__ void __launch_bounds__(OBJ_THREADS)
     objective_kernel(int32_t n, const float *__restrict__ z, const int32_t *__restrict__ idx,
                      const uint8_t *__restrict__ sid, const float *T, const float *wo, const float *wu,
                      int32_t n_struct, float *g, float *g_scatter, double *partial, unsigned *counter, double *F,
-                     double F_offset, const int32_t *skip) {
+                     double F_offset, const int32_t *skip, const int32_t *__restrict__ gpos) {
     if (skip && *skip) return;
     __shared__ float sT[256], sO[256], sU[256];
     __shared__ double sh[OBJ_THREADS / 32];
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(OBJ_THREADS)
         const float zi = z[i], t = sT[k];
         if (g || g_scatter) {
             const float gi = -2.f * sO[k] * fmaxf(0.f, zi - t) + 2.f * sU[k] * fmaxf(0.f, t - zi);
-            if (g_scatter) g_scatter[v] = gi;
+            if (g_scatter) g_scatter[gpos ? gpos[i] : v] = gi;
             else g[i] = gi;
         }
         if (F) { // the FP64 objective only when asked for (FP64 is slow on this GPU)
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(OBJ_THREADS)
         const int32_t v = P.idx[i];
         const int k = P.sid[v];
         const float zi = P.z[i], t = P.T[k];
-        P.g_scatter[v] = -2.f * P.wo[k] * fmaxf(0.f, zi - t) + 2.f * P.wu[k] * fmaxf(0.f, t - zi);
+        P.g_scatter[P.gpos ? P.gpos[i] : v] = -2.f * P.wo[k] * fmaxf(0.f, zi - t) + 2.f * P.wu[k] * fmaxf(0.f, t - zi);
     }
 }
 
@@ -146,14 +147,15 @@ size_t objective_scratch_bytes(int n_sm) { return 64 + (size_t)n_sm * 4 * sizeof
 
 vmat_status objective_impl_ws(int32_t n, const float *z, const int32_t *idx, const vmat_voxels *vox, float *g,
                               float *g_scatter, double *F, double F_offset, void *ws, cudaStream_t s,
-                              const int32_t *skip) {
+                              const int32_t *skip, const int32_t *gpos) {
     DeviceCtx *ctx;
     VMAT_TRY(device_ctx(&ctx));
     const int grid = obj_grid(n, ctx->n_sm);
     unsigned *counter = reinterpret_cast<unsigned *>(ws);
     double *partial = reinterpret_cast<double *>(static_cast<char *>(ws) + 64);
     objective_kernel<<<grid, OBJ_THREADS, 0, s>>>(n, z, idx, vox->struct_id, vox->T, vox->w_over, vox->w_under,
-                                                  vox->n_struct, g, g_scatter, partial, counter, F, F_offset, skip);
+                                                  vox->n_struct, g, g_scatter, partial, counter, F, F_offset, skip,
+                                                  gpos);
     VMAT_LAUNCH_CHECK();
     return VMAT_OK;
 }

@@ -997,13 +997,34 @@ vmat_status dose_forward_impl(const Ddc &h, const float *x, float *d, bool compa
     return spmv_run(h, h.D, xin, d, nullptr, all_rows(), s);
 }
 
+// g in voxel order to brick order: a thread per voxel (positions of the padding are never read).
+__global__ void g_to_brick_kernel(const float *__restrict__ g, int32_t V, BrickGrid b, float *__restrict__ gb) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+        gb[brick_pos(b, v)] = g[v];
+}
+
+vmat_status g_for_dt(const Ddc &h, const float *g, Scratch &ws, const float **out, cudaStream_t s) {
+    if (!h.brick.on()) {
+        *out = g;
+        return VMAT_OK;
+    }
+    DeviceCtx *ctx;
+    VMAT_TRY(device_ctx(&ctx));
+    VMAT_TRY(ws.alloc((size_t)h.brick.n_pos * 4, s));
+    float *gb = static_cast<float *>(ws.ptr);
+    g_to_brick_kernel<<<std::max(1, std::min(ctx->n_sm * 8, (h.V + 255) / 256)), 256, 0, s>>>(g, h.V, h.brick, gb);
+    VMAT_LAUNCH_CHECK();
+    *out = gb;
+    return VMAT_OK;
+}
+
 vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
     // Time every configuration on the handle's own matrices and keep the fastest.
     for (CsrMat *m : {&h.Dt, &h.D}) {
         const bool isDt = m == &h.Dt;
         if (isDt ? !h.built_Dt : !h.built_D) continue;
         float *x = nullptr, *y = nullptr;
-        const int32_t nin = isDt ? h.V : h.J;
+        const int32_t nin = isDt ? m->n_cols : h.J;
         const int32_t nout = isDt ? h.J : h.V;
         VMAT_CUDA(cudaMalloc(&x, (size_t)nin * 4));
         VMAT_CUDA(cudaMalloc(&y, (size_t)nout * 4));
@@ -1041,6 +1062,73 @@ vmat_status spmv_autotune(Ddc &h, cudaStream_t s) {
         VMAT_TRY(spmv_prepare_tiles(*m, best, s));
     }
     VMAT_CUDA(cudaStreamSynchronize(s));
+    h.tuned = true;
+    h.win_ncols = h.win_nseg = 0;
+    return VMAT_OK;
+}
+
+// Window [n_cols / 4, n_cols / 4 + max(1, n_cols / 2)) on every MLC row: a typical pass of the
+// plan reads about half of the unoccupied CPs' rows, in runs of neighbouring beamlets.
+__global__ void half_windows_kernel(short2 *win, int32_t nseg, int32_t n_cols) {
+    const short lo = (short)(n_cols / 4), hi = (short)(n_cols / 4 + max(1, n_cols / 2));
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += gridDim.x * blockDim.x)
+        win[q] = make_short2(lo, hi);
+}
+
+vmat_status ddc_window_config(Ddc &h, int32_t n_cols, int32_t nseg, cudaStream_t s, int *cfg) {
+    *cfg = h.Dt.cfg;
+    if (!h.tuned || h.Dt.nnz == 0) return VMAT_OK;
+    if (h.win_ncols == n_cols && h.win_nseg == nseg) {
+        *cfg = h.win_cfg;
+        return VMAT_OK;
+    }
+    DevBuf bw, bo, bx, by;
+    VMAT_CUDA(bw.alloc((size_t)nseg * sizeof(short2)));
+    VMAT_CUDA(bo.alloc((size_t)(nseg + 1) * 4));
+    VMAT_CUDA(bx.alloc((size_t)h.Dt.n_cols * 4));
+    VMAT_CUDA(by.alloc((size_t)h.J * 4));
+    VMAT_CUDA(cudaMemsetAsync(bx.p, 0, (size_t)h.Dt.n_cols * 4, s));
+    short2 *win = static_cast<short2 *>(bw.p);
+    int32_t *woff = static_cast<int32_t *>(bo.p);
+    half_windows_kernel<<<std::max(1, std::min(1024, (nseg + 255) / 256)), 256, 0, s>>>(win, nseg, n_cols);
+    VMAT_LAUNCH_CHECK();
+    VMAT_TRY(window_offsets(win, nseg, woff, nullptr, s));
+    const RowMask mask{nullptr, win, n_cols, n_cols, woff, nseg}; // no CP mask: bpc unused
+    cudaEvent_t a, b;
+    VMAT_CUDA(cudaEventCreate(&a));
+    VMAT_CUDA(cudaEventCreate(&b));
+    int best = h.Dt.cfg;
+    float best_ms = 1e30f;
+    for (int c = 0; c < N_CFG; ++c) {
+        const int fam = kCfgs[c].family;
+        if (c != h.Dt.cfg && !(fam == 1 || fam == 2 || (fam == 3 && h.Dt.col16))) continue;
+        CsrMat m = h.Dt;
+        m.cfg = c; // a warp-row configuration reads no tile structure; the handle's own has its tiles
+        float tot = 0.f;
+        vmat_status st = VMAT_OK;
+        for (int rep = 0; rep < 4 && st == VMAT_OK; ++rep) {
+            cudaEventRecord(a, s);
+            st = spmv_run(h, m, static_cast<const float *>(bx.p), static_cast<float *>(by.p),
+                          h.dtype == VMAT_FP8E4M3 ? h.scale : nullptr, mask, s);
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep >= 1) tot += ms;
+        }
+        if (st == VMAT_OK && tot < best_ms) {
+            best_ms = tot;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    VMAT_CUDA(cudaStreamSynchronize(s));
+    clear_error();
+    h.win_cfg = best;
+    h.win_ncols = n_cols;
+    h.win_nseg = nseg;
+    *cfg = best;
     return VMAT_OK;
 }
 
@@ -1066,8 +1154,12 @@ vmat_status beamlet_price(vmat_ddc hd, const float *g, float *pi, const uint8_t 
     if (!h->built_Dt) return set_error(VMAT_ESTATE, "beamlet_price: CSR(D^T) not built");
     if (cp_active && (beamlets_per_cp <= 0 || h->J % beamlets_per_cp != 0))
         return set_error(VMAT_EINVAL, "beamlet_price: beamlets_per_cp (%d) must divide J (%d)", beamlets_per_cp, h->J);
-    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
-                    RowMask{cp_active, nullptr, cp_active ? beamlets_per_cp : 1, 1}, as_stream(stream));
+    cudaStream_t s = as_stream(stream);
+    Scratch gws;
+    const float *gd;
+    VMAT_TRY(g_for_dt(*h, g, gws, &gd, s));
+    return spmv_run(*h, h->Dt, gd, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
+                    RowMask{cp_active, nullptr, cp_active ? beamlets_per_cp : 1, 1}, s);
 }
 
 vmat_status beamlet_price_windowed(vmat_ddc hd, const vmat_mlc *mlc, const uint8_t *occupied, const int16_t *leaves,
@@ -1089,7 +1181,10 @@ vmat_status beamlet_price_windowed(vmat_ddc hd, const vmat_mlc *mlc, const uint8
     int32_t *woff = reinterpret_cast<int32_t *>(win + nseg);
     VMAT_TRY(price_windows(pg, occupied, leaves, win, h->Dt.rowptr, nullptr, nullptr, nullptr, s));
     VMAT_TRY(window_offsets(win, nseg, woff, nullptr, s));
-    return spmv_run(*h, h->Dt, g, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
+    Scratch gws;
+    const float *gd;
+    VMAT_TRY(g_for_dt(*h, g, gws, &gd, s));
+    return spmv_run(*h, h->Dt, gd, pi, h->dtype == VMAT_FP8E4M3 ? h->scale : nullptr,
                     RowMask{nullptr, win, mlc->n_rows * mlc->n_cols, mlc->n_cols, woff, nseg}, s);
 }
 

@@ -35,8 +35,9 @@ def spmv_bound(abs_terms_sum, row_len=0):
     return (SPMV_C + np.asarray(row_len, np.float64) / 64.0) * U32 * abs_terms_sum + 1e-37
 
 
-def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None, index16=None, refine=False):
-    """index16 None: build the 16-bit column index when tile_cfg reads it."""
+def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None, index16=None, refine=False, brick=False):
+    """index16 None: build the 16-bit column index when tile_cfg reads it.  brick: CSR(D^T)
+    columns in brick order (a case's own grid)."""
     from paper_1503_01721_gb300 import api
     if hasattr(case_or_coo, "vox"):
         c = case_or_coo
@@ -45,5 +46,9 @@ def make_ddc(case_or_coo, dtype="f32", tile_cfg=-1, V=None, J=None, index16=None
         vox, blt, val = case_or_coo
     if index16 is None:
         index16 = tile_cfg in INDEX16_TWIN
+    grid = None
+    if brick:
+        g = case_or_coo.geom
+        grid = (g.nx, g.ny, g.nz)
     return api.Ddc(V, J, dev(vox, torch.int32), dev(blt, torch.int32), dev(val, torch.float32), dtype=dtype,
-                   tile_cfg=tile_cfg, index16=index16, refine=refine)
+                   tile_cfg=tile_cfg, index16=index16, refine=refine, vox_grid=grid)

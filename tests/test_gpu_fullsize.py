@@ -37,9 +37,10 @@ def _cuda():
 def _ddc(c, dtype="f32"):
     from paper_1503_01721_gb300 import api
     t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt)
-    # host COO, autotuned configuration: the bench's build
+    # host COO, autotuned configuration, CSR(D^T) columns in brick order: the bench's build
+    g = c.geom
     return api.Ddc(c.V, c.J, t(c.vox, torch.int32), t(c.blt, torch.int32), t(c.val, torch.float32), dtype=dtype,
-                   autotune=True)
+                   autotune=True, vox_grid=(g.nx, g.ny, g.nz))
 
 
 def _beamlet_offsets(c):
