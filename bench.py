@@ -54,18 +54,12 @@ SPMV_KERNELS = {0: "spmv_tile_kernel<256,16,2>", 1: "spmv_tile_kernel<256,8,3>",
                 13: "spmv_warp_row_z_kernel<256,8>", 14: "spmv_warp_row_z_kernel<512,4>"}
 # configurations that read the 16-bit column index (built with index16)
 INDEX16_CFGS = (12, 13, 14)
-# DRAM traffic over algorithmic bytes of the full D^T g pass on the 128x128x96 case, per (value type,
-# configuration): dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of each kernel.
-# The plan's passes are windowed (the rows inside the leaf-travel windows, taken as one list): their
-# ratio is WINDOWED_TRAFFIC_RATIO, the sum over the 30 windowed launches of the 45-CP plan (the same
-# kernels on a quarter of the CPs) over their algorithmic bytes; a configuration without such a
-# capture reports null.
-WINDOWED_TRAFFIC_RATIO = {("f32", 5): 0.9988, ("f32", 9): 1.0010, ("f32", 11): 1.0009}
-TRAFFIC_RATIO = {("f32", 4): 1.0055, ("f32", 5): 1.0063, ("f32", 6): 1.0032, ("f32", 7): 1.0036,
-                 ("f32", 8): 1.0008, ("f32", 9): 1.0101, ("f32", 10): 1.0082, ("f32", 11): 1.0091,
-                 ("bf16", 5): 1.0083, ("fp8", 5): 1.0082,
-                 # 16-bit index, on the 45-CP case
-                 ("f32", 12): 1.0044}
+# DRAM traffic over algorithmic bytes of the plan's windowed D^T g launches, per (value type,
+# configuration, CSR(D^T) column order): dram__bytes_read.sum + dram__bytes_write.sum over the 30
+# windowed launches of the 45-CP plan (the same kernels on a quarter of the CPs), over their algorithmic
+# bytes, from one ncu capture each; a configuration without such a capture reports null.
+WINDOWED_TRAFFIC_RATIO = {("f32", 5, "voxel"): 0.9988, ("f32", 9, "voxel"): 1.0010, ("f32", 11, "voxel"): 1.0009,
+                          ("f32", 11, "brick"): 1.0038}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
@@ -534,7 +528,7 @@ def run_ours(args, rank, world, local):
     kname = SPMV_KERNELS.get(cfg_dt, f"spmv configuration {cfg_dt}") + \
         (" + spmv_fixup" if cfg_dt < 4 else "") + " (beamlet price D^T g over the unoccupied CPs)"
     bytes_launch = spmv_bytes / max(spmv_n, 1)
-    ratio = WINDOWED_TRAFFIC_RATIO.get((args.dtype, cfg_dt))
+    ratio = WINDOWED_TRAFFIC_RATIO.get((args.dtype, cfg_dt, "brick" if info["vox_brick"] else "voxel"))
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4),
