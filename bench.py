@@ -59,7 +59,7 @@ INDEX16_CFGS = (12, 13, 14)
 # windowed launches of the 45-CP plan (the same kernels on a quarter of the CPs), over their algorithmic
 # bytes, from one ncu capture each; a configuration without such a capture reports null.
 WINDOWED_TRAFFIC_RATIO = {("f32", 5, "voxel"): 0.9988, ("f32", 9, "voxel"): 1.0010, ("f32", 11, "voxel"): 1.0009,
-                          ("f32", 11, "brick"): 1.0038}
+                          ("f32", 9, "brick"): 1.0039, ("f32", 11, "brick"): 1.0038}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5

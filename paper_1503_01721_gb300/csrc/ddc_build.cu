@@ -67,6 +67,43 @@ __global__ void flag_nonzero(const int32_t *cnt, int32_t n, int32_t *flag) {
         flag[i] = cnt[i] > 0 ? 1 : 0;
 }
 
+// Brick order: the voxel at brick position p (the inverse of brick_pos), or -1 for a position
+// of the padding.
+__device__ __forceinline__ int32_t brick_voxel(const BrickGrid &b, int64_t p) {
+    const int64_t brick = p >> 5;
+    const int32_t in = (int32_t)(p & 31);
+    const int32_t bx = (int32_t)(brick % b.nbx), by = (int32_t)((brick / b.nbx) % b.nby);
+    const int32_t bz = (int32_t)(brick / ((int64_t)b.nbx * b.nby));
+    const int32_t x = 4 * bx + (in & 3), y = 4 * by + ((in >> 2) & 3), z = 2 * bz + (in >> 4);
+    if (x >= b.nx || y >= b.ny || z >= b.nz) return -1;
+    return (z * b.ny + y) * b.nx + x;
+}
+
+__global__ void flag_nonzero_brick(const int32_t *cnt, BrickGrid b, int32_t *flag) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < b.n_pos; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = brick_voxel(b, p);
+        flag[p] = v >= 0 && cnt[v] > 0 ? 1 : 0;
+    }
+}
+
+// The compact rows of CSR(D) in brick order: off = the exclusive scan of flag_nonzero_brick.
+__global__ void compact_voxels_brick(const int32_t *cnt_vox, const int64_t *off, BrickGrid b, int32_t *act_vox,
+                                     int32_t *vox2act, int32_t *cnt_act) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < b.n_pos; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = brick_voxel(b, p);
+        if (v < 0) continue;
+        const int32_t c = cnt_vox[v];
+        if (c > 0) {
+            const int32_t a = (int32_t)off[p];
+            act_vox[a] = v;
+            vox2act[v] = a;
+            cnt_act[a] = c;
+        } else {
+            vox2act[v] = -1;
+        }
+    }
+}
+
 __global__ void compact_voxels(const int32_t *cnt_vox, const int64_t *off, int32_t V, int32_t *act_vox,
                                int32_t *vox2act, int32_t *cnt_act) {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
@@ -778,21 +815,31 @@ extern "C" vmat_status ddc_build(vmat_ddc hd, const vmat_build_opts *opts_in, vo
     // ---- CSR(D): rows = voxels with at least one entry
     int32_t n_active = 0;
     if (opts.build_D) {
-        VMAT_CUDA(b_flag.alloc((size_t)V * 4));
-        VMAT_CUDA(b_off.alloc((size_t)(V + 1) * 8));
-        flag_nonzero<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, V, (int32_t *)b_flag.p);
+        // compact rows in voxel order, or in brick order with vox_grid (then a 32-voxel tile of
+        // the master problem is a 4 x 4 x 2 brick, and g is written almost in order)
+        const int32_t npos = brick.on() ? (int32_t)brick.n_pos : V;
+        VMAT_CUDA(b_flag.alloc((size_t)npos * 4));
+        VMAT_CUDA(b_off.alloc((size_t)(npos + 1) * 8));
+        if (brick.on())
+            flag_nonzero_brick<<<grid_for(npos, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, brick, (int32_t *)b_flag.p);
+        else
+            flag_nonzero<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, V, (int32_t *)b_flag.p);
         VMAT_LAUNCH_CHECK();
-        VMAT_TRY(scan_counts((int32_t *)b_flag.p, (int64_t *)b_off.p, V, s));
+        VMAT_TRY(scan_counts((int32_t *)b_flag.p, (int64_t *)b_off.p, npos, s));
         int64_t na = 0;
-        VMAT_CUDA(cudaMemcpyAsync(&na, (int64_t *)b_off.p + V, 8, cudaMemcpyDeviceToHost, s));
+        VMAT_CUDA(cudaMemcpyAsync(&na, (int64_t *)b_off.p + npos, 8, cudaMemcpyDeviceToHost, s));
         VMAT_CUDA(cudaStreamSynchronize(s));
         n_active = (int32_t)na;
         VMAT_CUDA(b_act.alloc((size_t)std::max(n_active, 1) * 4));
         VMAT_CUDA(b_v2a.alloc((size_t)V * 4));
         VMAT_CUDA(b_cnt_act.alloc((size_t)std::max(n_active, 1) * 4));
-        compact_voxels<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, (int64_t *)b_off.p, V,
-                                                                  (int32_t *)b_act.p, (int32_t *)b_v2a.p,
-                                                                  (int32_t *)b_cnt_act.p);
+        if (brick.on())
+            compact_voxels_brick<<<grid_for(npos, n_sm), BUILD_THREADS, 0, s>>>(
+                cnt_vox, (int64_t *)b_off.p, brick, (int32_t *)b_act.p, (int32_t *)b_v2a.p, (int32_t *)b_cnt_act.p);
+        else
+            compact_voxels<<<grid_for(V, n_sm), BUILD_THREADS, 0, s>>>(cnt_vox, (int64_t *)b_off.p, V,
+                                                                      (int32_t *)b_act.p, (int32_t *)b_v2a.p,
+                                                                      (int32_t *)b_cnt_act.p);
         VMAT_LAUNCH_CHECK();
         VMAT_CUDA(b_rp_d.alloc((size_t)(n_active + 1) * 8));
         VMAT_TRY(scan_counts((int32_t *)b_cnt_act.p, (int64_t *)b_rp_d.p, n_active, s));
