@@ -371,6 +371,13 @@ vmat_status fluence_bounds(const vmat_mlc *mlc, int32_t n_ap, const int32_t *cps
  * int16 [n_apertures][n_rows][2], y_out float [n_apertures], dose_out float
  * [V].  F_out: host double.  stats: host struct or NULL.  Needs build_D and
  * build_Dt.  Synchronises.
+ * Device scratch: the call's working arrays (about 2 x the DA matrix plus O(V + J))
+ * come from the handle's cache of earlier calls' blocks of the same sizes, else from
+ * cudaMalloc, and return to that cache (at most 8 GiB; ddc_free and ddc_build release
+ * it) after the call has synchronised its stream.  The first call for an MLC shape
+ * also builds the handle's CP tables and, on an autotuned handle, times the windowed
+ * D^T g configurations; calls on one handle from several host threads must not
+ * overlap.
  * FP32 refinement (BF16 / FP8 handles built with refine_f32): after the last
  * aperture, every placed aperture's dose vector DA (Eq. 5) is recomputed from
  * the FP32 values, the master problem is solved again on those columns (warm

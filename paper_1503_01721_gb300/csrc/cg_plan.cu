@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace vmat {
@@ -55,20 +57,77 @@ __global__ void cp_offsets(const int64_t *rowptr, int32_t K, int32_t bpc, int64_
 
 namespace {
 
+// Device scratch of one cg_plan call.  Blocks come from the handle's cache of earlier calls'
+// blocks (same size) when it holds one, else from cudaMalloc; at the end of the call the
+// stream is synchronised and the blocks go back to the cache (at most PLAN_CACHE_BYTES in
+// all; the rest are freed), so a plan repeated on a handle allocates nothing.
+constexpr size_t PLAN_CACHE_BYTES = (size_t)8 << 30;
+std::mutex g_plan_cache_mu;
+
 struct DevArena {
-    std::vector<void *> ptrs;
+    Ddc &h;
+    cudaStream_t s;
+    std::vector<std::pair<size_t, void *>> got;
+    DevArena(Ddc &h_, cudaStream_t s_) : h(h_), s(s_) {}
     ~DevArena() {
-        for (void *p : ptrs) cudaFree(p);
+        if (got.empty()) return;
+        cudaStreamSynchronize(s); // nothing of this call still runs on its blocks
+        std::lock_guard<std::mutex> lk(g_plan_cache_mu);
+        size_t held = 0;
+        for (auto &b : h.plan_blocks) held += b.first;
+        for (auto &b : got) {
+            if (held + b.first <= PLAN_CACHE_BYTES) {
+                h.plan_blocks.push_back(b);
+                held += b.first;
+            } else {
+                cudaFree(b.second);
+            }
+        }
     }
     template <typename T> vmat_status get(T **out, size_t n) {
+        const size_t bytes = std::max<size_t>(n * sizeof(T), 16);
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, std::max<size_t>(n * sizeof(T), 16));
-        if (e != cudaSuccess)
-            return set_error(e == cudaErrorMemoryAllocation ? VMAT_ENOMEM : VMAT_ECUDA, "cg_plan: %s",
-                             cudaGetErrorString(e));
-        ptrs.push_back(p);
+        {
+            std::lock_guard<std::mutex> lk(g_plan_cache_mu);
+            for (size_t i = 0; i < h.plan_blocks.size(); ++i)
+                if (h.plan_blocks[i].first == bytes) {
+                    p = h.plan_blocks[i].second;
+                    h.plan_blocks.erase(h.plan_blocks.begin() + (std::ptrdiff_t)i);
+                    break;
+                }
+        }
+        if (!p) {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess)
+                return set_error(e == cudaErrorMemoryAllocation ? VMAT_ENOMEM : VMAT_ECUDA, "cg_plan: %s",
+                                 cudaGetErrorString(e));
+        }
+        got.emplace_back(bytes, p);
         *out = static_cast<T *>(p);
         return VMAT_OK;
+    }
+};
+
+// The handle's pinned control block when no other call holds it, else one of this call's own.
+struct HostCtl {
+    Ddc &h;
+    int32_t *p = nullptr;
+    bool own = false;
+    explicit HostCtl(Ddc &h_) : h(h_) {}
+    vmat_status get() {
+        {
+            std::lock_guard<std::mutex> lk(g_plan_cache_mu);
+            p = h.plan_hctl;
+            h.plan_hctl = nullptr;
+        }
+        if (!p) VMAT_CUDA(cudaMallocHost(&p, CTL_N * sizeof(int32_t)));
+        return VMAT_OK;
+    }
+    ~HostCtl() {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(g_plan_cache_mu);
+        if (!h.plan_hctl) h.plan_hctl = p;
+        else cudaFreeHost(p);
     }
 };
 
@@ -136,7 +195,7 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     const int nap_max = std::max(n_apertures, 1);
     const int g256 = std::max(1, ctx->n_sm * 4);
 
-    DevArena ar;
+    DevArena ar(h, s);
     float *z_c, *g_full, *pi, *DA, *y, *x, *dose;
     uint8_t *occupied, *active, *sid_c;
     int16_t *leaves_all, *best_leaves, *leaves_seq;
@@ -278,12 +337,9 @@ extern "C" vmat_status cg_plan(vmat_ddc hd, const vmat_mlc *mlc, const vmat_voxe
     const int vb = value_bytes(h.dtype);
     const double bytes_D_full = csr_pass_bytes(h.D.cfg, vb, (double)h.D.nnz, h.D.n_rows + 1.0, (double)h.D.n_chunks) +
                                 4.0 * J + 4.0 * V + (h.dtype == VMAT_FP8E4M3 ? 4.0 * J : 0.0);
-    int32_t *hctl;
-    VMAT_CUDA(cudaMallocHost(&hctl, CTL_N * sizeof(int32_t)));
-    struct FreeCtl {
-        int32_t *p;
-        ~FreeCtl() { cudaFreeHost(p); }
-    } fc{hctl};
+    HostCtl hc(h);
+    VMAT_TRY(hc.get());
+    int32_t *const hctl = hc.p;
 
     for (int t = 0; t < n_apertures; ++t) {
         if (t + 1 > n_cap) { // past the persistent solver's limit: the host decides whether to go on

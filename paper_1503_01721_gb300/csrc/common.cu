@@ -88,6 +88,10 @@ void Ddc::free_all() {
     tuned = false;
     win_cfg = -1;
     win_ncols = win_nseg = 0;
+    for (auto &b : plan_blocks) cudaFree(b.second);
+    plan_blocks.clear();
+    if (plan_hctl) cudaFreeHost(plan_hctl);
+    plan_hctl = nullptr;
     f(D_val_f32);
     D_val_f32 = nullptr;
     f(scale);

@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
+#include <utility>
+#include <vector>
 #include <stdint.h>
 
 #include <atomic>
@@ -150,6 +152,10 @@ struct Ddc {
     // shape (win_ncols, win_nseg; 0 = none yet) on a handle whose configurations were autotuned
     bool tuned = false;
     int32_t win_cfg = -1, win_ncols = 0, win_nseg = 0;
+    // Device blocks (size, pointer) and a pinned host control block of finished cg_plan
+    // calls, kept for the next call on this handle (guarded by the plan cache's mutex)
+    std::vector<std::pair<size_t, void *>> plan_blocks;
+    int32_t *plan_hctl = nullptr;
     // FP32 values of CSR(D) beside the stored BF16 / FP8 ones (build option refine_f32),
     // same order and padding; the FP32 refinement at the end of cg_plan reads them
     float *D_val_f32 = nullptr;
