@@ -944,48 +944,48 @@ vmat_status price_windows(const PricingGeom &g, const uint8_t *occupied, const i
     return VMAT_OK;
 }
 
-// Exclusive scan of the window lengths (one block of WO_THREADS): each thread sums a
-// contiguous run of segments, a block scan of the run totals (warp scans, then the warp
-// totals), then each thread writes its run's offsets.
-constexpr int WO_THREADS = 1024;
+// Exclusive scan of the window lengths (one block of WO_THREADS): warp w takes the
+// contiguous block of segments [w per, (w + 1) per), 32 consecutive ones per step (one
+// coalesced load), first to total its block, then, after a scan of the warp totals, to
+// write each segment's offset (warp scan per step, the running sum carried in lane 31).
+constexpr int WO_THREADS = 1024, WO_WARPS = WO_THREADS / 32;
 __global__ void __launch_bounds__(WO_THREADS)
     window_offsets_kernel(const short2 *__restrict__ win, int32_t nseg, int32_t *__restrict__ woff,
                           const int32_t *skip) {
     if (skip && *skip) return;
-    __shared__ int32_t wsum[WO_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (nseg + WO_THREADS - 1) / WO_THREADS;
-    const int q0 = min(tid * per, nseg), q1 = min(q0 + per, nseg);
-    int32_t run = 0;
-    for (int q = q0; q < q1; ++q) {
+    __shared__ int32_t wsum[WO_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int per = (nseg + WO_WARPS - 1) / WO_WARPS;
+    const int q0 = min(wid * per, nseg), q1 = min(q0 + per, nseg);
+    auto len = [&](int q) -> int32_t {
+        if (q >= q1) return 0;
         const short2 w = win[q];
-        run += max(0, (int)w.y - (int)w.x);
-    }
-    int32_t incl = run; // inclusive scan of the run totals within the warp
+        return max(0, (int)w.y - (int)w.x);
+    };
+    int32_t tot = 0;
+    for (int q = q0 + lane; q < q1; q += 32) tot += len(q);
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
-    }
-    if (lane == 31) wsum[wid] = incl;
+    for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+    if (lane == 0) wsum[wid] = tot;
     __syncthreads();
-    if (wid == 0) {
-        int32_t v = wsum[lane], x = v;
+    int32_t base = 0;
+    for (int w = 0; w < wid; ++w) base += wsum[w];
+    for (int q = q0; q < q1; q += 32) {
+        const int32_t v = len(q + lane);
+        int32_t incl = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int32_t o = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += o;
+            const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
         }
-        wsum[lane] = x - v; // exclusive prefix of the warp totals
+        if (q + lane < q1) woff[q + lane] = base + incl - v;
+        base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    __syncthreads();
-    int32_t off = wsum[wid] + incl - run;
-    for (int q = q0; q < q1; ++q) {
-        woff[q] = off;
-        const short2 w = win[q];
-        off += max(0, (int)w.y - (int)w.x);
+    if (wid == WO_WARPS - 1 && lane == 0) { // every segment counted: the total
+        int32_t all = 0;
+        for (int w = 0; w < WO_WARPS; ++w) all += wsum[w];
+        woff[nseg] = all;
     }
-    if (tid == WO_THREADS - 1) woff[nseg] = off;
 }
 
 vmat_status window_offsets(const short2 *win, int32_t nseg, int32_t *woff, const int32_t *skip, cudaStream_t s) {
