@@ -60,6 +60,16 @@ INDEX16_CFGS = (12, 13, 14)
 # bytes, from one ncu capture each; a configuration without such a capture reports null.
 WINDOWED_TRAFFIC_RATIO = {("f32", 5, "voxel"): 0.9988, ("f32", 9, "voxel"): 1.0010, ("f32", 11, "voxel"): 1.0009,
                           ("f32", 9, "brick"): 1.0039, ("f32", 11, "brick"): 1.0038}
+# The paper's own plan times (Table 2 and Table 3): other hardware, patient data and aperture
+# counts, so context for the line, not a baseline of its metric.
+PAPER_CONTEXT = {
+    "plan_total_s": 63.96, "t_pp1_s": 10.77, "t_pp2_s": 5.05, "t_mp_s": 21.24,
+    "workload": "head-and-neck case P1: 26,828 voxels, 128,516 beamlets, 608,447,419 nonzeros, 199 apertures, "
+                "9,364 BB iterations",
+    "hardware": "4x GTX 590 (Fermi, CUDA 4.0); PP2 and the DA vectors partly on the CPU",
+    "other_cases_total_s": [31.50, 37.36, 39.77, 45.46, 23.28],
+    "cpu_plan_total_s": 360.85, "cpu": "the paper's CPU version, pthreads on 4 cores / 8 threads",
+}
 # CPU sample: every 12th CP of the same geometry (15 CPs), 5 apertures
 SAMPLE_CP_STRIDE = 12
 SAMPLE_APERTURES = 5
@@ -660,6 +670,7 @@ def run_ours(args, rank, world, local):
                      "build_ms": round(info["build_ms"], 1)},
             "spmv_pair": pair,
             "mp_roofline": mp_roof,
+            "paper_context": PAPER_CONTEXT,
             "forms": forms,
         }
         out["plan"]["dose_err"] = dose_err
