@@ -233,7 +233,8 @@ vmat_status dose_forward(vmat_ddc h, const float *x, float *d, void *stream);
  * cp_active[k] != 0 are priced (the paper prices unoccupied CPs only) and
  * entries of inactive CPs are left unspecified.  beamlets_per_cp =
  * n_rows * n_cols (ignored when cp_active is NULL).  FP32 accumulation.
- * Needs build_Dt. */
+ * Needs build_Dt.  On a handle built with vox_grid, g is first copied into
+ * brick order (stream-ordered scratch of 4 bytes per padded voxel). */
 vmat_status beamlet_price(vmat_ddc h, const float *g, float *pi, const uint8_t *cp_active,
                           int32_t beamlets_per_cp, void *stream);
 
@@ -245,7 +246,8 @@ vmat_status beamlet_price(vmat_ddc h, const float *g, float *pi, const uint8_t *
  * entry; they are left unspecified.  mlc: host; occupied: device uint8 [K];
  * leaves: device int16 [K][n_rows][2], (L, R) of the occupied CPs; g: device
  * float [V]; pi: device float [J] with J = K * n_rows * n_cols.  Needs
- * build_Dt.  Allocates K * n_rows * 4 bytes of device scratch (stream-ordered). */
+ * build_Dt.  Allocates K * n_rows * 8 + 4 bytes of device scratch (stream-ordered; on
+ * a handle built with vox_grid also the brick-ordered copy of g, as beamlet_price). */
 vmat_status beamlet_price_windowed(vmat_ddc h, const vmat_mlc *mlc, const uint8_t *occupied, const int16_t *leaves,
                                    const float *g, float *pi, void *stream);
 
